@@ -1,0 +1,621 @@
+"""Pins of the FP64 oracle to facts other than itself (CPU only).
+
+Each test ties one oracle function to a library routine, a conservation law,
+a closed form or a value the paper prints, chosen so that a plausible mistake
+(a dropped term, a wrong sign or index, a transposed operand) fails one of them.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+from scipy import linalg, stats
+from scipy.spatial.transform import Rotation
+
+import workloads as W
+from oracle import mppi, philox, systems
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 and Box-Muller
+# ---------------------------------------------------------------------------
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+@triton.jit
+def k(out, seed, p0, p1, p2, p3, N: tl.constexpr):
+    o = tl.arange(0, N)
+    a, b, c, d = tl.philox(seed, tl.load(p0 + o), tl.load(p1 + o), tl.load(p2 + o), tl.load(p3 + o))
+    tl.store(out + o * 4, a); tl.store(out + o * 4 + 1, b)
+    tl.store(out + o * 4 + 2, c); tl.store(out + o * 4 + 3, d)
+cases = json.loads(sys.stdin.read())
+res = []
+for seed, ctr in cases:
+    N = len(ctr)
+    cols = [torch.tensor([c[j] for c in ctr], dtype=torch.int64).to(torch.uint32) for j in range(4)]
+    out = torch.zeros(4 * N, dtype=torch.uint32)
+    k[(1,)](out, seed, *cols, N=N)
+    res.append([int(v) & 0xffffffff for v in out.to(torch.int64).tolist()])
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_library_implementation():
+    """Philox words equal Triton's philox (an independent library implementation of
+    Salmon et al.'s generator), run by Triton's CPU interpreter."""
+    rng = np.random.default_rng(7)
+    edge = [0, 1, 0xFFFFFFFF, 0x80000000]
+    cases = []
+    for seed in (0, 1, 0xFFFFFFFFFFFFFFFF, 0x0123456789ABCDEF, int(rng.integers(0, 2 ** 63))):
+        ctr = [[a, b, c, d] for a in edge[:2] for b in edge[1:3] for c in edge[2:] for d in edge[::3]]
+        ctr += rng.integers(0, 2 ** 32, size=(16, 4)).tolist()
+        cases.append([seed, ctr[:32]])
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(cases),
+                         capture_output=True, text=True, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    ref = json.loads(out.stdout.strip().splitlines()[-1])
+    for (seed, ctr), words in zip(cases, ref):
+        c = np.array(ctr, dtype=np.uint64)
+        mine = philox.philox4x32_10(c[:, 0], c[:, 1], c[:, 2], c[:, 3], seed & 0xFFFFFFFF, seed >> 32)
+        got = np.stack(mine, axis=1).reshape(-1).astype(np.uint64)
+        assert np.array_equal(got, np.array(words, dtype=np.uint64)), f"seed {seed:#x}"
+
+
+def test_uniform_is_exact_in_fp32_and_inside_unit_interval():
+    w = np.array([0, 1, 511, 512, 0x7FFFFFFF, 0x80000000, 0xFFFFFDFF, 0xFFFFFFFF], dtype=np.uint64)
+    w = np.concatenate([w, np.random.default_rng(1).integers(0, 2 ** 32, 100000).astype(np.uint64)])
+    u = philox.uniform_from_word(w)
+    assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
+    assert u.min() == 2.0 ** -24 and u.max() == 1.0 - 2.0 ** -24
+    assert np.all((u > 0) & (u < 1))
+
+
+def test_normals_are_standard_normal():
+    eps = philox.standard_normals(seed=3, K=4096, T=64, m=4).ravel()   # 1M normals
+    assert abs(eps.mean()) < 5 / math.sqrt(eps.size)
+    assert abs(eps.var() - 1.0) < 5 * math.sqrt(2.0 / eps.size)
+    assert stats.kstest(eps, "norm").pvalue > 1e-4
+    # the two members of a Box-Muller pair are uncorrelated
+    e = philox.standard_normals(seed=3, K=65536, T=1, m=4)[0]
+    assert abs(np.corrcoef(e[0], e[1])[0, 1]) < 5 / math.sqrt(e.shape[1])
+    assert abs(np.corrcoef(e[0], e[2])[0, 1]) < 5 / math.sqrt(e.shape[1])
+
+
+def test_noise_layout_and_counter_streams():
+    # normal index r = i*m + j lives in Philox block r >> 2, lane r & 3, counter (b, k, c, g)
+    T, m, K = 3, 3, 5
+    eps = philox.standard_normals(seed=11, K=K, T=T, m=m, counter=4, gid=9)
+    words = philox.philox_words(11, K, T, m, 4, 9)
+    u = philox.uniform_from_word(words)
+    for i in range(T):
+        for j in range(m):
+            r = i * m + j
+            b, lane = r >> 2, r & 3
+            a_lane = lane & 2
+            rad = math.sqrt(-2 * math.log(u[b, a_lane, 2]))
+            ang = 2 * math.pi * u[b, a_lane + 1, 2]
+            want = rad * (math.cos(ang) if lane % 2 == 0 else math.sin(ang))
+            assert eps[i, j, 2] == pytest.approx(want, rel=1e-14)
+    other = philox.standard_normals(seed=11, K=K, T=T, m=m, counter=5, gid=9)
+    assert not np.any(other == eps)
+
+
+def test_cholesky_and_noise_covariance():
+    S = np.array([[0.5, 0.2, 0.0], [0.2, 0.4, 0.1], [0.0, 0.1, 0.3]])
+    assert np.allclose(philox.cholesky_psd(S), np.linalg.cholesky(S), rtol=0, atol=1e-14)
+    du = philox.exploration_noise(seed=2, K=200000, T=1, Sigma=S, nu=7.0)[0]
+    C = np.cov(du)
+    assert np.allclose(C, 7.0 * S, atol=0.03 * 7.0 * S.max())
+    assert np.array_equal(philox.exploration_noise(0, 8, 2, np.zeros((2, 2)), 10.0), np.zeros((2, 2, 8)))
+
+
+# ---------------------------------------------------------------------------
+# plants
+# ---------------------------------------------------------------------------
+def _cartpole_energy_momentum(x, p):
+    """Lagrangian of a cart with a uniform rod of half-length l (theta from upright)."""
+    mc, mp, l, g = p["mc"], p["mp"], p["l"], p["g"]
+    _, v, th, om = x
+    M = mc + mp
+    ke = 0.5 * M * v ** 2 + mp * l * v * om * np.cos(th) + (2.0 / 3.0) * mp * l * l * om ** 2
+    pe = mp * g * l * np.cos(th)
+    mom = M * v + mp * l * om * np.cos(th)
+    return ke + pe, mom
+
+
+def test_cartpole_equilibria_and_conservation():
+    cp = systems.CartPole(0.02)
+    for th in (0.0, math.pi):
+        x = cp.init([0.3, 0.0, th, 0.0], 1)
+        y = cp.step(x, np.zeros((1, 1)))
+        assert np.allclose(y, x, atol=1e-15)
+    # unforced motion conserves energy and horizontal momentum; Euler's drift is O(dt)
+    errs = []
+    for dt in (2e-3, 1e-3, 5e-4):
+        cp = systems.CartPole(dt)
+        x = cp.init([0.0, 0.4, 2.5, -1.0], 1)
+        E0, P0 = _cartpole_energy_momentum(x, cp.p)
+        for _ in range(int(round(0.5 / dt))):
+            x = cp.step(x, np.zeros((1, 1)))
+        E1, P1 = _cartpole_energy_momentum(x, cp.p)
+        errs.append((abs(E1 - E0).item(), abs(P1 - P0).item()))
+    for a, b in zip(errs, errs[1:]):
+        assert 1.6 < a[0] / b[0] < 2.4          # first order in dt
+    assert errs[-1][0] < 5e-3 and errs[-1][1] < 5e-3
+    # the force enters as d/dt momentum = F
+    cp = systems.CartPole(1e-4)
+    x = cp.init([0.0, 0.0, 1.0, 0.5], 1)
+    _, P0 = _cartpole_energy_momentum(x, cp.p)
+    for _ in range(1000):
+        x = cp.step(x, np.full((1, 1), 2.0))
+    _, P1 = _cartpole_energy_momentum(x, cp.p)
+    assert P1.item() - P0.item() == pytest.approx(2.0 * 0.1, rel=2e-3)
+
+
+def test_cartpole_cost_values():
+    cp = systems.CartPole(0.02)
+    x = cp.init([0.0, 0.0, math.pi, 0.0], 1)
+    assert cp.q(x)[0] == pytest.approx(10 * math.pi ** 2, rel=1e-15)
+    assert cp.q(cp.init([1.0, 2.0, 0.0, 3.0], 1))[0] == pytest.approx(1 + 4 + 9)
+
+
+def _flat_map(n=8, h=1.0, f=lambda X, Y: 0 * X):
+    g = h * np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    return f(X, Y)
+
+
+def test_bilinear_exact_on_bilinear_functions_and_clamped():
+    f = lambda X, Y: 3.0 + 2.0 * X - 0.5 * Y + 0.25 * X * Y
+    M = _flat_map(8, 0.5, f)
+    rng = np.random.default_rng(0)
+    X = rng.uniform(0, 3.5, 1000)
+    Y = rng.uniform(0, 3.5, 1000)
+    assert np.allclose(systems.bilinear(M, 0.0, 0.5, X, Y), f(X, Y), atol=1e-12)
+    # outside the grid the lookup clamps to the edge
+    assert systems.bilinear(M, 0.0, 0.5, np.array([-5.0]), np.array([1.0]))[0] == pytest.approx(f(0.0, 1.0))
+    assert systems.bilinear(M, 0.0, 0.5, np.array([9.0]), np.array([99.0]))[0] == pytest.approx(f(3.5, 3.5))
+
+
+def test_bilinear_error_bound_on_paper_ellipse_cost():
+    """The race-car cost of Sec. V-B, 100 d^2 with d = |(x/13)^2+(y/6)^2-1|, sampled on a grid:
+    bilinear lookup stays within the interpolation bound h^2/8 (|f_xx| + |f_yy|) + h^2/4 |f_xy|."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_costs.json")))["race_car_cost_sec_V_B"]
+    a, b, w = gold["ellipse_a"], gold["ellipse_b"], gold["w_track"]
+    f = lambda X, Y: w * ((X / a) ** 2 + (Y / b) ** 2 - 1.0) ** 2
+    h, origin, n = 0.05, -20.0, 801
+    g = origin + h * np.arange(n)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    M = f(X, Y)
+    rng = np.random.default_rng(1)
+    px = rng.uniform(-15, 15, 20000)
+    py = rng.uniform(-8, 8, 20000)
+    err = np.abs(systems.bilinear(M, origin, h, px, py) - f(px, py))
+    # second derivatives of w e^2, e = x^2/a^2 + y^2/b^2 - 1
+    e = (px / a) ** 2 + (py / b) ** 2 - 1
+    fxx = w * (8 * px ** 2 / a ** 4 + 4 * e / a ** 2)
+    fyy = w * (8 * py ** 2 / b ** 4 + 4 * e / b ** 2)
+    fxy = w * 8 * px * py / (a * a * b * b)
+    bound = h * h / 8 * (np.abs(fxx) + np.abs(fyy)) + h * h / 4 * np.abs(fxy) + 1e-9
+    # the bound uses the curvature at the point; allow the variation of f'' across one cell
+    assert np.all(err <= 1.5 * bound + 1e-6)
+    assert err.max() > 0.05 * bound.max()  # the interpolation is really happening
+
+
+def _car(dt=0.02, **kw):
+    M = np.zeros((16, 16), dtype=np.float32)
+    return systems.Car(dt, M, -100.0, 20.0, **kw)
+
+
+def test_car_straight_line_at_drag_balance():
+    car = _car(0.01)
+    p = car.p
+    v = 6.0
+    thr = (p["Crr"] * v + p["Cd"] * v * v) / p["Cm"]       # drive force equals drag
+    psi = 0.7
+    x = car.init([1.0, -2.0, psi, v, 0.0, 0.0, 0.0], 1)
+    for _ in range(200):
+        x = car.step(x, np.array([[0.0], [thr]]))
+    assert x[0, 0] == pytest.approx(1.0 + 2.0 * v * math.cos(psi), rel=1e-12)
+    assert x[1, 0] == pytest.approx(-2.0 + 2.0 * v * math.sin(psi), rel=1e-12)
+    assert np.allclose(x[2:, 0], [psi, v, 0, 0, 0], atol=1e-12)
+
+
+def test_car_mirror_symmetry():
+    car = _car()
+    rng = np.random.default_rng(4)
+    x = car.init([0.5, 0.3, 0.2, 4.0, 0.4, -0.3, 0.1], 1)
+    xm = x * np.array([[1], [-1], [-1], [1], [-1], [-1], [-1]])
+    for _ in range(50):
+        v = rng.normal(0, 1, (2, 1))
+        x = car.step(x, v)
+        xm = car.step(xm, v * np.array([[-1], [1]]))
+    assert np.allclose(xm, x * np.array([[1], [-1], [-1], [1], [-1], [-1], [-1]]), rtol=1e-12, atol=1e-12)
+
+
+def test_car_linear_bicycle_steady_turn():
+    """Small steady steer: the lateral states settle where the textbook linear bicycle
+    model (cornering stiffness C_a = B*C*D) has its equilibrium."""
+    car = _car()
+    p = car.p
+    vx, delta = 5.0, 0.002
+    L = p["lf"] + p["lr"]
+    Df = p["mu"] * p["m"] * p["g"] * p["lr"] / L
+    Dr = p["mu"] * p["m"] * p["g"] * p["lf"] / L
+    Cf, Cr = p["B"] * p["C"] * Df, p["B"] * p["C"] * Dr
+    m, Iz, lf, lr = p["m"], p["Iz"], p["lf"], p["lr"]
+    # m (vy' + vx r) = Fyf + Fyr ;  Iz r' = lf Fyf - lr Fyr ; linear tyres
+    A = np.array([[-(Cf + Cr) / vx, -(Cf * lf - Cr * lr) / vx - m * vx],
+                  [-(Cf * lf - Cr * lr) / vx, -(Cf * lf * lf + Cr * lr * lr) / vx]])
+    b = -np.array([Cf * delta, Cf * lf * delta])
+    vy_ss, r_ss = np.linalg.solve(A, b)
+    x = car.init([0, 0, 0, vx, vy_ss, r_ss, delta], 1)
+    d = car.deriv(x, np.array([[delta / p["delta_max"]], [0.0]]))
+    scale_vy, scale_r = abs(Cf * delta / m), abs(Cf * lf * delta / Iz)
+    assert abs(d[4, 0]) < 2e-4 * scale_vy      # residual is the tyre nonlinearity, O(delta^3)
+    assert abs(d[5, 0]) < 2e-4 * scale_r
+    assert abs(d[6, 0]) < 1e-12
+
+
+def _quad(dt=0.01, **kw):
+    return systems.Quadrotor(dt, np.array([[100.0, 100.0, 1.0]]), [0, 0, 2.0], **kw)
+
+
+def test_quad_hover_is_equilibrium():
+    qd = _quad()
+    hover = qd.p["mass"] * qd.p["g"] / 4
+    x0 = np.array([1.0, 2.0, 3.0, 0, 0, 0, 0, 0, 0.4, 0, 0, 0])
+    d = qd.deriv(x0[:, None], np.full((4, 1), hover))
+    assert np.allclose(d, 0.0, atol=1e-14)
+
+
+def test_quad_thrust_direction_matches_library_rotation():
+    qd = _quad()
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        ang = rng.uniform(-1.2, 1.2, 3)
+        f = rng.uniform(0.5, 2.0)
+        x = np.zeros(12)
+        x[6:9] = ang
+        d = qd.deriv(x[:, None], np.full((4, 1), f))
+        Rm = Rotation.from_euler("ZYX", [ang[2], ang[1], ang[0]]).as_matrix()
+        want = Rm @ np.array([0, 0, 4 * f / qd.p["mass"]]) - np.array([0, 0, qd.p["g"]])
+        assert np.allclose(d[3:6, 0], want, atol=1e-12)
+
+
+def test_quad_euler_kinematics_match_matrix_exponential():
+    """Isotropic inertia, no torque: body rate omega is constant and the attitude is
+    R(t) = R0 expm(t [omega]x).  The Euler-angle kinematics must reproduce it."""
+    qd = _quad(1e-3, Ixx=3e-3, Iyy=3e-3, Izz=3e-3)
+    om = np.array([0.7, -0.4, 1.1])
+    x = np.zeros(12)
+    x[6:9] = [0.1, -0.2, 0.3]
+    x[9:12] = om
+    hover = qd.p["mass"] * qd.p["g"] / 4
+    X = x[:, None]
+    for _ in range(1000):
+        X = qd.rk4(X, np.full((4, 1), hover))
+    skew = np.array([[0, -om[2], om[1]], [om[2], 0, -om[0]], [-om[1], om[0], 0]])
+    R0 = Rotation.from_euler("ZYX", [0.3, -0.2, 0.1]).as_matrix()
+    R1 = R0 @ linalg.expm(1.0 * skew)
+    got = Rotation.from_euler("ZYX", [X[8, 0], X[7, 0], X[6, 0]]).as_matrix()
+    assert np.allclose(got, R1, atol=1e-9)
+    assert np.allclose(X[9:12, 0], om, atol=1e-12)
+
+
+def test_quad_torque_free_body_conserves_energy_and_momentum():
+    qd = _quad(1e-3)
+    p = qd.p
+    I = np.array([p["Ixx"], p["Iyy"], p["Izz"]])
+    x = np.zeros(12)
+    x[9:12] = [3.0, 0.2, 1.5]
+    X = x[:, None]
+    hover = p["mass"] * p["g"] / 4
+    L0 = I * x[9:12]
+    for _ in range(2000):
+        X = qd.rk4(X, np.full((4, 1), hover))
+    w = X[9:12, 0]
+    assert 0.5 * (I * w * w).sum() == pytest.approx(0.5 * (I * x[9:12] ** 2).sum(), rel=1e-10)
+    assert np.linalg.norm(I * w) == pytest.approx(np.linalg.norm(L0), rel=1e-10)
+    # the torques of the "+" layout: rotor 2 (+y) rolls positive, rotor 3 (-x) pitches positive
+    f = np.full((4, 1), hover)
+    f[1] += 0.1
+    d = qd.deriv(np.zeros((12, 1)), f)
+    assert d[9, 0] == pytest.approx(p["arm"] * 0.1 / p["Ixx"])
+    f = np.full((4, 1), hover)
+    f[2] += 0.1
+    d = qd.deriv(np.zeros((12, 1)), f)
+    assert d[10, 0] == pytest.approx(p["arm"] * 0.1 / p["Iyy"])
+
+
+def test_quad_rk4_is_fourth_order():
+    def run(dt):
+        qd = _quad(dt)
+        X = np.array([0, 0, 5, 1, -1, 0.5, 0.2, -0.1, 0.3, 2.0, -1.0, 0.5])[:, None]
+        f = np.array([[1.5], [1.0], [1.3], [1.1]])
+        for _ in range(int(round(0.4 / dt))):
+            X = qd.rk4(X, f)
+        return X[:, 0]
+
+    ref = run(0.4 / 3200)
+    e1 = np.abs(run(0.4 / 40) - ref).max()
+    e2 = np.abs(run(0.4 / 80) - ref).max()
+    assert 12.0 < e1 / e2 < 20.0
+
+
+def test_quad_obstacle_distance_brute_force():
+    obs = W.quad_forest(0).astype(np.float64)
+    qd = systems.Quadrotor(0.01, obs, W.QUAD_GOAL)
+    rng = np.random.default_rng(2)
+    pts = rng.uniform(-2, 22, (2, 500))
+    x = np.zeros((12, 500))
+    x[0:2] = pts
+    d = qd.obstacle_distance(x)
+    from scipy.spatial.distance import cdist
+    want = (cdist(pts.T, obs[:, :2]) - obs[:, 2][None, :]).min(axis=1)
+    assert np.allclose(d, want, atol=1e-12)
+
+
+def test_quad_cost_weights_are_the_papers():
+    gold = json.load(open(os.path.join(GOLDEN, "paper_costs.json")))["quadrotor_cost_sec_V_C"]
+    goal = np.array([3.0, 4.0, 5.0])
+    qd = systems.Quadrotor(0.01, np.array([[1000.0, 1000.0, 1.0]]), goal, w_crash=gold["w_crash_paper"])
+
+    def cost(x, crashed=False):
+        st = systems.QuadState(x[:, None], np.array([crashed]), np.array([np.inf]))
+        return qd.q(st)[0]
+
+    base = np.zeros(12)
+    base[0:3] = goal
+    c0 = cost(base)
+    d0 = math.hypot(1000 - 3, 1000 - 4) - 1.0
+    assert c0 == pytest.approx(gold["w_obstacle"] * math.exp(-d0 / gold["obstacle_length_scale"]))
+    for idx, key in ((0, "w_px"), (1, "w_py"), (2, "w_pz"), (8, "w_yaw"), (3, "w_velocity"), (5, "w_velocity")):
+        x = base.copy()
+        x[idx] += 0.5
+        extra = 0.0
+        if idx in (0, 1):   # moving the vehicle also changes its obstacle distance
+            xx = x.copy()
+            dd = math.hypot(1000 - xx[0], 1000 - xx[1]) - 1.0
+            extra = gold["w_obstacle"] * (math.exp(-dd / gold["obstacle_length_scale"])) - c0
+        assert cost(x) - c0 - extra == pytest.approx(gold[key] * 0.25, rel=1e-9)
+    assert cost(base, True) - c0 == pytest.approx(gold["w_crash_paper"])
+    # the workload's own crash weight is ten times the paper's
+    assert systems.QUAD_DEFAULTS["w_crash"] == 10 * gold["w_crash_paper"]
+
+
+def test_quad_crash_freezes_state_and_keeps_charging():
+    qd = _quad()
+    st = qd.init(np.array([0, 0, 0.05, 0, 0, -2.0, 0, 0, 0, 0, 0, 0]), 1)
+    zero = np.zeros((4, 1))
+    xs, crashed = [], []
+    for _ in range(10):
+        st = qd.step(st, zero)
+        xs.append(st.x[:, 0].copy())
+        crashed.append(bool(st.crashed[0]))
+    first = crashed.index(True)
+    assert first > 0
+    for i in range(first, 10):
+        assert np.array_equal(xs[i], xs[first - 1])   # frozen at the last valid state
+        assert xs[i][2] >= 0.0
+    q_crashed = qd.q(st)[0]
+    assert q_crashed >= qd.p["w_crash"]
+
+
+# ---------------------------------------------------------------------------
+# MPPI core
+# ---------------------------------------------------------------------------
+class Linear:
+    """x' = A x + B v with q = x^T Q x and phi = x^T Qf x (the LQ case)."""
+
+    def __init__(self, A, B, Q, Qf):
+        self.A, self.B, self.Q, self.Qf = map(np.asarray, (A, B, Q, Qf))
+        self.n, self.m = self.B.shape
+
+    def init(self, x0, K):
+        return np.repeat(np.asarray(x0, dtype=np.float64)[:, None], K, axis=1)
+
+    def step(self, x, v):
+        return self.A @ x + self.B @ v
+
+    def q(self, x):
+        return np.einsum("ak,ab,bk->k", x, self.Q, x)
+
+    def phi(self, x):
+        return np.einsum("ak,ab,bk->k", x, self.Qf, x)
+
+
+def _double_integrator(dt=0.5):
+    return Linear([[1.0, dt], [0.0, 1.0]], [[0.5 * dt * dt], [dt]], np.diag([1.0, 0.1]), np.diag([2.0, 0.2]))
+
+
+def _J(system, x0, V, R):
+    """Deterministic cost of a control sequence V [T][m] for every column: sum q + 1/2 v^T R v + phi."""
+    st = system.init(x0, V.shape[2])
+    J = np.zeros(V.shape[2])
+    for i in range(V.shape[0]):
+        st = system.step(st, V[i])
+        J += system.q(st) + 0.5 * np.einsum("ak,ab,bk->k", V[i], R, V[i])
+    return J + system.phi(st)
+
+
+@pytest.mark.parametrize("nu", [1.0, 3.0, 40.0])
+def test_path_cost_identity(nu):
+    """Sec. III-C: S~ = J(u + du) - 1/(2 nu) sum_i du_i^T R du_i, where J is the
+    deterministic cost with the control cost 1/2 v^T R v.  At nu = 1 the
+    (1 - 1/nu) term drops out exactly and S~ is the Girsanov-only cost."""
+    sys_ = systems.CartPole(0.05)
+    T, K = 6, 64
+    rng = np.random.default_rng(8)
+    U = rng.normal(0, 1, (T, 1))
+    du = rng.normal(0, 2, (T, 1, K))
+    R = np.array([[0.7]])
+    S, _ = mppi.path_costs(sys_, [0.1, 0, 2.0, 0], U, du, R, nu)
+    J = _J(sys_, [0.1, 0, 2.0, 0], U[:, :, None] + du, R)
+    corr = np.einsum("tak,ab,tbk->k", du, R, du) / (2 * nu)
+    assert np.allclose(S, J - corr, rtol=1e-12, atol=1e-9)
+
+
+def test_weights_simplex_shift_invariance_and_ties():
+    rng = np.random.default_rng(0)
+    S = rng.normal(100, 3, 1000)
+    rho, k, eta, w = mppi.weights(S, 2.0)
+    assert np.all(w >= 0) and abs(w.sum() - 1) < 1e-12
+    assert k == int(np.argmin(S)) and rho == S.min() and eta >= 1.0
+    _, _, _, w2 = mppi.weights(S + 12345.0, 2.0)
+    assert np.allclose(w, w2, rtol=1e-9, atol=0)
+    # no shift at all: the weights are the plain softmax of -S/lambda (Eq. App_PI)
+    e = np.exp(-(S - 90.0) / 2.0)
+    assert np.allclose(w, e / e.sum(), rtol=1e-12)
+    Sties = np.array([5.0, 3.0, 3.0, 4.0])
+    assert mppi.weights(Sties, 1.0)[1] == 1
+    Snan = np.array([np.nan, 2.0, np.inf, 1.0])
+    _, k, _, w = mppi.weights(Snan, 1.0)
+    assert k == 3 and w[0] == 0 and w[2] == 0 and abs(w.sum() - 1) < 1e-15
+    _, _, eta, w = mppi.weights(np.array([np.inf, np.nan]), 1.0)
+    assert eta == 0.0 and not w.any()
+
+
+def test_zero_noise_gives_zero_update():
+    sys_ = systems.CartPole(0.02)
+    U = np.linspace(-1, 1, 20)[:, None]
+    r = mppi.iteration_seeded(sys_, [0, 0, math.pi, 0], U, 64, 1.0, 10.0, np.zeros((1, 1)), np.eye(1), seed=0)
+    assert np.array_equal(r.dU, np.zeros_like(U)) and np.array_equal(r.U, U)
+
+
+def test_single_sample_update_is_its_perturbation():
+    sys_ = systems.CartPole(0.02)
+    U = np.zeros((30, 1))
+    r = mppi.iteration_seeded(sys_, [0, 0, math.pi, 0], U, 1, 1.0, 10.0, np.eye(1), np.eye(1), seed=5)
+    assert np.array_equal(r.dU, r.du[:, :, 0])
+    assert r.w[0] == 1.0
+
+
+def test_temperature_limits():
+    sys_ = systems.CartPole(0.02)
+    U = np.zeros((20, 1))
+    du = philox.exploration_noise(1, 256, 20, np.eye(1), 10.0)
+    hot = mppi.iteration(sys_, [0, 0, math.pi, 0], U, 1e12, 10.0, np.eye(1), np.eye(1), 1, du=du)
+    assert np.allclose(hot.dU, du.mean(axis=2), rtol=1e-6, atol=1e-9)
+    cold = mppi.iteration(sys_, [0, 0, math.pi, 0], U, 1e-6, 10.0, np.eye(1), np.eye(1), 1, du=du)
+    assert np.allclose(cold.dU, du[:, :, cold.kstar], atol=1e-12)
+
+
+def test_brute_force_two_samples_two_steps():
+    """K = 2, T = 2, scalar x' = a x + b v, q = c x^2, phi = cf x^2, expanded by hand."""
+    a, b, c, cf, R, nu, lam = 0.9, 0.5, 2.0, 3.0, 1.5, 4.0, 0.7
+    x0, U = 1.2, np.array([[0.3], [-0.2]])
+    du = np.array([[[0.5, -1.0]], [[0.25, 2.0]]])
+    lin = Linear([[a]], [[b]], [[c]], [[cf]])
+    S, _ = mppi.path_costs(lin, [x0], U, du, np.array([[R]]), nu)
+    want = []
+    for k in range(2):
+        v0, v1 = U[0, 0] + du[0, 0, k], U[1, 0] + du[1, 0, k]
+        x1 = a * x0 + b * v0
+        x2 = a * x1 + b * v1
+        # hand expansion of q~ for each step (Sec. III-C), then phi
+        s = c * x1 ** 2 + 0.5 * (1 - 1 / nu) * R * du[0, 0, k] ** 2 + U[0, 0] * R * du[0, 0, k] + 0.5 * R * U[0, 0] ** 2
+        s += c * x2 ** 2 + 0.5 * (1 - 1 / nu) * R * du[1, 0, k] ** 2 + U[1, 0] * R * du[1, 0, k] + 0.5 * R * U[1, 0] ** 2
+        s += cf * x2 ** 2
+        want.append(s)
+    assert np.allclose(S, want, rtol=1e-14)
+    _, _, _, w = mppi.weights(S, lam)
+    w1 = 1.0 / (1.0 + math.exp(-(S[1] - S[0]) / lam))
+    assert w[0] == pytest.approx(w1, rel=1e-13)
+    dU, Un = mppi.weighted_update(U, du, w)
+    assert dU[0, 0] == pytest.approx(w1 * 0.5 + (1 - w1) * -1.0, rel=1e-13)
+    assert dU[1, 0] == pytest.approx(w1 * 0.25 + (1 - w1) * 2.0, rel=1e-13)
+
+
+def _lq_optimum(lin, x0, T, R):
+    """argmin_v J(v) for linear dynamics and quadratic costs, by one dense solve."""
+    n, m = lin.n, lin.m
+    Phi = np.zeros((T * n, n))
+    G = np.zeros((T * n, T * m))
+    Ak = np.eye(n)
+    for i in range(T):
+        Ak = lin.A @ Ak
+        Phi[i * n:(i + 1) * n] = Ak
+        for j in range(i + 1):
+            G[i * n:(i + 1) * n, j * m:(j + 1) * m] = np.linalg.matrix_power(lin.A, i - j) @ lin.B
+    Qbar = np.kron(np.eye(T), lin.Q)
+    Qbar[-n:, -n:] += lin.Qf
+    H = 2 * G.T @ Qbar @ G + np.kron(np.eye(T), R)
+    g = 2 * G.T @ Qbar @ Phi @ np.asarray(x0)
+    return np.linalg.solve(H, -g).reshape(T, m), H
+
+
+@pytest.mark.parametrize("nu", [1.0, 4.0])
+def test_one_iteration_reaches_the_lq_optimum(nu):
+    """With R = lambda Sigma^-1, p(du) exp(-S~/lambda) is proportional to exp(-J(u+du)/lambda)
+    for every nu (the variance change is cancelled by the (1 - 1/nu) term), so one
+    iteration's expected update lands on argmin J: the finite-horizon LQ control."""
+    lin = _double_integrator()
+    T, lam = 4, 1.0
+    Sigma = np.array([[0.5]])
+    R = lam * np.linalg.inv(Sigma)
+    x0 = np.array([1.0, -0.5])
+    U = np.array([[0.4], [-0.3], [0.2], [0.0]])
+    ustar, H = _lq_optimum(lin, x0, T, R)
+    K = 400000
+    r = mppi.iteration_seeded(lin, x0, U, K, lam, nu, Sigma, R, seed=21)
+    ess = 1.0 / np.sum(r.w ** 2)
+    se = np.sqrt(lam * np.diag(np.linalg.inv(H)) / ess).reshape(T, 1)
+    assert np.all(np.abs(r.U - ustar) < 5 * se), (r.U.ravel(), ustar.ravel(), se.ravel())
+    assert ess > 1000
+
+
+def test_lq_error_falls_like_inverse_sqrt_K():
+    lin = _double_integrator()
+    T, lam, nu = 4, 1.0, 2.0
+    Sigma = np.array([[0.5]])
+    R = lam * np.linalg.inv(Sigma)
+    x0 = np.array([1.0, -0.5])
+    U = np.zeros((T, 1))
+    ustar, _ = _lq_optimum(lin, x0, T, R)
+
+    def rms(K):
+        e = [np.abs(mppi.iteration_seeded(lin, x0, U, K, lam, nu, Sigma, R, seed=s).U - ustar).mean()
+             for s in range(24)]
+        return float(np.sqrt(np.mean(np.square(e))))
+
+    ratio = rms(500) / rms(8000)     # 16x the samples: ~4x smaller error
+    assert 2.5 < ratio < 6.5
+
+
+def test_variance_change_keeps_the_estimate_unbiased_on_the_cartpole():
+    """The paper's central claim: changing the exploration variance by nu with the
+    likelihood-ratio cost leaves the (large-K) update unchanged; only its variance moves."""
+    cp = systems.CartPole(0.02)
+    T, lam = 5, 10.0
+    Sigma = np.array([[4.0]])
+    R = lam * np.linalg.inv(Sigma)
+    U = np.zeros((T, 1))
+    x0 = [0.0, 0.0, 2.8, 0.0]
+    res = {}
+    for nu in (1.0, 3.0):
+        ests = [mppi.iteration_seeded(cp, x0, U, 100000, lam, nu, Sigma, R, seed=s).dU for s in range(6)]
+        res[nu] = (np.mean(ests, axis=0), np.std(ests, axis=0) / math.sqrt(len(ests)))
+    diff = np.abs(res[1.0][0] - res[3.0][0])
+    se = np.sqrt(res[1.0][1] ** 2 + res[3.0][1] ** 2)
+    assert np.all(diff < 5 * se + 1e-3), (diff, se)
+    # power check: wider noise scored with the nu = 1 cost (the (1 - 1/nu) term left out)
+    # is biased, and the comparison above detects it
+    wrong = []
+    for s in range(6):
+        du = philox.exploration_noise(s, 100000, T, Sigma, 3.0)
+        wrong.append(mppi.iteration(cp, x0, U, lam, 1.0, Sigma, R, s, du=du).dU)
+    bias = np.abs(np.mean(wrong, axis=0) - res[1.0][0])
+    assert np.any(bias > 5 * se + 1e-3), (bias, se)
+
+
+def test_shift_and_u_init():
+    U = np.arange(12, dtype=np.float64).reshape(6, 2)
+    s = mppi.shift(U, [7.0, -7.0])
+    assert np.array_equal(s[:-1], U[1:]) and np.array_equal(s[-1], [7.0, -7.0])
