@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""MPPI benchmark on B300: rollout-steps/s of one MPPI iteration.
+
+Workload (the car-on-a-track configuration): dynamic bicycle car on a 1024x1024
+FP32 cost-map track, K=16384 samples, T=100 steps, nu=10, lambda=1,
+Sigma=diag(0.3, 0.35), R = lambda Sigma^-1, receding horizon (update + shift every
+step), seeded synthetic inputs.  A step is one full MPPI iteration: noise,
+rollout, cost with the importance-sampling terms, weights, update, shift.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  value = rollout-steps/s with inputs resident in HBM (CUDA
+events on the controller's stream, L2 flushed between steps, outside the timed
+events).  e2e = the same metric through mppi_step with host buffers (x0 H2D and
+u0 D2H inside each timed step).  The plain single-controller loop on the same GPU
+(unfused kernels, sync per step) is reported beside it.  With torchrun, every rank
+runs its own independent controller (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "rollout-steps/s (K*T per MPPI iteration) and MPPI iters/s vs plain loop on same GPU; p50/p99 step latency"
+UNIT = "rollout-steps/s"
+SYSTEM = W.CAR
+K_SAMPLES, T_STEPS, NU = 16384, 100, 10.0
+
+# Algorithmic FP32 work of one rollout-step (one sample, one time step), counted from
+# the formulas: adds, multiplies and divides, each elementary function as one op.
+# Derivation in the design notes.
+ALGO_FLOPS_PER_ROLLOUT_STEP = {W.CARTPOLE: 55.5, W.CAR: 127.0, W.QUAD: 936.0}
+SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--plain-steps", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1509_01149_b300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_id: str | None):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("timestamp,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[3]),
+                                 reasons={r: parts[5 + i].lower().startswith("active") for i, r in enumerate(_REASONS)}))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        busy = [r for r in rows if r["util"] > 0] or rows
+        if not busy:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        reasons = sorted({r for row in busy for r, on in row["reasons"].items() if on})
+        return {"sm_mhz": statistics.median(r["sm"] for r in busy), "sm_max_mhz": max(r["smax"] for r in busy),
+                "reasons": reasons, "samples": len(busy)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+_ONE_THREAD = {v: "1" for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                  "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
+
+
+def _oracle_loop(seconds: float, k_sample: int, max_iters: int | None):
+    from oracle import mppi as om
+    from oracle import systems as osys
+    cfg = W.config(SYSTEM, K=k_sample, T=T_STEPS, nu=NU)
+    sysm = osys.Car(cfg["dt"], W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL)
+    U = cfg["U"].copy()
+    times = []
+    t_end = time.perf_counter() + seconds
+    while time.perf_counter() < t_end and (max_iters is None or len(times) < max_iters):
+        t0 = time.perf_counter()
+        r = om.iteration_seeded(sysm, cfg["x0"], U, k_sample, cfg["lam"], cfg["nu"], cfg["Sigma"], cfg["R"],
+                                0, counter=len(times))
+        U = om.shift(r.U, cfg["u_init"])
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def oracle_rate(seconds: float, k_sample: int = 1024, max_iters: int | None = None):
+    """Oracle iterations of the bench workload on a bounded sample of k_sample samples
+    (full horizon T), in a child process pinned to one thread (numpy/BLAS).
+    Returns (rollout-steps/s, iterations, per-iteration seconds)."""
+    env = dict(os.environ, **_ONE_THREAD)
+    arg = json.dumps([seconds, k_sample, max_iters])
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", arg], env=env,
+                         capture_output=True, text=True, check=True)
+    times = json.loads(out.stdout.strip().splitlines()[-1])
+    return k_sample * T_STEPS * len(times) / sum(times), len(times), times
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    k_sample = 1024
+    _, _, warm = oracle_rate(1e9, k_sample, max_iters=max(args.warmup, 1))
+    rate, n, times = oracle_rate(1e9, k_sample, max_iters=args.steps)
+    ms = 1e3 * statistics.mean(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "car on cost-map track (1024x1024 FP32 map), one MPPI iteration + shift per step",
+                   "K": K_SAMPLES, "T": T_STEPS, "nu": NU, "lambda": 1.0, "sample_K": k_sample,
+                   "parallelism": "single host core"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{k_sample} of the {K_SAMPLES} samples, full horizon T={T_STEPS}, per step"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def make_ctrl(N, impl, seed, gid, stream_handle):
+    cfg = W.config(SYSTEM, K=K_SAMPLES, T=T_STEPS, nu=NU, seed=seed, gid=gid)
+    c = N.Controller(cfg["system"], cfg["K"], cfg["T"], cfg["dt"], cfg["nu"], cfg["lam"], cfg["Sigma"], cfg["R"])
+    c.set_stream(stream_handle)
+    c.set_seed(seed)
+    c.set_controller_id(gid)
+    c.set_impl(impl)
+    c.set_cost_map(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL)
+    c.set_controls(cfg["U"].astype(np.float32))
+    c.set_u_init(cfg["u_init"].astype(np.float32))
+    return c, cfg
+
+
+def load_traffic(kernel_tag: str):
+    """DRAM traffic per launch from a committed ncu summary, if it was taken on the
+    current kernel sources (same source hash); else None."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_1509_01149_b300 import _native as N
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.Stream(device=dev)
+    ctrl, cfg = make_ctrl(N, N.MPPI_IMPL_FUSED, seed=1000 + rank, gid=rank, stream_handle=stream.cuda_stream)
+    n, m = ctrl.n, ctrl.m
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 126 MB L2
+    with torch.cuda.stream(stream):
+        d_x0 = torch.tensor(cfg["x0"], dtype=torch.float32, device=dev)
+        d_u0 = torch.zeros(m, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(args.warmup):
+        ctrl.step_async(d_x0.data_ptr(), d_u0.data_ptr())
+        ctrl.shift()
+    torch.cuda.synchronize()
+
+    try:
+        gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}"
+    except Exception:
+        gpu_id = None
+    clocks = ClockSampler(gpu_id)
+
+    # ---- value: inputs resident, CUDA events on the controller stream -------------
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()                              # evict L2 between timed steps
+            e0, e1, e2 = ev[s]
+            e0.record(stream)
+            ctrl.rollout_async(d_x0.data_ptr())
+            e1.record(stream)
+            ctrl.update_async(d_u0.data_ptr())
+            ctrl.shift()
+            e2.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in ev]
+    roll_ms = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    units = K_SAMPLES * T_STEPS * args.steps * world
+    value = units / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+    clk = clocks.stop()
+
+    # ---- e2e: host buffers through mppi_step (graph), x0 H2D + u0 D2H per step ---
+    e2e_steps = args.e2e_steps or max(args.steps // 2, 10)
+    x_host = np.asarray(cfg["x0"], dtype=np.float32)
+    lat = []
+    for s in range(e2e_steps + 5):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        ctrl.step(x_host)
+        ctrl.shift()
+        lat.append(time.perf_counter() - t0)
+    stream.synchronize()
+    lat = lat[5:]
+    e2e_total = sum(lat)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = K_SAMPLES * T_STEPS * e2e_steps * world / e2e_total
+
+    # ---- plain loop baseline (unfused kernels, sync per step) -----------------
+    plain_steps = args.plain_steps or max(args.steps // 4, 10)
+    pctrl, _ = make_ctrl(N, N.MPPI_IMPL_PLAIN, seed=1000 + rank, gid=rank, stream_handle=stream.cuda_stream)
+    plat = []
+    for s in range(plain_steps + 3):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        pctrl.step(x_host)
+        pctrl.shift()
+        plat.append(time.perf_counter() - t0)
+    stream.synchronize()
+    plat = plat[3:]
+    plain_value = K_SAMPLES * T_STEPS * len(plat) * world / sum(plat)
+    pctrl.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    flops = ALGO_FLOPS_PER_ROLLOUT_STEP[SYSTEM] * K_SAMPLES * T_STEPS
+    roll_mean_s = statistics.mean(roll_ms) / 1e3
+    achieved = flops / roll_mean_s / 1e12
+    peak = fp32_peak_tflops()
+    traffic = load_traffic("rollout_fused_car_k16384")
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, iters, _ = oracle_rate(args.cpu_seconds, 1024)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{iters} oracle iterations of 1024 of the {K_SAMPLES} samples at full horizon T={T_STEPS} "
+                         f"(FP64 numpy, one thread)"}
+    lat_ms = sorted(1e3 * x for x in lat)
+    plat_ms = sorted(1e3 * x for x in plat)
+
+    def pct(a, q):
+        return a[min(len(a) - 1, int(round(q * (len(a) - 1))))]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "car on cost-map track (1024x1024 FP32 map), one MPPI iteration + shift per step",
+                   "K": K_SAMPLES, "T": T_STEPS, "nu": NU, "lambda": 1.0, "Sigma": [0.3, 0.35],
+                   "parallelism": f"{world} independent controller(s), one per GPU",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed events)",
+                   "x0": "fixed state, receding-horizon warm start with shift"},
+        "iters_per_s": value / (K_SAMPLES * T_STEPS),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * m,
+                "p50_ms": pct(lat_ms, 0.5), "p99_ms": pct(lat_ms, 0.99), "steps": e2e_steps},
+        "plain_loop": {"value": plain_value, "unit": UNIT, "p50_ms": pct(plat_ms, 0.5), "p99_ms": pct(plat_ms, 0.99),
+                       "steps": len(plat), "e2e_speedup": e2e_value / plain_value,
+                       "what": "unfused: noise->HBM, rollout, min, normaliser, weighted-sum kernels, "
+                               "sync per step, no graph"},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "k_rollout_fused<Car,128>",
+                     "flops_per_rollout_step": ALGO_FLOPS_PER_ROLLOUT_STEP[SYSTEM],
+                     "rollout_ms_mean": 1e3 * roll_mean_s,
+                     "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived, not measured)",
+                     "frac_at_observed_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])) if clk.get("sm_mhz")
+                     else None},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "source_hash": source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    if len(sys.argv) == 3 and sys.argv[1] == "--oracle-child":
+        seconds, k_sample, max_iters = json.loads(sys.argv[2])
+        print(json.dumps(_oracle_loop(seconds, k_sample, max_iters)))
+        return
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * mppi.h -- C ABI of the B300 (sm_103a) MPPI library.
+ *
+ * One MPPI iteration with covariance-variable importance sampling (Williams,
+ * Aldrich, Theodorou, "Model Predictive Path Integral Control using Covariance
+ * Variable Importance Sampling"):
+ *
+ *   noise     du_{i,k} = sqrt(nu) chol(Sigma) eps_{i,k}          Theorem 1 with A = sqrt(nu) I (Sec. III-C)
+ *   rollout   x_{i+1} = F(x_i, u_i + du_{i,k}),  i = 0..T-1       Algorithm 1 (Sec. IV); Euler step of Sec. II-A
+ *   cost      S~_k = phi(x_T) + sum_i q~_i,
+ *             q~_i = q(x_{i+1}) + (1-1/nu)/2 du^T R du + u^T R du + 1/2 u^T R u   reduced q~ of Sec. III-C
+ *   weights   rho = min_k S~_k,  eta = sum_k exp(-(S~_k - rho)/lambda)
+ *   update    u_i <- u_i + sum_k exp(-(S~_k - rho)/lambda) du_{i,k} / eta          Eq. App_PI (Sec. III-C)
+ *   send/shift  u_0 out; u_i <- u_{i+1}, u_{T-1} <- u_init                         Algorithm 1
+ *
+ * Conventions shared by every call:
+ *   - Return value: MPPI_OK (0) or a negative MPPI_E* code.  Nothing throws across
+ *     the ABI.  mppi_last_error() gives the text of the last failure of a ctx.
+ *   - Ownership: every input array is copied before the call returns; outputs go
+ *     to caller-owned buffers.  The ctx owns all device memory it allocates and
+ *     frees it in mppi_destroy().
+ *   - Pointers named h_* (or documented "host") are host memory; d_* are device
+ *     memory on the ctx's device.  Arrays are dense, row-major, float32 unless
+ *     stated.  U is [T][m] (time-major), du and noise are [T][m][K] (K fastest).
+ *   - A ctx is not thread-safe: one host thread at a time.  All device work of a
+ *     ctx goes to its stream (mppi_set_stream); by default a non-blocking stream
+ *     the ctx creates on the device that is current at mppi_create.
+ *   - Floating point: rollouts and path costs in FP32 (Kahan-compensated sum);
+ *     the normaliser eta and the cross-block sums of the weighted perturbation in
+ *     FP64; controls stored in FP32.
+ */
+#ifndef MPPI_B300_H
+#define MPPI_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MPPI_OK 0
+#define MPPI_EINVAL (-1)   /* bad argument: null pointer, size out of range, not SPD, ...  */
+#define MPPI_ENOMEM (-2)   /* device or pinned host allocation failed                      */
+#define MPPI_ECUDA (-3)    /* a CUDA runtime call failed (text in mppi_last_error)          */
+#define MPPI_ETIMEOUT (-4) /* a bounded device-side wait ran out (serving)                  */
+#define MPPI_ESTATE (-5)   /* call not valid in the ctx's current state (e.g. no env set)   */
+#define MPPI_ENOSYS (-6)   /* feature not built into this library                           */
+
+/* systems (plants and their state costs; see the design notes for the models) */
+typedef enum {
+  MPPI_CARTPOLE = 0, /* n=4 (x, xdot, theta, thetadot), m=1 cart force; Euler          */
+  MPPI_CAR = 1,      /* n=7 (X, Y, psi, vx, vy, r, delta), m=2 (steer, throttle); Euler;
+                        cost map lookup + (vx-7)^2 (speed term of Sec. V-B)              */
+  MPPI_QUAD = 2,     /* n=12 (p, v, roll/pitch/yaw, body rates), m=4 rotor thrusts; RK4;
+                        cost of Sec. V-C with crash weight 1e4                          */
+  MPPI_CAR_MLP = 3   /* MPPI_CAR's cost with learned dynamics x' = x + MLP([x; u])       */
+} mppi_system;
+
+/* implementation of mppi_step */
+typedef enum {
+  MPPI_IMPL_FUSED = 0, /* default: one fused rollout+cost+block-reduction kernel, one merge
+                          kernel, both in a CUDA graph                                     */
+  MPPI_IMPL_PLAIN = 1  /* baseline "plain loop": noise kernel writes du to HBM, separate
+                          rollout, min, normaliser and weighted-sum kernels, a stream sync
+                          after each step, no graph                                        */
+} mppi_impl;
+
+typedef struct mppi_ctx mppi_ctx;
+
+/* Create a controller (Algorithm 1's "Given" block: K, N=T, dt, nu, Sigma, R, lambda).
+ *   sys      plant and cost
+ *   K        samples, 1 <= K <= 1048576
+ *   T        horizon steps, 1 <= T <= 1024
+ *   dt       integration step [s], > 0
+ *   nu       exploration variance factor (A = sqrt(nu) I), > 0.  nu = 1 is plain MPPI.
+ *   lambda   temperature, > 0
+ *   Sigma    host [m][m] natural control-noise covariance, symmetric positive
+ *            semi-definite (copied).  The perturbation covariance is nu * Sigma.
+ *   R        host [m][m] control-cost matrix, symmetric positive definite (copied), or
+ *            NULL for R = lambda * Sigma^-1 (the noise/cost relation of Sec. II), which
+ *            then needs Sigma positive definite.
+ *   out      receives the ctx.
+ * Initial state: U = 0, u_init = 0, seed 0, controller id 0, iteration counter 0.
+ * Errors: EINVAL (ranges, non-SPD), ENOMEM, ECUDA.  *out is NULL on failure. */
+int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
+                const float *Sigma, const float *R, mppi_ctx **out);
+
+/* Free every device and host resource of the ctx.  NULL is accepted. */
+int mppi_destroy(mppi_ctx *ctx);
+
+/* One MPPI iteration from state h_state (host [n], copied): noise, rollout, cost,
+ * weights and update of U (not the shift).  Writes the updated u_0 to h_u0_out
+ * (host [m]).  Blocks until the result is on the host.  ESTATE if the system needs
+ * an environment (car: cost map; quadrotor: forest; car_mlp: map + weights) that
+ * was not set. */
+int mppi_step(mppi_ctx *ctx, const float *h_state, float *h_u0_out);
+
+/* Same iteration, asynchronous on the ctx stream, device pointers: d_state [n] is
+ * read, d_u0_out [m] written (may be NULL), when the stream reaches the work.  No
+ * host sync.  Equivalent to mppi_rollout_async followed by mppi_update_async. */
+int mppi_step_async(mppi_ctx *ctx, const float *d_state, float *d_u0_out);
+
+/* The two phases of mppi_step_async, for callers that interleave their own work
+ * (events, other streams) between them:
+ *   mppi_rollout_async  copy d_state [n] into the ctx, then noise + rollout + cost
+ *                       (fused: one kernel that also forms the block partials of the
+ *                       weights; plain: noise kernel + rollout kernel).
+ *   mppi_update_async   min / normaliser / weighted sum and U update (fused: the FP64
+ *                       merge kernel; plain: min, normaliser and weighted-sum kernels),
+ *                       then copy u_0 to d_u0_out [m] if it is not NULL.
+ * update must follow rollout on the same stream. */
+int mppi_rollout_async(mppi_ctx *ctx, const float *d_state);
+int mppi_update_async(mppi_ctx *ctx, float *d_u0_out);
+
+/* Shift (Algorithm 1): u_i <- u_{i+1}, u_{T-1} <- u_init, iteration counter += 1.
+ * Asynchronous on the ctx stream. */
+int mppi_shift(mppi_ctx *ctx);
+
+/* Noise seed (Philox key = (seed & 0xffffffff, seed >> 32)) and controller id g (the
+ * fourth Philox counter word).  The normal of sample k, time i, control j at
+ * iteration counter c is lane (r & 3) of Philox4x32-10 block (r >> 2, k, c, g),
+ * r = i*m + j; words w become u = ((w >> 9) + 1/2) 2^-23; Box-Muller on lanes
+ * (0,1) and (2,3). */
+int mppi_set_seed(mppi_ctx *ctx, uint64_t seed);
+int mppi_set_controller_id(mppi_ctx *ctx, uint32_t gid);
+int mppi_set_iteration(mppi_ctx *ctx, uint32_t counter);
+int mppi_get_iteration(mppi_ctx *ctx, uint32_t *counter);
+
+/* Stream for all device work of the ctx (a cudaStream_t on the ctx's device). */
+int mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
+
+/* Select the fused path (default) or the plain-loop baseline. */
+int mppi_set_impl(mppi_ctx *ctx, mppi_impl impl);
+
+/* Nominal control sequence, host [T][m] (copied in / out; get synchronises). */
+int mppi_set_controls(mppi_ctx *ctx, const float *h_U);
+int mppi_get_controls(mppi_ctx *ctx, float *h_U);
+
+/* u_init: value new controls are initialised to by the shift, host [m]. */
+int mppi_set_u_init(mppi_ctx *ctx, const float *h_u);
+
+/* Environment of the system, host blob (copied):
+ *   MPPI_CAR / MPPI_CAR_MLP cost map: mppi_env_map header followed by
+ *     width*height float32 values, row-major [iy][ix]; node (ix, iy) is at world
+ *     (origin_x + ix*cell, origin_y + iy*cell); lookups are bilinear, clamped to the grid.
+ *   MPPI_QUAD forest: mppi_env_forest header followed by n_obstacles rows of
+ *     float32 (cx, cy, radius) (vertical cylinders), at most 256 rows.
+ * The blob kind must match the system; EINVAL otherwise. */
+#define MPPI_ENV_MAP 0x3150414du    /* "MAP1" */
+#define MPPI_ENV_FOREST 0x31524f46u /* "FOR1" */
+typedef struct {
+  uint32_t kind; /* MPPI_ENV_MAP */
+  int32_t width, height;
+  float origin_x, origin_y, cell;
+} mppi_env_map;
+typedef struct {
+  uint32_t kind; /* MPPI_ENV_FOREST */
+  int32_t n_obstacles;
+  float goal[3];
+  float pad;
+} mppi_env_forest;
+int mppi_set_env(mppi_ctx *ctx, const void *blob, size_t bytes);
+
+/* Results of the last mppi_step, host outputs (any may be NULL); synchronises.
+ *   S      [K]   path costs S~ (non-finite costs reported as +inf)
+ *   argmin       lowest k with S~_k = rho
+ *   eta          sum_k exp(-(S~_k - rho)/lambda) (FP64)
+ *   dU     [T][m] the weighted perturbation sum_k w_k du_{i,k} that was added to U */
+int mppi_get_debug(mppi_ctx *ctx, float *S, int *argmin, double *eta, float *dU);
+
+/* The perturbations du of iteration counter `counter`, recomputed on the device by
+ * the same noise code as the rollout, host [T][m][K] out. */
+int mppi_get_noise(mppi_ctx *ctx, uint32_t counter, float *h_du);
+
+/* Raw Philox4x32-10 words on the device, for checking the generator:
+ * out[b][4][k] for blocks b < n_blocks, samples k < K, counter (b, k, counter, gid),
+ * key (seed lo, seed hi).  h_out is host uint32 [n_blocks][4][K]. */
+int mppi_philox_words(uint64_t seed, int K, int n_blocks, uint32_t counter, uint32_t gid,
+                      uint32_t *h_out);
+
+/* Text of the last error on this ctx (or of the last failed create when ctx is NULL).
+ * Valid until the next call on the ctx. */
+const char *mppi_last_error(mppi_ctx *ctx);
+
+/* Library version string. */
+const char *mppi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPPI_B300_H */

@@ -1,0 +1,241 @@
+"""ctypes binding of the C ABI in include/mppi.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of libmppi_b300.so.  There is no CPU
+fallback: importing this module raises if the library is missing, and every
+call raises MppiError on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import struct
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmppi_b300.so")
+
+MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE, MPPI_ENOSYS = 0, -1, -2, -3, -4, -5, -6
+MPPI_CARTPOLE, MPPI_CAR, MPPI_QUAD, MPPI_CAR_MLP = 0, 1, 2, 3
+MPPI_IMPL_FUSED, MPPI_IMPL_PLAIN = 0, 1
+MPPI_ENV_MAP, MPPI_ENV_FOREST = 0x3150414D, 0x31524F46
+STATE_DIM = {MPPI_CARTPOLE: 4, MPPI_CAR: 7, MPPI_QUAD: 12, MPPI_CAR_MLP: 7}
+CONTROL_DIM = {MPPI_CARTPOLE: 1, MPPI_CAR: 2, MPPI_QUAD: 4, MPPI_CAR_MLP: 2}
+
+# (name, restype, argtypes) of every exported symbol declared in include/mppi.h
+_P = C.c_void_p
+_FP = C.POINTER(C.c_float)
+SIGNATURES = [
+    ("mppi_create", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, _FP, _FP, C.POINTER(_P)]),
+    ("mppi_destroy", C.c_int, [_P]),
+    ("mppi_step", C.c_int, [_P, _FP, _FP]),
+    ("mppi_step_async", C.c_int, [_P, _P, _P]),
+    ("mppi_rollout_async", C.c_int, [_P, _P]),
+    ("mppi_update_async", C.c_int, [_P, _P]),
+    ("mppi_shift", C.c_int, [_P]),
+    ("mppi_set_seed", C.c_int, [_P, C.c_uint64]),
+    ("mppi_set_controller_id", C.c_int, [_P, C.c_uint32]),
+    ("mppi_set_iteration", C.c_int, [_P, C.c_uint32]),
+    ("mppi_get_iteration", C.c_int, [_P, C.POINTER(C.c_uint32)]),
+    ("mppi_set_stream", C.c_int, [_P, _P]),
+    ("mppi_set_impl", C.c_int, [_P, C.c_int]),
+    ("mppi_set_controls", C.c_int, [_P, _FP]),
+    ("mppi_get_controls", C.c_int, [_P, _FP]),
+    ("mppi_set_u_init", C.c_int, [_P, _FP]),
+    ("mppi_set_env", C.c_int, [_P, C.c_char_p, C.c_size_t]),
+    ("mppi_get_debug", C.c_int, [_P, _FP, C.POINTER(C.c_int), C.POINTER(C.c_double), _FP]),
+    ("mppi_get_noise", C.c_int, [_P, C.c_uint32, _FP]),
+    ("mppi_philox_words", C.c_int, [C.c_uint64, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]),
+    ("mppi_last_error", C.c_char_p, [_P]),
+    ("mppi_version", C.c_char_p, []),
+]
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1509_01149_b300.build`")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load()
+
+
+class MppiError(RuntimeError):
+    def __init__(self, rc: int, msg: str):
+        super().__init__(f"status {rc}: {msg}")
+        self.rc = rc
+
+
+def _f32(a, n=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a
+
+
+def _fp(a: np.ndarray):
+    return a.ctypes.data_as(_FP)
+
+
+def map_blob(cost_map: np.ndarray, origin_x: float, origin_y: float, cell: float) -> bytes:
+    """mppi_env_map header + float32 map [height][width]."""
+    M = np.ascontiguousarray(cost_map, dtype=np.float32)
+    h, w = M.shape
+    return struct.pack("<Iiifff", MPPI_ENV_MAP, w, h, origin_x, origin_y, cell) + M.tobytes()
+
+
+def forest_blob(obstacles: np.ndarray, goal) -> bytes:
+    """mppi_env_forest header + float32 rows (cx, cy, r)."""
+    O = np.ascontiguousarray(obstacles, dtype=np.float32).reshape(-1, 3)
+    g = [float(v) for v in goal]
+    return struct.pack("<Iiffff", MPPI_ENV_FOREST, O.shape[0], g[0], g[1], g[2], 0.0) + O.tobytes()
+
+
+def mppi_philox_words(seed: int, K: int, n_blocks: int, counter: int, gid: int) -> np.ndarray:
+    out = np.zeros((n_blocks, 4, K), dtype=np.uint32)
+    rc = lib.mppi_philox_words(seed, K, n_blocks, counter, gid, out.ctypes.data_as(C.POINTER(C.c_uint32)))
+    if rc != MPPI_OK:
+        raise MppiError(rc, lib.mppi_last_error(None).decode())
+    return out
+
+
+class Controller:
+    """One MPPI controller context (mppi_ctx).  Methods map 1:1 onto the C ABI."""
+
+    def __init__(self, system: int, K: int, T: int, dt: float, nu: float, lam: float, Sigma, R=None):
+        self.system, self.K, self.T = int(system), int(K), int(T)
+        self.n, self.m = STATE_DIM[self.system], CONTROL_DIM[self.system]
+        S = _f32(Sigma, self.m * self.m)
+        Rm = None if R is None else _f32(R, self.m * self.m)
+        h = _P()
+        rc = lib.mppi_create(self.system, self.K, self.T, dt, nu, lam, _fp(S), None if Rm is None else _fp(Rm),
+                             C.byref(h))
+        if rc != MPPI_OK:
+            raise MppiError(rc, lib.mppi_last_error(None).decode())
+        self._h = h
+
+    # -- lifecycle ------------------------------------------------------------
+    def mppi_destroy(self):
+        if getattr(self, "_h", None):
+            lib.mppi_destroy(self._h)
+            self._h = None
+
+    close = mppi_destroy
+
+    def __del__(self):
+        try:
+            self.mppi_destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.mppi_destroy()
+
+    def _chk(self, rc: int):
+        if rc != MPPI_OK:
+            raise MppiError(rc, lib.mppi_last_error(self._h).decode())
+
+    # -- iteration ------------------------------------------------------------
+    def mppi_step(self, state) -> np.ndarray:
+        x = _f32(state, self.n)
+        u0 = np.zeros(self.m, dtype=np.float32)
+        self._chk(lib.mppi_step(self._h, _fp(x), _fp(u0)))
+        return u0
+
+    step = mppi_step
+
+    def mppi_step_async(self, d_state: int, d_u0_out: int | None):
+        self._chk(lib.mppi_step_async(self._h, C.c_void_p(d_state), C.c_void_p(d_u0_out or 0)))
+
+    step_async = mppi_step_async
+
+    def mppi_rollout_async(self, d_state: int):
+        self._chk(lib.mppi_rollout_async(self._h, C.c_void_p(d_state)))
+
+    def mppi_update_async(self, d_u0_out: int | None):
+        self._chk(lib.mppi_update_async(self._h, C.c_void_p(d_u0_out or 0)))
+
+    rollout_async = mppi_rollout_async
+    update_async = mppi_update_async
+
+    def mppi_shift(self):
+        self._chk(lib.mppi_shift(self._h))
+
+    shift = mppi_shift
+
+    # -- configuration ----------------------------------------------------------
+    def mppi_set_seed(self, seed: int):
+        self._chk(lib.mppi_set_seed(self._h, seed))
+
+    def mppi_set_controller_id(self, gid: int):
+        self._chk(lib.mppi_set_controller_id(self._h, gid))
+
+    def mppi_set_iteration(self, counter: int):
+        self._chk(lib.mppi_set_iteration(self._h, counter))
+
+    def mppi_get_iteration(self) -> int:
+        c = C.c_uint32()
+        self._chk(lib.mppi_get_iteration(self._h, C.byref(c)))
+        return c.value
+
+    def mppi_set_stream(self, stream_handle: int):
+        self._chk(lib.mppi_set_stream(self._h, C.c_void_p(stream_handle)))
+
+    def mppi_set_impl(self, impl: int):
+        self._chk(lib.mppi_set_impl(self._h, impl))
+
+    def mppi_set_controls(self, U):
+        self._chk(lib.mppi_set_controls(self._h, _fp(_f32(U, self.T * self.m))))
+
+    def mppi_get_controls(self) -> np.ndarray:
+        U = np.zeros((self.T, self.m), dtype=np.float32)
+        self._chk(lib.mppi_get_controls(self._h, _fp(U)))
+        return U
+
+    def mppi_set_u_init(self, u):
+        self._chk(lib.mppi_set_u_init(self._h, _fp(_f32(u, self.m))))
+
+    def mppi_set_env(self, blob: bytes):
+        self._chk(lib.mppi_set_env(self._h, blob, len(blob)))
+
+    def set_cost_map(self, cost_map, origin_x, origin_y, cell):
+        self.mppi_set_env(map_blob(cost_map, origin_x, origin_y, cell))
+
+    def set_forest(self, obstacles, goal):
+        self.mppi_set_env(forest_blob(obstacles, goal))
+
+    # -- results ----------------------------------------------------------------
+    def mppi_get_debug(self):
+        S = np.zeros(self.K, dtype=np.float32)
+        dU = np.zeros((self.T, self.m), dtype=np.float32)
+        k = C.c_int()
+        eta = C.c_double()
+        self._chk(lib.mppi_get_debug(self._h, _fp(S), C.byref(k), C.byref(eta), _fp(dU)))
+        return dict(S=S, kstar=k.value, eta=eta.value, dU=dU)
+
+    def mppi_get_noise(self, counter: int) -> np.ndarray:
+        du = np.zeros((self.T, self.m, self.K), dtype=np.float32)
+        self._chk(lib.mppi_get_noise(self._h, counter, _fp(du)))
+        return du
+
+    # short aliases
+    set_seed = mppi_set_seed
+    set_controller_id = mppi_set_controller_id
+    set_iteration = mppi_set_iteration
+    get_iteration = mppi_get_iteration
+    set_stream = mppi_set_stream
+    set_impl = mppi_set_impl
+    set_controls = mppi_set_controls
+    get_controls = mppi_get_controls
+    set_u_init = mppi_set_u_init
+    set_env = mppi_set_env
+    get_debug = mppi_get_debug
+    get_noise = mppi_get_noise

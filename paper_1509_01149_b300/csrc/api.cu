@@ -1,0 +1,582 @@
+// Host runtime of the MPPI C ABI (include/mppi.h): controller contexts, device
+// memory, the CUDA graph of one iteration, and the plain-loop baseline.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <string>
+#include <vector>
+
+#include "../../include/mppi.h"
+#include "kernels.cuh"
+
+using namespace mppi;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int state_dim(int sys) {
+  switch (sys) {
+    case MPPI_CARTPOLE: return 4;
+    case MPPI_CAR: return 7;
+    case MPPI_QUAD: return 12;
+    case MPPI_CAR_MLP: return 7;
+    default: return 0;
+  }
+}
+int control_dim(int sys) {
+  switch (sys) {
+    case MPPI_CARTPOLE: return 1;
+    case MPPI_CAR: return 2;
+    case MPPI_QUAD: return 4;
+    case MPPI_CAR_MLP: return 2;
+    default: return 0;
+  }
+}
+
+// Textbook Cholesky of a symmetric positive semi-definite m x m matrix (double).
+bool cholesky_psd(const double *S, int m, double *L) {
+  for (int i = 0; i < m * m; ++i) L[i] = 0.0;
+  for (int j = 0; j < m; ++j) {
+    double d = S[j * m + j];
+    for (int l = 0; l < j; ++l) d -= L[j * m + l] * L[j * m + l];
+    if (d < -1e-9 * std::fmax(1.0, std::fabs(S[j * m + j]))) return false;
+    L[j * m + j] = std::sqrt(std::fmax(d, 0.0));
+    for (int i = j + 1; i < m; ++i) {
+      double a = S[i * m + j];
+      for (int l = 0; l < j; ++l) a -= L[i * m + l] * L[j * m + l];
+      L[i * m + j] = L[j * m + j] > 0.0 ? a / L[j * m + j] : 0.0;
+    }
+  }
+  return true;
+}
+
+bool symmetric(const double *A, int m) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < i; ++j)
+      if (std::fabs(A[i * m + j] - A[j * m + i]) > 1e-6 * (std::fabs(A[i * m + j]) + std::fabs(A[j * m + i]) + 1e-30))
+        return false;
+  return true;
+}
+
+// Gauss-Jordan inverse (double), false if singular.
+bool invert(const double *A, int m, double *Ai) {
+  double a[kMaxM * 2 * kMaxM];
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < 2 * m; ++j) a[i * 2 * m + j] = j < m ? A[i * m + j] : (j - m == i ? 1.0 : 0.0);
+  for (int c = 0; c < m; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(a[r * 2 * m + c]) > std::fabs(a[piv * 2 * m + c])) piv = r;
+    if (std::fabs(a[piv * 2 * m + c]) < 1e-300) return false;
+    for (int j = 0; j < 2 * m; ++j) std::swap(a[c * 2 * m + j], a[piv * 2 * m + j]);
+    const double d = a[c * 2 * m + c];
+    for (int j = 0; j < 2 * m; ++j) a[c * 2 * m + j] /= d;
+    for (int r = 0; r < m; ++r)
+      if (r != c) {
+        const double f = a[r * 2 * m + c];
+        for (int j = 0; j < 2 * m; ++j) a[r * 2 * m + j] -= f * a[c * 2 * m + j];
+      }
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) Ai[i * m + j] = a[i * 2 * m + m + j];
+  return true;
+}
+
+// Bump allocator over one device allocation (256-byte aligned slices).
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0, used = 0;
+  template <class T>
+  T *take(size_t count) {
+    const size_t bytes = (sizeof(T) * count + 255) & ~static_cast<size_t>(255);
+    if (used + bytes > size) return nullptr;
+    T *p = reinterpret_cast<T *>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+
+}  // namespace
+
+struct mppi_ctx {
+  int sys = 0, K = 0, T = 0, m = 0, n = 0;
+  int impl = MPPI_IMPL_FUSED;
+  int blk = 0, nblk = 0;
+  CtrlParams p{};
+  uint64_t seed = 0;
+  std::string err;
+
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+
+  Arena arena;
+  CtrlState *d_st = nullptr;
+  float *d_U = nullptr, *d_uinit = nullptr, *d_u0 = nullptr, *d_S = nullptr, *d_psum = nullptr, *d_dU = nullptr;
+  BlockPartial *d_part = nullptr;
+  StepDebug *d_dbg = nullptr;
+  float *d_du = nullptr;       // plain-loop / debug noise [TM][K] (lazy)
+  uint32_t *d_ctr = nullptr;   // scratch counter for mppi_get_noise
+  float *d_env = nullptr;      // cost map or forest (separate allocation)
+  size_t env_bytes = 0;
+  bool env_ok = false;
+
+  float *h_x0 = nullptr, *h_u0 = nullptr;  // pinned staging
+
+  cudaGraphExec_t graph = nullptr;
+  bool graph_dirty = true;
+
+  int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+  int cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return MPPI_OK;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? MPPI_ENOMEM : MPPI_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+  bool needs_env() const { return sys == MPPI_CAR || sys == MPPI_QUAD || sys == MPPI_CAR_MLP; }
+};
+
+#define MPPI_TRY(expr)             \
+  do {                             \
+    const int _rc = (expr);        \
+    if (_rc != MPPI_OK) return _rc; \
+  } while (0)
+
+namespace {
+
+int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
+  MPPI_TRY(c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
+                   "fused rollout launch"));
+  return c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->d_u0, c->d_dU, c->d_dbg, s),
+                 "merge launch");
+}
+
+int ensure_noise_buffer(mppi_ctx *c) {
+  if (c->d_du) return MPPI_OK;
+  const size_t bytes = sizeof(float) * static_cast<size_t>(c->T) * c->m * c->K;
+  return c->cuda(cudaMalloc(&c->d_du, bytes), "cudaMalloc(noise)");
+}
+
+int enqueue_plain(mppi_ctx *c, cudaStream_t s) {
+  MPPI_TRY(ensure_noise_buffer(c));
+  MPPI_TRY(c->cuda(launch_plain_noise(c->p, &c->d_st->counter, c->d_du, s), "plain noise"));
+  MPPI_TRY(c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->d_U, c->d_du, c->d_S, s), "plain rollout"));
+  return c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, s),
+                 "plain reduce/update");
+}
+
+int build_graph(mppi_ctx *c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  MPPI_TRY(c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
+  int rc = c->cuda(cudaMemcpyAsync(c->d_st->x0, c->h_x0, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream),
+                   "x0 copy");
+  if (rc == MPPI_OK) rc = enqueue_fused(c, c->stream);
+  if (rc == MPPI_OK)
+    rc = c->cuda(cudaMemcpyAsync(c->h_u0, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToHost, c->stream),
+                 "u0 copy");
+  const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
+  if (rc != MPPI_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  MPPI_TRY(rc_end);
+  rc = c->cuda(cudaGraphInstantiate(&c->graph, g, 0), "graph instantiate");
+  cudaGraphDestroy(g);
+  if (rc == MPPI_OK) c->graph_dirty = false;
+  return rc;
+}
+
+int check_ready(mppi_ctx *c) {
+  if (c->needs_env() && !c->env_ok) return c->fail(MPPI_ESTATE, "system needs an environment (mppi_set_env)");
+  if (c->sys == MPPI_CAR_MLP) return c->fail(MPPI_ENOSYS, "learned dynamics not available in this build");
+  return MPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mppi_version(void) { return "mppi-b300 0.1 (sm_103a)"; }
+
+const char *mppi_last_error(mppi_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda, const float *Sigma, const float *R,
+                mppi_ctx **out) {
+  if (!out) return MPPI_EINVAL;
+  *out = nullptr;
+  const int n = state_dim(sys), m = control_dim(sys);
+  auto bad = [](const char *msg) {
+    g_create_error = msg;
+    return MPPI_EINVAL;
+  };
+  if (n == 0) return bad("unknown system");
+  if (K < 1 || K > (1 << 20)) return bad("K out of range [1, 1048576]");
+  if (T < 1 || T > 1024) return bad("T out of range [1, 1024]");
+  if (!(dt > 0.0f) || !std::isfinite(dt)) return bad("dt must be > 0");
+  if (!(nu > 0.0f) || !std::isfinite(nu)) return bad("nu must be > 0");
+  if (!(lambda > 0.0f) || !std::isfinite(lambda)) return bad("lambda must be > 0");
+  if (!Sigma) return bad("Sigma is NULL");
+
+  double S[kMaxM * kMaxM], L[kMaxM * kMaxM], Rd[kMaxM * kMaxM];
+  for (int i = 0; i < m * m; ++i) S[i] = Sigma[i];
+  if (!symmetric(S, m)) return bad("Sigma is not symmetric");
+  if (!cholesky_psd(S, m, L)) return bad("Sigma is not positive semi-definite");
+  if (R) {
+    for (int i = 0; i < m * m; ++i) Rd[i] = R[i];
+    double LR[kMaxM * kMaxM];
+    if (!symmetric(Rd, m)) return bad("R is not symmetric");
+    if (!cholesky_psd(Rd, m, LR)) return bad("R is not positive definite");
+    for (int j = 0; j < m; ++j)
+      if (!(LR[j * m + j] > 0.0)) return bad("R is not positive definite");
+  } else {
+    double Si[kMaxM * kMaxM];
+    if (!invert(S, m, Si)) return bad("R = lambda Sigma^-1 needs Sigma positive definite");
+    for (int i = 0; i < m * m; ++i) Rd[i] = lambda * Si[i];
+  }
+
+  mppi_ctx *c = new (std::nothrow) mppi_ctx();
+  if (!c) return MPPI_ENOMEM;
+  c->sys = sys;
+  c->K = K;
+  c->T = T;
+  c->m = m;
+  c->n = n;
+  CtrlParams &p = c->p;
+  p.K = K;
+  p.T = T;
+  p.m = m;
+  p.n = n;
+  p.dt = dt;
+  p.nu = nu;
+  p.lambda = lambda;
+  p.inv_lambda = 1.0f / lambda;
+  p.is_du = 0.5f * static_cast<float>(1.0 - 1.0 / static_cast<double>(nu));
+  const double snu = std::sqrt(static_cast<double>(nu));
+  for (int i = 0; i < m * m; ++i) {
+    p.Lnu[i] = static_cast<float>(snu * L[i]);
+    p.R[i] = static_cast<float>(Rd[i]);
+  }
+  p.key_lo = 0;
+  p.key_hi = 0;
+  p.gid = 0;
+  p.map_w = p.map_h = 2;
+  p.map_inv_cell = 1.0f;
+
+  c->blk = fused_block_size(p);
+  if (c->blk == 0) {
+    delete c;
+    return bad("T*m too large for the fused rollout's shared memory");
+  }
+  c->nblk = (K + c->blk - 1) / c->blk;
+
+  int rc = c->cuda(cudaGetDevice(&c->device), "cudaGetDevice");
+  if (rc == MPPI_OK) rc = c->cuda(prepare_kernels(), "kernel attributes");
+  if (rc == MPPI_OK) rc = c->cuda(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
+  if (rc == MPPI_OK) c->own_stream = true;
+  const size_t TM = static_cast<size_t>(T) * m;
+  const size_t nb_max = (K + kFusedBlockSmall - 1) / kFusedBlockSmall;
+  c->arena.size = 256 * 16 + sizeof(CtrlState) + sizeof(float) * (2 * TM + 2 * kMaxM + K + nb_max * TM) +
+                  sizeof(BlockPartial) * nb_max + sizeof(StepDebug) + sizeof(uint32_t);
+  if (rc == MPPI_OK) rc = c->cuda(cudaMalloc(&c->arena.base, c->arena.size), "cudaMalloc(arena)");
+  if (rc == MPPI_OK) {
+    c->d_st = c->arena.take<CtrlState>(1);
+    c->d_U = c->arena.take<float>(TM);
+    c->d_dU = c->arena.take<float>(TM);
+    c->d_uinit = c->arena.take<float>(kMaxM);
+    c->d_u0 = c->arena.take<float>(kMaxM);
+    c->d_S = c->arena.take<float>(K);
+    c->d_psum = c->arena.take<float>(nb_max * TM);
+    c->d_part = c->arena.take<BlockPartial>(nb_max);
+    c->d_dbg = c->arena.take<StepDebug>(1);
+    c->d_ctr = c->arena.take<uint32_t>(1);
+    if (!c->d_ctr) rc = c->fail(MPPI_ENOMEM, "arena too small");
+  }
+  if (rc == MPPI_OK) rc = c->cuda(cudaMemsetAsync(c->arena.base, 0, c->arena.size, c->stream), "memset");
+  if (rc == MPPI_OK) rc = c->cuda(cudaMallocHost(&c->h_x0, sizeof(float) * kMaxN), "cudaMallocHost");
+  if (rc == MPPI_OK) rc = c->cuda(cudaMallocHost(&c->h_u0, sizeof(float) * kMaxM), "cudaMallocHost");
+  if (rc == MPPI_OK) rc = c->cuda(cudaStreamSynchronize(c->stream), "sync");
+  if (rc != MPPI_OK) {
+    g_create_error = c->err;
+    mppi_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MPPI_OK;
+}
+
+int mppi_destroy(mppi_ctx *c) {
+  if (!c) return MPPI_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->arena.base) cudaFree(c->arena.base);
+  if (c->d_du) cudaFree(c->d_du);
+  if (c->d_env) cudaFree(c->d_env);
+  if (c->h_x0) cudaFreeHost(c->h_x0);
+  if (c->h_u0) cudaFreeHost(c->h_u0);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return MPPI_OK;
+}
+
+int mppi_set_stream(mppi_ctx *c, void *stream) {
+  if (!c) return MPPI_EINVAL;
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  c->own_stream = false;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->graph_dirty = true;
+  return MPPI_OK;
+}
+
+int mppi_set_impl(mppi_ctx *c, mppi_impl impl) {
+  if (!c || (impl != MPPI_IMPL_FUSED && impl != MPPI_IMPL_PLAIN)) return MPPI_EINVAL;
+  c->impl = impl;
+  return MPPI_OK;
+}
+
+int mppi_set_seed(mppi_ctx *c, uint64_t seed) {
+  if (!c) return MPPI_EINVAL;
+  c->seed = seed;
+  c->p.key_lo = static_cast<uint32_t>(seed & 0xffffffffu);
+  c->p.key_hi = static_cast<uint32_t>(seed >> 32);
+  c->graph_dirty = true;
+  return MPPI_OK;
+}
+
+int mppi_set_controller_id(mppi_ctx *c, uint32_t gid) {
+  if (!c) return MPPI_EINVAL;
+  c->p.gid = gid;
+  c->graph_dirty = true;
+  return MPPI_OK;
+}
+
+int mppi_set_iteration(mppi_ctx *c, uint32_t counter) {
+  if (!c) return MPPI_EINVAL;
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(&c->d_st->counter, &counter, sizeof counter, cudaMemcpyHostToDevice, c->stream),
+                   "counter copy"));
+  return c->cuda(cudaStreamSynchronize(c->stream), "sync");
+}
+
+int mppi_get_iteration(mppi_ctx *c, uint32_t *counter) {
+  if (!c || !counter) return MPPI_EINVAL;
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(counter, &c->d_st->counter, sizeof *counter, cudaMemcpyDeviceToHost, c->stream),
+                   "counter copy"));
+  return c->cuda(cudaStreamSynchronize(c->stream), "sync");
+}
+
+int mppi_set_controls(mppi_ctx *c, const float *U) {
+  if (!c || !U) return MPPI_EINVAL;
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_U, U, sizeof(float) * c->T * c->m, cudaMemcpyHostToDevice, c->stream),
+                   "U copy"));
+  return c->cuda(cudaStreamSynchronize(c->stream), "sync");
+}
+
+int mppi_get_controls(mppi_ctx *c, float *U) {
+  if (!c || !U) return MPPI_EINVAL;
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->T * c->m, cudaMemcpyDeviceToHost, c->stream),
+                   "U copy"));
+  return c->cuda(cudaStreamSynchronize(c->stream), "sync");
+}
+
+int mppi_set_u_init(mppi_ctx *c, const float *u) {
+  if (!c || !u) return MPPI_EINVAL;
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_uinit, u, sizeof(float) * c->m, cudaMemcpyHostToDevice, c->stream),
+                   "u_init copy"));
+  return c->cuda(cudaStreamSynchronize(c->stream), "sync");
+}
+
+int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
+  if (!c || !blob || bytes < sizeof(uint32_t)) return MPPI_EINVAL;
+  uint32_t kind;
+  std::memcpy(&kind, blob, sizeof kind);
+  const char *payload = nullptr;
+  size_t payload_bytes = 0;
+  CtrlParams np = c->p;
+  if (kind == MPPI_ENV_MAP) {
+    if (c->sys != MPPI_CAR && c->sys != MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "map env for a non-car system");
+    if (bytes < sizeof(mppi_env_map)) return c->fail(MPPI_EINVAL, "map header truncated");
+    mppi_env_map h;
+    std::memcpy(&h, blob, sizeof h);
+    if (h.width < 2 || h.height < 2 || h.width > 16384 || h.height > 16384)
+      return c->fail(MPPI_EINVAL, "map size out of range [2, 16384]");
+    if (!(h.cell > 0.0f) || !std::isfinite(h.origin_x) || !std::isfinite(h.origin_y))
+      return c->fail(MPPI_EINVAL, "bad map geometry");
+    payload_bytes = sizeof(float) * static_cast<size_t>(h.width) * h.height;
+    if (bytes != sizeof h + payload_bytes) return c->fail(MPPI_EINVAL, "map blob size mismatch");
+    payload = static_cast<const char *>(blob) + sizeof h;
+    np.map_w = h.width;
+    np.map_h = h.height;
+    np.map_ox = h.origin_x;
+    np.map_oy = h.origin_y;
+    np.map_inv_cell = 1.0f / h.cell;
+    np.n_obs = 0;
+  } else if (kind == MPPI_ENV_FOREST) {
+    if (c->sys != MPPI_QUAD) return c->fail(MPPI_EINVAL, "forest env for a non-quadrotor system");
+    if (bytes < sizeof(mppi_env_forest)) return c->fail(MPPI_EINVAL, "forest header truncated");
+    mppi_env_forest h;
+    std::memcpy(&h, blob, sizeof h);
+    if (h.n_obstacles < 0 || h.n_obstacles > 256) return c->fail(MPPI_EINVAL, "n_obstacles out of range [0, 256]");
+    payload_bytes = sizeof(float) * 3 * static_cast<size_t>(h.n_obstacles);
+    if (bytes != sizeof h + payload_bytes) return c->fail(MPPI_EINVAL, "forest blob size mismatch");
+    payload = static_cast<const char *>(blob) + sizeof h;
+    np.n_obs = h.n_obstacles;
+    for (int i = 0; i < 3; ++i) np.goal[i] = h.goal[i];
+    if (fused_block_size(np) == 0) return c->fail(MPPI_EINVAL, "forest too large for shared memory");
+  } else {
+    return c->fail(MPPI_EINVAL, "unknown env kind 0x%08x", kind);
+  }
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
+  if (c->d_env && c->env_bytes < payload_bytes) {
+    cudaFree(c->d_env);
+    c->d_env = nullptr;
+    c->env_bytes = 0;
+  }
+  if (!c->d_env && payload_bytes > 0) {
+    MPPI_TRY(c->cuda(cudaMalloc(&c->d_env, payload_bytes), "cudaMalloc(env)"));
+    c->env_bytes = payload_bytes;
+  }
+  if (payload_bytes > 0)
+    MPPI_TRY(c->cuda(cudaMemcpy(c->d_env, payload, payload_bytes, cudaMemcpyHostToDevice), "env copy"));
+  if (kind == MPPI_ENV_MAP) {
+    np.map = c->d_env;
+    np.obs = nullptr;
+  } else {
+    np.obs = c->d_env;
+    np.map = nullptr;
+  }
+  c->p = np;
+  c->blk = fused_block_size(c->p);
+  c->nblk = (c->K + c->blk - 1) / c->blk;
+  c->env_ok = true;
+  c->graph_dirty = true;
+  return MPPI_OK;
+}
+
+int mppi_step(mppi_ctx *c, const float *state, float *u0_out) {
+  if (!c || !state || !u0_out) return MPPI_EINVAL;
+  MPPI_TRY(check_ready(c));
+  std::memcpy(c->h_x0, state, sizeof(float) * c->n);
+  if (c->impl == MPPI_IMPL_PLAIN) {
+    MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_st->x0, c->h_x0, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream),
+                     "x0 copy"));
+    MPPI_TRY(enqueue_plain(c, c->stream));
+    MPPI_TRY(c->cuda(cudaMemcpyAsync(c->h_u0, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToHost, c->stream),
+                     "u0 copy"));
+  } else if (c->stream == nullptr) {
+    // the legacy stream cannot be captured: launch directly
+    MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_st->x0, c->h_x0, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream),
+                     "x0 copy"));
+    MPPI_TRY(enqueue_fused(c, c->stream));
+    MPPI_TRY(c->cuda(cudaMemcpyAsync(c->h_u0, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToHost, c->stream),
+                     "u0 copy"));
+  } else {
+    if (c->graph_dirty) MPPI_TRY(build_graph(c));
+    MPPI_TRY(c->cuda(cudaGraphLaunch(c->graph, c->stream), "graph launch"));
+  }
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
+  std::memcpy(u0_out, c->h_u0, sizeof(float) * c->m);
+  return MPPI_OK;
+}
+
+int mppi_rollout_async(mppi_ctx *c, const float *d_state) {
+  if (!c || !d_state) return MPPI_EINVAL;
+  MPPI_TRY(check_ready(c));
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_st->x0, d_state, sizeof(float) * c->n, cudaMemcpyDeviceToDevice, c->stream),
+                   "x0 copy"));
+  if (c->impl == MPPI_IMPL_PLAIN) {
+    MPPI_TRY(ensure_noise_buffer(c));
+    MPPI_TRY(c->cuda(launch_plain_noise(c->p, &c->d_st->counter, c->d_du, c->stream), "plain noise"));
+    return c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->d_U, c->d_du, c->d_S, c->stream), "plain rollout");
+  }
+  return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, c->stream),
+                 "fused rollout launch");
+}
+
+int mppi_update_async(mppi_ctx *c, float *d_u0_out) {
+  if (!c) return MPPI_EINVAL;
+  MPPI_TRY(check_ready(c));
+  if (c->impl == MPPI_IMPL_PLAIN)
+    MPPI_TRY(c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, c->stream),
+                     "plain reduce/update"));
+  else
+    MPPI_TRY(c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->d_u0, c->d_dU, c->d_dbg,
+                                         c->stream),
+                     "merge launch"));
+  if (d_u0_out)
+    MPPI_TRY(c->cuda(cudaMemcpyAsync(d_u0_out, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToDevice, c->stream),
+                     "u0 copy"));
+  return MPPI_OK;
+}
+
+int mppi_step_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
+  MPPI_TRY(mppi_rollout_async(c, d_state));
+  return mppi_update_async(c, d_u0_out);
+}
+
+int mppi_shift(mppi_ctx *c) {
+  if (!c) return MPPI_EINVAL;
+  return c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+}
+
+int mppi_get_debug(mppi_ctx *c, float *S, int *argmin, double *eta, float *dU) {
+  if (!c) return MPPI_EINVAL;
+  StepDebug d;
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(&d, c->d_dbg, sizeof d, cudaMemcpyDeviceToHost, c->stream), "dbg copy"));
+  if (S) MPPI_TRY(c->cuda(cudaMemcpyAsync(S, c->d_S, sizeof(float) * c->K, cudaMemcpyDeviceToHost, c->stream), "S"));
+  if (dU)
+    MPPI_TRY(c->cuda(cudaMemcpyAsync(dU, c->d_dU, sizeof(float) * c->T * c->m, cudaMemcpyDeviceToHost, c->stream),
+                     "dU"));
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
+  if (argmin) *argmin = d.kstar;
+  if (eta) *eta = d.eta;
+  return MPPI_OK;
+}
+
+int mppi_get_noise(mppi_ctx *c, uint32_t counter, float *h_du) {
+  if (!c || !h_du) return MPPI_EINVAL;
+  MPPI_TRY(ensure_noise_buffer(c));
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_ctr, &counter, sizeof counter, cudaMemcpyHostToDevice, c->stream), "ctr"));
+  MPPI_TRY(c->cuda(launch_plain_noise(c->p, c->d_ctr, c->d_du, c->stream), "noise launch"));
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(h_du, c->d_du, sizeof(float) * static_cast<size_t>(c->T) * c->m * c->K,
+                                   cudaMemcpyDeviceToHost, c->stream),
+                   "noise copy"));
+  return c->cuda(cudaStreamSynchronize(c->stream), "sync");
+}
+
+int mppi_philox_words(uint64_t seed, int K, int n_blocks, uint32_t counter, uint32_t gid, uint32_t *h_out) {
+  if (K < 1 || n_blocks < 1 || n_blocks > 65535 || !h_out || static_cast<size_t>(K) * n_blocks > (1u << 26))
+    return MPPI_EINVAL;
+  const size_t bytes = sizeof(uint32_t) * 4 * static_cast<size_t>(K) * n_blocks;
+  uint32_t *d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MPPI_ENOMEM;
+  }
+  cudaError_t e = launch_philox_words(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), K, n_blocks,
+                                      counter, gid, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(h_out, d, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    g_create_error = cudaGetErrorString(e);
+    cudaGetLastError();
+    return MPPI_ECUDA;
+  }
+  return MPPI_OK;
+}
+
+}  // extern "C"

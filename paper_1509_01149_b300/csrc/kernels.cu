@@ -1,0 +1,569 @@
+// MPPI iteration kernels for sm_103a.
+//
+// Fused path (two launches per iteration):
+//   k_rollout_fused  one thread per sample k.  Philox noise -> du (kept in shared
+//                    memory) -> T dynamics steps with the state in registers ->
+//                    q + importance-sampling running cost (Kahan FP32) -> phi.
+//                    Then, per block: rho_b = min S~, w_k = exp(-(S~_k - rho_b)/lambda),
+//                    eta_b = sum w_k (FP64) and the FP32 block sums sum_k w_k du_{i,k}.
+//   k_merge_update   FP64 merge of the block partials (flash-softmax style):
+//                    rho = min rho_b, eta = sum_b eta_b e^{-(rho_b - rho)/lambda},
+//                    du_i = sum_b e^{-(rho_b-rho)/lambda} part_b[i] / eta; U += du.
+// The min shift is exact algebra: it cancels between numerator and denominator of
+// Eq. App_PI and only keeps the exponentials in range.
+//
+// Plain loop (the single-controller baseline): noise -> HBM, rollout reading du
+// from HBM, single-block min, single-block normaliser, one block per output for
+// the weighted sum (FP64 throughout).
+#include <cfloat>
+#include <climits>
+
+#include "kernels.cuh"
+#include "systems.cuh"
+
+namespace mppi {
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs) {
+  Env e;
+  e.map = p.map;
+  e.map_w = p.map_w;
+  e.map_h = p.map_h;
+  e.map_ox = p.map_ox;
+  e.map_oy = p.map_oy;
+  e.map_inv_cell = p.map_inv_cell;
+  e.obs = obs;
+  e.n_obs = p.n_obs;
+  e.gx = p.goal[0];
+  e.gy = p.goal[1];
+  e.gz = p.goal[2];
+  return e;
+}
+
+// du_j = sum_{l <= j} Lnu[j][l] eps_l  (Lnu = sqrt(nu) chol(Sigma), lower triangular)
+template <int M>
+__device__ __forceinline__ void scale_noise(const float *Lnu, const float *eps, float *du) {
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    float a = 0.0f;
+#pragma unroll
+    for (int l = 0; l <= j; ++l) a = fmaf(Lnu[j * M + l], eps[l], a);
+    du[j] = a;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused rollout
+// ---------------------------------------------------------------------------
+template <class Sys, int BLK>
+__global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const CtrlState *__restrict__ st,
+                                                       const float *__restrict__ U, float *__restrict__ S_out,
+                                                       float *__restrict__ part_sums,
+                                                       BlockPartial *__restrict__ part) {
+  constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M, NW = BLK / 32;
+  static_assert(4 % M == 0, "controls per Philox block must divide 4");
+  extern __shared__ __align__(16) float smem[];
+  __shared__ float s_min[NW];
+  __shared__ int s_idx[NW];
+  __shared__ double s_eta[NW];
+
+  const int T = p.T, TM = T * M, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float *sU = smem;                 // [TM]  nominal controls
+  float *sRu = sU + TM;             // [TM]  R u_i
+  float *sHu = sRu + TM;            // [T]   1/2 u_i^T R u_i
+  float *sObs = sHu + T;            // [3 n_obs]
+  float *sW = sObs + 3 * p.n_obs;   // [BLK] weights
+  float *sDu = sW + BLK;            // [TM][BLK] perturbations of this block
+
+  for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
+  for (int o = tid; o < 3 * p.n_obs; o += BLK) sObs[o] = p.obs[o];
+  __syncthreads();
+  for (int i = tid; i < T; i += BLK) {
+    float h = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float ru = 0.0f;
+#pragma unroll
+      for (int l = 0; l < M; ++l) ru = fmaf(p.R[j * M + l], sU[i * M + l], ru);
+      sRu[i * M + j] = ru;
+      h = fmaf(sU[i * M + j], ru, h);
+    }
+    sHu[i] = 0.5f * h;
+  }
+  __syncthreads();
+
+  const Env env = make_env(p, sObs);
+  const int k = blockIdx.x * BLK + tid;
+  const bool valid = k < p.K;
+  float Lnu[M * M], R[M * M];
+#pragma unroll
+  for (int a = 0; a < M * M; ++a) {
+    Lnu[a] = p.Lnu[a];
+    R[a] = p.R[a];
+  }
+  float x[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) x[a] = st->x0[a];
+  const uint32_t ctr = st->counter;
+  typename Sys::Aux aux;
+  Sys::init(x, aux, env);
+  KahanSum S;
+
+  const int nb = (TM + 3) >> 2;
+  for (int b = 0; b < nb; ++b) {
+    float eps[4];
+    normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+#pragma unroll
+    for (int s = 0; s < SPB; ++s) {
+      const int i = b * SPB + s;
+      if (i < T) {
+        float du[M], v[M];
+        scale_noise<M>(Lnu, eps + s * M, du);
+        float duRdu = 0.0f, uRdu = 0.0f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          v[j] = sU[i * M + j] + du[j];
+          sDu[(i * M + j) * BLK + tid] = du[j];
+          uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
+          float rd = 0.0f;
+#pragma unroll
+          for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
+          duRdu = fmaf(du[j], rd, duRdu);
+        }
+        Sys::step(x, v, aux, env, p.dt);
+        const float q = Sys::cost(x, aux, env);
+        S.add(q + (p.is_du * duRdu + uRdu + sHu[i]));
+      }
+    }
+  }
+  S.add(Sys::cost(x, aux, env));  // phi(x_T) = q(x_T)
+
+  float Sk = S.s;
+  if (!valid || !isfinite(Sk)) Sk = INFINITY;
+  if (valid) S_out[k] = Sk;
+
+  // block minimum (lowest index on ties)
+  float mv = Sk;
+  int mi = valid ? k : INT_MAX;
+  warp_argmin(mv, mi);
+  if (lane == 0) {
+    s_min[warp] = mv;
+    s_idx[warp] = mi;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float v = lane < NW ? s_min[lane] : INFINITY;
+    int ii = lane < NW ? s_idx[lane] : INT_MAX;
+    warp_argmin(v, ii);
+    if (lane == 0) {
+      s_min[0] = v;
+      s_idx[0] = ii;
+    }
+  }
+  __syncthreads();
+  const float rho_b = s_min[0];
+  const float w = (isfinite(rho_b) && isfinite(Sk)) ? expf(-(Sk - rho_b) * p.inv_lambda) : 0.0f;
+  sW[tid] = w;
+  const double e = warp_sum_d(static_cast<double>(w));
+  if (lane == 0) s_eta[warp] = e;
+  __syncthreads();
+
+  // block sums of w_k du_{i,k}: warp per output, lanes over the block's samples (FP32)
+  float *dst = part_sums + static_cast<size_t>(blockIdx.x) * TM;
+  for (int o = warp; o < TM; o += NW) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < BLK / 32; ++c) acc = fmaf(sW[lane + 32 * c], sDu[o * BLK + lane + 32 * c], acc);
+    acc = warp_sum_f(acc);
+    if (lane == 0) dst[o] = acc;
+  }
+  if (tid == 0) {
+    double eta_b = 0.0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) eta_b += s_eta[q];
+    BlockPartial bp;
+    bp.eta = eta_b;
+    bp.rho = rho_b;
+    bp.kstar = s_idx[0];
+    part[blockIdx.x] = bp;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 merge of block partials + update of U
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM, int m, float inv_lambda,
+                                                                const float *__restrict__ part_sums,
+                                                                const BlockPartial *__restrict__ part,
+                                                                float *__restrict__ U, float *__restrict__ u0_out,
+                                                                float *__restrict__ dU_dbg,
+                                                                StepDebug *__restrict__ dbg) {
+  constexpr int NW = kMergeThreads / 32;
+  extern __shared__ double s_scale[];  // [nblk]
+  __shared__ float s_rho[NW];
+  __shared__ int s_k[NW];
+  __shared__ double s_e[NW];
+  __shared__ double s_acc[NW][kMergeOutputs];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  float v = INFINITY;
+  int idx = INT_MAX;
+  for (int b = tid; b < nblk; b += kMergeThreads) {
+    const float r = part[b].rho;
+    const int kk = part[b].kstar;
+    if (r < v || (r == v && kk < idx)) {
+      v = r;
+      idx = kk;
+    }
+  }
+  warp_argmin(v, idx);
+  if (lane == 0) {
+    s_rho[warp] = v;
+    s_k[warp] = idx;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float vv = lane < NW ? s_rho[lane] : INFINITY;
+    int ii = lane < NW ? s_k[lane] : INT_MAX;
+    warp_argmin(vv, ii);
+    if (lane == 0) {
+      s_rho[0] = vv;
+      s_k[0] = ii;
+    }
+  }
+  __syncthreads();
+  const float rho = s_rho[0];
+
+  double e = 0.0;
+  for (int b = tid; b < nblk; b += kMergeThreads) {
+    const float rb = part[b].rho;
+    const double sc = (isfinite(rho) && isfinite(rb)) ? static_cast<double>(expf(-(rb - rho) * inv_lambda)) : 0.0;
+    s_scale[b] = sc;
+    e += sc * part[b].eta;
+  }
+  e = warp_sum_d(e);
+  if (lane == 0) s_e[warp] = e;
+  __syncthreads();
+  double eta = 0.0;
+#pragma unroll
+  for (int q = 0; q < NW; ++q) eta += s_e[q];
+
+  const int o = blockIdx.x * kMergeOutputs + lane;
+  double acc = 0.0;
+  if (o < TM)
+    for (int b = warp; b < nblk; b += NW) acc += s_scale[b] * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
+  s_acc[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && o < TM) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) t += s_acc[q][lane];
+    const double du = eta > 0.0 ? t / eta : 0.0;
+    const float un = U[o] + static_cast<float>(du);
+    U[o] = un;
+    dU_dbg[o] = static_cast<float>(du);
+    if (o < m) u0_out[o] = un;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    dbg->rho = rho;
+    dbg->kstar = s_k[0];
+    dbg->eta = eta;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// shift (Algorithm 1): u_i <- u_{i+1}, u_{T-1} <- u_init; counter += 1
+// ---------------------------------------------------------------------------
+__global__ void k_shift(float *__restrict__ U, const float *__restrict__ u_init, int TM, int m,
+                        CtrlState *__restrict__ st) {
+  extern __shared__ float s_u[];
+  for (int o = threadIdx.x; o < TM; o += blockDim.x) s_u[o] = U[o];
+  __syncthreads();
+  for (int o = threadIdx.x; o < TM; o += blockDim.x) U[o] = (o + m < TM) ? s_u[o + m] : u_init[o - (TM - m)];
+  if (threadIdx.x == 0) st->counter += 1u;
+}
+
+// ---------------------------------------------------------------------------
+// plain-loop baseline kernels
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_plain_noise(const CtrlParams p, const uint32_t *__restrict__ counter, float *__restrict__ du) {
+  constexpr int SPB = 4 / M;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (k >= p.K) return;
+  float eps[4];
+  normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), *counter, p.gid, p.key_lo, p.key_hi, eps);
+  float Lnu[M * M];
+#pragma unroll
+  for (int a = 0; a < M * M; ++a) Lnu[a] = p.Lnu[a];
+#pragma unroll
+  for (int s = 0; s < SPB; ++s) {
+    const int i = b * SPB + s;
+    if (i < p.T) {
+      float d[M];
+      scale_noise<M>(Lnu, eps + s * M, d);
+#pragma unroll
+      for (int j = 0; j < M; ++j) du[static_cast<size_t>(i * M + j) * p.K + k] = d[j];
+    }
+  }
+}
+
+template <class Sys>
+__global__ void __launch_bounds__(128) k_plain_rollout(const CtrlParams p, const CtrlState *__restrict__ st,
+                                                       const float *__restrict__ U, const float *__restrict__ du,
+                                                       float *__restrict__ S_out) {
+  constexpr int M = Sys::M, N = Sys::N;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= p.K) return;
+  const Env env = make_env(p, p.obs);
+  float x[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) x[a] = st->x0[a];
+  typename Sys::Aux aux;
+  Sys::init(x, aux, env);
+  KahanSum S;
+  for (int i = 0; i < p.T; ++i) {
+    float d[M], v[M], u[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      u[j] = U[i * M + j];
+      d[j] = du[static_cast<size_t>(i * M + j) * p.K + k];
+      v[j] = u[j] + d[j];
+    }
+    float duRdu = 0.0f, uRdu = 0.0f, uRu = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float rd = 0.0f, ru = 0.0f;
+#pragma unroll
+      for (int l = 0; l < M; ++l) {
+        rd = fmaf(p.R[j * M + l], d[l], rd);
+        ru = fmaf(p.R[j * M + l], u[l], ru);
+      }
+      duRdu = fmaf(d[j], rd, duRdu);
+      uRdu = fmaf(ru, d[j], uRdu);
+      uRu = fmaf(u[j], ru, uRu);
+    }
+    Sys::step(x, v, aux, env, p.dt);
+    S.add(Sys::cost(x, aux, env) + (p.is_du * duRdu + uRdu + 0.5f * uRu));
+  }
+  S.add(Sys::cost(x, aux, env));
+  const float Sk = S.s;
+  S_out[k] = isfinite(Sk) ? Sk : INFINITY;
+}
+
+__global__ void __launch_bounds__(1024) k_plain_min(const float *__restrict__ S, int K, StepDebug *__restrict__ dbg) {
+  __shared__ float s_v[32];
+  __shared__ int s_i[32];
+  float v = INFINITY;
+  int idx = INT_MAX;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    if (S[k] < v || (S[k] == v && k < idx)) {
+      v = S[k];
+      idx = k;
+    }
+  }
+  warp_argmin(v, idx);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_v[warp] = v;
+    s_i[warp] = idx;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    v = lane < nw ? s_v[lane] : INFINITY;
+    idx = lane < nw ? s_i[lane] : INT_MAX;
+    warp_argmin(v, idx);
+    if (lane == 0) {
+      dbg->rho = v;
+      dbg->kstar = (idx == INT_MAX) ? 0 : idx;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_plain_eta(const float *__restrict__ S, int K, float inv_lambda,
+                                                    StepDebug *__restrict__ dbg) {
+  __shared__ double s_e[32];
+  const float rho = dbg->rho;
+  double e = 0.0;
+  if (isfinite(rho))
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+      if (isfinite(S[k])) e += exp(-static_cast<double>(S[k] - rho) * inv_lambda);
+  e = warp_sum_d(e);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_e[warp] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) t += s_e[q];
+    dbg->eta = t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_plain_wsum(const float *__restrict__ S, const float *__restrict__ du, int K,
+                                                    int m, float inv_lambda, const StepDebug *__restrict__ dbg,
+                                                    float *__restrict__ U, float *__restrict__ u0_out,
+                                                    float *__restrict__ dU_dbg) {
+  __shared__ double s_a[8];
+  const int o = blockIdx.x;
+  const float rho = dbg->rho;
+  const double eta = dbg->eta;
+  double acc = 0.0;
+  if (isfinite(rho))
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+      if (isfinite(S[k]))
+        acc += exp(-static_cast<double>(S[k] - rho) * inv_lambda) * static_cast<double>(du[static_cast<size_t>(o) * K + k]);
+  acc = warp_sum_d(acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_a[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += s_a[q];
+    const double d = eta > 0.0 ? t / eta : 0.0;
+    const float un = U[o] + static_cast<float>(d);
+    U[o] = un;
+    dU_dbg[o] = static_cast<float>(d);
+    if (o < m) u0_out[o] = un;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// debug
+// ---------------------------------------------------------------------------
+__global__ void k_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_blocks, uint32_t counter, uint32_t gid,
+                               uint32_t *__restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (k >= K || b >= n_blocks) return;
+  const Words4 w = philox4x32_10(static_cast<uint32_t>(b), static_cast<uint32_t>(k), counter, gid, key_lo, key_hi);
+  uint32_t *o = out + static_cast<size_t>(b) * 4 * K + k;
+  o[0] = w.x;
+  o[static_cast<size_t>(K)] = w.y;
+  o[2 * static_cast<size_t>(K)] = w.z;
+  o[3 * static_cast<size_t>(K)] = w.w;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+size_t fused_smem_bytes(const CtrlParams &p, int blk) {
+  const size_t TM = static_cast<size_t>(p.T) * p.m;
+  return sizeof(float) * (2 * TM + p.T + 3 * static_cast<size_t>(p.n_obs) + blk + TM * blk);
+}
+
+int fused_block_size(const CtrlParams &p) {
+  if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;
+  if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
+  return 0;
+}
+
+template <class Sys, int BLK>
+static cudaError_t launch_fused_t(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *ps,
+                                  BlockPartial *part, cudaStream_t s) {
+  const size_t smem = fused_smem_bytes(p, BLK);
+  const int grid = (p.K + BLK - 1) / BLK;
+  k_rollout_fused<Sys, BLK><<<grid, BLK, smem, s>>>(p, st, U, S, ps, part);
+  return cudaGetLastError();
+}
+
+template <class Sys>
+static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const CtrlState *st, const float *U, float *S,
+                                    float *ps, BlockPartial *part, cudaStream_t s) {
+  if (blk == kFusedBlockLarge) return launch_fused_t<Sys, kFusedBlockLarge>(p, st, U, S, ps, part, s);
+  if (blk == kFusedBlockSmall) return launch_fused_t<Sys, kFusedBlockSmall>(p, st, U, S, ps, part, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const CtrlState *st, const float *U,
+                                 float *S, float *part_sums, BlockPartial *part, cudaStream_t s) {
+  switch (sys) {
+    case 0: return launch_fused_sys<CartPole>(blk, p, st, U, S, part_sums, part, s);
+    case 1: return launch_fused_sys<Car>(blk, p, st, U, S, part_sums, part, s);
+    case 2: return launch_fused_sys<Quad>(blk, p, st, U, S, part_sums, part, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t prepare_kernels() {
+  // dynamic shared memory above the 48 KB default, set once (outside any capture)
+  const int big = 220 * 1024;
+  const void *fns[] = {
+      reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockLarge>),
+      reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockSmall>),
+      reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge>),
+      reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall>),
+      reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge>),
+      reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall>),
+      reinterpret_cast<const void *>(k_merge_update),
+  };
+  for (const void *f : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
+                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
+  const int TM = p.T * p.m;
+  const size_t smem = sizeof(double) * static_cast<size_t>(nblk);
+  const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
+  k_merge_update<<<grid, kMergeThreads, smem, s>>>(nblk, TM, p.m, p.inv_lambda, part_sums, part, U, u0_out, dU_dbg,
+                                                    dbg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s) {
+  const int TM = p.T * p.m;
+  k_shift<<<1, 1024, sizeof(float) * TM, s>>>(U, u_init, TM, p.m, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_noise(const CtrlParams &p, const uint32_t *counter, float *du, cudaStream_t s) {
+  const int nb = (p.T * p.m + 3) / 4;
+  const dim3 grid((p.K + 255) / 256, nb);
+  switch (p.m) {
+    case 1: k_plain_noise<1><<<grid, 256, 0, s>>>(p, counter, du); break;
+    case 2: k_plain_noise<2><<<grid, 256, 0, s>>>(p, counter, du); break;
+    case 4: k_plain_noise<4><<<grid, 256, 0, s>>>(p, counter, du); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_rollout(int sys, const CtrlParams &p, const CtrlState *st, const float *U, const float *du,
+                                 float *S, cudaStream_t s) {
+  const int grid = (p.K + 127) / 128;
+  switch (sys) {
+    case 0: k_plain_rollout<CartPole><<<grid, 128, 0, s>>>(p, st, U, du, S); break;
+    case 1: k_plain_rollout<Car><<<grid, 128, 0, s>>>(p, st, U, du, S); break;
+    case 2: k_plain_rollout<Quad><<<grid, 128, 0, s>>>(p, st, U, du, S); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_reduce_update(const CtrlParams &p, const float *S, const float *du, float *U, float *u0_out,
+                                       float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
+  k_plain_min<<<1, 1024, 0, s>>>(S, p.K, dbg);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_plain_eta<<<1, 1024, 0, s>>>(S, p.K, p.inv_lambda, dbg);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_plain_wsum<<<p.T * p.m, 256, 0, s>>>(S, du, p.K, p.m, p.inv_lambda, dbg, U, u0_out, dU_dbg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_blocks, uint32_t counter,
+                                uint32_t gid, uint32_t *out, cudaStream_t s) {
+  const dim3 grid((K + 255) / 256, n_blocks);
+  k_philox_words<<<grid, 256, 0, s>>>(key_lo, key_hi, K, n_blocks, counter, gid, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mppi

@@ -1,0 +1,44 @@
+// Host-side launchers of the MPPI kernels (implemented in kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include "mppi_device.cuh"
+
+namespace mppi {
+
+// Block sizes the fused rollout is built for.
+constexpr int kFusedBlockLarge = 128;
+constexpr int kFusedBlockSmall = 64;
+constexpr int kMergeThreads = 256;
+constexpr int kMergeOutputs = 32;       // outputs (i, j) per merge block
+constexpr size_t kFusedSmemLimit = 200 * 1024;
+
+// Raise the dynamic shared-memory limit of the kernels that need it (once per
+// device, before any launch or capture).
+cudaError_t prepare_kernels();
+
+// Fused path ---------------------------------------------------------------
+// Shared memory of the fused rollout for block size blk (bytes).
+size_t fused_smem_bytes(const CtrlParams &p, int blk);
+// Block size for this controller (largest of 128/64 whose shared memory fits), or 0.
+int fused_block_size(const CtrlParams &p);
+// Rollout + cost + IS term + block-local weights and weighted perturbation sums.
+cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const CtrlState *st, const float *U,
+                                 float *S, float *part_sums, BlockPartial *part, cudaStream_t s);
+// Cross-block FP64 merge: rho, kstar, eta, du; U += du; u0 out.
+cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
+                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s);
+// Shift of Algorithm 1 and iteration counter increment.
+cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s);
+
+// Plain-loop baseline ---------------------------------------------------------
+cudaError_t launch_plain_noise(const CtrlParams &p, const uint32_t *counter, float *du, cudaStream_t s);
+cudaError_t launch_plain_rollout(int sys, const CtrlParams &p, const CtrlState *st, const float *U,
+                                 const float *du, float *S, cudaStream_t s);
+cudaError_t launch_plain_reduce_update(const CtrlParams &p, const float *S, const float *du, float *U,
+                                       float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s);
+
+// Debug ------------------------------------------------------------------------
+cudaError_t launch_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_blocks, uint32_t counter,
+                                uint32_t gid, uint32_t *out, cudaStream_t s);
+
+}  // namespace mppi

@@ -1,0 +1,141 @@
+// Device primitives of the MPPI hot path: counter-based noise, compensated sums,
+// warp reductions and the kernel argument blocks.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mppi {
+
+constexpr int kMaxM = 4;   // largest control dimension of the built-in systems
+constexpr int kMaxN = 16;  // largest state dimension (padded)
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
+// multiplies on the counter, key bumped by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+struct Words4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return Words4{c0, c1, c2, c3};
+}
+
+// 23 random bits, centred in their cell: exact in FP32, inside [2^-24, 1 - 2^-24].
+__device__ __forceinline__ float unit_uniform(uint32_t w) {
+  return (static_cast<float>(w >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
+}
+
+// Box-Muller on one pair of words: rad = sqrt(-2 ln ua), angle 2 pi ub.
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &e0, float &e1) {
+  const float rad = sqrtf(-2.0f * logf(unit_uniform(wa)));
+  float s, c;
+  sincospif(2.0f * unit_uniform(wb), &s, &c);
+  e0 = rad * c;
+  e1 = rad * s;
+}
+
+// Four standard normals of Philox block (b, k, counter, gid).
+__device__ __forceinline__ void normals4(uint32_t b, uint32_t k, uint32_t counter, uint32_t gid,
+                                         uint32_t key_lo, uint32_t key_hi, float e[4]) {
+  const Words4 w = philox4x32_10(b, k, counter, gid, key_lo, key_hi);
+  box_muller(w.x, w.y, e[0], e[1]);
+  box_muller(w.z, w.w, e[2], e[3]);
+}
+
+// Kahan-compensated FP32 accumulator for the path cost.
+struct KahanSum {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// (value, index) minimum, lowest index on ties; +inf values never win over finite ones.
+__device__ __forceinline__ void warp_argmin(float &v, int &idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov < v || (ov == v && oi < idx)) {
+      v = ov;
+      idx = oi;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// argument blocks
+// ---------------------------------------------------------------------------
+// Per-controller constants (by value in the kernel argument space).
+struct CtrlParams {
+  int K, T, m, n;
+  float dt, nu, lambda, inv_lambda;
+  float is_du;              // (1 - 1/nu) / 2: weight of du^T R du in q~
+  float Lnu[kMaxM * kMaxM]; // sqrt(nu) * chol(Sigma), row-major lower triangle
+  float R[kMaxM * kMaxM];   // control-cost matrix, row-major
+  uint32_t key_lo, key_hi, gid;
+  // environment
+  const float *map;         // car cost map [H][W]
+  int map_w, map_h;
+  float map_ox, map_oy, map_inv_cell;
+  const float *obs;         // quadrotor cylinders [n_obs][3]
+  int n_obs;
+  float goal[3];
+  const void *mlp;          // learned dynamics weights (car_mlp)
+};
+
+// Per-controller mutable device state.
+struct CtrlState {
+  float x0[kMaxN];   // current state (written by the step's H2D copy)
+  uint32_t counter;  // iteration counter c (Philox counter word 2)
+  uint32_t pad[3];
+};
+
+// Per-block partial of the fused rollout (flash-softmax style merge later).
+struct BlockPartial {
+  double eta;    // sum over the block of exp(-(S~ - rho_b)/lambda), FP64
+  float rho;     // block minimum of S~ (+inf if none finite)
+  int kstar;     // lowest sample index attaining rho
+};
+
+// Results of the last iteration for the debug ABI.
+struct StepDebug {
+  double eta;
+  float rho;
+  int kstar;
+};
+
+}  // namespace mppi

@@ -1,0 +1,231 @@
+// The three plants of the MPPI workloads and their state costs, FP32 device code.
+//
+// Each model provides N (state size), M (control size), an Aux register block,
+//   init(x, aux, env)          -- set up per-sample auxiliaries at x0
+//   step(x, v, aux, env, dt)   -- advance the state under control v = u_i + du_i
+//   cost(x, aux, env)          -- running state cost q at the current state
+// The terminal cost phi is q of the final state.
+//
+// Models (the paper's own car and quadrotor models come from external works;
+// these are the synthetic stand-ins of the workloads):
+//   CartPole  force input, pole-on-cart with a uniform rod of half-length l,
+//             explicit Euler (Sec. II-A); q = x^2 + xdot^2 + 10 theta^2 + thetadot^2.
+//   Car       dynamic bicycle, first-order steering actuator, simplified Pacejka
+//             tyres D sin(C atan(B alpha)); explicit Euler (position and heading sums
+//             Kahan-compensated); q = bilinear cost-map lookup + (vx - 7)^2 (speed
+//             term of Sec. V-B).
+//   Quad      12-state rigid body, four rotor thrusts in a "+" layout, ZYX Euler
+//             angles, RK4; q of Sec. V-C with crash weight 1e4.  A crash (cylinder,
+//             ground, |pitch| >= 1.4 rad or a non-finite step) stops the rollout: the
+//             state stays at the last valid state and the crash cost keeps accruing.
+#pragma once
+#include "mppi_device.cuh"
+
+namespace mppi {
+
+struct Env {
+  const float *__restrict__ map;
+  int map_w, map_h;
+  float map_ox, map_oy, map_inv_cell;
+  const float *obs;  // shared-memory copy of the cylinders, [n_obs][3]
+  int n_obs;
+  float gx, gy, gz;
+};
+
+// ---------------------------------------------------------------------------
+struct CartPole {
+  static constexpr int N = 4, M = 1;
+  struct Aux {};
+  static constexpr float mc = 1.0f, mp = 0.1f, l = 0.5f, g = 9.81f;
+
+  __device__ __forceinline__ static void init(const float *, Aux &, const Env &) {}
+
+  __device__ __forceinline__ static void step(float x[N], const float v[M], Aux &, const Env &, float dt) {
+    constexpr float Mt = mc + mp;
+    float s, c;
+    sincosf(x[2], &s, &c);
+    const float tmp = (v[0] + mp * l * x[3] * x[3] * s) / Mt;
+    const float th_acc = (g * s - c * tmp) / (l * (4.0f / 3.0f - mp * c * c / Mt));
+    const float x_acc = tmp - mp * l * th_acc * c / Mt;
+    x[0] += dt * x[1];
+    x[1] += dt * x_acc;
+    x[2] += dt * x[3];
+    x[3] += dt * th_acc;
+  }
+
+  __device__ __forceinline__ static float cost(const float x[N], const Aux &, const Env &) {
+    return x[0] * x[0] + x[1] * x[1] + 10.0f * x[2] * x[2] + x[3] * x[3];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Bilinear lookup of a cost map [H][W], node (ix, iy) at (ox + ix/inv_cell, oy + iy/inv_cell),
+// coordinates clamped to the grid (NaN clamps to node 0).
+__device__ __forceinline__ float map_bilinear(const Env &e, float X, float Y) {
+  const float fx = fminf(fmaxf((X - e.map_ox) * e.map_inv_cell, 0.0f), static_cast<float>(e.map_w - 1));
+  const float fy = fminf(fmaxf((Y - e.map_oy) * e.map_inv_cell, 0.0f), static_cast<float>(e.map_h - 1));
+  const int ix = min(static_cast<int>(fx), e.map_w - 2);
+  const int iy = min(static_cast<int>(fy), e.map_h - 2);
+  const float tx = fx - static_cast<float>(ix);
+  const float ty = fy - static_cast<float>(iy);
+  const float *row = e.map + static_cast<size_t>(iy) * e.map_w + ix;
+  const float m00 = __ldg(row), m10 = __ldg(row + 1);
+  const float m01 = __ldg(row + e.map_w), m11 = __ldg(row + e.map_w + 1);
+  const float a = m00 + tx * (m10 - m00);
+  const float b = m01 + tx * (m11 - m01);
+  return a + ty * (b - a);
+}
+
+struct Car {
+  static constexpr int N = 7, M = 2;
+  // Compensation terms of the three states that accumulate without bound (X, Y, psi):
+  // their Euler sums are Kahan-compensated so that FP32 rounding of a large position
+  // does not drift along the horizon.
+  struct Aux {
+    float cX, cY, cpsi;
+  };
+  static constexpr float m = 21.7f, Iz = 1.12f, lf = 0.34f, lr = 0.23f;
+  static constexpr float B = 4.0f, C = 1.8f, mu = 0.9f, g = 9.81f;
+  static constexpr float delta_max = 0.5f, tau_delta = 0.1f;
+  static constexpr float Cm = 120.0f, Crr = 2.0f, Cd = 0.35f, vx_floor = 1.0f, v_target = 7.0f;
+  static constexpr float Df = mu * m * g * lr / (lf + lr);
+  static constexpr float Dr = mu * m * g * lf / (lf + lr);
+
+  __device__ __forceinline__ static void init(const float *, Aux &a, const Env &) { a.cX = a.cY = a.cpsi = 0.0f; }
+
+  __device__ __forceinline__ static void deriv(const float x[N], const float v[M], float d[N]) {
+    const float vx = x[3], vy = x[4], r = x[5], delta = x[6];
+    const float inv_vxs = 1.0f / fmaxf(vx, vx_floor);
+    const float alpha_f = delta - atanf((vy + lf * r) * inv_vxs);
+    const float alpha_r = -atanf((vy - lr * r) * inv_vxs);
+    const float Fyf = Df * sinf(C * atanf(B * alpha_f));
+    const float Fyr = Dr * sinf(C * atanf(B * alpha_r));
+    const float Fx = Cm * v[1] - Crr * vx - Cd * vx * fabsf(vx);
+    float sp, cp, sd, cd;
+    sincosf(x[2], &sp, &cp);
+    sincosf(delta, &sd, &cd);
+    d[0] = vx * cp - vy * sp;
+    d[1] = vx * sp + vy * cp;
+    d[2] = r;
+    d[3] = (Fx - Fyf * sd) * (1.0f / m) + vy * r;
+    d[4] = (Fyr + Fyf * cd) * (1.0f / m) - vx * r;
+    d[5] = (lf * Fyf * cd - lr * Fyr) * (1.0f / Iz);
+    d[6] = (delta_max * v[0] - delta) * (1.0f / tau_delta);
+  }
+
+  // x += h with the running compensation c (Kahan): keeps the rounding of x out of the sum.
+  __device__ __forceinline__ static void comp_add(float &x, float &c, float h) {
+    const float y = h - c;
+    const float t = x + y;
+    c = (t - x) - y;
+    x = t;
+  }
+
+  __device__ __forceinline__ static void step(float x[N], const float v[M], Aux &a, const Env &, float dt) {
+    float d[N];
+    deriv(x, v, d);
+    comp_add(x[0], a.cX, dt * d[0]);
+    comp_add(x[1], a.cY, dt * d[1]);
+    comp_add(x[2], a.cpsi, dt * d[2]);
+#pragma unroll
+    for (int i = 3; i < N; ++i) x[i] += dt * d[i];
+  }
+
+  __device__ __forceinline__ static float cost(const float x[N], const Aux &, const Env &e) {
+    const float dv = x[3] - v_target;
+    return map_bilinear(e, x[0], x[1]) + dv * dv;
+  }
+};
+
+// ---------------------------------------------------------------------------
+struct Quad {
+  static constexpr int N = 12, M = 4;
+  struct Aux {
+    float d;       // obstacle distance at the current state
+    bool crashed;
+  };
+  static constexpr float mass = 0.5f, g = 9.81f, arm = 0.17f, kappa = 0.016f;
+  static constexpr float Ixx = 2.3e-3f, Iyy = 2.3e-3f, Izz = 4.0e-3f, pitch_limit = 1.4f;
+  static constexpr float w_xy = 2.5f, w_z = 150.0f, w_yaw = 50.0f, w_v = 1.0f;
+  static constexpr float w_obs = 350.0f, obs_scale = 12.0f, w_crash = 1.0e4f;
+
+  __device__ __forceinline__ static float obstacle_distance(const Env &e, float px, float py) {
+    float d = INFINITY;
+    for (int j = 0; j < e.n_obs; ++j) {
+      const float dx = px - e.obs[3 * j], dy = py - e.obs[3 * j + 1];
+      d = fminf(d, sqrtf(dx * dx + dy * dy) - e.obs[3 * j + 2]);
+    }
+    return d;
+  }
+
+  __device__ __forceinline__ static void init(const float *x, Aux &a, const Env &e) {
+    a.crashed = false;
+    a.d = obstacle_distance(e, x[0], x[1]);
+  }
+
+  __device__ __forceinline__ static void deriv(const float x[N], const float f[M], float d[N]) {
+    const float F = f[0] + f[1] + f[2] + f[3];
+    const float tx = arm * (f[1] - f[3]);
+    const float ty = arm * (f[2] - f[0]);
+    const float tz = kappa * (f[0] - f[1] + f[2] - f[3]);
+    float sph, cph, sth, cth, sps, cps;
+    sincosf(x[6], &sph, &cph);
+    sincosf(x[7], &sth, &cth);
+    sincosf(x[8], &sps, &cps);
+    const float a = F * (1.0f / mass);
+    d[0] = x[3];
+    d[1] = x[4];
+    d[2] = x[5];
+    d[3] = a * (cps * sth * cph + sps * sph);
+    d[4] = a * (sps * sth * cph - cps * sph);
+    d[5] = a * (cth * cph) - g;
+    const float wp = x[9], wq = x[10], wr = x[11];
+    const float ws = wq * sph + wr * cph;
+    const float inv_cth = 1.0f / cth;
+    d[6] = wp + ws * sth * inv_cth;
+    d[7] = wq * cph - wr * sph;
+    d[8] = ws * inv_cth;
+    d[9] = (tx - (Izz - Iyy) * wq * wr) * (1.0f / Ixx);
+    d[10] = (ty - (Ixx - Izz) * wr * wp) * (1.0f / Iyy);
+    d[11] = (tz - (Iyy - Ixx) * wp * wq) * (1.0f / Izz);
+  }
+
+  __device__ __forceinline__ static void step(float x[N], const float f[M], Aux &a, const Env &e, float dt) {
+    if (a.crashed) return;
+    float k1[N], k2[N], k3[N], k4[N], y[N];
+    deriv(x, f, k1);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = x[i] + 0.5f * dt * k1[i];
+    deriv(y, f, k2);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = x[i] + 0.5f * dt * k2[i];
+    deriv(y, f, k3);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = x[i] + dt * k3[i];
+    deriv(y, f, k4);
+    bool finite = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      y[i] = x[i] + (dt / 6.0f) * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
+      finite = finite && isfinite(y[i]);
+    }
+    const float d = finite ? obstacle_distance(e, y[0], y[1]) : -1.0f;
+    const bool hit = !finite || d < 0.0f || y[2] < 0.0f || (pitch_limit - fabsf(y[7])) <= 0.0f;
+    if (hit) {
+      a.crashed = true;  // state stays at the last valid state
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = y[i];
+      a.d = d;
+    }
+  }
+
+  __device__ __forceinline__ static float cost(const float x[N], const Aux &a, const Env &e) {
+    const float ex = x[0] - e.gx, ey = x[1] - e.gy, ez = x[2] - e.gz;
+    float c = w_xy * ex * ex + w_xy * ey * ey + w_z * ez * ez + w_yaw * x[8] * x[8] +
+              w_v * (x[3] * x[3] + x[4] * x[4] + x[5] * x[5]) + w_obs * expf(-a.d * (1.0f / obs_scale));
+    return a.crashed ? c + w_crash : c;
+  }
+};
+
+}  // namespace mppi

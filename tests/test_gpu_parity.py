@@ -1,0 +1,172 @@
+"""GPU (sm_103a) vs FP64 oracle parity of one MPPI iteration, through the C ABI.
+
+Bars (from the method's requirements): Philox words and the argmin index
+bit-exact; path costs S~ within 1e-4 relative; updated controls within 1e-3
+relative to the control scale.  Quadrotor samples whose oracle trajectory
+passes within 1e-3 of a crash boundary are excluded from the S~ check (an FP32
+vs FP64 crash decision there is a tie, not an error)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_01149_b300 import _native
+    return _native
+
+
+# ---------------------------------------------------------------------------
+# noise
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,counter,gid", [(0, 0, 0), (0x0123456789ABCDEF, 7, 3), (2 ** 64 - 1, 2 ** 32 - 1, 99)])
+def test_philox_words_bit_exact(N, seed, counter, gid):
+    from oracle import philox
+    K, nb = 1000, 5
+    got = N.mppi_philox_words(seed, K, nb, counter, gid)
+    want = philox.philox_words(seed, K, nb * 4, 1, counter, gid)[:nb]
+    assert np.array_equal(got.astype(np.uint64), want)
+
+
+@pytest.mark.parametrize("system", [W.CARTPOLE, W.CAR, W.QUAD])
+def test_noise_matches_oracle(N, system):
+    cfg = W.config(system, K=777, T=13)
+    c = P.make_controller(cfg)
+    du = c.get_noise(3)
+    want = P.noise_oracle(cfg, 3)
+    scale = P.control_scale(cfg)[None, :, None]
+    # FP32 log/sqrt/sincospi (a few ulp each) against FP64
+    assert np.all(np.abs(du - want) <= 4e-6 * np.abs(want) + 1e-6 * scale)
+
+
+# ---------------------------------------------------------------------------
+# one iteration
+# ---------------------------------------------------------------------------
+def _check_iteration(cfg, g, o, margin_mask=None, s_rtol=P.S_RTOL, u_rtol=P.U_RTOL):
+    rel = P.s_errors(g["S"], o.S, margin_mask)
+    assert rel.size > 0
+    assert rel.max() <= s_rtol, f"S~ max rel err {rel.max():.3g}"
+    assert np.array_equal(np.isinf(g["S"]), ~np.isfinite(o.S))
+    if P.argmin_is_unique(o.S):
+        assert g["kstar"] == o.kstar
+    scale = P.control_scale(cfg)
+    err = np.abs(g["U"].astype(np.float64) - o.U)
+    bound = u_rtol * (np.abs(o.U) + scale[None, :])
+    assert np.all(err <= bound), f"U max err / bound {np.max(err / bound):.3g}"
+    assert np.allclose(g["u0"], o.u0, rtol=u_rtol, atol=u_rtol * scale.max())
+    assert g["eta"] == pytest.approx(o.eta, rel=5e-2)
+
+
+@pytest.mark.parametrize("impl", [0, 1])
+def test_cartpole_iteration(N, impl):
+    cfg = W.config(W.CARTPOLE)
+    g, _ = P.gpu_iteration(cfg, impl)
+    o = P.oracle_iteration(cfg)
+    _check_iteration(cfg, g, o)
+
+
+@pytest.mark.parametrize("lam", [100.0, 300.0])
+def test_cartpole_spread_weights(N, lam):
+    """Larger temperatures spread the weights over many samples, so the weighted
+    sum (not just the argmin) is exercised."""
+    cfg = W.config(W.CARTPOLE, lam=lam, K=4099)
+    g, _ = P.gpu_iteration(cfg)
+    o = P.oracle_iteration(cfg)
+    ess = 1.0 / np.sum(o.w ** 2)
+    assert ess > 5
+    _check_iteration(cfg, g, o)
+
+
+@pytest.mark.parametrize("K,nu", [(4096, 1.0), (4096, 10.0), (16384, 10.0), (16384, 100.0)])
+def test_car_iteration(N, K, nu):
+    cfg = W.config(W.CAR, K=K, nu=nu)
+    g, _ = P.gpu_iteration(cfg)
+    o = P.oracle_iteration(cfg)
+    _check_iteration(cfg, g, o)
+
+
+@pytest.mark.parametrize("lam", [30.0, 300.0])
+def test_car_spread_weights_plain_and_fused_agree(N, lam):
+    """R fixed (not lambda Sigma^-1), so a larger lambda really spreads the weights."""
+    cfg = W.config(W.CAR, K=2048, T=30, nu=10.0, lam=lam, R=np.linalg.inv(np.diag([0.3, 0.35])))
+    gf, _ = P.gpu_iteration(cfg, 0)
+    gp, _ = P.gpu_iteration(cfg, 1)
+    o = P.oracle_iteration(cfg)
+    assert 1.0 / np.sum(o.w ** 2) > 5
+    _check_iteration(cfg, gf, o)
+    _check_iteration(cfg, gp, o)
+
+
+def test_quad_iteration(N):
+    cfg = W.config(W.QUAD)
+    g, _ = P.gpu_iteration(cfg)
+    o = P.oracle_iteration(cfg)
+    keep = o.margin > 1e-3
+    assert keep.mean() > 0.9
+    _check_iteration(cfg, g, o, margin_mask=keep)
+
+
+@pytest.mark.parametrize("system,K,T", [(W.CARTPOLE, 1, 1), (W.CARTPOLE, 33, 3), (W.CARTPOLE, 129, 7),
+                                        (W.CAR, 65, 1), (W.CAR, 200, 5), (W.QUAD, 63, 2), (W.QUAD, 130, 9)])
+def test_ragged_sizes(N, system, K, T):
+    cfg = W.config(system, K=K, T=T)
+    for impl in (0, 1):
+        g, _ = P.gpu_iteration(cfg, impl)
+        o = P.oracle_iteration(cfg)
+        mask = o.margin > 1e-3 if o.margin is not None else None
+        _check_iteration(cfg, g, o, margin_mask=mask)
+
+
+def test_nonzero_controls_and_correlated_sigma(N):
+    rng = np.random.default_rng(3)
+    S = np.array([[0.3, 0.1], [0.1, 0.35]])
+    cfg = W.config(W.CAR, K=3000, T=40, Sigma=S, R=np.linalg.inv(S) * 1.0,
+                   U=rng.normal(0, 0.3, (40, 2)), lam=50.0)
+    g, _ = P.gpu_iteration(cfg)
+    o = P.oracle_iteration(cfg)
+    _check_iteration(cfg, g, o)
+
+
+def test_receding_horizon_counter_and_shift(N):
+    """Two iterations with the shift in between: counter 0 then 1, U shifted with u_init."""
+    cfg = W.config(W.CARTPOLE, K=2048, T=50, lam=20.0, u_init=np.array([0.25]))
+    g1, c = P.gpu_iteration(cfg)
+    c.shift()
+    assert c.get_iteration() == 1
+    U1 = c.get_controls()
+    o1 = P.oracle_iteration(cfg)
+    from oracle import mppi as om
+    Us = om.shift(o1.U, [0.25])
+    assert np.allclose(U1, Us, rtol=1e-3, atol=1e-3 * P.control_scale(cfg).max())
+    cfg2 = dict(cfg, U=U1.astype(np.float64))
+    u0 = c.step(np.asarray(cfg["x0"], dtype=np.float32))
+    g2 = c.get_debug()
+    o2 = P.oracle_iteration(cfg2, counter=1)
+    rel = P.s_errors(g2["S"], o2.S)
+    assert rel.max() <= P.S_RTOL
+    assert np.allclose(u0, o2.u0, rtol=1e-3, atol=1e-3 * P.control_scale(cfg).max())
+
+
+def test_zero_noise_leaves_controls_unchanged(N):
+    cfg = W.config(W.CAR, K=512, T=20, Sigma=np.zeros((2, 2)), R=np.eye(2), U=np.full((20, 2), 0.1))
+    g, _ = P.gpu_iteration(cfg)
+    assert np.array_equal(g["dU"], np.zeros((20, 2), dtype=np.float32))
+    assert np.array_equal(g["U"], np.full((20, 2), 0.1, dtype=np.float32))
+
+
+def test_step_without_env_is_a_state_error(N):
+    c = N.Controller(N.MPPI_CAR, 64, 10, 0.02, 10.0, 1.0, np.diag([0.3, 0.35]))
+    with pytest.raises(N.MppiError) as ei:
+        c.step(np.zeros(7))
+    assert ei.value.rc == -5
+    with pytest.raises(N.MppiError):
+        c.set_forest(W.quad_forest(0), W.QUAD_GOAL)   # wrong env kind for a car
