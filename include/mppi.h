@@ -180,6 +180,41 @@ int mppi_get_noise(mppi_ctx *ctx, uint32_t counter, float *h_du);
 int mppi_philox_words(uint64_t seed, int K, int n_blocks, uint32_t counter, uint32_t gid,
                       uint32_t *h_out);
 
+/* One MPPI iteration that allocates nothing (no ctx, no cudaMalloc, no pinned memory).
+ * The paper has no counterpart: this is a service for callers that may not allocate
+ * device memory while they run -- a real-time control loop that must not call
+ * cudaMalloc after start-up (it can synchronise the device and its latency has no
+ * bound), or a host whose own memory pool owns all device memory.
+ *
+ * It does what mppi_step_async does (noise, rollout, cost, weights, update of U, u_0
+ * out; not the shift) on buffers the caller owns:
+ *   sys, K, T, dt, nu, lambda, h_Sigma, h_R   as in mppi_create (host arrays, copied)
+ *   seed, gid, counter                        Philox key, controller id, iteration counter
+ *   h_env_header   host mppi_env_map (car) or mppi_env_forest (quadrotor); NULL for
+ *                  the cart-pole
+ *   d_env_payload  device: the map values [height][width] or the cylinder rows [n][3]
+ *   d_state        device [n] state, read
+ *   d_U            device [T][m] nominal controls, updated in place
+ *   d_u0_out       device [m] updated u_0
+ *   cuda_stream    stream for all work (cudaStream_t, may be NULL = legacy stream)
+ *   h_err, err_len optional host buffer that receives the error text (may be NULL)
+ * The work is enqueued on cuda_stream and not waited for.
+ *
+ * Scratch: a static device array of MPPI_STATIC_SCRATCH_BYTES (4 MiB) inside the
+ * library, which every GPU that loads the library holds until the process exits.
+ * A configuration needs about 4*K + 4*ceil(K/B)*T*m bytes (B = 128, or 64 when
+ * T*m*128 floats would not fit in shared memory) plus a few KB; larger ones return
+ * MPPI_EINVAL with the sizes in the error text.  Every call on a device shares the
+ * array and leaves the last call's contents in it, so calls whose work overlaps on
+ * the GPU (two streams, two host threads) race.  The first call on each device looks
+ * up the array's device address and sets kernel attributes (once per device); make
+ * that first call before any stream capture. */
+#define MPPI_STATIC_SCRATCH_BYTES (4u << 20)
+int mppi_step_static(mppi_system sys, int K, int T, float dt, float nu, float lambda, const float *h_Sigma,
+                     const float *h_R, uint64_t seed, uint32_t gid, uint32_t counter, const void *h_env_header,
+                     const float *d_env_payload, const float *d_state, float *d_U, float *d_u0_out,
+                     void *cuda_stream, char *h_err, size_t err_len);
+
 /* Text of the last error on this ctx (or of the last failed create when ctx is NULL).
  * Valid until the next call on the ctx. */
 const char *mppi_last_error(mppi_ctx *ctx);

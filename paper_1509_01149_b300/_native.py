@@ -46,6 +46,9 @@ SIGNATURES = [
     ("mppi_get_debug", C.c_int, [_P, _FP, C.POINTER(C.c_int), C.POINTER(C.c_double), _FP]),
     ("mppi_get_noise", C.c_int, [_P, C.c_uint32, _FP]),
     ("mppi_philox_words", C.c_int, [C.c_uint64, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]),
+    ("mppi_step_static", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, _FP, _FP,
+                                   C.c_uint64, C.c_uint32, C.c_uint32, C.c_char_p, _P, _P, _P, _P, _P,
+                                   C.c_char_p, C.c_size_t]),
     ("mppi_last_error", C.c_char_p, [_P]),
     ("mppi_version", C.c_char_p, []),
 ]
@@ -102,6 +105,22 @@ def mppi_philox_words(seed: int, K: int, n_blocks: int, counter: int, gid: int) 
     if rc != MPPI_OK:
         raise MppiError(rc, lib.mppi_last_error(None).decode())
     return out
+
+
+def mppi_step_static(system: int, K: int, T: int, dt: float, nu: float, lam: float, Sigma, R, seed: int, gid: int,
+                     counter: int, env_header: bytes | None, d_env_payload: int, d_state: int, d_U: int,
+                     d_u0_out: int, stream: int = 0):
+    """The allocation-free iteration (mppi_step_static): every buffer is a device pointer the
+    caller owns; the work is enqueued on `stream` and not waited for."""
+    m = CONTROL_DIM[int(system)]
+    S = _f32(Sigma, m * m)
+    Rm = None if R is None else _f32(R, m * m)
+    err = C.create_string_buffer(512)
+    rc = lib.mppi_step_static(int(system), K, T, dt, nu, lam, _fp(S), None if Rm is None else _fp(Rm), seed, gid,
+                              counter, env_header, C.c_void_p(d_env_payload or 0), C.c_void_p(d_state),
+                              C.c_void_p(d_U), C.c_void_p(d_u0_out), C.c_void_p(stream), err, len(err))
+    if rc != MPPI_OK:
+        raise MppiError(rc, err.value.decode())
 
 
 class Controller:
