@@ -47,6 +47,7 @@ extern "C" {
 #define MPPI_ETIMEOUT (-4) /* a bounded device-side wait ran out (serving)                  */
 #define MPPI_ESTATE (-5)   /* call not valid in the ctx's current state (e.g. no env set)   */
 #define MPPI_ENOSYS (-6)   /* feature not built into this library                           */
+#define MPPI_EBUSY (-7)    /* admission refused: no free slot or not enough arena memory     */
 
 /* systems (plants and their state costs; see the design notes for the models) */
 typedef enum {
@@ -214,6 +215,70 @@ int mppi_step_static(mppi_system sys, int K, int T, float dt, float nu, float la
                      const float *h_R, uint64_t seed, uint32_t gid, uint32_t counter, const void *h_env_header,
                      const float *d_env_payload, const float *d_state, float *d_U, float *d_u0_out,
                      void *cuda_stream, char *h_err, size_t err_len);
+
+/* ---------------------------------------------------------------------------------
+ * Serving: many controllers of different systems, K and T stepped together.
+ * (North-star extension; the paper runs one controller.)
+ *
+ * A server owns a device arena (allocated once at create) and a device slot table.
+ * mppi_server_admit places a controller in a free slot if its buffers fit in the arena
+ * (first-fit, coalescing free list): admission is by memory, and a refusal returns
+ * MPPI_EBUSY, which is not an error.  A controller's U, u_init, Philox key / id and
+ * iteration counter stay on the device from admission to release.
+ *
+ * mppi_server_tick runs, for the listed slots, one MPPI iteration followed by the
+ * shift of Algorithm 1 (receding horizon), all slots in the same two persistent
+ * kernels (rollout work items = (slot, block of samples), heaviest first, taken from
+ * an atomic queue; then one merge + update + shift per slot), replayed as one CUDA
+ * graph.  Every slot's result equals what a lone mppi_ctx with the same
+ * configuration, seed, controller id and iteration counter computes.
+ * --------------------------------------------------------------------------------- */
+typedef struct mppi_server mppi_server;
+
+/* Configuration of one controller (host struct, copied by admit).  Sigma and R are
+ * row-major m x m in their first m*m entries; has_R = 0 selects R = lambda Sigma^-1.
+ * env_id names an environment set with mppi_server_set_env (-1: none, cart-pole). */
+typedef struct {
+  int32_t system, K, T;
+  float dt, nu, lambda;
+  float Sigma[16];
+  float R[16];
+  int32_t has_R;
+  int32_t env_id;
+  uint64_t seed;
+  uint32_t gid;
+  uint32_t counter; /* initial iteration counter */
+  float u_init[4];
+} mppi_slot_config;
+
+typedef struct {
+  int32_t max_slots, active_slots;
+  uint64_t arena_bytes, arena_used;
+  int32_t rollout_block, rollout_ctas_per_sm; /* shapes in use (from the autotuner)   */
+  int32_t ticks;
+  double last_tick_ms;
+} mppi_server_info;
+
+/* max_slots in [1, 4096]; arena_bytes of device memory for the controllers' buffers. */
+int mppi_server_create(int max_slots, size_t arena_bytes, mppi_server **out);
+int mppi_server_destroy(mppi_server *srv);
+/* Environment env_id in [0, 16): same blob formats as mppi_set_env (copied). */
+int mppi_server_set_env(mppi_server *srv, int env_id, const void *blob, size_t bytes);
+/* Admit a controller: *slot_out receives its slot.  U starts at u_init repeated.
+ * MPPI_EBUSY when no slot is free or its buffers do not fit in the arena. */
+int mppi_server_admit(mppi_server *srv, const mppi_slot_config *cfg, int *slot_out);
+int mppi_server_release(mppi_server *srv, int slot);
+int mppi_server_set_controls(mppi_server *srv, int slot, const float *h_U);
+int mppi_server_get_controls(mppi_server *srv, int slot, float *h_U);
+/* One receding-horizon step of the n listed slots: h_states [n][16] (state in the first
+ * n_x entries of each row), h_u0_out [n][4] receives each slot's u_0 (first m entries).
+ * Blocks until the results are on the host. */
+int mppi_server_tick(mppi_server *srv, int n, const int *slots, const float *h_states, float *h_u0_out);
+/* Pick the rollout block shape and persistent grid by timing the current mix
+ * (tick on the listed slots, restoring their controls and counters afterwards). */
+int mppi_server_autotune(mppi_server *srv, int n, const int *slots, const float *h_states);
+int mppi_server_get_info(mppi_server *srv, mppi_server_info *out);
+const char *mppi_server_last_error(mppi_server *srv);
 
 /* Text of the last error on this ctx (or of the last failed create when ctx is NULL).
  * Valid until the next call on the ctx. */

@@ -22,6 +22,24 @@ MPPI_ENV_MAP, MPPI_ENV_FOREST = 0x3150414D, 0x31524F46
 STATE_DIM = {MPPI_CARTPOLE: 4, MPPI_CAR: 7, MPPI_QUAD: 12, MPPI_CAR_MLP: 7}
 CONTROL_DIM = {MPPI_CARTPOLE: 1, MPPI_CAR: 2, MPPI_QUAD: 4, MPPI_CAR_MLP: 2}
 
+MPPI_EBUSY = -7
+
+
+class SlotConfig(C.Structure):
+    """mppi_slot_config."""
+    _fields_ = [("system", C.c_int32), ("K", C.c_int32), ("T", C.c_int32), ("dt", C.c_float), ("nu", C.c_float),
+                ("lam", C.c_float), ("Sigma", C.c_float * 16), ("R", C.c_float * 16), ("has_R", C.c_int32),
+                ("env_id", C.c_int32), ("seed", C.c_uint64), ("gid", C.c_uint32), ("counter", C.c_uint32),
+                ("u_init", C.c_float * 4)]
+
+
+class ServerInfo(C.Structure):
+    """mppi_server_info."""
+    _fields_ = [("max_slots", C.c_int32), ("active_slots", C.c_int32), ("arena_bytes", C.c_uint64),
+                ("arena_used", C.c_uint64), ("rollout_block", C.c_int32), ("rollout_ctas_per_sm", C.c_int32),
+                ("ticks", C.c_int32), ("last_tick_ms", C.c_double)]
+
+
 # (name, restype, argtypes) of every exported symbol declared in include/mppi.h
 _P = C.c_void_p
 _FP = C.POINTER(C.c_float)
@@ -49,6 +67,17 @@ SIGNATURES = [
     ("mppi_step_static", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, _FP, _FP,
                                    C.c_uint64, C.c_uint32, C.c_uint32, C.c_char_p, _P, _P, _P, _P, _P,
                                    C.c_char_p, C.c_size_t]),
+    ("mppi_server_create", C.c_int, [C.c_int, C.c_size_t, C.POINTER(_P)]),
+    ("mppi_server_destroy", C.c_int, [_P]),
+    ("mppi_server_set_env", C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
+    ("mppi_server_admit", C.c_int, [_P, C.POINTER(SlotConfig), C.POINTER(C.c_int)]),
+    ("mppi_server_release", C.c_int, [_P, C.c_int]),
+    ("mppi_server_set_controls", C.c_int, [_P, C.c_int, _FP]),
+    ("mppi_server_get_controls", C.c_int, [_P, C.c_int, _FP]),
+    ("mppi_server_tick", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP, _FP]),
+    ("mppi_server_autotune", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP]),
+    ("mppi_server_get_info", C.c_int, [_P, C.POINTER(ServerInfo)]),
+    ("mppi_server_last_error", C.c_char_p, [_P]),
     ("mppi_last_error", C.c_char_p, [_P]),
     ("mppi_version", C.c_char_p, []),
 ]
@@ -258,3 +287,101 @@ class Controller:
     set_env = mppi_set_env
     get_debug = mppi_get_debug
     get_noise = mppi_get_noise
+
+
+class Server:
+    """An mppi_server: many controllers stepped together (methods map onto the C ABI)."""
+
+    def __init__(self, max_slots: int, arena_bytes: int):
+        h = _P()
+        rc = lib.mppi_server_create(max_slots, arena_bytes, C.byref(h))
+        if rc != MPPI_OK:
+            raise MppiError(rc, "mppi_server_create failed")
+        self._h = h
+        self.max_slots = max_slots
+        self._slots = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mppi_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc != MPPI_OK:
+            raise MppiError(rc, lib.mppi_server_last_error(self._h).decode())
+
+    def set_env(self, env_id: int, blob: bytes):
+        self._chk(lib.mppi_server_set_env(self._h, env_id, blob, len(blob)))
+
+    @staticmethod
+    def slot_config(system, K, T, dt, nu, lam, Sigma, R=None, seed=0, gid=0, counter=0, env_id=-1, u_init=None):
+        m = CONTROL_DIM[int(system)]
+        c = SlotConfig()
+        c.system, c.K, c.T, c.dt, c.nu, c.lam = int(system), int(K), int(T), dt, nu, lam
+        S = np.asarray(Sigma, dtype=np.float32).reshape(-1)
+        for i in range(m * m):
+            c.Sigma[i] = float(S[i])
+        if R is not None:
+            Rr = np.asarray(R, dtype=np.float32).reshape(-1)
+            for i in range(m * m):
+                c.R[i] = float(Rr[i])
+            c.has_R = 1
+        c.env_id, c.seed, c.gid, c.counter = env_id, seed, gid, counter
+        if u_init is not None:
+            for i, v in enumerate(np.asarray(u_init, dtype=np.float32).reshape(-1)[:m]):
+                c.u_init[i] = float(v)
+        return c
+
+    def admit(self, cfg: SlotConfig) -> int | None:
+        """Slot id, or None when admission is refused (no slot or no arena memory)."""
+        slot = C.c_int(-1)
+        rc = lib.mppi_server_admit(self._h, C.byref(cfg), C.byref(slot))
+        if rc == MPPI_EBUSY:
+            return None
+        self._chk(rc)
+        self._slots[slot.value] = (cfg.system, cfg.T)
+        return slot.value
+
+    def release(self, slot: int):
+        self._chk(lib.mppi_server_release(self._h, slot))
+        self._slots.pop(slot, None)
+
+    def set_controls(self, slot: int, U):
+        self._chk(lib.mppi_server_set_controls(self._h, slot, _fp(_f32(U))))
+
+    def get_controls(self, slot: int) -> np.ndarray:
+        system, T = self._slots[slot]
+        U = np.zeros((T, CONTROL_DIM[system]), dtype=np.float32)
+        self._chk(lib.mppi_server_get_controls(self._h, slot, _fp(U)))
+        return U
+
+    @staticmethod
+    def _pack(slots, states):
+        ids = np.ascontiguousarray(np.asarray(slots, dtype=np.int32))
+        st = np.zeros((len(ids), 16), dtype=np.float32)
+        for i, x in enumerate(states):
+            x = np.asarray(x, dtype=np.float32).reshape(-1)
+            st[i, :x.size] = x
+        return ids, st
+
+    def tick(self, slots, states) -> np.ndarray:
+        """One receding-horizon step of the listed slots; returns u0 [n][4]."""
+        ids, st = self._pack(slots, states)
+        u0 = np.zeros((len(ids), 4), dtype=np.float32)
+        self._chk(lib.mppi_server_tick(self._h, len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)), _fp(st), _fp(u0)))
+        return u0
+
+    def autotune(self, slots, states):
+        ids, st = self._pack(slots, states)
+        self._chk(lib.mppi_server_autotune(self._h, len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)), _fp(st)))
+
+    def info(self) -> dict:
+        i = ServerInfo()
+        self._chk(lib.mppi_server_get_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in ServerInfo._fields_}

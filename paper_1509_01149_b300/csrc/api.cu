@@ -282,7 +282,7 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
     delete c;
     return bad("T*m too large for the fused rollout's shared memory");
   }
-  c->nblk = (K + c->blk - 1) / c->blk;
+  c->nblk = (K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
 
   int rc = c->cuda(cudaGetDevice(&c->device), "cudaGetDevice");
   if (rc == MPPI_OK) rc = c->cuda(prepare_kernels(), "kernel attributes");
@@ -461,7 +461,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   }
   c->p = np;
   c->blk = fused_block_size(c->p);
-  c->nblk = (c->K + c->blk - 1) / c->blk;
+  c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
   c->env_ok = true;
   c->graph_dirty = true;
   return MPPI_OK;

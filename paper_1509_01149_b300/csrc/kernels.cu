@@ -19,176 +19,22 @@
 #include <climits>
 
 #include "kernels.cuh"
-#include "systems.cuh"
+#include "rollout_body.cuh"
 
 namespace mppi {
 
 // ---------------------------------------------------------------------------
-// shared helpers
+// fused rollout: one block of BLK samples per CTA (body in rollout_body.cuh)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs) {
-  Env e;
-  e.map = p.map;
-  e.map_w = p.map_w;
-  e.map_h = p.map_h;
-  e.map_ox = p.map_ox;
-  e.map_oy = p.map_oy;
-  e.map_inv_cell = p.map_inv_cell;
-  e.obs = obs;
-  e.n_obs = p.n_obs;
-  e.gx = p.goal[0];
-  e.gy = p.goal[1];
-  e.gz = p.goal[2];
-  return e;
-}
-
-// du_j = sum_{l <= j} Lnu[j][l] eps_l  (Lnu = sqrt(nu) chol(Sigma), lower triangular)
-template <int M>
-__device__ __forceinline__ void scale_noise(const float *Lnu, const float *eps, float *du) {
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    float a = 0.0f;
-#pragma unroll
-    for (int l = 0; l <= j; ++l) a = fmaf(Lnu[j * M + l], eps[l], a);
-    du[j] = a;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// fused rollout
-// ---------------------------------------------------------------------------
-template <class Sys, int BLK>
+template <class Sys, int BLK, bool REGEN>
 __global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const CtrlState *__restrict__ st,
                                                        const float *__restrict__ U, float *__restrict__ S_out,
                                                        float *__restrict__ part_sums,
                                                        BlockPartial *__restrict__ part) {
-  constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M, NW = BLK / 32;
-  static_assert(4 % M == 0, "controls per Philox block must divide 4");
   extern __shared__ __align__(16) float smem[];
-  __shared__ float s_min[NW];
-  __shared__ int s_idx[NW];
-  __shared__ double s_eta[NW];
-
-  const int T = p.T, TM = T * M, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float *sU = smem;                 // [TM]  nominal controls
-  float *sRu = sU + TM;             // [TM]  R u_i
-  float *sHu = sRu + TM;            // [T]   1/2 u_i^T R u_i
-  float *sObs = sHu + T;            // [3 n_obs]
-  float *sW = sObs + 3 * p.n_obs;   // [BLK] weights
-  float *sDu = sW + BLK;            // [TM][BLK] perturbations of this block
-
-  for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
-  for (int o = tid; o < 3 * p.n_obs; o += BLK) sObs[o] = p.obs[o];
-  __syncthreads();
-  for (int i = tid; i < T; i += BLK) {
-    float h = 0.0f;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-      float ru = 0.0f;
-#pragma unroll
-      for (int l = 0; l < M; ++l) ru = fmaf(p.R[j * M + l], sU[i * M + l], ru);
-      sRu[i * M + j] = ru;
-      h = fmaf(sU[i * M + j], ru, h);
-    }
-    sHu[i] = 0.5f * h;
-  }
-  __syncthreads();
-
-  const Env env = make_env(p, sObs);
-  const int k = blockIdx.x * BLK + tid;
-  const bool valid = k < p.K;
-  float Lnu[M * M], R[M * M];
-#pragma unroll
-  for (int a = 0; a < M * M; ++a) {
-    Lnu[a] = p.Lnu[a];
-    R[a] = p.R[a];
-  }
-  float x[N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) x[a] = st->x0[a];
-  const uint32_t ctr = st->counter;
-  typename Sys::Aux aux;
-  Sys::init(x, aux, env);
-  KahanSum S;
-
-  const int nb = (TM + 3) >> 2;
-  for (int b = 0; b < nb; ++b) {
-    float eps[4];
-    normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
-#pragma unroll
-    for (int s = 0; s < SPB; ++s) {
-      const int i = b * SPB + s;
-      if (i < T) {
-        float du[M], v[M];
-        scale_noise<M>(Lnu, eps + s * M, du);
-        float duRdu = 0.0f, uRdu = 0.0f;
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-          v[j] = sU[i * M + j] + du[j];
-          sDu[(i * M + j) * BLK + tid] = du[j];
-          uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
-          float rd = 0.0f;
-#pragma unroll
-          for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
-          duRdu = fmaf(du[j], rd, duRdu);
-        }
-        Sys::step(x, v, aux, env, p.dt);
-        const float q = Sys::cost(x, aux, env);
-        S.add(q + (p.is_du * duRdu + uRdu + sHu[i]));
-      }
-    }
-  }
-  S.add(Sys::cost(x, aux, env));  // phi(x_T) = q(x_T)
-
-  float Sk = S.s;
-  if (!valid || !isfinite(Sk)) Sk = INFINITY;
-  if (valid) S_out[k] = Sk;
-
-  // block minimum (lowest index on ties)
-  float mv = Sk;
-  int mi = valid ? k : INT_MAX;
-  warp_argmin(mv, mi);
-  if (lane == 0) {
-    s_min[warp] = mv;
-    s_idx[warp] = mi;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    float v = lane < NW ? s_min[lane] : INFINITY;
-    int ii = lane < NW ? s_idx[lane] : INT_MAX;
-    warp_argmin(v, ii);
-    if (lane == 0) {
-      s_min[0] = v;
-      s_idx[0] = ii;
-    }
-  }
-  __syncthreads();
-  const float rho_b = s_min[0];
-  const float w = (isfinite(rho_b) && isfinite(Sk)) ? expf(-(Sk - rho_b) * p.inv_lambda) : 0.0f;
-  sW[tid] = w;
-  const double e = warp_sum_d(static_cast<double>(w));
-  if (lane == 0) s_eta[warp] = e;
-  __syncthreads();
-
-  // block sums of w_k du_{i,k}: warp per output, lanes over the block's samples (FP32)
-  float *dst = part_sums + static_cast<size_t>(blockIdx.x) * TM;
-  for (int o = warp; o < TM; o += NW) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int c = 0; c < BLK / 32; ++c) acc = fmaf(sW[lane + 32 * c], sDu[o * BLK + lane + 32 * c], acc);
-    acc = warp_sum_f(acc);
-    if (lane == 0) dst[o] = acc;
-  }
-  if (tid == 0) {
-    double eta_b = 0.0;
-#pragma unroll
-    for (int q = 0; q < NW; ++q) eta_b += s_eta[q];
-    BlockPartial bp;
-    bp.eta = eta_b;
-    bp.rho = rho_b;
-    bp.kstar = s_idx[0];
-    part[blockIdx.x] = bp;
-  }
+  rollout_block<Sys, BLK, REGEN>(p, st->x0, st->counter, U, blockIdx.x * BLK, S_out,
+                                 part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
+                                 smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -451,30 +297,34 @@ __global__ void k_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_bl
 // host launchers
 // ---------------------------------------------------------------------------
 size_t fused_smem_bytes(const CtrlParams &p, int blk) {
-  const size_t TM = static_cast<size_t>(p.T) * p.m;
-  return sizeof(float) * (2 * TM + p.T + 3 * static_cast<size_t>(p.n_obs) + blk + TM * blk);
+  const bool regen = blk == kFusedBlockRegen;
+  return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen);
 }
 
 int fused_block_size(const CtrlParams &p) {
   if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;
   if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
+  if (fused_smem_bytes(p, kFusedBlockRegen) <= kFusedSmemLimit) return kFusedBlockRegen;
   return 0;
 }
 
-template <class Sys, int BLK>
+int fused_block_samples(int blk) { return blk == kFusedBlockRegen ? kFusedBlockLarge : blk; }
+
+template <class Sys, int BLK, bool REGEN>
 static cudaError_t launch_fused_t(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *ps,
                                   BlockPartial *part, cudaStream_t s) {
-  const size_t smem = fused_smem_bytes(p, BLK);
+  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, REGEN);
   const int grid = (p.K + BLK - 1) / BLK;
-  k_rollout_fused<Sys, BLK><<<grid, BLK, smem, s>>>(p, st, U, S, ps, part);
+  k_rollout_fused<Sys, BLK, REGEN><<<grid, BLK, smem, s>>>(p, st, U, S, ps, part);
   return cudaGetLastError();
 }
 
 template <class Sys>
 static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const CtrlState *st, const float *U, float *S,
                                     float *ps, BlockPartial *part, cudaStream_t s) {
-  if (blk == kFusedBlockLarge) return launch_fused_t<Sys, kFusedBlockLarge>(p, st, U, S, ps, part, s);
-  if (blk == kFusedBlockSmall) return launch_fused_t<Sys, kFusedBlockSmall>(p, st, U, S, ps, part, s);
+  if (blk == kFusedBlockLarge) return launch_fused_t<Sys, kFusedBlockLarge, false>(p, st, U, S, ps, part, s);
+  if (blk == kFusedBlockSmall) return launch_fused_t<Sys, kFusedBlockSmall, false>(p, st, U, S, ps, part, s);
+  if (blk == kFusedBlockRegen) return launch_fused_t<Sys, kFusedBlockLarge, true>(p, st, U, S, ps, part, s);
   return cudaErrorInvalidValue;
 }
 
@@ -492,12 +342,15 @@ cudaError_t prepare_kernels() {
   // dynamic shared memory above the 48 KB default, set once (outside any capture)
   const int big = 220 * 1024;
   const void *fns[] = {
-      reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockLarge>),
-      reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockSmall>),
-      reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge>),
-      reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall>),
-      reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge>),
-      reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall>),
+      reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockLarge, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockSmall, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockLarge, true>),
+      reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, true>),
+      reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, true>),
       reinterpret_cast<const void *>(k_merge_update),
   };
   for (const void *f : fns) {

@@ -8,6 +8,7 @@ namespace mppi {
 // Block sizes the fused rollout is built for.
 constexpr int kFusedBlockLarge = 128;
 constexpr int kFusedBlockSmall = 64;
+constexpr int kFusedBlockRegen = 129;   // code for "128 samples, du regenerated (no shared-memory copy)"
 constexpr int kMergeThreads = 256;
 constexpr int kMergeOutputs = 32;       // outputs (i, j) per merge block
 constexpr size_t kFusedSmemLimit = 200 * 1024;
@@ -19,8 +20,11 @@ cudaError_t prepare_kernels();
 // Fused path ---------------------------------------------------------------
 // Shared memory of the fused rollout for block size blk (bytes).
 size_t fused_smem_bytes(const CtrlParams &p, int blk);
-// Block size for this controller (largest of 128/64 whose shared memory fits), or 0.
+// Block shape for this controller: 128 or 64 samples with du kept in shared memory,
+// else kFusedBlockRegen (128 samples, du regenerated); 0 if nothing fits.
 int fused_block_size(const CtrlParams &p);
+// Samples per block of a block shape.
+int fused_block_samples(int blk);
 // Rollout + cost + IS term + block-local weights and weighted perturbation sums.
 cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const CtrlState *st, const float *U,
                                  float *S, float *part_sums, BlockPartial *part, cudaStream_t s);

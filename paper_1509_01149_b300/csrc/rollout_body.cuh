@@ -1,0 +1,242 @@
+// Per-block body of the fused MPPI rollout, shared by the single-controller kernel
+// and the batched (serving) kernel.
+//
+// One thread per sample k.  For i = 0..T-1: Philox normals -> du_i = Lnu eps ->
+// x_{i+1} = F(x_i, u_i + du_i) -> S~ += q(x_{i+1}) + IS running cost (Kahan FP32);
+// then S~ += phi(x_T).  The block then forms its softmax partial:
+//   rho_b = min_k S~_k (lowest k on ties), w_k = exp(-(S~_k - rho_b)/lambda),
+//   eta_b = sum_k w_k (FP64), part_b[i][j] = sum_k w_k du_{i,j,k} (FP32 block sum).
+// Two ways to get du back for the block sums:
+//   STORE: du kept in shared memory during the rollout ([T*M][BLK] floats);
+//   REGEN: du regenerated from the counter-based generator after the rollout (no
+//          shared memory, so many blocks fit on an SM), reduced with a transposed
+//          butterfly across the warp (31 shuffles per 32 outputs).
+#pragma once
+#include <climits>
+
+#include "systems.cuh"
+
+namespace mppi {
+
+// du_j = sum_{l <= j} Lnu[j][l] eps_l  (Lnu = sqrt(nu) chol(Sigma), lower triangular)
+template <int M>
+__device__ __forceinline__ void scale_noise(const float *Lnu, const float *eps, float *du) {
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    float a = 0.0f;
+#pragma unroll
+    for (int l = 0; l <= j; ++l) a = fmaf(Lnu[j * M + l], eps[l], a);
+    du[j] = a;
+  }
+}
+
+__device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs) {
+  Env e;
+  e.map = p.map;
+  e.map_w = p.map_w;
+  e.map_h = p.map_h;
+  e.map_ox = p.map_ox;
+  e.map_oy = p.map_oy;
+  e.map_inv_cell = p.map_inv_cell;
+  e.obs = obs;
+  e.n_obs = p.n_obs;
+  e.gx = p.goal[0];
+  e.gy = p.goal[1];
+  e.gz = p.goal[2];
+  return e;
+}
+
+// Sum over the 32 lanes of each of 32 per-lane values: afterwards lane l holds the
+// warp total of value l (recursive halving; 31 shuffles in all).
+__device__ __forceinline__ float transpose_reduce32(float v[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = upper ? v[i] : v[i + s];
+      const float keep = upper ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+// Shared-memory bytes of rollout_block (dynamic part) for T*M outputs.
+__host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, int blk, bool regen) {
+  const size_t TM = static_cast<size_t>(T) * M;
+  return sizeof(float) * (2 * TM + T + 3 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk));
+}
+
+// One block of BLK samples of one controller.
+//   p        controller constants; x0/ctr the state and iteration counter
+//   U        [T][M] nominal controls (global)
+//   k0       first sample index of this block
+//   S_out    [K] path costs (global), part_sums [T*M] and part: this block's partial
+//   smem     dynamic shared memory of rollout_smem_bytes(...)
+template <class Sys, int BLK, bool REGEN>
+__device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
+                                              const float *__restrict__ U, int k0, float *__restrict__ S_out,
+                                              float *__restrict__ part_sums, BlockPartial *__restrict__ part,
+                                              float *smem) {
+  constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M, NW = BLK / 32;
+  static_assert(4 % M == 0, "controls per Philox block must divide 4");
+  __shared__ float s_min[NW];
+  __shared__ int s_idx[NW];
+  __shared__ double s_eta[NW];
+  __shared__ float s_red[NW][32];
+
+  const int T = p.T, TM = T * M, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float *sU = smem;                 // [TM]  nominal controls
+  float *sRu = sU + TM;             // [TM]  R u_i
+  float *sHu = sRu + TM;            // [T]   1/2 u_i^T R u_i
+  float *sObs = sHu + T;            // [3 n_obs]
+  float *sW = sObs + 3 * p.n_obs;   // [BLK] weights
+  float *sDu = sW + BLK;            // STORE only: [TM][BLK] perturbations of this block
+
+  for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
+  for (int o = tid; o < 3 * p.n_obs; o += BLK) sObs[o] = p.obs[o];
+  __syncthreads();
+  for (int i = tid; i < T; i += BLK) {
+    float h = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float ru = 0.0f;
+#pragma unroll
+      for (int l = 0; l < M; ++l) ru = fmaf(p.R[j * M + l], sU[i * M + l], ru);
+      sRu[i * M + j] = ru;
+      h = fmaf(sU[i * M + j], ru, h);
+    }
+    sHu[i] = 0.5f * h;
+  }
+  __syncthreads();
+
+  const Env env = make_env(p, sObs);
+  const int k = k0 + tid;
+  const bool valid = k < p.K;
+  float Lnu[M * M], R[M * M];
+#pragma unroll
+  for (int a = 0; a < M * M; ++a) {
+    Lnu[a] = p.Lnu[a];
+    R[a] = p.R[a];
+  }
+  float x[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) x[a] = x0[a];
+  typename Sys::Aux aux;
+  Sys::init(x, aux, env);
+  KahanSum S;
+
+  const int nb = (TM + 3) >> 2;
+  for (int b = 0; b < nb; ++b) {
+    float eps[4];
+    normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+#pragma unroll
+    for (int s = 0; s < SPB; ++s) {
+      const int i = b * SPB + s;
+      if (i < T) {
+        float du[M], v[M];
+        scale_noise<M>(Lnu, eps + s * M, du);
+        float duRdu = 0.0f, uRdu = 0.0f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          v[j] = sU[i * M + j] + du[j];
+          if (!REGEN) sDu[(i * M + j) * BLK + tid] = du[j];
+          uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
+          float rd = 0.0f;
+#pragma unroll
+          for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
+          duRdu = fmaf(du[j], rd, duRdu);
+        }
+        Sys::step(x, v, aux, env, p.dt);
+        const float q = Sys::cost(x, aux, env);
+        S.add(q + (p.is_du * duRdu + uRdu + sHu[i]));
+      }
+    }
+  }
+  S.add(Sys::cost(x, aux, env));  // phi(x_T) = q(x_T)
+
+  float Sk = S.s;
+  if (!valid || !isfinite(Sk)) Sk = INFINITY;
+  if (valid) S_out[k] = Sk;
+
+  // block minimum (lowest index on ties)
+  float mv = Sk;
+  int mi = valid ? k : INT_MAX;
+  warp_argmin(mv, mi);
+  if (lane == 0) {
+    s_min[warp] = mv;
+    s_idx[warp] = mi;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float v = lane < NW ? s_min[lane] : INFINITY;
+    int ii = lane < NW ? s_idx[lane] : INT_MAX;
+    warp_argmin(v, ii);
+    if (lane == 0) {
+      s_min[0] = v;
+      s_idx[0] = ii;
+    }
+  }
+  __syncthreads();
+  const float rho_b = s_min[0];
+  const float w = (isfinite(rho_b) && isfinite(Sk)) ? expf(-(Sk - rho_b) * p.inv_lambda) : 0.0f;
+  const double e = warp_sum_d(static_cast<double>(w));
+  if (lane == 0) s_eta[warp] = e;
+
+  if (!REGEN) {
+    sW[tid] = w;
+    __syncthreads();
+    // warp per output, lanes over the block's samples (FP32)
+    for (int o = warp; o < TM; o += NW) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int c = 0; c < BLK / 32; ++c) acc = fmaf(sW[lane + 32 * c], sDu[o * BLK + lane + 32 * c], acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) part_sums[o] = acc;
+    }
+  } else {
+    // regenerate du, weight it, transpose-reduce 32 outputs (8 Philox blocks) at a time
+    for (int g = 0; g < nb; g += 8) {
+      float v[32];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (g + q < nb)
+          normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+#pragma unroll
+        for (int s = 0; s < SPB; ++s) {
+          float du[M];
+          scale_noise<M>(Lnu, eps + s * M, du);
+#pragma unroll
+          for (int j = 0; j < M; ++j) v[q * 4 + s * M + j] = w * du[j];
+        }
+      }
+      const float wsum = transpose_reduce32(v);
+      s_red[warp][lane] = wsum;
+      __syncthreads();
+      if (warp == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) t += s_red[q][lane];
+        const int o = 4 * g + lane;
+        if (o < TM) part_sums[o] = t;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double eta_b = 0.0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) eta_b += s_eta[q];
+    BlockPartial bp;
+    bp.eta = eta_b;
+    bp.rho = rho_b;
+    bp.kstar = s_idx[0];
+    *part = bp;
+  }
+}
+
+}  // namespace mppi

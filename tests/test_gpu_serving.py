@@ -1,0 +1,144 @@
+"""Serving on the GPU: a controller's result is the same alone and in a mixed batch,
+equals the single-controller ctx path and the oracle, admission is by arena memory,
+and the autotuner leaves the controllers' state untouched."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests import parity as P
+
+pytestmark = pytest.mark.gpu
+
+ENV = {W.CAR: 0, W.QUAD: 1}
+MIX = [(W.CARTPOLE, 1000, 100), (W.CAR, 4096, 100), (W.QUAD, 2048, 150), (W.CAR, 512, 50),
+       (W.CARTPOLE, 16384, 200), (W.QUAD, 1024, 50), (W.CAR, 16384, 200), (W.CARTPOLE, 513, 150),
+       (W.QUAD, 777, 7), (W.CAR, 129, 3)]
+
+
+@pytest.fixture(scope="module")
+def N():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_01149_b300 import _native
+    return _native
+
+
+def make_server(N, max_slots=64, arena=512 << 20):
+    srv = N.Server(max_slots, arena)
+    srv.set_env(0, N.map_blob(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL))
+    srv.set_env(1, N.forest_blob(W.quad_forest(0), W.QUAD_GOAL))
+    return srv
+
+
+def admit(srv, system, K, T, rid):
+    c = W.config(system, K=K, T=T)
+    cfg = srv.slot_config(system, K, T, c["dt"], c["nu"], c["lam"], c["Sigma"], c["R"], seed=rid, gid=rid,
+                          env_id=ENV.get(system, -1), u_init=c["u_init"])
+    slot = srv.admit(cfg)
+    assert slot is not None
+    return slot, c
+
+
+def run_ticks(srv, slots, systems, n_ticks):
+    states = [W.config(s)["x0"] for s in systems]
+    out = []
+    for _ in range(n_ticks):
+        out.append(srv.tick(slots, states))
+    return out
+
+
+def within(got, want, c):
+    scale = P.control_scale(c)
+    return np.all(np.abs(np.asarray(got, np.float64) - want) <= P.U_RTOL * (np.abs(want) + scale))
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(N):
+    srv = make_server(N)
+    slots = [admit(srv, s, K, T, rid)[0] for rid, (s, K, T) in enumerate(MIX)]
+    mix_u0 = run_ticks(srv, slots, [m[0] for m in MIX], 2)
+    mix_U = [srv.get_controls(sl) for sl in slots]
+    srv.close()
+    for rid, (s, K, T) in enumerate(MIX):
+        alone = make_server(N, max_slots=4)
+        sl, c = admit(alone, s, K, T, rid)
+        u0 = run_ticks(alone, [sl], [s], 2)
+        m = W.CONTROL_DIM[s]
+        for t in range(2):
+            assert within(u0[t][0, :m], mix_u0[t][rid, :m], c), (rid, t)
+        assert within(alone.get_controls(sl), mix_U[rid], c)
+        alone.close()
+
+
+def test_served_controller_equals_the_single_controller_path(N):
+    srv = make_server(N)
+    slots, cfgs = zip(*[admit(srv, s, K, T, rid) for rid, (s, K, T) in enumerate(MIX)])
+    u0s = run_ticks(srv, list(slots), [m[0] for m in MIX], 2)
+    for rid, (s, K, T) in enumerate(MIX):
+        c = dict(cfgs[rid], seed=rid, gid=rid)
+        ctrl = P.make_controller(c)
+        m = W.CONTROL_DIM[s]
+        for t in range(2):
+            u0 = ctrl.step(np.asarray(c["x0"], dtype=np.float32))
+            ctrl.shift()
+            assert within(u0s[t][rid, :m], u0, c), (rid, t)
+        assert within(srv.get_controls(slots[rid]), ctrl.get_controls(), c)
+        ctrl.close()
+    srv.close()
+
+
+def test_served_result_matches_the_oracle(N):
+    srv = make_server(N)
+    picks = [(W.CAR, 2048, 60), (W.CARTPOLE, 1000, 100), (W.QUAD, 1024, 40)]
+    slots, cfgs = zip(*[admit(srv, s, K, T, 100 + i) for i, (s, K, T) in enumerate(picks)])
+    u0 = run_ticks(srv, list(slots), [p[0] for p in picks], 1)[0]
+    for i, (s, K, T) in enumerate(picks):
+        c = dict(cfgs[i], seed=100 + i, gid=100 + i)
+        o = P.oracle_iteration(c)
+        assert within(u0[i, :W.CONTROL_DIM[s]], o.u0, c)
+    srv.close()
+
+
+def test_admission_is_by_arena_memory(N):
+    srv = make_server(N, max_slots=64, arena=6 << 20)
+    got = []
+    while True:
+        c = W.config(W.CAR, K=16384, T=200)
+        cfg = srv.slot_config(W.CAR, 16384, 200, c["dt"], c["nu"], c["lam"], c["Sigma"], c["R"], seed=len(got),
+                              gid=len(got), env_id=0, u_init=c["u_init"])
+        sl = srv.admit(cfg)
+        if sl is None:
+            break
+        got.append(sl)
+        assert len(got) < 64
+    info = srv.info()
+    assert 1 <= len(got) < 64 and info["active_slots"] == len(got)
+    assert info["arena_used"] <= info["arena_bytes"]
+    srv.release(got[0])
+    assert srv.admit(cfg) is not None       # the freed memory admits the waiting controller
+    srv.close()
+
+
+def test_slot_limit_refuses_admission(N):
+    srv = make_server(N, max_slots=2)
+    assert admit(srv, W.CARTPOLE, 64, 10, 0)[0] == 0
+    assert admit(srv, W.CARTPOLE, 64, 10, 1)[0] == 1
+    c = W.config(W.CARTPOLE)
+    assert srv.admit(srv.slot_config(W.CARTPOLE, 64, 10, 0.02, 10.0, 1.0, [[1.0]], [[1.0]])) is None
+    srv.close()
+
+
+def test_autotune_leaves_no_trace(N):
+    ref = make_server(N)
+    slots_ref = [admit(ref, s, K, T, rid)[0] for rid, (s, K, T) in enumerate(MIX)]
+    want = run_ticks(ref, slots_ref, [m[0] for m in MIX], 1)[0]
+    ref.close()
+    srv = make_server(N)
+    slots = [admit(srv, s, K, T, rid)[0] for rid, (s, K, T) in enumerate(MIX)]
+    srv.autotune(slots, [W.config(m[0])["x0"] for m in MIX])
+    info = srv.info()
+    assert info["rollout_block"] in (64, 128, 256) and info["rollout_ctas_per_sm"] >= 1
+    got = run_ticks(srv, slots, [m[0] for m in MIX], 1)[0]
+    for rid, (s, K, T) in enumerate(MIX):
+        assert within(got[rid, :W.CONTROL_DIM[s]], want[rid, :W.CONTROL_DIM[s]], W.config(s))
+    srv.close()
