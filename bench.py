@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", default="256,512,1024",
+                    help="concurrency levels of the serving measurement ('' to skip)")
+    ap.add_argument("--serving-ticks", type=int, default=30)
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     return ap.parse_args()
 
 
@@ -194,6 +198,43 @@ def make_ctrl(N, impl, seed, gid, stream_handle):
     return c, cfg
 
 
+def run_serving(levels, n_ticks, seed=0):
+    """Batched serving of a Poisson stream of controllers (uniform mix of cart-pole / car /
+    quadrotor, K in {512, 1024, 4096, 16384}, T in {50, 100, 150, 200}) at each target
+    concurrency: prefill, autotune, then n_ticks receding-horizon ticks with arrivals and
+    departures.  Per level: tick latency p50/p99, deadline misses, rollout-steps/s and the
+    algorithmic FP32 rate of the rollouts against the FP32 peak."""
+    from paper_1509_01149_b300 import _native as N
+    from paper_1509_01149_b300 import serving
+    out = {}
+    for target in levels:
+        srv = N.Server(max(2 * target, 64), max(256 << 20, target << 21))
+        srv.set_env(0, N.map_blob(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL))
+        srv.set_env(1, N.forest_blob(W.quad_forest(0), W.QUAD_GOAL))
+        loop = serving.ServingLoop(srv, W, {W.CAR: 0, W.QUAD: 1}, seed=seed + target)
+        loop.prefill(target, 200.0)
+        srv.autotune([r.slot for r in loop.active], [W.config(r.system)["x0"] for r in loop.active])
+        flops = []
+        orig_step = loop.step
+
+        def step(rate, life, record=True, _loop=loop):
+            f = sum(r.K * r.T * ALGO_FLOPS_PER_ROLLOUT_STEP[r.system] for r in _loop.active)
+            orig_step(rate, life, record)
+            if record:
+                flops.append(f)
+        loop.step = step
+        summ = loop.run(n_ticks, target_active=target, mean_lifetime=200.0)
+        info = srv.info()
+        busy = sum(loop.stats.tick_ms) / 1e3
+        tf = sum(flops) / busy / 1e12 if busy > 0 else None
+        summ.update({"algorithmic_tflops": tf, "fp32_frac": tf / fp32_peak_tflops() if tf else None,
+                     "rollout_block": info["rollout_block"], "ctas_per_sm": info["rollout_ctas_per_sm"]})
+        out[str(target)] = summ
+        loop.drain()
+        srv.close()
+    return out
+
+
 def load_traffic(kernel_tag: str):
     """DRAM traffic per launch from a committed ncu summary, if it was taken on the
     current kernel sources (same source hash); else None."""
@@ -216,6 +257,10 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    levels = [int(v) for v in args.serving.split(",") if v.strip()]
+    if args.serving_only:
+        print(json.dumps({"serving": run_serving(levels, args.serving_ticks)}), flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -313,6 +358,8 @@ def run_ours(args, rank, world, local_rank):
     plain_value = K_SAMPLES * T_STEPS * len(plat) * world / sum(plat)
     pctrl.close()
 
+    serving_res = run_serving(levels, args.serving_ticks, seed=rank) if levels else None
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -361,6 +408,7 @@ def run_ours(args, rank, world, local_rank):
                      else None},
         "clocks": clk,
         "cpu_baseline": cpu,
+        "serving": serving_res,
         "source_hash": source_hash(),
     }
     print(json.dumps(line), flush=True)
