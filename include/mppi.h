@@ -280,6 +280,13 @@ int mppi_server_autotune(mppi_server *srv, int n, const int *slots, const float 
 int mppi_server_get_info(mppi_server *srv, mppi_server_info *out);
 const char *mppi_server_last_error(mppi_server *srv);
 
+/* Check hook for the tensor-core GEMM used by the learned-dynamics training step:
+ * C[m*ldc + n] = sum_k A[m*sam + k*sak] * B[k*sbk + n*sbn] on device buffers (A, B BF16,
+ * C FP32), BN the output tile width (multiple of 16, <= 256).  Synchronises.
+ * Returns 0, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA or MPPI_ETIMEOUT (a bounded wait ran out). */
+int mppi_debug_gemm_bf16(int M, int N, int K, const void *dA, int64_t sam, int64_t sak, const void *dB, int64_t sbk,
+                         int64_t sbn, float *dC, int64_t ldc, int BN);
+
 /* Text of the last error on this ctx (or of the last failed create when ctx is NULL).
  * Valid until the next call on the ctx. */
 const char *mppi_last_error(mppi_ctx *ctx);

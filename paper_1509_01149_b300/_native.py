@@ -78,6 +78,8 @@ SIGNATURES = [
     ("mppi_server_autotune", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP]),
     ("mppi_server_get_info", C.c_int, [_P, C.POINTER(ServerInfo)]),
     ("mppi_server_last_error", C.c_char_p, [_P]),
+    ("mppi_debug_gemm_bf16", C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.c_int64, C.c_int64, _P, C.c_int64,
+                                       C.c_int64, _P, C.c_int64, C.c_int]),
     ("mppi_last_error", C.c_char_p, [_P]),
     ("mppi_version", C.c_char_p, []),
 ]

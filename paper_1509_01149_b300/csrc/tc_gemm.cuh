@@ -1,0 +1,41 @@
+// Host interface of the tcgen05 BF16 GEMM (tc_gemm.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace mppi {
+
+enum GemmEpilogue {
+  kEpiStoreF32 = 0,   // Cf = alpha * acc
+  kEpiAddF32 = 1,     // Cf += alpha * acc
+  kEpiBiasTanh = 2,   // Cb = bf16(tanh(alpha * acc + bias)); Cf (optional) = the same in FP32
+  kEpiBiasF32 = 3,    // Cf = alpha * acc + bias
+  kEpiTanhGrad = 4,   // Cb = bf16(alpha * acc * (1 - H^2))  (backward through tanh)
+};
+
+struct GemmArgs {
+  int M, N, K, BN;              // BN: output tile width (multiple of 16, <= 256)
+  const __nv_bfloat16 *A;
+  int64_t sam, sak;
+  const __nv_bfloat16 *B;
+  int64_t sbk, sbn;
+  int mode;
+  float alpha;
+  float *Cf;
+  int64_t ldc;
+  __nv_bfloat16 *Cb;
+  int64_t ldcb;
+  const float *bias;
+  const __nv_bfloat16 *H;
+  int64_t ldh;
+  int *err;                     // set to 1 if a bounded wait ran out
+};
+
+// Dynamic shared memory of the GEMM CTA.  Sized so the tiles (48 KB) sit well inside the
+// allocation: one CTA per SM, which also keeps the 512-column TMEM allocation uncontended.
+constexpr size_t kGemmSmemBytes = 200 * 1024;
+
+cudaError_t launch_gemm_bf16(const GemmArgs &g, cudaStream_t s);
+
+}  // namespace mppi
