@@ -280,6 +280,40 @@ int mppi_server_autotune(mppi_server *srv, int n, const int *slots, const float 
 int mppi_server_get_info(mppi_server *srv, mppi_server_info *out);
 const char *mppi_server_last_error(mppi_server *srv);
 
+/* ---------------------------------------------------------------------------------
+ * Learned car dynamics (spec extension; not in the paper).
+ *   features  z (16) = (X/20, Y/20, wrap(psi)/pi, (vx-5)/5, vy/2, r/3, delta/0.5,
+ *             u_steer/1.6, u_throttle/1.8, 0 ...), psi wrapped to (-pi, pi]
+ *   network   h1 = tanh(W1 z + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3
+ *   step      x' = x + y[0:7] * out_scale
+ * Parameters: one flat float array of MPPI_MLP_NUM_PARAMS values, W1 [256][16], b1 [256],
+ * W2 [256][256], b2 [256], W3 [16][256], b3 [16] (row = output unit).
+ * Training and prediction run on the tensor cores (tcgen05, BF16 operands, FP32
+ * accumulation); the FP32 master weights are updated by Adam.
+ * --------------------------------------------------------------------------------- */
+#define MPPI_MLP_NUM_PARAMS 74256
+typedef struct mppi_mlp mppi_mlp;
+/* Random initial weights (uniform +-1/sqrt(fan_in), zero biases) from `seed`. */
+int mppi_mlp_create(uint64_t seed, mppi_mlp **out);
+int mppi_mlp_destroy(mppi_mlp *mlp);
+/* Host parameters in (copied; resets the Adam state) / out; out_scale [7] may be NULL. */
+int mppi_mlp_set_params(mppi_mlp *mlp, const float *h_params, const float *h_out_scale);
+int mppi_mlp_get_params(mppi_mlp *mlp, float *h_params, float *h_out_scale);
+/* Training set from device (state [n][7], control [n][2]) pairs: the analytic car step
+ * (dt) gives each next state on the GPU; out_scale becomes the per-state standard
+ * deviation of the increments.  The pairs are only read during the call. */
+int mppi_mlp_set_data(mppi_mlp *mlp, const float *d_states, const float *d_controls, int n, float dt);
+/* `steps` Adam steps (learning rate lr) on random batches of `batch` rows (multiple of
+ * 128) drawn with Philox under `seed`; h_loss_trace [steps] receives each batch loss
+ * (may be NULL; recording it synchronises every step). */
+int mppi_mlp_train(mppi_mlp *mlp, int steps, int batch, float lr, uint64_t seed, float *h_loss_trace);
+/* Loss and gradients of one batch: d_X [B][16] BF16 features, d_T [B][16] FP32 targets
+ * (normalised increments; entries 7..15 ignored).  h_grads [MPPI_MLP_NUM_PARAMS]. */
+int mppi_mlp_grad(mppi_mlp *mlp, const void *d_X, const float *d_T, int B, float *h_grads, double *h_loss);
+/* One learned step for n device (state [n][7], control [n][2]) pairs into d_next [n][7]. */
+int mppi_mlp_predict(mppi_mlp *mlp, const float *d_states, const float *d_controls, int n, float *d_next);
+const char *mppi_mlp_last_error(mppi_mlp *mlp);
+
 /* Check hook for the tensor-core GEMM used by the learned-dynamics training step:
  * C[m*ldc + n] = sum_k A[m*sam + k*sak] * B[k*sbk + n*sbn] on device buffers (A, B BF16,
  * C FP32), BN the output tile width (multiple of 16, <= 256).  Synchronises.

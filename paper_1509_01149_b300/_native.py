@@ -80,6 +80,15 @@ SIGNATURES = [
     ("mppi_server_last_error", C.c_char_p, [_P]),
     ("mppi_debug_gemm_bf16", C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.c_int64, C.c_int64, _P, C.c_int64,
                                        C.c_int64, _P, C.c_int64, C.c_int]),
+    ("mppi_mlp_create", C.c_int, [C.c_uint64, C.POINTER(_P)]),
+    ("mppi_mlp_destroy", C.c_int, [_P]),
+    ("mppi_mlp_set_params", C.c_int, [_P, _FP, _FP]),
+    ("mppi_mlp_get_params", C.c_int, [_P, _FP, _FP]),
+    ("mppi_mlp_set_data", C.c_int, [_P, _P, _P, C.c_int, C.c_float]),
+    ("mppi_mlp_train", C.c_int, [_P, C.c_int, C.c_int, C.c_float, C.c_uint64, _FP]),
+    ("mppi_mlp_grad", C.c_int, [_P, _P, _P, C.c_int, _FP, C.POINTER(C.c_double)]),
+    ("mppi_mlp_predict", C.c_int, [_P, _P, _P, C.c_int, _P]),
+    ("mppi_mlp_last_error", C.c_char_p, [_P]),
     ("mppi_last_error", C.c_char_p, [_P]),
     ("mppi_version", C.c_char_p, []),
 ]
@@ -387,3 +396,75 @@ class Server:
         i = ServerInfo()
         self._chk(lib.mppi_server_get_info(self._h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in ServerInfo._fields_}
+
+
+MLP_NUM_PARAMS = 74256
+MLP_LAYOUT = (("W1", (256, 16)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (16, 256)), ("b3", (16,)))
+
+
+def mlp_pack(params: dict) -> np.ndarray:
+    """Flat float32 parameter array in the order of the C ABI."""
+    return np.concatenate([np.asarray(params[k], dtype=np.float32).reshape(-1) for k, _ in MLP_LAYOUT])
+
+
+def mlp_unpack(flat) -> dict:
+    out, o = {}, 0
+    for k, shape in MLP_LAYOUT:
+        n = int(np.prod(shape))
+        out[k] = np.asarray(flat[o:o + n], dtype=np.float32).reshape(shape)
+        o += n
+    return out
+
+
+class MLP:
+    """The learned car-dynamics surrogate (mppi_mlp): training and prediction on the GPU."""
+
+    def __init__(self, seed: int = 0):
+        h = _P()
+        rc = lib.mppi_mlp_create(seed, C.byref(h))
+        if rc != MPPI_OK:
+            raise MppiError(rc, "mppi_mlp_create failed")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.mppi_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc != MPPI_OK:
+            raise MppiError(rc, lib.mppi_mlp_last_error(self._h).decode())
+
+    def set_params(self, params: dict, out_scale=None):
+        flat = mlp_pack(params)
+        sc = None if out_scale is None else _f32(out_scale, 7)
+        self._chk(lib.mppi_mlp_set_params(self._h, _fp(flat), None if sc is None else _fp(sc)))
+
+    def get_params(self):
+        flat = np.zeros(MLP_NUM_PARAMS, dtype=np.float32)
+        sc = np.zeros(7, dtype=np.float32)
+        self._chk(lib.mppi_mlp_get_params(self._h, _fp(flat), _fp(sc)))
+        return mlp_unpack(flat), sc
+
+    def set_data(self, d_states: int, d_controls: int, n: int, dt: float):
+        self._chk(lib.mppi_mlp_set_data(self._h, C.c_void_p(d_states), C.c_void_p(d_controls), n, dt))
+
+    def train(self, steps: int, batch: int, lr: float, seed: int = 0, trace: bool = False):
+        tr = np.zeros(max(steps, 1), dtype=np.float32) if trace else None
+        self._chk(lib.mppi_mlp_train(self._h, steps, batch, lr, seed, None if tr is None else _fp(tr)))
+        return tr
+
+    def grad(self, d_X: int, d_T: int, B: int):
+        g = np.zeros(MLP_NUM_PARAMS, dtype=np.float32)
+        loss = C.c_double()
+        self._chk(lib.mppi_mlp_grad(self._h, C.c_void_p(d_X), C.c_void_p(d_T), B, _fp(g), C.byref(loss)))
+        return mlp_unpack(g), loss.value
+
+    def predict(self, d_states: int, d_controls: int, n: int, d_next: int):
+        self._chk(lib.mppi_mlp_predict(self._h, C.c_void_p(d_states), C.c_void_p(d_controls), n, C.c_void_p(d_next)))

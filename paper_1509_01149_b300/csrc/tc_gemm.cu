@@ -42,8 +42,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
   uint32_t phase = 0;
   bool ok = true;
 
-  for (int k0 = 0; k0 < g.K && ok; k0 += kKT) {
-    const int klen = min(kKT, g.K - k0);
+  // split-K: this CTA reduces K in [kbeg, kend)
+  const int nsplit = g.ksplit > 1 ? g.ksplit : 1;
+  const int kchunk = ((g.K + nsplit - 1) / nsplit + kKT - 1) / kKT * kKT;
+  const int kbeg = blockIdx.z * kchunk, kend = min(g.K, kbeg + kchunk);
+  const int64_t csn = g.ldcn ? g.ldcn : 1;
+  for (int k0 = kbeg; k0 < kend && ok; k0 += kKT) {
+    const int klen = min(kKT, kend - k0);
     const int kpad = (klen + 15) & ~15;
     // gather the A slab
     for (int idx = tid; idx < kBM * kpad; idx += kThreads) {
@@ -84,7 +89,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
       for (int kk = 0; kk < kpad / 16; ++kk) {
         const uint64_t ad = tc::smem_desc(a0 + kk * 2 * lbo_a, lbo_a, 128);
         const uint64_t bd = tc::smem_desc(b0 + kk * 2 * lbo_b, lbo_b, 128);
-        tc::mma_bf16(tmem, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
+        tc::mma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || kk > 0) ? 1u : 0u);
       }
       tc::mma_commit(&bar);
     }
@@ -100,7 +105,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
   } else {
     // epilogue: row m = m0 + 32*warp + lane, columns n0 .. n0+BN
     const int m = m0 + 32 * warp + lane;
-    for (int c0 = 0; c0 < BN; c0 += 8) {
+    const bool empty = kbeg >= kend;  // a split with no K range contributes nothing
+    for (int c0 = 0; c0 < BN && !empty; c0 += 8) {
       float v[8];
       tc::tmem_ld8(tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(c0), v);
       tc::tmem_ld_wait();
@@ -112,19 +118,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
           float a = g.alpha * v[j];
           switch (g.mode) {
             case kEpiStoreF32:
-              g.Cf[static_cast<int64_t>(m) * g.ldc + n] = a;
+              g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = a;
               break;
             case kEpiAddF32:
-              g.Cf[static_cast<int64_t>(m) * g.ldc + n] += a;
+              g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] += a;
+              break;
+            case kEpiAtomicF32:
+              atomicAdd(&g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn], a);
               break;
             case kEpiBiasTanh: {
               const float h = tanhf(a + g.bias[n]);
               g.Cb[static_cast<int64_t>(m) * g.ldcb + n] = __float2bfloat16(h);
-              if (g.Cf) g.Cf[static_cast<int64_t>(m) * g.ldc + n] = h;
+              if (g.Cf) g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = h;
               break;
             }
             case kEpiBiasF32:
-              g.Cf[static_cast<int64_t>(m) * g.ldc + n] = a + g.bias[n];
+              g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = a + g.bias[n];
               break;
             case kEpiTanhGrad: {
               const float h = __bfloat162float(g.H[static_cast<int64_t>(m) * g.ldh + n]);
@@ -154,7 +163,9 @@ cudaError_t launch_gemm_bf16(const GemmArgs &g, cudaStream_t s) {
     attr_set = true;
   }
   if (g.BN < 16 || g.BN > 256 || (g.BN & 15) != 0) return cudaErrorInvalidValue;
-  const dim3 grid((g.M + kBM - 1) / kBM, (g.N + g.BN - 1) / g.BN);
+  const int nsplit = g.ksplit > 1 ? g.ksplit : 1;
+  if (nsplit > 1 && g.mode != kEpiAtomicF32) return cudaErrorInvalidValue;
+  const dim3 grid((g.M + kBM - 1) / kBM, (g.N + g.BN - 1) / g.BN, nsplit);
   k_gemm_bf16<<<grid, kThreads, kGemmSmemBytes, s>>>(g);
   return cudaGetLastError();
 }

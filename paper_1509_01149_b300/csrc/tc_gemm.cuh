@@ -12,6 +12,7 @@ enum GemmEpilogue {
   kEpiBiasTanh = 2,   // Cb = bf16(tanh(alpha * acc + bias)); Cf (optional) = the same in FP32
   kEpiBiasF32 = 3,    // Cf = alpha * acc + bias
   kEpiTanhGrad = 4,   // Cb = bf16(alpha * acc * (1 - H^2))  (backward through tanh)
+  kEpiAtomicF32 = 5,  // Cf += alpha * acc with atomicAdd (split-K partial sums)
 };
 
 struct GemmArgs {
@@ -23,13 +24,15 @@ struct GemmArgs {
   int mode;
   float alpha;
   float *Cf;
-  int64_t ldc;
+  int64_t ldc;                  // Cf(m, n) = Cf[m*ldc + n*ldcn]
+  int64_t ldcn;                 // column stride of Cf (1 = row-major; 0 is read as 1)
   __nv_bfloat16 *Cb;
   int64_t ldcb;
   const float *bias;
   const __nv_bfloat16 *H;
   int64_t ldh;
   int *err;                     // set to 1 if a bounded wait ran out
+  int ksplit;                   // K range split over gridDim.z CTAs (mode kEpiAtomicF32); 0/1 = no split
 };
 
 // Dynamic shared memory of the GEMM CTA.  Sized so the tiles (48 KB) sit well inside the

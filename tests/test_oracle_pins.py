@@ -619,3 +619,78 @@ def test_shift_and_u_init():
     U = np.arange(12, dtype=np.float64).reshape(6, 2)
     s = mppi.shift(U, [7.0, -7.0])
     assert np.array_equal(s[:-1], U[1:]) and np.array_equal(s[-1], [7.0, -7.0])
+
+
+# ---------------------------------------------------------------------------
+# learned dynamics (oracle/mlp.py)
+# ---------------------------------------------------------------------------
+def test_mlp_backward_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    p = mlp.init_params(3)
+    for k in p:                       # non-trivial biases and padded entries too
+        p[k] = p[k] + 0.05 * rng.normal(size=p[k].shape)
+    z = rng.normal(size=(16, 6))
+    t = rng.normal(size=(16, 6))
+    _, g = mlp.loss_and_grads(p, z, t)
+    h = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(12, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = mlp.loss_and_grads(p, z, t)
+            flat[idx] = old - h
+            lm, _ = mlp.loss_and_grads(p, z, t)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[k].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd)), (k, idx, fd, an)
+
+
+def test_mlp_first_adam_step_closed_form():
+    from oracle import mlp
+    p = mlp.init_params(1)
+    g = {k: np.random.default_rng(2).normal(size=v.shape) for k, v in p.items()}
+    p0 = {k: v.copy() for k, v in p.items()}
+    st = mlp.adam_init(p)
+    mlp.adam_step(p, g, st, lr=1e-3)
+    for k in p:   # m_hat = g, v_hat = g^2 at t = 1
+        assert np.allclose(p[k], p0[k] - 1e-3 * g[k] / (np.abs(g[k]) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_mlp_features_periodic_in_heading_and_zero_layer_is_identity():
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(7, 50)) * 3
+    u = rng.normal(size=(2, 50))
+    x2 = x.copy()
+    x2[2] += 2 * math.pi * rng.integers(-3, 4, 50)
+    assert np.allclose(mlp.features(x, u), mlp.features(x2, u), atol=1e-12)
+    w = mlp.wrap_angle(np.linspace(-20, 20, 1001))
+    assert np.all((w > -math.pi - 1e-12) & (w <= math.pi + 1e-12))
+    p = mlp.init_params(0)
+    p["W3"][:] = 0.0
+    p["b3"][:] = 0.0
+    assert np.array_equal(mlp.predict(p, np.ones(7), x, u), x)
+
+
+def test_mlp_training_reduces_loss_on_analytic_transitions():
+    """A few hundred Adam steps on analytic car transitions cut the normalised loss."""
+    from oracle import mlp
+    xs, us = W.car_transition_inputs(11, 512)
+    car = _car(0.02)
+    x, u = xs.T.astype(np.float64), us.T.astype(np.float64)
+    dx = car.step(x, u) - x
+    scale = dx.std(axis=1) + 1e-9
+    t = np.zeros((16, x.shape[1]))
+    t[:7] = dx / scale[:, None]
+    z = mlp.features(x, u)
+    p = mlp.init_params(0)
+    st = mlp.adam_init(p)
+    l0, _ = mlp.loss_and_grads(p, z, t)
+    for _ in range(300):
+        _, g = mlp.loss_and_grads(p, z, t)
+        mlp.adam_step(p, g, st, 3e-3)
+    l1, _ = mlp.loss_and_grads(p, z, t)
+    assert l1 < 0.1 * l0

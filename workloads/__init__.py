@@ -187,3 +187,31 @@ def env_for(system: int, seed: int = 0):
     if system == QUAD:
         return quad_forest(seed)
     return None
+
+
+# ----------------------------------------------------------------------------
+# learned-dynamics training inputs (states along the track, random controls)
+# ----------------------------------------------------------------------------
+def car_transition_inputs(seed: int, n: int, track_seed: int = 0):
+    """n (state, control) pairs for training the car surrogate: positions on the track
+    (centreline point + lateral offset U[-2, 2] m), heading = tangent + N(0, 0.3),
+    vx ~ U[1, 12], vy ~ N(0, 0.5), r ~ N(0, 1), delta ~ U[-0.5, 0.5]; controls uniform in
+    +-3 sigma of Sigma = diag(0.3, 0.35).  Returns float32 arrays [n][7], [n][2]."""
+    rng = np.random.default_rng(seed)
+    c = track_centreline(track_seed)
+    npts = len(c)
+    idx = rng.integers(0, npts, n)
+    p0, p1 = c[idx], c[(idx + 1) % npts]
+    tang = np.arctan2(p1[:, 1] - p0[:, 1], p1[:, 0] - p0[:, 0])
+    lat = rng.uniform(-2.0, 2.0, n)
+    x = np.empty((n, 7), dtype=np.float64)
+    x[:, 0] = p0[:, 0] - lat * np.sin(tang)
+    x[:, 1] = p0[:, 1] + lat * np.cos(tang)
+    x[:, 2] = tang + rng.normal(0.0, 0.3, n)
+    x[:, 3] = rng.uniform(1.0, 12.0, n)
+    x[:, 4] = rng.normal(0.0, 0.5, n)
+    x[:, 5] = rng.normal(0.0, 1.0, n)
+    x[:, 6] = rng.uniform(-0.5, 0.5, n)
+    sig = np.sqrt([0.3, 0.35])
+    u = rng.uniform(-3.0, 3.0, (n, 2)) * sig
+    return x.astype(np.float32), u.astype(np.float32)
