@@ -151,6 +151,7 @@ int mppi_set_u_init(mppi_ctx *ctx, const float *h_u);
  * The blob kind must match the system; EINVAL otherwise. */
 #define MPPI_ENV_MAP 0x3150414du    /* "MAP1" */
 #define MPPI_ENV_FOREST 0x31524f46u /* "FOR1" */
+#define MPPI_ENV_MLP 0x31504c4du    /* "MLP1" */
 typedef struct {
   uint32_t kind; /* MPPI_ENV_MAP */
   int32_t width, height;
@@ -162,6 +163,15 @@ typedef struct {
   float goal[3];
   float pad;
 } mppi_env_forest;
+/*   MPPI_CAR_MLP also needs the learned dynamics: mppi_env_mlp header followed by
+ *     MPPI_MLP_NUM_PARAMS float32 parameters (layout of the mppi_mlp_* functions);
+ *     converted to BF16 tensor-core tiles on the device.  precision 0 = BF16. */
+typedef struct {
+  uint32_t kind; /* MPPI_ENV_MLP */
+  int32_t precision;
+  float out_scale[7];
+  float pad;
+} mppi_env_mlp;
 int mppi_set_env(mppi_ctx *ctx, const void *blob, size_t bytes);
 
 /* Results of the last mppi_step, host outputs (any may be NULL); synchronises.

@@ -63,10 +63,25 @@ def init_params(seed: int = 0):
     return p
 
 
-def forward(p, z):
-    """z [16][B] -> (y [16][B], cache)."""
-    h1 = np.tanh(p["W1"] @ z + p["b1"][:, None])
-    h2 = np.tanh(p["W2"] @ h1 + p["b2"][:, None])
+def round_bf16(a):
+    """Round to the nearest bfloat16 value (ties to even), returned as float64.  bfloat16
+    keeps the sign, the 8 exponent bits and the top 7 fraction bits of a float32."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    out = (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32).astype(np.float64)
+    return np.where(np.isfinite(f), out, f.astype(np.float64))
+
+
+def forward(p, z, act_round=None):
+    """z [16][B] -> (y [16][B], cache).  act_round (e.g. round_bf16) is applied to the
+    network input and to both hidden activations: the storage precision of a kernel
+    that keeps them in that format between its matrix products."""
+    q = act_round or (lambda a: a)
+    z = q(z)
+    h1 = q(np.tanh(p["W1"] @ z + p["b1"][:, None]))
+    h2 = q(np.tanh(p["W2"] @ h1 + p["b2"][:, None]))
     y = p["W3"] @ h2 + p["b3"][:, None]
     return y, (z, h1, h2)
 
@@ -103,18 +118,21 @@ def adam_step(p, g, st, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
 
 
-def predict(p, out_scale, x, u):
+def predict(p, out_scale, x, u, act_round=None):
     """x' = x + y[0:7] * out_scale for x [7][K], u [2][K]."""
-    y, _ = forward(p, features(x, u))
+    y, _ = forward(p, features(x, u), act_round)
     return np.asarray(x, dtype=np.float64) + y[:N_STATE] * np.asarray(out_scale, dtype=np.float64)[:, None]
 
 
 class CarMLP(systems.Car):
-    """The car workload with the learned step in place of the analytic one (same cost)."""
+    """The car workload with the learned step in place of the analytic one (same cost).
+    act_round=round_bf16 models a network whose inputs and hidden activations are stored
+    in bfloat16 (weights are passed already rounded by the caller)."""
 
-    def __init__(self, dt, cost_map, origin, h, params, out_scale, **kw):
+    def __init__(self, dt, cost_map, origin, h, params, out_scale, act_round=None, **kw):
         super().__init__(dt, cost_map, origin, h, **kw)
         self.params, self.out_scale = params, np.asarray(out_scale, dtype=np.float64)
+        self.act_round = act_round
 
     def step(self, x, v):
-        return predict(self.params, self.out_scale, x, v)
+        return predict(self.params, self.out_scale, x, v, self.act_round)

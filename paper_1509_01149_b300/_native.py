@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmppi_b300.so")
 MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE, MPPI_ENOSYS = 0, -1, -2, -3, -4, -5, -6
 MPPI_CARTPOLE, MPPI_CAR, MPPI_QUAD, MPPI_CAR_MLP = 0, 1, 2, 3
 MPPI_IMPL_FUSED, MPPI_IMPL_PLAIN = 0, 1
-MPPI_ENV_MAP, MPPI_ENV_FOREST = 0x3150414D, 0x31524F46
+MPPI_ENV_MAP, MPPI_ENV_FOREST, MPPI_ENV_MLP = 0x3150414D, 0x31524F46, 0x31504C4D
 STATE_DIM = {MPPI_CARTPOLE: 4, MPPI_CAR: 7, MPPI_QUAD: 12, MPPI_CAR_MLP: 7}
 CONTROL_DIM = {MPPI_CARTPOLE: 1, MPPI_CAR: 2, MPPI_QUAD: 4, MPPI_CAR_MLP: 2}
 
@@ -137,6 +137,12 @@ def forest_blob(obstacles: np.ndarray, goal) -> bytes:
     O = np.ascontiguousarray(obstacles, dtype=np.float32).reshape(-1, 3)
     g = [float(v) for v in goal]
     return struct.pack("<Iiffff", MPPI_ENV_FOREST, O.shape[0], g[0], g[1], g[2], 0.0) + O.tobytes()
+
+
+def mlp_blob(params: dict, out_scale, precision: int = 0) -> bytes:
+    """mppi_env_mlp header + the flat float32 parameters (learned dynamics of MPPI_CAR_MLP)."""
+    sc = [float(v) for v in np.asarray(out_scale, dtype=np.float32).reshape(-1)[:7]]
+    return struct.pack("<Ii7ff", MPPI_ENV_MLP, precision, *sc, 0.0) + mlp_pack(params).tobytes()
 
 
 def mppi_philox_words(seed: int, K: int, n_blocks: int, counter: int, gid: int) -> np.ndarray:

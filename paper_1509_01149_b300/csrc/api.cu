@@ -11,6 +11,7 @@
 
 #include "../../include/mppi.h"
 #include "kernels.cuh"
+#include "mlp_model.cuh"
 
 using namespace mppi;
 
@@ -124,6 +125,9 @@ struct mppi_ctx {
   float *d_env = nullptr;      // cost map or forest (separate allocation)
   size_t env_bytes = 0;
   bool env_ok = false;
+  unsigned char *d_mlp = nullptr;  // learned dynamics: MlpDev + tiles + biases
+  bool mlp_ok = false;
+  int *d_mlp_err = nullptr;
 
   float *h_x0 = nullptr, *h_u0 = nullptr;  // pinned staging
 
@@ -155,9 +159,15 @@ struct mppi_ctx {
 
 namespace {
 
+int launch_rollout(mppi_ctx *c, cudaStream_t s) {
+  if (c->sys == MPPI_CAR_MLP)
+    return c->cuda(launch_rollout_mlp(c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s), "mlp rollout launch");
+  return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
+                 "fused rollout launch");
+}
+
 int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
-  MPPI_TRY(c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
-                   "fused rollout launch"));
+  MPPI_TRY(launch_rollout(c, s));
   return c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->d_u0, c->d_dU, c->d_dbg, s),
                  "merge launch");
 }
@@ -203,7 +213,76 @@ int build_graph(mppi_ctx *c) {
 
 int check_ready(mppi_ctx *c) {
   if (c->needs_env() && !c->env_ok) return c->fail(MPPI_ESTATE, "system needs an environment (mppi_set_env)");
-  if (c->sys == MPPI_CAR_MLP) return c->fail(MPPI_ENOSYS, "learned dynamics not available in this build");
+  if (c->sys == MPPI_CAR_MLP && !c->mlp_ok) return c->fail(MPPI_ESTATE, "learned dynamics need MPPI_ENV_MLP weights");
+  if (c->sys == MPPI_CAR_MLP && c->impl == MPPI_IMPL_PLAIN)
+    return c->fail(MPPI_EINVAL, "the plain loop is not built for the learned dynamics");
+  return MPPI_OK;
+}
+
+int check_mlp_error(mppi_ctx *c) {
+  if (c->sys != MPPI_CAR_MLP) return MPPI_OK;
+  int e = 0;
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(&e, c->d_mlp_err, sizeof e, cudaMemcpyDeviceToHost, c->stream), "err copy"));
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
+  return e ? c->fail(MPPI_ETIMEOUT, "a tensor-core wait of the learned-dynamics rollout ran out") : MPPI_OK;
+}
+
+// round-to-nearest-even float -> bfloat16 bits
+uint16_t to_bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return static_cast<uint16_t>((u >> 16) | ((u & 0xffffu) ? 0x40u : 0u));
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return static_cast<uint16_t>(u >> 16);
+}
+
+// weights W [rows][cols] -> BF16 K-major core-matrix tile (rows = output units, K = cols)
+void to_tile(const float *W, int rows, int cols, unsigned char *dst) {
+  for (int r = 0; r < rows; ++r)
+    for (int k = 0; k < cols; ++k) {
+      const uint32_t off = static_cast<uint32_t>((((k >> 3) * (rows >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+      const uint16_t b = to_bf16_bits(W[static_cast<size_t>(r) * cols + k]);
+      std::memcpy(dst + off, &b, 2);
+    }
+}
+
+int set_mlp_env(mppi_ctx *c, const void *blob, size_t bytes) {
+  if (c->sys != MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "learned-dynamics weights for a system without them");
+  if (bytes != sizeof(mppi_env_mlp) + sizeof(float) * mlp::kNumParams)
+    return c->fail(MPPI_EINVAL, "MLP blob must hold the header and %d floats", static_cast<int>(mlp::kNumParams));
+  mppi_env_mlp h;
+  std::memcpy(&h, blob, sizeof h);
+  if (h.precision != 0) return c->fail(MPPI_EINVAL, "unsupported MLP precision %d", h.precision);
+  const float *P = reinterpret_cast<const float *>(static_cast<const char *>(blob) + sizeof h);
+  for (size_t i = 0; i < mlp::kNumParams; ++i)
+    if (!std::isfinite(P[i])) return c->fail(MPPI_EINVAL, "non-finite MLP parameter");
+  const size_t off_w1 = 256, off_w2 = off_w1 + 256 * 16 * 2, off_w3 = off_w2 + 256 * 256 * 2,
+               off_b = off_w3 + 16 * 256 * 2, total = off_b + sizeof(float) * (256 + 256 + 16);
+  std::vector<unsigned char> host(total, 0);
+  to_tile(P + mlp::kOffW1, 256, 16, host.data() + off_w1);
+  to_tile(P + mlp::kOffW2, 256, 256, host.data() + off_w2);
+  to_tile(P + mlp::kOffW3, 16, 256, host.data() + off_w3);
+  std::memcpy(host.data() + off_b, P + mlp::kOffB1, sizeof(float) * 256);
+  std::memcpy(host.data() + off_b + 1024, P + mlp::kOffB2, sizeof(float) * 256);
+  std::memcpy(host.data() + off_b + 2048, P + mlp::kOffB3, sizeof(float) * 16);
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
+  if (!c->d_mlp) MPPI_TRY(c->cuda(cudaMalloc(&c->d_mlp, total), "cudaMalloc(mlp)"));
+  MlpDev d{};
+  d.w1 = c->d_mlp + off_w1;
+  d.w2 = c->d_mlp + off_w2;
+  d.w3 = c->d_mlp + off_w3;
+  d.b1 = reinterpret_cast<const float *>(c->d_mlp + off_b);
+  d.b2 = d.b1 + 256;
+  d.b3 = d.b2 + 256;
+  for (int i = 0; i < 7; ++i) d.out_scale[i] = h.out_scale[i];
+  d.err = c->d_mlp_err;
+  d.precision = h.precision;
+  std::memcpy(host.data(), &d, sizeof d);
+  MPPI_TRY(c->cuda(cudaMemcpy(c->d_mlp, host.data(), total, cudaMemcpyHostToDevice), "mlp copy"));
+  MPPI_TRY(c->cuda(cudaMemset(c->d_mlp_err, 0, sizeof(int)), "err zero"));
+  c->p.mlp = c->d_mlp;
+  c->mlp_ok = true;
+  c->graph_dirty = true;
   return MPPI_OK;
 }
 
@@ -278,6 +357,13 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   p.map_inv_cell = 1.0f;
 
   c->blk = fused_block_size(p);
+  if (sys == MPPI_CAR_MLP) {
+    if (T > kMlpMaxT) {
+      delete c;
+      return bad("T out of range [1, 600] for the learned dynamics");
+    }
+    c->blk = kFusedBlockRegen;  // 128 samples per block, du regenerated
+  }
   if (c->blk == 0) {
     delete c;
     return bad("T*m too large for the fused rollout's shared memory");
@@ -286,12 +372,13 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
 
   int rc = c->cuda(cudaGetDevice(&c->device), "cudaGetDevice");
   if (rc == MPPI_OK) rc = c->cuda(prepare_kernels(), "kernel attributes");
+  if (rc == MPPI_OK && sys == MPPI_CAR_MLP) rc = c->cuda(prepare_mlp_kernel(), "mlp kernel attributes");
   if (rc == MPPI_OK) rc = c->cuda(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
   if (rc == MPPI_OK) c->own_stream = true;
   const size_t TM = static_cast<size_t>(T) * m;
   const size_t nb_max = (K + kFusedBlockSmall - 1) / kFusedBlockSmall;
   c->arena.size = 256 * 16 + sizeof(CtrlState) + sizeof(float) * (2 * TM + 2 * kMaxM + K + nb_max * TM) +
-                  sizeof(BlockPartial) * nb_max + sizeof(StepDebug) + sizeof(uint32_t);
+                  sizeof(BlockPartial) * nb_max + sizeof(StepDebug) + 2 * sizeof(uint32_t);
   if (rc == MPPI_OK) rc = c->cuda(cudaMalloc(&c->arena.base, c->arena.size), "cudaMalloc(arena)");
   if (rc == MPPI_OK) {
     c->d_st = c->arena.take<CtrlState>(1);
@@ -304,7 +391,8 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
     c->d_part = c->arena.take<BlockPartial>(nb_max);
     c->d_dbg = c->arena.take<StepDebug>(1);
     c->d_ctr = c->arena.take<uint32_t>(1);
-    if (!c->d_ctr) rc = c->fail(MPPI_ENOMEM, "arena too small");
+    c->d_mlp_err = c->arena.take<int>(1);
+    if (!c->d_mlp_err) rc = c->fail(MPPI_ENOMEM, "arena too small");
   }
   if (rc == MPPI_OK) rc = c->cuda(cudaMemsetAsync(c->arena.base, 0, c->arena.size, c->stream), "memset");
   if (rc == MPPI_OK) rc = c->cuda(cudaMallocHost(&c->h_x0, sizeof(float) * kMaxN), "cudaMallocHost");
@@ -326,6 +414,7 @@ int mppi_destroy(mppi_ctx *c) {
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->d_du) cudaFree(c->d_du);
   if (c->d_env) cudaFree(c->d_env);
+  if (c->d_mlp) cudaFree(c->d_mlp);
   if (c->h_x0) cudaFreeHost(c->h_x0);
   if (c->h_u0) cudaFreeHost(c->h_u0);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -407,6 +496,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   const char *payload = nullptr;
   size_t payload_bytes = 0;
   CtrlParams np = c->p;
+  if (kind == MPPI_ENV_MLP) return set_mlp_env(c, blob, bytes);
   if (kind == MPPI_ENV_MAP) {
     if (c->sys != MPPI_CAR && c->sys != MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "map env for a non-car system");
     if (bytes < sizeof(mppi_env_map)) return c->fail(MPPI_EINVAL, "map header truncated");
@@ -459,8 +549,9 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
     np.obs = c->d_env;
     np.map = nullptr;
   }
+  np.mlp = c->p.mlp;
   c->p = np;
-  c->blk = fused_block_size(c->p);
+  c->blk = c->sys == MPPI_CAR_MLP ? kFusedBlockRegen : fused_block_size(c->p);
   c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
   c->env_ok = true;
   c->graph_dirty = true;
@@ -489,6 +580,7 @@ int mppi_step(mppi_ctx *c, const float *state, float *u0_out) {
     MPPI_TRY(c->cuda(cudaGraphLaunch(c->graph, c->stream), "graph launch"));
   }
   MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
+  MPPI_TRY(check_mlp_error(c));
   std::memcpy(u0_out, c->h_u0, sizeof(float) * c->m);
   return MPPI_OK;
 }
@@ -503,8 +595,7 @@ int mppi_rollout_async(mppi_ctx *c, const float *d_state) {
     MPPI_TRY(c->cuda(launch_plain_noise(c->p, &c->d_st->counter, c->d_du, c->stream), "plain noise"));
     return c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->d_U, c->d_du, c->d_S, c->stream), "plain rollout");
   }
-  return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, c->stream),
-                 "fused rollout launch");
+  return launch_rollout(c, c->stream);
 }
 
 int mppi_update_async(mppi_ctx *c, float *d_u0_out) {

@@ -34,6 +34,14 @@ cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part
 // Shift of Algorithm 1 and iteration counter increment.
 cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s);
 
+// Learned car dynamics (mlp_rollout.cu) -----------------------------------------
+constexpr size_t kMlpSmemLimit = 226 * 1024;
+constexpr int kMlpMaxT = 600;
+size_t mlp_rollout_smem_bytes(int T);
+cudaError_t prepare_mlp_kernel();
+cudaError_t launch_rollout_mlp(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *part_sums,
+                               BlockPartial *part, cudaStream_t s);
+
 // Plain-loop baseline ---------------------------------------------------------
 cudaError_t launch_plain_noise(const CtrlParams &p, const uint32_t *counter, float *du, cudaStream_t s);
 cudaError_t launch_plain_rollout(int sys, const CtrlParams &p, const CtrlState *st, const float *U,

@@ -1,0 +1,292 @@
+// Fused MPPI rollout with the learned car dynamics on the tensor cores (sm_103a).
+//
+// One CTA of 128 threads owns 128 samples (thread t = sample k0 + t = TMEM lane t = row
+// t of every activation tile).  The network weights are copied once into shared memory
+// in the K-major core-matrix layout; TMEM holds the FP32 accumulators (columns 0..255
+// for the two hidden layers, 256..271 for the output layer).  Per time step:
+//   noise du_i (Philox), v = u_i + du_i, features z(x, v) -> X tile (BF16)
+//   MMA  D = X W1^T       (M=128, N=256, K=16)   -> tanh(D + b1) -> H (BF16, smem)
+//   MMA  D = H W2^T       (M=128, N=256, K=256)  -> tanh(D + b2) -> H
+//   MMA  D3 = H W3^T      (M=128, N=16,  K=256)  -> x += (D3 + b3) * out_scale  (FP32)
+//   S~ += q(x) + IS running cost (Kahan FP32)
+// tanh runs on the special-function unit (its error, ~2^-11, is below the BF16 step of
+// the activations it feeds).  After the horizon the block forms its softmax partial with
+// du regenerated from the counter-based generator (shared memory is full of weights).
+// Every mbarrier wait is bounded; on a timeout the kernel flags the error, waits once
+// more (bounded) for its MMAs, frees its TMEM and returns.
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "mlp_model.cuh"
+#include "rollout_body.cuh"
+#include "tc_common.cuh"
+
+namespace mppi {
+
+namespace {
+constexpr int kMlpThreads = 128;
+constexpr uint32_t kTmemCols = 512;
+// shared-memory layout (bytes)
+constexpr uint32_t kSW2 = 0;                       // W2 tile 256 x 256 bf16
+constexpr uint32_t kSW1 = kSW2 + 256 * 256 * 2;    // W1 tile 256 x 16
+constexpr uint32_t kSW3 = kSW1 + 256 * 16 * 2;     // W3 tile 16 x 256
+constexpr uint32_t kSH = kSW3 + 16 * 256 * 2;      // H tile 128 x 256
+constexpr uint32_t kSX = kSH + 128 * 256 * 2;      // X tile 128 x 16
+constexpr uint32_t kSB = kSX + 128 * 16 * 2;       // b1 [256], b2 [256], b3 [16], out_scale [8] (f32)
+constexpr uint32_t kSU = kSB + (256 + 256 + 16 + 8) * 4;  // sU [TM], sRu [TM], sHu [T] (f32)
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// H row `row` (columns 0..255) = bf16(tanh(D[row][:] + bias)), D read from TMEM columns 0..255
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bias, unsigned char *smem, int row) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < 256; c0 += 32) {
+    float v[32];
+    tmem_ld32(tmem_row + static_cast<uint32_t>(c0), v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = c0 + q * 8 + 2 * j;
+        w[j] = pack_bf16(tc::tanh_approx(v[q * 8 + 2 * j] + bias[c]), tc::tanh_approx(v[q * 8 + 2 * j + 1] + bias[c + 1]));
+      }
+      *reinterpret_cast<uint4 *>(smem + kSH + tc::kmajor_offset(row, c0 + q * 8, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams p, const CtrlState *__restrict__ st,
+                                                                const float *__restrict__ U, float *__restrict__ S_out,
+                                                                float *__restrict__ part_sums,
+                                                                BlockPartial *__restrict__ part) {
+  constexpr int M = 2, N = 7;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const MlpDev *md = static_cast<const MlpDev *>(p.mlp);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int T = p.T, TM = T * M;
+  float *sb1 = reinterpret_cast<float *>(smem + kSB);
+  float *sb2 = sb1 + 256;
+  float *sb3 = sb2 + 256;
+  float *sscale = sb3 + 16;
+  float *sU = reinterpret_cast<float *>(smem + kSU);
+  float *sRu = sU + TM;
+  float *sHu = sRu + TM;
+
+  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  if (tid == 0) tc::mbar_init(&bar, 1);
+  // weights (already in tile layout) and biases
+  {
+    const uint4 *w2 = reinterpret_cast<const uint4 *>(md->w2);
+    const uint4 *w1 = reinterpret_cast<const uint4 *>(md->w1);
+    const uint4 *w3 = reinterpret_cast<const uint4 *>(md->w3);
+    uint4 *d2 = reinterpret_cast<uint4 *>(smem + kSW2);
+    uint4 *d1 = reinterpret_cast<uint4 *>(smem + kSW1);
+    uint4 *d3 = reinterpret_cast<uint4 *>(smem + kSW3);
+    for (int i = tid; i < 256 * 256 * 2 / 16; i += kMlpThreads) d2[i] = w2[i];
+    for (int i = tid; i < 256 * 16 * 2 / 16; i += kMlpThreads) d1[i] = w1[i];
+    for (int i = tid; i < 16 * 256 * 2 / 16; i += kMlpThreads) d3[i] = w3[i];
+    for (int i = tid; i < 256; i += kMlpThreads) {
+      sb1[i] = md->b1[i];
+      sb2[i] = md->b2[i];
+    }
+    if (tid < 16) sb3[tid] = md->b3[tid];
+    if (tid < 8) sscale[tid] = md->out_scale[tid];
+  }
+  for (int o = tid; o < TM; o += kMlpThreads) sU[o] = U[o];
+  __syncthreads();
+  for (int i = tid; i < T; i += kMlpThreads) {
+    float h = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float ru = 0.0f;
+#pragma unroll
+      for (int l = 0; l < M; ++l) ru = fmaf(p.R[j * M + l], sU[i * M + l], ru);
+      sRu[i * M + j] = ru;
+      h = fmaf(sU[i * M + j], ru, h);
+    }
+    sHu[i] = 0.5f * h;
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+
+  const uint32_t tmem = tmem_base;
+  const uint32_t tmem_row = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+  const uint32_t sbase = tc::smem_u32(smem);
+  const uint32_t id256 = tc::idesc_bf16_f32(128, 256), id16 = tc::idesc_bf16_f32(128, 16);
+  const Env env = make_env(p, nullptr);
+  const int k = blockIdx.x * kMlpThreads + tid;
+  float Lnu[M * M], R[M * M];
+#pragma unroll
+  for (int a = 0; a < M * M; ++a) {
+    Lnu[a] = p.Lnu[a];
+    R[a] = p.R[a];
+  }
+  float x[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) x[a] = st->x0[a];
+  const uint32_t ctr = st->counter;
+  KahanSum S;
+  uint32_t phase = 0;
+  bool ok = true;
+  float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+
+  for (int i = 0; i < T && ok; ++i) {
+    if ((i & 1) == 0)
+      normals4(static_cast<uint32_t>(i >> 1), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+    float du[M], v[M];
+    {
+      const float pair[2] = {(i & 1) ? eps[2] : eps[0], (i & 1) ? eps[3] : eps[1]};
+      scale_noise<M>(Lnu, pair, du);
+    }
+    float duRdu = 0.0f, uRdu = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      v[j] = sU[i * M + j] + du[j];
+      uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
+      float rd = 0.0f;
+#pragma unroll
+      for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
+      duRdu = fmaf(du[j], rd, duRdu);
+    }
+    const float is_cost = p.is_du * duRdu + uRdu + sHu[i];
+    // features -> X tile row tid
+    {
+      float z[mlp::kIn];
+      mlp::features(x, v, z);
+      uint4 a, b;
+      a.x = pack_bf16(z[0], z[1]);
+      a.y = pack_bf16(z[2], z[3]);
+      a.z = pack_bf16(z[4], z[5]);
+      a.w = pack_bf16(z[6], z[7]);
+      b.x = pack_bf16(z[8], z[9]);
+      b.y = pack_bf16(z[10], z[11]);
+      b.z = pack_bf16(z[12], z[13]);
+      b.w = pack_bf16(z[14], z[15]);
+      *reinterpret_cast<uint4 *>(smem + kSX + tc::kmajor_offset(tid, 0, 128)) = a;
+      *reinterpret_cast<uint4 *>(smem + kSX + tc::kmajor_offset(tid, 8, 128)) = b;
+    }
+    // layer 1
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      tc::mma_bf16(tmem, tc::smem_desc(sbase + kSX, 128 * 16, 128), tc::smem_desc(sbase + kSW1, 256 * 16, 128), id256,
+                   0u);
+      tc::mma_commit(&bar);
+    }
+    bool got = tc::mbar_wait(&bar, phase);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    hidden_epilogue(tmem_row, sb1, smem, tid);
+    // layer 2
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int kk = 0; kk < 16; ++kk)
+        tc::mma_bf16(tmem, tc::smem_desc(sbase + kSH + kk * 2 * 2048, 2048, 128),
+                     tc::smem_desc(sbase + kSW2 + kk * 2 * 4096, 4096, 128), id256, kk > 0 ? 1u : 0u);
+      tc::mma_commit(&bar);
+    }
+    got = tc::mbar_wait(&bar, phase);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    hidden_epilogue(tmem_row, sb2, smem, tid);
+    // layer 3
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int kk = 0; kk < 16; ++kk)
+        tc::mma_bf16(tmem + 256, tc::smem_desc(sbase + kSH + kk * 2 * 2048, 2048, 128),
+                     tc::smem_desc(sbase + kSW3 + kk * 2 * 256, 256, 128), id16, kk > 0 ? 1u : 0u);
+      tc::mma_commit(&bar);
+    }
+    got = tc::mbar_wait(&bar, phase);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    float y[16];
+    tc::tmem_ld8(tmem_row + 256, y);
+    tc::tmem_ld8(tmem_row + 264, y + 8);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] += (y[j] + sb3[j]) * sscale[j];
+    const float dv = x[3] - Car::v_target;
+    S.add(map_bilinear(env, x[0], x[1]) + dv * dv + is_cost);
+  }
+  float Sk;
+  if (ok) {
+    const float dv = x[3] - Car::v_target;
+    S.add(map_bilinear(env, x[0], x[1]) + dv * dv);  // phi(x_T) = q(x_T)
+    Sk = S.s;
+  } else {
+    Sk = INFINITY;
+    if (tid == 0) atomicExch(md->err, 1);
+    tc::mbar_wait(&bar, phase ^ 1u);  // bounded second chance for the MMAs in flight
+  }
+  block_partial<M, kMlpThreads, true>(p, k, ctr, Sk, Lnu, S_out, part_sums + static_cast<size_t>(blockIdx.x) * TM,
+                                      part + blockIdx.x, nullptr, nullptr);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+size_t mlp_rollout_smem_bytes(int T) { return kSU + sizeof(float) * (2 * static_cast<size_t>(T) * 2 + T); }
+
+cudaError_t launch_rollout_mlp(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *part_sums,
+                               BlockPartial *part, cudaStream_t s) {
+  const size_t smem = mlp_rollout_smem_bytes(p.T);
+  const int grid = (p.K + kMlpThreads - 1) / kMlpThreads;
+  k_rollout_mlp<<<grid, kMlpThreads, smem, s>>>(p, st, U, S, part_sums, part);
+  return cudaGetLastError();
+}
+
+cudaError_t prepare_mlp_kernel() {
+  return cudaFuncSetAttribute(k_rollout_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kMlpSmemLimit));
+}
+
+}  // namespace mppi

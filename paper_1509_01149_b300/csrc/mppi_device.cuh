@@ -131,6 +131,18 @@ struct BlockPartial {
   int kstar;     // lowest sample index attaining rho
 };
 
+// Learned-dynamics weights on the device (BF16 tiles in the K-major core-matrix layout
+// the tensor-core kernel copies verbatim into shared memory).
+struct MlpDev {
+  const unsigned char *w1;  // 256 x 16 tile
+  const unsigned char *w2;  // 256 x 256 tile
+  const unsigned char *w3;  // 16 x 256 tile
+  const float *b1, *b2, *b3;
+  float out_scale[8];
+  int *err;                 // set to 1 when a bounded tensor-core wait runs out
+  int precision, pad;
+};
+
 // Results of the last iteration for the debug ABI.
 struct StepDebug {
   double eta;

@@ -69,6 +69,104 @@ __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, in
   return sizeof(float) * (2 * TM + T + 3 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk));
 }
 
+// The block's softmax partial from each thread's path cost Sk_raw (sample k):
+//   rho_b = min_k S~_k (lowest k on ties), w_k = exp(-(S~_k - rho_b)/lambda),
+//   eta_b = sum_k w_k (FP64), part_sums[i*M+j] = sum_k w_k du_{i,j,k} (FP32)
+// with du from shared memory (STORE: sDu [T*M][BLK]) or regenerated (REGEN).
+// Non-finite costs and samples k >= K count as +inf (weight 0).
+template <int M, int BLK, bool REGEN>
+__device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32_t ctr, float Sk_raw, const float *Lnu,
+                                              float *__restrict__ S_out, float *__restrict__ part_sums,
+                                              BlockPartial *__restrict__ part, float *sW, const float *sDu) {
+  constexpr int SPB = 4 / M, NW = BLK / 32;
+  __shared__ float s_min[NW];
+  __shared__ int s_idx[NW];
+  __shared__ double s_eta[NW];
+  __shared__ float s_red[NW][32];
+  const int TM = p.T * M, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool valid = k < p.K;
+  float Sk = Sk_raw;
+  if (!valid || !isfinite(Sk)) Sk = INFINITY;
+  if (valid) S_out[k] = Sk;
+
+  float mv = Sk;
+  int mi = valid ? k : INT_MAX;
+  warp_argmin(mv, mi);
+  if (lane == 0) {
+    s_min[warp] = mv;
+    s_idx[warp] = mi;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float v = lane < NW ? s_min[lane] : INFINITY;
+    int ii = lane < NW ? s_idx[lane] : INT_MAX;
+    warp_argmin(v, ii);
+    if (lane == 0) {
+      s_min[0] = v;
+      s_idx[0] = ii;
+    }
+  }
+  __syncthreads();
+  const float rho_b = s_min[0];
+  const float w = (isfinite(rho_b) && isfinite(Sk)) ? expf(-(Sk - rho_b) * p.inv_lambda) : 0.0f;
+  const double e = warp_sum_d(static_cast<double>(w));
+  if (lane == 0) s_eta[warp] = e;
+
+  if (!REGEN) {
+    sW[tid] = w;
+    __syncthreads();
+    // warp per output, lanes over the block's samples (FP32)
+    for (int o = warp; o < TM; o += NW) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int c = 0; c < BLK / 32; ++c) acc = fmaf(sW[lane + 32 * c], sDu[o * BLK + lane + 32 * c], acc);
+      acc = warp_sum_f(acc);
+      if (lane == 0) part_sums[o] = acc;
+    }
+  } else {
+    const int nb = (TM + 3) >> 2;
+    // regenerate du, weight it, transpose-reduce 32 outputs (8 Philox blocks) at a time
+    for (int g = 0; g < nb; g += 8) {
+      float v[32];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (g + q < nb)
+          normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+#pragma unroll
+        for (int s = 0; s < SPB; ++s) {
+          float du[M];
+          scale_noise<M>(Lnu, eps + s * M, du);
+#pragma unroll
+          for (int j = 0; j < M; ++j) v[q * 4 + s * M + j] = w * du[j];
+        }
+      }
+      const float wsum = transpose_reduce32(v);
+      s_red[warp][lane] = wsum;
+      __syncthreads();
+      if (warp == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) t += s_red[q][lane];
+        const int o = 4 * g + lane;
+        if (o < TM) part_sums[o] = t;
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double eta_b = 0.0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) eta_b += s_eta[q];
+    BlockPartial bp;
+    bp.eta = eta_b;
+    bp.rho = rho_b;
+    bp.kstar = s_idx[0];
+    *part = bp;
+  }
+}
+
 // One block of BLK samples of one controller.
 //   p        controller constants; x0/ctr the state and iteration counter
 //   U        [T][M] nominal controls (global)
@@ -80,14 +178,9 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
                                               const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                               float *__restrict__ part_sums, BlockPartial *__restrict__ part,
                                               float *smem) {
-  constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M, NW = BLK / 32;
+  constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M;
   static_assert(4 % M == 0, "controls per Philox block must divide 4");
-  __shared__ float s_min[NW];
-  __shared__ int s_idx[NW];
-  __shared__ double s_eta[NW];
-  __shared__ float s_red[NW][32];
-
-  const int T = p.T, TM = T * M, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = p.T, TM = T * M, tid = threadIdx.x;
   float *sU = smem;                 // [TM]  nominal controls
   float *sRu = sU + TM;             // [TM]  R u_i
   float *sHu = sRu + TM;            // [T]   1/2 u_i^T R u_i
@@ -114,7 +207,6 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
 
   const Env env = make_env(p, sObs);
   const int k = k0 + tid;
-  const bool valid = k < p.K;
   float Lnu[M * M], R[M * M];
 #pragma unroll
   for (int a = 0; a < M * M; ++a) {
@@ -156,87 +248,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
     }
   }
   S.add(Sys::cost(x, aux, env));  // phi(x_T) = q(x_T)
-
-  float Sk = S.s;
-  if (!valid || !isfinite(Sk)) Sk = INFINITY;
-  if (valid) S_out[k] = Sk;
-
-  // block minimum (lowest index on ties)
-  float mv = Sk;
-  int mi = valid ? k : INT_MAX;
-  warp_argmin(mv, mi);
-  if (lane == 0) {
-    s_min[warp] = mv;
-    s_idx[warp] = mi;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    float v = lane < NW ? s_min[lane] : INFINITY;
-    int ii = lane < NW ? s_idx[lane] : INT_MAX;
-    warp_argmin(v, ii);
-    if (lane == 0) {
-      s_min[0] = v;
-      s_idx[0] = ii;
-    }
-  }
-  __syncthreads();
-  const float rho_b = s_min[0];
-  const float w = (isfinite(rho_b) && isfinite(Sk)) ? expf(-(Sk - rho_b) * p.inv_lambda) : 0.0f;
-  const double e = warp_sum_d(static_cast<double>(w));
-  if (lane == 0) s_eta[warp] = e;
-
-  if (!REGEN) {
-    sW[tid] = w;
-    __syncthreads();
-    // warp per output, lanes over the block's samples (FP32)
-    for (int o = warp; o < TM; o += NW) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int c = 0; c < BLK / 32; ++c) acc = fmaf(sW[lane + 32 * c], sDu[o * BLK + lane + 32 * c], acc);
-      acc = warp_sum_f(acc);
-      if (lane == 0) part_sums[o] = acc;
-    }
-  } else {
-    // regenerate du, weight it, transpose-reduce 32 outputs (8 Philox blocks) at a time
-    for (int g = 0; g < nb; g += 8) {
-      float v[32];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (g + q < nb)
-          normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
-#pragma unroll
-        for (int s = 0; s < SPB; ++s) {
-          float du[M];
-          scale_noise<M>(Lnu, eps + s * M, du);
-#pragma unroll
-          for (int j = 0; j < M; ++j) v[q * 4 + s * M + j] = w * du[j];
-        }
-      }
-      const float wsum = transpose_reduce32(v);
-      s_red[warp][lane] = wsum;
-      __syncthreads();
-      if (warp == 0) {
-        float t = 0.0f;
-#pragma unroll
-        for (int q = 0; q < NW; ++q) t += s_red[q][lane];
-        const int o = 4 * g + lane;
-        if (o < TM) part_sums[o] = t;
-      }
-      __syncthreads();
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double eta_b = 0.0;
-#pragma unroll
-    for (int q = 0; q < NW; ++q) eta_b += s_eta[q];
-    BlockPartial bp;
-    bp.eta = eta_b;
-    bp.rho = rho_b;
-    bp.kstar = s_idx[0];
-    *part = bp;
-  }
+  block_partial<M, BLK, REGEN>(p, k, ctr, S.s, Lnu, S_out, part_sums, part, sW, sDu);
 }
 
 }  // namespace mppi

@@ -694,3 +694,14 @@ def test_mlp_training_reduces_loss_on_analytic_transitions():
         mlp.adam_step(p, g, st, 3e-3)
     l1, _ = mlp.loss_and_grads(p, z, t)
     assert l1 < 0.1 * l0
+
+
+def test_bf16_rounding_matches_the_library_format():
+    """round_bf16 agrees with torch's bfloat16 conversion (round to nearest even)."""
+    import torch
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    a = np.concatenate([rng.normal(size=5000) * 10.0 ** rng.integers(-8, 8, 5000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38, -1e-40]]).astype(np.float32)
+    want = torch.tensor(a).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(mlp.round_bf16(a), want)
