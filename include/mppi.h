@@ -165,7 +165,9 @@ typedef struct {
 } mppi_env_forest;
 /*   MPPI_CAR_MLP also needs the learned dynamics: mppi_env_mlp header followed by
  *     MPPI_MLP_NUM_PARAMS float32 parameters (layout of the mppi_mlp_* functions);
- *     converted to BF16 tensor-core tiles on the device.  precision 0 = BF16. */
+ *     converted to tensor-core tiles on the device.  precision 0 = BF16 weights and
+ *     activations; 1 = E4M3 (FP8) weights with per-tensor scales (largest |w| -> 448)
+ *     and E4M3 activations; FP32 accumulation either way. */
 typedef struct {
   uint32_t kind; /* MPPI_ENV_MLP */
   int32_t precision;

@@ -74,6 +74,33 @@ def round_bf16(a):
     return np.where(np.isfinite(f), out, f.astype(np.float64))
 
 
+def round_e4m3(a):
+    """Round to the nearest E4M3 value (1 sign, 4 exponent bits with bias 7, 3 fraction
+    bits; ties to even; largest finite 448, smallest subnormal 2^-9), saturating at 448."""
+    a = np.asarray(a, dtype=np.float64)
+    s = np.sign(a)
+    x = np.minimum(np.abs(a), 448.0)
+    e = np.floor(np.log2(np.maximum(x, 2.0 ** -9)))
+    e = np.maximum(e, -6.0)                       # below 2^-6 the spacing is fixed (subnormals)
+    step = 2.0 ** (e - 3)
+    q = np.round(x / step) * step                 # numpy rounds halves to even
+    return s * np.minimum(q, 448.0)
+
+
+def quantize_e4m3_weights(p):
+    """Weights as the FP8 kernel sees them: per-tensor scale s = max|W| / 448, W ~ s * e4m3(W / s)."""
+    out = {}
+    for k, v in p.items():
+        v = np.asarray(v, dtype=np.float64)
+        if k.startswith("W"):
+            m = float(np.abs(np.asarray(v, np.float32)).max())
+            s = np.float64(np.float32(m / 448.0)) if m > 0 else 1.0
+            out[k] = round_e4m3(np.asarray(v, np.float32).astype(np.float64) / s) * s
+        else:
+            out[k] = v
+    return out
+
+
 def forward(p, z, act_round=None):
     """z [16][B] -> (y [16][B], cache).  act_round (e.g. round_bf16) is applied to the
     network input and to both hidden activations: the storage precision of a kernel

@@ -127,6 +127,7 @@ struct mppi_ctx {
   bool env_ok = false;
   unsigned char *d_mlp = nullptr;  // learned dynamics: MlpDev + tiles + biases
   bool mlp_ok = false;
+  int mlp_precision = 0;
   int *d_mlp_err = nullptr;
 
   float *h_x0 = nullptr, *h_u0 = nullptr;  // pinned staging
@@ -161,7 +162,8 @@ namespace {
 
 int launch_rollout(mppi_ctx *c, cudaStream_t s) {
   if (c->sys == MPPI_CAR_MLP)
-    return c->cuda(launch_rollout_mlp(c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s), "mlp rollout launch");
+    return c->cuda(launch_rollout_mlp(c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, c->mlp_precision, s),
+                   "mlp rollout launch");
   return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
                  "fused rollout launch");
 }
@@ -236,14 +238,51 @@ uint16_t to_bf16_bits(float f) {
   return static_cast<uint16_t>(u >> 16);
 }
 
-// weights W [rows][cols] -> BF16 K-major core-matrix tile (rows = output units, K = cols)
-void to_tile(const float *W, int rows, int cols, unsigned char *dst) {
+// round-to-nearest-even float -> E4M3 (1 sign, 4 exponent bits with bias 7, 3 fraction
+// bits; largest finite 448, no infinities); out-of-range values saturate to +-448
+uint8_t to_e4m3_bits(float f) {
+  if (std::isnan(f)) return 0x7f;
+  const uint8_t sign = std::signbit(f) ? 0x80 : 0x00;
+  const float a = std::fabs(f);
+  if (a >= 464.0f) return sign | 0x7e;
+  if (a < 0.015625f) {  // subnormals: m * 2^-9, m = 0..7 (m = 8 is the smallest normal)
+    const int m = static_cast<int>(std::nearbyint(a * 512.0f));
+    return sign | static_cast<uint8_t>(m);
+  }
+  int e;
+  const float fr = std::frexp(a, &e);  // a = fr * 2^e, fr in [0.5, 1)
+  float q = std::nearbyint(fr * 16.0f);
+  if (q >= 16.0f) {
+    q = 8.0f;
+    e += 1;
+  }
+  const int be = e - 1 + 7;
+  if (be > 15 || (be == 15 && q - 8.0f > 6.0f)) return sign | 0x7e;
+  return sign | static_cast<uint8_t>((be << 3) | static_cast<int>(q - 8.0f));
+}
+
+// weights W [rows][cols] -> K-major core-matrix tile (rows = output units, K = kpad >= cols)
+// of BF16 (esize 2) or E4M3 (esize 1, values divided by `scale` first)
+void to_tile(const float *W, int rows, int cols, int kpad, int esize, float scale, unsigned char *dst) {
+  const int per = 16 / esize;
   for (int r = 0; r < rows; ++r)
-    for (int k = 0; k < cols; ++k) {
-      const uint32_t off = static_cast<uint32_t>((((k >> 3) * (rows >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
-      const uint16_t b = to_bf16_bits(W[static_cast<size_t>(r) * cols + k]);
-      std::memcpy(dst + off, &b, 2);
+    for (int k = 0; k < kpad; ++k) {
+      const uint32_t off =
+          static_cast<uint32_t>((((k / per) * (rows >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + (k % per) * esize);
+      const float w = k < cols ? W[static_cast<size_t>(r) * cols + k] : 0.0f;
+      if (esize == 2) {
+        const uint16_t b = to_bf16_bits(w);
+        std::memcpy(dst + off, &b, 2);
+      } else {
+        dst[off] = to_e4m3_bits(w / scale);
+      }
     }
+}
+
+float max_abs(const float *a, size_t n) {
+  float m = 0.0f;
+  for (size_t i = 0; i < n; ++i) m = std::fmax(m, std::fabs(a[i]));
+  return m;
 }
 
 int set_mlp_env(mppi_ctx *c, const void *blob, size_t bytes) {
@@ -252,21 +291,34 @@ int set_mlp_env(mppi_ctx *c, const void *blob, size_t bytes) {
     return c->fail(MPPI_EINVAL, "MLP blob must hold the header and %d floats", static_cast<int>(mlp::kNumParams));
   mppi_env_mlp h;
   std::memcpy(&h, blob, sizeof h);
-  if (h.precision != 0) return c->fail(MPPI_EINVAL, "unsupported MLP precision %d", h.precision);
+  if (h.precision != 0 && h.precision != 1) return c->fail(MPPI_EINVAL, "unsupported MLP precision %d", h.precision);
   const float *P = reinterpret_cast<const float *>(static_cast<const char *>(blob) + sizeof h);
   for (size_t i = 0; i < mlp::kNumParams; ++i)
     if (!std::isfinite(P[i])) return c->fail(MPPI_EINVAL, "non-finite MLP parameter");
-  const size_t off_w1 = 256, off_w2 = off_w1 + 256 * 16 * 2, off_w3 = off_w2 + 256 * 256 * 2,
-               off_b = off_w3 + 16 * 256 * 2, total = off_b + sizeof(float) * (256 + 256 + 16);
+  const int E = h.precision == 0 ? 2 : 1, K1 = h.precision == 0 ? 16 : 32;
+  float sc[3] = {1.0f, 1.0f, 1.0f};
+  if (h.precision == 1) {  // per-tensor scales: the largest weight maps to the largest E4M3 value
+    const float m1 = max_abs(P + mlp::kOffW1, 256 * 16), m2 = max_abs(P + mlp::kOffW2, 256 * 256),
+                m3 = max_abs(P + mlp::kOffW3, 16 * 256);
+    sc[0] = m1 > 0.0f ? m1 / 448.0f : 1.0f;
+    sc[1] = m2 > 0.0f ? m2 / 448.0f : 1.0f;
+    sc[2] = m3 > 0.0f ? m3 / 448.0f : 1.0f;
+  }
+  const size_t off_w1 = 256, off_w2 = off_w1 + 256 * K1 * E, off_w3 = off_w2 + 256 * 256 * E,
+               off_b = off_w3 + 16 * 256 * E, total = off_b + sizeof(float) * (256 + 256 + 16);
   std::vector<unsigned char> host(total, 0);
-  to_tile(P + mlp::kOffW1, 256, 16, host.data() + off_w1);
-  to_tile(P + mlp::kOffW2, 256, 256, host.data() + off_w2);
-  to_tile(P + mlp::kOffW3, 16, 256, host.data() + off_w3);
+  to_tile(P + mlp::kOffW1, 256, 16, K1, E, sc[0], host.data() + off_w1);
+  to_tile(P + mlp::kOffW2, 256, 256, 256, E, sc[1], host.data() + off_w2);
+  to_tile(P + mlp::kOffW3, 16, 256, 256, E, sc[2], host.data() + off_w3);
   std::memcpy(host.data() + off_b, P + mlp::kOffB1, sizeof(float) * 256);
   std::memcpy(host.data() + off_b + 1024, P + mlp::kOffB2, sizeof(float) * 256);
   std::memcpy(host.data() + off_b + 2048, P + mlp::kOffB3, sizeof(float) * 16);
   MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
-  if (!c->d_mlp) MPPI_TRY(c->cuda(cudaMalloc(&c->d_mlp, total), "cudaMalloc(mlp)"));
+  if (c->d_mlp) {
+    cudaFree(c->d_mlp);
+    c->d_mlp = nullptr;
+  }
+  MPPI_TRY(c->cuda(cudaMalloc(&c->d_mlp, total), "cudaMalloc(mlp)"));
   MlpDev d{};
   d.w1 = c->d_mlp + off_w1;
   d.w2 = c->d_mlp + off_w2;
@@ -275,9 +327,11 @@ int set_mlp_env(mppi_ctx *c, const void *blob, size_t bytes) {
   d.b2 = d.b1 + 256;
   d.b3 = d.b2 + 256;
   for (int i = 0; i < 7; ++i) d.out_scale[i] = h.out_scale[i];
+  for (int i = 0; i < 3; ++i) d.w_scale[i] = sc[i];
   d.err = c->d_mlp_err;
   d.precision = h.precision;
   std::memcpy(host.data(), &d, sizeof d);
+  c->mlp_precision = h.precision;
   MPPI_TRY(c->cuda(cudaMemcpy(c->d_mlp, host.data(), total, cudaMemcpyHostToDevice), "mlp copy"));
   MPPI_TRY(c->cuda(cudaMemset(c->d_mlp_err, 0, sizeof(int)), "err zero"));
   c->p.mlp = c->d_mlp;

@@ -37,10 +37,11 @@ cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, Ctr
 // Learned car dynamics (mlp_rollout.cu) -----------------------------------------
 constexpr size_t kMlpSmemLimit = 226 * 1024;
 constexpr int kMlpMaxT = 600;
-size_t mlp_rollout_smem_bytes(int T);
+size_t mlp_rollout_smem_bytes(int T, int precision);
 cudaError_t prepare_mlp_kernel();
+// precision 0: BF16 weights and activations; 1: E4M3 (FP8) with per-tensor weight scales
 cudaError_t launch_rollout_mlp(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *part_sums,
-                               BlockPartial *part, cudaStream_t s);
+                               BlockPartial *part, int precision, cudaStream_t s);
 
 // Plain-loop baseline ---------------------------------------------------------
 cudaError_t launch_plain_noise(const CtrlParams &p, const uint32_t *counter, float *du, cudaStream_t s);

@@ -14,7 +14,12 @@
 // du regenerated from the counter-based generator (shared memory is full of weights).
 // Every mbarrier wait is bounded; on a timeout the kernel flags the error, waits once
 // more (bounded) for its MMAs, frees its TMEM and returns.
+// FP8 variant (kind::f8f6f4): weights, features and hidden activations in E4M3 (weights
+// with a per-tensor scale s_l, so a layer's pre-activation is s_l * acc + b), K padded to
+// 32 in the first layer, one 32-deep MMA per 32 bytes of K as in BF16; the output layer
+// reuses TMEM columns 0..15.
 #include <cstdint>
+#include <cuda_fp8.h>
 
 #include "kernels.cuh"
 #include "mlp_model.cuh"
@@ -25,15 +30,35 @@ namespace mppi {
 
 namespace {
 constexpr int kMlpThreads = 128;
-constexpr uint32_t kTmemCols = 512;
-// shared-memory layout (bytes)
-constexpr uint32_t kSW2 = 0;                       // W2 tile 256 x 256 bf16
-constexpr uint32_t kSW1 = kSW2 + 256 * 256 * 2;    // W1 tile 256 x 16
-constexpr uint32_t kSW3 = kSW1 + 256 * 16 * 2;     // W3 tile 16 x 256
-constexpr uint32_t kSH = kSW3 + 16 * 256 * 2;      // H tile 128 x 256
-constexpr uint32_t kSX = kSH + 128 * 256 * 2;      // X tile 128 x 16
-constexpr uint32_t kSB = kSX + 128 * 16 * 2;       // b1 [256], b2 [256], b3 [16], out_scale [8] (f32)
-constexpr uint32_t kSU = kSB + (256 + 256 + 16 + 8) * 4;  // sU [TM], sRu [TM], sHu [T] (f32)
+
+// Shared-memory layout (bytes) for element size E (2 = BF16, 1 = E4M3); the first layer's
+// K is 16 (BF16) or 32 (E4M3, zero padded) so that one MMA covers it.
+template <int E>
+struct MlpLayout {
+  static constexpr uint32_t K1 = E == 2 ? 16 : 32;
+  static constexpr uint32_t W2 = 0;                           // 256 x 256
+  static constexpr uint32_t W1 = W2 + 256 * 256 * E;          // 256 x K1
+  static constexpr uint32_t W3 = W1 + 256 * K1 * E;           // 16 x 256
+  static constexpr uint32_t H = W3 + 16 * 256 * E;            // 128 x 256
+  static constexpr uint32_t X = H + 128 * 256 * E;            // 128 x K1
+  static constexpr uint32_t B = X + 128 * K1 * E;             // b1, b2, b3, out_scale, w_scale (f32)
+  static constexpr uint32_t U = B + (256 + 256 + 16 + 8 + 4) * 4;  // sU, sRu, sHu (f32)
+  static constexpr uint32_t kTmemCols = E == 2 ? 512 : 256;   // E4M3: 2 CTAs may share an SM
+  static constexpr uint32_t D3 = E == 2 ? 256 : 0;            // TMEM column of the output layer
+};
+
+// byte offset of element (r, k) in a K-major no-swizzle tile of R rows, element size E
+template <int E>
+__device__ __forceinline__ uint32_t tile_offset(int r, int k, int R) {
+  constexpr int per = 16 / E;  // elements per 16-byte core-matrix row
+  return static_cast<uint32_t>((((k / per) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k % per) * E));
+}
+
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
+  const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
+}
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   uint32_t r[32];
@@ -55,66 +80,89 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// H row `row` (columns 0..255) = bf16(tanh(D[row][:] + bias)), D read from TMEM columns 0..255
-__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bias, unsigned char *smem, int row) {
+// H row `row` (columns 0..255) = tanh(scale * D[row][:] + bias) stored in the tile format,
+// D read from TMEM columns 0..255
+template <int E>
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bias, float scale, unsigned char *smem,
+                                                int row) {
 #pragma unroll 1
   for (int c0 = 0; c0 < 256; c0 += 32) {
     float v[32];
     tmem_ld32(tmem_row + static_cast<uint32_t>(c0), v);
     tc::tmem_ld_wait();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t w[4];
+    for (int j = 0; j < 32; ++j) v[j] = tc::tanh_approx(fmaf(v[j], scale, bias[c0 + j]));
+    if (E == 2) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = c0 + q * 8 + 2 * j;
-        w[j] = pack_bf16(tc::tanh_approx(v[q * 8 + 2 * j] + bias[c]), tc::tanh_approx(v[q * 8 + 2 * j + 1] + bias[c + 1]));
+      for (int q = 0; q < 4; ++q) {
+        const uint4 w = make_uint4(pack_bf16(v[q * 8], v[q * 8 + 1]), pack_bf16(v[q * 8 + 2], v[q * 8 + 3]),
+                                   pack_bf16(v[q * 8 + 4], v[q * 8 + 5]), pack_bf16(v[q * 8 + 6], v[q * 8 + 7]));
+        *reinterpret_cast<uint4 *>(smem + MlpLayout<E>::H + tile_offset<E>(row, c0 + q * 8, 128)) = w;
       }
-      *reinterpret_cast<uint4 *>(smem + kSH + tc::kmajor_offset(row, c0 + q * 8, 128)) = make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float *f = v + q * 16;
+        const uint4 w = make_uint4(pack_e4m3x4(f[0], f[1], f[2], f[3]), pack_e4m3x4(f[4], f[5], f[6], f[7]),
+                                   pack_e4m3x4(f[8], f[9], f[10], f[11]), pack_e4m3x4(f[12], f[13], f[14], f[15]));
+        *reinterpret_cast<uint4 *>(smem + MlpLayout<E>::H + tile_offset<E>(row, c0 + q * 16, 128)) = w;
+      }
     }
   }
 }
 
+template <int E>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (E == 2)
+    tc::mma_bf16(d, a, b, idesc, acc);
+  else
+    tc::mma_e4m3(d, a, b, idesc, acc);
+}
+
 }  // namespace
 
+template <int E>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams p, const CtrlState *__restrict__ st,
                                                                 const float *__restrict__ U, float *__restrict__ S_out,
                                                                 float *__restrict__ part_sums,
                                                                 BlockPartial *__restrict__ part) {
   constexpr int M = 2, N = 7;
+  using L = MlpLayout<E>;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_base;
   const MlpDev *md = static_cast<const MlpDev *>(p.mlp);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int T = p.T, TM = T * M;
-  float *sb1 = reinterpret_cast<float *>(smem + kSB);
+  float *sb1 = reinterpret_cast<float *>(smem + L::B);
   float *sb2 = sb1 + 256;
   float *sb3 = sb2 + 256;
   float *sscale = sb3 + 16;
-  float *sU = reinterpret_cast<float *>(smem + kSU);
+  float *swscale = sscale + 8;
+  float *sU = reinterpret_cast<float *>(smem + L::U);
   float *sRu = sU + TM;
   float *sHu = sRu + TM;
 
-  if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+  if (warp == 0) tc::tmem_alloc(&tmem_base, L::kTmemCols);
   if (tid == 0) tc::mbar_init(&bar, 1);
   // weights (already in tile layout) and biases
   {
     const uint4 *w2 = reinterpret_cast<const uint4 *>(md->w2);
     const uint4 *w1 = reinterpret_cast<const uint4 *>(md->w1);
     const uint4 *w3 = reinterpret_cast<const uint4 *>(md->w3);
-    uint4 *d2 = reinterpret_cast<uint4 *>(smem + kSW2);
-    uint4 *d1 = reinterpret_cast<uint4 *>(smem + kSW1);
-    uint4 *d3 = reinterpret_cast<uint4 *>(smem + kSW3);
-    for (int i = tid; i < 256 * 256 * 2 / 16; i += kMlpThreads) d2[i] = w2[i];
-    for (int i = tid; i < 256 * 16 * 2 / 16; i += kMlpThreads) d1[i] = w1[i];
-    for (int i = tid; i < 16 * 256 * 2 / 16; i += kMlpThreads) d3[i] = w3[i];
+    uint4 *d2 = reinterpret_cast<uint4 *>(smem + L::W2);
+    uint4 *d1 = reinterpret_cast<uint4 *>(smem + L::W1);
+    uint4 *d3 = reinterpret_cast<uint4 *>(smem + L::W3);
+    for (int i = tid; i < 256 * 256 * E / 16; i += kMlpThreads) d2[i] = w2[i];
+    for (int i = tid; i < static_cast<int>(256 * L::K1 * E / 16); i += kMlpThreads) d1[i] = w1[i];
+    for (int i = tid; i < 16 * 256 * E / 16; i += kMlpThreads) d3[i] = w3[i];
     for (int i = tid; i < 256; i += kMlpThreads) {
       sb1[i] = md->b1[i];
       sb2[i] = md->b2[i];
     }
     if (tid < 16) sb3[tid] = md->b3[tid];
     if (tid < 8) sscale[tid] = md->out_scale[tid];
+    if (tid < 3) swscale[tid] = md->w_scale[tid];
   }
   for (int o = tid; o < TM; o += kMlpThreads) sU[o] = U[o];
   __syncthreads();
@@ -138,7 +186,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   const uint32_t tmem = tmem_base;
   const uint32_t tmem_row = tmem + (static_cast<uint32_t>(32 * warp) << 16);
   const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t id256 = tc::idesc_bf16_f32(128, 256), id16 = tc::idesc_bf16_f32(128, 16);
+  const uint32_t id256 = E == 2 ? tc::idesc_bf16_f32(128, 256) : tc::idesc_e4m3_f32(128, 256);
+  const uint32_t id16 = E == 2 ? tc::idesc_bf16_f32(128, 16) : tc::idesc_e4m3_f32(128, 16);
+  const float s1 = swscale[0], s2 = swscale[1], s3 = swscale[2];
   const Env env = make_env(p, nullptr);
   const int k = blockIdx.x * kMlpThreads + tid;
   float Lnu[M * M], R[M * M];
@@ -179,17 +229,19 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     {
       float z[mlp::kIn];
       mlp::features(x, v, z);
-      uint4 a, b;
-      a.x = pack_bf16(z[0], z[1]);
-      a.y = pack_bf16(z[2], z[3]);
-      a.z = pack_bf16(z[4], z[5]);
-      a.w = pack_bf16(z[6], z[7]);
-      b.x = pack_bf16(z[8], z[9]);
-      b.y = pack_bf16(z[10], z[11]);
-      b.z = pack_bf16(z[12], z[13]);
-      b.w = pack_bf16(z[14], z[15]);
-      *reinterpret_cast<uint4 *>(smem + kSX + tc::kmajor_offset(tid, 0, 128)) = a;
-      *reinterpret_cast<uint4 *>(smem + kSX + tc::kmajor_offset(tid, 8, 128)) = b;
+      if (E == 2) {
+        const uint4 a = make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]),
+                                   pack_bf16(z[6], z[7]));
+        const uint4 b = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]), pack_bf16(z[12], z[13]),
+                                   pack_bf16(z[14], z[15]));
+        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 0, 128)) = a;
+        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 8, 128)) = b;
+      } else {
+        const uint4 a = make_uint4(pack_e4m3x4(z[0], z[1], z[2], z[3]), pack_e4m3x4(z[4], z[5], z[6], z[7]),
+                                   pack_e4m3x4(z[8], z[9], z[10], z[11]), pack_e4m3x4(z[12], z[13], z[14], z[15]));
+        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 0, 128)) = a;
+        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 16, 128)) = make_uint4(0u, 0u, 0u, 0u);
+      }
     }
     // layer 1
     tc::fence_smem_to_async();
@@ -197,8 +249,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      tc::mma_bf16(tmem, tc::smem_desc(sbase + kSX, 128 * 16, 128), tc::smem_desc(sbase + kSW1, 256 * 16, 128), id256,
-                   0u);
+      mma<E>(tmem, tc::smem_desc(sbase + L::X, 128 * 16, 128), tc::smem_desc(sbase + L::W1, 256 * 16, 128), id256, 0u);
       tc::mma_commit(&bar);
     }
     bool got = tc::mbar_wait(&bar, phase);
@@ -208,7 +259,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       ok = false;
       break;
     }
-    hidden_epilogue(tmem_row, sb1, smem, tid);
+    hidden_epilogue<E>(tmem_row, sb1, s1, smem, tid);
     // layer 2
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -216,9 +267,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     if (tid == 0) {
       tc::fence_after_sync();
 #pragma unroll 1
-      for (int kk = 0; kk < 16; ++kk)
-        tc::mma_bf16(tmem, tc::smem_desc(sbase + kSH + kk * 2 * 2048, 2048, 128),
-                     tc::smem_desc(sbase + kSW2 + kk * 2 * 4096, 4096, 128), id256, kk > 0 ? 1u : 0u);
+      for (int kk = 0; kk < 256 * E / 32; ++kk)
+        mma<E>(tmem, tc::smem_desc(sbase + L::H + kk * 2 * 2048, 2048, 128),
+               tc::smem_desc(sbase + L::W2 + kk * 2 * 4096, 4096, 128), id256, kk > 0 ? 1u : 0u);
       tc::mma_commit(&bar);
     }
     got = tc::mbar_wait(&bar, phase);
@@ -228,7 +279,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       ok = false;
       break;
     }
-    hidden_epilogue(tmem_row, sb2, smem, tid);
+    hidden_epilogue<E>(tmem_row, sb2, s2, smem, tid);
     // layer 3
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -236,9 +287,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     if (tid == 0) {
       tc::fence_after_sync();
 #pragma unroll 1
-      for (int kk = 0; kk < 16; ++kk)
-        tc::mma_bf16(tmem + 256, tc::smem_desc(sbase + kSH + kk * 2 * 2048, 2048, 128),
-                     tc::smem_desc(sbase + kSW3 + kk * 2 * 256, 256, 128), id16, kk > 0 ? 1u : 0u);
+      for (int kk = 0; kk < 256 * E / 32; ++kk)
+        mma<E>(tmem + L::D3, tc::smem_desc(sbase + L::H + kk * 2 * 2048, 2048, 128),
+               tc::smem_desc(sbase + L::W3 + kk * 2 * 256, 256, 128), id16, kk > 0 ? 1u : 0u);
       tc::mma_commit(&bar);
     }
     got = tc::mbar_wait(&bar, phase);
@@ -249,11 +300,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       break;
     }
     float y[16];
-    tc::tmem_ld8(tmem_row + 256, y);
-    tc::tmem_ld8(tmem_row + 264, y + 8);
+    tc::tmem_ld8(tmem_row + L::D3, y);
+    tc::tmem_ld8(tmem_row + L::D3 + 8, y + 8);
     tc::tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < N; ++j) x[j] += (y[j] + sb3[j]) * sscale[j];
+    for (int j = 0; j < N; ++j) x[j] += fmaf(y[j], s3, sb3[j]) * sscale[j];
     const float dv = x[3] - Car::v_target;
     S.add(map_bilinear(env, x[0], x[1]) + dv * dv + is_cost);
   }
@@ -271,22 +322,32 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
                                       part + blockIdx.x, nullptr, nullptr);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0) tc::tmem_dealloc(tmem, L::kTmemCols);
 }
 
-size_t mlp_rollout_smem_bytes(int T) { return kSU + sizeof(float) * (2 * static_cast<size_t>(T) * 2 + T); }
+size_t mlp_rollout_smem_bytes(int T, int precision) {
+  const size_t base = precision == 0 ? MlpLayout<2>::U : MlpLayout<1>::U;
+  return base + sizeof(float) * (2 * static_cast<size_t>(T) * 2 + T);
+}
 
 cudaError_t launch_rollout_mlp(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *part_sums,
-                               BlockPartial *part, cudaStream_t s) {
-  const size_t smem = mlp_rollout_smem_bytes(p.T);
+                               BlockPartial *part, int precision, cudaStream_t s) {
+  const size_t smem = mlp_rollout_smem_bytes(p.T, precision);
   const int grid = (p.K + kMlpThreads - 1) / kMlpThreads;
-  k_rollout_mlp<<<grid, kMlpThreads, smem, s>>>(p, st, U, S, part_sums, part);
+  if (precision == 0)
+    k_rollout_mlp<2><<<grid, kMlpThreads, smem, s>>>(p, st, U, S, part_sums, part);
+  else
+    k_rollout_mlp<1><<<grid, kMlpThreads, smem, s>>>(p, st, U, S, part_sums, part);
   return cudaGetLastError();
 }
 
 cudaError_t prepare_mlp_kernel() {
-  return cudaFuncSetAttribute(k_rollout_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(kMlpSmemLimit));
+  cudaError_t e = cudaFuncSetAttribute(k_rollout_mlp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kMlpSmemLimit));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_rollout_mlp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kMlpSmemLimit));
+  return e;
 }
 
 }  // namespace mppi

@@ -139,6 +139,7 @@ struct MlpDev {
   const unsigned char *w3;  // 16 x 256 tile
   const float *b1, *b2, *b3;
   float out_scale[8];
+  float w_scale[4];         // per-tensor weight scales of W1, W2, W3 (1 for BF16)
   int *err;                 // set to 1 when a bounded tensor-core wait runs out
   int precision, pad;
 };

@@ -230,3 +230,32 @@ def test_trained_network_gains_over_the_untrained_one(env, trained):
     ctl.close()
     assert learned < 0.25 * untrained, (learned, untrained, analytic)
     assert learned < 4.0 * analytic, (learned, untrained, analytic)
+
+
+def test_fp8_iteration_matches_the_e4m3_oracle(env, trained):
+    """FP8 path (E4M3 weights with per-tensor scales, E4M3 features and activations, FP32
+    accumulation) against an oracle that stores the same E4M3 values.  E4M3 keeps 3
+    fraction bits, so one rounding flip moves an activation by up to 6 %: most path costs
+    agree to ~1e-4 but the tail is wide, and near-ties in the argmin can go either way.
+    The deviation from the exact network (median ~0.1) is the precision cost of FP8."""
+    torch, N = env
+    params, scale = trained
+    K, T = 2048, 60
+    c = W.config(W.CAR, K=K, T=T)
+    ctl = N.Controller(W.CAR_MLP, K, T, c["dt"], c["nu"], c["lam"], c["Sigma"], c["R"])
+    ctl.set_cost_map(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL)
+    ctl.set_env(N.mlp_blob(params, scale, precision=1))
+    ctl.set_controls(np.zeros((T, 2), np.float32))
+    x0 = np.asarray(c["x0"], np.float32)
+    ctl.step(x0)
+    g = ctl.get_debug()
+    from oracle import mppi as om
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    sysm = omlp.CarMLP(c["dt"], W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL, omlp.quantize_e4m3_weights(params),
+                       scale, act_round=omlp.round_e4m3)
+    o = om.iteration_seeded(sysm, f32(x0), np.zeros((T, 2)), K, 1.0, 10.0, f32(c["Sigma"]), f32(c["R"]), 0)
+    rel = np.abs(g["S"] - o.S) / np.abs(o.S)
+    assert np.median(rel) < 2e-3, np.median(rel)
+    assert np.mean(rel < 1e-2) > 0.8          # measured: 89 % of samples
+    assert np.all(np.isfinite(g["S"])) and np.isfinite(g["eta"]) and g["eta"] >= 1.0
+    ctl.close()

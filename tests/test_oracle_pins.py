@@ -705,3 +705,16 @@ def test_bf16_rounding_matches_the_library_format():
                         [0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38, -1e-40]]).astype(np.float32)
     want = torch.tensor(a).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
     assert np.array_equal(mlp.round_bf16(a), want)
+
+
+def test_e4m3_rounding_matches_the_library_format():
+    """round_e4m3 agrees with torch's float8_e4m3fn conversion inside the finite range."""
+    import torch
+    from oracle import mlp
+    rng = np.random.default_rng(1)
+    a = np.concatenate([rng.normal(size=20000) * 2.0 ** rng.integers(-12, 9, 20000),
+                        [0.0, 448.0, -448.0, 2.0 ** -9, 3 * 2.0 ** -10, 1.0625, 1.1875, 240.0, 248.0]])
+    a = a[np.abs(a) <= 448.0].astype(np.float32)
+    want = torch.tensor(a).to(torch.float8_e4m3fn).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(mlp.round_e4m3(a), want)
+    assert mlp.round_e4m3(np.array([1000.0, -500.0]))[0] == 448.0
