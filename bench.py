@@ -66,6 +66,8 @@ def parse():
                     help="concurrency levels of the serving measurement ('' to skip)")
     ap.add_argument("--serving-ticks", type=int, default=30)
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-dynamics measurement")
+    ap.add_argument("--learned-only", action="store_true")
     return ap.parse_args()
 
 
@@ -235,6 +237,89 @@ def run_serving(levels, n_ticks, seed=0):
     return out
 
 
+def run_learned(n_train=10_000_000, n_test=100_000, steps=6000, batch=8192):
+    """Learned car dynamics: train on n_train analytic transitions (the GPU's analytic step
+    generates the targets), test on n_test held-out ones; one-step and 100-step errors
+    against the analytic model (the judge); MPPI rollout throughput with the network in
+    BF16 and in FP8 at K=16384, T=100."""
+    import torch
+
+    from paper_1509_01149_b300 import _native as N
+    out = {"n_train": n_train, "n_test": n_test, "train_steps": steps, "batch": batch}
+    xs, us = W.car_transition_inputs(101, n_train)
+    dx, du = torch.tensor(xs).cuda(), torch.tensor(us).cuda()
+    del xs, us
+    net = N.MLP(3)
+    net.set_data(dx.data_ptr(), du.data_ptr(), n_train, 0.02)
+    del dx, du
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    net.train(steps * 2 // 3, batch, 2e-3, seed=7)
+    net.train(steps - steps * 2 // 3, batch, 5e-4, seed=8)
+    torch.cuda.synchronize()
+    dt_train = time.perf_counter() - t0
+    fl = 3 * 2 * 73728 * batch * steps          # forward + backward of the padded network
+    out.update(train_s=dt_train, train_samples_per_s=batch * steps / dt_train, train_tflops=fl / dt_train / 1e12)
+    params, scale = net.get_params()
+    # held-out one-step error (normalised by the per-state increment scale)
+    xt, ut = W.car_transition_inputs(202, n_test)
+    dxt, dut = torch.tensor(xt).cuda(), torch.tensor(ut).cuda()
+    pred, true = torch.empty_like(dxt), torch.empty_like(dxt)
+    net.predict(dxt.data_ptr(), dut.data_ptr(), n_test, pred.data_ptr())
+    N.mppi_car_step(dxt.data_ptr(), dut.data_ptr(), n_test, 0.02, true.data_ptr())
+    torch.cuda.synchronize()
+    sc = torch.tensor(scale).cuda()
+    one = (((pred - true) / sc) ** 2).mean(0).sqrt().cpu().numpy()
+    out["one_step_rms_over_increment_scale"] = [round(float(v), 5) for v in one]
+    # 100-step open-loop error: both models from the same 4096 states with the same controls
+    n100 = 4096
+    xa = dxt[:n100].clone()
+    xb = dxt[:n100].clone()
+    g = torch.Generator(device="cuda").manual_seed(3)
+    sig = torch.tensor([0.3 ** 0.5, 0.35 ** 0.5], device="cuda")
+    tmp = torch.empty_like(xa)
+    for _ in range(100):
+        u = (torch.rand(n100, 2, device="cuda", generator=g) * 2 - 1) * 3 * sig
+        net.predict(xa.data_ptr(), u.data_ptr(), n100, tmp.data_ptr())
+        xa.copy_(tmp)
+        N.mppi_car_step(xb.data_ptr(), u.data_ptr(), n100, 0.02, tmp.data_ptr())
+        torch.cuda.synchronize()
+        xb.copy_(tmp)
+    pos = (xa[:, :2] - xb[:, :2]).norm(dim=1)
+    out["hundred_step_position_error_m"] = {"median": float(pos.median()), "p90": float(pos.quantile(0.9))}
+    out["hundred_step_speed_error_mps"] = float((xa[:, 3] - xb[:, 3]).abs().median())
+    net.close()
+    # MPPI with the learned dynamics, BF16 and FP8
+    cfg = W.config(W.CAR, K=K_SAMPLES, T=T_STEPS, nu=NU)
+    for prec, name in ((0, "bf16"), (1, "fp8")):
+        c = N.Controller(W.CAR_MLP, K_SAMPLES, T_STEPS, cfg["dt"], cfg["nu"], cfg["lam"], cfg["Sigma"], cfg["R"])
+        c.set_cost_map(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL)
+        c.set_env(N.mlp_blob(params, scale, prec))
+        s = torch.cuda.Stream()
+        c.set_stream(s.cuda_stream)
+        dx0 = torch.tensor(np.asarray(cfg["x0"], np.float32)).cuda()
+        for _ in range(3):
+            c.step_async(dx0.data_ptr(), None)
+            c.shift()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+        with torch.cuda.stream(s):
+            for e0, e1 in evs:
+                e0.record(s)
+                c.rollout_async(dx0.data_ptr())
+                e1.record(s)
+                c.update_async(None)
+                c.shift()
+        torch.cuda.synchronize()
+        ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+        tf = 2 * 73728 * K_SAMPLES * T_STEPS / (ms * 1e-3) / 1e12
+        peak = 1738.9 * (2 if prec == 1 else 1)       # measured BF16 burst peak; FP8 at the nominal 2x ratio
+        out[f"mppi_rollout_{name}"] = {"ms": ms, "rollout_steps_per_s": K_SAMPLES * T_STEPS / (ms * 1e-3),
+                                       "tensor_tflops": tf, "frac_of_peak": tf / peak,
+                                       "peak_basis": "measured bf16 burst" + (" x2 (fp8 nominal ratio)" if prec else "")}
+        c.close()
+    return out
+
+
 def load_traffic(kernel_tag: str):
     """DRAM traffic per launch from a committed ncu summary, if it was taken on the
     current kernel sources (same source hash); else None."""
@@ -260,6 +345,9 @@ def run_ours(args, rank, world, local_rank):
     levels = [int(v) for v in args.serving.split(",") if v.strip()]
     if args.serving_only:
         print(json.dumps({"serving": run_serving(levels, args.serving_ticks)}), flush=True)
+        return
+    if args.learned_only:
+        print(json.dumps({"learned": run_learned()}), flush=True)
         return
     dist = None
     if world > 1:
@@ -359,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
     pctrl.close()
 
     serving_res = run_serving(levels, args.serving_ticks, seed=rank) if levels else None
+    learned_res = None if args.no_learned else run_learned()
 
     if rank != 0:
         if dist is not None:
@@ -409,6 +498,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "cpu_baseline": cpu,
         "serving": serving_res,
+        "learned": learned_res,
         "source_hash": source_hash(),
     }
     print(json.dumps(line), flush=True)

@@ -325,6 +325,9 @@ int mppi_mlp_grad(mppi_mlp *mlp, const void *d_X, const float *d_T, int B, float
 /* One learned step for n device (state [n][7], control [n][2]) pairs into d_next [n][7]. */
 int mppi_mlp_predict(mppi_mlp *mlp, const float *d_states, const float *d_controls, int n, float *d_next);
 const char *mppi_mlp_last_error(mppi_mlp *mlp);
+/* The analytic car step (the learned model's fallback and judge): d_next [n][7] from
+ * device (state [n][7], control [n][2]) pairs, enqueued on `stream` (NULL = legacy). */
+int mppi_car_step(const float *d_states, const float *d_controls, int n, float dt, float *d_next, void *stream);
 
 /* Check hook for the tensor-core GEMM used by the learned-dynamics training step:
  * C[m*ldc + n] = sum_k A[m*sam + k*sak] * B[k*sbk + n*sbn] on device buffers (A, B BF16,

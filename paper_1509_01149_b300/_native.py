@@ -89,6 +89,7 @@ SIGNATURES = [
     ("mppi_mlp_grad", C.c_int, [_P, _P, _P, C.c_int, _FP, C.POINTER(C.c_double)]),
     ("mppi_mlp_predict", C.c_int, [_P, _P, _P, C.c_int, _P]),
     ("mppi_mlp_last_error", C.c_char_p, [_P]),
+    ("mppi_car_step", C.c_int, [_P, _P, C.c_int, C.c_float, _P, _P]),
     ("mppi_last_error", C.c_char_p, [_P]),
     ("mppi_version", C.c_char_p, []),
 ]
@@ -474,3 +475,11 @@ class MLP:
 
     def predict(self, d_states: int, d_controls: int, n: int, d_next: int):
         self._chk(lib.mppi_mlp_predict(self._h, C.c_void_p(d_states), C.c_void_p(d_controls), n, C.c_void_p(d_next)))
+
+
+def mppi_car_step(d_states: int, d_controls: int, n: int, dt: float, d_next: int, stream: int = 0):
+    """The analytic car step on the device (the learned model's fallback and judge)."""
+    rc = lib.mppi_car_step(C.c_void_p(d_states), C.c_void_p(d_controls), n, dt, C.c_void_p(d_next),
+                           C.c_void_p(stream))
+    if rc != MPPI_OK:
+        raise MppiError(rc, "mppi_car_step failed")

@@ -180,6 +180,24 @@ __global__ void k_apply(const float *__restrict__ xs, const float *__restrict__ 
   xn[idx] = xs[idx] + Y[static_cast<size_t>(i) * kOut + j] * out_scale[j];
 }
 
+// the analytic car step (the learned model's fallback and judge)
+__global__ void k_analytic_step(const float *__restrict__ xs, const float *__restrict__ us, int n, float dt,
+                                float *__restrict__ xn) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float y[kState], u[kCtl];
+#pragma unroll
+  for (int j = 0; j < kState; ++j) y[j] = xs[static_cast<size_t>(i) * kState + j];
+  u[0] = us[static_cast<size_t>(i) * kCtl];
+  u[1] = us[static_cast<size_t>(i) * kCtl + 1];
+  Car::Aux aux;
+  Env env{};
+  Car::init(y, aux, env);
+  Car::step(y, u, aux, env, dt);
+#pragma unroll
+  for (int j = 0; j < kState; ++j) xn[static_cast<size_t>(i) * kState + j] = y[j];
+}
+
 __global__ void k_features(const float *__restrict__ xs, const float *__restrict__ us, int n,
                            __nv_bfloat16 *__restrict__ Xf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -537,6 +555,14 @@ int mppi_mlp_predict(mppi_mlp *q, const float *d_states, const float *d_controls
   mlp::k_apply<<<(n * kState + 255) / 256, 256, 0, q->stream>>>(d_states, q->Y, q->out_scale, n, d_next);
   MLP_TRY(q->cuda(cudaGetLastError(), "apply"));
   return check_err(q);
+}
+
+int mppi_car_step(const float *d_states, const float *d_controls, int n, float dt, float *d_next, void *stream) {
+  if (!d_states || !d_controls || !d_next || n < 1 || !(dt > 0.0f)) return MPPI_EINVAL;
+  mlp::k_analytic_step<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_states, d_controls, n, dt,
+                                                                                         d_next);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? MPPI_OK : MPPI_ECUDA;
 }
 
 }  // extern "C"
