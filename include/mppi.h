@@ -115,6 +115,12 @@ int mppi_step_async(mppi_ctx *ctx, const float *d_state, float *d_u0_out);
 int mppi_rollout_async(mppi_ctx *ctx, const float *d_state);
 int mppi_update_async(mppi_ctx *ctx, float *d_u0_out);
 
+/* One receding-horizon iteration on device buffers: mppi_step_async followed by
+ * mppi_shift, launched as one CUDA graph (captured on the first call, and again when
+ * d_state / d_u0_out or the ctx configuration change).  d_u0_out may be NULL.
+ * Asynchronous on the ctx stream (the legacy stream runs the three launches directly). */
+int mppi_iterate_async(mppi_ctx *ctx, const float *d_state, float *d_u0_out);
+
 /* Shift (Algorithm 1): u_i <- u_{i+1}, u_{T-1} <- u_init, iteration counter += 1.
  * Asynchronous on the ctx stream. */
 int mppi_shift(mppi_ctx *ctx);

@@ -50,6 +50,7 @@ SIGNATURES = [
     ("mppi_step_async", C.c_int, [_P, _P, _P]),
     ("mppi_rollout_async", C.c_int, [_P, _P]),
     ("mppi_update_async", C.c_int, [_P, _P]),
+    ("mppi_iterate_async", C.c_int, [_P, _P, _P]),
     ("mppi_shift", C.c_int, [_P]),
     ("mppi_set_seed", C.c_int, [_P, C.c_uint64]),
     ("mppi_set_controller_id", C.c_int, [_P, C.c_uint32]),
@@ -231,6 +232,11 @@ class Controller:
 
     rollout_async = mppi_rollout_async
     update_async = mppi_update_async
+
+    def mppi_iterate_async(self, d_state: int, d_u0_out: int | None = None):
+        self._chk(lib.mppi_iterate_async(self._h, C.c_void_p(d_state), C.c_void_p(d_u0_out or 0)))
+
+    iterate_async = mppi_iterate_async
 
     def mppi_shift(self):
         self._chk(lib.mppi_shift(self._h))

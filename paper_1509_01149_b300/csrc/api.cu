@@ -134,6 +134,10 @@ struct mppi_ctx {
 
   cudaGraphExec_t graph = nullptr;
   bool graph_dirty = true;
+  cudaGraphExec_t iter_graph = nullptr;  // mppi_iterate_async: rollout -> merge -> shift
+  bool iter_graph_dirty = true;
+  const float *iter_x0 = nullptr;
+  float *iter_u0 = nullptr;
 
   int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -160,18 +164,22 @@ struct mppi_ctx {
 
 namespace {
 
-int launch_rollout(mppi_ctx *c, cudaStream_t s) {
+int launch_rollout(mppi_ctx *c, const float *x0, cudaStream_t s) {
   if (c->sys == MPPI_CAR_MLP)
-    return c->cuda(launch_rollout_mlp(c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, c->mlp_precision, s),
+    return c->cuda(launch_rollout_mlp(c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, c->mlp_precision, s),
                    "mlp rollout launch");
-  return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
+  return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
                  "fused rollout launch");
 }
 
-int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
-  MPPI_TRY(launch_rollout(c, s));
-  return c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->d_u0, c->d_dU, c->d_dbg, s),
+int launch_update(mppi_ctx *c, float *u0_out, cudaStream_t s) {
+  return c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU, c->d_dbg, s),
                  "merge launch");
+}
+
+int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
+  MPPI_TRY(launch_rollout(c, c->d_st->x0, s));
+  return launch_update(c, c->d_u0, s);
 }
 
 int ensure_noise_buffer(mppi_ctx *c) {
@@ -336,7 +344,7 @@ int set_mlp_env(mppi_ctx *c, const void *blob, size_t bytes) {
   MPPI_TRY(c->cuda(cudaMemset(c->d_mlp_err, 0, sizeof(int)), "err zero"));
   c->p.mlp = c->d_mlp;
   c->mlp_ok = true;
-  c->graph_dirty = true;
+  c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
 
@@ -465,6 +473,7 @@ int mppi_destroy(mppi_ctx *c) {
   if (!c) return MPPI_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->d_du) cudaFree(c->d_du);
   if (c->d_env) cudaFree(c->d_env);
@@ -482,7 +491,7 @@ int mppi_set_stream(mppi_ctx *c, void *stream) {
   if (c->own_stream) cudaStreamDestroy(c->stream);
   c->own_stream = false;
   c->stream = static_cast<cudaStream_t>(stream);
-  c->graph_dirty = true;
+  c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
 
@@ -497,14 +506,14 @@ int mppi_set_seed(mppi_ctx *c, uint64_t seed) {
   c->seed = seed;
   c->p.key_lo = static_cast<uint32_t>(seed & 0xffffffffu);
   c->p.key_hi = static_cast<uint32_t>(seed >> 32);
-  c->graph_dirty = true;
+  c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
 
 int mppi_set_controller_id(mppi_ctx *c, uint32_t gid) {
   if (!c) return MPPI_EINVAL;
   c->p.gid = gid;
-  c->graph_dirty = true;
+  c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
 
@@ -608,7 +617,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   c->blk = c->sys == MPPI_CAR_MLP ? kFusedBlockRegen : fused_block_size(c->p);
   c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
   c->env_ok = true;
-  c->graph_dirty = true;
+  c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
 
@@ -642,35 +651,64 @@ int mppi_step(mppi_ctx *c, const float *state, float *u0_out) {
 int mppi_rollout_async(mppi_ctx *c, const float *d_state) {
   if (!c || !d_state) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
-  MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_st->x0, d_state, sizeof(float) * c->n, cudaMemcpyDeviceToDevice, c->stream),
-                   "x0 copy"));
   if (c->impl == MPPI_IMPL_PLAIN) {
+    MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_st->x0, d_state, sizeof(float) * c->n, cudaMemcpyDeviceToDevice, c->stream),
+                     "x0 copy"));
     MPPI_TRY(ensure_noise_buffer(c));
     MPPI_TRY(c->cuda(launch_plain_noise(c->p, &c->d_st->counter, c->d_du, c->stream), "plain noise"));
     return c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->d_U, c->d_du, c->d_S, c->stream), "plain rollout");
   }
-  return launch_rollout(c, c->stream);
+  return launch_rollout(c, d_state, c->stream);  // the kernel reads the caller's state directly
 }
 
 int mppi_update_async(mppi_ctx *c, float *d_u0_out) {
   if (!c) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
-  if (c->impl == MPPI_IMPL_PLAIN)
+  if (c->impl == MPPI_IMPL_PLAIN) {
     MPPI_TRY(c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, c->stream),
                      "plain reduce/update"));
-  else
-    MPPI_TRY(c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->d_u0, c->d_dU, c->d_dbg,
-                                         c->stream),
-                     "merge launch"));
-  if (d_u0_out)
-    MPPI_TRY(c->cuda(cudaMemcpyAsync(d_u0_out, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToDevice, c->stream),
-                     "u0 copy"));
-  return MPPI_OK;
+    if (d_u0_out)
+      MPPI_TRY(c->cuda(cudaMemcpyAsync(d_u0_out, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToDevice, c->stream),
+                       "u0 copy"));
+    return MPPI_OK;
+  }
+  return launch_update(c, d_u0_out ? d_u0_out : c->d_u0, c->stream);  // u0 written in place
 }
 
 int mppi_step_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
   MPPI_TRY(mppi_rollout_async(c, d_state));
   return mppi_update_async(c, d_u0_out);
+}
+
+int mppi_iterate_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
+  if (!c || !d_state) return MPPI_EINVAL;
+  MPPI_TRY(check_ready(c));
+  if (c->impl == MPPI_IMPL_PLAIN || c->stream == nullptr) {
+    MPPI_TRY(mppi_step_async(c, d_state, d_u0_out));
+    return c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+  }
+  float *u0 = d_u0_out ? d_u0_out : c->d_u0;
+  if (c->iter_graph_dirty || c->iter_graph == nullptr || c->iter_x0 != d_state || c->iter_u0 != u0) {
+    if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
+    c->iter_graph = nullptr;
+    cudaGraph_t g = nullptr;
+    MPPI_TRY(c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
+    int rc = launch_rollout(c, d_state, c->stream);
+    if (rc == MPPI_OK) rc = launch_update(c, u0, c->stream);
+    if (rc == MPPI_OK) rc = c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+    const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
+    if (rc != MPPI_OK || rc_end != MPPI_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc != MPPI_OK ? rc : rc_end;
+    }
+    rc = c->cuda(cudaGraphInstantiate(&c->iter_graph, g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    MPPI_TRY(rc);
+    c->iter_x0 = d_state;
+    c->iter_u0 = u0;
+    c->iter_graph_dirty = false;
+  }
+  return c->cuda(cudaGraphLaunch(c->iter_graph, c->stream), "graph launch");
 }
 
 int mppi_shift(mppi_ctx *c) {

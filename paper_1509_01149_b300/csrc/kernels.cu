@@ -27,12 +27,12 @@ namespace mppi {
 // fused rollout: one block of BLK samples per CTA (body in rollout_body.cuh)
 // ---------------------------------------------------------------------------
 template <class Sys, int BLK, bool REGEN>
-__global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const CtrlState *__restrict__ st,
-                                                       const float *__restrict__ U, float *__restrict__ S_out,
-                                                       float *__restrict__ part_sums,
+__global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const float *__restrict__ x0,
+                                                       const CtrlState *__restrict__ st, const float *__restrict__ U,
+                                                       float *__restrict__ S_out, float *__restrict__ part_sums,
                                                        BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block<Sys, BLK, REGEN>(p, st->x0, st->counter, U, blockIdx.x * BLK, S_out,
+  rollout_block<Sys, BLK, REGEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
                                  part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
                                  smem);
 }
@@ -46,12 +46,16 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
                                                                 float *__restrict__ U, float *__restrict__ u0_out,
                                                                 float *__restrict__ dU_dbg,
                                                                 StepDebug *__restrict__ dbg) {
+  // B300 runs FP64 at a small fraction of the FP32 rate, so the FP64 work here is laid
+  // out for short dependency chains: 4 independent accumulators per lane, a 3-level tree
+  // across warps, one division (1/eta) per CTA.
   constexpr int NW = kMergeThreads / 32;
   extern __shared__ double s_scale[];  // [nblk]
   __shared__ float s_rho[NW];
   __shared__ int s_k[NW];
   __shared__ double s_e[NW];
   __shared__ double s_acc[NW][kMergeOutputs];
+  __shared__ double s_inv_eta;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   float v = INFINITY;
@@ -92,30 +96,43 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   e = warp_sum_d(e);
   if (lane == 0) s_e[warp] = e;
   __syncthreads();
-  double eta = 0.0;
+  if (tid == 0) {
+    double eta = 0.0;
 #pragma unroll
-  for (int q = 0; q < NW; ++q) eta += s_e[q];
+    for (int q = 0; q < NW; ++q) eta += s_e[q];
+    s_inv_eta = eta > 0.0 ? 1.0 / eta : 0.0;
+    if (blockIdx.x == 0) {
+      dbg->rho = rho;
+      dbg->kstar = s_k[0];
+      dbg->eta = eta;
+    }
+  }
 
   const int o = blockIdx.x * kMergeOutputs + lane;
-  double acc = 0.0;
-  if (o < TM)
-    for (int b = warp; b < nblk; b += NW) acc += s_scale[b] * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
-  s_acc[warp][lane] = acc;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (o < TM) {
+    int b = warp;
+    for (; b + 3 * NW < nblk; b += 4 * NW) {
+      a0 += s_scale[b] * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
+      a1 += s_scale[b + NW] * static_cast<double>(part_sums[static_cast<size_t>(b + NW) * TM + o]);
+      a2 += s_scale[b + 2 * NW] * static_cast<double>(part_sums[static_cast<size_t>(b + 2 * NW) * TM + o]);
+      a3 += s_scale[b + 3 * NW] * static_cast<double>(part_sums[static_cast<size_t>(b + 3 * NW) * TM + o]);
+    }
+    for (; b < nblk; b += NW) a0 += s_scale[b] * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
+  }
+  s_acc[warp][lane] = (a0 + a1) + (a2 + a3);
   __syncthreads();
-  if (warp == 0 && o < TM) {
-    double t = 0.0;
 #pragma unroll
-    for (int q = 0; q < NW; ++q) t += s_acc[q][lane];
-    const double du = eta > 0.0 ? t / eta : 0.0;
+  for (int h = NW / 2; h > 0; h >>= 1) {
+    if (warp < h) s_acc[warp][lane] += s_acc[warp + h][lane];
+    __syncthreads();
+  }
+  if (warp == 0 && o < TM) {
+    const double du = s_acc[0][lane] * s_inv_eta;
     const float un = U[o] + static_cast<float>(du);
     U[o] = un;
     dU_dbg[o] = static_cast<float>(du);
     if (o < m) u0_out[o] = un;
-  }
-  if (blockIdx.x == 0 && tid == 0) {
-    dbg->rho = rho;
-    dbg->kstar = s_k[0];
-    dbg->eta = eta;
   }
 }
 
@@ -311,29 +328,29 @@ int fused_block_size(const CtrlParams &p) {
 int fused_block_samples(int blk) { return blk == kFusedBlockRegen ? kFusedBlockLarge : blk; }
 
 template <class Sys, int BLK, bool REGEN>
-static cudaError_t launch_fused_t(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *ps,
-                                  BlockPartial *part, cudaStream_t s) {
+static cudaError_t launch_fused_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
+                                  float *ps, BlockPartial *part, cudaStream_t s) {
   const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, REGEN);
   const int grid = (p.K + BLK - 1) / BLK;
-  k_rollout_fused<Sys, BLK, REGEN><<<grid, BLK, smem, s>>>(p, st, U, S, ps, part);
+  k_rollout_fused<Sys, BLK, REGEN><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part);
   return cudaGetLastError();
 }
 
 template <class Sys>
-static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const CtrlState *st, const float *U, float *S,
-                                    float *ps, BlockPartial *part, cudaStream_t s) {
-  if (blk == kFusedBlockLarge) return launch_fused_t<Sys, kFusedBlockLarge, false>(p, st, U, S, ps, part, s);
-  if (blk == kFusedBlockSmall) return launch_fused_t<Sys, kFusedBlockSmall, false>(p, st, U, S, ps, part, s);
-  if (blk == kFusedBlockRegen) return launch_fused_t<Sys, kFusedBlockLarge, true>(p, st, U, S, ps, part, s);
+static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const float *x0, const CtrlState *st, const float *U,
+                                    float *S, float *ps, BlockPartial *part, cudaStream_t s) {
+  if (blk == kFusedBlockLarge) return launch_fused_t<Sys, kFusedBlockLarge, false>(p, x0, st, U, S, ps, part, s);
+  if (blk == kFusedBlockSmall) return launch_fused_t<Sys, kFusedBlockSmall, false>(p, x0, st, U, S, ps, part, s);
+  if (blk == kFusedBlockRegen) return launch_fused_t<Sys, kFusedBlockLarge, true>(p, x0, st, U, S, ps, part, s);
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const CtrlState *st, const float *U,
-                                 float *S, float *part_sums, BlockPartial *part, cudaStream_t s) {
+cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
+                                 const float *U, float *S, float *part_sums, BlockPartial *part, cudaStream_t s) {
   switch (sys) {
-    case 0: return launch_fused_sys<CartPole>(blk, p, st, U, S, part_sums, part, s);
-    case 1: return launch_fused_sys<Car>(blk, p, st, U, S, part_sums, part, s);
-    case 2: return launch_fused_sys<Quad>(blk, p, st, U, S, part_sums, part, s);
+    case 0: return launch_fused_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, s);
+    case 1: return launch_fused_sys<Car>(blk, p, x0, st, U, S, part_sums, part, s);
+    case 2: return launch_fused_sys<Quad>(blk, p, x0, st, U, S, part_sums, part, s);
     default: return cudaErrorInvalidValue;
   }
 }

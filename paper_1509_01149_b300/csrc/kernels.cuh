@@ -26,8 +26,10 @@ int fused_block_size(const CtrlParams &p);
 // Samples per block of a block shape.
 int fused_block_samples(int blk);
 // Rollout + cost + IS term + block-local weights and weighted perturbation sums.
-cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const CtrlState *st, const float *U,
-                                 float *S, float *part_sums, BlockPartial *part, cudaStream_t s);
+// x0: device state [n] read at launch time (the ctx's own copy or the caller's buffer);
+// st: iteration counter.
+cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
+                                 const float *U, float *S, float *part_sums, BlockPartial *part, cudaStream_t s);
 // Cross-block FP64 merge: rho, kstar, eta, du; U += du; u0 out.
 cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                 float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s);
@@ -40,8 +42,8 @@ constexpr int kMlpMaxT = 600;
 size_t mlp_rollout_smem_bytes(int T, int precision);
 cudaError_t prepare_mlp_kernel();
 // precision 0: BF16 weights and activations; 1: E4M3 (FP8) with per-tensor weight scales
-cudaError_t launch_rollout_mlp(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *part_sums,
-                               BlockPartial *part, int precision, cudaStream_t s);
+cudaError_t launch_rollout_mlp(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
+                               float *part_sums, BlockPartial *part, int precision, cudaStream_t s);
 
 // Plain-loop baseline ---------------------------------------------------------
 cudaError_t launch_plain_noise(const CtrlParams &p, const uint32_t *counter, float *du, cudaStream_t s);

@@ -122,7 +122,8 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
 }  // namespace
 
 template <int E>
-__global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams p, const CtrlState *__restrict__ st,
+__global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams p, const float *__restrict__ x0,
+                                                                const CtrlState *__restrict__ st,
                                                                 const float *__restrict__ U, float *__restrict__ S_out,
                                                                 float *__restrict__ part_sums,
                                                                 BlockPartial *__restrict__ part) {
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   }
   float x[N];
 #pragma unroll
-  for (int a = 0; a < N; ++a) x[a] = st->x0[a];
+  for (int a = 0; a < N; ++a) x[a] = x0[a];
   const uint32_t ctr = st->counter;
   KahanSum S;
   uint32_t phase = 0;
@@ -330,14 +331,14 @@ size_t mlp_rollout_smem_bytes(int T, int precision) {
   return base + sizeof(float) * (2 * static_cast<size_t>(T) * 2 + T);
 }
 
-cudaError_t launch_rollout_mlp(const CtrlParams &p, const CtrlState *st, const float *U, float *S, float *part_sums,
-                               BlockPartial *part, int precision, cudaStream_t s) {
+cudaError_t launch_rollout_mlp(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
+                               float *part_sums, BlockPartial *part, int precision, cudaStream_t s) {
   const size_t smem = mlp_rollout_smem_bytes(p.T, precision);
   const int grid = (p.K + kMlpThreads - 1) / kMlpThreads;
   if (precision == 0)
-    k_rollout_mlp<2><<<grid, kMlpThreads, smem, s>>>(p, st, U, S, part_sums, part);
+    k_rollout_mlp<2><<<grid, kMlpThreads, smem, s>>>(p, x0, st, U, S, part_sums, part);
   else
-    k_rollout_mlp<1><<<grid, kMlpThreads, smem, s>>>(p, st, U, S, part_sums, part);
+    k_rollout_mlp<1><<<grid, kMlpThreads, smem, s>>>(p, x0, st, U, S, part_sums, part);
   return cudaGetLastError();
 }
 

@@ -242,7 +242,7 @@ extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float n
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   k_static_state<<<1, 32, 0, s>>>(d_state, n, counter, st);
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_rollout_fused(sys, blk, p, st, d_U, Sk, psum, part, s);
+  if (e == cudaSuccess) e = launch_rollout_fused(sys, blk, p, st->x0, st, d_U, Sk, psum, part, s);
   if (e == cudaSuccess) e = launch_merge_update(nblk, p, psum, part, d_U, d_u0_out, dU, dbg, s);
   if (e != cudaSuccess) {
     cudaGetLastError();

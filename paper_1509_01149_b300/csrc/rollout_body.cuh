@@ -220,33 +220,53 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   Sys::init(x, aux, env);
   KahanSum S;
 
+  // One time step: noise -> control -> dynamics; the cost of the new state is issued now
+  // and finished after the next step's dynamics (same summation order as q_i + is_i).
+  typename Sys::Pending pend;
+  float pend_is = 0.0f;
+  bool have = false;
+  auto step_at = [&](int i, const float *e) {
+    float du[M], v[M];
+    scale_noise<M>(Lnu, e, du);
+    float duRdu = 0.0f, uRdu = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      v[j] = sU[i * M + j] + du[j];
+      if (!REGEN) sDu[(i * M + j) * BLK + tid] = du[j];
+      uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
+      float rd = 0.0f;
+#pragma unroll
+      for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
+      duRdu = fmaf(du[j], rd, duRdu);
+    }
+    Sys::step(x, v, aux, env, p.dt);
+    if (have) S.add(Sys::cost_finish(pend, env) + pend_is);
+    pend = Sys::cost_issue(x, aux, env);
+    pend_is = p.is_du * duRdu + uRdu + sHu[i];
+    have = true;
+  };
+
+  // Philox blocks: the normals of block b+1 are drawn while block b's steps run
   const int nb = (TM + 3) >> 2;
-  for (int b = 0; b < nb; ++b) {
-    float eps[4];
-    normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+  const int nb_full = T / SPB;  // blocks whose SPB steps are all inside the horizon
+  float eps[4];
+  normals4(0u, static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+  for (int b = 0; b < nb_full; ++b) {
+    float nxt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (b + 1 < nb) normals4(static_cast<uint32_t>(b + 1), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, nxt);
+#pragma unroll
+    for (int s = 0; s < SPB; ++s) step_at(b * SPB + s, eps + s * M);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) eps[j] = nxt[j];
+  }
+  if (nb_full < nb) {  // the last block holds fewer than SPB steps
 #pragma unroll
     for (int s = 0; s < SPB; ++s) {
-      const int i = b * SPB + s;
-      if (i < T) {
-        float du[M], v[M];
-        scale_noise<M>(Lnu, eps + s * M, du);
-        float duRdu = 0.0f, uRdu = 0.0f;
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-          v[j] = sU[i * M + j] + du[j];
-          if (!REGEN) sDu[(i * M + j) * BLK + tid] = du[j];
-          uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
-          float rd = 0.0f;
-#pragma unroll
-          for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
-          duRdu = fmaf(du[j], rd, duRdu);
-        }
-        Sys::step(x, v, aux, env, p.dt);
-        const float q = Sys::cost(x, aux, env);
-        S.add(q + (p.is_du * duRdu + uRdu + sHu[i]));
-      }
+      const int i = nb_full * SPB + s;
+      if (i < T) step_at(i, eps + s * M);
     }
   }
+  if (have) S.add(Sys::cost_finish(pend, env) + pend_is);
   S.add(Sys::cost(x, aux, env));  // phi(x_T) = q(x_T)
   block_partial<M, BLK, REGEN>(p, k, ctr, S.s, Lnu, S_out, part_sums, part, sW, sDu);
 }

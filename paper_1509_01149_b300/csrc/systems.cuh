@@ -56,6 +56,15 @@ struct CartPole {
   __device__ __forceinline__ static float cost(const float x[N], const Aux &, const Env &) {
     return x[0] * x[0] + x[1] * x[1] + 10.0f * x[2] * x[2] + x[3] * x[3];
   }
+
+  // cost in two halves (see Car): nothing to load here
+  struct Pending {
+    float q;
+  };
+  __device__ __forceinline__ static Pending cost_issue(const float x[N], const Aux &a, const Env &e) {
+    return Pending{cost(x, a, e)};
+  }
+  __device__ __forceinline__ static float cost_finish(const Pending &pd, const Env &) { return pd.q; }
 };
 
 // ---------------------------------------------------------------------------
@@ -134,6 +143,35 @@ struct Car {
   __device__ __forceinline__ static float cost(const float x[N], const Aux &, const Env &e) {
     const float dv = x[3] - v_target;
     return map_bilinear(e, x[0], x[1]) + dv * dv;
+  }
+
+  // The cost in two halves: cost_issue starts the four map loads of q(x) and returns at
+  // once; cost_finish combines them.  The rollout finishes step i's cost only after the
+  // dynamics of step i+1, so the L2 latency of the loads overlaps a step of arithmetic.
+  struct Pending {
+    float m00, m10, m01, m11, tx, ty, speed;
+  };
+  __device__ __forceinline__ static Pending cost_issue(const float x[N], const Aux &, const Env &e) {
+    Pending pd;
+    const float fx = fminf(fmaxf((x[0] - e.map_ox) * e.map_inv_cell, 0.0f), static_cast<float>(e.map_w - 1));
+    const float fy = fminf(fmaxf((x[1] - e.map_oy) * e.map_inv_cell, 0.0f), static_cast<float>(e.map_h - 1));
+    const int ix = min(static_cast<int>(fx), e.map_w - 2);
+    const int iy = min(static_cast<int>(fy), e.map_h - 2);
+    pd.tx = fx - static_cast<float>(ix);
+    pd.ty = fy - static_cast<float>(iy);
+    const float *row = e.map + static_cast<size_t>(iy) * e.map_w + ix;
+    pd.m00 = __ldg(row);
+    pd.m10 = __ldg(row + 1);
+    pd.m01 = __ldg(row + e.map_w);
+    pd.m11 = __ldg(row + e.map_w + 1);
+    const float dv = x[3] - v_target;
+    pd.speed = dv * dv;
+    return pd;
+  }
+  __device__ __forceinline__ static float cost_finish(const Pending &pd, const Env &) {
+    const float a = pd.m00 + pd.tx * (pd.m10 - pd.m00);
+    const float b = pd.m01 + pd.tx * (pd.m11 - pd.m01);
+    return (a + pd.ty * (b - a)) + pd.speed;
   }
 };
 
@@ -235,6 +273,14 @@ struct Quad {
               w_v * (x[3] * x[3] + x[4] * x[4] + x[5] * x[5]) + w_obs * __expf(-a.d * (1.0f / obs_scale));
     return a.crashed ? c + w_crash : c;
   }
+
+  struct Pending {
+    float q;
+  };
+  __device__ __forceinline__ static Pending cost_issue(const float x[N], const Aux &a, const Env &e) {
+    return Pending{cost(x, a, e)};
+  }
+  __device__ __forceinline__ static float cost_finish(const Pending &pd, const Env &) { return pd.q; }
 };
 
 }  // namespace mppi

@@ -170,3 +170,21 @@ def test_step_without_env_is_a_state_error(N):
     assert ei.value.rc == -5
     with pytest.raises(N.MppiError):
         c.set_forest(W.quad_forest(0), W.QUAD_GOAL)   # wrong env kind for a car
+
+
+def test_graph_iteration_equals_step_and_shift(N):
+    """mppi_iterate_async (one CUDA graph: rollout, merge, shift) gives the same controls,
+    u0 and counter as mppi_step_async followed by mppi_shift, over three iterations."""
+    import torch
+    cfg = W.config(W.CAR, K=3000, T=40, lam=50.0)
+    a, b = P.make_controller(cfg), P.make_controller(cfg)
+    dx = torch.tensor(np.asarray(cfg["x0"], np.float32), device="cuda")
+    ua, ub = torch.zeros(2, device="cuda"), torch.zeros(2, device="cuda")
+    for _ in range(3):
+        a.step_async(dx.data_ptr(), ua.data_ptr())
+        a.shift()
+        b.iterate_async(dx.data_ptr(), ub.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(ua, ub)
+    assert np.array_equal(a.get_controls(), b.get_controls())
+    assert a.get_iteration() == b.get_iteration() == 3
