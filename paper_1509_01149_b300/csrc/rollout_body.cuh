@@ -30,8 +30,9 @@ __device__ __forceinline__ void scale_noise(const float *Lnu, const float *eps, 
   }
 }
 
-__device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs) {
+__device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs, int packed = 0) {
   Env e;
+  e.obs_packed = packed;
   e.map = p.map;
   e.map_w = p.map_w;
   e.map_h = p.map_h;
@@ -66,7 +67,7 @@ __device__ __forceinline__ float transpose_reduce32(float v[32]) {
 // Shared-memory bytes of rollout_block (dynamic part) for T*M outputs.
 __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, int blk, bool regen) {
   const size_t TM = static_cast<size_t>(T) * M;
-  return sizeof(float) * (2 * TM + T + 3 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk));
+  return 16 + sizeof(float) * (2 * TM + T + 4 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk));
 }
 
 // The block's softmax partial from each thread's path cost Sk_raw (sample k):
@@ -173,23 +174,25 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
 //   k0       first sample index of this block
 //   S_out    [K] path costs (global), part_sums [T*M] and part: this block's partial
 //   smem     dynamic shared memory of rollout_smem_bytes(...)
+//   du_ext   STORE only: if not null, the [TM][BLK] perturbation buffer lives there (a
+//            global-memory slab owned by this CTA) instead of in shared memory
 template <class Sys, int BLK, bool REGEN>
 __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                               const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                               float *__restrict__ part_sums, BlockPartial *__restrict__ part,
-                                              float *smem) {
+                                              float *smem, float *du_ext = nullptr) {
   constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M;
   static_assert(4 % M == 0, "controls per Philox block must divide 4");
   const int T = p.T, TM = T * M, tid = threadIdx.x;
-  float *sU = smem;                 // [TM]  nominal controls
+  float *sObs = smem;               // [n_obs][4] cylinders (16-byte aligned, first)
+  float *sU = sObs + 4 * p.n_obs;   // [TM]  nominal controls
   float *sRu = sU + TM;             // [TM]  R u_i
   float *sHu = sRu + TM;            // [T]   1/2 u_i^T R u_i
-  float *sObs = sHu + T;            // [3 n_obs]
-  float *sW = sObs + 3 * p.n_obs;   // [BLK] weights
-  float *sDu = sW + BLK;            // STORE only: [TM][BLK] perturbations of this block
+  float *sW = sHu + T;              // [BLK] weights
+  float *sDu = du_ext ? du_ext : sW + BLK;  // STORE only: [TM][BLK] perturbations of this block
 
   for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
-  for (int o = tid; o < 3 * p.n_obs; o += BLK) sObs[o] = p.obs[o];
+  for (int o = tid; o < 4 * p.n_obs; o += BLK) sObs[o] = (o & 3) == 3 ? 0.0f : p.obs[3 * (o >> 2) + (o & 3)];
   __syncthreads();
   for (int i = tid; i < T; i += BLK) {
     float h = 0.0f;
@@ -205,7 +208,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   }
   __syncthreads();
 
-  const Env env = make_env(p, sObs);
+  const Env env = make_env(p, sObs, 1);
   const int k = k0 + tid;
   float Lnu[M * M], R[M * M];
 #pragma unroll

@@ -5,8 +5,10 @@
 //                arena, iteration counter (persistent between ticks).
 //   k_serve_rollout<BLK>  persistent: each CTA takes work items (slot, block of BLK
 //                samples) from an atomic queue, heaviest first, and runs the fused
-//                rollout body with du regenerated (no shared-memory copy, so many CTAs
-//                share an SM).  Items of different systems / K / T run side by side.
+//                rollout body.  du goes to the CTA's own global-memory slab (written and
+//                read back by the same CTA, so it stays in L2) rather than to shared
+//                memory, so many CTAs share an SM.  Items of different systems / K / T
+//                run side by side.
 //   k_serve_merge          persistent: one slot per CTA taken from a second queue; FP64
 //                merge of the slot's block partials, U update, u_0 out, shift, counter++.
 // Host side
@@ -59,14 +61,16 @@ struct ServeArgs {
   const WorkItem *items;   // [n_items]
   float *u0_out;           // [n_slots][4]
   int *counters;           // [0] rollout queue, [1] merge queue
+  float *du_slab;          // per persistent CTA: [max_tm][BLK] perturbations (global, L2-resident)
+  int slab_floats;         // floats per CTA slab
 };
 
 constexpr int kServeMergeThreads = 256;
 constexpr int kServeMaxK = 65536;
 constexpr int kServeMaxT = 256;
 
-template <int BLK>
-__global__ void __launch_bounds__(BLK) k_serve_rollout(const ServeArgs a) {
+template <int BLK, int MINB>
+__global__ void __launch_bounds__(BLK, MINB) k_serve_rollout(const ServeArgs a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ CtrlParams s_p;
   __shared__ int s_item;
@@ -83,16 +87,19 @@ __global__ void __launch_bounds__(BLK) k_serve_rollout(const ServeArgs a) {
     __syncthreads();
     const float *x0 = a.states + 16 * w.tick;
     float *ps = d->part_sums + static_cast<size_t>(w.block) * d->tm;
+    float *slab = a.du_slab + static_cast<size_t>(blockIdx.x) * a.slab_floats;
     switch (d->sys) {
       case MPPI_CARTPOLE:
-        rollout_block<CartPole, BLK, true>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block,
-                                           smem);
+        rollout_block<CartPole, BLK, false>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block,
+                                            smem, slab);
         break;
       case MPPI_CAR:
-        rollout_block<Car, BLK, true>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block, smem);
+        rollout_block<Car, BLK, false>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block, smem,
+                                       slab);
         break;
       case MPPI_QUAD:
-        rollout_block<Quad, BLK, true>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block, smem);
+        rollout_block<Quad, BLK, false>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block, smem,
+                                        slab);
         break;
       default:
         break;
@@ -313,9 +320,11 @@ struct mppi_server {
   unsigned char *d_tick = nullptr, *h_tick = nullptr;
   float *d_u0 = nullptr, *h_u0 = nullptr;
   int *d_counters = nullptr;
+  float *d_slab = nullptr;
+  size_t slab_cap = 0;
   int max_tm = 1, max_nblk = 1, max_nobs = 0;
 
-  int blk = 128, ctas_per_sm = 0;
+  int blk = 128, ctas_per_sm = 0, variant = 1;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t n_memset = nullptr, n_h2d = nullptr, n_roll = nullptr, n_merge = nullptr, n_d2h = nullptr;
@@ -360,14 +369,20 @@ size_t slot_bytes(int K, int T, int m) {
 size_t rollout_smem(const mppi_server *s, int blk) { return rollout_smem_bytes(s->max_tm, 1, s->max_nobs, blk, true); }
 size_t merge_smem(const mppi_server *s) { return sizeof(double) * s->max_nblk + sizeof(float) * s->max_tm; }
 
-const void *rollout_fn(int blk) {
-  switch (blk) {
-    case 64: return reinterpret_cast<const void *>(k_serve_rollout<64>);
-    case 128: return reinterpret_cast<const void *>(k_serve_rollout<128>);
-    case 256: return reinterpret_cast<const void *>(k_serve_rollout<256>);
-    default: return nullptr;
-  }
-}
+// Rollout kernel variants the autotuner chooses from: block size and the register cap
+// implied by a minimum number of resident blocks per SM.
+struct RolloutVariant {
+  int blk, minb;
+  const void *fn;
+};
+const RolloutVariant kVariants[] = {
+    {64, 8, reinterpret_cast<const void *>(k_serve_rollout<64, 8>)},
+    {128, 4, reinterpret_cast<const void *>(k_serve_rollout<128, 4>)},
+    {128, 6, reinterpret_cast<const void *>(k_serve_rollout<128, 6>)},
+    {256, 2, reinterpret_cast<const void *>(k_serve_rollout<256, 2>)},
+    {256, 3, reinterpret_cast<const void *>(k_serve_rollout<256, 3>)},
+};
+constexpr int kNumVariants = static_cast<int>(sizeof(kVariants) / sizeof(kVariants[0]));
 
 int ensure_tick_capacity(mppi_server *s, size_t items) {
   if (items <= s->item_cap && s->d_tick) return MPPI_OK;
@@ -395,8 +410,9 @@ int build_graph(mppi_server *s) {
   if (s->graph) cudaGraphDestroy(s->graph);
   s->exec = nullptr;
   s->graph = nullptr;
-  const void *rfn = rollout_fn(s->blk);
-  if (!rfn) return s->fail(MPPI_EINVAL, "bad block shape %d", s->blk);
+  if (s->variant < 0 || s->variant >= kNumVariants) return s->fail(MPPI_EINVAL, "bad kernel variant");
+  const void *rfn = kVariants[s->variant].fn;
+  s->blk = kVariants[s->variant].blk;
   const size_t rsm = rollout_smem(s, s->blk), msm = merge_smem(s);
   SRV_TRY(s->cuda(cudaFuncSetAttribute(rfn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(rsm)),
                   "rollout smem attribute"));
@@ -411,7 +427,19 @@ int build_graph(mppi_server *s) {
   if (occ < 1 || mocc < 1) return s->fail(MPPI_EINVAL, "serving kernels do not fit on an SM");
   const int cps = s->ctas_per_sm > 0 ? std::min(s->ctas_per_sm, occ) : occ;
 
+  // per-CTA du slabs
+  const size_t grid_ctas = static_cast<size_t>(s->num_sms) * cps;
+  const size_t slab = static_cast<size_t>(s->max_tm) * s->blk;
+  if (grid_ctas * slab > s->slab_cap) {
+    if (s->d_slab) cudaFree(s->d_slab);
+    s->d_slab = nullptr;
+    s->slab_cap = 0;
+    SRV_TRY(s->cuda(cudaMalloc(&s->d_slab, sizeof(float) * grid_ctas * slab), "cudaMalloc(du slabs)"));
+    s->slab_cap = grid_ctas * slab;
+  }
   ServeArgs &a = s->args;
+  a.du_slab = s->d_slab;
+  a.slab_floats = static_cast<int>(slab);
   a.slots = s->d_slots;
   a.hdr = reinterpret_cast<const TickHeader *>(s->d_tick);
   a.tick_slots = reinterpret_cast<const int *>(s->d_tick + s->off_slots);
@@ -584,6 +612,7 @@ int mppi_server_destroy(mppi_server *s) {
   if (s->d_u0) cudaFree(s->d_u0);
   if (s->h_u0) cudaFreeHost(s->h_u0);
   if (s->d_counters) cudaFree(s->d_counters);
+  if (s->d_slab) cudaFree(s->d_slab);
   if (s->d_tick) cudaFree(s->d_tick);
   if (s->h_tick) cudaFreeHost(s->h_tick);
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -801,12 +830,11 @@ int mppi_server_autotune(mppi_server *s, int n, const int *slot_ids, const float
     return s->cuda(cudaMemcpy(s->d_slots, D.data(), sizeof(SlotDesc) * s->max_slots, cudaMemcpyHostToDevice),
                    "restore");
   };
-  const int shapes[3] = {64, 128, 256};
   double best = 1e30;
-  int best_blk = s->blk, best_cps = 0;
-  for (int bi = 0; bi < 3; ++bi) {
+  int best_var = s->variant, best_cps = 0;
+  for (int bi = 0; bi < kNumVariants; ++bi) {
     for (int cps_try = 0; cps_try < 2; ++cps_try) {
-      s->blk = shapes[bi];
+      s->variant = bi;
       s->ctas_per_sm = 0;
       s->graph_dirty = true;
       SRV_TRY(build_graph(s));
@@ -825,12 +853,13 @@ int mppi_server_autotune(mppi_server *s, int n, const int *slot_ids, const float
       SRV_TRY(restore());
       if (t < best) {
         best = t;
-        best_blk = s->blk;
+        best_var = s->variant;
         best_cps = s->ctas_per_sm;
       }
     }
   }
-  s->blk = best_blk;
+  s->variant = best_var;
+  s->blk = kVariants[best_var].blk;
   s->ctas_per_sm = best_cps;
   s->graph_dirty = true;
   for (int i = 0; i < s->max_slots; ++i)

@@ -27,8 +27,10 @@ struct Env {
   const float *__restrict__ map;
   int map_w, map_h;
   float map_ox, map_oy, map_inv_cell;
-  const float *obs;  // shared-memory copy of the cylinders, [n_obs][3]
+  const float *obs;  // cylinders: [n_obs][4] (cx, cy, r, 0) in shared memory when obs_packed,
+                     // else [n_obs][3] in global memory
   int n_obs;
+  int obs_packed;
   float gx, gy, gz;
 };
 
@@ -104,15 +106,19 @@ struct Car {
 
   __device__ __forceinline__ static void deriv(const float x[N], const float v[M], float d[N]) {
     const float vx = x[3], vy = x[4], r = x[5], delta = x[6];
-    const float inv_vxs = 1.0f / fmaxf(vx, vx_floor);
+    // The tyre-force sines have arguments |C atan(.)| <= 1.8 pi/2 < pi and the steering
+    // angle stays small, where the special-function-unit sine/cosine are accurate to about
+    // 2^-21 absolute: they run as single SFU operations with no slow-path branch, which
+    // keeps the two tyre chains interleavable.  The heading (unbounded) keeps sincosf.
+    const float inv_vxs = __fdividef(1.0f, fmaxf(vx, vx_floor));
     const float alpha_f = delta - atanf((vy + lf * r) * inv_vxs);
     const float alpha_r = -atanf((vy - lr * r) * inv_vxs);
-    const float Fyf = Df * sinf(C * atanf(B * alpha_f));
-    const float Fyr = Dr * sinf(C * atanf(B * alpha_r));
+    const float Fyf = Df * __sinf(C * atanf(B * alpha_f));
+    const float Fyr = Dr * __sinf(C * atanf(B * alpha_r));
     const float Fx = Cm * v[1] - Crr * vx - Cd * vx * fabsf(vx);
     float sp, cp, sd, cd;
     sincosf(x[2], &sp, &cp);
-    sincosf(delta, &sd, &cd);
+    __sincosf(delta, &sd, &cd);
     d[0] = vx * cp - vy * sp;
     d[1] = vx * sp + vy * cp;
     d[2] = r;
@@ -197,10 +203,20 @@ struct Quad {
 
   __device__ __forceinline__ static float obstacle_distance(const Env &e, float px, float py) {
     float d = INFINITY;
+    if (e.obs_packed) {  // one 128-bit broadcast load per cylinder
+      const float4 *o4 = reinterpret_cast<const float4 *>(e.obs);
 #pragma unroll 4
-    for (int j = 0; j < e.n_obs; ++j) {
-      const float dx = px - e.obs[3 * j], dy = py - e.obs[3 * j + 1];
-      d = fminf(d, fast_sqrt(fmaf(dx, dx, dy * dy)) - e.obs[3 * j + 2]);
+      for (int j = 0; j < e.n_obs; ++j) {
+        const float4 c = o4[j];
+        const float dx = px - c.x, dy = py - c.y;
+        d = fminf(d, fast_sqrt(fmaf(dx, dx, dy * dy)) - c.z);
+      }
+    } else {
+#pragma unroll 4
+      for (int j = 0; j < e.n_obs; ++j) {
+        const float dx = px - e.obs[3 * j], dy = py - e.obs[3 * j + 1];
+        d = fminf(d, fast_sqrt(fmaf(dx, dx, dy * dy)) - e.obs[3 * j + 2]);
+      }
     }
     return d;
   }
