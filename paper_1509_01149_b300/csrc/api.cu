@@ -422,7 +422,7 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   if (sys == MPPI_CAR_MLP) {
     if (T > kMlpMaxT) {
       delete c;
-      return bad("T out of range [1, 600] for the learned dynamics");
+      return bad("T out of range [1, 500] for the learned dynamics");
     }
     c->blk = kFusedBlockRegen;  // 128 samples per block, du regenerated
   }

@@ -37,8 +37,8 @@ cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part
 cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s);
 
 // Learned car dynamics (mlp_rollout.cu) -----------------------------------------
-constexpr size_t kMlpSmemLimit = 226 * 1024;
-constexpr int kMlpMaxT = 600;
+constexpr size_t kMlpSmemLimit = 225 * 1024;
+constexpr int kMlpMaxT = 500;
 size_t mlp_rollout_smem_bytes(int T, int precision);
 cudaError_t prepare_mlp_kernel();
 // precision 0: BF16 weights and activations; 1: E4M3 (FP8) with per-tensor weight scales

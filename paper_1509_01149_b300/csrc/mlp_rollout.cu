@@ -1,7 +1,8 @@
 // Fused MPPI rollout with the learned car dynamics on the tensor cores (sm_103a).
 //
-// One CTA of 128 threads owns 128 samples (thread t = sample k0 + t = TMEM lane t = row
-// t of every activation tile).  The network weights are copied once into shared memory
+// One CTA of 256 threads owns 128 samples: thread t < 128 holds sample k0 + t (TMEM lane t,
+// row t of every activation tile); in the hidden-layer epilogues warps w and w + 4 share TMEM
+// lane quadrant w % 4 and take column halves [0, 128) and [128, 256).  The network weights are copied once into shared memory
 // in the K-major core-matrix layout; TMEM holds the FP32 accumulators (columns 0..255
 // for the two hidden layers, 256..271 for the output layer).  Per time step:
 //   noise du_i (Philox), v = u_i + du_i, features z(x, v) -> X tile (BF16)
@@ -29,7 +30,8 @@
 namespace mppi {
 
 namespace {
-constexpr int kMlpThreads = 128;
+constexpr int kMlpThreads = 256;   // 8 warps: two per TMEM lane quadrant in the epilogues
+constexpr int kMlpSamples = 128;   // rows of the MMA tile; threads 0..127 own one sample each
 
 // Shared-memory layout (bytes) for element size E (2 = BF16, 1 = E4M3); the first layer's
 // K is 16 (BF16) or 32 (E4M3, zero padded) so that one MMA covers it.
@@ -80,13 +82,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// H row `row` (columns 0..255) = tanh(scale * D[row][:] + bias) stored in the tile format,
-// D read from TMEM columns 0..255
+// H row `row`, columns [cbeg, cbeg + 128) = tanh(scale * D + bias) stored in the tile format,
+// D read from the same TMEM columns
 template <int E>
 __device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bias, float scale, unsigned char *smem,
-                                                int row) {
+                                                int row, int cbeg) {
 #pragma unroll 1
-  for (int c0 = 0; c0 < 256; c0 += 32) {
+  for (int c0 = cbeg; c0 < cbeg + 128; c0 += 32) {
     float v[32];
     tmem_ld32(tmem_row + static_cast<uint32_t>(c0), v);
     tc::tmem_ld_wait();
@@ -185,13 +187,16 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   tc::fence_after_sync();
 
   const uint32_t tmem = tmem_base;
-  const uint32_t tmem_row = tmem + (static_cast<uint32_t>(32 * warp) << 16);
+  const uint32_t tmem_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+  const int erow = 32 * (warp & 3) + (tid & 31);  // epilogue row (= sample) of this thread
+  const int ecol = (warp >> 2) * 128;             // epilogue column half
+  const bool owner = tid < kMlpSamples;
   const uint32_t sbase = tc::smem_u32(smem);
   const uint32_t id256 = E == 2 ? tc::idesc_bf16_f32(128, 256) : tc::idesc_e4m3_f32(128, 256);
   const uint32_t id16 = E == 2 ? tc::idesc_bf16_f32(128, 16) : tc::idesc_e4m3_f32(128, 16);
   const float s1 = swscale[0], s2 = swscale[1], s3 = swscale[2];
   const Env env = make_env(p, nullptr);
-  const int k = blockIdx.x * kMlpThreads + tid;
+  const int k = blockIdx.x * kMlpSamples + tid;
   float Lnu[M * M], R[M * M];
 #pragma unroll
   for (int a = 0; a < M * M; ++a) {
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 
   for (int i = 0; i < T && ok; ++i) {
-    if ((i & 1) == 0)
+    if ((i & 1) == 0 && owner)
       normals4(static_cast<uint32_t>(i >> 1), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
     float du[M], v[M];
     {
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     }
     const float is_cost = p.is_du * duRdu + uRdu + sHu[i];
     // features -> X tile row tid
-    {
+    if (owner) {
       float z[mlp::kIn];
       mlp::features(x, v, z);
       if (E == 2) {
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       ok = false;
       break;
     }
-    hidden_epilogue<E>(tmem_row, sb1, s1, smem, tid);
+    hidden_epilogue<E>(tmem_row, sb1, s1, smem, erow, ecol);
     // layer 2
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       ok = false;
       break;
     }
-    hidden_epilogue<E>(tmem_row, sb2, s2, smem, tid);
+    hidden_epilogue<E>(tmem_row, sb2, s2, smem, erow, ecol);
     // layer 3
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -300,27 +305,32 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       ok = false;
       break;
     }
-    float y[16];
-    tc::tmem_ld8(tmem_row + L::D3, y);
-    tc::tmem_ld8(tmem_row + L::D3 + 8, y + 8);
-    tc::tmem_ld_wait();
+    if (owner) {  // warps 0..3: TMEM lane quadrant = warp, row = sample
+      float y[16];
+      tc::tmem_ld8(tmem_row + L::D3, y);
+      tc::tmem_ld8(tmem_row + L::D3 + 8, y + 8);
+      tc::tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < N; ++j) x[j] += fmaf(y[j], s3, sb3[j]) * sscale[j];
-    const float dv = x[3] - Car::v_target;
-    S.add(map_bilinear(env, x[0], x[1]) + dv * dv + is_cost);
+      for (int j = 0; j < N; ++j) x[j] += fmaf(y[j], s3, sb3[j]) * sscale[j];
+      const float dv = x[3] - Car::v_target;
+      S.add(map_bilinear(env, x[0], x[1]) + dv * dv + is_cost);
+    }
   }
   float Sk;
   if (ok) {
-    const float dv = x[3] - Car::v_target;
-    S.add(map_bilinear(env, x[0], x[1]) + dv * dv);  // phi(x_T) = q(x_T)
-    Sk = S.s;
+    if (owner) {
+      const float dv = x[3] - Car::v_target;
+      S.add(map_bilinear(env, x[0], x[1]) + dv * dv);  // phi(x_T) = q(x_T)
+    }
+    Sk = owner ? S.s : INFINITY;
   } else {
     Sk = INFINITY;
     if (tid == 0) atomicExch(md->err, 1);
     tc::mbar_wait(&bar, phase ^ 1u);  // bounded second chance for the MMAs in flight
   }
-  block_partial<M, kMlpThreads, true>(p, k, ctr, Sk, Lnu, S_out, part_sums + static_cast<size_t>(blockIdx.x) * TM,
-                                      part + blockIdx.x, nullptr, nullptr);
+  block_partial<M, kMlpThreads, true>(p, owner ? k : INT_MAX, ctr, Sk, Lnu, S_out,
+                                      part_sums + static_cast<size_t>(blockIdx.x) * TM, part + blockIdx.x, nullptr,
+                                      nullptr);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, L::kTmemCols);
@@ -334,7 +344,7 @@ size_t mlp_rollout_smem_bytes(int T, int precision) {
 cudaError_t launch_rollout_mlp(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                float *part_sums, BlockPartial *part, int precision, cudaStream_t s) {
   const size_t smem = mlp_rollout_smem_bytes(p.T, precision);
-  const int grid = (p.K + kMlpThreads - 1) / kMlpThreads;
+  const int grid = (p.K + kMlpSamples - 1) / kMlpSamples;
   if (precision == 0)
     k_rollout_mlp<2><<<grid, kMlpThreads, smem, s>>>(p, x0, st, U, S, part_sums, part);
   else

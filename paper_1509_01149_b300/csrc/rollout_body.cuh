@@ -74,7 +74,8 @@ __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, in
 //   rho_b = min_k S~_k (lowest k on ties), w_k = exp(-(S~_k - rho_b)/lambda),
 //   eta_b = sum_k w_k (FP64), part_sums[i*M+j] = sum_k w_k du_{i,j,k} (FP32)
 // with du from shared memory (STORE: sDu [T*M][BLK]) or regenerated (REGEN).
-// Non-finite costs and samples k >= K count as +inf (weight 0).
+// Non-finite costs and samples k >= K count as +inf (weight 0); k == INT_MAX marks a thread
+// that owns no sample (it only takes part in the block reduction).
 template <int M, int BLK, bool REGEN>
 __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32_t ctr, float Sk_raw, const float *Lnu,
                                               float *__restrict__ S_out, float *__restrict__ part_sums,
@@ -132,7 +133,7 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (g + q < nb)
+        if (g + q < nb && k != INT_MAX)  // k == INT_MAX: a thread that owns no sample
           normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
 #pragma unroll
         for (int s = 0; s < SPB; ++s) {
