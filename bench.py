@@ -466,7 +466,7 @@ def run_ours(args, rank, world, local_rank):
     roll_mean_s = statistics.mean(roll_ms) / 1e3
     achieved = flops / roll_mean_s / 1e12
     peak = fp32_peak_tflops()
-    traffic = load_traffic("rollout_fused_car_k16384")
+    traffic = load_traffic("rollout_car_ws_k16384")
     cpu = None
     if not args.no_cpu_baseline:
         rate, iters, _ = oracle_rate(args.cpu_seconds, 1024)
@@ -498,7 +498,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 3 * args.steps,
         "launch_note": "per step one CUDA-graph launch of 3 kernels (rollout, FP64 merge + update, shift)",
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_rollout_fused<Car,128>",
+                     "traffic": traffic, "kernel": "k_rollout_car_ws<128> (core, noise and pose warps per 128 samples)",
                      "flops_per_rollout_step": ALGO_FLOPS_PER_ROLLOUT_STEP[SYSTEM],
                      "rollout_ms_mean": 1e3 * roll_mean_s,
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived, not measured)",

@@ -418,7 +418,7 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   p.map_w = p.map_h = 2;
   p.map_inv_cell = 1.0f;
 
-  c->blk = fused_block_size(p);
+  c->blk = fused_block_size(sys, p);
   if (sys == MPPI_CAR_MLP) {
     if (T > kMlpMaxT) {
       delete c;
@@ -589,7 +589,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
     payload = static_cast<const char *>(blob) + sizeof h;
     np.n_obs = h.n_obstacles;
     for (int i = 0; i < 3; ++i) np.goal[i] = h.goal[i];
-    if (fused_block_size(np) == 0) return c->fail(MPPI_EINVAL, "forest too large for shared memory");
+    if (fused_block_size(c->sys, np) == 0) return c->fail(MPPI_EINVAL, "forest too large for shared memory");
   } else {
     return c->fail(MPPI_EINVAL, "unknown env kind 0x%08x", kind);
   }
@@ -614,7 +614,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   }
   np.mlp = c->p.mlp;
   c->p = np;
-  c->blk = c->sys == MPPI_CAR_MLP ? kFusedBlockRegen : fused_block_size(c->p);
+  c->blk = c->sys == MPPI_CAR_MLP ? kFusedBlockRegen : fused_block_size(c->sys, c->p);
   c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
   c->env_ok = true;
   c->graph_dirty = c->iter_graph_dirty = true;

@@ -20,6 +20,7 @@
 
 #include "kernels.cuh"
 #include "rollout_body.cuh"
+#include "rollout_ws.cuh"
 
 namespace mppi {
 
@@ -35,6 +36,18 @@ __global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const
   rollout_block<Sys, BLK, REGEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
                                  part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
                                  smem);
+}
+
+// car: three threads per sample (velocity recurrence / noise / pose and cost), see rollout_ws.cuh
+template <int NS>
+__global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlParams p, const float *__restrict__ x0,
+                                                              const CtrlState *__restrict__ st,
+                                                              const float *__restrict__ U, float *__restrict__ S_out,
+                                                              float *__restrict__ part_sums,
+                                                              BlockPartial *__restrict__ part) {
+  extern __shared__ __align__(16) float smem[];
+  rollout_block_car_ws<NS>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+                           part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -314,18 +327,24 @@ __global__ void k_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_bl
 // host launchers
 // ---------------------------------------------------------------------------
 size_t fused_smem_bytes(const CtrlParams &p, int blk) {
+  if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples);
   const bool regen = blk == kFusedBlockRegen;
   return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen);
 }
 
-int fused_block_size(const CtrlParams &p) {
+int fused_block_size(int sys, const CtrlParams &p) {
+  if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && fused_smem_bytes(p, kFusedBlockCarWs) <= kFusedSmemLimit)
+    return kFusedBlockCarWs;
   if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;
   if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
   if (fused_smem_bytes(p, kFusedBlockRegen) <= kFusedSmemLimit) return kFusedBlockRegen;
   return 0;
 }
 
-int fused_block_samples(int blk) { return blk == kFusedBlockRegen ? kFusedBlockLarge : blk; }
+int fused_block_samples(int blk) {
+  if (blk == kFusedBlockCarWs) return kWsSamples;
+  return blk == kFusedBlockRegen ? kFusedBlockLarge : blk;
+}
 
 template <class Sys, int BLK, bool REGEN>
 static cudaError_t launch_fused_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
@@ -345,11 +364,21 @@ static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const float *x
   return cudaErrorInvalidValue;
 }
 
+static cudaError_t launch_car_ws(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
+                                 float *ps, BlockPartial *part, cudaStream_t s) {
+  const size_t smem = car_ws_smem_bytes(p.T, kWsSamples);
+  const int grid = (p.K + kWsSamples - 1) / kWsSamples;
+  k_rollout_car_ws<kWsSamples><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, ps, part);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
                                  const float *U, float *S, float *part_sums, BlockPartial *part, cudaStream_t s) {
   switch (sys) {
     case 0: return launch_fused_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, s);
-    case 1: return launch_fused_sys<Car>(blk, p, x0, st, U, S, part_sums, part, s);
+    case 1:
+      if (blk == kFusedBlockCarWs) return launch_car_ws(p, x0, st, U, S, part_sums, part, s);
+      return launch_fused_sys<Car>(blk, p, x0, st, U, S, part_sums, part, s);
     case 2: return launch_fused_sys<Quad>(blk, p, x0, st, U, S, part_sums, part, s);
     default: return cudaErrorInvalidValue;
   }
@@ -365,6 +394,7 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, true>),
+      reinterpret_cast<const void *>(k_rollout_car_ws<kWsSamples>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, true>),

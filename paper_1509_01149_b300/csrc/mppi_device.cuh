@@ -42,9 +42,12 @@ __device__ __forceinline__ float unit_uniform(uint32_t w) {
   return (static_cast<float>(w >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
 }
 
-// Box-Muller on one pair of words: rad = sqrt(-2 ln ua), angle 2 pi ub.
+// Box-Muller on one pair of words: rad = sqrt(-2 ln ua), angle 2 pi ub.  The radicand is at
+// least 2^-23 (ua <= 1 - 2^-24), a normal number, so the square root is taken as s * rsqrt(s)
+// (a few ulp, no special-case branch).
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &e0, float &e1) {
-  const float rad = sqrtf(-2.0f * logf(unit_uniform(wa)));
+  const float s2 = -2.0f * logf(unit_uniform(wa));
+  const float rad = s2 * rsqrtf(s2);
   float s, c;
   sincospif(2.0f * unit_uniform(wb), &s, &c);
   e0 = rad * c;

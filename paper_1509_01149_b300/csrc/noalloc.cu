@@ -203,7 +203,7 @@ extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float n
     }
   }
 
-  const int blk = fused_block_size(p);
+  const int blk = fused_block_size(sys, p);
   if (blk == 0) return fail(MPPI_EINVAL, "T*m too large for the fused rollout's shared memory");
   const int nblk = (K + fused_block_samples(blk) - 1) / fused_block_samples(blk);
   const size_t TM = static_cast<size_t>(T) * m;

@@ -75,8 +75,10 @@ __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, in
 //   eta_b = sum_k w_k (FP64), part_sums[i*M+j] = sum_k w_k du_{i,j,k} (FP32)
 // with du from shared memory (STORE: sDu [T*M][BLK]) or regenerated (REGEN).
 // Non-finite costs and samples k >= K count as +inf (weight 0); k == INT_MAX marks a thread
-// that owns no sample (it only takes part in the block reduction).
-template <int M, int BLK, bool REGEN>
+// that owns no sample (it only takes part in the block reduction).  BLK is the thread count;
+// in STORE mode threads 0..NS-1 own the NS samples of sDu's columns (NS = BLK unless some
+// threads hold no sample).
+template <int M, int BLK, bool REGEN, int NS = BLK>
 __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32_t ctr, float Sk_raw, const float *Lnu,
                                               float *__restrict__ S_out, float *__restrict__ part_sums,
                                               BlockPartial *__restrict__ part, float *sW, const float *sDu) {
@@ -111,19 +113,35 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
   __syncthreads();
   const float rho_b = s_min[0];
   const float w = (isfinite(rho_b) && isfinite(Sk)) ? expf(-(Sk - rho_b) * p.inv_lambda) : 0.0f;
-  const double e = warp_sum_d(static_cast<double>(w));
+  // (warps whose threads own no sample skip the FP64 shuffles)
+  const double e = __any_sync(0xffffffffu, k != INT_MAX) ? warp_sum_d(static_cast<double>(w)) : 0.0;
   if (lane == 0) s_eta[warp] = e;
 
   if (!REGEN) {
-    sW[tid] = w;
+    static_assert(NS % 32 == 0 && NS <= BLK, "samples per block");
+    constexpr int CPL = NS / 32;  // samples per lane
+    if (tid < NS) sW[tid] = w;
     __syncthreads();
-    // warp per output, lanes over the block's samples (FP32)
-    for (int o = warp; o < TM; o += NW) {
-      float acc = 0.0f;
+    // warp per 32 outputs: lane l sums its CPL samples of each output (conflict-free rows of
+    // sDu), then the transposed butterfly leaves output g*32 + l's block sum in lane l (FP32)
+    float wl[CPL];
 #pragma unroll
-      for (int c = 0; c < BLK / 32; ++c) acc = fmaf(sW[lane + 32 * c], sDu[o * BLK + lane + 32 * c], acc);
-      acc = warp_sum_f(acc);
-      if (lane == 0) part_sums[o] = acc;
+    for (int c = 0; c < CPL; ++c) wl[c] = sW[lane + 32 * c];
+    for (int g = warp; g * 32 < TM; g += NW) {
+      float v[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int o = g * 32 + q;
+        float acc = 0.0f;
+        if (o < TM) {
+#pragma unroll
+          for (int c = 0; c < CPL; ++c) acc = fmaf(wl[c], sDu[o * NS + lane + 32 * c], acc);
+        }
+        v[q] = acc;
+      }
+      const float tot = transpose_reduce32(v);
+      const int o = g * 32 + lane;
+      if (o < TM) part_sums[o] = tot;
     }
   } else {
     const int nb = (TM + 3) >> 2;

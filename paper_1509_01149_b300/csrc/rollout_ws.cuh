@@ -1,0 +1,255 @@
+// Car rollout with each sample's work split over three threads in different warps
+// (warp specialisation).
+//
+// With one thread per sample, K = 16384 samples make 512 warps: at most one per SM
+// sub-partition, so every dependency latency of the step is exposed.  The car step
+// separates into
+//   the velocity recurrence (vx, vy, r, delta): slip angles, tyre forces and the steering
+//       actuator; it reads only itself and the control v_i = u_i + du_i;
+//   the pose sums (X, Y, psi), the cost map and the importance-sampling terms, which read
+//       the velocities and du but never feed back into them;
+//   the noise du_i, which depends on nothing of the state.
+// A CTA owns NS samples with 3 NS threads in three warp-uniform roles:
+//   core  (threads 0..NS-1)      the recurrence;
+//   noise (threads NS..2NS-1)    Philox normals -> du = sqrt(nu) L eps, ahead of the core;
+//   pose  (threads 2NS..3NS-1)   pose, q(x), IS terms and S~ (Kahan), in the same order
+//                                and arithmetic as the one-thread kernel.
+// Shared memory carries the hand-offs, in chunks of C steps:
+//   du  [T*M][NS]      noise -> core and pose, one single-use mbarrier per chunk (also the
+//                      operand of the block sums)
+//   vel [R][C][3][NS]  core -> pose, (vx, vy, r) after each step, a ring of R chunks with
+//                      full/empty mbarriers
+// Every wait is bounded; a thread whose wait runs out stops and its sample's cost is +inf.
+#pragma once
+#include <type_traits>
+
+#include "rollout_body.cuh"
+#include "tc_common.cuh"
+
+namespace mppi {
+
+constexpr int kWsSamples = 128;   // samples per CTA (3x threads)
+constexpr int kWsRoles = 3;
+constexpr int kWsChunk = 8;       // steps per hand-off
+constexpr int kWsRing = 4;        // chunks in the velocity ring
+constexpr int kWsMaxChunks = 32;  // noise barriers: T <= kWsChunk * kWsMaxChunks
+
+__host__ __device__ inline size_t car_ws_smem_bytes(int T, int ns) {
+  const size_t TM = 2 * static_cast<size_t>(T);
+  return sizeof(float) * (2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
+                          static_cast<size_t>(kWsRing) * kWsChunk * 3 * ns);
+}
+
+template <int NS>
+__device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
+                                                     const float *__restrict__ U, int k0, float *__restrict__ S_out,
+                                                     float *__restrict__ part_sums, BlockPartial *__restrict__ part,
+                                                     float *smem) {
+  static_assert(NS % 32 == 0, "roles must be warp-uniform");
+  constexpr int M = 2, C = kWsChunk, R = kWsRing, NT = kWsRoles * NS;
+  __shared__ uint64_t bar_noise[kWsMaxChunks], bar_full[R], bar_empty[R];
+  const int T = p.T, TM = T * M, tid = threadIdx.x;
+  const int nch = (T + C - 1) / C;
+  float *sU = smem;         // [TM]  nominal controls
+  float *sRu = sU + TM;     // [TM]  R u_i
+  float *sHu = sRu + TM;    // [T]   1/2 u_i^T R u_i
+  float *sW = sHu + T;      // [NS]  weights
+  float *sS = sW + NS;      // [NS]  path costs (pose -> owner of the block partial)
+  float *sDu = sS + NS;     // [TM][NS] perturbations
+  float *sVel = sDu + static_cast<size_t>(TM) * NS;  // [R][C][3][NS]
+
+  for (int o = tid; o < TM; o += NT) sU[o] = U[o];
+  if (tid == 0) {
+    for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], NS);
+    for (int r = 0; r < R; ++r) {
+      tc::mbar_init(&bar_full[r], NS);
+      tc::mbar_init(&bar_empty[r], NS);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < T; i += NT) {
+    float h = 0.0f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float ru = 0.0f;
+#pragma unroll
+      for (int l = 0; l < M; ++l) ru = fmaf(p.R[j * M + l], sU[i * M + l], ru);
+      sRu[i * M + j] = ru;
+      h = fmaf(sU[i * M + j], ru, h);
+    }
+    sHu[i] = 0.5f * h;
+  }
+  __syncthreads();
+
+  const int role = tid / NS;
+  const int slot = tid - role * NS;
+  const int k = k0 + slot;
+  bool ok = true;
+
+  // Each role runs whole chunks through one fully unrolled body (one basic block, so the
+  // compiler can interleave the steps) and the ragged last chunk through a small rolled
+  // loop: three roles share each sub-partition's instruction cache.
+  if (role == 0) {
+    // ---- core: the velocity recurrence ----------------------------------------------
+    float xv[4] = {x0[3], x0[4], x0[5], x0[6]};
+    for (int c = 0; c < nch; ++c) {
+      ok = tc::mbar_wait(&bar_noise[c], 0u);
+      if (ok && c >= R) ok = tc::mbar_wait(&bar_empty[c % R], static_cast<uint32_t>((c / R - 1) & 1));
+      if (!ok) break;
+      float *vel = sVel + (c % R) * (C * 3 * NS);
+      const int i0 = c * C;
+      if (i0 + C <= T) {
+        // the controls of all C steps first: the compiler cannot move a shared load above
+        // the velocity stores of earlier steps
+        float vv[C][M];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const int i = i0 + j;
+          vv[j][0] = sU[i * M] + sDu[(i * M) * NS + slot];
+          vv[j][1] = sU[i * M + 1] + sDu[(i * M + 1) * NS + slot];
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          Car::vel_step(xv, vv[j], p.dt);
+          vel[(3 * j) * NS + slot] = xv[0];
+          vel[(3 * j + 1) * NS + slot] = xv[1];
+          vel[(3 * j + 2) * NS + slot] = xv[2];
+        }
+      } else {
+#pragma unroll 1
+        for (int j = 0; j < T - i0; ++j) {
+          const int i = i0 + j;
+          const float v[M] = {sU[i * M] + sDu[(i * M) * NS + slot], sU[i * M + 1] + sDu[(i * M + 1) * NS + slot]};
+          Car::vel_step(xv, v, p.dt);
+          vel[(3 * j) * NS + slot] = xv[0];
+          vel[(3 * j + 1) * NS + slot] = xv[1];
+          vel[(3 * j + 2) * NS + slot] = xv[2];
+        }
+      }
+      tc::mbar_arrive(&bar_full[c % R]);
+    }
+  } else if (role == 1) {
+    // ---- noise: du of chunk c into sDu (block b of the generator covers steps 2b, 2b+1) --
+    float Lnu[M * M];
+#pragma unroll
+    for (int a = 0; a < M * M; ++a) Lnu[a] = p.Lnu[a];
+    auto block = [&](int b) {  // Philox block b -> du of steps 2b and 2b+1 (those < T)
+      float e[4];
+      normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, e);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const int i = 2 * b + s;
+        float du[M];
+        scale_noise<M>(Lnu, e + s * M, du);
+        if (i < T) {
+#pragma unroll
+          for (int a = 0; a < M; ++a) sDu[(i * M + a) * NS + slot] = du[a];
+        }
+      }
+    };
+    for (int c = 0; c < nch; ++c) {
+      const int b0 = c * (C / 2);
+      if ((c + 1) * C <= T) {
+#pragma unroll
+        for (int q = 0; q < C / 2; ++q) block(b0 + q);
+      } else {
+#pragma unroll 1
+        for (int b = b0; 2 * b < T; ++b) block(b);
+      }
+      tc::mbar_arrive(&bar_noise[c]);
+    }
+  } else {
+    // ---- pose: heading and position sums, q(x), IS terms, S~ ------------------------
+    const Env env = make_env(p, nullptr);
+    float Rm[M * M];
+#pragma unroll
+    for (int a = 0; a < M * M; ++a) Rm[a] = p.R[a];
+    float X = x0[0], Y = x0[1], psi = x0[2], vx = x0[3], vy = x0[4], r = x0[5];
+    Car::Aux aux;
+    aux.cX = aux.cY = aux.cpsi = 0.0f;
+    KahanSum S;
+    auto is_term = [&](int i) {  // importance-sampling running term of step i
+      float du[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a) du[a] = sDu[(i * M + a) * NS + slot];
+      float duRdu = 0.0f, uRdu = 0.0f;
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        uRdu = fmaf(sRu[i * M + a], du[a], uRdu);
+        float rd = 0.0f;
+#pragma unroll
+        for (int l = 0; l < M; ++l) rd = fmaf(Rm[a * M + l], du[l], rd);
+        duRdu = fmaf(du[a], rd, duRdu);
+      }
+      return p.is_du * duRdu + uRdu + sHu[i];
+    };
+    // S~ gains q(x_{i+1}) + is_i one step late (the cost-map loads of a step are issued
+    // before they are needed).  The pending term starts as an exact zero, whose Kahan
+    // addition leaves the sum unchanged, so no step needs a first-step test.
+    Car::Pending pend{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float pend_is = 0.0f;
+    for (int c = 0; c < nch; ++c) {
+      // the noise wait is already satisfied (the core waited on it before publishing this
+      // chunk); taking it here makes the du writes visible to this thread directly
+      ok = tc::mbar_wait(&bar_full[c % R], static_cast<uint32_t>((c / R) & 1)) && tc::mbar_wait(&bar_noise[c], 0u);
+      if (!ok) break;
+      const float *vel = sVel + (c % R) * (C * 3 * NS);
+      const int i0 = c * C;
+      if (i0 + C <= T) {
+        float nv[C][3], is[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          nv[j][0] = vel[(3 * j) * NS + slot];
+          nv[j][1] = vel[(3 * j + 1) * NS + slot];
+          nv[j][2] = vel[(3 * j + 2) * NS + slot];
+        }
+        tc::mbar_arrive(&bar_empty[c % R]);
+#pragma unroll
+        for (int j = 0; j < C; ++j) is[j] = is_term(i0 + j);
+        // all C poses and their map loads first, then the C cost additions in step order
+        Car::Pending pq[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          Car::pose_step(X, Y, psi, aux, vx, vy, r, p.dt);
+          vx = nv[j][0];
+          vy = nv[j][1];
+          r = nv[j][2];
+          const float xq[Car::N] = {X, Y, psi, vx, vy, r, 0.0f};
+          pq[j] = Car::cost_issue(xq, aux, env);
+        }
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          S.add(Car::cost_finish(pend, env) + pend_is);
+          pend = pq[j];
+          pend_is = is[j];
+        }
+      } else {
+#pragma unroll 1
+        for (int j = 0; j < T - i0; ++j) {
+          Car::pose_step(X, Y, psi, aux, vx, vy, r, p.dt);
+          vx = vel[(3 * j) * NS + slot];
+          vy = vel[(3 * j + 1) * NS + slot];
+          r = vel[(3 * j + 2) * NS + slot];
+          S.add(Car::cost_finish(pend, env) + pend_is);
+          const float xq[Car::N] = {X, Y, psi, vx, vy, r, 0.0f};
+          pend = Car::cost_issue(xq, aux, env);
+          pend_is = is_term(i0 + j);
+        }
+        tc::mbar_arrive(&bar_empty[c % R]);
+      }
+    }
+    if (ok) {
+      S.add(Car::cost_finish(pend, env) + pend_is);
+      const float xq[Car::N] = {X, Y, psi, vx, vy, r, 0.0f};
+      S.add(Car::cost(xq, aux, env));  // phi(x_T) = q(x_T)
+    }
+    sS[slot] = ok ? S.s : INFINITY;
+  }
+  __syncthreads();
+  const bool owner = role == 0;
+  float Lnu_unused[M * M] = {0.0f, 0.0f, 0.0f, 0.0f};
+  block_partial<M, NT, false, NS>(p, owner ? k : INT_MAX, ctr, owner ? sS[tid] : INFINITY, Lnu_unused, S_out,
+                                  part_sums, part, sW, sDu);
+}
+
+}  // namespace mppi

@@ -104,28 +104,54 @@ struct Car {
 
   __device__ __forceinline__ static void init(const float *, Aux &a, const Env &) { a.cX = a.cY = a.cpsi = 0.0f; }
 
-  __device__ __forceinline__ static void deriv(const float x[N], const float v[M], float d[N]) {
-    const float vx = x[3], vy = x[4], r = x[5], delta = x[6];
-    // The tyre-force sines have arguments |C atan(.)| <= 1.8 pi/2 < pi and the steering
-    // angle stays small, where the special-function-unit sine/cosine are accurate to about
-    // 2^-21 absolute: they run as single SFU operations with no slow-path branch, which
-    // keeps the two tyre chains interleavable.  The heading (unbounded) keeps sincosf.
+  // The step splits into the velocity recurrence (vx, vy, r, delta), which depends only on
+  // itself and the control, and the pose rates (X, Y, psi), which read the velocities but
+  // never feed back into them.
+  //
+  // The tyre-force sines have arguments |C atan(.)| <= 1.8 pi/2 < pi and the steering
+  // angle stays small, where the special-function-unit sine/cosine are accurate to about
+  // 2^-21 absolute: they run as single SFU operations with no slow-path branch, which
+  // keeps the two tyre chains interleavable.
+  __device__ __forceinline__ static void deriv_vel(float vx, float vy, float r, float delta, const float v[M],
+                                                   float d[4]) {
     const float inv_vxs = __fdividef(1.0f, fmaxf(vx, vx_floor));
     const float alpha_f = delta - atanf((vy + lf * r) * inv_vxs);
     const float alpha_r = -atanf((vy - lr * r) * inv_vxs);
     const float Fyf = Df * __sinf(C * atanf(B * alpha_f));
     const float Fyr = Dr * __sinf(C * atanf(B * alpha_r));
     const float Fx = Cm * v[1] - Crr * vx - Cd * vx * fabsf(vx);
-    float sp, cp, sd, cd;
-    sincosf(x[2], &sp, &cp);
+    float sd, cd;
     __sincosf(delta, &sd, &cd);
-    d[0] = vx * cp - vy * sp;
-    d[1] = vx * sp + vy * cp;
-    d[2] = r;
-    d[3] = (Fx - Fyf * sd) * (1.0f / m) + vy * r;
-    d[4] = (Fyr + Fyf * cd) * (1.0f / m) - vx * r;
-    d[5] = (lf * Fyf * cd - lr * Fyr) * (1.0f / Iz);
-    d[6] = (delta_max * v[0] - delta) * (1.0f / tau_delta);
+    d[0] = (Fx - Fyf * sd) * (1.0f / m) + vy * r;
+    d[1] = (Fyr + Fyf * cd) * (1.0f / m) - vx * r;
+    d[2] = (lf * Fyf * cd - lr * Fyr) * (1.0f / Iz);
+    d[3] = (delta_max * v[0] - delta) * (1.0f / tau_delta);
+  }
+  // The heading is unbounded: it is first reduced to [-pi, pi] by the two-constant
+  // Cody-Waite scheme (k = nearest integer to psi / 2 pi; psi - k hi - k lo with
+  // hi + lo = 2 pi, hi the nearest float), then its sine and cosine run on the SFU
+  // (about 2^-21 absolute on the reduced range).  No slow-path branch, so the pose
+  // updates of consecutive steps interleave.
+  __device__ __forceinline__ static void sincos_heading(float psi, float &s, float &c) {
+    constexpr float two_pi_hi = 6.28318548202514648f;
+    constexpr float two_pi_lo = -1.7484556025237907e-07f;
+    constexpr float inv_two_pi = 0.159154943091895336f;
+    const float kk = rintf(psi * inv_two_pi);
+    float red = fmaf(-kk, two_pi_hi, psi);
+    red = fmaf(-kk, two_pi_lo, red);
+    __sincosf(red, &s, &c);
+  }
+  __device__ __forceinline__ static void pose_rates(float psi, float vx, float vy, float &dX, float &dY) {
+    float sp, cp;
+    sincos_heading(psi, sp, cp);
+    dX = vx * cp - vy * sp;
+    dY = vx * sp + vy * cp;
+  }
+
+  __device__ __forceinline__ static void deriv(const float x[N], const float v[M], float d[N]) {
+    pose_rates(x[2], x[3], x[4], d[0], d[1]);
+    d[2] = x[5];
+    deriv_vel(x[3], x[4], x[5], x[6], v, d + 3);
   }
 
   // x += h with the running compensation c (Kahan): keeps the rounding of x out of the sum.
@@ -144,6 +170,22 @@ struct Car {
     comp_add(x[2], a.cpsi, dt * d[2]);
 #pragma unroll
     for (int i = 3; i < N; ++i) x[i] += dt * d[i];
+  }
+  // The two halves of step() on their own (same arithmetic): xv = (vx, vy, r, delta).
+  __device__ __forceinline__ static void vel_step(float xv[4], const float v[M], float dt) {
+    float d[4];
+    deriv_vel(xv[0], xv[1], xv[2], xv[3], v, d);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xv[i] += dt * d[i];
+  }
+  // pose (X, Y, psi) over one step from the velocities (vx, vy, r) at the step's start
+  __device__ __forceinline__ static void pose_step(float &X, float &Y, float &psi, Aux &a, float vx, float vy, float r,
+                                                   float dt) {
+    float dX, dY;
+    pose_rates(psi, vx, vy, dX, dY);
+    comp_add(X, a.cX, dt * dX);
+    comp_add(Y, a.cY, dt * dY);
+    comp_add(psi, a.cpsi, dt * r);
   }
 
   __device__ __forceinline__ static float cost(const float x[N], const Aux &, const Env &e) {
