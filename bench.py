@@ -71,11 +71,21 @@ def parse():
     return ap.parse_args()
 
 
-def source_hash():
+def source_hash(names=None):
+    """sha256 prefix of the CUDA sources (all of csrc/, or the named files in it)."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1509_01149_b300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_1509_01149_b300", "csrc")
+    paths = [os.path.join(csrc, n) for n in names] if names else sorted(glob.glob(os.path.join(csrc, "*")))
+    for p in paths:
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
+
+
+# device code of each profiled kernel (a capture stays valid while these files are unchanged)
+KERNEL_SOURCES = {
+    "rollout_car_ws_k16384": ["rollout_ws.cuh", "rollout_body.cuh", "systems.cuh", "mppi_device.cuh",
+                              "tc_common.cuh"],
+}
 
 
 # ---------------------------------------------------------------------------
@@ -330,7 +340,7 @@ def load_traffic(kernel_tag: str):
         d = json.load(open(p))
     except Exception:
         return None
-    if d.get("source_hash") != source_hash():
+    if d.get("source_hash") != source_hash(KERNEL_SOURCES.get(kernel_tag)):
         return None
     return d.get("dram_bytes_per_launch")
 
