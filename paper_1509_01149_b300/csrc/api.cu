@@ -694,8 +694,14 @@ int mppi_iterate_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
     cudaGraph_t g = nullptr;
     MPPI_TRY(c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
     int rc = launch_rollout(c, d_state, c->stream);
-    if (rc == MPPI_OK) rc = launch_update(c, u0, c->stream);
-    if (rc == MPPI_OK) rc = c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+    if (rc == MPPI_OK && merge_shift_fusable(c->p)) {
+      rc = c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0, c->d_dU, c->d_dbg,
+                                             c->d_uinit, c->d_st, c->stream),
+                   "merge + shift launch");
+    } else {
+      if (rc == MPPI_OK) rc = launch_update(c, u0, c->stream);
+      if (rc == MPPI_OK) rc = c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+    }
     const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
     if (rc != MPPI_OK || rc_end != MPPI_OK) {
       if (g) cudaGraphDestroy(g);

@@ -51,14 +51,32 @@ __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlP
 }
 
 // ---------------------------------------------------------------------------
-// FP64 merge of block partials + update of U
+// FP64 merge of block partials + update of U (+ the shift, fused, in one cluster)
 // ---------------------------------------------------------------------------
+namespace {
+constexpr int kMergePrefetch = 16;  // block partials per thread loaded before the reductions
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+}  // namespace
+
+// One CTA per 32 outputs (i, j).  All loads of the CTA (its lanes' block partials and the
+// first kMergePrefetch block sums of each lane) are issued first, so their latency is paid
+// once; then rho/kstar (argmin), the FP64 block scales and eta, and the FP64 weighted sum.
+// SHIFT: the grid is one thread-block cluster (all outputs in <= 8 CTAs); after the update
+// the cluster barrier makes every CTA's new U visible, each CTA reads its shifted values,
+// a second barrier separates those reads from the in-place writes, and CTA 0 advances the
+// iteration counter (Algorithm 1's shift, otherwise a kernel of its own).
+template <bool SHIFT>
 __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM, int m, float inv_lambda,
                                                                 const float *__restrict__ part_sums,
                                                                 const BlockPartial *__restrict__ part,
                                                                 float *__restrict__ U, float *__restrict__ u0_out,
                                                                 float *__restrict__ dU_dbg,
-                                                                StepDebug *__restrict__ dbg) {
+                                                                StepDebug *__restrict__ dbg,
+                                                                const float *__restrict__ u_init,
+                                                                CtrlState *__restrict__ st) {
   // B300 runs FP64 at a small fraction of the FP32 rate, so the FP64 work here is laid
   // out for short dependency chains: 4 independent accumulators per lane, a 3-level tree
   // across warps, one division (1/eta) per CTA.
@@ -70,10 +88,21 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   __shared__ double s_acc[NW][kMergeOutputs];
   __shared__ double s_inv_eta;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int o = blockIdx.x * kMergeOutputs + lane;
 
-  float v = INFINITY;
-  int idx = INT_MAX;
-  for (int b = tid; b < nblk; b += kMergeThreads) {
+  // loads first: this thread's block partial (b = tid) and its lane's first block sums
+  BlockPartial mine{0.0, INFINITY, INT_MAX};
+  if (tid < nblk) mine = part[tid];
+  float pre[kMergePrefetch];
+#pragma unroll
+  for (int j = 0; j < kMergePrefetch; ++j) {
+    const int b = warp + j * NW;
+    pre[j] = (o < TM && b < nblk) ? part_sums[static_cast<size_t>(b) * TM + o] : 0.0f;
+  }
+
+  float v = mine.rho;
+  int idx = mine.kstar;
+  for (int b = tid + kMergeThreads; b < nblk; b += kMergeThreads) {
     const float r = part[b].rho;
     const int kk = part[b].kstar;
     if (r < v || (r == v && kk < idx)) {
@@ -100,7 +129,13 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   const float rho = s_rho[0];
 
   double e = 0.0;
-  for (int b = tid; b < nblk; b += kMergeThreads) {
+  if (tid < nblk) {
+    const double sc =
+        (isfinite(rho) && isfinite(mine.rho)) ? static_cast<double>(expf(-(mine.rho - rho) * inv_lambda)) : 0.0;
+    s_scale[tid] = sc;
+    e = sc * mine.eta;
+  }
+  for (int b = tid + kMergeThreads; b < nblk; b += kMergeThreads) {
     const float rb = part[b].rho;
     const double sc = (isfinite(rho) && isfinite(rb)) ? static_cast<double>(expf(-(rb - rho) * inv_lambda)) : 0.0;
     s_scale[b] = sc;
@@ -121,10 +156,17 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
     }
   }
 
-  const int o = blockIdx.x * kMergeOutputs + lane;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+  for (int j = 0; j < kMergePrefetch; j += 4) {
+    const int b = warp + j * NW;
+    if (b < nblk) a0 += s_scale[b] * static_cast<double>(pre[j]);
+    if (b + NW < nblk) a1 += s_scale[b + NW] * static_cast<double>(pre[j + 1]);
+    if (b + 2 * NW < nblk) a2 += s_scale[b + 2 * NW] * static_cast<double>(pre[j + 2]);
+    if (b + 3 * NW < nblk) a3 += s_scale[b + 3 * NW] * static_cast<double>(pre[j + 3]);
+  }
   if (o < TM) {
-    int b = warp;
+    int b = warp + kMergePrefetch * NW;
     for (; b + 3 * NW < nblk; b += 4 * NW) {
       a0 += s_scale[b] * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
       a1 += s_scale[b + NW] * static_cast<double>(part_sums[static_cast<size_t>(b + NW) * TM + o]);
@@ -146,6 +188,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
     U[o] = un;
     dU_dbg[o] = static_cast<float>(du);
     if (o < m) u0_out[o] = un;
+  }
+  if (SHIFT) {
+    cluster_sync_all();  // every CTA's updated U visible to the cluster
+    float sh = 0.0f;
+    if (warp == 0 && o < TM) sh = (o + m < TM) ? U[o + m] : u_init[o - (TM - m)];
+    cluster_sync_all();  // all shifted values read before any is overwritten
+    if (warp == 0 && o < TM) U[o] = sh;
+    if (blockIdx.x == 0 && tid == 0) st->counter += 1u;
   }
 }
 
@@ -398,7 +448,8 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, true>),
-      reinterpret_cast<const void *>(k_merge_update),
+      reinterpret_cast<const void *>(k_merge_update<false>),
+      reinterpret_cast<const void *>(k_merge_update<true>),
   };
   for (const void *f : fns) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -412,9 +463,37 @@ cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part
   const int TM = p.T * p.m;
   const size_t smem = sizeof(double) * static_cast<size_t>(nblk);
   const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
-  k_merge_update<<<grid, kMergeThreads, smem, s>>>(nblk, TM, p.m, p.inv_lambda, part_sums, part, U, u0_out, dU_dbg,
-                                                    dbg);
+  k_merge_update<false><<<grid, kMergeThreads, smem, s>>>(nblk, TM, p.m, p.inv_lambda, part_sums, part, U, u0_out,
+                                                          dU_dbg, dbg, nullptr, nullptr);
   return cudaGetLastError();
+}
+
+bool merge_shift_fusable(const CtrlParams &p) {
+  return (p.T * p.m + kMergeOutputs - 1) / kMergeOutputs <= kMergeClusterMax;
+}
+
+cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
+                                      float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
+                                      CtrlState *st, cudaStream_t s) {
+  const int TM = p.T * p.m;
+  const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
+  if (grid > kMergeClusterMax) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kMergeThreads, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(double) * static_cast<size_t>(nblk);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = grid;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int m = p.m;
+  const float il = p.inv_lambda;
+  return cudaLaunchKernelEx(&cfg, k_merge_update<true>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,
+                            u_init, st);
 }
 
 cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s) {

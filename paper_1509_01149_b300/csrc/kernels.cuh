@@ -35,6 +35,13 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
 // Cross-block FP64 merge: rho, kstar, eta, du; U += du; u0 out.
 cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                 float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s);
+// The merge and the shift of Algorithm 1 in one launch (a thread-block cluster of one CTA
+// per 32 outputs), when the outputs fit in kMergeClusterMax CTAs.
+constexpr int kMergeClusterMax = 8;
+bool merge_shift_fusable(const CtrlParams &p);
+cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
+                                      float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
+                                      CtrlState *st, cudaStream_t s);
 // Shift of Algorithm 1 and iteration counter increment.
 cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s);
 
