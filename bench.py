@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-dynamics measurement")
     ap.add_argument("--learned-only", action="store_true")
+    ap.add_argument("--learned-train", type=int, default=10_000_000, help="training transitions")
+    ap.add_argument("--learned-steps", type=int, default=6000, help="training steps")
     return ap.parse_args()
 
 
@@ -357,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps({"serving": run_serving(levels, args.serving_ticks)}), flush=True)
         return
     if args.learned_only:
-        print(json.dumps({"learned": run_learned()}), flush=True)
+        print(json.dumps({"learned": run_learned(args.learned_train, steps=args.learned_steps)}), flush=True)
         return
     dist = None
     if world > 1:
@@ -471,7 +473,7 @@ def run_ours(args, rank, world, local_rank):
     pctrl.close()
 
     serving_res = run_serving(levels, args.serving_ticks, seed=rank) if levels else None
-    learned_res = None if args.no_learned else run_learned()
+    learned_res = None if args.no_learned else run_learned(args.learned_train, steps=args.learned_steps)
 
     if rank != 0:
         if dist is not None:

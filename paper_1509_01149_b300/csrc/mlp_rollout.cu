@@ -1,24 +1,31 @@
 // Fused MPPI rollout with the learned car dynamics on the tensor cores (sm_103a).
 //
-// One CTA of 256 threads owns 128 samples: thread t < 128 holds sample k0 + t (TMEM lane t,
-// row t of every activation tile); in the hidden-layer epilogues warps w and w + 4 share TMEM
-// lane quadrant w % 4 and take column halves [0, 128) and [128, 256).  The network weights are copied once into shared memory
-// in the K-major core-matrix layout; TMEM holds the FP32 accumulators (columns 0..255
-// for the two hidden layers, 256..271 for the output layer).  Per time step:
-//   noise du_i (Philox), v = u_i + du_i, features z(x, v) -> X tile (BF16)
-//   MMA  D = X W1^T       (M=128, N=256, K=16)   -> tanh(D + b1) -> H (BF16, smem)
-//   MMA  D = H W2^T       (M=128, N=256, K=256)  -> tanh(D + b2) -> H
-//   MMA  D3 = H W3^T      (M=128, N=16,  K=256)  -> x += (D3 + b3) * out_scale  (FP32)
-//   S~ += q(x) + IS running cost (Kahan FP32)
-// tanh runs on the special-function unit (its error, ~2^-11, is below the BF16 step of
-// the activations it feeds).  After the horizon the block forms its softmax partial with
-// du regenerated from the counter-based generator (shared memory is full of weights).
-// Every mbarrier wait is bounded; on a timeout the kernel flags the error, waits once
-// more (bounded) for its MMAs, frees its TMEM and returns.
+// One CTA owns 128 samples (the MMA tile's M) with nine warps:
+//   epilogue warps 0..7  warp w reads TMEM lane quadrant w % 4 (rows 32 (w % 4) .. +31) and
+//                        the column half (w / 4) * 128 of each hidden layer, 32 columns at
+//                        a time; threads 0..127 also own one sample each (noise, features,
+//                        state update, cost);
+//   MMA warp 8           one thread issues every tcgen05.mma and commit.
+// The weights are copied once into shared memory in the K-major core-matrix layout.  TMEM
+// (512 columns) holds the FP32 accumulators: layer 1 in columns 0..255, layer 2 in
+// 256..511, the output layer in 0..15.  Per time step:
+//   owners: noise du_i (Philox), v = u_i + du_i, features z(x, v) -> X tile    [bar_x]
+//   MMA  D1 = X W1^T  (M=128, N=256, K=16)                                     [bar_l1]
+//   epilogue 1: H[:, 32 c .. 32 c + 31] = tanh(D1 + b1) chunk by chunk        [hb[c]]
+//   MMA  D2 = H W2^T, one 32-deep K chunk as soon as its H chunk is written    [bar_l2]
+//   epilogue 2: H = tanh(D2 + b2) chunk by chunk (H overwritten in place)      [hb[c]]
+//   MMA  D3 = H W3^T  (N=16), again one K chunk per H chunk                    [bar_l3]
+//   owners: x += (D3 + b3) * out_scale, S~ += q(x) + IS running cost (Kahan FP32, the
+//           cost-map loads of a step finished during the next step)
+// so the second and third products run under the epilogues (tanh on the special-function
+// unit) instead of after them.  tanh.approx's error (~2^-11) is below the BF16 step of the
+// activations it feeds.  After the horizon the block forms its softmax partial with du
+// regenerated from the counter-based generator (shared memory is full of weights).
+// Every mbarrier wait is bounded; a thread whose wait runs out stops waiting, the kernel
+// flags the error, the MMA thread drains its MMAs (bounded) and TMEM is freed.
 // FP8 variant (kind::f8f6f4): weights, features and hidden activations in E4M3 (weights
 // with a per-tensor scale s_l, so a layer's pre-activation is s_l * acc + b), K padded to
-// 32 in the first layer, one 32-deep MMA per 32 bytes of K as in BF16; the output layer
-// reuses TMEM columns 0..15.
+// 32 in the first layer, one 32-deep MMA per 32 bytes of K.
 #include <cstdint>
 #include <cuda_fp8.h>
 
@@ -30,7 +37,8 @@
 namespace mppi {
 
 namespace {
-constexpr int kMlpThreads = 256;   // 8 warps: two per TMEM lane quadrant in the epilogues
+constexpr int kMlpThreads = 288;   // 8 epilogue warps (two per TMEM lane quadrant) + 1 MMA warp
+constexpr int kMlpMmaWarp = 8;
 constexpr int kMlpSamples = 128;   // rows of the MMA tile; threads 0..127 own one sample each
 
 // Shared-memory layout (bytes) for element size E (2 = BF16, 1 = E4M3); the first layer's
@@ -45,8 +53,9 @@ struct MlpLayout {
   static constexpr uint32_t X = H + 128 * 256 * E;            // 128 x K1
   static constexpr uint32_t B = X + 128 * K1 * E;             // b1, b2, b3, out_scale, w_scale (f32)
   static constexpr uint32_t U = B + (256 + 256 + 16 + 8 + 4) * 4;  // sU, sRu, sHu (f32)
-  static constexpr uint32_t kTmemCols = E == 2 ? 512 : 256;   // E4M3: 2 CTAs may share an SM
-  static constexpr uint32_t D3 = E == 2 ? 256 : 0;            // TMEM column of the output layer
+  static constexpr uint32_t kTmemCols = 512;
+  static constexpr uint32_t D1 = 0, D2 = 256, D3 = 0;         // TMEM columns of the three products
+  static constexpr int KK = E;                                // MMAs per 32 columns of K (16-bit: K = 16 per MMA)
 };
 
 // byte offset of element (r, k) in a K-major no-swizzle tile of R rows, element size E
@@ -82,36 +91,37 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// H row `row`, columns [cbeg, cbeg + 128) = tanh(scale * D + bias) stored in the tile format,
-// D read from the same TMEM columns
+// H row `row`, columns [c0, c0 + 32) = tanh(scale * D + bias) in the tile format, D read
+// from TMEM columns taddr .. taddr + 31 of this thread's lane
 template <int E>
-__device__ __forceinline__ void hidden_epilogue(uint32_t tmem_row, const float *bias, float scale, unsigned char *smem,
-                                                int row, int cbeg) {
-#pragma unroll 1
-  for (int c0 = cbeg; c0 < cbeg + 128; c0 += 32) {
-    float v[32];
-    tmem_ld32(tmem_row + static_cast<uint32_t>(c0), v);
-    tc::tmem_ld_wait();
+__device__ __forceinline__ void hidden_chunk(uint32_t taddr, const float *bias, float scale, unsigned char *smem,
+                                             int row, int c0) {
+  float v[32];
+  tmem_ld32(taddr, v);
+  tc::tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = tc::tanh_approx(fmaf(v[j], scale, bias[c0 + j]));
-    if (E == 2) {
+  for (int j = 0; j < 32; ++j) v[j] = tc::tanh_approx(fmaf(v[j], scale, bias[c0 + j]));
+  if (E == 2) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint4 w = make_uint4(pack_bf16(v[q * 8], v[q * 8 + 1]), pack_bf16(v[q * 8 + 2], v[q * 8 + 3]),
-                                   pack_bf16(v[q * 8 + 4], v[q * 8 + 5]), pack_bf16(v[q * 8 + 6], v[q * 8 + 7]));
-        *reinterpret_cast<uint4 *>(smem + MlpLayout<E>::H + tile_offset<E>(row, c0 + q * 8, 128)) = w;
-      }
-    } else {
+    for (int q = 0; q < 4; ++q) {
+      const uint4 w = make_uint4(pack_bf16(v[q * 8], v[q * 8 + 1]), pack_bf16(v[q * 8 + 2], v[q * 8 + 3]),
+                                 pack_bf16(v[q * 8 + 4], v[q * 8 + 5]), pack_bf16(v[q * 8 + 6], v[q * 8 + 7]));
+      *reinterpret_cast<uint4 *>(smem + MlpLayout<E>::H + tile_offset<E>(row, c0 + q * 8, 128)) = w;
+    }
+  } else {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float *f = v + q * 16;
-        const uint4 w = make_uint4(pack_e4m3x4(f[0], f[1], f[2], f[3]), pack_e4m3x4(f[4], f[5], f[6], f[7]),
-                                   pack_e4m3x4(f[8], f[9], f[10], f[11]), pack_e4m3x4(f[12], f[13], f[14], f[15]));
-        *reinterpret_cast<uint4 *>(smem + MlpLayout<E>::H + tile_offset<E>(row, c0 + q * 16, 128)) = w;
-      }
+    for (int q = 0; q < 2; ++q) {
+      const float *f = v + q * 16;
+      const uint4 w = make_uint4(pack_e4m3x4(f[0], f[1], f[2], f[3]), pack_e4m3x4(f[4], f[5], f[6], f[7]),
+                                 pack_e4m3x4(f[8], f[9], f[10], f[11]), pack_e4m3x4(f[12], f[13], f[14], f[15]));
+      *reinterpret_cast<uint4 *>(smem + MlpLayout<E>::H + tile_offset<E>(row, c0 + q * 16, 128)) = w;
     }
   }
 }
+
+// order in which the MMA thread consumes the 32-column chunks of H: the two column halves
+// are written side by side (warps 0..3 and 4..7), so chunks c and c + 4 complete together
+__device__ __forceinline__ int chunk_at(int n) { return (n >> 1) + ((n & 1) << 2); }
 
 template <int E>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -132,7 +142,10 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   constexpr int M = 2, N = 7;
   using L = MlpLayout<E>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t bar;
+  // bar_x: X tile written (128 owner threads); bar_l1/l2/l3: products done (MMA commits);
+  // hb[c]: H columns 32c..32c+31 written (128 threads of one column half), twice per step;
+  // bar_drain: the MMA thread's last commit before TMEM is freed
+  __shared__ uint64_t bar_x, bar_l1, bar_l2, bar_l3, bar_drain, hb[8];
   __shared__ uint32_t tmem_base;
   const MlpDev *md = static_cast<const MlpDev *>(p.mlp);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -147,7 +160,14 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   float *sHu = sRu + TM;
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, L::kTmemCols);
-  if (tid == 0) tc::mbar_init(&bar, 1);
+  if (tid == 0) {
+    tc::mbar_init(&bar_x, kMlpSamples);
+    tc::mbar_init(&bar_l1, 1);
+    tc::mbar_init(&bar_l2, 1);
+    tc::mbar_init(&bar_l3, 1);
+    tc::mbar_init(&bar_drain, 1);
+    for (int c = 0; c < 8; ++c) tc::mbar_init(&hb[c], 128);
+  }
   // weights (already in tile layout) and biases
   {
     const uint4 *w2 = reinterpret_cast<const uint4 *>(md->w2);
@@ -187,147 +207,199 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   tc::fence_after_sync();
 
   const uint32_t tmem = tmem_base;
-  const uint32_t tmem_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
-  const int erow = 32 * (warp & 3) + (tid & 31);  // epilogue row (= sample) of this thread
-  const int ecol = (warp >> 2) * 128;             // epilogue column half
-  const bool owner = tid < kMlpSamples;
-  const uint32_t sbase = tc::smem_u32(smem);
-  const uint32_t id256 = E == 2 ? tc::idesc_bf16_f32(128, 256) : tc::idesc_e4m3_f32(128, 256);
-  const uint32_t id16 = E == 2 ? tc::idesc_bf16_f32(128, 16) : tc::idesc_e4m3_f32(128, 16);
-  const float s1 = swscale[0], s2 = swscale[1], s3 = swscale[2];
-  const Env env = make_env(p, nullptr);
-  const int k = blockIdx.x * kMlpSamples + tid;
-  float Lnu[M * M], R[M * M];
-#pragma unroll
-  for (int a = 0; a < M * M; ++a) {
-    Lnu[a] = p.Lnu[a];
-    R[a] = p.R[a];
-  }
-  float x[N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) x[a] = x0[a];
   const uint32_t ctr = st->counter;
-  KahanSum S;
-  uint32_t phase = 0;
+  const bool owner = tid < kMlpSamples;
+  const int k = blockIdx.x * kMlpSamples + tid;
+  float Lnu[M * M];
+#pragma unroll
+  for (int a = 0; a < M * M; ++a) Lnu[a] = p.Lnu[a];
   bool ok = true;
-  float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float Sk = INFINITY;
 
-  for (int i = 0; i < T && ok; ++i) {
-    if ((i & 1) == 0 && owner)
-      normals4(static_cast<uint32_t>(i >> 1), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
-    float du[M], v[M];
-    {
-      const float pair[2] = {(i & 1) ? eps[2] : eps[0], (i & 1) ? eps[3] : eps[1]};
-      scale_noise<M>(Lnu, pair, du);
-    }
-    float duRdu = 0.0f, uRdu = 0.0f;
+  if (warp == kMlpMmaWarp) {
+    // ---- MMA issue ---------------------------------------------------------------------
+    if ((tid & 31) == 0) {
+      const uint32_t sbase = tc::smem_u32(smem);
+      const uint32_t id256 = E == 2 ? tc::idesc_bf16_f32(128, 256) : tc::idesc_e4m3_f32(128, 256);
+      const uint32_t id16 = E == 2 ? tc::idesc_bf16_f32(128, 16) : tc::idesc_e4m3_f32(128, 16);
+      for (int i = 0; i < T && ok; ++i) {
+        const uint32_t ph = static_cast<uint32_t>(i & 1);
+        ok = tc::mbar_wait(&bar_x, ph);
+        if (!ok) break;
+        tc::fence_after_sync();
+        mma<E>(tmem + L::D1, tc::smem_desc(sbase + L::X, 128 * 16, 128), tc::smem_desc(sbase + L::W1, 256 * 16, 128),
+               id256, 0u);
+        tc::mma_commit(&bar_l1);
+        // layer 2: K chunk c (32 columns of H) as soon as epilogue 1 wrote it
+        for (int n = 0; n < 8 && ok; ++n) {
+          const int c = chunk_at(n);
+          ok = tc::mbar_wait(&hb[c], 0u);
+          if (!ok) break;
+          tc::fence_after_sync();
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
-      v[j] = sU[i * M + j] + du[j];
-      uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
-      float rd = 0.0f;
+          for (int q = 0; q < L::KK; ++q) {
+            const int kk = c * L::KK + q;
+            mma<E>(tmem + L::D2, tc::smem_desc(sbase + L::H + kk * 2 * 2048, 2048, 128),
+                   tc::smem_desc(sbase + L::W2 + kk * 2 * 4096, 4096, 128), id256, (n | q) ? 1u : 0u);
+          }
+        }
+        if (!ok) break;
+        tc::mma_commit(&bar_l2);
+        // output layer: K chunk c as soon as epilogue 2 wrote it
+        for (int n = 0; n < 8 && ok; ++n) {
+          const int c = chunk_at(n);
+          ok = tc::mbar_wait(&hb[c], 1u);
+          if (!ok) break;
+          tc::fence_after_sync();
 #pragma unroll
-      for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
-      duRdu = fmaf(du[j], rd, duRdu);
+          for (int q = 0; q < L::KK; ++q) {
+            const int kk = c * L::KK + q;
+            mma<E>(tmem + L::D3, tc::smem_desc(sbase + L::H + kk * 2 * 2048, 2048, 128),
+                   tc::smem_desc(sbase + L::W3 + kk * 2 * 256, 256, 128), id16, (n | q) ? 1u : 0u);
+          }
+        }
+        if (!ok) break;
+        tc::mma_commit(&bar_l3);
+      }
+      // every MMA issued above has completed once this commit arrives
+      tc::mma_commit(&bar_drain);
+      if (!tc::mbar_wait(&bar_drain, 0u)) ok = false;
     }
-    const float is_cost = p.is_du * duRdu + uRdu + sHu[i];
-    // features -> X tile row tid
-    if (owner) {
-      float z[mlp::kIn];
-      mlp::features(x, v, z);
-      if (E == 2) {
-        const uint4 a = make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]),
-                                   pack_bf16(z[6], z[7]));
-        const uint4 b = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]), pack_bf16(z[12], z[13]),
-                                   pack_bf16(z[14], z[15]));
-        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 0, 128)) = a;
-        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 8, 128)) = b;
-      } else {
-        const uint4 a = make_uint4(pack_e4m3x4(z[0], z[1], z[2], z[3]), pack_e4m3x4(z[4], z[5], z[6], z[7]),
-                                   pack_e4m3x4(z[8], z[9], z[10], z[11]), pack_e4m3x4(z[12], z[13], z[14], z[15]));
-        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 0, 128)) = a;
-        *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 16, 128)) = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    // ---- epilogue warps (threads 0..127 also own the samples) ---------------------------
+    const uint32_t tmem_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+    const int erow = 32 * (warp & 3) + (tid & 31);  // epilogue row (= sample) of this thread
+    const int half = warp >> 2;                     // column half of this warp
+    const float s1 = swscale[0], s2 = swscale[1], s3 = swscale[2];
+    const Env env = make_env(p, nullptr);
+    float R[M * M];
+#pragma unroll
+    for (int a = 0; a < M * M; ++a) R[a] = p.R[a];
+    float x[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) x[a] = x0[a];
+    KahanSum S;
+    float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // the previous step's state cost is combined one step late (its map loads in flight meanwhile)
+    bool have_pend = false;
+    const float *pend_row = nullptr;
+    float pend_tx = 0.0f, pend_ty = 0.0f, pend_speed = 0.0f, pend_is = 0.0f;
+    for (int i = 0; i < T && ok; ++i) {
+      const uint32_t ph = static_cast<uint32_t>(i & 1);
+      float is_cost = 0.0f;
+      if (owner) {
+        if ((i & 1) == 0)
+          normals4(static_cast<uint32_t>(i >> 1), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+        float du[M], v[M];
+        {
+          const float pair[2] = {(i & 1) ? eps[2] : eps[0], (i & 1) ? eps[3] : eps[1]};
+          scale_noise<M>(Lnu, pair, du);
+        }
+        float duRdu = 0.0f, uRdu = 0.0f;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          v[j] = sU[i * M + j] + du[j];
+          uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
+          float rd = 0.0f;
+#pragma unroll
+          for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
+          duRdu = fmaf(du[j], rd, duRdu);
+        }
+        is_cost = p.is_du * duRdu + uRdu + sHu[i];
+        float z[mlp::kIn];
+        mlp::features(x, v, z);
+        if (E == 2) {
+          const uint4 a = make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]),
+                                     pack_bf16(z[6], z[7]));
+          const uint4 b = make_uint4(pack_bf16(z[8], z[9]), pack_bf16(z[10], z[11]), pack_bf16(z[12], z[13]),
+                                     pack_bf16(z[14], z[15]));
+          *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 0, 128)) = a;
+          *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 8, 128)) = b;
+        } else {
+          const uint4 a = make_uint4(pack_e4m3x4(z[0], z[1], z[2], z[3]), pack_e4m3x4(z[4], z[5], z[6], z[7]),
+                                     pack_e4m3x4(z[8], z[9], z[10], z[11]), pack_e4m3x4(z[12], z[13], z[14], z[15]));
+          *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 0, 128)) = a;
+          *reinterpret_cast<uint4 *>(smem + L::X + tile_offset<E>(tid, 16, 128)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        tc::mbar_arrive(&bar_x);
+        // the previous step's cost, its map loads issued a step ago
+        if (have_pend) {
+          const float m00 = __ldg(pend_row), m10 = __ldg(pend_row + 1);
+          const float m01 = __ldg(pend_row + env.map_w), m11 = __ldg(pend_row + env.map_w + 1);
+          const float aa = m00 + pend_tx * (m10 - m00);
+          const float bb = m01 + pend_tx * (m11 - m01);
+          S.add((aa + pend_ty * (bb - aa)) + pend_speed + pend_is);
+        }
+      }
+      // epilogue 1
+      ok = tc::mbar_wait(&bar_l1, ph);
+      if (!ok) break;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        const int c = half * 4 + q;
+        hidden_chunk<E>(tmem_row + L::D1 + 32 * c, sb1, s1, smem, erow, 32 * c);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        tc::mbar_arrive(&hb[c]);
+      }
+      // epilogue 2 (H is overwritten only after every layer-2 MMA has read it)
+      ok = tc::mbar_wait(&bar_l2, ph);
+      if (!ok) break;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+        const int c = half * 4 + q;
+        hidden_chunk<E>(tmem_row + L::D2 + 32 * c, sb2, s2, smem, erow, 32 * c);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        tc::mbar_arrive(&hb[c]);
+      }
+      if (owner) {  // warps 0..3: TMEM lane quadrant = warp, row = sample
+        ok = tc::mbar_wait(&bar_l3, ph);
+        if (!ok) break;
+        tc::fence_after_sync();
+        float y[16];
+        tc::tmem_ld8(tmem_row + L::D3, y);
+        tc::tmem_ld8(tmem_row + L::D3 + 8, y + 8);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] += fmaf(y[j], s3, sb3[j]) * sscale[j];
+        // cost of the new state: map loads issued now, combined next step (same sum order)
+        const float fx = fminf(fmaxf((x[0] - env.map_ox) * env.map_inv_cell, 0.0f), static_cast<float>(env.map_w - 1));
+        const float fy = fminf(fmaxf((x[1] - env.map_oy) * env.map_inv_cell, 0.0f), static_cast<float>(env.map_h - 1));
+        const int ix = min(static_cast<int>(fx), env.map_w - 2);
+        const int iy = min(static_cast<int>(fy), env.map_h - 2);
+        pend_tx = fx - static_cast<float>(ix);
+        pend_ty = fy - static_cast<float>(iy);
+        pend_row = env.map + static_cast<size_t>(iy) * env.map_w + ix;
+        const float dv = x[3] - Car::v_target;
+        pend_speed = dv * dv;
+        pend_is = is_cost;
+        have_pend = true;
       }
     }
-    // layer 1
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      mma<E>(tmem, tc::smem_desc(sbase + L::X, 128 * 16, 128), tc::smem_desc(sbase + L::W1, 256 * 16, 128), id256, 0u);
-      tc::mma_commit(&bar);
-    }
-    bool got = tc::mbar_wait(&bar, phase);
-    phase ^= 1u;
-    tc::fence_after_sync();
-    if (!__syncthreads_and(got)) {
-      ok = false;
-      break;
-    }
-    hidden_epilogue<E>(tmem_row, sb1, s1, smem, erow, ecol);
-    // layer 2
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-#pragma unroll 1
-      for (int kk = 0; kk < 256 * E / 32; ++kk)
-        mma<E>(tmem, tc::smem_desc(sbase + L::H + kk * 2 * 2048, 2048, 128),
-               tc::smem_desc(sbase + L::W2 + kk * 2 * 4096, 4096, 128), id256, kk > 0 ? 1u : 0u);
-      tc::mma_commit(&bar);
-    }
-    got = tc::mbar_wait(&bar, phase);
-    phase ^= 1u;
-    tc::fence_after_sync();
-    if (!__syncthreads_and(got)) {
-      ok = false;
-      break;
-    }
-    hidden_epilogue<E>(tmem_row, sb2, s2, smem, erow, ecol);
-    // layer 3
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-#pragma unroll 1
-      for (int kk = 0; kk < 256 * E / 32; ++kk)
-        mma<E>(tmem + L::D3, tc::smem_desc(sbase + L::H + kk * 2 * 2048, 2048, 128),
-               tc::smem_desc(sbase + L::W3 + kk * 2 * 256, 256, 128), id16, kk > 0 ? 1u : 0u);
-      tc::mma_commit(&bar);
-    }
-    got = tc::mbar_wait(&bar, phase);
-    phase ^= 1u;
-    tc::fence_after_sync();
-    if (!__syncthreads_and(got)) {
-      ok = false;
-      break;
-    }
-    if (owner) {  // warps 0..3: TMEM lane quadrant = warp, row = sample
-      float y[16];
-      tc::tmem_ld8(tmem_row + L::D3, y);
-      tc::tmem_ld8(tmem_row + L::D3 + 8, y + 8);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < N; ++j) x[j] += fmaf(y[j], s3, sb3[j]) * sscale[j];
-      const float dv = x[3] - Car::v_target;
-      S.add(map_bilinear(env, x[0], x[1]) + dv * dv + is_cost);
-    }
-  }
-  float Sk;
-  if (ok) {
-    if (owner) {
+    if (ok && owner) {
+      if (have_pend) {
+        const float m00 = __ldg(pend_row), m10 = __ldg(pend_row + 1);
+        const float m01 = __ldg(pend_row + env.map_w), m11 = __ldg(pend_row + env.map_w + 1);
+        const float aa = m00 + pend_tx * (m10 - m00);
+        const float bb = m01 + pend_tx * (m11 - m01);
+        S.add((aa + pend_ty * (bb - aa)) + pend_speed + pend_is);
+      }
       const float dv = x[3] - Car::v_target;
       S.add(map_bilinear(env, x[0], x[1]) + dv * dv);  // phi(x_T) = q(x_T)
+      Sk = S.s;
     }
-    Sk = owner ? S.s : INFINITY;
-  } else {
+  }
+  tc::fence_before_sync();
+  if (!__syncthreads_and(ok)) {
     Sk = INFINITY;
     if (tid == 0) atomicExch(md->err, 1);
-    tc::mbar_wait(&bar, phase ^ 1u);  // bounded second chance for the MMAs in flight
   }
+  tc::fence_after_sync();
   block_partial<M, kMlpThreads, true>(p, owner ? k : INT_MAX, ctr, Sk, Lnu, S_out,
                                       part_sums + static_cast<size_t>(blockIdx.x) * TM, part + blockIdx.x, nullptr,
                                       nullptr);

@@ -168,12 +168,30 @@ def test_mlp_iteration_matches_the_bf16_oracle(env, trained, K, T, lam):
     from tests import parity as P
     if P.argmin_is_unique(o.S, rtol=0.1):
         assert g["kstar"] == o.kstar
-    if 1.0 / np.sum(o.w ** 2) < 1.5:        # weights on one sample: the update is exact
-        scale_u = P.control_scale(c)
-        assert np.all(np.abs(Ug - o.U) <= 1e-3 * (np.abs(o.U) + scale_u))
-    else:                                   # spread weights: agreement within the cost error
-        assert np.abs(Ug - o.U).max() < 0.05 * np.abs(o.U).max() + 1e-3
     ctl.close()
+    _check_update_within_cost_error(Ug, o, lam, P.control_scale(c))
+
+
+def _check_update_within_cost_error(Ug, o, lam, scale_u):
+    """The update is a weighted mean of the perturbations; BF16 storage moves each path cost
+    by ~1e-3 relative, which at a small lambda may reorder samples whose oracle costs are
+    within that error of the best.  Samples more than 20 lambda above the best keep weights
+    below e^-20 on both sides, so the GPU update must be a convex combination of the
+    perturbations of the candidate set A = {k : S_k - rho <= max(20 lambda, 5e-3 |rho|)}
+    (one candidate: the oracle update itself)."""
+    from scipy.optimize import nnls
+    band = max(20.0 * lam, 5e-3 * abs(o.rho))
+    A = np.flatnonzero(o.S - o.rho <= band)
+    tol = 1e-3 * (np.abs(o.U) + scale_u)
+    if A.size == 1:
+        assert np.all(np.abs(Ug - o.U) <= tol)
+        return
+    U0 = o.U - o.dU                                    # the controls before the update
+    D = o.du[:, :, A].reshape(-1, A.size)              # candidate perturbations as columns
+    big = 1e3
+    w, _ = nnls(np.vstack([D, big * np.ones((1, A.size))]), np.concatenate([(Ug - U0).ravel(), [big]]))
+    fit = U0 + (D @ w).reshape(o.U.shape)
+    assert np.all(np.abs(Ug - fit) <= tol), np.abs(Ug - fit).max()
 
 
 def test_mlp_needs_its_weights_and_has_no_plain_loop(env, trained):
