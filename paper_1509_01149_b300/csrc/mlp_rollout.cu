@@ -91,14 +91,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// H row `row`, columns [c0, c0 + 32) = tanh(scale * D + bias) in the tile format, D read
-// from TMEM columns taddr .. taddr + 31 of this thread's lane
+// H row `row`, columns [c0, c0 + 32) = tanh(scale * v + bias) in the tile format (v: the 32
+// accumulator columns of this thread's lane, already loaded from TMEM)
 template <int E>
-__device__ __forceinline__ void hidden_chunk(uint32_t taddr, const float *bias, float scale, unsigned char *smem,
-                                             int row, int c0) {
-  float v[32];
-  tmem_ld32(taddr, v);
-  tc::tmem_ld_wait();
+__device__ __forceinline__ void hidden_store(float v[32], const float *bias, float scale, unsigned char *smem, int row,
+                                             int c0) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) v[j] = tc::tanh_approx(fmaf(v[j], scale, bias[c0 + j]));
   if (E == 2) {
@@ -280,34 +277,59 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     for (int a = 0; a < N; ++a) x[a] = x0[a];
     KahanSum S;
     float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // control v_i = u_i + du_i and IS running term of step i (owners); step i+1's are
+    // drawn during step i's second epilogue, off the step's critical path
+    float v_cur[M] = {0.0f, 0.0f}, is_cur = 0.0f;
+    auto noise_step = [&](int i, float v[M], float &is) {
+      if ((i & 1) == 0)
+        normals4(static_cast<uint32_t>(i >> 1), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+      float du[M];
+      {
+        const float pair[2] = {(i & 1) ? eps[2] : eps[0], (i & 1) ? eps[3] : eps[1]};
+        scale_noise<M>(Lnu, pair, du);
+      }
+      float duRdu = 0.0f, uRdu = 0.0f;
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        v[j] = sU[i * M + j] + du[j];
+        uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
+        float rd = 0.0f;
+#pragma unroll
+        for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
+        duRdu = fmaf(du[j], rd, duRdu);
+      }
+      is = p.is_du * duRdu + uRdu + sHu[i];
+    };
+    // one hidden layer's epilogue for this warp's column half: the TMEM load of chunk q+1 is
+    // in flight while chunk q is activated and stored; mid() runs after the second chunk
+    auto epilogue = [&](uint32_t dcol, const float *bias, float scale, auto mid) {
+      float va[32], vb[32];
+      tmem_ld32(tmem_row + dcol + 32 * (half * 4), va);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = half * 4 + q;
+        float *cur = (q & 1) ? vb : va;
+        float *nxt = (q & 1) ? va : vb;
+        if (q < 3) tmem_ld32(tmem_row + dcol + 32 * (c + 1), nxt);
+        hidden_store<E>(cur, bias, scale, smem, erow, 32 * c);
+        tc::fence_smem_to_async();
+        tc::fence_before_sync();
+        tc::mbar_arrive(&hb[c]);
+        if (q == 1) mid();
+        if (q < 3) tc::tmem_ld_wait();
+      }
+    };
     // the previous step's state cost is combined one step late (its map loads in flight meanwhile)
     bool have_pend = false;
     const float *pend_row = nullptr;
     float pend_tx = 0.0f, pend_ty = 0.0f, pend_speed = 0.0f, pend_is = 0.0f;
+    if (owner) noise_step(0, v_cur, is_cur);
     for (int i = 0; i < T && ok; ++i) {
       const uint32_t ph = static_cast<uint32_t>(i & 1);
-      float is_cost = 0.0f;
       if (owner) {
-        if ((i & 1) == 0)
-          normals4(static_cast<uint32_t>(i >> 1), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
-        float du[M], v[M];
-        {
-          const float pair[2] = {(i & 1) ? eps[2] : eps[0], (i & 1) ? eps[3] : eps[1]};
-          scale_noise<M>(Lnu, pair, du);
-        }
-        float duRdu = 0.0f, uRdu = 0.0f;
-#pragma unroll
-        for (int j = 0; j < M; ++j) {
-          v[j] = sU[i * M + j] + du[j];
-          uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
-          float rd = 0.0f;
-#pragma unroll
-          for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
-          duRdu = fmaf(du[j], rd, duRdu);
-        }
-        is_cost = p.is_du * duRdu + uRdu + sHu[i];
         float z[mlp::kIn];
-        mlp::features(x, v, z);
+        mlp::features(x, v_cur, z);
         if (E == 2) {
           const uint4 a = make_uint4(pack_bf16(z[0], z[1]), pack_bf16(z[2], z[3]), pack_bf16(z[4], z[5]),
                                      pack_bf16(z[6], z[7]));
@@ -337,26 +359,15 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       ok = tc::mbar_wait(&bar_l1, ph);
       if (!ok) break;
       tc::fence_after_sync();
-#pragma unroll 1
-      for (int q = 0; q < 4; ++q) {
-        const int c = half * 4 + q;
-        hidden_chunk<E>(tmem_row + L::D1 + 32 * c, sb1, s1, smem, erow, 32 * c);
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        tc::mbar_arrive(&hb[c]);
-      }
+      epilogue(L::D1, sb1, s1, [] {});
       // epilogue 2 (H is overwritten only after every layer-2 MMA has read it)
       ok = tc::mbar_wait(&bar_l2, ph);
       if (!ok) break;
       tc::fence_after_sync();
-#pragma unroll 1
-      for (int q = 0; q < 4; ++q) {
-        const int c = half * 4 + q;
-        hidden_chunk<E>(tmem_row + L::D2 + 32 * c, sb2, s2, smem, erow, 32 * c);
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        tc::mbar_arrive(&hb[c]);
-      }
+      float v_nxt[M] = {0.0f, 0.0f}, is_nxt = 0.0f;
+      epilogue(L::D2, sb2, s2, [&] {
+        if (owner && i + 1 < T) noise_step(i + 1, v_nxt, is_nxt);
+      });
       if (owner) {  // warps 0..3: TMEM lane quadrant = warp, row = sample
         ok = tc::mbar_wait(&bar_l3, ph);
         if (!ok) break;
@@ -377,8 +388,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
         pend_row = env.map + static_cast<size_t>(iy) * env.map_w + ix;
         const float dv = x[3] - Car::v_target;
         pend_speed = dv * dv;
-        pend_is = is_cost;
+        pend_is = is_cur;
         have_pend = true;
+        v_cur[0] = v_nxt[0];
+        v_cur[1] = v_nxt[1];
+        is_cur = is_nxt;
       }
     }
     if (ok && owner) {
