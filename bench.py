@@ -443,8 +443,7 @@ def run_ours(args, rank, world, local_rank):
             flush.zero_()
         stream.synchronize()
         t0 = time.perf_counter()
-        ctrl.step(x_host)
-        ctrl.shift()
+        ctrl.step_shift(x_host)
         lat.append(time.perf_counter() - t0)
     stream.synchronize()
     lat = lat[5:]
@@ -508,7 +507,9 @@ def run_ours(args, rank, world, local_rank):
                    "x0": "fixed state, receding-horizon warm start with shift"},
         "iters_per_s": value / (K_SAMPLES * T_STEPS),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * m,
-                "p50_ms": pct(lat_ms, 0.5), "p99_ms": pct(lat_ms, 0.99), "steps": e2e_steps},
+                "p50_ms": pct(lat_ms, 0.5), "p99_ms": pct(lat_ms, 0.99), "steps": e2e_steps,
+                "call": "mppi_step_shift (x0 copied from pinned host memory, u0 written by the update kernel "
+                        "into mapped pinned memory; one graph per step, blocking until u0 is on the host)"},
         "plain_loop": {"value": plain_value, "unit": UNIT, "p50_ms": pct(plat_ms, 0.5), "p99_ms": pct(plat_ms, 0.99),
                        "steps": len(plat), "e2e_speedup": e2e_value / plain_value,
                        "what": "unfused: noise->HBM, rollout, min, normaliser, weighted-sum kernels, "

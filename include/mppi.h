@@ -98,6 +98,13 @@ int mppi_destroy(mppi_ctx *ctx);
  * was not set. */
 int mppi_step(mppi_ctx *ctx, const float *h_state, float *h_u0_out);
 
+/* One pass of Algorithm 1's loop body from host buffers: the iteration of mppi_step,
+ * u_0 to h_u0_out (host [m]), then the shift of mppi_shift (u_i <- u_{i+1},
+ * u_{T-1} <- u_init, iteration counter += 1).  Blocks until u_0 is on the host; the
+ * shift has completed by then too.  Same errors as mppi_step.  On the fused path this is
+ * one CUDA graph in which the shift runs inside the update's launch when T*m <= 256. */
+int mppi_step_shift(mppi_ctx *ctx, const float *h_state, float *h_u0_out);
+
 /* Same iteration, asynchronous on the ctx stream, device pointers: d_state [n] is
  * read, d_u0_out [m] written (may be NULL), when the stream reaches the work.  No
  * host sync.  Equivalent to mppi_rollout_async followed by mppi_update_async. */

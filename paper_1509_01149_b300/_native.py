@@ -47,6 +47,7 @@ SIGNATURES = [
     ("mppi_create", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, _FP, _FP, C.POINTER(_P)]),
     ("mppi_destroy", C.c_int, [_P]),
     ("mppi_step", C.c_int, [_P, _FP, _FP]),
+    ("mppi_step_shift", C.c_int, [_P, _FP, _FP]),
     ("mppi_step_async", C.c_int, [_P, _P, _P]),
     ("mppi_rollout_async", C.c_int, [_P, _P]),
     ("mppi_update_async", C.c_int, [_P, _P]),
@@ -218,6 +219,14 @@ class Controller:
         return u0
 
     step = mppi_step
+
+    def mppi_step_shift(self, state) -> np.ndarray:
+        x = _f32(state, self.n)
+        u0 = np.zeros(self.m, dtype=np.float32)
+        self._chk(lib.mppi_step_shift(self._h, _fp(x), _fp(u0)))
+        return u0
+
+    step_shift = mppi_step_shift
 
     def mppi_step_async(self, d_state: int, d_u0_out: int | None):
         self._chk(lib.mppi_step_async(self._h, C.c_void_p(d_state), C.c_void_p(d_u0_out or 0)))

@@ -130,9 +130,11 @@ struct mppi_ctx {
   int mlp_precision = 0;
   int *d_mlp_err = nullptr;
 
-  float *h_x0 = nullptr, *h_u0 = nullptr;  // pinned staging
+  float *h_x0 = nullptr, *h_u0 = nullptr;    // pinned, mapped: the step graphs copy x0 from
+  float *dh_x0 = nullptr, *dh_u0 = nullptr;  // h_x0 and write u0 into h_u0 directly
 
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;        // mppi_step: rollout -> merge
+  cudaGraphExec_t graph_shift = nullptr;  // mppi_step_shift: rollout -> merge + shift
   bool graph_dirty = true;
   cudaGraphExec_t iter_graph = nullptr;  // mppi_iterate_async: rollout -> merge -> shift
   bool iter_graph_dirty = true;
@@ -196,29 +198,47 @@ int enqueue_plain(mppi_ctx *c, cudaStream_t s) {
                  "plain reduce/update");
 }
 
-int build_graph(mppi_ctx *c) {
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
+// Capture one step graph: x0 copied from the pinned buffer (one DMA: cheaper than every CTA
+// reading mapped host memory), the merge writes u0 straight into the mapped pinned buffer
+// (no copy node), and with `shift` the shift runs in the same launch when the outputs fit one
+// cluster, else by the shift kernel after it.
+int capture_step(mppi_ctx *c, bool shift, cudaGraphExec_t *out) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
   }
   cudaGraph_t g = nullptr;
   MPPI_TRY(c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
   int rc = c->cuda(cudaMemcpyAsync(c->d_st->x0, c->h_x0, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream),
                    "x0 copy");
-  if (rc == MPPI_OK) rc = enqueue_fused(c, c->stream);
-  if (rc == MPPI_OK)
-    rc = c->cuda(cudaMemcpyAsync(c->h_u0, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToHost, c->stream),
-                 "u0 copy");
+  if (rc == MPPI_OK) rc = launch_rollout(c, c->d_st->x0, c->stream);
+  if (rc == MPPI_OK) {
+    if (shift && merge_shift_fusable(c->p)) {
+      rc = c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->dh_u0, c->d_dU,
+                                             c->d_dbg, c->d_uinit, c->d_st, c->stream),
+                   "merge + shift launch");
+    } else {
+      rc = launch_update(c, c->dh_u0, c->stream);
+      if (rc == MPPI_OK && shift)
+        rc = c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+    }
+  }
   const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
   if (rc != MPPI_OK) {
     if (g) cudaGraphDestroy(g);
     return rc;
   }
   MPPI_TRY(rc_end);
-  rc = c->cuda(cudaGraphInstantiate(&c->graph, g, 0), "graph instantiate");
+  rc = c->cuda(cudaGraphInstantiate(out, g, 0), "graph instantiate");
   cudaGraphDestroy(g);
-  if (rc == MPPI_OK) c->graph_dirty = false;
   return rc;
+}
+
+int build_graph(mppi_ctx *c) {
+  MPPI_TRY(capture_step(c, false, &c->graph));
+  MPPI_TRY(capture_step(c, true, &c->graph_shift));
+  c->graph_dirty = false;
+  return MPPI_OK;
 }
 
 int check_ready(mppi_ctx *c) {
@@ -457,8 +477,16 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
     if (!c->d_mlp_err) rc = c->fail(MPPI_ENOMEM, "arena too small");
   }
   if (rc == MPPI_OK) rc = c->cuda(cudaMemsetAsync(c->arena.base, 0, c->arena.size, c->stream), "memset");
-  if (rc == MPPI_OK) rc = c->cuda(cudaMallocHost(&c->h_x0, sizeof(float) * kMaxN), "cudaMallocHost");
-  if (rc == MPPI_OK) rc = c->cuda(cudaMallocHost(&c->h_u0, sizeof(float) * kMaxM), "cudaMallocHost");
+  if (rc == MPPI_OK)
+    rc = c->cuda(cudaHostAlloc(reinterpret_cast<void **>(&c->h_x0), sizeof(float) * kMaxN, cudaHostAllocMapped),
+                 "cudaHostAlloc");
+  if (rc == MPPI_OK)
+    rc = c->cuda(cudaHostAlloc(reinterpret_cast<void **>(&c->h_u0), sizeof(float) * kMaxM, cudaHostAllocMapped),
+                 "cudaHostAlloc");
+  if (rc == MPPI_OK)
+    rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_x0), c->h_x0, 0), "mapped x0");
+  if (rc == MPPI_OK)
+    rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_u0), c->h_u0, 0), "mapped u0");
   if (rc == MPPI_OK) rc = c->cuda(cudaStreamSynchronize(c->stream), "sync");
   if (rc != MPPI_OK) {
     g_create_error = c->err;
@@ -473,6 +501,7 @@ int mppi_destroy(mppi_ctx *c) {
   if (!c) return MPPI_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_shift) cudaGraphExecDestroy(c->graph_shift);
   if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->d_du) cudaFree(c->d_du);
@@ -621,32 +650,33 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   return MPPI_OK;
 }
 
-int mppi_step(mppi_ctx *c, const float *state, float *u0_out) {
+namespace {
+int step_host(mppi_ctx *c, const float *state, float *u0_out, bool shift) {
   if (!c || !state || !u0_out) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
   std::memcpy(c->h_x0, state, sizeof(float) * c->n);
-  if (c->impl == MPPI_IMPL_PLAIN) {
+  if (c->impl == MPPI_IMPL_PLAIN || c->stream == nullptr) {
+    // the plain loop, or the legacy stream (which cannot be captured): launch directly
     MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_st->x0, c->h_x0, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream),
                      "x0 copy"));
-    MPPI_TRY(enqueue_plain(c, c->stream));
+    MPPI_TRY(c->impl == MPPI_IMPL_PLAIN ? enqueue_plain(c, c->stream) : enqueue_fused(c, c->stream));
     MPPI_TRY(c->cuda(cudaMemcpyAsync(c->h_u0, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToHost, c->stream),
                      "u0 copy"));
-  } else if (c->stream == nullptr) {
-    // the legacy stream cannot be captured: launch directly
-    MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_st->x0, c->h_x0, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream),
-                     "x0 copy"));
-    MPPI_TRY(enqueue_fused(c, c->stream));
-    MPPI_TRY(c->cuda(cudaMemcpyAsync(c->h_u0, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToHost, c->stream),
-                     "u0 copy"));
+    if (shift) MPPI_TRY(c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch"));
   } else {
     if (c->graph_dirty) MPPI_TRY(build_graph(c));
-    MPPI_TRY(c->cuda(cudaGraphLaunch(c->graph, c->stream), "graph launch"));
+    MPPI_TRY(c->cuda(cudaGraphLaunch(shift ? c->graph_shift : c->graph, c->stream), "graph launch"));
   }
   MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
   MPPI_TRY(check_mlp_error(c));
   std::memcpy(u0_out, c->h_u0, sizeof(float) * c->m);
   return MPPI_OK;
 }
+}  // namespace
+
+int mppi_step(mppi_ctx *c, const float *state, float *u0_out) { return step_host(c, state, u0_out, false); }
+
+int mppi_step_shift(mppi_ctx *c, const float *state, float *u0_out) { return step_host(c, state, u0_out, true); }
 
 int mppi_rollout_async(mppi_ctx *c, const float *d_state) {
   if (!c || !d_state) return MPPI_EINVAL;

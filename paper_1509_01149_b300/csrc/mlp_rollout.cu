@@ -184,7 +184,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     if (tid < 8) sscale[tid] = md->out_scale[tid];
     if (tid < 3) swscale[tid] = md->w_scale[tid];
   }
+  __shared__ float sx0[N];  // x0 staged once (it may live in mapped host memory)
   for (int o = tid; o < TM; o += kMlpThreads) sU[o] = U[o];
+  if (tid < N) sx0[tid] = x0[tid];
   __syncthreads();
   for (int i = tid; i < T; i += kMlpThreads) {
     float h = 0.0f;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     for (int a = 0; a < M * M; ++a) R[a] = p.R[a];
     float x[N];
 #pragma unroll
-    for (int a = 0; a < N; ++a) x[a] = x0[a];
+    for (int a = 0; a < N; ++a) x[a] = sx0[a];
     KahanSum S;
     float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     // control v_i = u_i + du_i and IS running term of step i (owners); step i+1's are

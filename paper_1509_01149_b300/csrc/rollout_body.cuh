@@ -210,8 +210,10 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   float *sW = sHu + T;              // [BLK] weights
   float *sDu = du_ext ? du_ext : sW + BLK;  // STORE only: [TM][BLK] perturbations of this block
 
+  __shared__ float sx0[N];  // x0 staged once per block (it may live in mapped host memory)
   for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
   for (int o = tid; o < 4 * p.n_obs; o += BLK) sObs[o] = (o & 3) == 3 ? 0.0f : p.obs[3 * (o >> 2) + (o & 3)];
+  if (tid < N) sx0[tid] = x0[tid];
   __syncthreads();
   for (int i = tid; i < T; i += BLK) {
     float h = 0.0f;
@@ -237,7 +239,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   }
   float x[N];
 #pragma unroll
-  for (int a = 0; a < N; ++a) x[a] = x0[a];
+  for (int a = 0; a < N; ++a) x[a] = sx0[a];
   typename Sys::Aux aux;
   Sys::init(x, aux, env);
   KahanSum S;

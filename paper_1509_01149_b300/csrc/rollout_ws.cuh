@@ -58,7 +58,9 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
   float *sDu = sS + NS;     // [TM][NS] perturbations
   float *sVel = sDu + static_cast<size_t>(TM) * NS;  // [R][C][3][NS]
 
+  __shared__ float sx0[Car::N];  // x0 staged once (it may live in mapped host memory)
   for (int o = tid; o < TM; o += NT) sU[o] = U[o];
+  if (tid < Car::N) sx0[tid] = x0[tid];
   if (tid == 0) {
     for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], NS);
     for (int r = 0; r < R; ++r) {
@@ -91,7 +93,7 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
   // loop: three roles share each sub-partition's instruction cache.
   if (role == 0) {
     // ---- core: the velocity recurrence ----------------------------------------------
-    float xv[4] = {x0[3], x0[4], x0[5], x0[6]};
+    float xv[4] = {sx0[3], sx0[4], sx0[5], sx0[6]};
     for (int c = 0; c < nch; ++c) {
       ok = tc::mbar_wait(&bar_noise[c], 0u);
       if (ok && c >= R) ok = tc::mbar_wait(&bar_empty[c % R], static_cast<uint32_t>((c / R - 1) & 1));
@@ -164,7 +166,7 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
     float Rm[M * M];
 #pragma unroll
     for (int a = 0; a < M * M; ++a) Rm[a] = p.R[a];
-    float X = x0[0], Y = x0[1], psi = x0[2], vx = x0[3], vy = x0[4], r = x0[5];
+    float X = sx0[0], Y = sx0[1], psi = sx0[2], vx = sx0[3], vy = sx0[4], r = sx0[5];
     Car::Aux aux;
     aux.cX = aux.cY = aux.cpsi = 0.0f;
     KahanSum S;

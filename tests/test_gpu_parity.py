@@ -188,3 +188,21 @@ def test_graph_iteration_equals_step_and_shift(N):
         assert torch.equal(ua, ub)
     assert np.array_equal(a.get_controls(), b.get_controls())
     assert a.get_iteration() == b.get_iteration() == 3
+
+
+@pytest.mark.parametrize("system,T", [(W.CAR, 40), (W.QUAD, 80), (W.CARTPOLE, 30)])
+def test_step_shift_equals_step_then_shift(N, system, T):
+    """mppi_step_shift (host buffers; one graph with the shift in the update's launch when
+    T*m <= 256, else a shift kernel after it) gives the same u0, controls and counter as
+    mppi_step followed by mppi_shift, over three iterations from changing states."""
+    cfg = W.config(system, K=2000, T=T)
+    a, b = P.make_controller(cfg), P.make_controller(cfg)
+    x = np.asarray(cfg["x0"], np.float32)
+    for it in range(3):
+        xs = x + np.float32(0.01 * it)
+        ua = a.step(xs)
+        a.shift()
+        ub = b.step_shift(xs)
+        assert np.array_equal(ua, ub)
+    assert np.array_equal(a.get_controls(), b.get_controls())
+    assert a.get_iteration() == b.get_iteration() == 3
