@@ -116,7 +116,8 @@ def test_quad_iteration(N):
 
 
 @pytest.mark.parametrize("system,K,T", [(W.CARTPOLE, 1, 1), (W.CARTPOLE, 33, 3), (W.CARTPOLE, 129, 7),
-                                        (W.CAR, 65, 1), (W.CAR, 200, 5), (W.QUAD, 63, 2), (W.QUAD, 130, 9)])
+                                        (W.CAR, 65, 1), (W.CAR, 200, 5), (W.CAR, 1000, 9), (W.CAR, 300, 17),
+                                        (W.CAR, 257, 33), (W.QUAD, 63, 2), (W.QUAD, 130, 9)])
 def test_ragged_sizes(N, system, K, T):
     cfg = W.config(system, K=K, T=T)
     for impl in (0, 1):
@@ -124,6 +125,17 @@ def test_ragged_sizes(N, system, K, T):
         o = P.oracle_iteration(cfg)
         mask = o.margin > 1e-3 if o.margin is not None else None
         _check_iteration(cfg, g, o, margin_mask=mask)
+
+
+@pytest.mark.parametrize("T", [148, 149])
+def test_car_horizon_at_the_warp_role_limit(N, T):
+    """The car's three-warp-role kernel keeps du for the whole horizon in shared memory; the
+    longest horizon that fits uses it (T = 148: 8-step chunks, a ragged last chunk of 4), the
+    next one falls back to the one-thread-per-sample kernel (T = 149).  Both match the oracle."""
+    cfg = W.config(W.CAR, K=700, T=T)
+    g, _ = P.gpu_iteration(cfg)
+    o = P.oracle_iteration(cfg)
+    _check_iteration(cfg, g, o)
 
 
 def test_nonzero_controls_and_correlated_sigma(N):
