@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   __shared__ double s_inv_eta;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int o = blockIdx.x * kMergeOutputs + lane;
+  // launched as a programmatic dependent of the rollout: its partials are complete and
+  // visible after this wait (a no-op for an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   // loads first: this thread's block partial (b = tid) and its lane's first block sums
   BlockPartial mine{0.0, INFINITY, INT_MAX};
@@ -461,11 +464,24 @@ cudaError_t prepare_kernels() {
 cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                 float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
   const int TM = p.T * p.m;
-  const size_t smem = sizeof(double) * static_cast<size_t>(nblk);
-  const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
-  k_merge_update<false><<<grid, kMergeThreads, smem, s>>>(nblk, TM, p.m, p.inv_lambda, part_sums, part, U, u0_out,
-                                                          dU_dbg, dbg, nullptr, nullptr);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((TM + kMergeOutputs - 1) / kMergeOutputs, 1, 1);
+  cfg.blockDim = dim3(kMergeThreads, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(double) * static_cast<size_t>(nblk);
+  cfg.stream = s;
+  // programmatic dependent launch: the merge's CTAs start while the rollout drains and wait
+  // (griddepcontrol.wait) for its results
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int m = p.m;
+  const float il = p.inv_lambda;
+  const float *no_uinit = nullptr;
+  CtrlState *no_st = nullptr;
+  return cudaLaunchKernelEx(&cfg, k_merge_update<false>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,
+                            no_uinit, no_st);
 }
 
 bool merge_shift_fusable(const CtrlParams &p) {
@@ -483,13 +499,15 @@ cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float
   cfg.blockDim = dim3(kMergeThreads, 1, 1);
   cfg.dynamicSmemBytes = sizeof(double) * static_cast<size_t>(nblk);
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = grid;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   const int m = p.m;
   const float il = p.inv_lambda;
   return cudaLaunchKernelEx(&cfg, k_merge_update<true>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,

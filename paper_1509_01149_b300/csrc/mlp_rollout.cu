@@ -416,6 +416,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     if (tid == 0) atomicExch(md->err, 1);
   }
   tc::fence_after_sync();
+  // the update kernel may start launching now (it waits for this grid's results itself)
+  asm volatile("griddepcontrol.launch_dependents;");
   block_partial<M, kMlpThreads, true>(p, owner ? k : INT_MAX, ctr, Sk, Lnu, S_out,
                                       part_sums + static_cast<size_t>(blockIdx.x) * TM, part + blockIdx.x, nullptr,
                                       nullptr);

@@ -292,6 +292,8 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   }
   if (have) S.add(Sys::cost_finish(pend, env) + pend_is);
   S.add(Sys::cost(x, aux, env));  // phi(x_T) = q(x_T)
+  // the update kernel may start launching now (it waits for this grid's results itself)
+  asm volatile("griddepcontrol.launch_dependents;");
   block_partial<M, BLK, REGEN>(p, k, ctr, S.s, Lnu, S_out, part_sums, part, sW, sDu);
 }
 

@@ -248,6 +248,8 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
     sS[slot] = ok ? S.s : INFINITY;
   }
   __syncthreads();
+  // the update kernel may start launching now (it waits for this grid's results itself)
+  asm volatile("griddepcontrol.launch_dependents;");
   const bool owner = role == 0;
   float Lnu_unused[M * M] = {0.0f, 0.0f, 0.0f, 0.0f};
   block_partial<M, NT, false, NS>(p, owner ? k : INT_MAX, ctr, owner ? sS[tid] : INFINITY, Lnu_unused, S_out,
