@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--serving", default="256,512,1024",
                     help="concurrency levels of the serving measurement ('' to skip)")
     ap.add_argument("--serving-ticks", type=int, default=30)
+    ap.add_argument("--serving-heavy", default="256",
+                    help="concurrency levels of the heavy-skewed serving mix ('' to skip)")
+    ap.add_argument("--serving-capacity", action="store_true",
+                    help="measure the largest 50 Hz concurrency of every (system, K, T) (about a minute)")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-dynamics measurement")
     ap.add_argument("--learned-only", action="store_true")
@@ -212,12 +216,13 @@ def make_ctrl(N, impl, seed, gid, stream_handle):
     return c, cfg
 
 
-def run_serving(levels, n_ticks, seed=0):
-    """Batched serving of a Poisson stream of controllers (uniform mix of cart-pole / car /
-    quadrotor, K in {512, 1024, 4096, 16384}, T in {50, 100, 150, 200}) at each target
-    concurrency: prefill, autotune, then n_ticks receding-horizon ticks with arrivals and
-    departures.  Per level: tick latency p50/p99, deadline misses, rollout-steps/s and the
-    algorithmic FP32 rate of the rollouts against the FP32 peak."""
+def run_serving(levels, n_ticks, seed=0, mix=None):
+    """Batched serving of a Poisson stream of controllers (by default a uniform mix of
+    cart-pole / car / quadrotor, K in {512, 1024, 4096, 16384}, T in {50, 100, 150, 200};
+    `mix` gives choice probabilities) at each target concurrency: prefill, autotune, then
+    n_ticks receding-horizon ticks with arrivals and departures.  Per level: tick latency
+    p50/p99, deadline misses, rollout-steps/s and the algorithmic FP32 rate of the rollouts
+    against the FP32 peak."""
     from paper_1509_01149_b300 import _native as N
     from paper_1509_01149_b300 import serving
     out = {}
@@ -225,7 +230,7 @@ def run_serving(levels, n_ticks, seed=0):
         srv = N.Server(max(2 * target, 64), max(256 << 20, target << 21))
         srv.set_env(0, N.map_blob(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL))
         srv.set_env(1, N.forest_blob(W.quad_forest(0), W.QUAD_GOAL))
-        loop = serving.ServingLoop(srv, W, {W.CAR: 0, W.QUAD: 1}, seed=seed + target)
+        loop = serving.ServingLoop(srv, W, {W.CAR: 0, W.QUAD: 1}, seed=seed + target, **(mix or {}))
         loop.prefill(target, 200.0)
         srv.autotune([r.slot for r in loop.active], [W.config(r.system)["x0"] for r in loop.active])
         flops = []
@@ -246,6 +251,67 @@ def run_serving(levels, n_ticks, seed=0):
         out[str(target)] = summ
         loop.drain()
         srv.close()
+    return out
+
+
+def run_capacity(probe=(16, 64), ticks=5, cap=2048, seed=0):
+    """Largest number of identical controllers of each (system, K, T) that one server steps
+    within the 20 ms (50 Hz) deadline: tick time measured at two probe sizes (autotuned at the
+    larger), a line t(N) = a + b N fitted, N* = (20 ms - a) / b capped at `cap`, then checked
+    by running N* controllers (the worst of `ticks` ticks must meet the deadline; else N* is
+    lowered by 10 % and checked again, up to three times)."""
+    from paper_1509_01149_b300 import _native as N
+    from paper_1509_01149_b300 import serving
+    srv = N.Server(cap + 64, 6 << 30)
+    srv.set_env(0, N.map_blob(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL))
+    srv.set_env(1, N.forest_blob(W.quad_forest(0), W.QUAD_GOAL))
+    env_ids = {W.CAR: 0, W.QUAD: 1}
+    out = {}
+
+    def timed(system, K, T, n, tune=False):
+        slots = []
+        for i in range(n):
+            slot = srv.admit(serving.default_config(system, K, T, seed * 100000 + i, srv, W, env_ids))
+            if slot is None:
+                break
+            slots.append(slot)
+        x0 = [W.config(system)["x0"]] * len(slots)
+        try:
+            if len(slots) < n:
+                return None
+            if tune:
+                srv.autotune(slots, x0)
+            for _ in range(2):
+                srv.tick(slots, x0)
+            ts = []
+            for _ in range(ticks):
+                t0 = time.perf_counter()
+                srv.tick(slots, x0)
+                ts.append(1e3 * (time.perf_counter() - t0))
+            return statistics.median(ts), max(ts)
+        finally:
+            for s in slots:
+                srv.release(s)
+
+    for system in serving.SYSTEMS:
+        for K in serving.K_CHOICES:
+            for T in serving.T_CHOICES:
+                pts = [(n, timed(system, K, T, n, tune=(n == probe[-1]))) for n in probe]
+                (n1, r1), (n2, r2) = pts[0], pts[-1]
+                b = (r2[0] - r1[0]) / (n2 - n1)
+                a = r1[0] - b * n1
+                est = cap if b <= 0 else int(min(cap, max(1, (serving.DEADLINE_MS - a) / b)))
+                n, got = est, None
+                for _ in range(4):
+                    got = timed(system, K, T, n)
+                    if got is not None and got[1] <= serving.DEADLINE_MS:
+                        break
+                    n = max(1, int(n * 0.9))
+                out[f"{system}/{K}/{T}"] = {"max_controllers": n if got and got[1] <= serving.DEADLINE_MS else None,
+                                           "capped": n >= cap, "tick_ms_p50": got[0] if got else None,
+                                           "tick_ms_max": got[1] if got else None,
+                                           "probe_ms": [[nn, r[0]] for nn, r in pts]}
+    srv.close()
     return out
 
 
@@ -355,8 +421,15 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     levels = [int(v) for v in args.serving.split(",") if v.strip()]
+    heavy_levels = [int(v) for v in args.serving_heavy.split(",") if v.strip()]
     if args.serving_only:
-        print(json.dumps({"serving": run_serving(levels, args.serving_ticks)}), flush=True)
+        from paper_1509_01149_b300.serving import HEAVY_MIX
+        res = {"serving": run_serving(levels, args.serving_ticks)}
+        if heavy_levels:
+            res["serving_heavy"] = run_serving(heavy_levels, args.serving_ticks, mix=HEAVY_MIX)
+        if args.serving_capacity:
+            res["serving_capacity"] = run_capacity()
+        print(json.dumps(res), flush=True)
         return
     if args.learned_only:
         print(json.dumps({"learned": run_learned(args.learned_train, steps=args.learned_steps)}), flush=True)
@@ -472,6 +545,9 @@ def run_ours(args, rank, world, local_rank):
     pctrl.close()
 
     serving_res = run_serving(levels, args.serving_ticks, seed=rank) if levels else None
+    from paper_1509_01149_b300.serving import HEAVY_MIX
+    heavy_res = run_serving(heavy_levels, args.serving_ticks, seed=rank, mix=HEAVY_MIX) if heavy_levels else None
+    capacity_res = run_capacity(seed=rank) if args.serving_capacity else None
     learned_res = None if args.no_learned else run_learned(args.learned_train, steps=args.learned_steps)
 
     if rank != 0:
@@ -526,6 +602,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "cpu_baseline": cpu,
         "serving": serving_res,
+        "serving_heavy": heavy_res and dict(heavy_res, mix=HEAVY_MIX),
+        "serving_capacity": capacity_res,
         "learned": learned_res,
         "source_hash": source_hash(),
     }

@@ -79,14 +79,21 @@ def default_config(system: int, K: int, T: int, rid: int, server, workloads_mod,
                               env_id=env_ids.get(system, -1), u_init=c["u_init"])
 
 
+# A heavy-skewed mix: mostly quadrotors, mostly the largest K and T.
+HEAVY_MIX = {"system_p": (0.1, 0.3, 0.6), "k_p": (0.1, 0.1, 0.3, 0.5), "t_p": (0.1, 0.1, 0.3, 0.5)}
+
+
 class ServingLoop:
+    """system_p, k_p, t_p: probabilities of the choices (None: uniform)."""
+
     def __init__(self, server, workloads_mod, env_ids: dict, seed: int = 0, systems=SYSTEMS, k_choices=K_CHOICES,
-                 t_choices=T_CHOICES):
+                 t_choices=T_CHOICES, system_p=None, k_p=None, t_p=None):
         self.server = server
         self.W = workloads_mod
         self.env_ids = env_ids
         self.rng = np.random.default_rng(seed)
         self.systems, self.k_choices, self.t_choices = systems, k_choices, t_choices
+        self.system_p, self.k_p, self.t_p = system_p, k_p, t_p
         self.queue: list[Request] = []
         self.active: list[Request] = []
         self.next_rid = 0
@@ -95,8 +102,8 @@ class ServingLoop:
         self._x0 = {s: self.W.config(s)["x0"] for s in systems}
 
     def new_request(self, mean_lifetime: float) -> Request:
-        r = Request(rid=self.next_rid, system=int(self.rng.choice(self.systems)),
-                    K=int(self.rng.choice(self.k_choices)), T=int(self.rng.choice(self.t_choices)),
+        r = Request(rid=self.next_rid, system=int(self.rng.choice(self.systems, p=self.system_p)),
+                    K=int(self.rng.choice(self.k_choices, p=self.k_p)), T=int(self.rng.choice(self.t_choices, p=self.t_p)),
                     lifetime=max(1, int(self.rng.geometric(1.0 / max(mean_lifetime, 1.0)))),
                     arrival_tick=self.tick_no)
         self.next_rid += 1
