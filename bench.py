@@ -179,6 +179,33 @@ def oracle_rate(seconds: float, k_sample: int = 1024, max_iters: int | None = No
     return k_sample * T_STEPS * len(times) / sum(times), len(times), times
 
 
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_rate_all_cores(seconds: float, k_sample: int = 1024, max_procs: int = 64):
+    """The same oracle loop in one single-threaded child process per host core (up to
+    max_procs), all at once, each on its own k_sample-sample batch; returns the summed
+    rollout-steps/s and the number of processes."""
+    procs = max(1, min(os.cpu_count() or 1, max_procs))
+    env = dict(os.environ, **_ONE_THREAD)
+    arg = json.dumps([seconds, k_sample, None])
+    ps = [subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-child", arg], env=env,
+                           stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True) for _ in range(procs)]
+    total = 0.0
+    for p in ps:
+        out, _ = p.communicate()
+        times = json.loads(out.strip().splitlines()[-1])
+        total += k_sample * T_STEPS * len(times) / sum(times)
+    return total, procs
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -562,10 +589,13 @@ def run_ours(args, rank, world, local_rank):
     traffic = load_traffic("rollout_car_ws_k16384")
     cpu = None
     if not args.no_cpu_baseline:
-        rate, iters, _ = oracle_rate(args.cpu_seconds, 1024)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{iters} oracle iterations of 1024 of the {K_SAMPLES} samples at full horizon T={T_STEPS} "
-                         f"(FP64 numpy, one thread)"}
+        rate1, iters, _ = oracle_rate(args.cpu_seconds, 1024)
+        rate_all, procs = oracle_rate_all_cores(args.cpu_seconds, 1024)
+        cpu = {"value": rate_all, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": f"{procs} single-threaded oracle processes at once, each running ~{args.cpu_seconds:.0f} s of "
+                         f"iterations on its own 1024 of the {K_SAMPLES} samples at full horizon T={T_STEPS} "
+                         f"(FP64 numpy); one core alone: {iters} iterations",
+               "one_core_value": rate1, "cpu_model": cpu_model(), "nproc": os.cpu_count()}
     lat_ms = sorted(1e3 * x for x in lat)
     plat_ms = sorted(1e3 * x for x in plat)
 
