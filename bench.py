@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-dynamics measurement")
     ap.add_argument("--learned-only", action="store_true")
+    ap.add_argument("--no-systems", action="store_true", help="skip the per-workload iteration table")
+    ap.add_argument("--systems-only", action="store_true")
     ap.add_argument("--learned-train", type=int, default=10_000_000, help="training transitions")
     ap.add_argument("--learned-steps", type=int, default=6000, help="training steps")
     return ap.parse_args()
@@ -281,6 +283,61 @@ def run_serving(levels, n_ticks, seed=0, mix=None):
     return out
 
 
+SYSTEM_CONFIGS = (("cart-pole", W.CARTPOLE, 1000, 100), ("car", W.CAR, 4096, 100), ("car", W.CAR, 16384, 100),
+                  ("quadrotor", W.QUAD, 8192, 150))
+
+
+def run_systems(steps=200, warmup=10):
+    """Device-resident receding-horizon iterations (mppi_iterate_async: one graph per
+    iteration) of each workload configuration: cart-pole K=1000 T=100, car K=4096 and 16384
+    T=100, quadrotor K=8192 T=150.  Per configuration: rollout-steps/s, iteration time and the
+    rollout kernel's algorithmic FP32 rate against the FP32 peak (rollout timed alone)."""
+    import torch
+
+    from paper_1509_01149_b300 import _native as N
+    out = []
+    s = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for name, system, K, T in SYSTEM_CONFIGS:
+        cfg = W.config(system, K=K, T=T)
+        c = N.Controller(system, K, T, cfg["dt"], cfg["nu"], cfg["lam"], cfg["Sigma"], cfg["R"])
+        c.set_stream(s.cuda_stream)
+        if system == W.CAR:
+            c.set_cost_map(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL)
+        elif system == W.QUAD:
+            c.set_forest(W.quad_forest(0), W.QUAD_GOAL)
+        c.set_controls(np.asarray(cfg["U"], np.float32))
+        c.set_u_init(np.asarray(cfg["u_init"], np.float32))
+        dx = torch.tensor(np.asarray(cfg["x0"], np.float32), device="cuda")
+        du = torch.zeros(4, device="cuda")
+        for _ in range(warmup):
+            c.iterate_async(dx.data_ptr(), du.data_ptr())
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        rv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        with torch.cuda.stream(s):
+            for a, b in ev:
+                flush.zero_()
+                a.record(s)
+                c.iterate_async(dx.data_ptr(), du.data_ptr())
+                b.record(s)
+            for a, b in rv:
+                flush.zero_()
+                a.record(s)
+                c.rollout_async(dx.data_ptr())
+                b.record(s)
+                c.update_async(None)
+                c.shift()
+        torch.cuda.synchronize()
+        it_ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        ro_ms = statistics.median(a.elapsed_time(b) for a, b in rv)
+        tf = ALGO_FLOPS_PER_ROLLOUT_STEP[system] * K * T / (ro_ms * 1e-3) / 1e12
+        out.append({"system": name, "K": K, "T": T, "iteration_ms": it_ms, "rollout_ms": ro_ms,
+                    "rollout_steps_per_s": K * T / (it_ms * 1e-3), "iters_per_s": 1e3 / it_ms,
+                    "rollout_tflops_algorithmic": tf, "fp32_frac": tf / fp32_peak_tflops()})
+        c.close()
+    return out
+
+
 def run_capacity(probe=(16, 64), ticks=5, cap=2048, seed=0):
     """Largest number of identical controllers of each (system, K, T) that one server steps
     within the 20 ms (50 Hz) deadline: tick time measured at two probe sizes (autotuned at the
@@ -449,6 +506,9 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     levels = [int(v) for v in args.serving.split(",") if v.strip()]
     heavy_levels = [int(v) for v in args.serving_heavy.split(",") if v.strip()]
+    if args.systems_only:
+        print(json.dumps({"systems": run_systems()}), flush=True)
+        return
     if args.serving_only:
         from paper_1509_01149_b300.serving import HEAVY_MIX
         res = {"serving": run_serving(levels, args.serving_ticks)}
@@ -576,6 +636,7 @@ def run_ours(args, rank, world, local_rank):
     heavy_res = run_serving(heavy_levels, args.serving_ticks, seed=rank, mix=HEAVY_MIX) if heavy_levels else None
     capacity_res = run_capacity(seed=rank) if args.serving_capacity else None
     learned_res = None if args.no_learned else run_learned(args.learned_train, steps=args.learned_steps)
+    systems_res = None if args.no_systems else run_systems()
 
     if rank != 0:
         if dist is not None:
@@ -634,6 +695,7 @@ def run_ours(args, rank, world, local_rank):
         "serving": serving_res,
         "serving_heavy": heavy_res and dict(heavy_res, mix=HEAVY_MIX),
         "serving_capacity": capacity_res,
+        "systems": systems_res,
         "learned": learned_res,
         "source_hash": source_hash(),
     }

@@ -107,6 +107,7 @@ struct mppi_ctx {
   int sys = 0, K = 0, T = 0, m = 0, n = 0;
   int impl = MPPI_IMPL_FUSED;
   int blk = 0, nblk = 0;
+  int nblk_cap = 0;  // block partials the arena holds
   CtrlParams p{};
   uint64_t seed = 0;
   std::string err;
@@ -458,7 +459,8 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   if (rc == MPPI_OK) rc = c->cuda(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream");
   if (rc == MPPI_OK) c->own_stream = true;
   const size_t TM = static_cast<size_t>(T) * m;
-  const size_t nb_max = (K + kFusedBlockSmall - 1) / kFusedBlockSmall;
+  const size_t nb_max = (K + kMinBlockSamples - 1) / kMinBlockSamples;  // block partials of any shape fit
+  c->nblk_cap = static_cast<int>(nb_max);
   c->arena.size = 256 * 16 + sizeof(CtrlState) + sizeof(float) * (2 * TM + 2 * kMaxM + K + nb_max * TM) +
                   sizeof(BlockPartial) * nb_max + sizeof(StepDebug) + 2 * sizeof(uint32_t);
   if (rc == MPPI_OK) rc = c->cuda(cudaMalloc(&c->arena.base, c->arena.size), "cudaMalloc(arena)");
@@ -645,6 +647,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   c->p = np;
   c->blk = c->sys == MPPI_CAR_MLP ? kFusedBlockRegen : fused_block_size(c->sys, c->p);
   c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+  if (c->nblk > c->nblk_cap) return c->fail(MPPI_EINVAL, "block shape needs more partials than allocated");
   c->env_ok = true;
   c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;

@@ -10,6 +10,9 @@ constexpr int kFusedBlockLarge = 128;
 constexpr int kFusedBlockSmall = 64;
 constexpr int kFusedBlockRegen = 129;   // code for "128 samples, du regenerated (no shared-memory copy)"
 constexpr int kFusedBlockCarWs = 257;   // code for "car, 128 samples, three threads per sample"
+constexpr int kFusedBlockQuadLanes = 513;  // code for "quadrotor, 32 samples, four lanes per sample"
+constexpr int kQuadLanesBlock = 128, kQuadLanes = 4;
+constexpr int kMinBlockSamples = kQuadLanesBlock / kQuadLanes;  // fewest samples per block of any shape
 constexpr int kMergeThreads = 256;
 constexpr int kMergeOutputs = 32;       // outputs (i, j) per merge block
 constexpr size_t kFusedSmemLimit = 200 * 1024;
@@ -21,9 +24,10 @@ cudaError_t prepare_kernels();
 // Fused path ---------------------------------------------------------------
 // Shared memory of the fused rollout for block size blk (bytes).
 size_t fused_smem_bytes(const CtrlParams &p, int blk);
-// Block shape for a controller of system sys: for the car, kFusedBlockCarWs when its
-// shared memory fits; else 128 or 64 samples with du kept in shared memory, else
-// kFusedBlockRegen (128 samples, du regenerated); 0 if nothing fits.
+// Block shape for a controller of system sys: for the car kFusedBlockCarWs and for the
+// quadrotor kFusedBlockQuadLanes when their shared memory fits; else 128 or 64 samples with
+// du kept in shared memory, else kFusedBlockRegen (128 samples, du regenerated); 0 if
+// nothing fits.
 int fused_block_size(int sys, const CtrlParams &p);
 // Samples per block of a block shape.
 int fused_block_samples(int blk);

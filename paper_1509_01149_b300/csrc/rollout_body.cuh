@@ -78,10 +78,13 @@ __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, in
 // that owns no sample (it only takes part in the block reduction).  BLK is the thread count;
 // in STORE mode threads 0..NS-1 own the NS samples of sDu's columns (NS = BLK unless some
 // threads hold no sample).
+// slot: the column of sDu (and of sW) this thread's sample owns in STORE mode, -1 for a
+// thread that owns none; by default thread t < NS owns column t.
 template <int M, int BLK, bool REGEN, int NS = BLK>
 __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32_t ctr, float Sk_raw, const float *Lnu,
                                               float *__restrict__ S_out, float *__restrict__ part_sums,
-                                              BlockPartial *__restrict__ part, float *sW, const float *sDu) {
+                                              BlockPartial *__restrict__ part, float *sW, const float *sDu,
+                                              int slot = -2) {
   constexpr int SPB = 4 / M, NW = BLK / 32;
   __shared__ float s_min[NW];
   __shared__ int s_idx[NW];
@@ -120,7 +123,8 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
   if (!REGEN) {
     static_assert(NS % 32 == 0 && NS <= BLK, "samples per block");
     constexpr int CPL = NS / 32;  // samples per lane
-    if (tid < NS) sW[tid] = w;
+    if (slot == -2) slot = tid < NS ? tid : -1;
+    if (slot >= 0) sW[slot] = w;
     __syncthreads();
     // warp per 32 outputs: lane l sums its CPL samples of each output (conflict-free rows of
     // sDu), then the transposed butterfly leaves output g*32 + l's block sum in lane l (FP32)

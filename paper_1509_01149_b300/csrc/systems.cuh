@@ -243,16 +243,32 @@ struct Quad {
     return s * rsqrtf(s);
   }
 
+  // Nearest cylinder surface.  The minimum is exact in any order, so the packed path keeps
+  // four independent running minima (a 4-wide dependency chain instead of one of n_obs).
   __device__ __forceinline__ static float obstacle_distance(const Env &e, float px, float py) {
     float d = INFINITY;
     if (e.obs_packed) {  // one 128-bit broadcast load per cylinder
       const float4 *o4 = reinterpret_cast<const float4 *>(e.obs);
-#pragma unroll 4
-      for (int j = 0; j < e.n_obs; ++j) {
-        const float4 c = o4[j];
-        const float dx = px - c.x, dy = py - c.y;
-        d = fminf(d, fast_sqrt(fmaf(dx, dx, dy * dy)) - c.z);
+      float d0 = INFINITY, d1 = INFINITY, d2 = INFINITY, d3 = INFINITY;
+      int j = 0;
+#pragma unroll 2
+      for (; j + 3 < e.n_obs; j += 4) {
+        const float4 c0 = o4[j], c1 = o4[j + 1], c2 = o4[j + 2], c3 = o4[j + 3];
+        float ax = px - c0.x, ay = py - c0.y;
+        d0 = fminf(d0, fast_sqrt(fmaf(ax, ax, ay * ay)) - c0.z);
+        ax = px - c1.x, ay = py - c1.y;
+        d1 = fminf(d1, fast_sqrt(fmaf(ax, ax, ay * ay)) - c1.z);
+        ax = px - c2.x, ay = py - c2.y;
+        d2 = fminf(d2, fast_sqrt(fmaf(ax, ax, ay * ay)) - c2.z);
+        ax = px - c3.x, ay = py - c3.y;
+        d3 = fminf(d3, fast_sqrt(fmaf(ax, ax, ay * ay)) - c3.z);
       }
+      for (; j < e.n_obs; ++j) {
+        const float4 c = o4[j];
+        const float ax = px - c.x, ay = py - c.y;
+        d0 = fminf(d0, fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z);
+      }
+      d = fminf(fminf(d0, d1), fminf(d2, d3));
     } else {
 #pragma unroll 4
       for (int j = 0; j < e.n_obs; ++j) {
@@ -260,6 +276,31 @@ struct Quad {
         d = fminf(d, fast_sqrt(fmaf(dx, dx, dy * dy)) - e.obs[3 * j + 2]);
       }
     }
+    return d;
+  }
+
+  // The same minimum split over a group of `lanes` consecutive lanes that hold the same
+  // sample (lane s takes cylinders s, s + lanes, ...), combined by butterfly shuffles.  Every
+  // lane of the warp must call it together; obstacles packed as float4.
+  __device__ __forceinline__ static float obstacle_distance_lanes(const Env &e, float px, float py, int sub,
+                                                                  int lanes) {
+    const float4 *o4 = reinterpret_cast<const float4 *>(e.obs);
+    float d0 = INFINITY, d1 = INFINITY;
+    int j = sub;
+    for (; j + lanes < e.n_obs; j += 2 * lanes) {
+      const float4 c0 = o4[j], c1 = o4[j + lanes];
+      float ax = px - c0.x, ay = py - c0.y;
+      d0 = fminf(d0, fast_sqrt(fmaf(ax, ax, ay * ay)) - c0.z);
+      ax = px - c1.x, ay = py - c1.y;
+      d1 = fminf(d1, fast_sqrt(fmaf(ax, ax, ay * ay)) - c1.z);
+    }
+    if (j < e.n_obs) {
+      const float4 c = o4[j];
+      const float ax = px - c.x, ay = py - c.y;
+      d0 = fminf(d0, fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z);
+    }
+    float d = fminf(d0, d1);
+    for (int o = 1; o < lanes; o <<= 1) d = fminf(d, __shfl_xor_sync(0xffffffffu, d, o));
     return d;
   }
 
@@ -323,6 +364,39 @@ struct Quad {
       for (int i = 0; i < N; ++i) x[i] = y[i];
       a.d = d;
     }
+  }
+
+  // step() for a lane group holding one sample: the RK4 step is taken by every lane (and by
+  // crashed samples, whose result is then discarded) so that the lanes of a warp stay together
+  // through the shuffles of the obstacle distance.  Same result as step().
+  __device__ __forceinline__ static void step_lanes(float x[N], const float f[M], Aux &a, const Env &e, float dt,
+                                                    int sub, int lanes) {
+    float k1[N], k2[N], k3[N], k4[N], y[N];
+    deriv(x, f, k1);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = x[i] + 0.5f * dt * k1[i];
+    deriv(y, f, k2);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = x[i] + 0.5f * dt * k2[i];
+    deriv(y, f, k3);
+#pragma unroll
+    for (int i = 0; i < N; ++i) y[i] = x[i] + dt * k3[i];
+    deriv(y, f, k4);
+    bool finite = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      y[i] = x[i] + (dt / 6.0f) * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
+      finite = finite && isfinite(y[i]);
+    }
+    float d = obstacle_distance_lanes(e, y[0], y[1], sub, lanes);
+    if (!finite) d = -1.0f;
+    const bool hit = !finite || d < 0.0f || y[2] < 0.0f || (pitch_limit - fabsf(y[7])) <= 0.0f;
+    if (!a.crashed && !hit) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) x[i] = y[i];
+      a.d = d;
+    }
+    a.crashed = a.crashed || hit;
   }
 
   __device__ __forceinline__ static float cost(const float x[N], const Aux &a, const Env &e) {
