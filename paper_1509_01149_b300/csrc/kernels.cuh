@@ -10,8 +10,8 @@ constexpr int kFusedBlockLarge = 128;
 constexpr int kFusedBlockSmall = 64;
 constexpr int kFusedBlockRegen = 129;   // code for "128 samples, du regenerated (no shared-memory copy)"
 constexpr int kFusedBlockCarWs = 257;   // code for "car, 128 samples, three threads per sample"
-constexpr int kFusedBlockQuadLanes = 513;  // code for "quadrotor, 32 samples, four lanes per sample"
-constexpr int kQuadLanesBlock = 128, kQuadLanes = 4;
+constexpr int kFusedBlockQuadLanes = 513;  // code for "quadrotor, 32 samples, a group of lanes per sample"
+constexpr int kQuadLanesBlock = 64, kQuadLanes = 2;
 constexpr int kMinBlockSamples = kQuadLanesBlock / kQuadLanes;  // fewest samples per block of any shape
 constexpr int kMergeThreads = 256;
 constexpr int kMergeOutputs = 32;       // outputs (i, j) per merge block
