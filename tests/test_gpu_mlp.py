@@ -277,3 +277,42 @@ def test_fp8_iteration_matches_the_e4m3_oracle(env, trained):
     assert np.mean(rel < 1e-2) > 0.8          # measured: 89 % of samples
     assert np.all(np.isfinite(g["S"])) and np.isfinite(g["eta"]) and g["eta"] >= 1.0
     ctl.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_learned_rollout_on_sampled_samples(env, trained, precision):
+    """The benchmark's learned-dynamics configuration (K = 16384, T = 100, the kernel launch the
+    bench times): path costs of 512 samples spread over every block, computed by the oracle one
+    sample at a time with the same noise, agree within the BF16 (median 2e-3, p99 5e-2) or FP8
+    (median 2e-3, 80 % within 1e-2) bars."""
+    torch, N = env
+    params, scale = trained
+    K, T = 16384, 100
+    c = W.config(W.CAR, K=K, T=T)
+    ctl = N.Controller(W.CAR_MLP, K, T, c["dt"], c["nu"], c["lam"], c["Sigma"], c["R"])
+    ctl.set_cost_map(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL)
+    ctl.set_env(N.mlp_blob(params, scale, precision=precision))
+    ctl.set_controls(np.zeros((T, 2), np.float32))
+    x0 = np.asarray(c["x0"], np.float32)
+    ctl.step(x0)
+    g = ctl.get_debug()
+    ctl.close()
+    from oracle import mppi as om
+    from oracle import philox as ophilox
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    idx = np.unique(np.concatenate([np.arange(0, K, 37), [K - 1]]))[:512]
+    du = ophilox.exploration_noise(0, K, T, f32(c["Sigma"]), 10.0, 0, 0)[:, :, idx]
+    if precision == 0:
+        q = {k: (omlp.round_bf16(v) if k.startswith("W") else v.astype(np.float64)) for k, v in params.items()}
+        sysm = omlp.CarMLP(c["dt"], W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL, q, scale,
+                           act_round=omlp.round_bf16)
+    else:
+        sysm = omlp.CarMLP(c["dt"], W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL,
+                           omlp.quantize_e4m3_weights(params), scale, act_round=omlp.round_e4m3)
+    S, _ = om.path_costs(sysm, f32(x0), np.zeros((T, 2)), du, f32(c["R"]), 10.0)
+    rel = np.abs(g["S"][idx] - S) / np.abs(S)
+    assert np.median(rel) < 2e-3, np.median(rel)
+    if precision == 0:
+        assert np.percentile(rel, 99) < 5e-2, np.percentile(rel, 99)
+    else:
+        assert np.mean(rel < 1e-2) > 0.8, np.mean(rel < 1e-2)
