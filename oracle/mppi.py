@@ -14,6 +14,11 @@ Follows Algorithm 1 (Sec. IV) with the special case of Sec. III-C
 * update: u_i <- u_i + sum_k w_k delta_u_{i,k}                (Eq. App_PI; Algorithm 1)
 * send u_0, then shift: u_i <- u_{i+1}, u_{T-1} <- u_init      (Algorithm 1)
 
+Per-time-step variant (Eq. App_PI read literally): u_i is weighted by the cost-to-go
+of each rollout from t_i onward, S~(tau_{i,k}) = sum_{j >= i} q~_{j,k} + phi(x_T), with
+its own minimum rho_i and normaliser eta_i (`iteration_to_go`).  At i = 0 this is the total
+path cost; with T = 1 the two weightings coincide.
+
 Readings where the paper is ambiguous (each is listed with its reason in the
 design notes):
 * no dt factor on q~ in S~ (Sec. III-B and Algorithm 1 add q~ without dt);
@@ -71,6 +76,27 @@ def path_costs(system, x0, U, du, R, nu):
     return S, st
 
 
+def step_costs(system, x0, U, du, R, nu):
+    """Per-step running costs C [T][K] (C[i] = q(x_{i+1}) + the IS terms of step i) and
+    phi(x_T) [K], in the order path_costs adds them."""
+    U = np.asarray(U, dtype=np.float64)
+    T, m, K = du.shape
+    st = system.init(x0, K)
+    C = np.zeros((T, K))
+    with np.errstate(all="ignore"):
+        for i in range(T):
+            v = U[i][:, None] + du[i]
+            st = system.step(st, v)
+            C[i] = system.q(st) + is_running_cost(U[i], du[i], R, nu)
+        phi = system.phi(st)
+    return C, phi, st
+
+
+def costs_to_go(C, phi):
+    """S~(tau_{i,k}) = sum_{j >= i} C[j, k] + phi[k]  (Eq. App_PI), [T][K]."""
+    return np.cumsum(C[::-1], axis=0)[::-1] + phi[None, :]
+
+
 def weights(S, lam):
     """(rho, kstar, eta, w) of the min-shifted exponential weighting."""
     S = np.where(np.isfinite(S), S, np.inf)
@@ -109,6 +135,34 @@ def iteration(system, x0, U, lam, nu, Sigma, R, seed, counter=0, gid=0, du=None)
     margin = getattr(st, "margin", None)
     return IterationResult(S=S, rho=rho, kstar=kstar, eta=eta, w=w, dU=dU, U=Un, u0=Un[0].copy(),
                            du=du, margin=margin)
+
+
+@dataclass
+class ToGoResult:
+    S: np.ndarray          # [T][K] costs-to-go (row 0: the total path cost)
+    rho: np.ndarray        # [T] per-step minimum
+    kstar: np.ndarray      # [T] per-step argmin
+    eta: np.ndarray        # [T] per-step normaliser
+    dU: np.ndarray         # [T][m] update
+    U: np.ndarray          # [T][m] updated controls
+    du: np.ndarray         # [T][m][K]
+
+
+def iteration_to_go(system, x0, U, K, lam, nu, Sigma, R, seed, counter=0, gid=0, du=None):
+    """One MPPI iteration with u_i weighted by the cost-to-go from t_i (no shift); the
+    counter-based noise of `philox` unless du [T][m][K] is given."""
+    U = np.asarray(U, dtype=np.float64)
+    if du is None:
+        du = philox.exploration_noise(seed, K, U.shape[0], Sigma, nu, counter, gid)
+    C, phi, _ = step_costs(system, x0, U, du, R, nu)
+    Sg = costs_to_go(C, phi)
+    T = U.shape[0]
+    rho, kst, eta = np.zeros(T), np.zeros(T, dtype=np.int64), np.zeros(T)
+    dU = np.zeros_like(U)
+    for i in range(T):
+        rho[i], kst[i], eta[i], w = weights(Sg[i], lam)
+        dU[i] = du[i] @ w
+    return ToGoResult(S=Sg, rho=rho, kstar=kst, eta=eta, dU=dU, U=U + dU, du=du)
 
 
 def iteration_seeded(system, x0, U, K, lam, nu, Sigma, R, seed, counter=0, gid=0):

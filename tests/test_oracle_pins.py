@@ -718,3 +718,59 @@ def test_e4m3_rounding_matches_the_library_format():
     want = torch.tensor(a).to(torch.float8_e4m3fn).to(torch.float32).numpy().astype(np.float64)
     assert np.array_equal(mlp.round_e4m3(a), want)
     assert mlp.round_e4m3(np.array([1000.0, -500.0]))[0] == 448.0
+
+
+# ---------------------------------------------------------------------------
+# per-time-step cost-to-go weighting (Eq. App_PI read literally)
+# ---------------------------------------------------------------------------
+def test_cost_to_go_weighting_reduces_to_the_path_weighting():
+    """Row 0 of the costs-to-go is the total path cost, so u_0's update is the path-weighted
+    one; with T = 1 the two weightings are the same iteration."""
+    lin = _double_integrator()
+    x0, lam, nu, R = np.array([1.0, -0.5]), 0.8, 3.0, np.eye(1) * 0.5
+    for T in (1, 5):
+        U = np.linspace(-0.3, 0.2, T)[:, None]
+        du = philox.exploration_noise(9, 300, T, np.eye(1) * 0.4, nu, 0, 0)
+        a = mppi.iteration(lin, x0, U, lam, nu, None, R, 0, du=du)
+        b = mppi.iteration_to_go(lin, x0, U, 300, lam, nu, None, R, 0, du=du)
+        assert np.allclose(b.S[0], a.S, rtol=1e-13)
+        assert np.allclose(b.dU[0], a.dU[0], rtol=1e-11, atol=1e-14)
+        if T == 1:
+            assert np.allclose(b.U, a.U, rtol=1e-11, atol=1e-14)
+
+
+def test_cost_to_go_weighting_brute_force():
+    """K = 2, T = 2 on x_{i+1} = v_i (memoryless), q = x^2, phi = 2 x^2, scalar R: the costs-to-go
+    and the two-sample logistic weights written out by hand."""
+    memo = Linear([[0.0]], [[1.0]], [[1.0]], [[2.0]])
+    nu, lam, r = 4.0, 0.7, 1.3
+    U = np.array([[0.2], [-0.1]])
+    d = np.array([[0.3, -0.5], [0.8, 0.1]])            # d[i][k]
+    du = d[:, None, :]
+    isc = lambda u, e: 0.5 * (1 - 1 / nu) * r * e * e + u * r * e + 0.5 * r * u * u
+    x1, x2 = U[0, 0] + d[0], U[1, 0] + d[1]
+    C0, C1 = x1 ** 2 + isc(U[0, 0], d[0]), x2 ** 2 + isc(U[1, 0], d[1])
+    phi = 2 * x2 ** 2
+    S = [C0 + C1 + phi, C1 + phi]
+    res = mppi.iteration_to_go(memo, [0.0], U, 2, lam, nu, None, np.array([[r]]), 0, du=du)
+    for i in range(2):
+        w1 = 1.0 / (1.0 + math.exp(-(S[i][1] - S[i][0]) / lam))
+        assert res.S[i] == pytest.approx(S[i], rel=1e-14)
+        assert res.dU[i, 0] == pytest.approx(w1 * d[i, 0] + (1 - w1) * d[i, 1], rel=1e-12)
+
+
+def test_cost_to_go_ignores_costs_before_t_i():
+    """On x_{i+1} = v_i each step's cost depends on that step's perturbation only: changing the
+    step-0 perturbations leaves the cost-to-go weights of every later step, and so their
+    updates, unchanged, while the path weighting changes them."""
+    memo = Linear([[0.0]], [[1.0]], [[1.0]], [[2.0]])
+    T, K, nu, lam, R = 4, 50, 2.0, 0.5, np.eye(1)
+    U = np.zeros((T, 1))
+    du = philox.exploration_noise(3, K, T, np.eye(1), nu, 0, 0)
+    du2 = du.copy()
+    du2[0] = philox.exploration_noise(4, K, 1, np.eye(1), nu, 0, 0)[0]
+    a, b = (mppi.iteration_to_go(memo, [0.0], U, K, lam, nu, None, R, 0, du=x) for x in (du, du2))
+    assert np.array_equal(a.dU[1:], b.dU[1:])
+    assert not np.allclose(a.dU[0], b.dU[0])
+    pa, pb = (mppi.iteration(memo, [0.0], U, lam, nu, None, R, 0, du=x) for x in (du, du2))
+    assert not np.allclose(pa.dU[1:], pb.dU[1:])
