@@ -68,6 +68,14 @@ typedef enum {
                           after each step, no graph                                        */
 } mppi_impl;
 
+/* weighting of the update (Eq. App_PI) */
+typedef enum {
+  MPPI_WEIGHT_PATH = 0,  /* default: one total path cost S~_k weights every u_i (Algorithm 1) */
+  MPPI_WEIGHT_TO_GO = 1  /* u_i weighted by each rollout's cost-to-go from t_i onward,
+                            S~(tau_{i,k}) = sum_{j >= i} q~_{j,k} + phi(x_T), with its own
+                            minimum and normaliser per i (Eq. App_PI read literally)        */
+} mppi_weighting;
+
 typedef struct mppi_ctx mppi_ctx;
 
 /* Create a controller (Algorithm 1's "Given" block: K, N=T, dt, nu, Sigma, R, lambda).
@@ -145,8 +153,16 @@ int mppi_get_iteration(mppi_ctx *ctx, uint32_t *counter);
 /* Stream for all device work of the ctx (a cudaStream_t on the ctx's device). */
 int mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
 
-/* Select the fused path (default) or the plain-loop baseline. */
+/* Select the fused path (default) or the plain-loop baseline.  EINVAL for the plain loop
+ * while the cost-to-go weighting is selected. */
 int mppi_set_impl(mppi_ctx *ctx, mppi_impl impl);
+
+/* Select the weighting of the update (mppi_weighting).  MPPI_WEIGHT_TO_GO runs on the fused
+ * path only, with one thread per sample and du and the per-step costs kept in shared memory
+ * (4*T*(m+1) bytes per sample); the update and the shift are then two launches.
+ * Errors: EINVAL (unknown mode; learned dynamics; plain loop selected; horizon too long for
+ * the shared memory), ENOMEM. */
+int mppi_set_weighting(mppi_ctx *ctx, int mode);
 
 /* Nominal control sequence, host [T][m] (copied in / out; get synchronises). */
 int mppi_set_controls(mppi_ctx *ctx, const float *h_U);

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmppi_b300.so")
 MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE, MPPI_ENOSYS = 0, -1, -2, -3, -4, -5, -6
 MPPI_CARTPOLE, MPPI_CAR, MPPI_QUAD, MPPI_CAR_MLP = 0, 1, 2, 3
 MPPI_IMPL_FUSED, MPPI_IMPL_PLAIN = 0, 1
+MPPI_WEIGHT_PATH, MPPI_WEIGHT_TO_GO = 0, 1
 MPPI_ENV_MAP, MPPI_ENV_FOREST, MPPI_ENV_MLP = 0x3150414D, 0x31524F46, 0x31504C4D
 STATE_DIM = {MPPI_CARTPOLE: 4, MPPI_CAR: 7, MPPI_QUAD: 12, MPPI_CAR_MLP: 7}
 CONTROL_DIM = {MPPI_CARTPOLE: 1, MPPI_CAR: 2, MPPI_QUAD: 4, MPPI_CAR_MLP: 2}
@@ -59,6 +60,7 @@ SIGNATURES = [
     ("mppi_get_iteration", C.c_int, [_P, C.POINTER(C.c_uint32)]),
     ("mppi_set_stream", C.c_int, [_P, _P]),
     ("mppi_set_impl", C.c_int, [_P, C.c_int]),
+    ("mppi_set_weighting", C.c_int, [_P, C.c_int]),
     ("mppi_set_controls", C.c_int, [_P, _FP]),
     ("mppi_get_controls", C.c_int, [_P, _FP]),
     ("mppi_set_u_init", C.c_int, [_P, _FP]),
@@ -272,6 +274,11 @@ class Controller:
 
     def mppi_set_impl(self, impl: int):
         self._chk(lib.mppi_set_impl(self._h, impl))
+
+    def mppi_set_weighting(self, mode: int):
+        self._chk(lib.mppi_set_weighting(self._h, mode))
+
+    set_weighting = mppi_set_weighting
 
     def mppi_set_controls(self, U):
         self._chk(lib.mppi_set_controls(self._h, _fp(_f32(U, self.T * self.m))))

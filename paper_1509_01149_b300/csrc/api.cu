@@ -106,6 +106,9 @@ struct Arena {
 struct mppi_ctx {
   int sys = 0, K = 0, T = 0, m = 0, n = 0;
   int impl = MPPI_IMPL_FUSED;
+  int weighting = MPPI_WEIGHT_PATH;
+  float *d_prho = nullptr;   // cost-to-go weighting: per-step block minima [nblk_cap][T]
+  double *d_peta = nullptr;  // and normalisers [nblk_cap][T]
   int blk = 0, nblk = 0;
   int nblk_cap = 0;  // block partials the arena holds
   CtrlParams p{};
@@ -171,11 +174,19 @@ int launch_rollout(mppi_ctx *c, const float *x0, cudaStream_t s) {
   if (c->sys == MPPI_CAR_MLP)
     return c->cuda(launch_rollout_mlp(c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, c->mlp_precision, s),
                    "mlp rollout launch");
+  if (c->weighting == MPPI_WEIGHT_TO_GO)
+    return c->cuda(launch_rollout_to_go(c->sys, c->blk, c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part,
+                                        c->d_prho, c->d_peta, s),
+                   "cost-to-go rollout launch");
   return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
                  "fused rollout launch");
 }
 
 int launch_update(mppi_ctx *c, float *u0_out, cudaStream_t s) {
+  if (c->weighting == MPPI_WEIGHT_TO_GO)
+    return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->d_U, u0_out,
+                                      c->d_dU, c->d_dbg, s),
+                   "cost-to-go merge launch");
   return c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU, c->d_dbg, s),
                  "merge launch");
 }
@@ -214,7 +225,7 @@ int capture_step(mppi_ctx *c, bool shift, cudaGraphExec_t *out) {
                    "x0 copy");
   if (rc == MPPI_OK) rc = launch_rollout(c, c->d_st->x0, c->stream);
   if (rc == MPPI_OK) {
-    if (shift && merge_shift_fusable(c->p)) {
+    if (shift && merge_shift_fusable(c->p) && c->weighting == MPPI_WEIGHT_PATH) {
       rc = c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->dh_u0, c->d_dU,
                                              c->d_dbg, c->d_uinit, c->d_st, c->stream),
                    "merge + shift launch");
@@ -507,6 +518,8 @@ int mppi_destroy(mppi_ctx *c) {
   if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->d_du) cudaFree(c->d_du);
+  if (c->d_prho) cudaFree(c->d_prho);
+  if (c->d_peta) cudaFree(c->d_peta);
   if (c->d_env) cudaFree(c->d_env);
   if (c->d_mlp) cudaFree(c->d_mlp);
   if (c->h_x0) cudaFreeHost(c->h_x0);
@@ -528,7 +541,37 @@ int mppi_set_stream(mppi_ctx *c, void *stream) {
 
 int mppi_set_impl(mppi_ctx *c, mppi_impl impl) {
   if (!c || (impl != MPPI_IMPL_FUSED && impl != MPPI_IMPL_PLAIN)) return MPPI_EINVAL;
+  if (impl == MPPI_IMPL_PLAIN && c->weighting == MPPI_WEIGHT_TO_GO)
+    return c->fail(MPPI_EINVAL, "the plain loop is built for the path weighting only");
   c->impl = impl;
+  return MPPI_OK;
+}
+
+namespace {
+// block shape for the ctx's system, environment and weighting (0 if nothing fits)
+int block_shape(mppi_ctx *c, const CtrlParams &p) {
+  if (c->sys == MPPI_CAR_MLP) return kFusedBlockRegen;
+  return c->weighting == MPPI_WEIGHT_TO_GO ? fused_block_size_to_go(p) : fused_block_size(c->sys, p);
+}
+}  // namespace
+
+int mppi_set_weighting(mppi_ctx *c, int mode) {
+  if (!c || (mode != MPPI_WEIGHT_PATH && mode != MPPI_WEIGHT_TO_GO)) return MPPI_EINVAL;
+  if (mode == MPPI_WEIGHT_TO_GO) {
+    if (c->sys == MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "the cost-to-go weighting is not built for the learned dynamics");
+    if (c->impl == MPPI_IMPL_PLAIN) return c->fail(MPPI_EINVAL, "the plain loop is built for the path weighting only");
+    if (fused_block_size_to_go(c->p) == 0)
+      return c->fail(MPPI_EINVAL, "horizon too long for the cost-to-go weighting's shared memory");
+    if (!c->d_prho) {
+      const size_t n = static_cast<size_t>(c->nblk_cap) * c->T;
+      MPPI_TRY(c->cuda(cudaMalloc(&c->d_prho, sizeof(float) * n), "cudaMalloc(step minima)"));
+      MPPI_TRY(c->cuda(cudaMalloc(&c->d_peta, sizeof(double) * n), "cudaMalloc(step normalisers)"));
+    }
+  }
+  c->weighting = mode;
+  c->blk = block_shape(c, c->p);
+  c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+  c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
 
@@ -620,7 +663,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
     payload = static_cast<const char *>(blob) + sizeof h;
     np.n_obs = h.n_obstacles;
     for (int i = 0; i < 3; ++i) np.goal[i] = h.goal[i];
-    if (fused_block_size(c->sys, np) == 0) return c->fail(MPPI_EINVAL, "forest too large for shared memory");
+    if (block_shape(c, np) == 0) return c->fail(MPPI_EINVAL, "forest too large for shared memory");
   } else {
     return c->fail(MPPI_EINVAL, "unknown env kind 0x%08x", kind);
   }
@@ -645,7 +688,8 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   }
   np.mlp = c->p.mlp;
   c->p = np;
-  c->blk = c->sys == MPPI_CAR_MLP ? kFusedBlockRegen : fused_block_size(c->sys, c->p);
+  c->blk = block_shape(c, c->p);
+  if (c->blk == 0) return c->fail(MPPI_EINVAL, "environment too large for the block's shared memory");
   c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
   if (c->nblk > c->nblk_cap) return c->fail(MPPI_EINVAL, "block shape needs more partials than allocated");
   c->env_ok = true;
@@ -727,7 +771,7 @@ int mppi_iterate_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
     cudaGraph_t g = nullptr;
     MPPI_TRY(c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
     int rc = launch_rollout(c, d_state, c->stream);
-    if (rc == MPPI_OK && merge_shift_fusable(c->p)) {
+    if (rc == MPPI_OK && merge_shift_fusable(c->p) && c->weighting == MPPI_WEIGHT_PATH) {
       rc = c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0, c->d_dU, c->d_dbg,
                                              c->d_uinit, c->d_st, c->stream),
                    "merge + shift launch");

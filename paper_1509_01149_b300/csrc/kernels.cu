@@ -39,6 +39,20 @@ __global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const
                                  smem);
 }
 
+// cost-to-go weighting: one thread per sample, du in shared memory, per-step block partials
+template <class Sys, int BLK>
+__global__ void __launch_bounds__(BLK) k_rollout_to_go(const CtrlParams p, const float *__restrict__ x0,
+                                                       const CtrlState *__restrict__ st, const float *__restrict__ U,
+                                                       float *__restrict__ S_out, float *__restrict__ part_sums,
+                                                       BlockPartial *__restrict__ part, float *__restrict__ part_rho,
+                                                       double *__restrict__ part_eta) {
+  extern __shared__ __align__(16) float smem[];
+  rollout_block<Sys, BLK, false, true>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
+                                       part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
+                                       smem, nullptr, part_rho + static_cast<size_t>(blockIdx.x) * p.T,
+                                       part_eta + static_cast<size_t>(blockIdx.x) * p.T);
+}
+
 // car: three threads per sample (velocity recurrence / noise / pose and cost), see rollout_ws.cuh
 template <int NS>
 __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlParams p, const float *__restrict__ x0,
@@ -214,6 +228,108 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
     cluster_sync_all();  // all shifted values read before any is overwritten
     if (warp == 0 && o < TM) U[o] = sh;
     if (blockIdx.x == 0 && tid == 0) st->counter += 1u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 merge of the per-step block partials of the cost-to-go weighting + update of U
+// ---------------------------------------------------------------------------
+// One CTA per 32 outputs o = (i, j); lane = output, warps split the blocks.  Per output:
+//   rho_i = min_b rho_{b,i},  s_b = exp(-(rho_{b,i} - rho_i)/lambda),
+//   eta_i = sum_b s_b eta_{b,i},  du_o = sum_b s_b part_b[o] / eta_i   (FP64),
+// U[o] += du_o.  CTA 0 also reports step 0's (rho, k*, eta) from the BlockPartials.
+__global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, int m, float inv_lambda,
+                                                               const float *__restrict__ part_sums,
+                                                               const float *__restrict__ part_rho,
+                                                               const double *__restrict__ part_eta,
+                                                               const BlockPartial *__restrict__ part,
+                                                               float *__restrict__ U, float *__restrict__ u0_out,
+                                                               float *__restrict__ dU_dbg,
+                                                               StepDebug *__restrict__ dbg) {
+  constexpr int NW = kMergeThreads / 32;
+  __shared__ float s_r[NW][32];
+  __shared__ double s_e[NW][32], s_a[NW][32];
+  __shared__ float s_rho0[NW];
+  __shared__ int s_k0[NW];
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int TM = T * m;
+  const int o = blockIdx.x * kMergeOutputs + lane;
+  const bool live = o < TM;
+  const int i = live ? o / m : 0;
+  float r = INFINITY;
+  for (int b = warp; b < nblk; b += NW) r = fminf(r, part_rho[static_cast<size_t>(b) * T + i]);
+  s_r[warp][lane] = r;
+  __syncthreads();
+  float rho = INFINITY;
+#pragma unroll
+  for (int q = 0; q < NW; ++q) rho = fminf(rho, s_r[q][lane]);
+  double e = 0.0, a = 0.0;
+  if (live && isfinite(rho)) {
+    for (int b = warp; b < nblk; b += NW) {
+      const float rb = part_rho[static_cast<size_t>(b) * T + i];
+      const double sc = isfinite(rb) ? static_cast<double>(expf(-(rb - rho) * inv_lambda)) : 0.0;
+      e += sc * part_eta[static_cast<size_t>(b) * T + i];
+      a += sc * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
+    }
+  }
+  s_e[warp][lane] = e;
+  s_a[warp][lane] = a;
+  __syncthreads();
+  if (warp == 0 && live) {
+    double et = 0.0, at = 0.0;
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+      et += s_e[q][lane];
+      at += s_a[q][lane];
+    }
+    const double du = et > 0.0 ? at / et : 0.0;
+    const float un = U[o] + static_cast<float>(du);
+    U[o] = un;
+    dU_dbg[o] = static_cast<float>(du);
+    if (o < m) u0_out[o] = un;
+  }
+  if (blockIdx.x == 0) {  // step 0's scalars for the debug surface
+    float v = INFINITY;
+    int idx = INT_MAX;
+    for (int b = tid; b < nblk; b += kMergeThreads) {
+      const float rb = part[b].rho;
+      const int kk = part[b].kstar;
+      if (rb < v || (rb == v && kk < idx)) {
+        v = rb;
+        idx = kk;
+      }
+    }
+    warp_argmin(v, idx);
+    if (lane == 0) {
+      s_rho0[warp] = v;
+      s_k0[warp] = idx;
+    }
+    __syncthreads();
+    float vv = INFINITY;
+    int ii = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < NW; ++q)
+      if (s_rho0[q] < vv || (s_rho0[q] == vv && s_k0[q] < ii)) {
+        vv = s_rho0[q];
+        ii = s_k0[q];
+      }
+    double e0 = 0.0;
+    if (isfinite(vv))
+      for (int b = tid; b < nblk; b += kMergeThreads)
+        e0 += (isfinite(part[b].rho) ? static_cast<double>(expf(-(part[b].rho - vv) * inv_lambda)) : 0.0) *
+              part[b].eta;
+    e0 = warp_sum_d(e0);
+    if (lane == 0) s_e[warp][0] = e0;
+    __syncthreads();
+    if (tid == 0) {
+      double eta = 0.0;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) eta += s_e[q][0];
+      dbg->rho = vv;
+      dbg->kstar = ii;
+      dbg->eta = eta;
+    }
   }
 }
 
@@ -463,6 +579,50 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
   }
 }
 
+int fused_block_size_to_go(const CtrlParams &p) {
+  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true) <= kFusedSmemLimit) return kFusedBlockLarge;
+  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockSmall, false, true) <= kFusedSmemLimit) return kFusedBlockSmall;
+  return 0;
+}
+
+template <class Sys, int BLK>
+static cudaError_t launch_to_go_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
+                                  float *ps, BlockPartial *part, float *prho, double *peta, cudaStream_t s) {
+  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, false, true);
+  const int grid = (p.K + BLK - 1) / BLK;
+  k_rollout_to_go<Sys, BLK><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part, prho, peta);
+  return cudaGetLastError();
+}
+
+template <class Sys>
+static cudaError_t launch_to_go_sys(int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
+                                    const float *U, float *S, float *ps, BlockPartial *part, float *prho,
+                                    double *peta, cudaStream_t s) {
+  if (blk == kFusedBlockLarge) return launch_to_go_t<Sys, kFusedBlockLarge>(p, x0, st, U, S, ps, part, prho, peta, s);
+  if (blk == kFusedBlockSmall) return launch_to_go_t<Sys, kFusedBlockSmall>(p, x0, st, U, S, ps, part, prho, peta, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
+                                 const float *U, float *S, float *part_sums, BlockPartial *part, float *part_rho,
+                                 double *part_eta, cudaStream_t s) {
+  switch (sys) {
+    case 0: return launch_to_go_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
+    case 1: return launch_to_go_sys<Car>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
+    case 2: return launch_to_go_sys<Quad>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_merge_to_go(int nblk, const CtrlParams &p, const float *part_sums, const float *part_rho,
+                               const double *part_eta, const BlockPartial *part, float *U, float *u0_out,
+                               float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
+  const int TM = p.T * p.m;
+  k_merge_to_go<<<(TM + kMergeOutputs - 1) / kMergeOutputs, kMergeThreads, 0, s>>>(
+      nblk, p.T, p.m, p.inv_lambda, part_sums, part_rho, part_eta, part, U, u0_out, dU_dbg, dbg);
+  return cudaGetLastError();
+}
+
 cudaError_t prepare_kernels() {
   // dynamic shared memory above the 48 KB default, set once (outside any capture)
   const int big = 220 * 1024;
@@ -474,6 +634,12 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, true>),
       reinterpret_cast<const void *>(k_rollout_car_ws<kWsSamples>),
+      reinterpret_cast<const void *>(k_rollout_to_go<CartPole, kFusedBlockLarge>),
+      reinterpret_cast<const void *>(k_rollout_to_go<CartPole, kFusedBlockSmall>),
+      reinterpret_cast<const void *>(k_rollout_to_go<Car, kFusedBlockLarge>),
+      reinterpret_cast<const void *>(k_rollout_to_go<Car, kFusedBlockSmall>),
+      reinterpret_cast<const void *>(k_rollout_to_go<Quad, kFusedBlockLarge>),
+      reinterpret_cast<const void *>(k_rollout_to_go<Quad, kFusedBlockSmall>),
       reinterpret_cast<const void *>(k_rollout_quad_lanes<kQuadLanesBlock, kQuadLanes>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall, false>),

@@ -46,6 +46,16 @@ bool merge_shift_fusable(const CtrlParams &p);
 cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                       float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
                                       CtrlState *st, cudaStream_t s);
+// Cost-to-go weighting (Eq. App_PI per time step): block shape (128 or 64 samples, du and the
+// step costs in shared memory; 0 if they do not fit), the rollout with per-step block partials
+// (part_rho / part_eta [nblk][T]) and their FP64 merge + update.
+int fused_block_size_to_go(const CtrlParams &p);
+cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
+                                 const float *U, float *S, float *part_sums, BlockPartial *part, float *part_rho,
+                                 double *part_eta, cudaStream_t s);
+cudaError_t launch_merge_to_go(int nblk, const CtrlParams &p, const float *part_sums, const float *part_rho,
+                               const double *part_eta, const BlockPartial *part, float *U, float *u0_out,
+                               float *dU_dbg, StepDebug *dbg, cudaStream_t s);
 // Shift of Algorithm 1 and iteration counter increment.
 cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s);
 

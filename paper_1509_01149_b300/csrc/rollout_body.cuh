@@ -64,10 +64,83 @@ __device__ __forceinline__ float transpose_reduce32(float v[32]) {
   return v[0];
 }
 
-// Shared-memory bytes of rollout_block (dynamic part) for T*M outputs.
-__host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, int blk, bool regen) {
+// Shared-memory bytes of rollout_block (dynamic part) for T*M outputs; to_go adds the
+// per-step costs [T][blk] of the cost-to-go weighting.
+__host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, int blk, bool regen, bool to_go = false) {
   const size_t TM = static_cast<size_t>(T) * M;
-  return 16 + sizeof(float) * (2 * TM + T + 4 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk));
+  return 16 + sizeof(float) * (2 * TM + T + 4 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk) +
+                               (to_go ? static_cast<size_t>(T) * blk : 0));
+}
+
+// Per-time-step block partials of the cost-to-go weighting (Eq. App_PI read literally: u_i
+// weighted by each rollout's cost from t_i onward).  sC [T][BLK] holds each thread's step
+// costs c_i (the terms its path sum added); the block turns them into costs-to-go
+// S_i = c_i + ... + c_{T-1} + phi (compensated, backward, in place), then per step i, one warp
+// per step:
+//   rho_{b,i} = min_k S_i,  eta_{b,i} = sum_k exp(-(S_i - rho_{b,i})/lambda) (FP64),
+//   part_sums[i*M+j] = sum_k w_{i,k} du_{i,j,k} (FP32),
+// and `part` gets step 0's (rho, k*, eta) (the total path cost's, for the debug surface).
+// Samples k >= K and non-finite costs count as +inf.
+template <int M, int BLK>
+__device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k, float phi, float *sC,
+                                                    const float *sDu, float *__restrict__ part_sums,
+                                                    float *__restrict__ part_rho, double *__restrict__ part_eta,
+                                                    BlockPartial *__restrict__ part) {
+  constexpr int NW = BLK / 32, CPL = BLK / 32;
+  const int T = p.T, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool valid = k < p.K;
+  {
+    KahanSum s;
+    s.s = phi;
+    for (int i = T - 1; i >= 0; --i) {
+      s.add(sC[i * BLK + tid]);
+      sC[i * BLK + tid] = valid && isfinite(s.s) ? s.s : INFINITY;
+    }
+  }
+  __syncthreads();
+  for (int i = warp; i < T; i += NW) {
+    float sv[CPL];
+    float mv = INFINITY;
+    int mi = INT_MAX;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      sv[c] = sC[i * BLK + lane + 32 * c];
+      const int kk = k - tid + lane + 32 * c;  // sample of that column
+      if (sv[c] < mv || (sv[c] == mv && kk < mi)) {
+        mv = sv[c];
+        mi = isfinite(sv[c]) ? kk : INT_MAX;
+      }
+    }
+    warp_argmin(mv, mi);
+    const float rho = mv;
+    double e = 0.0;
+    float acc[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) acc[j] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const float w = (isfinite(rho) && isfinite(sv[c])) ? expf(-(sv[c] - rho) * p.inv_lambda) : 0.0f;
+      e += static_cast<double>(w);
+#pragma unroll
+      for (int j = 0; j < M; ++j) acc[j] = fmaf(w, sDu[(i * M + j) * BLK + lane + 32 * c], acc[j]);
+    }
+    e = warp_sum_d(e);
+#pragma unroll
+    for (int j = 0; j < M; ++j) acc[j] = warp_sum_f(acc[j]);
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < M; ++j) part_sums[i * M + j] = acc[j];
+      part_rho[i] = rho;
+      part_eta[i] = e;
+      if (i == 0) {
+        BlockPartial bp;
+        bp.eta = e;
+        bp.rho = rho;
+        bp.kstar = mi;
+        *part = bp;
+      }
+    }
+  }
 }
 
 // The block's softmax partial from each thread's path cost Sk_raw (sample k):
@@ -199,11 +272,15 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
 //   smem     dynamic shared memory of rollout_smem_bytes(...)
 //   du_ext   STORE only: if not null, the [TM][BLK] perturbation buffer lives there (a
 //            global-memory slab owned by this CTA) instead of in shared memory
-template <class Sys, int BLK, bool REGEN>
+//   TOGO     cost-to-go weighting (STORE only): per-step partials into part_sums, part_rho
+//            [T] and part_eta [T] of this block (block_partial_to_go)
+template <class Sys, int BLK, bool REGEN, bool TOGO = false>
 __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                               const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                               float *__restrict__ part_sums, BlockPartial *__restrict__ part,
-                                              float *smem, float *du_ext = nullptr) {
+                                              float *smem, float *du_ext = nullptr, float *part_rho = nullptr,
+                                              double *part_eta = nullptr) {
+  static_assert(!(TOGO && REGEN), "the cost-to-go weighting keeps du in shared memory");
   constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M;
   static_assert(4 % M == 0, "controls per Philox block must divide 4");
   const int T = p.T, TM = T * M, tid = threadIdx.x;
@@ -213,6 +290,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   float *sHu = sRu + TM;            // [T]   1/2 u_i^T R u_i
   float *sW = sHu + T;              // [BLK] weights
   float *sDu = du_ext ? du_ext : sW + BLK;  // STORE only: [TM][BLK] perturbations of this block
+  float *sC = sW + BLK + static_cast<size_t>(TM) * BLK;  // TOGO only: [T][BLK] step costs
 
   __shared__ float sx0[N];  // x0 staged once per block (it may live in mapped host memory)
   for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
@@ -268,7 +346,11 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
       duRdu = fmaf(du[j], rd, duRdu);
     }
     Sys::step(x, v, aux, env, p.dt);
-    if (have) S.add(Sys::cost_finish(pend, env) + pend_is);
+    if (have) {
+      const float c = Sys::cost_finish(pend, env) + pend_is;
+      S.add(c);
+      if (TOGO) sC[(i - 1) * BLK + tid] = c;
+    }
     pend = Sys::cost_issue(x, aux, env);
     pend_is = p.is_du * duRdu + uRdu + sHu[i];
     have = true;
@@ -294,10 +376,20 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
       if (i < T) step_at(i, eps + s * M);
     }
   }
-  if (have) S.add(Sys::cost_finish(pend, env) + pend_is);
-  S.add(Sys::cost(x, aux, env));  // phi(x_T) = q(x_T)
+  if (have) {
+    const float c = Sys::cost_finish(pend, env) + pend_is;
+    S.add(c);
+    if (TOGO) sC[(T - 1) * BLK + tid] = c;
+  }
+  const float phi = Sys::cost(x, aux, env);
+  S.add(phi);  // phi(x_T) = q(x_T)
   // the update kernel may start launching now (it waits for this grid's results itself)
   asm volatile("griddepcontrol.launch_dependents;");
+  if (TOGO) {
+    if (k < p.K) S_out[k] = isfinite(S.s) ? S.s : INFINITY;
+    block_partial_to_go<M, BLK>(p, k, phi, sC, sDu, part_sums, part_rho, part_eta, part);
+    return;
+  }
   block_partial<M, BLK, REGEN>(p, k, ctr, S.s, Lnu, S_out, part_sums, part, sW, sDu);
 }
 

@@ -66,6 +66,22 @@ def oracle_iteration(cfg: dict, counter: int = 0, env_seed: int = 0):
                                   cfg.get("gid", 0))
 
 
+def oracle_iteration_to_go(cfg: dict, counter: int = 0, env_seed: int = 0):
+    """oracle_iteration with the per-time-step cost-to-go weighting (Eq. App_PI)."""
+    sys_ = oracle_system(cfg["system"], cfg["dt"], env_seed)
+    x0 = np.asarray(cfg["x0"], dtype=np.float32).astype(np.float64)
+    U = np.asarray(cfg["U"], dtype=np.float32).astype(np.float64)
+    R = cfg.get("R")
+    if R is None:
+        R = cfg["lam"] * np.linalg.inv(cfg["Sigma"])
+    Rf = np.asarray(R, dtype=np.float32).astype(np.float64)
+    Sf = np.asarray(cfg["Sigma"], dtype=np.float32).astype(np.float64)
+    nu = float(np.float32(cfg["nu"]))
+    lam = float(np.float32(cfg["lam"]))
+    return omppi.iteration_to_go(sys_, x0, U, cfg["K"], lam, nu, Sf, Rf, cfg.get("seed", 0), counter,
+                                 cfg.get("gid", 0))
+
+
 def s_errors(S_gpu, S_orc, mask=None):
     S_gpu = S_gpu.astype(np.float64)
     fin = np.isfinite(S_orc)
@@ -88,3 +104,20 @@ def control_scale(cfg):
 def noise_oracle(cfg, counter=0):
     return ophilox.exploration_noise(cfg.get("seed", 0), cfg["K"], cfg["T"], cfg["Sigma"], cfg["nu"], counter,
                                      cfg.get("gid", 0))
+
+
+def update_step_within_cost_error(U_gpu, U_orc, U0, du, S, rho, lam, tol, band_rtol=2 * S_RTOL):
+    """One time step's update checked where the costs determine it.  Samples more than
+    max(20 lambda, band_rtol |rho|) above the oracle's best keep weights below e^-20 on both
+    sides (the GPU's costs are within S_RTOL of the oracle's), so the GPU update U_gpu - U0 [m]
+    must be a convex combination (non-negative least squares) of the candidates'
+    perturbations du [m][K] within tol [m]; with one candidate that is the oracle's update."""
+    from scipy.optimize import nnls
+    band = max(20.0 * lam, band_rtol * abs(rho))
+    A = np.flatnonzero(np.nan_to_num(S, nan=np.inf, posinf=np.inf) - rho <= band)
+    if A.size <= 1:
+        return bool(np.all(np.abs(U_gpu - U_orc) <= tol))
+    D = du[:, A]
+    big = 1e3
+    w, _ = nnls(np.vstack([D, big * np.ones((1, A.size))]), np.concatenate([U_gpu - U0, [big]]))
+    return bool(np.all(np.abs(U_gpu - (U0 + D @ w)) <= tol))

@@ -218,3 +218,74 @@ def test_step_shift_equals_step_then_shift(N, system, T):
         assert np.array_equal(ua, ub)
     assert np.array_equal(a.get_controls(), b.get_controls())
     assert a.get_iteration() == b.get_iteration() == 3
+
+
+# ---------------------------------------------------------------------------
+# per-time-step cost-to-go weighting (Eq. App_PI read literally)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("system,K,T,lam", [(W.CARTPOLE, 1000, 100, 1.0), (W.CAR, 4096, 100, 30.0),
+                                            (W.CAR, 1000, 37, 300.0), (W.QUAD, 2048, 60, 1.0)])
+def test_cost_to_go_iteration(N, system, K, T, lam):
+    """u_i weighted by each rollout's cost from t_i onward: path costs (row 0) within the S~
+    bar, step 0's argmin exact, and every updated control within 1e-3 of the control scale."""
+    over = {"K": K, "T": T, "lam": lam}
+    if system == W.CAR and lam != 1.0:
+        over["R"] = np.linalg.inv(np.diag([0.3, 0.35]))   # R fixed: a larger lambda spreads the weights
+    cfg = W.config(system, **over)
+    c = P.make_controller(cfg)
+    c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    g, _ = P.gpu_iteration(cfg, ctrl=c)
+    o = P.oracle_iteration_to_go(cfg)
+    mask = None
+    if system == W.QUAD:
+        mask = P.oracle_iteration(cfg).margin > 1e-3
+    rel = P.s_errors(g["S"], o.S[0], mask)
+    assert rel.max() <= P.S_RTOL, rel.max()
+    if P.argmin_is_unique(o.S[0]):
+        assert g["kstar"] == o.kstar[0]
+    scale = P.control_scale(cfg)
+    err = np.abs(g["U"].astype(np.float64) - o.U)
+    bound = P.U_RTOL * (np.abs(o.U) + scale[None, :])
+    steps = np.ones(T, dtype=bool)
+    lamf = float(np.float32(lam))
+    if mask is not None:
+        # a quadrotor sample within 1e-3 of a crash boundary may crash one step apart in FP32
+        # and FP64, which moves its cost-to-go by the crash weight: check the steps whose
+        # oracle weights put less than 1e-3 of their mass on such samples (most of them)
+        with np.errstate(over="ignore", invalid="ignore"):
+            w = np.exp(-(o.S - o.rho[:, None]) / lamf) / o.eta[:, None]
+        steps = np.nan_to_num(w[:, ~mask]).sum(axis=1) < 1e-3
+        assert steps.mean() > 0.5, steps.mean()
+    # each step's weights may have near-ties (costs-to-go within the FP32 error of the best):
+    # there the update must lie in the hull of the near-tied candidates' perturbations
+    U0 = np.asarray(cfg["U"], np.float32).astype(np.float64)
+    for i in np.flatnonzero(steps):
+        assert P.update_step_within_cost_error(g["U"][i].astype(np.float64), o.U[i], U0[i], o.du[i], o.S[i],
+                                               o.rho[i], lamf, bound[i]), (i, np.max(err[i] / bound[i]))
+
+
+def test_cost_to_go_with_one_step_equals_the_path_weighting(N):
+    cfg = W.config(W.CAR, K=3000, T=1, lam=50.0)
+    a = P.make_controller(cfg)
+    b = P.make_controller(cfg)
+    b.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    x = np.asarray(cfg["x0"], np.float32)
+    ua, ub = a.step(x), b.step(x)
+    # (the path weighting runs the car's warp-role kernel, this one the one-thread kernel:
+    # the same arithmetic, compiled apart, so equal to FP32 rounding)
+    assert np.allclose(ua, ub, rtol=1e-5, atol=1e-6)
+    assert np.allclose(a.get_debug()["S"], b.get_debug()["S"], rtol=2e-6)
+
+
+def test_cost_to_go_weighting_limits(N):
+    cfg = W.config(W.CAR, K=256, T=20)
+    c = P.make_controller(cfg)
+    c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    with pytest.raises(N.MppiError):
+        c.set_impl(N.MPPI_IMPL_PLAIN)
+    c.set_weighting(N.MPPI_WEIGHT_PATH)
+    c.set_impl(N.MPPI_IMPL_PLAIN)
+    with pytest.raises(N.MppiError):
+        c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    with pytest.raises(N.MppiError):
+        c.set_weighting(7)
