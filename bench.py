@@ -181,6 +181,22 @@ def oracle_rate(seconds: float, k_sample: int = 1024, max_iters: int | None = No
     return k_sample * T_STEPS * len(times) / sum(times), len(times), times
 
 
+def reduce_max(value: float, dist=None, device=None) -> float:
+    """The largest value over the ranks of the process group (float64 all-reduce), or the
+    value itself without one: the timed region of a multi-rank run is the slowest rank's."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def cpu_model() -> str:
     try:
         for line in open("/proc/cpuinfo"):
@@ -570,13 +586,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    units = K_SAMPLES * T_STEPS * args.steps * world
-    value = units / total_s
+    total_s = reduce_max(sum(step_ms) / 1e3, dist, dev)
+    value = whole_job_rate(K_SAMPLES * T_STEPS * args.steps, world, total_s)
     # the merge and the shift share one cluster launch while the T*m outputs fit 8 CTAs of 32
     fused_shift = T_STEPS * W.CONTROL_DIM[SYSTEM] <= 8 * 32
     launches_per_step = 2 if fused_shift else 3
@@ -612,12 +623,8 @@ def run_ours(args, rank, world, local_rank):
         lat.append(time.perf_counter() - t0)
     stream.synchronize()
     lat = lat[5:]
-    e2e_total = sum(lat)
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = K_SAMPLES * T_STEPS * e2e_steps * world / e2e_total
+    e2e_total = reduce_max(sum(lat), dist, dev)
+    e2e_value = whole_job_rate(K_SAMPLES * T_STEPS * e2e_steps, world, e2e_total)
 
     # ---- plain loop baseline (unfused kernels, sync per step) -----------------
     plain_steps = args.plain_steps or max(args.steps // 4, 10)
