@@ -13,6 +13,11 @@ models below are therefore readings, each stated where it is defined.
 * CartPole: force input, classic pole-on-cart equations (uniform rod of
   half-length l), explicit Euler (Sec. II-A).  Cost diag(1,1,10,1) on
   (x, xdot, theta, thetadot), theta = 0 upright, raw angle (no wrapping).
+* CartPoleVel: the cart-pole of Sec. V-A: the control is a desired cart velocity,
+  p'' = 10 (u - p'); the pole is a uniform rod of half-length l pivoted on the cart,
+  theta = 0 hanging down, theta'' = -(3 / (4 l)) (g sin theta + p'' cos theta); explicit
+  Euler.  Cost of Sec. V-A: p^2 + 500 (1 + cos theta)^2 + theta'^2 + p'^2 (zero at rest
+  upright, 2000 at rest hanging down).
 * Car: 7-state dynamic bicycle (X, Y, psi, vx, vy, r, delta) with a
   first-order steering actuator and simplified Pacejka tyres
   F_y = D sin(C atan(B alpha)); explicit Euler.  Cost: bilinear lookup of the
@@ -65,6 +70,40 @@ class CartPole:
     def q(self, x):
         w = self.p["w"]
         return w[0] * x[0] ** 2 + w[1] * x[1] ** 2 + w[2] * x[2] ** 2 + w[3] * x[3] ** 2
+
+    def phi(self, x):
+        return self.q(x)
+
+
+# ---------------------------------------------------------------------------
+# cart-pole of Sec. V-A (velocity input)
+# ---------------------------------------------------------------------------
+CARTPOLE_VEL_DEFAULTS = dict(l=0.5, g=9.81, k_vel=10.0)
+
+
+class CartPoleVel:
+    n, m = 4, 1
+
+    def __init__(self, dt: float, **params):
+        self.dt = dt
+        self.p = dict(CARTPOLE_VEL_DEFAULTS, **params)
+
+    def deriv(self, x, u):
+        """Time derivative of (p, p', theta, theta') under the desired velocity u."""
+        l, g, kv = self.p["l"], self.p["g"], self.p["k_vel"]
+        _, vel, th, om = x
+        acc = kv * (u - vel)
+        th_acc = -(3.0 / (4.0 * l)) * (g * np.sin(th) + acc * np.cos(th))
+        return np.stack([vel, acc, om, th_acc])
+
+    def init(self, x0, K):
+        return np.repeat(np.asarray(x0, dtype=np.float64)[:, None], K, axis=1)
+
+    def step(self, x, v):
+        return x + self.dt * self.deriv(x, v[0])
+
+    def q(self, x):
+        return x[0] ** 2 + 500.0 * (1.0 + np.cos(x[2])) ** 2 + x[3] ** 2 + x[1] ** 2
 
     def phi(self, x):
         return self.q(x)

@@ -21,6 +21,8 @@ def oracle_system(system: int, dt: float, env_seed: int = 0):
         return osys.Car(dt, W.car_cost_map(env_seed), W.MAP_ORIGIN, W.MAP_H_CELL)
     if system == W.QUAD:
         return osys.Quadrotor(dt, W.quad_forest(env_seed), W.QUAD_GOAL)
+    if system == W.CARTPOLE_VEL:
+        return osys.CartPoleVel(dt)
     raise ValueError(system)
 
 

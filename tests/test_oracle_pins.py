@@ -774,3 +774,50 @@ def test_cost_to_go_ignores_costs_before_t_i():
     assert not np.allclose(a.dU[0], b.dU[0])
     pa, pb = (mppi.iteration(memo, [0.0], U, lam, nu, None, R, 0, du=x) for x in (du, du2))
     assert not np.allclose(pa.dU[1:], pb.dU[1:])
+
+
+# ---------------------------------------------------------------------------
+# the cart-pole of Sec. V-A (velocity input)
+# ---------------------------------------------------------------------------
+def test_cartpole_vel_cost_is_the_papers():
+    """The Sec. V-A cost: the paper's weights, 2000 for the pole hanging at rest (the cost the
+    paper reports when the pole is never swung up), zero at rest upright."""
+    gold = json.load(open(os.path.join(GOLDEN, "paper_costs.json")))["cartpole_sec_V_A"]
+    cp = systems.CartPoleVel(0.02)
+    x = np.array([[0.3], [-0.2], [1.1], [0.7]])
+    want = (gold["w_p"] * 0.09 + gold["w_cos"] * (1 + math.cos(1.1)) ** 2 + gold["w_thetadot"] * 0.49 +
+            gold["w_pdot"] * 0.04)
+    assert cp.q(x)[0] == pytest.approx(want, rel=1e-14)
+    assert cp.q(np.zeros((4, 1)))[0] == pytest.approx(gold["hanging_cost_never_swung_up"], rel=1e-15)
+    assert cp.q(np.array([[0.0], [0.0], [math.pi], [0.0]]))[0] == pytest.approx(0.0, abs=1e-20)
+
+
+def test_cartpole_vel_equilibria_and_velocity_servo():
+    """Hanging and upright at rest with u = 0 are equilibria; the cart velocity follows the
+    commanded one with time constant 1/10 s: p'(t) = u (1 - e^{-10 t}) (Sec. V-A)."""
+    cp = systems.CartPoleVel(0.02)
+    for th in (0.0, math.pi):
+        assert np.allclose(cp.deriv(np.array([[0.5], [0.0], [th], [0.0]]), np.array([0.0])), 0.0, atol=1e-12)
+    gold = json.load(open(os.path.join(GOLDEN, "paper_costs.json")))["cartpole_sec_V_A"]
+    fine = systems.CartPoleVel(1e-5)
+    x = np.zeros((4, 1))
+    for _ in range(int(0.3 / 1e-5)):
+        x = fine.step(x, np.array([[1.5]]))
+    assert x[1, 0] == pytest.approx(1.5 * (1 - math.exp(-gold["velocity_gain"] * 0.3)), rel=1e-4)
+
+
+def test_cartpole_vel_small_oscillation_is_the_rod_pendulums():
+    """With the cart held (u = 0, at rest), a small swing of the uniform rod (length 2 l)
+    about its end has the textbook period 2 pi sqrt(2 (2 l) / (3 g))."""
+    l, g, dt = 0.5, 9.81, 1e-5
+    cp = systems.CartPoleVel(dt, l=l, g=g)
+    x = np.array([[0.0], [0.0], [0.01], [0.0]])
+    t, crossings, prev = 0.0, [], x[2, 0]
+    while len(crossings) < 3:
+        x = x + dt * cp.deriv(x, np.array([0.0]))       # explicit Euler at a tiny step
+        t += dt
+        if prev > 0 >= x[2, 0] or prev < 0 <= x[2, 0]:
+            crossings.append(t)
+        prev = x[2, 0]
+    period = crossings[2] - crossings[0]
+    assert period == pytest.approx(2 * math.pi * math.sqrt(2 * (2 * l) / (3 * g)), rel=2e-4)

@@ -27,10 +27,14 @@ import numpy as np
 # ----------------------------------------------------------------------------
 # system identifiers (must match the C enum mppi_system)
 # ----------------------------------------------------------------------------
-CARTPOLE, CAR, QUAD, CAR_MLP = 0, 1, 2, 3
-STATE_DIM = {CARTPOLE: 4, CAR: 7, QUAD: 12, CAR_MLP: 7}
-CONTROL_DIM = {CARTPOLE: 1, CAR: 2, QUAD: 4, CAR_MLP: 2}
-SYSTEM_NAME = {CARTPOLE: "cartpole", CAR: "car", QUAD: "quadrotor", CAR_MLP: "car_mlp"}
+CARTPOLE, CAR, QUAD, CAR_MLP, CARTPOLE_VEL = 0, 1, 2, 3, 4
+STATE_DIM = {CARTPOLE: 4, CAR: 7, QUAD: 12, CAR_MLP: 7, CARTPOLE_VEL: 4}
+CONTROL_DIM = {CARTPOLE: 1, CAR: 2, QUAD: 4, CAR_MLP: 2, CARTPOLE_VEL: 1}
+SYSTEM_NAME = {CARTPOLE: "cartpole", CAR: "car", QUAD: "quadrotor", CAR_MLP: "car_mlp",
+               CARTPOLE_VEL: "cartpole_vel"}
+# Sec. V-A: disturbance 1/sqrt(rho) = 0.01 in continuous time, i.e. a per-step control
+# standard deviation of 0.01 / sqrt(dt); control cost R = 1; lambda from Sigma = lambda R^-1
+CARTPOLE_VEL_SIGMA = 0.01 ** 2 / 0.02
 
 # ----------------------------------------------------------------------------
 # car track geometry (input recipe)
@@ -165,6 +169,10 @@ def config(system: int, **over) -> dict:
         c = dict(system=system, K=16384, T=100, dt=0.02, nu=10.0, lam=1.0,
                  Sigma=S, R=1.0 * np.linalg.inv(S), x0=car_x0(0), U=None,
                  u_init=np.zeros(2), seed=0)
+    elif system == CARTPOLE_VEL:
+        c = dict(system=CARTPOLE_VEL, K=1000, T=50, dt=0.02, nu=100.0, lam=CARTPOLE_VEL_SIGMA,
+                 Sigma=np.array([[CARTPOLE_VEL_SIGMA]]), R=np.array([[1.0]]),
+                 x0=np.zeros(4), U=None, u_init=np.zeros(1), seed=0)
     elif system == QUAD:
         S = quad_sigma()
         c = dict(system=QUAD, K=8192, T=150, dt=0.01, nu=50.0, lam=1.0,
@@ -173,7 +181,7 @@ def config(system: int, **over) -> dict:
     else:
         raise ValueError(system)
     c.update(over)
-    if "R" not in over and system != CARTPOLE:
+    if "R" not in over and system not in (CARTPOLE, CARTPOLE_VEL):
         c["R"] = c["lam"] * np.linalg.inv(c["Sigma"])
     if c["U"] is None:
         c["U"] = np.tile(np.asarray(c["u_init"], dtype=np.float64), (c["T"], 1))
