@@ -56,7 +56,11 @@ typedef enum {
                         cost map lookup + (vx-7)^2 (speed term of Sec. V-B)              */
   MPPI_QUAD = 2,     /* n=12 (p, v, roll/pitch/yaw, body rates), m=4 rotor thrusts; RK4;
                         cost of Sec. V-C with crash weight 1e4                          */
-  MPPI_CAR_MLP = 3   /* MPPI_CAR's cost with learned dynamics x' = x + MLP([x; u])       */
+  MPPI_CAR_MLP = 3,  /* MPPI_CAR's cost with learned dynamics x' = x + MLP([x; u])       */
+  MPPI_CARTPOLE_VEL = 4 /* the cart-pole of Sec. V-A: n=4 (p, pdot, theta, thetadot), theta = 0
+                           hanging down; m=1 desired cart velocity, pddot = 10 (u - pdot); Euler;
+                           q = p^2 + 500 (1 + cos theta)^2 + thetadot^2 + pdot^2.  Single
+                           controllers only (not in the server)                              */
 } mppi_system;
 
 /* implementation of mppi_step */

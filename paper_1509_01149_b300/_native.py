@@ -16,12 +16,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmppi_b300.so")
 
 MPPI_OK, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA, MPPI_ETIMEOUT, MPPI_ESTATE, MPPI_ENOSYS = 0, -1, -2, -3, -4, -5, -6
-MPPI_CARTPOLE, MPPI_CAR, MPPI_QUAD, MPPI_CAR_MLP = 0, 1, 2, 3
+MPPI_CARTPOLE, MPPI_CAR, MPPI_QUAD, MPPI_CAR_MLP, MPPI_CARTPOLE_VEL = 0, 1, 2, 3, 4
 MPPI_IMPL_FUSED, MPPI_IMPL_PLAIN = 0, 1
 MPPI_WEIGHT_PATH, MPPI_WEIGHT_TO_GO = 0, 1
 MPPI_ENV_MAP, MPPI_ENV_FOREST, MPPI_ENV_MLP = 0x3150414D, 0x31524F46, 0x31504C4D
-STATE_DIM = {MPPI_CARTPOLE: 4, MPPI_CAR: 7, MPPI_QUAD: 12, MPPI_CAR_MLP: 7}
-CONTROL_DIM = {MPPI_CARTPOLE: 1, MPPI_CAR: 2, MPPI_QUAD: 4, MPPI_CAR_MLP: 2}
+STATE_DIM = {MPPI_CARTPOLE: 4, MPPI_CAR: 7, MPPI_QUAD: 12, MPPI_CAR_MLP: 7, MPPI_CARTPOLE_VEL: 4}
+CONTROL_DIM = {MPPI_CARTPOLE: 1, MPPI_CAR: 2, MPPI_QUAD: 4, MPPI_CAR_MLP: 2, MPPI_CARTPOLE_VEL: 1}
 
 MPPI_EBUSY = -7
 

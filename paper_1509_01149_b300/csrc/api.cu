@@ -25,6 +25,7 @@ int state_dim(int sys) {
     case MPPI_CAR: return 7;
     case MPPI_QUAD: return 12;
     case MPPI_CAR_MLP: return 7;
+    case MPPI_CARTPOLE_VEL: return 4;
     default: return 0;
   }
 }
@@ -34,6 +35,7 @@ int control_dim(int sys) {
     case MPPI_CAR: return 2;
     case MPPI_QUAD: return 4;
     case MPPI_CAR_MLP: return 2;
+    case MPPI_CARTPOLE_VEL: return 1;
     default: return 0;
   }
 }

@@ -563,6 +563,7 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
                                  const float *U, float *S, float *part_sums, BlockPartial *part, cudaStream_t s) {
   switch (sys) {
     case 0: return launch_fused_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, s);
+    case 4: return launch_fused_sys<CartPoleVel>(blk, p, x0, st, U, S, part_sums, part, s);
     case 1:
       if (blk == kFusedBlockCarWs) return launch_car_ws(p, x0, st, U, S, part_sums, part, s);
       return launch_fused_sys<Car>(blk, p, x0, st, U, S, part_sums, part, s);
@@ -608,6 +609,7 @@ cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const fl
                                  double *part_eta, cudaStream_t s) {
   switch (sys) {
     case 0: return launch_to_go_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
+    case 4: return launch_to_go_sys<CartPoleVel>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     case 1: return launch_to_go_sys<Car>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     case 2: return launch_to_go_sys<Quad>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     default: return cudaErrorInvalidValue;
@@ -630,6 +632,11 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<CartPole, kFusedBlockLarge, true>),
+      reinterpret_cast<const void *>(k_rollout_fused<CartPoleVel, kFusedBlockLarge, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<CartPoleVel, kFusedBlockSmall, false>),
+      reinterpret_cast<const void *>(k_rollout_fused<CartPoleVel, kFusedBlockLarge, true>),
+      reinterpret_cast<const void *>(k_rollout_to_go<CartPoleVel, kFusedBlockLarge>),
+      reinterpret_cast<const void *>(k_rollout_to_go<CartPoleVel, kFusedBlockSmall>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, true>),
@@ -730,6 +737,7 @@ cudaError_t launch_plain_rollout(int sys, const CtrlParams &p, const CtrlState *
   const int grid = (p.K + 127) / 128;
   switch (sys) {
     case 0: k_plain_rollout<CartPole><<<grid, 128, 0, s>>>(p, st, U, du, S); break;
+    case 4: k_plain_rollout<CartPoleVel><<<grid, 128, 0, s>>>(p, st, U, du, S); break;
     case 1: k_plain_rollout<Car><<<grid, 128, 0, s>>>(p, st, U, du, S); break;
     case 2: k_plain_rollout<Quad><<<grid, 128, 0, s>>>(p, st, U, du, S); break;
     default: return cudaErrorInvalidValue;

@@ -78,6 +78,7 @@ int dims(int sys, int *n, int *m) {
     case MPPI_CARTPOLE: *n = 4; *m = 1; return MPPI_OK;
     case MPPI_CAR: *n = 7; *m = 2; return MPPI_OK;
     case MPPI_QUAD: *n = 12; *m = 4; return MPPI_OK;
+    case MPPI_CARTPOLE_VEL: *n = 4; *m = 1; return MPPI_OK;
     default: return MPPI_EINVAL;
   }
 }

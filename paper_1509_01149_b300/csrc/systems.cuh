@@ -70,6 +70,43 @@ struct CartPole {
 };
 
 // ---------------------------------------------------------------------------
+// The cart-pole of Sec. V-A: the control is a desired cart velocity, p'' = 10 (u - p');
+// the pole is a uniform rod of half-length l with theta = 0 hanging down,
+// theta'' = -(3 / (4 l)) (g sin theta + p'' cos theta); explicit Euler.
+// q = p^2 + 500 (1 + cos theta)^2 + theta'^2 + p'^2.
+struct CartPoleVel {
+  static constexpr int N = 4, M = 1;
+  struct Aux {};
+  static constexpr float l = 0.5f, g = 9.81f, k_vel = 10.0f;
+
+  __device__ __forceinline__ static void init(const float *, Aux &, const Env &) {}
+
+  __device__ __forceinline__ static void step(float x[N], const float v[M], Aux &, const Env &, float dt) {
+    float s, c;
+    sincosf(x[2], &s, &c);
+    const float acc = k_vel * (v[0] - x[1]);
+    const float th_acc = -(3.0f / (4.0f * l)) * (g * s + acc * c);
+    x[0] += dt * x[1];
+    x[1] += dt * acc;
+    x[2] += dt * x[3];
+    x[3] += dt * th_acc;
+  }
+
+  __device__ __forceinline__ static float cost(const float x[N], const Aux &, const Env &) {
+    const float up = 1.0f + cosf(x[2]);
+    return x[0] * x[0] + 500.0f * up * up + x[3] * x[3] + x[1] * x[1];
+  }
+
+  struct Pending {
+    float q;
+  };
+  __device__ __forceinline__ static Pending cost_issue(const float x[N], const Aux &a, const Env &e) {
+    return Pending{cost(x, a, e)};
+  }
+  __device__ __forceinline__ static float cost_finish(const Pending &pd, const Env &) { return pd.q; }
+};
+
+// ---------------------------------------------------------------------------
 // Bilinear lookup of a cost map [H][W], node (ix, iy) at (ox + ix/inv_cell, oy + iy/inv_cell),
 // coordinates clamped to the grid (NaN clamps to node 0).
 __device__ __forceinline__ float map_bilinear(const Env &e, float X, float Y) {

@@ -289,3 +289,42 @@ def test_cost_to_go_weighting_limits(N):
         c.set_weighting(N.MPPI_WEIGHT_TO_GO)
     with pytest.raises(N.MppiError):
         c.set_weighting(7)
+
+
+# ---------------------------------------------------------------------------
+# the cart-pole of Sec. V-A (velocity input), with the paper's lambda = Sigma R
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("impl,nu", [(0, 100.0), (1, 100.0), (0, 1.0), (0, 1500.0)])
+def test_cartpole_vel_iteration(N, impl, nu):
+    """At the paper's temperature (lambda = 0.005 against path costs of ~1e5) the weights sit
+    on the best few samples, so each step's update is checked where the costs determine it."""
+    cfg = W.config(W.CARTPOLE_VEL, nu=nu)
+    g, _ = P.gpu_iteration(cfg, impl)
+    o = P.oracle_iteration(cfg)
+    rel = P.s_errors(g["S"], o.S)
+    assert rel.max() <= P.S_RTOL, rel.max()
+    if P.argmin_is_unique(o.S):
+        assert g["kstar"] == o.kstar
+    scale = P.control_scale(cfg)
+    bound = P.U_RTOL * (np.abs(o.U) + scale[None, :])
+    U0 = np.asarray(cfg["U"], np.float32).astype(np.float64)
+    lam = float(np.float32(cfg["lam"]))
+    for i in range(cfg["T"]):
+        assert P.update_step_within_cost_error(g["U"][i].astype(np.float64), o.U[i], U0[i], o.du[i], o.S, o.rho,
+                                               lam, bound[i]), i
+
+
+def test_cartpole_vel_cost_to_go(N):
+    cfg = W.config(W.CARTPOLE_VEL, nu=300.0)
+    c = P.make_controller(cfg)
+    c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    g, _ = P.gpu_iteration(cfg, ctrl=c)
+    o = P.oracle_iteration_to_go(cfg)
+    assert P.s_errors(g["S"], o.S[0]).max() <= P.S_RTOL
+    scale = P.control_scale(cfg)
+    bound = P.U_RTOL * (np.abs(o.U) + scale[None, :])
+    U0 = np.asarray(cfg["U"], np.float32).astype(np.float64)
+    lam = float(np.float32(cfg["lam"]))
+    for i in range(cfg["T"]):
+        assert P.update_step_within_cost_error(g["U"][i].astype(np.float64), o.U[i], U0[i], o.du[i], o.S[i],
+                                               o.rho[i], lam, bound[i]), i
