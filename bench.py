@@ -22,6 +22,7 @@ import argparse
 import glob
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -73,6 +74,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-dynamics measurement")
     ap.add_argument("--learned-only", action="store_true")
     ap.add_argument("--no-systems", action="store_true", help="skip the per-workload iteration table")
+    ap.add_argument("--nu-sweep", action="store_true",
+                    help="only the Sec. V-A cart-pole swing-up over exploration variance and K")
     ap.add_argument("--systems-only", action="store_true")
     ap.add_argument("--learned-train", type=int, default=10_000_000, help="training transitions")
     ap.add_argument("--learned-steps", type=int, default=6000, help="training steps")
@@ -359,6 +362,46 @@ def run_systems(steps=200, warmup=10):
     return out
 
 
+def cartpole_vel_plant(x, u, dt):
+    """The Sec. V-A cart-pole (desired-velocity input) as the simulated plant: one explicit
+    Euler step in FP64 on the host (x = p, p', theta, theta'; theta = 0 hanging down)."""
+    p, v, th, om = x
+    acc = 10.0 * (u - v)
+    th_acc = -(3.0 / (4.0 * 0.5)) * (9.81 * np.sin(th) + acc * np.cos(th))
+    return np.array([p + dt * v, v + dt * acc, th + dt * om, om + dt * th_acc])
+
+
+def run_nu_sweep(nus=(1.0, 10.0, 50.0, 100.0, 300.0, 1000.0, 1500.0), Ks=(100, 1000, 10000), seconds=10.0, seed=0):
+    """The cart-pole swing-up of Sec. V-A in closed loop: 50 Hz receding horizon (T = 50,
+    1 s), the paper's natural noise 1/sqrt(rho) = 0.01 (Sigma = 0.005 per step, also applied to
+    the plant's control), R = 1, lambda = Sigma R, exploration variance nu Sigma.  Per (nu, K):
+    the average running cost of the plant's state over the run and the first time the pole
+    is within 0.3 rad of upright."""
+    from paper_1509_01149_b300 import _native as N
+    out = {}
+    for nu in nus:
+        for K in Ks:
+            cfg = W.config(W.CARTPOLE_VEL, K=K, nu=nu)
+            c = N.Controller(W.CARTPOLE_VEL, K, cfg["T"], cfg["dt"], nu, cfg["lam"], cfg["Sigma"], cfg["R"])
+            c.set_seed(seed)
+            c.set_controls(np.zeros((cfg["T"], 1), np.float32))
+            rng = np.random.default_rng(seed + 17)
+            x = np.zeros(4)
+            ticks = int(round(seconds / cfg["dt"]))
+            costs, up = [], None
+            sd = math.sqrt(cfg["Sigma"][0, 0])
+            for t in range(ticks):
+                u0 = float(c.step_shift(x.astype(np.float32))[0])
+                x = cartpole_vel_plant(x, u0 + sd * rng.standard_normal(), cfg["dt"])
+                q = x[0] ** 2 + 500.0 * (1.0 + math.cos(x[2])) ** 2 + x[3] ** 2 + x[1] ** 2
+                costs.append(q)
+                if up is None and abs(math.remainder(x[2] - math.pi, 2 * math.pi)) < 0.3:
+                    up = (t + 1) * cfg["dt"]
+            out[f"{nu:g}/{K}"] = {"nu": nu, "K": K, "average_cost": float(np.mean(costs)), "swing_up_s": up}
+            c.close()
+    return out
+
+
 def run_capacity(probe=(16, 64), ticks=5, cap=2048, seed=0):
     """Largest number of identical controllers of each (system, K, T) that one server steps
     within the 20 ms (50 Hz) deadline: tick time measured at two probe sizes (autotuned at the
@@ -529,6 +572,9 @@ def run_ours(args, rank, world, local_rank):
     heavy_levels = [int(v) for v in args.serving_heavy.split(",") if v.strip()]
     if args.systems_only:
         print(json.dumps({"systems": run_systems()}), flush=True)
+        return
+    if args.nu_sweep:
+        print(json.dumps({"nu_sweep": run_nu_sweep()}), flush=True)
         return
     if args.serving_only:
         from paper_1509_01149_b300.serving import HEAVY_MIX
