@@ -14,6 +14,12 @@ Follows Algorithm 1 (Sec. IV) with the special case of Sec. III-C
 * update: u_i <- u_i + sum_k w_k delta_u_{i,k}                (Eq. App_PI; Algorithm 1)
 * send u_0, then shift: u_i <- u_{i+1}, u_{T-1} <- u_init      (Algorithm 1)
 
+General sampling covariance (Theorem 1 with a general A_t, in control space): the noise
+of step i is drawn from N(0, Sigma_E,i) for any SPD Sigma_E,i instead of nu Sigma; with
+Sigma = lambda R^-1 the likelihood ratio of Theorem 1 becomes the running term
+  1/2 du^T (R - lambda Sigma_E,i^-1) du + u_i^T R du + 1/2 u_i^T R u_i,
+which is the (1 - 1/nu)/2 form above when Sigma_E,i = nu Sigma (`iteration_general`).
+
 Per-time-step variant (Eq. App_PI read literally): u_i is weighted by the cost-to-go
 of each rollout from t_i onward, S~(tau_{i,k}) = sum_{j >= i} q~_{j,k} + phi(x_T), with
 its own minimum rho_i and normaliser eta_i (`iteration_to_go`).  At i = 0 this is the total
@@ -74,6 +80,43 @@ def path_costs(system, x0, U, du, R, nu):
             S = S + system.q(st) + is_running_cost(U[i], du[i], R, nu)
         S = S + system.phi(st)
     return S, st
+
+
+def general_noise(seed: int, K: int, Sigma_E, counter: int = 0, gid: int = 0):
+    """delta_u[i][:, k] = L_i eps[i][:, k], L_i = chol(Sigma_E[i]); Sigma_E [T][m][m]."""
+    Sigma_E = np.asarray(Sigma_E, dtype=np.float64)
+    T, m, _ = Sigma_E.shape
+    eps = philox.standard_normals(seed, K, T, m, counter, gid)
+    L = np.stack([philox.cholesky_psd(S) for S in Sigma_E])
+    return np.einsum("tab,tbk->tak", L, eps)
+
+
+def is_running_cost_general(u, du, R, lam, Sigma_E_i):
+    """1/2 du^T (R - lambda Sigma_E^-1) du + u^T R du + 1/2 u^T R u for u [m], du [m][K]."""
+    R = np.asarray(R, dtype=np.float64)
+    Rq = R - lam * np.linalg.inv(np.asarray(Sigma_E_i, dtype=np.float64))
+    quad_du = np.einsum("ak,ab,bk->k", du, Rq, du)
+    cross = np.einsum("a,ab,bk->k", u, R, du)
+    return 0.5 * quad_du + cross + 0.5 * (u @ R @ u)
+
+
+def iteration_general(system, x0, U, K, lam, R, Sigma_E, seed, counter=0, gid=0, du=None):
+    """One MPPI iteration with per-step sampling covariances Sigma_E [T][m][m] (no shift)."""
+    U = np.asarray(U, dtype=np.float64)
+    if du is None:
+        du = general_noise(seed, K, Sigma_E, counter, gid)
+    T = U.shape[0]
+    st = system.init(x0, du.shape[2])
+    S = np.zeros(du.shape[2])
+    with np.errstate(all="ignore"):
+        for i in range(T):
+            st = system.step(st, U[i][:, None] + du[i])
+            S = S + system.q(st) + is_running_cost_general(U[i], du[i], R, lam, Sigma_E[i])
+        S = S + system.phi(st)
+    rho, kstar, eta, w = weights(S, lam)
+    dU, Un = weighted_update(U, du, w)
+    return IterationResult(S=S, rho=rho, kstar=kstar, eta=eta, w=w, dU=dU, U=Un, u0=Un[0].copy(), du=du,
+                           margin=getattr(st, "margin", None))
 
 
 def step_costs(system, x0, U, du, R, nu):

@@ -821,3 +821,43 @@ def test_cartpole_vel_small_oscillation_is_the_rod_pendulums():
         prev = x[2, 0]
     period = crossings[2] - crossings[0]
     assert period == pytest.approx(2 * math.pi * math.sqrt(2 * (2 * l) / (3 * g)), rel=2e-4)
+
+
+# ---------------------------------------------------------------------------
+# general sampling covariance (Theorem 1 with a general A_t, control space)
+# ---------------------------------------------------------------------------
+def test_general_covariance_with_nu_sigma_is_the_scalar_iteration():
+    lin = _double_integrator()
+    T, K, lam, nu = 5, 400, 0.9, 6.0
+    Sigma = np.array([[0.7]])
+    R = lam * np.linalg.inv(Sigma)
+    U = np.linspace(0.2, -0.1, T)[:, None]
+    a = mppi.iteration_seeded(lin, [1.0, 0.0], U, K, lam, nu, Sigma, R, seed=4)
+    b = mppi.iteration_general(lin, [1.0, 0.0], U, K, lam, R, np.repeat(nu * Sigma[None], T, 0), seed=4)
+    assert np.allclose(b.du, a.du, rtol=1e-13, atol=1e-15)
+    assert np.allclose(b.S, a.S, rtol=1e-12)
+    assert np.allclose(b.U, a.U, rtol=1e-11, atol=1e-14)
+
+
+def test_general_covariance_noise_has_the_requested_covariance():
+    SE = np.array([[[0.5, 0.2], [0.2, 0.3]], [[2.0, -0.7], [-0.7, 1.1]]])
+    du = mppi.general_noise(8, 200000, SE)
+    for i in range(2):
+        C = np.cov(du[i])
+        assert np.allclose(C, SE[i], atol=6 * np.sqrt(2.0 / 200000) * SE[i].diagonal().max())
+
+
+def test_general_covariance_one_iteration_reaches_the_lq_optimum():
+    """With R = lambda Sigma^-1 the likelihood-ratio term makes p(du) exp(-S~/lambda) proportional
+    to exp(-J(u + du)/lambda) for any sampling covariance, so with per-step covariances that are
+    neither scalar multiples of Sigma nor constant in time one iteration's expected update still
+    lands on the finite-horizon LQ optimum."""
+    lin = Linear([[1.0, 0.4], [0.0, 1.0]], [[0.08, 0.0], [0.4, 0.3]], np.diag([1.0, 0.2]), np.diag([2.0, 0.5]))
+    T, lam = 3, 1.0
+    Sigma = np.array([[0.6, 0.1], [0.1, 0.4]])
+    R = lam * np.linalg.inv(Sigma)
+    SE = np.stack([np.array([[1.5, 0.3], [0.3, 0.8]]), np.array([[0.9, -0.2], [-0.2, 2.0]]), 3.0 * Sigma])
+    x0, U = np.array([1.0, -0.5]), np.zeros((T, 2))
+    ustar, _ = _lq_optimum(lin, x0, T, R)
+    est = np.mean([mppi.iteration_general(lin, x0, U, 200000, lam, R, SE, seed=s).U for s in range(4)], axis=0)
+    assert np.abs(est - ustar).max() < 0.02 * np.abs(ustar).max() + 0.01
