@@ -158,8 +158,18 @@ int mppi_get_iteration(mppi_ctx *ctx, uint32_t *counter);
 int mppi_set_stream(mppi_ctx *ctx, void *cuda_stream);
 
 /* Select the fused path (default) or the plain-loop baseline.  EINVAL for the plain loop
- * while the cost-to-go weighting is selected. */
+ * while the cost-to-go weighting or per-step sampling covariances are selected. */
 int mppi_set_impl(mppi_ctx *ctx, mppi_impl impl);
+
+/* Per-step sampling covariances Sigma_E [T][m][m] (host, row-major, each symmetric positive
+ * definite; copied) in place of nu * Sigma: Theorem 1 with a general A_t in control space.
+ * The noise of step i is chol(Sigma_E,i) eps and the likelihood-ratio running term becomes
+ * 1/2 du^T (R - lambda Sigma_E,i^-1) du + u_i^T R du + 1/2 u_i^T R u_i (with Sigma_E,i = nu Sigma
+ * the (1 - 1/nu)/2 form).  The covariances stay indexed by horizon step across shifts.  NULL
+ * restores nu * Sigma.  Fused path only, one thread per sample with du and the per-step
+ * matrices in shared memory.  Errors: EINVAL (not symmetric / not positive definite; learned
+ * dynamics; plain loop selected; horizon too long for the shared memory), ENOMEM. */
+int mppi_set_sampling_covariance(mppi_ctx *ctx, const float *h_Sigma_E);
 
 /* Select the weighting of the update (mppi_weighting).  MPPI_WEIGHT_TO_GO runs on the fused
  * path only, with one thread per sample and du and the per-step costs kept in shared memory

@@ -60,6 +60,7 @@ SIGNATURES = [
     ("mppi_get_iteration", C.c_int, [_P, C.POINTER(C.c_uint32)]),
     ("mppi_set_stream", C.c_int, [_P, _P]),
     ("mppi_set_impl", C.c_int, [_P, C.c_int]),
+    ("mppi_set_sampling_covariance", C.c_int, [_P, _FP]),
     ("mppi_set_weighting", C.c_int, [_P, C.c_int]),
     ("mppi_set_controls", C.c_int, [_P, _FP]),
     ("mppi_get_controls", C.c_int, [_P, _FP]),
@@ -279,6 +280,15 @@ class Controller:
         self._chk(lib.mppi_set_weighting(self._h, mode))
 
     set_weighting = mppi_set_weighting
+
+    def mppi_set_sampling_covariance(self, Sigma_E=None):
+        """Per-step sampling covariances [T][m][m], or None for nu * Sigma."""
+        if Sigma_E is None:
+            self._chk(lib.mppi_set_sampling_covariance(self._h, None))
+        else:
+            self._chk(lib.mppi_set_sampling_covariance(self._h, _fp(_f32(Sigma_E, self.T * self.m * self.m))))
+
+    set_sampling_covariance = mppi_set_sampling_covariance
 
     def mppi_set_controls(self, U):
         self._chk(lib.mppi_set_controls(self._h, _fp(_f32(U, self.T * self.m))))

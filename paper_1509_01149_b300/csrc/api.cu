@@ -109,6 +109,7 @@ struct mppi_ctx {
   int sys = 0, K = 0, T = 0, m = 0, n = 0;
   int impl = MPPI_IMPL_FUSED;
   int weighting = MPPI_WEIGHT_PATH;
+  float *d_gen = nullptr;    // general sampling covariance: [T][2][m][m] (chol, R - lambda Sigma_E^-1)
   float *d_prho = nullptr;   // cost-to-go weighting: per-step block minima [nblk_cap][T]
   double *d_peta = nullptr;  // and normalisers [nblk_cap][T]
   int blk = 0, nblk = 0;
@@ -521,6 +522,7 @@ int mppi_destroy(mppi_ctx *c) {
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->d_du) cudaFree(c->d_du);
   if (c->d_prho) cudaFree(c->d_prho);
+  if (c->d_gen) cudaFree(c->d_gen);
   if (c->d_peta) cudaFree(c->d_peta);
   if (c->d_env) cudaFree(c->d_env);
   if (c->d_mlp) cudaFree(c->d_mlp);
@@ -545,6 +547,8 @@ int mppi_set_impl(mppi_ctx *c, mppi_impl impl) {
   if (!c || (impl != MPPI_IMPL_FUSED && impl != MPPI_IMPL_PLAIN)) return MPPI_EINVAL;
   if (impl == MPPI_IMPL_PLAIN && c->weighting == MPPI_WEIGHT_TO_GO)
     return c->fail(MPPI_EINVAL, "the plain loop is built for the path weighting only");
+  if (impl == MPPI_IMPL_PLAIN && c->p.gen)
+    return c->fail(MPPI_EINVAL, "the plain loop is built for the nu * Sigma sampling covariance only");
   c->impl = impl;
   return MPPI_OK;
 }
@@ -556,6 +560,52 @@ int block_shape(mppi_ctx *c, const CtrlParams &p) {
   return c->weighting == MPPI_WEIGHT_TO_GO ? fused_block_size_to_go(p) : fused_block_size(c->sys, p);
 }
 }  // namespace
+
+int mppi_set_sampling_covariance(mppi_ctx *c, const float *h_Sigma_E) {
+  if (!c) return MPPI_EINVAL;
+  if (!h_Sigma_E) {
+    c->p.gen = nullptr;
+  } else {
+    if (c->sys == MPPI_CAR_MLP)
+      return c->fail(MPPI_EINVAL, "the general sampling covariance is not built for the learned dynamics");
+    if (c->impl == MPPI_IMPL_PLAIN)
+      return c->fail(MPPI_EINVAL, "the plain loop is built for the nu * Sigma sampling covariance only");
+    const int m = c->m, T = c->T, mm = m * m;
+    std::vector<float> host(static_cast<size_t>(T) * 2 * mm);
+    double Rd[kMaxM * kMaxM];
+    for (int a = 0; a < mm; ++a) Rd[a] = c->p.R[a];
+    for (int i = 0; i < T; ++i) {
+      double S[kMaxM * kMaxM], L[kMaxM * kMaxM], Si[kMaxM * kMaxM];
+      for (int a = 0; a < mm; ++a) S[a] = h_Sigma_E[static_cast<size_t>(i) * mm + a];
+      if (!symmetric(S, m)) return c->fail(MPPI_EINVAL, "Sigma_E[%d] is not symmetric", i);
+      if (!cholesky_psd(S, m, L) || !invert(S, m, Si))
+        return c->fail(MPPI_EINVAL, "Sigma_E[%d] is not positive definite", i);
+      for (int a = 0; a < m; ++a)
+        if (!(L[a * m + a] > 0.0)) return c->fail(MPPI_EINVAL, "Sigma_E[%d] is not positive definite", i);
+      float *dst = host.data() + static_cast<size_t>(i) * 2 * mm;
+      for (int a = 0; a < mm; ++a) {
+        dst[a] = static_cast<float>(L[a]);
+        dst[mm + a] = static_cast<float>(Rd[a] - static_cast<double>(c->p.lambda) * Si[a]);
+      }
+    }
+    if (!c->d_gen) MPPI_TRY(c->cuda(cudaMalloc(&c->d_gen, sizeof(float) * host.size()), "cudaMalloc(covariances)"));
+    MPPI_TRY(c->cuda(cudaMemcpy(c->d_gen, host.data(), sizeof(float) * host.size(), cudaMemcpyHostToDevice),
+                     "covariance copy"));
+    c->p.gen = c->d_gen;
+  }
+  const int blk = block_shape(c, c->p);
+  if (blk == 0) {
+    c->p.gen = nullptr;
+    c->blk = block_shape(c, c->p);
+    c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+    c->graph_dirty = c->iter_graph_dirty = true;
+    return c->fail(MPPI_EINVAL, "horizon too long for the per-step covariances in shared memory");
+  }
+  c->blk = blk;
+  c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+  c->graph_dirty = c->iter_graph_dirty = true;
+  return MPPI_OK;
+}
 
 int mppi_set_weighting(mppi_ctx *c, int mode) {
   if (!c || (mode != MPPI_WEIGHT_PATH && mode != MPPI_WEIGHT_TO_GO)) return MPPI_EINVAL;
@@ -817,6 +867,7 @@ int mppi_get_debug(mppi_ctx *c, float *S, int *argmin, double *eta, float *dU) {
 
 int mppi_get_noise(mppi_ctx *c, uint32_t counter, float *h_du) {
   if (!c || !h_du) return MPPI_EINVAL;
+  if (c->p.gen) return c->fail(MPPI_EINVAL, "the noise check hook draws the nu * Sigma noise only");
   MPPI_TRY(ensure_noise_buffer(c));
   MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_ctr, &counter, sizeof counter, cudaMemcpyHostToDevice, c->stream), "ctr"));
   MPPI_TRY(c->cuda(launch_plain_noise(c->p, c->d_ctr, c->d_du, c->stream), "noise launch"));

@@ -28,26 +28,26 @@ namespace mppi {
 // ---------------------------------------------------------------------------
 // fused rollout: one block of BLK samples per CTA (body in rollout_body.cuh)
 // ---------------------------------------------------------------------------
-template <class Sys, int BLK, bool REGEN>
+template <class Sys, int BLK, bool REGEN, bool GEN = false>
 __global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const float *__restrict__ x0,
                                                        const CtrlState *__restrict__ st, const float *__restrict__ U,
                                                        float *__restrict__ S_out, float *__restrict__ part_sums,
                                                        BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block<Sys, BLK, REGEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
+  rollout_block<Sys, BLK, REGEN, false, GEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
                                  part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
                                  smem);
 }
 
 // cost-to-go weighting: one thread per sample, du in shared memory, per-step block partials
-template <class Sys, int BLK>
+template <class Sys, int BLK, bool GEN = false>
 __global__ void __launch_bounds__(BLK) k_rollout_to_go(const CtrlParams p, const float *__restrict__ x0,
                                                        const CtrlState *__restrict__ st, const float *__restrict__ U,
                                                        float *__restrict__ S_out, float *__restrict__ part_sums,
                                                        BlockPartial *__restrict__ part, float *__restrict__ part_rho,
                                                        double *__restrict__ part_eta) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block<Sys, BLK, false, true>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
+  rollout_block<Sys, BLK, false, true, GEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
                                        part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
                                        smem, nullptr, part_rho + static_cast<size_t>(blockIdx.x) * p.T,
                                        part_eta + static_cast<size_t>(blockIdx.x) * p.T);
@@ -514,10 +514,15 @@ size_t fused_smem_bytes(const CtrlParams &p, int blk) {
   if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples);
   if (blk == kFusedBlockQuadLanes) return quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
   const bool regen = blk == kFusedBlockRegen;
-  return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen);
+  return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen, false, p.gen != nullptr);
 }
 
 int fused_block_size(int sys, const CtrlParams &p) {
+  if (p.gen) {  // the general sampling covariance runs on the one-thread kernels with du in shared memory
+    if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;
+    if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
+    return 0;
+  }
   if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && fused_smem_bytes(p, kFusedBlockCarWs) <= kFusedSmemLimit)
     return kFusedBlockCarWs;
   if (sys == 2 && fused_smem_bytes(p, kFusedBlockQuadLanes) <= kFusedSmemLimit) return kFusedBlockQuadLanes;
@@ -536,9 +541,15 @@ int fused_block_samples(int blk) {
 template <class Sys, int BLK, bool REGEN>
 static cudaError_t launch_fused_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                   float *ps, BlockPartial *part, cudaStream_t s) {
-  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, REGEN);
+  const bool gen = p.gen != nullptr;
+  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, REGEN, false, gen);
   const int grid = (p.K + BLK - 1) / BLK;
-  k_rollout_fused<Sys, BLK, REGEN><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part);
+  if (gen) {
+    if (REGEN) return cudaErrorInvalidValue;
+    k_rollout_fused<Sys, BLK, false, true><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part);
+  } else {
+    k_rollout_fused<Sys, BLK, REGEN><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part);
+  }
   return cudaGetLastError();
 }
 
@@ -581,17 +592,24 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
 }
 
 int fused_block_size_to_go(const CtrlParams &p) {
-  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true) <= kFusedSmemLimit) return kFusedBlockLarge;
-  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockSmall, false, true) <= kFusedSmemLimit) return kFusedBlockSmall;
+  const bool gen = p.gen != nullptr;
+  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true, gen) <= kFusedSmemLimit)
+    return kFusedBlockLarge;
+  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockSmall, false, true, gen) <= kFusedSmemLimit)
+    return kFusedBlockSmall;
   return 0;
 }
 
 template <class Sys, int BLK>
 static cudaError_t launch_to_go_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                   float *ps, BlockPartial *part, float *prho, double *peta, cudaStream_t s) {
-  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, false, true);
+  const bool gen = p.gen != nullptr;
+  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, false, true, gen);
   const int grid = (p.K + BLK - 1) / BLK;
-  k_rollout_to_go<Sys, BLK><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part, prho, peta);
+  if (gen)
+    k_rollout_to_go<Sys, BLK, true><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part, prho, peta);
+  else
+    k_rollout_to_go<Sys, BLK><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part, prho, peta);
   return cudaGetLastError();
 }
 
@@ -637,6 +655,13 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<CartPoleVel, kFusedBlockLarge, true>),
       reinterpret_cast<const void *>(k_rollout_to_go<CartPoleVel, kFusedBlockLarge>),
       reinterpret_cast<const void *>(k_rollout_to_go<CartPoleVel, kFusedBlockSmall>),
+#define MPPI_GEN_KERNELS(S)                                                              \
+  reinterpret_cast<const void *>(k_rollout_fused<S, kFusedBlockLarge, false, true>),   \
+      reinterpret_cast<const void *>(k_rollout_fused<S, kFusedBlockSmall, false, true>), \
+      reinterpret_cast<const void *>(k_rollout_to_go<S, kFusedBlockLarge, true>),      \
+      reinterpret_cast<const void *>(k_rollout_to_go<S, kFusedBlockSmall, true>)
+      MPPI_GEN_KERNELS(CartPole), MPPI_GEN_KERNELS(Car), MPPI_GEN_KERNELS(Quad), MPPI_GEN_KERNELS(CartPoleVel),
+#undef MPPI_GEN_KERNELS
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, true>),

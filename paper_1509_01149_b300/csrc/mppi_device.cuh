@@ -118,6 +118,8 @@ struct CtrlParams {
   int n_obs;
   float goal[3];
   const void *mlp;          // learned dynamics weights (car_mlp)
+  const float *gen;         // general sampling covariance: [T][2][m][m] = (chol(Sigma_E,i),
+                            // R - lambda Sigma_E,i^-1) per step, row-major; null: nu Sigma
 };
 
 // Per-controller mutable device state.

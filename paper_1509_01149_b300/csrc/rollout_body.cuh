@@ -66,10 +66,11 @@ __device__ __forceinline__ float transpose_reduce32(float v[32]) {
 
 // Shared-memory bytes of rollout_block (dynamic part) for T*M outputs; to_go adds the
 // per-step costs [T][blk] of the cost-to-go weighting.
-__host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, int blk, bool regen, bool to_go = false) {
+__host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, int blk, bool regen, bool to_go = false,
+                                                   bool gen = false) {
   const size_t TM = static_cast<size_t>(T) * M;
   return 16 + sizeof(float) * (2 * TM + T + 4 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk) +
-                               (to_go ? static_cast<size_t>(T) * blk : 0));
+                               (to_go ? static_cast<size_t>(T) * blk : 0) + (gen ? 2 * TM * M : 0));
 }
 
 // Per-time-step block partials of the cost-to-go weighting (Eq. App_PI read literally: u_i
@@ -274,13 +275,17 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
 //            global-memory slab owned by this CTA) instead of in shared memory
 //   TOGO     cost-to-go weighting (STORE only): per-step partials into part_sums, part_rho
 //            [T] and part_eta [T] of this block (block_partial_to_go)
-template <class Sys, int BLK, bool REGEN, bool TOGO = false>
+//   GEN      general sampling covariance (STORE only): du_i = chol(Sigma_E,i) eps and the
+//            running term 1/2 du^T (R - lambda Sigma_E,i^-1) du + u^T R du + 1/2 u^T R u, the
+//            per-step matrices from p.gen
+template <class Sys, int BLK, bool REGEN, bool TOGO = false, bool GEN = false>
 __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                               const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                               float *__restrict__ part_sums, BlockPartial *__restrict__ part,
                                               float *smem, float *du_ext = nullptr, float *part_rho = nullptr,
                                               double *part_eta = nullptr) {
   static_assert(!(TOGO && REGEN), "the cost-to-go weighting keeps du in shared memory");
+  static_assert(!(GEN && REGEN), "the general sampling covariance keeps du in shared memory");
   constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M;
   static_assert(4 % M == 0, "controls per Philox block must divide 4");
   const int T = p.T, TM = T * M, tid = threadIdx.x;
@@ -291,11 +296,14 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   float *sW = sHu + T;              // [BLK] weights
   float *sDu = du_ext ? du_ext : sW + BLK;  // STORE only: [TM][BLK] perturbations of this block
   float *sC = sW + BLK + static_cast<size_t>(TM) * BLK;  // TOGO only: [T][BLK] step costs
+  float *sGen = sC + (TOGO ? static_cast<size_t>(T) * BLK : 0);  // GEN only: [T][2][M][M]
 
   __shared__ float sx0[N];  // x0 staged once per block (it may live in mapped host memory)
   for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
   for (int o = tid; o < 4 * p.n_obs; o += BLK) sObs[o] = (o & 3) == 3 ? 0.0f : p.obs[3 * (o >> 2) + (o & 3)];
   if (tid < N) sx0[tid] = x0[tid];
+  if (GEN)
+    for (int o = tid; o < 2 * TM * M; o += BLK) sGen[o] = p.gen[o];
   __syncthreads();
   for (int i = tid; i < T; i += BLK) {
     float h = 0.0f;
@@ -333,7 +341,8 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   bool have = false;
   auto step_at = [&](int i, const float *e) {
     float du[M], v[M];
-    scale_noise<M>(Lnu, e, du);
+    const float *Lg = sGen + static_cast<size_t>(i) * 2 * M * M;  // GEN: chol(Sigma_E,i), then R_IS,i
+    scale_noise<M>(GEN ? Lg : Lnu, e, du);
     float duRdu = 0.0f, uRdu = 0.0f;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
@@ -342,7 +351,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
       uRdu = fmaf(sRu[i * M + j], du[j], uRdu);
       float rd = 0.0f;
 #pragma unroll
-      for (int l = 0; l < M; ++l) rd = fmaf(R[j * M + l], du[l], rd);
+      for (int l = 0; l < M; ++l) rd = fmaf(GEN ? Lg[M * M + j * M + l] : R[j * M + l], du[l], rd);
       duRdu = fmaf(du[j], rd, duRdu);
     }
     Sys::step(x, v, aux, env, p.dt);
@@ -352,7 +361,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
       if (TOGO) sC[(i - 1) * BLK + tid] = c;
     }
     pend = Sys::cost_issue(x, aux, env);
-    pend_is = p.is_du * duRdu + uRdu + sHu[i];
+    pend_is = (GEN ? 0.5f : p.is_du) * duRdu + uRdu + sHu[i];
     have = true;
   };
 

@@ -328,3 +328,106 @@ def test_cartpole_vel_cost_to_go(N):
     for i in range(cfg["T"]):
         assert P.update_step_within_cost_error(g["U"][i].astype(np.float64), o.U[i], U0[i], o.du[i], o.S[i],
                                                o.rho[i], lam, bound[i]), i
+
+
+# ---------------------------------------------------------------------------
+# general per-step sampling covariance (Theorem 1 with a general A_t, control space)
+# ---------------------------------------------------------------------------
+def _sigma_e(cfg, seed=5):
+    """Per-step SPD covariances around nu * Sigma: a rotation-and-scale that varies over the
+    horizon (neither a scalar multiple of Sigma nor constant in time)."""
+    rng = np.random.default_rng(seed)
+    m, T = np.atleast_2d(cfg["Sigma"]).shape[0], cfg["T"]
+    base = cfg["nu"] * np.atleast_2d(cfg["Sigma"])
+    out = []
+    for i in range(T):
+        A = np.eye(m) + 0.3 * rng.standard_normal((m, m))
+        s = 0.5 + 1.5 * (i + 1) / T
+        out.append(s * A @ base @ A.T + 1e-3 * np.trace(base) * np.eye(m))
+    return np.asarray(out, np.float32).astype(np.float64)
+
+
+def _oracle_general(cfg, SE, to_go=False):
+    from oracle import mppi as om
+    sys_ = P.oracle_system(cfg["system"], cfg["dt"])
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    R = cfg["R"] if cfg.get("R") is not None else cfg["lam"] * np.linalg.inv(cfg["Sigma"])
+    lam = float(np.float32(cfg["lam"]))
+    x0, U, Rf = f32(cfg["x0"]), f32(cfg["U"]), f32(R)
+    if not to_go:
+        return om.iteration_general(sys_, x0, U, cfg["K"], lam, Rf, SE, cfg.get("seed", 0))
+    du = om.general_noise(cfg.get("seed", 0), cfg["K"], SE)
+    st = sys_.init(x0, cfg["K"])
+    C = np.zeros((cfg["T"], cfg["K"]))
+    with np.errstate(all="ignore"):
+        for i in range(cfg["T"]):
+            st = sys_.step(st, U[i][:, None] + du[i])
+            C[i] = sys_.q(st) + om.is_running_cost_general(U[i], du[i], Rf, lam, SE[i])
+        phi = sys_.phi(st)
+    Sg = om.costs_to_go(C, phi)
+    rho = np.zeros(cfg["T"])
+    Un = U.copy()
+    for i in range(cfg["T"]):
+        rho[i], _, _, w = om.weights(Sg[i], lam)
+        Un[i] = U[i] + du[i] @ w
+    return dict(S=Sg, rho=rho, U=Un, du=du, margin=getattr(st, "margin", None))
+
+
+@pytest.mark.parametrize("system,K,T,lam", [(W.CARTPOLE, 1000, 100, 1.0), (W.CAR, 4096, 60, 30.0),
+                                            (W.QUAD, 2048, 60, 1.0), (W.CARTPOLE_VEL, 1000, 50, None)])
+def test_general_sampling_covariance_iteration(N, system, K, T, lam):
+    # R = lambda Sigma^-1 (the premise of Theorem 1's control-space form): the running term's
+    # matrix R - lambda Sigma_E^-1 = lambda (Sigma^-1 - Sigma_E^-1) is then small beside the costs
+    over = {"K": K, "T": T}
+    if lam is not None:
+        over["lam"] = lam
+    cfg = W.config(system, **over)
+    SE = _sigma_e(cfg)
+    c = P.make_controller(cfg)
+    c.set_sampling_covariance(SE)
+    g, _ = P.gpu_iteration(cfg, ctrl=c)
+    o = _oracle_general(cfg, SE)
+    mask = o.margin > 1e-3 if o.margin is not None else None
+    assert P.s_errors(g["S"], o.S, mask).max() <= P.S_RTOL
+    if P.argmin_is_unique(o.S) and (mask is None or mask[o.kstar]):
+        assert g["kstar"] == o.kstar
+    scale = np.sqrt(np.max(SE, axis=0).diagonal())
+    bound = P.U_RTOL * (np.abs(o.U) + scale[None, :])
+    U0 = np.asarray(cfg["U"], np.float32).astype(np.float64)
+    lamf = float(np.float32(cfg["lam"]))
+    for i in range(T):
+        assert P.update_step_within_cost_error(g["U"][i].astype(np.float64), o.U[i], U0[i], o.du[i], o.S, o.rho,
+                                               lamf, bound[i]), i
+
+
+def test_general_sampling_covariance_with_the_cost_to_go_weighting(N):
+    cfg = W.config(W.CAR, K=2048, T=40, lam=30.0)
+    SE = _sigma_e(cfg, seed=9)
+    c = P.make_controller(cfg)
+    c.set_sampling_covariance(SE)
+    c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    g, _ = P.gpu_iteration(cfg, ctrl=c)
+    o = _oracle_general(cfg, SE, to_go=True)
+    assert P.s_errors(g["S"], o["S"][0]).max() <= P.S_RTOL
+    scale = np.sqrt(np.max(SE, axis=0).diagonal())
+    bound = P.U_RTOL * (np.abs(o["U"]) + scale[None, :])
+    U0 = np.asarray(cfg["U"], np.float32).astype(np.float64)
+    for i in range(cfg["T"]):
+        assert P.update_step_within_cost_error(g["U"][i].astype(np.float64), o["U"][i], U0[i], o["du"][i], o["S"][i],
+                                               o["rho"][i], 30.0, bound[i]), i
+
+
+def test_general_sampling_covariance_limits(N):
+    cfg = W.config(W.CAR, K=256, T=20)
+    c = P.make_controller(cfg)
+    bad = _sigma_e(cfg)
+    bad[3] = -bad[3]
+    with pytest.raises(N.MppiError):
+        c.set_sampling_covariance(bad)                  # not positive definite
+    c.set_sampling_covariance(_sigma_e(cfg))
+    with pytest.raises(N.MppiError):
+        c.set_impl(N.MPPI_IMPL_PLAIN)
+    with pytest.raises(N.MppiError):
+        c.get_noise(0)
+    c.set_sampling_covariance(None)                     # back to nu * Sigma
+    c.set_impl(N.MPPI_IMPL_PLAIN)
