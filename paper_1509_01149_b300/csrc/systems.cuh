@@ -145,17 +145,40 @@ struct Car {
   // itself and the control, and the pose rates (X, Y, psi), which read the velocities but
   // never feed back into them.
   //
-  // The tyre-force sines have arguments |C atan(.)| <= 1.8 pi/2 < pi and the steering
-  // angle stays small, where the special-function-unit sine/cosine are accurate to about
-  // 2^-21 absolute: they run as single SFU operations with no slow-path branch, which
-  // keeps the two tyre chains interleavable.
+  // The steering angle stays small, where the special-function-unit sine/cosine are
+  // accurate to about 2^-21 absolute: they run as single SFU operations with no slow-path
+  // branch.
+  //
+  // The shape sin(C atan z), z = B alpha, is evaluated on the whole real line through
+  // v = |z| / (1 + |z|) in [0, 1], where it is analytic: sign(z) v P(v) / Q(v), a rational
+  // fitted towards minimax (maximum absolute error 3.0e-7 in exact arithmetic, ~6.5e-7 in
+  // FP32; tyre_shape_fit.py prints the coefficients).  Two reciprocals and ten FMAs with no
+  // branch replace an arctangent and a sine on the recurrence's critical path.  |z| is capped
+  // at 1e30 (the shape equals its limit sin(C pi / 2) there to FP32 precision; the cap keeps
+  // the fast reciprocal in range); NaN propagates.
+  __device__ __forceinline__ static float tyre_shape(float z) {
+    const float a = fabsf(z) > 1.0e30f ? 1.0e30f : fabsf(z);
+    const float v = __fdividef(a, 1.0f + a);
+    float P = -1.802042631e+00f;
+    P = fmaf(P, v, 2.115236191e+00f);
+    P = fmaf(P, v, 2.735651234e-01f);
+    P = fmaf(P, v, -1.707349900e+00f);
+    P = fmaf(P, v, 1.799983406e+00f);
+    float Q = 2.216846433e+00f;
+    Q = fmaf(Q, v, -2.120366621e+00f);
+    Q = fmaf(Q, v, 1.076769485e+00f);
+    Q = fmaf(Q, v, 1.973980183e+00f);
+    Q = fmaf(Q, v, -1.948672322e+00f);
+    Q = fmaf(Q, v, 1.000000000e+00f);
+    return copysignf(__fdividef(v * P, Q), z);
+  }
   __device__ __forceinline__ static void deriv_vel(float vx, float vy, float r, float delta, const float v[M],
                                                    float d[4]) {
     const float inv_vxs = __fdividef(1.0f, fmaxf(vx, vx_floor));
     const float alpha_f = delta - atanf((vy + lf * r) * inv_vxs);
     const float alpha_r = -atanf((vy - lr * r) * inv_vxs);
-    const float Fyf = Df * __sinf(C * atanf(B * alpha_f));
-    const float Fyr = Dr * __sinf(C * atanf(B * alpha_r));
+    const float Fyf = Df * tyre_shape(B * alpha_f);
+    const float Fyr = Dr * tyre_shape(B * alpha_r);
     const float Fx = Cm * v[1] - Crr * vx - Cd * vx * fabsf(vx);
     float sd, cd;
     __sincosf(delta, &sd, &cd);

@@ -138,6 +138,30 @@ def test_car_horizon_at_the_warp_role_limit(N, T):
     _check_iteration(cfg, g, o)
 
 
+def test_car_extreme_steering_spans_the_tyre_curve(N):
+    """Steering commands of 8 (a steering angle heading for 4 rad) drive the front slip angle
+    from 0.8 to past 2.5 rad (B alpha from 3 to 16), far out on the tyre curve that the kernels
+    evaluate as a fitted rational in |z| / (1 + |z|): both kernels agree with the oracle."""
+    from oracle import systems as osys
+    T = 40
+    U = np.zeros((T, 2))
+    U[:, 0], U[:, 1] = 8.0, 0.5
+    cfg = W.config(W.CAR, K=2048, T=T, U=U, lam=50.0)
+    car = osys.Car(cfg["dt"], W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL)
+    x = car.init(cfg["x0"], 1)
+    z = []
+    for i in range(T):
+        x = car.step(x, U[i][:, None])
+        vxs = max(x[3, 0], car.p["vx_floor"])
+        z.append(car.p["B"] * (x[6, 0] - math.atan((x[4, 0] + car.p["lf"] * x[5, 0]) / vxs)))
+    z = np.abs(np.array(z))
+    assert z.max() > 10.0 and z.min() < 10.0, (z.min(), z.max())
+    for impl in (0, 1):
+        g, _ = P.gpu_iteration(cfg, impl)
+        o = P.oracle_iteration(cfg)
+        _check_iteration(cfg, g, o)
+
+
 def test_nonzero_controls_and_correlated_sigma(N):
     rng = np.random.default_rng(3)
     S = np.array([[0.3, 0.1], [0.1, 0.35]])
