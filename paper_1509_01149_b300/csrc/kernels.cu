@@ -6,9 +6,10 @@
 //                    q + importance-sampling running cost (Kahan FP32) -> phi.
 //                    Then, per block: rho_b = min S~, w_k = exp(-(S~_k - rho_b)/lambda),
 //                    eta_b = sum w_k (FP64) and the FP32 block sums sum_k w_k du_{i,k}.
-//   k_merge_update   FP64 merge of the block partials (flash-softmax style):
-//                    rho = min rho_b, eta = sum_b eta_b e^{-(rho_b - rho)/lambda},
-//                    du_i = sum_b e^{-(rho_b-rho)/lambda} part_b[i] / eta; U += du.
+//   k_merge_update   merge of the block partials (flash-softmax style):
+//                    rho = min rho_b, eta = sum_b eta_b e^{-(rho_b - rho)/lambda} (FP64),
+//                    du_i = sum_b e^{-(rho_b-rho)/lambda} part_b[i] / eta (double-FP32
+//                    sums in a fixed order, FP64 division; merge_common.cuh); U += du.
 // The min shift is exact algebra: it cancels between numerator and denominator of
 // Eq. App_PI and only keeps the exponentials in range.
 //
@@ -19,6 +20,7 @@
 #include <climits>
 
 #include "kernels.cuh"
+#include "merge_common.cuh"
 #include "rollout_body.cuh"
 #include "rollout_lanes.cuh"
 #include "rollout_ws.cuh"
@@ -90,9 +92,11 @@ __device__ __forceinline__ void cluster_sync_all() {
 }
 }  // namespace
 
-// One CTA per 32 outputs (i, j).  All loads of the CTA (its lanes' block partials and the
-// first kMergePrefetch block sums of each lane) are issued first, so their latency is paid
-// once; then rho/kstar (argmin), the FP64 block scales and eta, and the FP64 weighted sum.
+// One CTA per 32 outputs (i, j), warp r = range r of the block partials (merge_common.cuh:
+// the fixed arithmetic order every path shares).  The CTA's loads (block partials, the first
+// kMergePrefetch block sums of each lane's range) are issued first, so their latency is paid
+// once; then rho/k* (argmin), the block scales, eta (warp 0, FP64) and the double-FP32 range
+// sums, combined in range order by warp 0.
 // SHIFT: the grid is one thread-block cluster (all outputs in <= 8 CTAs); after the update
 // the cluster barrier makes every CTA's new U visible, each CTA reads its shifted values,
 // a second barrier separates those reads from the in-place writes, and CTA 0 advances the
@@ -106,40 +110,37 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
                                                                 StepDebug *__restrict__ dbg,
                                                                 const float *__restrict__ u_init,
                                                                 CtrlState *__restrict__ st) {
-  // B300 runs FP64 at a small fraction of the FP32 rate, so the FP64 work here is laid
-  // out for short dependency chains: 4 independent accumulators per lane, a 3-level tree
-  // across warps, one division (1/eta) per CTA.
   constexpr int NW = kMergeThreads / 32;
-  extern __shared__ double s_scale[];  // [nblk]
+  static_assert(NW == kMergeRanges, "one warp per range of block partials");
+  extern __shared__ double s_eb[];  // [nblk] eta_b, then [nblk] floats: rho_b, then s_b
+  float *s_sc = reinterpret_cast<float *>(s_eb + nblk);
   __shared__ float s_rho[NW];
   __shared__ int s_k[NW];
-  __shared__ double s_e[NW];
-  __shared__ double s_acc[NW][kMergeOutputs];
+  __shared__ DF s_part[NW][kMergeOutputs];
   __shared__ double s_inv_eta;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int o = blockIdx.x * kMergeOutputs + lane;
+  const int L = merge_range_len(nblk), b0 = min(nblk, warp * L), b1 = min(nblk, b0 + L);
   // launched as a programmatic dependent of the rollout: its partials are complete and
   // visible after this wait (a no-op for an ordinary launch)
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
-  // loads first: this thread's block partial (b = tid) and its lane's first block sums
-  BlockPartial mine{0.0, INFINITY, INT_MAX};
-  if (tid < nblk) mine = part[tid];
+  // loads first: the first kMergePrefetch block sums of this lane's output in the warp's range
   float pre[kMergePrefetch];
 #pragma unroll
   for (int j = 0; j < kMergePrefetch; ++j) {
-    const int b = warp + j * NW;
-    pre[j] = (o < TM && b < nblk) ? part_sums[static_cast<size_t>(b) * TM + o] : 0.0f;
+    const int b = b0 + j;
+    pre[j] = (o < TM && b < b1) ? part_sums[static_cast<size_t>(b) * TM + o] : 0.0f;
   }
-
-  float v = mine.rho;
-  int idx = mine.kstar;
-  for (int b = tid + kMergeThreads; b < nblk; b += kMergeThreads) {
-    const float r = part[b].rho;
-    const int kk = part[b].kstar;
-    if (r < v || (r == v && kk < idx)) {
-      v = r;
-      idx = kk;
+  float v = INFINITY;
+  int idx = INT_MAX;
+  for (int b = tid; b < nblk; b += kMergeThreads) {
+    const BlockPartial bp = part[b];
+    s_eb[b] = bp.eta;
+    s_sc[b] = bp.rho;
+    if (bp.rho < v || (bp.rho == v && bp.kstar < idx)) {
+      v = bp.rho;
+      idx = bp.kstar;
     }
   }
   warp_argmin(v, idx);
@@ -159,63 +160,34 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   }
   __syncthreads();
   const float rho = s_rho[0];
-
-  double e = 0.0;
-  if (tid < nblk) {
-    const double sc =
-        (isfinite(rho) && isfinite(mine.rho)) ? static_cast<double>(expf(-(mine.rho - rho) * inv_lambda)) : 0.0;
-    s_scale[tid] = sc;
-    e = sc * mine.eta;
-  }
-  for (int b = tid + kMergeThreads; b < nblk; b += kMergeThreads) {
-    const float rb = part[b].rho;
-    const double sc = (isfinite(rho) && isfinite(rb)) ? static_cast<double>(expf(-(rb - rho) * inv_lambda)) : 0.0;
-    s_scale[b] = sc;
-    e += sc * part[b].eta;
-  }
-  e = warp_sum_d(e);
-  if (lane == 0) s_e[warp] = e;
+  for (int b = tid; b < nblk; b += kMergeThreads) s_sc[b] = merge_scale(s_sc[b], rho, inv_lambda);
   __syncthreads();
-  if (tid == 0) {
-    double eta = 0.0;
-#pragma unroll
-    for (int q = 0; q < NW; ++q) eta += s_e[q];
-    s_inv_eta = eta > 0.0 ? 1.0 / eta : 0.0;
-    if (blockIdx.x == 0) {
-      dbg->rho = rho;
-      dbg->kstar = s_k[0];
-      dbg->eta = eta;
+  if (warp == 0) {
+    const double eta = merge_eta_warp(s_sc, s_eb, nblk, lane);
+    if (lane == 0) {
+      s_inv_eta = eta > 0.0 ? 1.0 / eta : 0.0;
+      if (blockIdx.x == 0) {
+        dbg->rho = rho;
+        dbg->kstar = s_k[0];
+        dbg->eta = eta;
+      }
     }
   }
 
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  DF acc{0.0f, 0.0f};
 #pragma unroll
-  for (int j = 0; j < kMergePrefetch; j += 4) {
-    const int b = warp + j * NW;
-    if (b < nblk) a0 += s_scale[b] * static_cast<double>(pre[j]);
-    if (b + NW < nblk) a1 += s_scale[b + NW] * static_cast<double>(pre[j + 1]);
-    if (b + 2 * NW < nblk) a2 += s_scale[b + 2 * NW] * static_cast<double>(pre[j + 2]);
-    if (b + 3 * NW < nblk) a3 += s_scale[b + 3 * NW] * static_cast<double>(pre[j + 3]);
-  }
-  if (o < TM) {
-    int b = warp + kMergePrefetch * NW;
-    for (; b + 3 * NW < nblk; b += 4 * NW) {
-      a0 += s_scale[b] * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
-      a1 += s_scale[b + NW] * static_cast<double>(part_sums[static_cast<size_t>(b + NW) * TM + o]);
-      a2 += s_scale[b + 2 * NW] * static_cast<double>(part_sums[static_cast<size_t>(b + 2 * NW) * TM + o]);
-      a3 += s_scale[b + 3 * NW] * static_cast<double>(part_sums[static_cast<size_t>(b + 3 * NW) * TM + o]);
-    }
-    for (; b < nblk; b += NW) a0 += s_scale[b] * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
-  }
-  s_acc[warp][lane] = (a0 + a1) + (a2 + a3);
+  for (int j = 0; j < kMergePrefetch; ++j)
+    if (b0 + j < b1) df_add_prod(acc, s_sc[b0 + j], pre[j]);
+  if (o < TM)
+    for (int b = b0 + kMergePrefetch; b < b1; ++b)
+      df_add_prod(acc, s_sc[b], part_sums[static_cast<size_t>(b) * TM + o]);
+  s_part[warp][lane] = acc;
   __syncthreads();
-#pragma unroll
-  for (int h = NW / 2; h > 0; h >>= 1) {
-    if (warp < h) s_acc[warp][lane] += s_acc[warp + h][lane];
-    __syncthreads();
-  }
   if (warp == 0 && o < TM) {
-    const double du = s_acc[0][lane] * s_inv_eta;
+    DF tot = s_part[0][lane];
+#pragma unroll
+    for (int r = 1; r < kMergeRanges; ++r) df_add(tot, s_part[r][lane]);
+    const double du = merge_du(tot, s_inv_eta);
     const float un = U[o] + static_cast<float>(du);
     U[o] = un;
     dU_dbg[o] = static_cast<float>(du);
@@ -692,7 +664,7 @@ cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((TM + kMergeOutputs - 1) / kMergeOutputs, 1, 1);
   cfg.blockDim = dim3(kMergeThreads, 1, 1);
-  cfg.dynamicSmemBytes = sizeof(double) * static_cast<size_t>(nblk);
+  cfg.dynamicSmemBytes = (sizeof(double) + sizeof(float)) * static_cast<size_t>(nblk);
   cfg.stream = s;
   // programmatic dependent launch: the merge's CTAs start while the rollout drains and wait
   // (griddepcontrol.wait) for its results
@@ -722,7 +694,7 @@ cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kMergeThreads, 1, 1);
-  cfg.dynamicSmemBytes = sizeof(double) * static_cast<size_t>(nblk);
+  cfg.dynamicSmemBytes = (sizeof(double) + sizeof(float)) * static_cast<size_t>(nblk);
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;

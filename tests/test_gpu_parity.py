@@ -226,6 +226,29 @@ def test_graph_iteration_equals_step_and_shift(N):
     assert a.get_iteration() == b.get_iteration() == 3
 
 
+@pytest.mark.parametrize("K,T", [(40000, 33), (32768, 100), (65, 1), (16384, 100)])
+def test_merge_with_shift_equals_merge_then_shift_kernel(N, K, T):
+    """The iteration graph runs the merge and the shift in one thread-block cluster;
+    step_async runs the merge alone, then mppi_shift's kernel.  With up to 313 block partials
+    (ranges of 40 blocks, beyond the merge's register prefetch) the fixed reduction order
+    gives the same controls, u0, debug values and counter bit for bit, over three iterations."""
+    import torch
+    cfg = W.config(W.CAR, K=K, T=T, lam=30.0)
+    a, b = P.make_controller(cfg), P.make_controller(cfg)
+    dx = torch.tensor(np.asarray(cfg["x0"], np.float32), device="cuda")
+    ua, ub = torch.zeros(2, device="cuda"), torch.zeros(2, device="cuda")
+    for _ in range(3):
+        a.step_async(dx.data_ptr(), ua.data_ptr())
+        a.shift()
+        b.iterate_async(dx.data_ptr(), ub.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(ua, ub)
+        ga, gb = a.get_debug(), b.get_debug()
+        assert ga["kstar"] == gb["kstar"] and ga["eta"] == gb["eta"] and np.array_equal(ga["dU"], gb["dU"])
+    assert np.array_equal(a.get_controls(), b.get_controls())
+    assert a.get_iteration() == b.get_iteration() == 3
+
+
 @pytest.mark.parametrize("system,T", [(W.CAR, 40), (W.QUAD, 80), (W.CARTPOLE, 30)])
 def test_step_shift_equals_step_then_shift(N, system, T):
     """mppi_step_shift (host buffers; one graph with the shift in the update's launch when
