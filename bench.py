@@ -86,7 +86,8 @@ def source_hash(names=None):
     """sha256 prefix of the CUDA sources (all of csrc/, or the named files in it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1509_01149_b300", "csrc")
-    paths = [os.path.join(csrc, n) for n in names] if names else sorted(glob.glob(os.path.join(csrc, "*")))
+    paths = ([os.path.join(csrc, n) for n in names] if names else
+             sorted(q for q in glob.glob(os.path.join(csrc, "*")) if os.path.isfile(q) and not q.endswith(".pyc")))
     for p in paths:
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
@@ -637,9 +638,9 @@ def run_ours(args, rank, world, local_rank):
     # the merge and the shift share one cluster launch while the T*m outputs fit 8 CTAs of 32
     fused_shift = T_STEPS * W.CONTROL_DIM[SYSTEM] <= 8 * 32
     launches_per_step = 2 if fused_shift else 3
-    launch_note = ("per step one CUDA-graph launch of 2 kernels (rollout; FP64 merge + update + shift in one "
+    launch_note = ("per step one CUDA-graph launch of 2 kernels (rollout; merge (FP64 normaliser, double-FP32 sums) + update + shift in one "
                    "thread-block cluster)" if fused_shift else
-                   "per step one CUDA-graph launch of 3 kernels (rollout, FP64 merge + update, shift)")
+                   "per step one CUDA-graph launch of 3 kernels (rollout, merge (FP64 normaliser, double-FP32 sums) + update, shift)")
     ms_per_step = 1e3 * total_s / args.steps
     clk = clocks.stop()
     # the dominant kernel alone (for the roofline): rollout launches between events, same stream
