@@ -105,16 +105,21 @@ int mppi_destroy(mppi_ctx *ctx);
 
 /* One MPPI iteration from state h_state (host [n], copied): noise, rollout, cost,
  * weights and update of U (not the shift).  Writes the updated u_0 to h_u0_out
- * (host [m]).  Blocks until the result is on the host.  ESTATE if the system needs
- * an environment (car: cost map; quadrotor: forest; car_mlp: map + weights) that
- * was not set. */
+ * (host [m]).  Blocks until u_0 is on the host: on the fused path with the path-cost
+ * weighting the update kernel raises a flag in mapped host memory as soon as u_0 is
+ * there, and the call returns while the rest of the iteration (the write of U, a shift)
+ * may still run on the ctx's stream; every later call on the ctx is ordered after it,
+ * and an error of that remainder is returned by the next call that synchronises.
+ * ESTATE if the system needs an environment (car: cost map; quadrotor: forest;
+ * car_mlp: map + weights) that was not set. */
 int mppi_step(mppi_ctx *ctx, const float *h_state, float *h_u0_out);
 
 /* One pass of Algorithm 1's loop body from host buffers: the iteration of mppi_step,
  * u_0 to h_u0_out (host [m]), then the shift of mppi_shift (u_i <- u_{i+1},
- * u_{T-1} <- u_init, iteration counter += 1).  Blocks until u_0 is on the host; the
- * shift has completed by then too.  Same errors as mppi_step.  On the fused path this is
- * one CUDA graph in which the shift runs inside the update's launch when T*m <= 256. */
+ * u_{T-1} <- u_init, iteration counter += 1).  Blocks until u_0 is on the host, as
+ * mppi_step does (the shift is ordered before every later call on the ctx).  Same errors
+ * as mppi_step.  On the fused path this is one CUDA graph in which the shift runs inside
+ * the update's launch when T*m <= 256. */
 int mppi_step_shift(mppi_ctx *ctx, const float *h_state, float *h_u0_out);
 
 /* Same iteration, asynchronous on the ctx stream, device pointers: d_state [n] is

@@ -1,8 +1,10 @@
 // Host runtime of the MPPI C ABI (include/mppi.h): controller contexts, device
 // memory, the CUDA graph of one iteration, and the plain-loop baseline.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+
 #include <cstring>
 #include <new>
 #include <utility>
@@ -139,6 +141,7 @@ struct mppi_ctx {
 
   float *h_x0 = nullptr, *h_u0 = nullptr;    // pinned, mapped: the step graphs copy x0 from
   float *dh_x0 = nullptr, *dh_u0 = nullptr;  // h_x0 and write u0 into h_u0 directly
+  unsigned int *h_ready = nullptr, *dh_ready = nullptr;  // pinned, mapped: set once u0 is in h_u0
 
   cudaGraphExec_t graph = nullptr;        // mppi_step: rollout -> merge
   cudaGraphExec_t graph_shift = nullptr;  // mppi_step_shift: rollout -> merge + shift
@@ -185,13 +188,15 @@ int launch_rollout(mppi_ctx *c, const float *x0, cudaStream_t s) {
                  "fused rollout launch");
 }
 
-int launch_update(mppi_ctx *c, float *u0_out, cudaStream_t s) {
+// u0_ready: the path-weighting merge raises this mapped flag once u0 is in u0_out
+int launch_update(mppi_ctx *c, float *u0_out, cudaStream_t s, unsigned int *u0_ready = nullptr) {
   if (c->weighting == MPPI_WEIGHT_TO_GO)
     return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->d_U, u0_out,
                                       c->d_dU, c->d_dbg, s),
                    "cost-to-go merge launch");
-  return c->cuda(launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU, c->d_dbg, s),
-                 "merge launch");
+  return c->cuda(
+      launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU, c->d_dbg, s, u0_ready),
+      "merge launch");
 }
 
 int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
@@ -215,8 +220,8 @@ int enqueue_plain(mppi_ctx *c, cudaStream_t s) {
 
 // Capture one step graph: x0 copied from the pinned buffer (one DMA: cheaper than every CTA
 // reading mapped host memory), the merge writes u0 straight into the mapped pinned buffer
-// (no copy node), and with `shift` the shift runs in the same launch when the outputs fit one
-// cluster, else by the shift kernel after it.
+// (no copy node) and then raises the mapped ready flag, and with `shift` the shift runs in
+// the same launch when the outputs fit one cluster, else by the shift kernel after it.
 int capture_step(mppi_ctx *c, bool shift, cudaGraphExec_t *out) {
   if (*out) {
     cudaGraphExecDestroy(*out);
@@ -230,10 +235,10 @@ int capture_step(mppi_ctx *c, bool shift, cudaGraphExec_t *out) {
   if (rc == MPPI_OK) {
     if (shift && merge_shift_fusable(c->p) && c->weighting == MPPI_WEIGHT_PATH) {
       rc = c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->dh_u0, c->d_dU,
-                                             c->d_dbg, c->d_uinit, c->d_st, c->stream),
+                                             c->d_dbg, c->d_uinit, c->d_st, c->stream, c->dh_ready),
                    "merge + shift launch");
     } else {
-      rc = launch_update(c, c->dh_u0, c->stream);
+      rc = launch_update(c, c->dh_u0, c->stream, c->dh_ready);
       if (rc == MPPI_OK && shift)
         rc = c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
     }
@@ -338,6 +343,7 @@ int set_mlp_env(mppi_ctx *c, const void *blob, size_t bytes) {
   const float *P = reinterpret_cast<const float *>(static_cast<const char *>(blob) + sizeof h);
   for (size_t i = 0; i < mlp::kNumParams; ++i)
     if (!std::isfinite(P[i])) return c->fail(MPPI_EINVAL, "non-finite MLP parameter");
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));  // no step of this ctx in flight
   const int E = h.precision == 0 ? 2 : 1, K1 = h.precision == 0 ? 16 : 32;
   float sc[3] = {1.0f, 1.0f, 1.0f};
   if (h.precision == 1) {  // per-tensor scales: the largest weight maps to the largest E4M3 value
@@ -503,6 +509,11 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
     rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_x0), c->h_x0, 0), "mapped x0");
   if (rc == MPPI_OK)
     rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_u0), c->h_u0, 0), "mapped u0");
+  if (rc == MPPI_OK)
+    rc = c->cuda(cudaHostAlloc(reinterpret_cast<void **>(&c->h_ready), sizeof(unsigned int), cudaHostAllocMapped),
+                 "cudaHostAlloc");
+  if (rc == MPPI_OK)
+    rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_ready), c->h_ready, 0), "mapped flag");
   if (rc == MPPI_OK) rc = c->cuda(cudaStreamSynchronize(c->stream), "sync");
   if (rc != MPPI_OK) {
     g_create_error = c->err;
@@ -528,6 +539,7 @@ int mppi_destroy(mppi_ctx *c) {
   if (c->d_mlp) cudaFree(c->d_mlp);
   if (c->h_x0) cudaFreeHost(c->h_x0);
   if (c->h_u0) cudaFreeHost(c->h_u0);
+  if (c->h_ready) cudaFreeHost(c->h_ready);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return MPPI_OK;
@@ -588,6 +600,7 @@ int mppi_set_sampling_covariance(mppi_ctx *c, const float *h_Sigma_E) {
         dst[mm + a] = static_cast<float>(Rd[a] - static_cast<double>(c->p.lambda) * Si[a]);
       }
     }
+    MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));  // no step of this ctx in flight
     if (!c->d_gen) MPPI_TRY(c->cuda(cudaMalloc(&c->d_gen, sizeof(float) * host.size()), "cudaMalloc(covariances)"));
     MPPI_TRY(c->cuda(cudaMemcpy(c->d_gen, host.data(), sizeof(float) * host.size(), cudaMemcpyHostToDevice),
                      "covariance copy"));
@@ -750,6 +763,22 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
 }
 
 namespace {
+// Wait until the step graph's merge has put u0 into host memory (its mapped ready flag), or
+// the stream has finished; the rest of the iteration (U, the shift, the counter) may still be
+// running, and every later call on the ctx's stream is ordered after it.
+int wait_u0(mppi_ctx *c) {
+  for (unsigned long it = 1;; ++it) {
+    if (*reinterpret_cast<volatile unsigned int *>(c->h_ready) != 0u) break;
+    if ((it & 63u) == 0u) {
+      const cudaError_t q = cudaStreamQuery(c->stream);
+      if (q == cudaSuccess) break;
+      if (q != cudaErrorNotReady) return c->cuda(q, "step");
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  return MPPI_OK;
+}
+
 int step_host(mppi_ctx *c, const float *state, float *u0_out, bool shift) {
   if (!c || !state || !u0_out) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
@@ -764,7 +793,16 @@ int step_host(mppi_ctx *c, const float *state, float *u0_out, bool shift) {
     if (shift) MPPI_TRY(c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch"));
   } else {
     if (c->graph_dirty) MPPI_TRY(build_graph(c));
+    // the path-weighting merge raises the ready flag; the learned dynamics also need the
+    // kernel's own status, read after the stream finishes
+    const bool flag = c->weighting == MPPI_WEIGHT_PATH && c->sys != MPPI_CAR_MLP;
+    if (flag) *reinterpret_cast<volatile unsigned int *>(c->h_ready) = 0u;
     MPPI_TRY(c->cuda(cudaGraphLaunch(shift ? c->graph_shift : c->graph, c->stream), "graph launch"));
+    if (flag) {
+      MPPI_TRY(wait_u0(c));
+      std::memcpy(u0_out, c->h_u0, sizeof(float) * c->m);
+      return MPPI_OK;
+    }
   }
   MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));
   MPPI_TRY(check_mlp_error(c));

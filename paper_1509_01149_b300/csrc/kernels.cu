@@ -109,7 +109,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
                                                                 float *__restrict__ dU_dbg,
                                                                 StepDebug *__restrict__ dbg,
                                                                 const float *__restrict__ u_init,
-                                                                CtrlState *__restrict__ st) {
+                                                                CtrlState *__restrict__ st,
+                                                                unsigned int *__restrict__ u0_ready) {
   constexpr int NW = kMergeThreads / 32;
   static_assert(NW == kMergeRanges, "one warp per range of block partials");
   extern __shared__ double s_eb[];  // [nblk] eta_b, then [nblk] floats: rho_b, then s_b
@@ -192,6 +193,14 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
     U[o] = un;
     dU_dbg[o] = static_cast<float>(du);
     if (o < m) u0_out[o] = un;
+  }
+  // u0 is final: raise the host's flag (u0 in host memory before it) ahead of the rest
+  if (u0_ready != nullptr && blockIdx.x == 0 && warp == 0) {
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_system();
+      *reinterpret_cast<volatile unsigned int *>(u0_ready) = 1u;
+    }
   }
   if (SHIFT) {
     cluster_sync_all();  // every CTA's updated U visible to the cluster
@@ -659,7 +668,8 @@ cudaError_t prepare_kernels() {
 }
 
 cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
-                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
+                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s,
+                                unsigned int *u0_ready) {
   const int TM = p.T * p.m;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((TM + kMergeOutputs - 1) / kMergeOutputs, 1, 1);
@@ -678,7 +688,7 @@ cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part
   const float *no_uinit = nullptr;
   CtrlState *no_st = nullptr;
   return cudaLaunchKernelEx(&cfg, k_merge_update<false>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,
-                            no_uinit, no_st);
+                            no_uinit, no_st, u0_ready);
 }
 
 bool merge_shift_fusable(const CtrlParams &p) {
@@ -687,7 +697,7 @@ bool merge_shift_fusable(const CtrlParams &p) {
 
 cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                       float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
-                                      CtrlState *st, cudaStream_t s) {
+                                      CtrlState *st, cudaStream_t s, unsigned int *u0_ready) {
   const int TM = p.T * p.m;
   const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
   if (grid > kMergeClusterMax) return cudaErrorInvalidValue;
@@ -708,7 +718,7 @@ cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float
   const int m = p.m;
   const float il = p.inv_lambda;
   return cudaLaunchKernelEx(&cfg, k_merge_update<true>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,
-                            u_init, st);
+                            u_init, st, u0_ready);
 }
 
 cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s) {

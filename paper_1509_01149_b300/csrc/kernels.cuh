@@ -36,16 +36,19 @@ int fused_block_samples(int blk);
 // st: iteration counter.
 cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
                                  const float *U, float *S, float *part_sums, BlockPartial *part, cudaStream_t s);
-// Cross-block FP64 merge: rho, kstar, eta, du; U += du; u0 out.
+// Cross-block merge (FP64 normaliser, double-FP32 sums in a fixed order): rho, kstar, eta,
+// du; U += du; u0 out.  u0_ready (optional, mapped host memory): set to 1 once u0_out holds
+// u0 (visible to the host before the flag), ahead of the kernel's remaining work.
 cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
-                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s);
+                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s,
+                                unsigned int *u0_ready = nullptr);
 // The merge and the shift of Algorithm 1 in one launch (a thread-block cluster of one CTA
 // per 32 outputs), when the outputs fit in kMergeClusterMax CTAs.
 constexpr int kMergeClusterMax = 8;
 bool merge_shift_fusable(const CtrlParams &p);
 cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                       float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
-                                      CtrlState *st, cudaStream_t s);
+                                      CtrlState *st, cudaStream_t s, unsigned int *u0_ready = nullptr);
 // Cost-to-go weighting (Eq. App_PI per time step): block shape (128 or 64 samples, du and the
 // step costs in shared memory; 0 if they do not fit), the rollout with per-step block partials
 // (part_rho / part_eta [nblk][T]) and their FP64 merge + update.
