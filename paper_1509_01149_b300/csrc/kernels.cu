@@ -23,6 +23,7 @@
 #include "merge_common.cuh"
 #include "rollout_body.cuh"
 #include "rollout_lanes.cuh"
+#include "rollout_quad_ws.cuh"
 #include "rollout_ws.cuh"
 
 namespace mppi {
@@ -65,6 +66,18 @@ __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlP
   extern __shared__ __align__(16) float smem[];
   rollout_block_car_ws<NS>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
                            part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem);
+}
+
+// quadrotor: noise / RK4 dynamics / crash decisions and cost in three warp roles, see rollout_quad_ws.cuh
+template <int NS>
+__global__ void __launch_bounds__(4 * NS, 1) k_rollout_quad_ws(const CtrlParams p, const float *__restrict__ x0,
+                                                               const CtrlState *__restrict__ st,
+                                                               const float *__restrict__ U, float *__restrict__ S_out,
+                                                               float *__restrict__ part_sums,
+                                                               BlockPartial *__restrict__ part) {
+  extern __shared__ __align__(16) float smem[];
+  rollout_block_quad_ws<NS>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+                            part_sums + static_cast<size_t>(blockIdx.x) * p.T * Quad::M, part + blockIdx.x, smem);
 }
 
 // quadrotor: four lanes per sample (shared RK4 step, split cylinder search), see rollout_lanes.cuh
@@ -494,6 +507,7 @@ __global__ void k_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_bl
 size_t fused_smem_bytes(const CtrlParams &p, int blk) {
   if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples);
   if (blk == kFusedBlockQuadLanes) return quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
+  if (blk == kFusedBlockQuadWs) return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples);
   const bool regen = blk == kFusedBlockRegen;
   return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen, false, p.gen != nullptr);
 }
@@ -506,6 +520,8 @@ int fused_block_size(int sys, const CtrlParams &p) {
   }
   if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && fused_smem_bytes(p, kFusedBlockCarWs) <= kFusedSmemLimit)
     return kFusedBlockCarWs;
+  if (sys == 2 && p.T <= kQwsChunk * kQwsMaxChunks && fused_smem_bytes(p, kFusedBlockQuadWs) <= kFusedSmemLimit)
+    return kFusedBlockQuadWs;
   if (sys == 2 && fused_smem_bytes(p, kFusedBlockQuadLanes) <= kFusedSmemLimit) return kFusedBlockQuadLanes;
   if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;
   if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
@@ -516,6 +532,7 @@ int fused_block_size(int sys, const CtrlParams &p) {
 int fused_block_samples(int blk) {
   if (blk == kFusedBlockCarWs) return kWsSamples;
   if (blk == kFusedBlockQuadLanes) return kQuadLanesBlock / kQuadLanes;
+  if (blk == kFusedBlockQuadWs) return kQwsSamples;
   return blk == kFusedBlockRegen ? kFusedBlockLarge : blk;
 }
 
@@ -560,6 +577,12 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
       if (blk == kFusedBlockCarWs) return launch_car_ws(p, x0, st, U, S, part_sums, part, s);
       return launch_fused_sys<Car>(blk, p, x0, st, U, S, part_sums, part, s);
     case 2:
+      if (blk == kFusedBlockQuadWs) {
+        const size_t smem = quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples);
+        const int grid = (p.K + kQwsSamples - 1) / kQwsSamples;
+        k_rollout_quad_ws<kQwsSamples><<<grid, 4 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part);
+        return cudaGetLastError();
+      }
       if (blk == kFusedBlockQuadLanes) {
         const size_t smem = quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
         const int grid = (p.K + kQuadLanesBlock / kQuadLanes - 1) / (kQuadLanesBlock / kQuadLanes);
@@ -654,6 +677,7 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_to_go<Quad, kFusedBlockLarge>),
       reinterpret_cast<const void *>(k_rollout_to_go<Quad, kFusedBlockSmall>),
       reinterpret_cast<const void *>(k_rollout_quad_lanes<kQuadLanesBlock, kQuadLanes>),
+      reinterpret_cast<const void *>(k_rollout_quad_ws<kQwsSamples>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, true>),

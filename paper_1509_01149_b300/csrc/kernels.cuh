@@ -11,6 +11,7 @@ constexpr int kFusedBlockSmall = 64;
 constexpr int kFusedBlockRegen = 129;   // code for "128 samples, du regenerated (no shared-memory copy)"
 constexpr int kFusedBlockCarWs = 257;   // code for "car, 128 samples, three threads per sample"
 constexpr int kFusedBlockQuadLanes = 513;  // code for "quadrotor, 32 samples, a group of lanes per sample"
+constexpr int kFusedBlockQuadWs = 1025;    // code for "quadrotor, 64 samples, three warp roles"
 constexpr int kQuadLanesBlock = 64, kQuadLanes = 2;
 constexpr int kMinBlockSamples = kQuadLanesBlock / kQuadLanes;  // fewest samples per block of any shape
 constexpr int kMergeThreads = 256;
@@ -25,7 +26,8 @@ cudaError_t prepare_kernels();
 // Shared memory of the fused rollout for block size blk (bytes).
 size_t fused_smem_bytes(const CtrlParams &p, int blk);
 // Block shape for a controller of system sys: for the car kFusedBlockCarWs and for the
-// quadrotor kFusedBlockQuadLanes when their shared memory fits; else 128 or 64 samples with
+// quadrotor kFusedBlockQuadWs (else kFusedBlockQuadLanes) when their shared memory fits; else
+// 128 or 64 samples with
 // du kept in shared memory, else kFusedBlockRegen (128 samples, du regenerated); 0 if
 // nothing fits.
 int fused_block_size(int sys, const CtrlParams &p);

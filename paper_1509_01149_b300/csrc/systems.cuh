@@ -396,9 +396,10 @@ struct Quad {
     d[11] = (tz - (Iyy - Ixx) * wp * wq) * (1.0f / Izz);
   }
 
-  __device__ __forceinline__ static void step(float x[N], const float f[M], Aux &a, const Env &e, float dt) {
-    if (a.crashed) return;
-    float k1[N], k2[N], k3[N], k4[N], y[N];
+  // One classical RK4 step y = x + dt/6 (k1 + 2 k2 + 2 k3 + k4); returns whether every
+  // component of y is finite.
+  __device__ __forceinline__ static bool rk4(const float x[N], const float f[M], float dt, float y[N]) {
+    float k1[N], k2[N], k3[N], k4[N];
     deriv(x, f, k1);
 #pragma unroll
     for (int i = 0; i < N; ++i) y[i] = x[i] + 0.5f * dt * k1[i];
@@ -415,6 +416,13 @@ struct Quad {
       y[i] = x[i] + (dt / 6.0f) * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
       finite = finite && isfinite(y[i]);
     }
+    return finite;
+  }
+
+  __device__ __forceinline__ static void step(float x[N], const float f[M], Aux &a, const Env &e, float dt) {
+    if (a.crashed) return;
+    float y[N];
+    const bool finite = rk4(x, f, dt, y);
     const float d = finite ? obstacle_distance(e, y[0], y[1]) : -1.0f;
     const bool hit = !finite || d < 0.0f || y[2] < 0.0f || (pitch_limit - fabsf(y[7])) <= 0.0f;
     if (hit) {
@@ -431,23 +439,8 @@ struct Quad {
   // through the shuffles of the obstacle distance.  Same result as step().
   __device__ __forceinline__ static void step_lanes(float x[N], const float f[M], Aux &a, const Env &e, float dt,
                                                     int sub, int lanes) {
-    float k1[N], k2[N], k3[N], k4[N], y[N];
-    deriv(x, f, k1);
-#pragma unroll
-    for (int i = 0; i < N; ++i) y[i] = x[i] + 0.5f * dt * k1[i];
-    deriv(y, f, k2);
-#pragma unroll
-    for (int i = 0; i < N; ++i) y[i] = x[i] + 0.5f * dt * k2[i];
-    deriv(y, f, k3);
-#pragma unroll
-    for (int i = 0; i < N; ++i) y[i] = x[i] + dt * k3[i];
-    deriv(y, f, k4);
-    bool finite = true;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      y[i] = x[i] + (dt / 6.0f) * (k1[i] + 2.0f * k2[i] + 2.0f * k3[i] + k4[i]);
-      finite = finite && isfinite(y[i]);
-    }
+    float y[N];
+    const bool finite = rk4(x, f, dt, y);
     float d = obstacle_distance_lanes(e, y[0], y[1], sub, lanes);
     if (!finite) d = -1.0f;
     const bool hit = !finite || d < 0.0f || y[2] < 0.0f || (pitch_limit - fabsf(y[7])) <= 0.0f;
