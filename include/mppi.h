@@ -384,6 +384,17 @@ int mppi_car_step(const float *d_states, const float *d_controls, int n, float d
 int mppi_debug_gemm_bf16(int M, int N, int K, const void *dA, int64_t sam, int64_t sak, const void *dB, int64_t sbk,
                          int64_t sbn, float *dC, int64_t ldc, int BN);
 
+/* Check hook for the quadrotor's nearest-cylinder grid (host only, no GPU needed).  Builds
+ * the grid that mppi_set_env builds for the forest obs [n_obs][3] (x, y, radius; n_obs in
+ * [1, 256]) and, for each of the n_points host points (px[i], py[i]), writes the distance
+ * to the nearest cylinder surface, sqrt((x - cx)^2 + (y - cy)^2) - r in FP32, minimised over
+ * the candidate list of the point's cell (d_grid[i]) and over every cylinder (d_all[i]), and
+ * in_grid[i] = 1 when the point lies inside the grid (else 0 and d_grid[i] = d_all[i]).
+ * Caller-owned host buffers.  Returns 0, or MPPI_EINVAL for bad arguments or when no grid
+ * fits its caps. */
+int mppi_debug_forest_nearest(const float *obs, int n_obs, int n_points, const float *px, const float *py,
+                              float *d_grid, float *d_all, int *in_grid);
+
 /* Text of the last error on this ctx (or of the last failed create when ctx is NULL).
  * Valid until the next call on the ctx. */
 const char *mppi_last_error(mppi_ctx *ctx);

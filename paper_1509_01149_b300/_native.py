@@ -83,6 +83,7 @@ SIGNATURES = [
     ("mppi_server_autotune", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP]),
     ("mppi_server_get_info", C.c_int, [_P, C.POINTER(ServerInfo)]),
     ("mppi_server_last_error", C.c_char_p, [_P]),
+    ("mppi_debug_forest_nearest", C.c_int, [_FP, C.c_int, C.c_int, _FP, _FP, _FP, _FP, C.POINTER(C.c_int)]),
     ("mppi_debug_gemm_bf16", C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.c_int64, C.c_int64, _P, C.c_int64,
                                        C.c_int64, _P, C.c_int64, C.c_int]),
     ("mppi_mlp_create", C.c_int, [C.c_uint64, C.POINTER(_P)]),
@@ -135,6 +136,21 @@ def _f32(a, n=None) -> np.ndarray:
 
 def _fp(a: np.ndarray):
     return a.ctypes.data_as(_FP)
+
+
+def forest_nearest(obs, px, py):
+    """mppi_debug_forest_nearest: (d over the cell's candidate list, d over every cylinder,
+    in-grid flags) for host points, with the grid mppi_set_env builds for this forest."""
+    O = _f32(obs)
+    x, y = _f32(px), _f32(py)
+    n = x.size
+    dg, da = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    ig = np.zeros(n, np.int32)
+    rc = lib.mppi_debug_forest_nearest(_fp(O), O.size // 3, n, _fp(x), _fp(y), _fp(dg), _fp(da),
+                                       ig.ctypes.data_as(C.POINTER(C.c_int)))
+    if rc != MPPI_OK:
+        raise MppiError(rc, "mppi_debug_forest_nearest")
+    return dg, da, ig.astype(bool)
 
 
 def map_blob(cost_map: np.ndarray, origin_x: float, origin_y: float, cell: float) -> bytes:

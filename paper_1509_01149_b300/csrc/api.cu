@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/mppi.h"
+#include "forest_grid.h"
 #include "kernels.cuh"
 #include "mlp_model.cuh"
 
@@ -524,6 +525,34 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   return MPPI_OK;
 }
 
+int mppi_debug_forest_nearest(const float *obs, int n_obs, int n_points, const float *px, const float *py,
+                              float *d_grid, float *d_all, int *in_grid) {
+  if (!obs || n_obs < 1 || n_obs > 256 || n_points < 0 || (n_points > 0 && (!px || !py || !d_grid || !d_all || !in_grid)))
+    return MPPI_EINVAL;
+  ForestGrid g;
+  if (!build_forest_grid(obs, n_obs, g)) return MPPI_EINVAL;
+  auto dist = [&](int j, float x, float y) {
+    const float ax = x - obs[3 * j], ay = y - obs[3 * j + 1];
+    return std::sqrt(std::fma(ax, ax, ay * ay)) - obs[3 * j + 2];
+  };
+  for (int i = 0; i < n_points; ++i) {
+    float all = INFINITY;
+    for (int j = 0; j < n_obs; ++j) all = std::fmin(all, dist(j, px[i], py[i]));
+    d_all[i] = all;
+    const float gx = (px[i] - g.ox) * g.inv_h, gy = (py[i] - g.oy) * g.inv_h;
+    in_grid[i] = gx >= 0.0f && gy >= 0.0f && gx < static_cast<float>(g.nx) && gy < static_cast<float>(g.ny);
+    if (!in_grid[i]) {
+      d_grid[i] = all;
+      continue;
+    }
+    const int cell = static_cast<int>(gy) * g.nx + static_cast<int>(gx);
+    float d = INFINITY;
+    for (int t = g.off[cell]; t < g.off[cell + 1]; ++t) d = std::fmin(d, dist(g.idx[t], px[i], py[i]));
+    d_grid[i] = d;
+  }
+  return MPPI_OK;
+}
+
 int mppi_destroy(mppi_ctx *c) {
   if (!c) return MPPI_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -698,6 +727,8 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   const char *payload = nullptr;
   size_t payload_bytes = 0;
   CtrlParams np = c->p;
+  ForestGrid grid;
+  std::vector<char> forest;  // cylinders + grid, when there is a grid
   if (kind == MPPI_ENV_MLP) return set_mlp_env(c, blob, bytes);
   if (kind == MPPI_ENV_MAP) {
     if (c->sys != MPPI_CAR && c->sys != MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "map env for a non-car system");
@@ -717,6 +748,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
     np.map_oy = h.origin_y;
     np.map_inv_cell = 1.0f / h.cell;
     np.n_obs = 0;
+    np.grid_nx = np.grid_ny = np.grid_nidx = 0;
   } else if (kind == MPPI_ENV_FOREST) {
     if (c->sys != MPPI_QUAD) return c->fail(MPPI_EINVAL, "forest env for a non-quadrotor system");
     if (bytes < sizeof(mppi_env_forest)) return c->fail(MPPI_EINVAL, "forest header truncated");
@@ -728,6 +760,24 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
     payload = static_cast<const char *>(blob) + sizeof h;
     np.n_obs = h.n_obstacles;
     for (int i = 0; i < 3; ++i) np.goal[i] = h.goal[i];
+    // the cylinders, then the nearest-cylinder grid (offsets, indices) in one device buffer
+    if (build_forest_grid(reinterpret_cast<const float *>(payload), h.n_obstacles, grid)) {
+      np.grid_nx = grid.nx;
+      np.grid_ny = grid.ny;
+      np.grid_nidx = static_cast<int>(grid.idx.size());
+      np.grid_ox = grid.ox;
+      np.grid_oy = grid.oy;
+      np.grid_inv_h = grid.inv_h;
+      forest.assign(payload, payload + payload_bytes);
+      const size_t at = forest.size();
+      forest.resize(at + grid.bytes());
+      std::memcpy(forest.data() + at, grid.off.data(), sizeof(uint16_t) * grid.off.size());
+      std::memcpy(forest.data() + at + sizeof(uint16_t) * grid.off.size(), grid.idx.data(), grid.idx.size());
+      payload = forest.data();
+      payload_bytes = forest.size();
+    } else {
+      np.grid_nx = np.grid_ny = np.grid_nidx = 0;
+    }
     if (block_shape(c, np) == 0) return c->fail(MPPI_EINVAL, "forest too large for shared memory");
   } else {
     return c->fail(MPPI_EINVAL, "unknown env kind 0x%08x", kind);
@@ -750,6 +800,12 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   } else {
     np.obs = c->d_env;
     np.map = nullptr;
+    const char *g = reinterpret_cast<const char *>(c->d_env) + sizeof(float) * 3 * static_cast<size_t>(np.n_obs);
+    np.grid_off = np.grid_nx > 0 ? reinterpret_cast<const unsigned short *>(g) : nullptr;
+    np.grid_idx = np.grid_nx > 0 ? reinterpret_cast<const unsigned char *>(g) + sizeof(uint16_t) *
+                                                                                   (static_cast<size_t>(np.grid_nx) *
+                                                                                        np.grid_ny + 1)
+                                 : nullptr;
   }
   np.mlp = c->p.mlp;
   c->p = np;

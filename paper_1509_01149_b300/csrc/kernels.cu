@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlP
 
 // quadrotor: noise / RK4 dynamics / crash decisions and cost in three warp roles, see rollout_quad_ws.cuh
 template <int NS>
-__global__ void __launch_bounds__(4 * NS, 1) k_rollout_quad_ws(const CtrlParams p, const float *__restrict__ x0,
+__global__ void __launch_bounds__(3 * NS, 1) k_rollout_quad_ws(const CtrlParams p, const float *__restrict__ x0,
                                                                const CtrlState *__restrict__ st,
                                                                const float *__restrict__ U, float *__restrict__ S_out,
                                                                float *__restrict__ part_sums,
@@ -507,7 +507,8 @@ __global__ void k_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_bl
 size_t fused_smem_bytes(const CtrlParams &p, int blk) {
   if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples);
   if (blk == kFusedBlockQuadLanes) return quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
-  if (blk == kFusedBlockQuadWs) return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples);
+  if (blk == kFusedBlockQuadWs)
+    return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p.grid_nx, p.grid_ny, p.grid_nidx));
   const bool regen = blk == kFusedBlockRegen;
   return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen, false, p.gen != nullptr);
 }
@@ -578,9 +579,9 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
       return launch_fused_sys<Car>(blk, p, x0, st, U, S, part_sums, part, s);
     case 2:
       if (blk == kFusedBlockQuadWs) {
-        const size_t smem = quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples);
+        const size_t smem = fused_smem_bytes(p, kFusedBlockQuadWs);
         const int grid = (p.K + kQwsSamples - 1) / kQwsSamples;
-        k_rollout_quad_ws<kQwsSamples><<<grid, 4 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part);
+        k_rollout_quad_ws<kQwsSamples><<<grid, 3 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part);
         return cudaGetLastError();
       }
       if (blk == kFusedBlockQuadLanes) {

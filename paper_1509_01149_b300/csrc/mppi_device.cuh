@@ -116,6 +116,12 @@ struct CtrlParams {
   float map_ox, map_oy, map_inv_cell;
   const float *obs;         // quadrotor cylinders [n_obs][3]
   int n_obs;
+  // quadrotor: uniform grid of nearest-cylinder candidate lists over the forest (built on the
+  // host, forest_grid.h); grid_nx == 0: none, every query searches all cylinders
+  const unsigned short *grid_off;  // [grid_nx * grid_ny + 1] list starts in grid_idx
+  const unsigned char *grid_idx;   // [grid_nidx] cylinder indices, cell by cell
+  int grid_nx, grid_ny, grid_nidx;
+  float grid_ox, grid_oy, grid_inv_h;  // cell (ix, iy) covers [ox + ix/inv_h, ox + (ix+1)/inv_h) x ...
   float goal[3];
   const void *mlp;          // learned dynamics weights (car_mlp)
   const float *gen;         // general sampling covariance: [T][2][m][m] = (chol(Sigma_E,i),

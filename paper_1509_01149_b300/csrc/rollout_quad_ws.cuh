@@ -10,13 +10,13 @@
 // after a crash are simply never used, so the costs are those of the sequential step:
 // same arithmetic, same order.
 //
-// A CTA owns NS samples with 4 NS threads in three warp-uniform roles:
+// A CTA owns NS samples with 3 NS threads in three warp-uniform roles:
 //   noise     (threads 0..NS-1)        Philox block i -> du_i = sqrt(nu) L eps (m = 4),
 //                                      ahead of the others;
 //   dynamics  (threads NS..2NS-1)      the RK4 chain, nothing else;
-//   cost      (threads 2NS..4NS-1)     two lanes per sample: the cylinder search split
-//                                      between them, crash logic, q(x), the
-//                                      importance-sampling terms and S~ (Kahan).
+//   cost      (threads 2NS..3NS-1)     the nearest cylinder (searched over its grid cell's
+//                                      candidate list, forest_grid.h), crash logic, q(x),
+//                                      the importance-sampling terms and S~ (Kahan).
 // Shared memory carries the hand-offs in chunks of C steps:
 //   du   [T*M][NS]       noise -> dynamics and cost, one single-use mbarrier per chunk (also
 //                        the operand of the block sums)
@@ -30,16 +30,59 @@
 
 namespace mppi {
 
-constexpr int kQwsSamples = 64;  // samples per CTA (4x threads)
+constexpr int kQwsSamples = 64;  // samples per CTA (3x threads)
 constexpr int kQwsChunk = 8;     // steps per hand-off
 constexpr int kQwsRing = 2;      // chunks in the state ring
 constexpr int kQwsMaxChunks = 32;
 constexpr int kQwsPass = 8;      // values per step handed from the dynamics to the cost role
 
-__host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns) {
+// bytes of the nearest-cylinder grid in shared memory (offsets, then indices, 16-byte padded)
+__host__ __device__ inline size_t quad_grid_bytes(int nx, int ny, int nidx) {
+  if (nx <= 0) return 0;
+  return (sizeof(unsigned short) * (static_cast<size_t>(nx) * ny + 1) + static_cast<size_t>(nidx) + 15) &
+         ~static_cast<size_t>(15);
+}
+
+__host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns, size_t grid_bytes) {
   const size_t TM = 4 * static_cast<size_t>(T);
   return sizeof(float) * (4 * static_cast<size_t>(n_obs) + 2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
-                          static_cast<size_t>(kQwsRing) * kQwsChunk * kQwsPass * ns);
+                          static_cast<size_t>(kQwsRing) * kQwsChunk * kQwsPass * ns) +
+         grid_bytes;
+}
+
+// Nearest cylinder surface: over the candidate list of the point's grid cell when the point
+// is inside the grid, else over every cylinder (the same float either way, forest_grid.h).
+// The first kQwsWindow entries of the list are read as one unrolled window whose positions
+// past the list's end repeat its last entry (a repeat leaves a minimum unchanged), so their
+// loads are independent and issue together; longer lists finish in a loop.
+constexpr int kQwsWindow = 8;
+__device__ __forceinline__ float quad_nearest(const Env &env, const CtrlParams &p, const unsigned short *sOff,
+                                              const unsigned char *sIdx, float px, float py) {
+  const float gx = (px - p.grid_ox) * p.grid_inv_h, gy = (py - p.grid_oy) * p.grid_inv_h;
+  if (gx >= 0.0f && gy >= 0.0f && gx < static_cast<float>(p.grid_nx) && gy < static_cast<float>(p.grid_ny)) {
+    const int cell = static_cast<int>(gy) * p.grid_nx + static_cast<int>(gx);
+    const float4 *o4 = reinterpret_cast<const float4 *>(env.obs);
+    const int t0 = sOff[cell], t1 = sOff[cell + 1];  // t1 > t0: every list holds a cylinder
+    float dw[kQwsWindow];
+#pragma unroll
+    for (int q = 0; q < kQwsWindow; ++q) {
+      const float4 c = o4[sIdx[min(t0 + q, t1 - 1)]];
+      const float ax = px - c.x, ay = py - c.y;
+      dw[q] = Quad::fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z;
+    }
+#pragma unroll
+    for (int w = kQwsWindow / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int q = 0; q < w; ++q) dw[q] = fminf(dw[q], dw[q + w]);
+    float d = dw[0];
+    for (int t = t0 + kQwsWindow; t < t1; ++t) {
+      const float4 c = o4[sIdx[t]];
+      const float ax = px - c.x, ay = py - c.y;
+      d = fminf(d, Quad::fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z);
+    }
+    return d;
+  }
+  return Quad::obstacle_distance(env, px, py);
 }
 
 template <int NS>
@@ -48,7 +91,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
                                                       float *__restrict__ S_out, float *__restrict__ part_sums,
                                                       BlockPartial *__restrict__ part, float *smem) {
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
-  constexpr int M = Quad::M, N = Quad::N, C = kQwsChunk, R = kQwsRing, P = kQwsPass, NT = 4 * NS;
+  constexpr int M = Quad::M, N = Quad::N, C = kQwsChunk, R = kQwsRing, P = kQwsPass, NT = 3 * NS;
   __shared__ uint64_t bar_noise[kQwsMaxChunks], bar_full[R], bar_empty[R];
   __shared__ float sx0[N];
   const int T = p.T, TM = T * M, tid = threadIdx.x;
@@ -61,15 +104,22 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
   float *sS = sW + NS;                                   // [NS]  path costs (cost role -> block partial)
   float *sDu = sS + NS;                                  // [TM][NS] perturbations
   float *sRing = sDu + static_cast<size_t>(TM) * NS;     // [R][C][P][NS]
+  unsigned short *sOff = reinterpret_cast<unsigned short *>(sRing + R * C * P * NS);  // [cells + 1]
+  const int ncell = p.grid_nx * p.grid_ny;
+  unsigned char *sIdx = reinterpret_cast<unsigned char *>(sOff + (ncell + 1));       // [grid_nidx]
 
   for (int o = tid; o < TM; o += NT) sU[o] = U[o];
   for (int o = tid; o < 4 * p.n_obs; o += NT) sObs[o] = (o & 3) == 3 ? 0.0f : p.obs[3 * (o >> 2) + (o & 3)];
+  if (p.grid_nx > 0) {
+    for (int o = tid; o <= ncell; o += NT) sOff[o] = p.grid_off[o];
+    for (int o = tid; o < p.grid_nidx; o += NT) sIdx[o] = p.grid_idx[o];
+  }
   if (tid < N) sx0[tid] = x0[tid];
   if (tid == 0) {
     for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], NS);
     for (int r = 0; r < R; ++r) {
       tc::mbar_init(&bar_full[r], NS);
-      tc::mbar_init(&bar_empty[r], 2 * NS);
+      tc::mbar_init(&bar_empty[r], NS);
     }
   }
   __syncthreads();
@@ -148,8 +198,8 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
       tc::mbar_arrive(&bar_full[c % R]);
     }
   } else {
-    // ---- cost: crash decisions, q(x), IS terms, S~ (two lanes per sample) -----------------
-    const int ct = tid - 2 * NS, slot = ct >> 1, sub = ct & 1;
+    // ---- cost: crash decisions, q(x), IS terms, S~ ------------------------------------------
+    const int slot = tid - 2 * NS;
     const Env env = make_env(p, sObs, 1);
     float Rm[M * M];
 #pragma unroll
@@ -159,13 +209,12 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
     for (int a = 0; a < N; ++a) x[a] = sx0[a];
     Quad::Aux aux;
     aux.crashed = false;
-    aux.d = Quad::obstacle_distance_lanes(env, x[0], x[1], sub, 2);
+    aux.d = quad_nearest(env, p, sOff, sIdx, x[0], x[1]);
     KahanSum S;
     for (int c = 0; c < nch; ++c) {
       // the noise wait is already satisfied (the dynamics waited on it before publishing
       // this chunk); taking it here makes the du writes visible to this thread directly
       ok = tc::mbar_wait(&bar_full[c % R], static_cast<uint32_t>((c / R) & 1)) && tc::mbar_wait(&bar_noise[c], 0u);
-      ok = __all_sync(0xffffffffu, ok);  // the lane pairs' shuffles need the whole warp
       if (!ok) break;
       const float *ring = sRing + (c % R) * (C * P * NS);
       const int i0 = c * C, steps = min(C, T - i0);
@@ -187,9 +236,10 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
           for (int l = 0; l < M; ++l) rd = fmaf(Rm[a * M + l], du[l], rd);
           duRdu = fmaf(du[a], rd, duRdu);
         }
-        // the sequential step's crash test on the new state (every lane of the warp takes
-        // part in the shuffles of the cylinder search, crashed samples included)
-        float d = Quad::obstacle_distance_lanes(env, px, py, sub, 2);
+        // the sequential step's crash test on the new state (a crashed sample keeps its state
+        // whatever the test says, and the states handed over after its crash can be far
+        // outside the forest, so it skips the search)
+        float d = aux.crashed ? 0.0f : quad_nearest(env, p, sOff, sIdx, px, py);
         const bool finite = isfinite(px);
         if (!finite) d = -1.0f;
         const bool hit = !finite || d < 0.0f || pz < 0.0f || (Quad::pitch_limit - fabsf(pitch)) <= 0.0f;
@@ -210,7 +260,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
       tc::mbar_arrive(&bar_empty[c % R]);
     }
     if (ok) S.add(Quad::cost(x, aux, env));  // phi(x_T) = q(x_T)
-    if (sub == 0) sS[slot] = ok ? S.s : INFINITY;
+    sS[slot] = ok ? S.s : INFINITY;
   }
   __syncthreads();
   // the update kernel may start launching now (it waits for this grid's results itself)
