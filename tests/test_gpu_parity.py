@@ -226,17 +226,21 @@ def test_graph_iteration_equals_step_and_shift(N):
     assert a.get_iteration() == b.get_iteration() == 3
 
 
-@pytest.mark.parametrize("K,T", [(40000, 33), (32768, 100), (65, 1), (16384, 100)])
-def test_merge_with_shift_equals_merge_then_shift_kernel(N, K, T):
-    """The iteration graph runs the merge and the shift in one thread-block cluster;
-    step_async runs the merge alone, then mppi_shift's kernel.  With up to 313 block partials
-    (ranges of 40 blocks, beyond the merge's register prefetch) the fixed reduction order
-    gives the same controls, u0, debug values and counter bit for bit, over three iterations."""
+@pytest.mark.parametrize("system,K,T", [(W.CAR, 40000, 33), (W.CAR, 32768, 100), (W.CAR, 65, 1),
+                                        (W.CAR, 16384, 100), (W.QUAD, 8192, 150), (W.CAR, 1024, 1000)])
+def test_merge_with_shift_equals_merge_then_shift_kernel(N, system, K, T):
+    """The iteration graph runs the merge and the shift in one thread-block cluster when
+    T*m <= 256 (else the merge, then the shift kernel: the quadrotor at T = 150, the car at
+    T = 1000); step_async runs the merge alone, then mppi_shift's kernel.  With up to 313 block
+    partials (ranges of 40 blocks, beyond the merge's register prefetch) the fixed reduction
+    order gives the same controls, u0, debug values and counter bit for bit, over three
+    iterations."""
     import torch
-    cfg = W.config(W.CAR, K=K, T=T, lam=30.0)
+    cfg = W.config(system, K=K, T=T, lam=30.0)
     a, b = P.make_controller(cfg), P.make_controller(cfg)
     dx = torch.tensor(np.asarray(cfg["x0"], np.float32), device="cuda")
-    ua, ub = torch.zeros(2, device="cuda"), torch.zeros(2, device="cuda")
+    m = a.m
+    ua, ub = torch.zeros(m, device="cuda"), torch.zeros(m, device="cuda")
     for _ in range(3):
         a.step_async(dx.data_ptr(), ua.data_ptr())
         a.shift()
