@@ -598,7 +598,7 @@ namespace {
 // block shape for the ctx's system, environment and weighting (0 if nothing fits)
 int block_shape(mppi_ctx *c, const CtrlParams &p) {
   if (c->sys == MPPI_CAR_MLP) return kFusedBlockRegen;
-  return c->weighting == MPPI_WEIGHT_TO_GO ? fused_block_size_to_go(p) : fused_block_size(c->sys, p);
+  return c->weighting == MPPI_WEIGHT_TO_GO ? fused_block_size_to_go(c->sys, p) : fused_block_size(c->sys, p);
 }
 }  // namespace
 
@@ -654,7 +654,7 @@ int mppi_set_weighting(mppi_ctx *c, int mode) {
   if (mode == MPPI_WEIGHT_TO_GO) {
     if (c->sys == MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "the cost-to-go weighting is not built for the learned dynamics");
     if (c->impl == MPPI_IMPL_PLAIN) return c->fail(MPPI_EINVAL, "the plain loop is built for the path weighting only");
-    if (fused_block_size_to_go(c->p) == 0)
+    if (fused_block_size_to_go(c->sys, c->p) == 0)
       return c->fail(MPPI_EINVAL, "horizon too long for the cost-to-go weighting's shared memory");
     if (!c->d_prho) {
       const size_t n = static_cast<size_t>(c->nblk_cap) * c->T;

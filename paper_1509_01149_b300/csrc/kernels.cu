@@ -68,6 +68,19 @@ __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlP
                            part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem);
 }
 
+// car, cost-to-go weighting: the three warp roles with per-step partials
+template <int NS>
+__global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws_to_go(
+    const CtrlParams p, const float *__restrict__ x0, const CtrlState *__restrict__ st, const float *__restrict__ U,
+    float *__restrict__ S_out, float *__restrict__ part_sums, BlockPartial *__restrict__ part,
+    float *__restrict__ part_rho, double *__restrict__ part_eta) {
+  extern __shared__ __align__(16) float smem[];
+  rollout_block_car_ws<NS, true>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+                                 part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem,
+                                 part_rho + static_cast<size_t>(blockIdx.x) * p.T,
+                                 part_eta + static_cast<size_t>(blockIdx.x) * p.T);
+}
+
 // quadrotor: noise / RK4 dynamics / crash decisions and cost in three warp roles, see rollout_quad_ws.cuh
 template <int NS>
 __global__ void __launch_bounds__(3 * NS, 1) k_rollout_quad_ws(const CtrlParams p, const float *__restrict__ x0,
@@ -596,8 +609,10 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
   }
 }
 
-int fused_block_size_to_go(const CtrlParams &p) {
+int fused_block_size_to_go(int sys, const CtrlParams &p) {
   const bool gen = p.gen != nullptr;
+  if (sys == 1 && !gen && p.T <= kWsChunk * kWsMaxChunks && car_ws_smem_bytes(p.T, kWsSamples, true) <= kToGoWsSmemLimit)
+    return kFusedBlockCarWs;
   if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true, gen) <= kFusedSmemLimit)
     return kFusedBlockLarge;
   if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockSmall, false, true, gen) <= kFusedSmemLimit)
@@ -633,7 +648,15 @@ cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const fl
   switch (sys) {
     case 0: return launch_to_go_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     case 4: return launch_to_go_sys<CartPoleVel>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
-    case 1: return launch_to_go_sys<Car>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
+    case 1:
+      if (blk == kFusedBlockCarWs) {
+        const size_t smem = car_ws_smem_bytes(p.T, kWsSamples, true);
+        const int grid = (p.K + kWsSamples - 1) / kWsSamples;
+        k_rollout_car_ws_to_go<kWsSamples><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part,
+                                                                                   part_rho, part_eta);
+        return cudaGetLastError();
+      }
+      return launch_to_go_sys<Car>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     case 2: return launch_to_go_sys<Quad>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     default: return cudaErrorInvalidValue;
   }
@@ -671,6 +694,7 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, true>),
       reinterpret_cast<const void *>(k_rollout_car_ws<kWsSamples>),
+      reinterpret_cast<const void *>(k_rollout_car_ws_to_go<kWsSamples>),
       reinterpret_cast<const void *>(k_rollout_to_go<CartPole, kFusedBlockLarge>),
       reinterpret_cast<const void *>(k_rollout_to_go<CartPole, kFusedBlockSmall>),
       reinterpret_cast<const void *>(k_rollout_to_go<Car, kFusedBlockLarge>),

@@ -17,6 +17,7 @@ constexpr int kMinBlockSamples = kQuadLanesBlock / kQuadLanes;  // fewest sample
 constexpr int kMergeThreads = 256;
 constexpr int kMergeOutputs = 32;       // outputs (i, j) per merge block
 constexpr size_t kFusedSmemLimit = 200 * 1024;
+constexpr size_t kToGoWsSmemLimit = 220 * 1024;  // the car's warp roles with per-step cost storage
 
 // Raise the dynamic shared-memory limit of the kernels that need it (once per
 // device, before any launch or capture).
@@ -51,10 +52,12 @@ bool merge_shift_fusable(const CtrlParams &p);
 cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                       float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
                                       CtrlState *st, cudaStream_t s, unsigned int *u0_ready = nullptr);
-// Cost-to-go weighting (Eq. App_PI per time step): block shape (128 or 64 samples, du and the
-// step costs in shared memory; 0 if they do not fit), the rollout with per-step block partials
+// Cost-to-go weighting (Eq. App_PI per time step): block shape (the car's warp roles,
+// kFusedBlockCarWs, when their shared memory fits kToGoWsSmemLimit; else 128 or 64 samples,
+// du and the step costs in shared memory; 0 if they do not fit), the rollout with per-step
+// block partials
 // (part_rho / part_eta [nblk][T]) and their FP64 merge + update.
-int fused_block_size_to_go(const CtrlParams &p);
+int fused_block_size_to_go(int sys, const CtrlParams &p);
 cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
                                  const float *U, float *S, float *part_sums, BlockPartial *part, float *part_rho,
                                  double *part_eta, cudaStream_t s);

@@ -82,20 +82,24 @@ __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, in
 //   part_sums[i*M+j] = sum_k w_{i,k} du_{i,j,k} (FP32),
 // and `part` gets step 0's (rho, k*, eta) (the total path cost's, for the debug surface).
 // Samples k >= K and non-finite costs count as +inf.
-template <int M, int BLK>
-__device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k, float phi, float *sC,
+//
+// BLK threads run it; the block's NS samples (k0 + column) are sC's and sDu's columns, and
+// threads 0..NS-1 own them (phi: the owner's terminal cost).
+template <int M, int BLK, int NS = BLK>
+__device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k0, float phi, float *sC,
                                                     const float *sDu, float *__restrict__ part_sums,
                                                     float *__restrict__ part_rho, double *__restrict__ part_eta,
                                                     BlockPartial *__restrict__ part) {
-  constexpr int NW = BLK / 32, CPL = BLK / 32;
+  static_assert(NS % 32 == 0 && NS <= BLK, "samples per block");
+  constexpr int NW = BLK / 32, CPL = NS / 32;
   const int T = p.T, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool valid = k < p.K;
-  {
+  if (tid < NS) {
+    const bool valid = k0 + tid < p.K;
     KahanSum s;
     s.s = phi;
     for (int i = T - 1; i >= 0; --i) {
-      s.add(sC[i * BLK + tid]);
-      sC[i * BLK + tid] = valid && isfinite(s.s) ? s.s : INFINITY;
+      s.add(sC[i * NS + tid]);
+      sC[i * NS + tid] = valid && isfinite(s.s) ? s.s : INFINITY;
     }
   }
   __syncthreads();
@@ -105,8 +109,8 @@ __device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k, 
     int mi = INT_MAX;
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
-      sv[c] = sC[i * BLK + lane + 32 * c];
-      const int kk = k - tid + lane + 32 * c;  // sample of that column
+      sv[c] = sC[i * NS + lane + 32 * c];
+      const int kk = k0 + lane + 32 * c;  // sample of that column
       if (sv[c] < mv || (sv[c] == mv && kk < mi)) {
         mv = sv[c];
         mi = isfinite(sv[c]) ? kk : INT_MAX;
@@ -123,7 +127,7 @@ __device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k, 
       const float w = (isfinite(rho) && isfinite(sv[c])) ? expf(-(sv[c] - rho) * p.inv_lambda) : 0.0f;
       e += static_cast<double>(w);
 #pragma unroll
-      for (int j = 0; j < M; ++j) acc[j] = fmaf(w, sDu[(i * M + j) * BLK + lane + 32 * c], acc[j]);
+      for (int j = 0; j < M; ++j) acc[j] = fmaf(w, sDu[(i * M + j) * NS + lane + 32 * c], acc[j]);
     }
     e = warp_sum_d(e);
 #pragma unroll
@@ -396,7 +400,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   asm volatile("griddepcontrol.launch_dependents;");
   if (TOGO) {
     if (k < p.K) S_out[k] = isfinite(S.s) ? S.s : INFINITY;
-    block_partial_to_go<M, BLK>(p, k, phi, sC, sDu, part_sums, part_rho, part_eta, part);
+    block_partial_to_go<M, BLK>(p, k0, phi, sC, sDu, part_sums, part_rho, part_eta, part);
     return;
   }
   block_partial<M, BLK, REGEN>(p, k, ctr, S.s, Lnu, S_out, part_sums, part, sW, sDu);

@@ -19,6 +19,8 @@
 //                      operand of the block sums)
 //   vel [R][C][3][NS]  core -> pose, (vx, vy, r) after each step, a ring of R chunks with
 //                      full/empty mbarriers
+// With TOGO (the per-time-step cost-to-go weighting) the pose role also keeps each step's
+// term of S~ in sC [T][NS] and its terminal cost, and the block forms per-step partials.
 // Every wait is bounded; a thread whose wait runs out stops and its sample's cost is +inf.
 #pragma once
 #include <type_traits>
@@ -34,17 +36,19 @@ constexpr int kWsChunk = 8;       // steps per hand-off
 constexpr int kWsRing = 4;        // chunks in the velocity ring
 constexpr int kWsMaxChunks = 32;  // noise barriers: T <= kWsChunk * kWsMaxChunks
 
-__host__ __device__ inline size_t car_ws_smem_bytes(int T, int ns) {
+__host__ __device__ inline size_t car_ws_smem_bytes(int T, int ns, bool to_go = false) {
   const size_t TM = 2 * static_cast<size_t>(T);
   return sizeof(float) * (2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
-                          static_cast<size_t>(kWsRing) * kWsChunk * 3 * ns);
+                          static_cast<size_t>(kWsRing) * kWsChunk * 3 * ns +
+                          (to_go ? (static_cast<size_t>(T) + 1) * ns : 0));
 }
 
-template <int NS>
+template <int NS, bool TOGO = false>
 __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                                      const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                                      float *__restrict__ part_sums, BlockPartial *__restrict__ part,
-                                                     float *smem) {
+                                                     float *smem, float *__restrict__ part_rho = nullptr,
+                                                     double *__restrict__ part_eta = nullptr) {
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
   constexpr int M = 2, C = kWsChunk, R = kWsRing, NT = kWsRoles * NS;
   __shared__ uint64_t bar_noise[kWsMaxChunks], bar_full[R], bar_empty[R];
@@ -57,6 +61,8 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
   float *sS = sW + NS;      // [NS]  path costs (pose -> owner of the block partial)
   float *sDu = sS + NS;     // [TM][NS] perturbations
   float *sVel = sDu + static_cast<size_t>(TM) * NS;  // [R][C][3][NS]
+  float *sC = sVel + R * C * 3 * NS;                 // TOGO: [T][NS] step terms of S~
+  float *sPhi = sC + static_cast<size_t>(T) * NS;    // TOGO: [NS] terminal costs
 
   __shared__ float sx0[Car::N];  // x0 staged once (it may live in mapped host memory)
   for (int o = tid; o < TM; o += NT) sU[o] = U[o];
@@ -221,7 +227,9 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
         }
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-          S.add(Car::cost_finish(pend, env) + pend_is);
+          const float cv = Car::cost_finish(pend, env) + pend_is;  // the term of step i0 + j - 1
+          S.add(cv);
+          if (TOGO && i0 + j > 0) sC[(i0 + j - 1) * NS + slot] = cv;
           pend = pq[j];
           pend_is = is[j];
         }
@@ -232,7 +240,9 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
           vx = vel[(3 * j) * NS + slot];
           vy = vel[(3 * j + 1) * NS + slot];
           r = vel[(3 * j + 2) * NS + slot];
-          S.add(Car::cost_finish(pend, env) + pend_is);
+          const float cv = Car::cost_finish(pend, env) + pend_is;
+          S.add(cv);
+          if (TOGO && i0 + j > 0) sC[(i0 + j - 1) * NS + slot] = cv;
           const float xq[Car::N] = {X, Y, psi, vx, vy, r, 0.0f};
           pend = Car::cost_issue(xq, aux, env);
           pend_is = is_term(i0 + j);
@@ -240,17 +250,27 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
         tc::mbar_arrive(&bar_empty[c % R]);
       }
     }
+    float phi = INFINITY;
     if (ok) {
-      S.add(Car::cost_finish(pend, env) + pend_is);
+      const float cv = Car::cost_finish(pend, env) + pend_is;
+      S.add(cv);
+      if (TOGO) sC[(T - 1) * NS + slot] = cv;
       const float xq[Car::N] = {X, Y, psi, vx, vy, r, 0.0f};
-      S.add(Car::cost(xq, aux, env));  // phi(x_T) = q(x_T)
+      phi = Car::cost(xq, aux, env);
+      S.add(phi);  // phi(x_T) = q(x_T)
     }
     sS[slot] = ok ? S.s : INFINITY;
+    if (TOGO) sPhi[slot] = phi;
   }
   __syncthreads();
   // the update kernel may start launching now (it waits for this grid's results itself)
   asm volatile("griddepcontrol.launch_dependents;");
   const bool owner = role == 0;
+  if (TOGO) {
+    if (owner && k < p.K) S_out[k] = isfinite(sS[tid]) ? sS[tid] : INFINITY;
+    block_partial_to_go<M, NT, NS>(p, k0, owner ? sPhi[tid] : 0.0f, sC, sDu, part_sums, part_rho, part_eta, part);
+    return;
+  }
   float Lnu_unused[M * M] = {0.0f, 0.0f, 0.0f, 0.0f};
   block_partial<M, NT, false, NS>(p, owner ? k : INT_MAX, ctr, owner ? sS[tid] : INFINITY, Lnu_unused, S_out,
                                   part_sums, part, sW, sDu);
