@@ -14,6 +14,7 @@
 #pragma once
 #include <climits>
 
+#include "merge_common.cuh"
 #include "systems.cuh"
 
 namespace mppi {
@@ -78,7 +79,7 @@ __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, in
 // costs c_i (the terms its path sum added); the block turns them into costs-to-go
 // S_i = c_i + ... + c_{T-1} + phi (compensated, backward, in place), then per step i, one warp
 // per step:
-//   rho_{b,i} = min_k S_i,  eta_{b,i} = sum_k exp(-(S_i - rho_{b,i})/lambda) (FP64),
+//   rho_{b,i} = min_k S_i,  eta_{b,i} = sum_k exp(-(S_i - rho_{b,i})/lambda) (double-FP32 sums),
 //   part_sums[i*M+j] = sum_k w_{i,k} du_{i,j,k} (FP32),
 // and `part` gets step 0's (rho, k*, eta) (the total path cost's, for the debug surface).
 // Samples k >= K and non-finite costs count as +inf.
@@ -118,18 +119,23 @@ __device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k0,
     }
     warp_argmin(mv, mi);
     const float rho = mv;
-    double e = 0.0;
+    // eta in double-FP32 (error-free sums: ~48 bits, as FP64 would give, without B300's slow
+    // FP64 pipe, which a per-step normaliser would otherwise keep busy)
+    DF ed{0.0f, 0.0f};
     float acc[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) acc[j] = 0.0f;
 #pragma unroll
     for (int c = 0; c < CPL; ++c) {
       const float w = (isfinite(rho) && isfinite(sv[c])) ? expf(-(sv[c] - rho) * p.inv_lambda) : 0.0f;
-      e += static_cast<double>(w);
+      df_add(ed, DF{w, 0.0f});
 #pragma unroll
       for (int j = 0; j < M; ++j) acc[j] = fmaf(w, sDu[(i * M + j) * NS + lane + 32 * c], acc[j]);
     }
-    e = warp_sum_d(e);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      df_add(ed, DF{__shfl_xor_sync(0xffffffffu, ed.hi, o), __shfl_xor_sync(0xffffffffu, ed.lo, o)});
+    const double e = static_cast<double>(ed.hi) + static_cast<double>(ed.lo);  // lane 0's is used
 #pragma unroll
     for (int j = 0; j < M; ++j) acc[j] = warp_sum_f(acc[j]);
     if (lane == 0) {
