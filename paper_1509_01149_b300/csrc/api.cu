@@ -114,7 +114,7 @@ struct mppi_ctx {
   int weighting = MPPI_WEIGHT_PATH;
   float *d_gen = nullptr;    // general sampling covariance: [T][2][m][m] (chol, R - lambda Sigma_E^-1)
   float *d_prho = nullptr;   // cost-to-go weighting: per-step block minima [nblk_cap][T]
-  double *d_peta = nullptr;  // and normalisers [nblk_cap][T]
+  DF *d_peta = nullptr;      // and normalisers [nblk_cap][T] (double-FP32 pairs)
   int blk = 0, nblk = 0;
   int nblk_cap = 0;  // block partials the arena holds
   CtrlParams p{};
@@ -193,11 +193,27 @@ int launch_rollout(mppi_ctx *c, const float *x0, cudaStream_t s) {
 int launch_update(mppi_ctx *c, float *u0_out, cudaStream_t s, unsigned int *u0_ready = nullptr) {
   if (c->weighting == MPPI_WEIGHT_TO_GO)
     return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->d_U, u0_out,
-                                      c->d_dU, c->d_dbg, s),
+                                      c->d_dU, c->d_dbg, s, false, nullptr, nullptr, u0_ready),
                    "cost-to-go merge launch");
   return c->cuda(
       launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU, c->d_dbg, s, u0_ready),
       "merge launch");
+}
+
+// The update and Algorithm 1's shift: in one launch (a thread-block cluster) when the outputs
+// fit one, else the update, then the shift kernel.
+int launch_update_shift(mppi_ctx *c, float *u0_out, cudaStream_t s, unsigned int *u0_ready = nullptr) {
+  if (merge_shift_fusable(c->p)) {
+    if (c->weighting == MPPI_WEIGHT_PATH)
+      return c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU,
+                                               c->d_dbg, c->d_uinit, c->d_st, s, u0_ready),
+                     "merge + shift launch");
+    return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->d_U, u0_out,
+                                      c->d_dU, c->d_dbg, s, true, c->d_uinit, c->d_st, u0_ready),
+                   "cost-to-go merge + shift launch");
+  }
+  MPPI_TRY(launch_update(c, u0_out, s, u0_ready));
+  return c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, s), "shift launch");
 }
 
 int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
@@ -233,17 +249,9 @@ int capture_step(mppi_ctx *c, bool shift, cudaGraphExec_t *out) {
   int rc = c->cuda(cudaMemcpyAsync(c->d_st->x0, c->h_x0, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream),
                    "x0 copy");
   if (rc == MPPI_OK) rc = launch_rollout(c, c->d_st->x0, c->stream);
-  if (rc == MPPI_OK) {
-    if (shift && merge_shift_fusable(c->p) && c->weighting == MPPI_WEIGHT_PATH) {
-      rc = c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, c->dh_u0, c->d_dU,
-                                             c->d_dbg, c->d_uinit, c->d_st, c->stream, c->dh_ready),
-                   "merge + shift launch");
-    } else {
-      rc = launch_update(c, c->dh_u0, c->stream, c->dh_ready);
-      if (rc == MPPI_OK && shift)
-        rc = c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
-    }
-  }
+  if (rc == MPPI_OK)
+    rc = shift ? launch_update_shift(c, c->dh_u0, c->stream, c->dh_ready)
+               : launch_update(c, c->dh_u0, c->stream, c->dh_ready);
   const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
   if (rc != MPPI_OK) {
     if (g) cudaGraphDestroy(g);
@@ -659,7 +667,7 @@ int mppi_set_weighting(mppi_ctx *c, int mode) {
     if (!c->d_prho) {
       const size_t n = static_cast<size_t>(c->nblk_cap) * c->T;
       MPPI_TRY(c->cuda(cudaMalloc(&c->d_prho, sizeof(float) * n), "cudaMalloc(step minima)"));
-      MPPI_TRY(c->cuda(cudaMalloc(&c->d_peta, sizeof(double) * n), "cudaMalloc(step normalisers)"));
+      MPPI_TRY(c->cuda(cudaMalloc(&c->d_peta, sizeof(DF) * n), "cudaMalloc(step normalisers)"));
     }
   }
   c->weighting = mode;
@@ -849,9 +857,9 @@ int step_host(mppi_ctx *c, const float *state, float *u0_out, bool shift) {
     if (shift) MPPI_TRY(c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch"));
   } else {
     if (c->graph_dirty) MPPI_TRY(build_graph(c));
-    // the path-weighting merge raises the ready flag; the learned dynamics also need the
-    // kernel's own status, read after the stream finishes
-    const bool flag = c->weighting == MPPI_WEIGHT_PATH && c->sys != MPPI_CAR_MLP;
+    // the merge raises the ready flag; the learned dynamics also need the kernel's own
+    // status, read after the stream finishes
+    const bool flag = c->sys != MPPI_CAR_MLP;
     if (flag) *reinterpret_cast<volatile unsigned int *>(c->h_ready) = 0u;
     MPPI_TRY(c->cuda(cudaGraphLaunch(shift ? c->graph_shift : c->graph, c->stream), "graph launch"));
     if (flag) {
@@ -917,14 +925,7 @@ int mppi_iterate_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
     cudaGraph_t g = nullptr;
     MPPI_TRY(c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
     int rc = launch_rollout(c, d_state, c->stream);
-    if (rc == MPPI_OK && merge_shift_fusable(c->p) && c->weighting == MPPI_WEIGHT_PATH) {
-      rc = c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0, c->d_dU, c->d_dbg,
-                                             c->d_uinit, c->d_st, c->stream),
-                   "merge + shift launch");
-    } else {
-      if (rc == MPPI_OK) rc = launch_update(c, u0, c->stream);
-      if (rc == MPPI_OK) rc = c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
-    }
+    if (rc == MPPI_OK) rc = launch_update_shift(c, u0, c->stream);
     const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
     if (rc != MPPI_OK || rc_end != MPPI_OK) {
       if (g) cudaGraphDestroy(g);

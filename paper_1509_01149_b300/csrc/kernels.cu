@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(BLK) k_rollout_to_go(const CtrlParams p, const
                                                        const CtrlState *__restrict__ st, const float *__restrict__ U,
                                                        float *__restrict__ S_out, float *__restrict__ part_sums,
                                                        BlockPartial *__restrict__ part, float *__restrict__ part_rho,
-                                                       double *__restrict__ part_eta) {
+                                                       DF *__restrict__ part_eta) {
   extern __shared__ __align__(16) float smem[];
   rollout_block<Sys, BLK, false, true, GEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
                                        part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
@@ -73,7 +73,7 @@ template <int NS>
 __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws_to_go(
     const CtrlParams p, const float *__restrict__ x0, const CtrlState *__restrict__ st, const float *__restrict__ U,
     float *__restrict__ S_out, float *__restrict__ part_sums, BlockPartial *__restrict__ part,
-    float *__restrict__ part_rho, double *__restrict__ part_eta) {
+    float *__restrict__ part_rho, DF *__restrict__ part_eta) {
   extern __shared__ __align__(16) float smem[];
   rollout_block_car_ws<NS, true>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
                                  part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem,
@@ -239,62 +239,102 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
 }
 
 // ---------------------------------------------------------------------------
-// FP64 merge of the per-step block partials of the cost-to-go weighting + update of U
+// merge of the per-step block partials of the cost-to-go weighting + update of U (+ the shift)
 // ---------------------------------------------------------------------------
-// One CTA per 32 outputs o = (i, j); lane = output, warps split the blocks.  Per output:
-//   rho_i = min_b rho_{b,i},  s_b = exp(-(rho_{b,i} - rho_i)/lambda),
-//   eta_i = sum_b s_b eta_{b,i},  du_o = sum_b s_b part_b[o] / eta_i   (FP64),
-// U[o] += du_o.  CTA 0 also reports step 0's (rho, k*, eta) from the BlockPartials.
+// One CTA per 32 outputs o = (i, j); lane = output, warp w takes blocks w, w + 8, ... .  Per
+// output:
+//   rho_i = min_b rho_{b,i},  s_b = exp(-(rho_{b,i} - rho_i)/lambda) (FP32),
+//   eta_i = sum_b s_b eta_{b,i},  N_o = sum_b s_b part_b[o]   (double-FP32, warps combined in
+//   order), du_o = N_o / eta_i (FP64), U[o] += du_o.
+// CTA 0 also reports step 0's (rho, k*, eta) from the BlockPartials.  SHIFT: the grid is one
+// thread-block cluster and Algorithm 1's shift follows the update as in k_merge_update.
+template <bool SHIFT>
 __global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, int m, float inv_lambda,
                                                                const float *__restrict__ part_sums,
                                                                const float *__restrict__ part_rho,
-                                                               const double *__restrict__ part_eta,
+                                                               const DF *__restrict__ part_eta,
                                                                const BlockPartial *__restrict__ part,
                                                                float *__restrict__ U, float *__restrict__ u0_out,
                                                                float *__restrict__ dU_dbg,
-                                                               StepDebug *__restrict__ dbg) {
+                                                               StepDebug *__restrict__ dbg,
+                                                               const float *__restrict__ u_init,
+                                                               CtrlState *__restrict__ st,
+                                                               unsigned int *__restrict__ u0_ready) {
   constexpr int NW = kMergeThreads / 32;
   __shared__ float s_r[NW][32];
-  __shared__ double s_e[NW][32], s_a[NW][32];
+  __shared__ DF s_e[NW][32], s_a[NW][32];
   __shared__ float s_rho0[NW];
   __shared__ int s_k0[NW];
+  __shared__ double s_e0[NW];
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int TM = T * m;
   const int o = blockIdx.x * kMergeOutputs + lane;
   const bool live = o < TM;
   const int i = live ? o / m : 0;
+  // loads first: this lane's first kMergePrefetch blocks (b = warp, warp + NW, ...)
+  float pr[kMergePrefetch], ps[kMergePrefetch];
+  DF pe[kMergePrefetch];
+#pragma unroll
+  for (int j = 0; j < kMergePrefetch; ++j) {
+    const int b = warp + j * NW;
+    const bool in = live && b < nblk;
+    pr[j] = in ? part_rho[static_cast<size_t>(b) * T + i] : INFINITY;
+    ps[j] = in ? part_sums[static_cast<size_t>(b) * TM + o] : 0.0f;
+    pe[j] = in ? part_eta[static_cast<size_t>(b) * T + i] : DF{0.0f, 0.0f};
+  }
   float r = INFINITY;
-  for (int b = warp; b < nblk; b += NW) r = fminf(r, part_rho[static_cast<size_t>(b) * T + i]);
+#pragma unroll
+  for (int j = 0; j < kMergePrefetch; ++j) r = fminf(r, pr[j]);
+  for (int b = warp + kMergePrefetch * NW; b < nblk; b += NW) r = fminf(r, part_rho[static_cast<size_t>(b) * T + i]);
   s_r[warp][lane] = r;
   __syncthreads();
   float rho = INFINITY;
 #pragma unroll
   for (int q = 0; q < NW; ++q) rho = fminf(rho, s_r[q][lane]);
-  double e = 0.0, a = 0.0;
+  DF e{0.0f, 0.0f}, a{0.0f, 0.0f};
   if (live && isfinite(rho)) {
-    for (int b = warp; b < nblk; b += NW) {
+#pragma unroll
+    for (int j = 0; j < kMergePrefetch; ++j) {
+      if (warp + j * NW >= nblk) break;
+      const float sc = isfinite(pr[j]) ? expf(-(pr[j] - rho) * inv_lambda) : 0.0f;
+      df_add_prod(e, sc, pe[j].hi);
+      e.lo = __fmaf_rn(sc, pe[j].lo, e.lo);
+      df_add_prod(a, sc, ps[j]);
+    }
+    for (int b = warp + kMergePrefetch * NW; b < nblk; b += NW) {
       const float rb = part_rho[static_cast<size_t>(b) * T + i];
-      const double sc = isfinite(rb) ? static_cast<double>(expf(-(rb - rho) * inv_lambda)) : 0.0;
-      e += sc * part_eta[static_cast<size_t>(b) * T + i];
-      a += sc * static_cast<double>(part_sums[static_cast<size_t>(b) * TM + o]);
+      const float sc = isfinite(rb) ? expf(-(rb - rho) * inv_lambda) : 0.0f;
+      const DF pq = part_eta[static_cast<size_t>(b) * T + i];
+      df_add_prod(e, sc, pq.hi);
+      e.lo = __fmaf_rn(sc, pq.lo, e.lo);
+      df_add_prod(a, sc, part_sums[static_cast<size_t>(b) * TM + o]);
     }
   }
   s_e[warp][lane] = e;
   s_a[warp][lane] = a;
   __syncthreads();
   if (warp == 0 && live) {
-    double et = 0.0, at = 0.0;
+    DF et = s_e[0][lane], at = s_a[0][lane];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) {
-      et += s_e[q][lane];
-      at += s_a[q][lane];
+    for (int q = 1; q < NW; ++q) {
+      df_add(et, s_e[q][lane]);
+      df_add(at, s_a[q][lane]);
     }
-    const double du = et > 0.0 ? at / et : 0.0;
+    const double eta = static_cast<double>(et.hi) + static_cast<double>(et.lo);
+    const double du = eta > 0.0 ? (static_cast<double>(at.hi) + static_cast<double>(at.lo)) / eta : 0.0;
     const float un = U[o] + static_cast<float>(du);
     U[o] = un;
     dU_dbg[o] = static_cast<float>(du);
     if (o < m) u0_out[o] = un;
+  }
+  // u0 is final: raise the host's flag (u0 in host memory before it) ahead of the rest
+  if (u0_ready != nullptr && blockIdx.x == 0 && warp == 0) {
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_system();
+      *reinterpret_cast<volatile unsigned int *>(u0_ready) = 1u;
+    }
   }
   if (blockIdx.x == 0) {  // step 0's scalars for the debug surface
     float v = INFINITY;
@@ -327,16 +367,24 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, 
         e0 += (isfinite(part[b].rho) ? static_cast<double>(expf(-(part[b].rho - vv) * inv_lambda)) : 0.0) *
               part[b].eta;
     e0 = warp_sum_d(e0);
-    if (lane == 0) s_e[warp][0] = e0;
+    if (lane == 0) s_e0[warp] = e0;
     __syncthreads();
     if (tid == 0) {
       double eta = 0.0;
 #pragma unroll
-      for (int q = 0; q < NW; ++q) eta += s_e[q][0];
+      for (int q = 0; q < NW; ++q) eta += s_e0[q];
       dbg->rho = vv;
       dbg->kstar = ii;
       dbg->eta = eta;
     }
+  }
+  if (SHIFT) {
+    cluster_sync_all();  // every CTA's updated U visible to the cluster
+    float sh = 0.0f;
+    if (warp == 0 && live) sh = (o + m < TM) ? U[o + m] : u_init[o - (TM - m)];
+    cluster_sync_all();  // all shifted values read before any is overwritten
+    if (warp == 0 && live) U[o] = sh;
+    if (blockIdx.x == 0 && tid == 0) st->counter += 1u;
   }
 }
 
@@ -622,7 +670,7 @@ int fused_block_size_to_go(int sys, const CtrlParams &p) {
 
 template <class Sys, int BLK>
 static cudaError_t launch_to_go_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
-                                  float *ps, BlockPartial *part, float *prho, double *peta, cudaStream_t s) {
+                                  float *ps, BlockPartial *part, float *prho, DF *peta, cudaStream_t s) {
   const bool gen = p.gen != nullptr;
   const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, false, true, gen);
   const int grid = (p.K + BLK - 1) / BLK;
@@ -636,7 +684,7 @@ static cudaError_t launch_to_go_t(const CtrlParams &p, const float *x0, const Ct
 template <class Sys>
 static cudaError_t launch_to_go_sys(int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
                                     const float *U, float *S, float *ps, BlockPartial *part, float *prho,
-                                    double *peta, cudaStream_t s) {
+                                    DF *peta, cudaStream_t s) {
   if (blk == kFusedBlockLarge) return launch_to_go_t<Sys, kFusedBlockLarge>(p, x0, st, U, S, ps, part, prho, peta, s);
   if (blk == kFusedBlockSmall) return launch_to_go_t<Sys, kFusedBlockSmall>(p, x0, st, U, S, ps, part, prho, peta, s);
   return cudaErrorInvalidValue;
@@ -644,7 +692,7 @@ static cudaError_t launch_to_go_sys(int blk, const CtrlParams &p, const float *x
 
 cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
                                  const float *U, float *S, float *part_sums, BlockPartial *part, float *part_rho,
-                                 double *part_eta, cudaStream_t s) {
+                                 DF *part_eta, cudaStream_t s) {
   switch (sys) {
     case 0: return launch_to_go_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     case 4: return launch_to_go_sys<CartPoleVel>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
@@ -663,12 +711,37 @@ cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const fl
 }
 
 cudaError_t launch_merge_to_go(int nblk, const CtrlParams &p, const float *part_sums, const float *part_rho,
-                               const double *part_eta, const BlockPartial *part, float *U, float *u0_out,
-                               float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
+                               const DF *part_eta, const BlockPartial *part, float *U, float *u0_out,
+                               float *dU_dbg, StepDebug *dbg, cudaStream_t s, bool shift, const float *u_init,
+                               CtrlState *st, unsigned int *u0_ready) {
   const int TM = p.T * p.m;
-  k_merge_to_go<<<(TM + kMergeOutputs - 1) / kMergeOutputs, kMergeThreads, 0, s>>>(
-      nblk, p.T, p.m, p.inv_lambda, part_sums, part_rho, part_eta, part, U, u0_out, dU_dbg, dbg);
-  return cudaGetLastError();
+  const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
+  if (shift && grid > kMergeClusterMax) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kMergeThreads, 1, 1);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[na++].val.programmaticStreamSerializationAllowed = 1;
+  if (shift) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = grid;
+    attr[na].val.clusterDim.y = 1;
+    attr[na++].val.clusterDim.z = 1;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  const int T = p.T, m = p.m;
+  const float il = p.inv_lambda;
+  if (shift)
+    return cudaLaunchKernelEx(&cfg, k_merge_to_go<true>, nblk, T, m, il, part_sums, part_rho, part_eta, part, U,
+                              u0_out, dU_dbg, dbg, u_init, st, u0_ready);
+  const float *no_uinit = nullptr;
+  CtrlState *no_st = nullptr;
+  return cudaLaunchKernelEx(&cfg, k_merge_to_go<false>, nblk, T, m, il, part_sums, part_rho, part_eta, part, U,
+                            u0_out, dU_dbg, dbg, no_uinit, no_st, u0_ready);
 }
 
 cudaError_t prepare_kernels() {

@@ -1,6 +1,7 @@
 // Host-side launchers of the MPPI kernels (implemented in kernels.cu).
 #pragma once
 #include <cuda_runtime.h>
+#include "merge_common.cuh"
 #include "mppi_device.cuh"
 
 namespace mppi {
@@ -60,10 +61,15 @@ cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float
 int fused_block_size_to_go(int sys, const CtrlParams &p);
 cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
                                  const float *U, float *S, float *part_sums, BlockPartial *part, float *part_rho,
-                                 double *part_eta, cudaStream_t s);
+                                 DF *part_eta, cudaStream_t s);
+// The merge of the per-step partials and the update; with `shift` (T*m <= 32 kMergeClusterMax)
+// also Algorithm 1's shift in the same launch (one thread-block cluster).  u0_ready as for
+// launch_merge_update.
 cudaError_t launch_merge_to_go(int nblk, const CtrlParams &p, const float *part_sums, const float *part_rho,
-                               const double *part_eta, const BlockPartial *part, float *U, float *u0_out,
-                               float *dU_dbg, StepDebug *dbg, cudaStream_t s);
+                               const DF *part_eta, const BlockPartial *part, float *U, float *u0_out,
+                               float *dU_dbg, StepDebug *dbg, cudaStream_t s, bool shift = false,
+                               const float *u_init = nullptr, CtrlState *st = nullptr,
+                               unsigned int *u0_ready = nullptr);
 // Shift of Algorithm 1 and iteration counter increment.
 cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s);
 

@@ -89,7 +89,7 @@ __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, in
 template <int M, int BLK, int NS = BLK>
 __device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k0, float phi, float *sC,
                                                     const float *sDu, float *__restrict__ part_sums,
-                                                    float *__restrict__ part_rho, double *__restrict__ part_eta,
+                                                    float *__restrict__ part_rho, DF *__restrict__ part_eta,
                                                     BlockPartial *__restrict__ part) {
   static_assert(NS % 32 == 0 && NS <= BLK, "samples per block");
   constexpr int NW = BLK / 32, CPL = NS / 32;
@@ -142,7 +142,7 @@ __device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k0,
 #pragma unroll
       for (int j = 0; j < M; ++j) part_sums[i * M + j] = acc[j];
       part_rho[i] = rho;
-      part_eta[i] = e;
+      part_eta[i] = ed;
       if (i == 0) {
         BlockPartial bp;
         bp.eta = e;
@@ -293,7 +293,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
                                               const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                               float *__restrict__ part_sums, BlockPartial *__restrict__ part,
                                               float *smem, float *du_ext = nullptr, float *part_rho = nullptr,
-                                              double *part_eta = nullptr) {
+                                              DF *part_eta = nullptr) {
   static_assert(!(TOGO && REGEN), "the cost-to-go weighting keeps du in shared memory");
   static_assert(!(GEN && REGEN), "the general sampling covariance keeps du in shared memory");
   constexpr int M = Sys::M, N = Sys::N, SPB = 4 / M;

@@ -48,7 +48,7 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
                                                      const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                                      float *__restrict__ part_sums, BlockPartial *__restrict__ part,
                                                      float *smem, float *__restrict__ part_rho = nullptr,
-                                                     double *__restrict__ part_eta = nullptr) {
+                                                     DF *__restrict__ part_eta = nullptr) {
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
   constexpr int M = 2, C = kWsChunk, R = kWsRing, NT = kWsRoles * NS;
   __shared__ uint64_t bar_noise[kWsMaxChunks], bar_full[R], bar_empty[R];

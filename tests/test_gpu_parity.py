@@ -315,6 +315,26 @@ def test_cost_to_go_iteration(N, system, K, T, lam):
                                                o.rho[i], lamf, bound[i]), (i, np.max(err[i] / bound[i]))
 
 
+@pytest.mark.parametrize("system,T", [(W.CAR, 100), (W.QUAD, 60), (W.CARTPOLE, 300)])
+def test_cost_to_go_step_shift_equals_step_then_shift(N, system, T):
+    """With the cost-to-go weighting, mppi_step_shift runs the per-step merge and the shift in
+    one thread-block cluster when T*m <= 256 (else the merge, then the shift kernel); mppi_step
+    then mppi_shift gives the same u0, controls and counter bit for bit, over three iterations."""
+    cfg = W.config(system, K=2048, T=T)
+    a, b = P.make_controller(cfg), P.make_controller(cfg)
+    for c in (a, b):
+        c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    x = np.asarray(cfg["x0"], np.float32)
+    for it in range(3):
+        xs = x + np.float32(0.01 * it)
+        ua = a.step(xs)
+        a.shift()
+        ub = b.step_shift(xs)
+        assert np.array_equal(ua, ub)
+    assert np.array_equal(a.get_controls(), b.get_controls())
+    assert a.get_iteration() == b.get_iteration() == 3
+
+
 def test_cost_to_go_with_one_step_equals_the_path_weighting(N):
     cfg = W.config(W.CAR, K=3000, T=1, lam=50.0)
     a = P.make_controller(cfg)
