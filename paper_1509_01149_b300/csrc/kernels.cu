@@ -569,9 +569,10 @@ size_t fused_smem_bytes(const CtrlParams &p, int blk) {
   if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples);
   if (blk == kFusedBlockQuadLanes) return quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
   if (blk == kFusedBlockQuadWs)
-    return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p.grid_nx, p.grid_ny, p.grid_nidx));
+    return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p));
   const bool regen = blk == kFusedBlockRegen;
-  return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen, false, p.gen != nullptr);
+  return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen, false, p.gen != nullptr,
+                            quad_grid_bytes(p));
 }
 
 int fused_block_size(int sys, const CtrlParams &p) {
@@ -602,7 +603,7 @@ template <class Sys, int BLK, bool REGEN>
 static cudaError_t launch_fused_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                   float *ps, BlockPartial *part, cudaStream_t s) {
   const bool gen = p.gen != nullptr;
-  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, REGEN, false, gen);
+  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, REGEN, false, gen, quad_grid_bytes(p));
   const int grid = (p.K + BLK - 1) / BLK;
   if (gen) {
     if (REGEN) return cudaErrorInvalidValue;
@@ -661,9 +662,9 @@ int fused_block_size_to_go(int sys, const CtrlParams &p) {
   const bool gen = p.gen != nullptr;
   if (sys == 1 && !gen && p.T <= kWsChunk * kWsMaxChunks && car_ws_smem_bytes(p.T, kWsSamples, true) <= kToGoWsSmemLimit)
     return kFusedBlockCarWs;
-  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true, gen) <= kFusedSmemLimit)
+  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true, gen, quad_grid_bytes(p)) <= kFusedSmemLimit)
     return kFusedBlockLarge;
-  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockSmall, false, true, gen) <= kFusedSmemLimit)
+  if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockSmall, false, true, gen, quad_grid_bytes(p)) <= kFusedSmemLimit)
     return kFusedBlockSmall;
   return 0;
 }
@@ -672,7 +673,7 @@ template <class Sys, int BLK>
 static cudaError_t launch_to_go_t(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                   float *ps, BlockPartial *part, float *prho, DF *peta, cudaStream_t s) {
   const bool gen = p.gen != nullptr;
-  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, false, true, gen);
+  const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, false, true, gen, quad_grid_bytes(p));
   const int grid = (p.K + BLK - 1) / BLK;
   if (gen)
     k_rollout_to_go<Sys, BLK, true><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part, prho, peta);

@@ -31,7 +31,10 @@ __device__ __forceinline__ void scale_noise(const float *Lnu, const float *eps, 
   }
 }
 
-__device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs, int packed = 0) {
+// grid_off / grid_idx: the nearest-cylinder grid staged in shared memory (or null: none)
+__device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs, int packed = 0,
+                                        const unsigned short *grid_off = nullptr,
+                                        const unsigned char *grid_idx = nullptr) {
   Env e;
   e.obs_packed = packed;
   e.map = p.map;
@@ -45,6 +48,13 @@ __device__ __forceinline__ Env make_env(const CtrlParams &p, const float *obs, i
   e.gx = p.goal[0];
   e.gy = p.goal[1];
   e.gz = p.goal[2];
+  e.grid_off = grid_off;
+  e.grid_idx = grid_idx;
+  e.grid_nx = grid_off ? p.grid_nx : 0;
+  e.grid_ny = p.grid_ny;
+  e.grid_ox = p.grid_ox;
+  e.grid_oy = p.grid_oy;
+  e.grid_inv_h = p.grid_inv_h;
   return e;
 }
 
@@ -65,13 +75,25 @@ __device__ __forceinline__ float transpose_reduce32(float v[32]) {
   return v[0];
 }
 
+// Bytes of the quadrotor's nearest-cylinder grid in shared memory (offsets, then indices,
+// 16-byte padded; 0 without a grid).
+__host__ __device__ inline size_t quad_grid_bytes(int nx, int ny, int nidx) {
+  if (nx <= 0) return 0;
+  return (sizeof(unsigned short) * (static_cast<size_t>(nx) * ny + 1) + static_cast<size_t>(nidx) + 15) &
+         ~static_cast<size_t>(15);
+}
+__host__ __device__ inline size_t quad_grid_bytes(const CtrlParams &p) {
+  return quad_grid_bytes(p.grid_nx, p.grid_ny, p.grid_nidx);
+}
+
 // Shared-memory bytes of rollout_block (dynamic part) for T*M outputs; to_go adds the
-// per-step costs [T][blk] of the cost-to-go weighting.
+// per-step costs [T][blk] of the cost-to-go weighting, grid_bytes the nearest-cylinder grid.
 __host__ __device__ inline size_t rollout_smem_bytes(int T, int M, int n_obs, int blk, bool regen, bool to_go = false,
-                                                   bool gen = false) {
+                                                   bool gen = false, size_t grid_bytes = 0) {
   const size_t TM = static_cast<size_t>(T) * M;
   return 16 + sizeof(float) * (2 * TM + T + 4 * static_cast<size_t>(n_obs) + blk + (regen ? 0 : TM * blk) +
-                               (to_go ? static_cast<size_t>(T) * blk : 0) + (gen ? 2 * TM * M : 0));
+                               (to_go ? static_cast<size_t>(T) * blk : 0) + (gen ? 2 * TM * M : 0)) +
+         (grid_bytes ? grid_bytes + 16 : 0);
 }
 
 // Per-time-step block partials of the cost-to-go weighting (Eq. App_PI read literally: u_i
@@ -307,6 +329,12 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   float *sDu = du_ext ? du_ext : sW + BLK;  // STORE only: [TM][BLK] perturbations of this block
   float *sC = sW + BLK + static_cast<size_t>(TM) * BLK;  // TOGO only: [T][BLK] step costs
   float *sGen = sC + (TOGO ? static_cast<size_t>(T) * BLK : 0);  // GEN only: [T][2][M][M]
+  // the nearest-cylinder grid follows the arrays in use (du in shared memory or not)
+  float *tail = (REGEN || du_ext) ? sW + BLK : sGen + (GEN ? 2 * TM * M : 0);
+  unsigned short *sOff = reinterpret_cast<unsigned short *>((reinterpret_cast<uintptr_t>(tail) + 15) & ~uintptr_t(15));
+  const int ncell = p.grid_nx * p.grid_ny;
+  unsigned char *sIdx = reinterpret_cast<unsigned char *>(sOff + (ncell + 1));
+  const bool grid = p.grid_nx > 0 && p.n_obs > 0;
 
   __shared__ float sx0[N];  // x0 staged once per block (it may live in mapped host memory)
   for (int o = tid; o < TM; o += BLK) sU[o] = U[o];
@@ -314,6 +342,10 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   if (tid < N) sx0[tid] = x0[tid];
   if (GEN)
     for (int o = tid; o < 2 * TM * M; o += BLK) sGen[o] = p.gen[o];
+  if (grid) {
+    for (int o = tid; o <= ncell; o += BLK) sOff[o] = p.grid_off[o];
+    for (int o = tid; o < p.grid_nidx; o += BLK) sIdx[o] = p.grid_idx[o];
+  }
   __syncthreads();
   for (int i = tid; i < T; i += BLK) {
     float h = 0.0f;
@@ -329,7 +361,7 @@ __device__ __forceinline__ void rollout_block(const CtrlParams &p, const float *
   }
   __syncthreads();
 
-  const Env env = make_env(p, sObs, 1);
+  const Env env = make_env(p, sObs, 1, grid ? sOff : nullptr, grid ? sIdx : nullptr);
   const int k = k0 + tid;
   float Lnu[M * M], R[M * M];
 #pragma unroll

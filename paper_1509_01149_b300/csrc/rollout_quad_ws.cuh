@@ -36,53 +36,11 @@ constexpr int kQwsRing = 2;      // chunks in the state ring
 constexpr int kQwsMaxChunks = 32;
 constexpr int kQwsPass = 8;      // values per step handed from the dynamics to the cost role
 
-// bytes of the nearest-cylinder grid in shared memory (offsets, then indices, 16-byte padded)
-__host__ __device__ inline size_t quad_grid_bytes(int nx, int ny, int nidx) {
-  if (nx <= 0) return 0;
-  return (sizeof(unsigned short) * (static_cast<size_t>(nx) * ny + 1) + static_cast<size_t>(nidx) + 15) &
-         ~static_cast<size_t>(15);
-}
-
 __host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns, size_t grid_bytes) {
   const size_t TM = 4 * static_cast<size_t>(T);
   return sizeof(float) * (4 * static_cast<size_t>(n_obs) + 2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
                           static_cast<size_t>(kQwsRing) * kQwsChunk * kQwsPass * ns) +
          grid_bytes;
-}
-
-// Nearest cylinder surface: over the candidate list of the point's grid cell when the point
-// is inside the grid, else over every cylinder (the same float either way, forest_grid.h).
-// The first kQwsWindow entries of the list are read as one unrolled window whose positions
-// past the list's end repeat its last entry (a repeat leaves a minimum unchanged), so their
-// loads are independent and issue together; longer lists finish in a loop.
-constexpr int kQwsWindow = 8;
-__device__ __forceinline__ float quad_nearest(const Env &env, const CtrlParams &p, const unsigned short *sOff,
-                                              const unsigned char *sIdx, float px, float py) {
-  const float gx = (px - p.grid_ox) * p.grid_inv_h, gy = (py - p.grid_oy) * p.grid_inv_h;
-  if (gx >= 0.0f && gy >= 0.0f && gx < static_cast<float>(p.grid_nx) && gy < static_cast<float>(p.grid_ny)) {
-    const int cell = static_cast<int>(gy) * p.grid_nx + static_cast<int>(gx);
-    const float4 *o4 = reinterpret_cast<const float4 *>(env.obs);
-    const int t0 = sOff[cell], t1 = sOff[cell + 1];  // t1 > t0: every list holds a cylinder
-    float dw[kQwsWindow];
-#pragma unroll
-    for (int q = 0; q < kQwsWindow; ++q) {
-      const float4 c = o4[sIdx[min(t0 + q, t1 - 1)]];
-      const float ax = px - c.x, ay = py - c.y;
-      dw[q] = Quad::fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z;
-    }
-#pragma unroll
-    for (int w = kQwsWindow / 2; w > 0; w >>= 1)
-#pragma unroll
-      for (int q = 0; q < w; ++q) dw[q] = fminf(dw[q], dw[q + w]);
-    float d = dw[0];
-    for (int t = t0 + kQwsWindow; t < t1; ++t) {
-      const float4 c = o4[sIdx[t]];
-      const float ax = px - c.x, ay = py - c.y;
-      d = fminf(d, Quad::fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z);
-    }
-    return d;
-  }
-  return Quad::obstacle_distance(env, px, py);
 }
 
 template <int NS>
@@ -200,7 +158,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
   } else {
     // ---- cost: crash decisions, q(x), IS terms, S~ ------------------------------------------
     const int slot = tid - 2 * NS;
-    const Env env = make_env(p, sObs, 1);
+    const Env env = make_env(p, sObs, 1, p.grid_nx > 0 ? sOff : nullptr, sIdx);
     float Rm[M * M];
 #pragma unroll
     for (int a = 0; a < M * M; ++a) Rm[a] = p.R[a];
@@ -209,7 +167,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
     for (int a = 0; a < N; ++a) x[a] = sx0[a];
     Quad::Aux aux;
     aux.crashed = false;
-    aux.d = quad_nearest(env, p, sOff, sIdx, x[0], x[1]);
+    aux.d = Quad::nearest(env, x[0], x[1]);
     KahanSum S;
     for (int c = 0; c < nch; ++c) {
       // the noise wait is already satisfied (the dynamics waited on it before publishing
@@ -239,7 +197,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
         // the sequential step's crash test on the new state (a crashed sample keeps its state
         // whatever the test says, and the states handed over after its crash can be far
         // outside the forest, so it skips the search)
-        float d = aux.crashed ? 0.0f : quad_nearest(env, p, sOff, sIdx, px, py);
+        float d = aux.crashed ? 0.0f : Quad::nearest(env, px, py);
         const bool finite = isfinite(px);
         if (!finite) d = -1.0f;
         const bool hit = !finite || d < 0.0f || pz < 0.0f || (Quad::pitch_limit - fabsf(pitch)) <= 0.0f;

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "../../include/mppi.h"
+#include "forest_grid.h"
 #include "kernels.cuh"
 #include "rollout_body.cuh"
 
@@ -294,7 +295,9 @@ struct EnvSlot {
   uint32_t kind = 0;
   mppi_env_map map{};
   mppi_env_forest forest{};
-  float *ptr = nullptr;
+  float *ptr = nullptr;  // map, or cylinders followed by the nearest-cylinder grid (offsets, indices)
+  int grid_nx = 0, grid_ny = 0, grid_nidx = 0;
+  float grid_ox = 0.0f, grid_oy = 0.0f, grid_inv_h = 0.0f;
 };
 
 constexpr int kMaxEnvs = 16;
@@ -323,6 +326,7 @@ struct mppi_server {
   float *d_slab = nullptr;
   size_t slab_cap = 0;
   int max_tm = 1, max_nblk = 1, max_nobs = 0;
+  size_t max_grid = 0;  // largest nearest-cylinder grid of an admitted slot (bytes in shared memory)
 
   int blk = 128, ctas_per_sm = 0, variant = 1;
   cudaGraph_t graph = nullptr;
@@ -366,7 +370,9 @@ size_t slot_bytes(int K, int T, int m) {
          round256(sizeof(float) * nb * TM) + round256(sizeof(BlockPartial) * nb);
 }
 
-size_t rollout_smem(const mppi_server *s, int blk) { return rollout_smem_bytes(s->max_tm, 1, s->max_nobs, blk, true); }
+size_t rollout_smem(const mppi_server *s, int blk) {
+  return rollout_smem_bytes(s->max_tm, 1, s->max_nobs, blk, true, false, false, s->max_grid);
+}
 size_t merge_smem(const mppi_server *s) { return sizeof(double) * s->max_nblk + sizeof(float) * s->max_tm; }
 
 // Rollout kernel variants the autotuner chooses from: block size and the register cap
@@ -645,11 +651,28 @@ int mppi_server_set_env(mppi_server *s, int env_id, const void *blob, size_t byt
   } else {
     return s->fail(MPPI_EINVAL, "unknown env kind");
   }
+  const char *src = static_cast<const char *>(blob) + (e.kind == MPPI_ENV_MAP ? sizeof e.map : sizeof e.forest);
+  std::vector<char> forest;  // cylinders + grid
+  ForestGrid grid;
+  if (e.kind == MPPI_ENV_FOREST &&
+      build_forest_grid(reinterpret_cast<const float *>(src), e.forest.n_obstacles, grid)) {
+    e.grid_nx = grid.nx;
+    e.grid_ny = grid.ny;
+    e.grid_nidx = static_cast<int>(grid.idx.size());
+    e.grid_ox = grid.ox;
+    e.grid_oy = grid.oy;
+    e.grid_inv_h = grid.inv_h;
+    forest.assign(src, src + payload);
+    forest.resize(payload + grid.bytes());
+    std::memcpy(forest.data() + payload, grid.off.data(), sizeof(uint16_t) * grid.off.size());
+    std::memcpy(forest.data() + payload + sizeof(uint16_t) * grid.off.size(), grid.idx.data(), grid.idx.size());
+    src = forest.data();
+    payload = forest.size();
+  }
   SRV_TRY(s->cuda(cudaStreamSynchronize(s->stream), "sync"));
   if (s->envs[env_id].ptr) cudaFree(s->envs[env_id].ptr);
   s->envs[env_id].ptr = nullptr;
   SRV_TRY(s->cuda(cudaMalloc(&e.ptr, std::max<size_t>(payload, 16)), "cudaMalloc(env)"));
-  const char *src = static_cast<const char *>(blob) + (e.kind == MPPI_ENV_MAP ? sizeof e.map : sizeof e.forest);
   if (payload) SRV_TRY(s->cuda(cudaMemcpy(e.ptr, src, payload, cudaMemcpyHostToDevice), "env copy"));
   e.set = true;
   s->envs[env_id] = e;
@@ -717,6 +740,16 @@ int mppi_server_admit(mppi_server *s, const mppi_slot_config *c, int *slot_out) 
       p.obs = e.ptr;
       p.n_obs = e.forest.n_obstacles;
       for (int i = 0; i < 3; ++i) p.goal[i] = e.forest.goal[i];
+      p.grid_nx = e.grid_nx;
+      p.grid_ny = e.grid_ny;
+      p.grid_nidx = e.grid_nidx;
+      p.grid_ox = e.grid_ox;
+      p.grid_oy = e.grid_oy;
+      p.grid_inv_h = e.grid_inv_h;
+      if (e.grid_nx > 0) {
+        p.grid_off = reinterpret_cast<const unsigned short *>(e.ptr + 3 * static_cast<size_t>(p.n_obs));
+        p.grid_idx = reinterpret_cast<const unsigned char *>(p.grid_off + (static_cast<size_t>(e.grid_nx) * e.grid_ny + 1));
+      }
     }
   }
   int slot = -1;
@@ -772,10 +805,12 @@ int mppi_server_admit(mppi_server *s, const mppi_slot_config *c, int *slot_out) 
   }
   // shapes the persistent kernels' shared memory must cover
   const int nblk_max = (c->K + kMaxBlockShape - 1) / kMaxBlockShape;
-  if (static_cast<int>(TM) > s->max_tm || nblk_max > s->max_nblk || p.n_obs > s->max_nobs) {
+  if (static_cast<int>(TM) > s->max_tm || nblk_max > s->max_nblk || p.n_obs > s->max_nobs ||
+      quad_grid_bytes(p) > s->max_grid) {
     s->max_tm = std::max(s->max_tm, static_cast<int>(TM));
     s->max_nblk = std::max(s->max_nblk, nblk_max);
     s->max_nobs = std::max(s->max_nobs, p.n_obs);
+    s->max_grid = std::max(s->max_grid, quad_grid_bytes(p));
     s->graph_dirty = true;
   }
   *slot_out = slot;

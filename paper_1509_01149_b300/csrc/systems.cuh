@@ -32,6 +32,12 @@ struct Env {
   int n_obs;
   int obs_packed;
   float gx, gy, gz;
+  // nearest-cylinder grid in shared memory (with obs_packed; grid_nx == 0: none): per cell the
+  // list of cylinders that can be nearest to a point of the cell (see forest_grid.h)
+  const unsigned short *grid_off;  // [grid_nx * grid_ny + 1] list starts in grid_idx
+  const unsigned char *grid_idx;
+  int grid_nx, grid_ny;
+  float grid_ox, grid_oy, grid_inv_h;
 };
 
 // ---------------------------------------------------------------------------
@@ -364,9 +370,44 @@ struct Quad {
     return d;
   }
 
+  // Nearest cylinder surface: over the candidate list of the point's grid cell when there is
+  // a grid and the point is inside it, else over every cylinder (the same float either way).
+  // The first kNearestWindow entries of a list are read as one unrolled window whose
+  // positions past the list's end repeat its last entry (a repeat leaves a minimum unchanged),
+  // so their loads are independent and issue together; longer lists finish in a loop.
+  static constexpr int kNearestWindow = 8;
+  __device__ __forceinline__ static float nearest(const Env &e, float px, float py) {
+    const float gx = (px - e.grid_ox) * e.grid_inv_h, gy = (py - e.grid_oy) * e.grid_inv_h;
+    if (e.grid_nx > 0 && gx >= 0.0f && gy >= 0.0f && gx < static_cast<float>(e.grid_nx) &&
+        gy < static_cast<float>(e.grid_ny)) {
+      const int cell = static_cast<int>(gy) * e.grid_nx + static_cast<int>(gx);
+      const float4 *o4 = reinterpret_cast<const float4 *>(e.obs);
+      const int t0 = e.grid_off[cell], t1 = e.grid_off[cell + 1];  // t1 > t0: every list holds one
+      float dw[kNearestWindow];
+#pragma unroll
+      for (int q = 0; q < kNearestWindow; ++q) {
+        const float4 c = o4[e.grid_idx[min(t0 + q, t1 - 1)]];
+        const float ax = px - c.x, ay = py - c.y;
+        dw[q] = fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z;
+      }
+#pragma unroll
+      for (int w = kNearestWindow / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q) dw[q] = fminf(dw[q], dw[q + w]);
+      float d = dw[0];
+      for (int t = t0 + kNearestWindow; t < t1; ++t) {
+        const float4 c = o4[e.grid_idx[t]];
+        const float ax = px - c.x, ay = py - c.y;
+        d = fminf(d, fast_sqrt(fmaf(ax, ax, ay * ay)) - c.z);
+      }
+      return d;
+    }
+    return obstacle_distance(e, px, py);
+  }
+
   __device__ __forceinline__ static void init(const float *x, Aux &a, const Env &e) {
     a.crashed = false;
-    a.d = obstacle_distance(e, x[0], x[1]);
+    a.d = nearest(e, x[0], x[1]);
   }
 
   __device__ __forceinline__ static void deriv(const float x[N], const float f[M], float d[N]) {
@@ -423,7 +464,7 @@ struct Quad {
     if (a.crashed) return;
     float y[N];
     const bool finite = rk4(x, f, dt, y);
-    const float d = finite ? obstacle_distance(e, y[0], y[1]) : -1.0f;
+    const float d = finite ? nearest(e, y[0], y[1]) : -1.0f;
     const bool hit = !finite || d < 0.0f || y[2] < 0.0f || (pitch_limit - fabsf(y[7])) <= 0.0f;
     if (hit) {
       a.crashed = true;  // state stays at the last valid state
