@@ -5,7 +5,7 @@
 // x_{i+1} = F(x_i, u_i + du_i) -> S~ += q(x_{i+1}) + IS running cost (Kahan FP32);
 // then S~ += phi(x_T).  The block then forms its softmax partial:
 //   rho_b = min_k S~_k (lowest k on ties), w_k = exp(-(S~_k - rho_b)/lambda),
-//   eta_b = sum_k w_k (FP64), part_b[i][j] = sum_k w_k du_{i,j,k} (FP32 block sum).
+//   eta_b = sum_k w_k (double-FP32), part_b[i][j] = sum_k w_k du_{i,j,k} (FP32 block sum).
 // Two ways to get du back for the block sums:
 //   STORE: du kept in shared memory during the rollout ([T*M][BLK] floats);
 //   REGEN: du regenerated from the counter-based generator after the rollout (no
@@ -178,7 +178,7 @@ __device__ __forceinline__ void block_partial_to_go(const CtrlParams &p, int k0,
 
 // The block's softmax partial from each thread's path cost Sk_raw (sample k):
 //   rho_b = min_k S~_k (lowest k on ties), w_k = exp(-(S~_k - rho_b)/lambda),
-//   eta_b = sum_k w_k (FP64), part_sums[i*M+j] = sum_k w_k du_{i,j,k} (FP32)
+//   eta_b = sum_k w_k (double-FP32), part_sums[i*M+j] = sum_k w_k du_{i,j,k} (FP32)
 // with du from shared memory (STORE: sDu [T*M][BLK]) or regenerated (REGEN).
 // Non-finite costs and samples k >= K count as +inf (weight 0); k == INT_MAX marks a thread
 // that owns no sample (it only takes part in the block reduction).  BLK is the thread count;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
   constexpr int SPB = 4 / M, NW = BLK / 32;
   __shared__ float s_min[NW];
   __shared__ int s_idx[NW];
-  __shared__ double s_eta[NW];
+  __shared__ DF s_eta[NW];
   __shared__ float s_red[NW][32];
   const int TM = p.T * M, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool valid = k < p.K;
@@ -222,8 +222,16 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
   __syncthreads();
   const float rho_b = s_min[0];
   const float w = (isfinite(rho_b) && isfinite(Sk)) ? expf(-(Sk - rho_b) * p.inv_lambda) : 0.0f;
-  // (warps whose threads own no sample skip the FP64 shuffles)
-  const double e = __any_sync(0xffffffffu, k != INT_MAX) ? warp_sum_d(static_cast<double>(w)) : 0.0;
+  // eta_b in double-FP32 (error-free sums, ~48 bits) rather than on B300's slow FP64 pipe;
+  // warps whose threads own no sample skip the shuffles
+  DF e{w, 0.0f};
+  if (__any_sync(0xffffffffu, k != INT_MAX)) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      df_add(e, DF{__shfl_xor_sync(0xffffffffu, e.hi, o), __shfl_xor_sync(0xffffffffu, e.lo, o)});
+  } else {
+    e = DF{0.0f, 0.0f};
+  }
   if (lane == 0) s_eta[warp] = e;
 
   if (!REGEN) {
@@ -286,11 +294,11 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
   }
   __syncthreads();
   if (tid == 0) {
-    double eta_b = 0.0;
+    DF eb = s_eta[0];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) eta_b += s_eta[q];
+    for (int q = 1; q < NW; ++q) df_add(eb, s_eta[q]);
     BlockPartial bp;
-    bp.eta = eta_b;
+    bp.eta = static_cast<double>(eb.hi) + static_cast<double>(eb.lo);
     bp.rho = rho_b;
     bp.kstar = s_idx[0];
     *part = bp;
