@@ -303,17 +303,20 @@ def run_serving(levels, n_ticks, seed=0, mix=None):
     return out
 
 
-SYSTEM_CONFIGS = (("cart-pole", W.CARTPOLE, 1000, 100, 0), ("car", W.CAR, 4096, 100, 0),
-                  ("car", W.CAR, 16384, 100, 0), ("quadrotor", W.QUAD, 8192, 150, 0),
-                  ("car, cost-to-go weighting", W.CAR, 16384, 100, 1),
-                  ("quadrotor, cost-to-go weighting", W.QUAD, 8192, 150, 1))
+# (name, system, K, T, cost-to-go weighting, general per-step sampling covariance)
+SYSTEM_CONFIGS = (("cart-pole", W.CARTPOLE, 1000, 100, 0, 0), ("car", W.CAR, 4096, 100, 0, 0),
+                  ("car", W.CAR, 16384, 100, 0, 0), ("quadrotor", W.QUAD, 8192, 150, 0, 0),
+                  ("car, cost-to-go weighting", W.CAR, 16384, 100, 1, 0),
+                  ("quadrotor, cost-to-go weighting", W.QUAD, 8192, 150, 1, 0),
+                  ("car, general sampling covariance", W.CAR, 16384, 100, 0, 1),
+                  ("quadrotor, general sampling covariance", W.QUAD, 8192, 150, 0, 1))
 
 
 def run_systems(steps=200, warmup=10):
     """Device-resident receding-horizon iterations (mppi_iterate_async: one graph per
     iteration) of each workload configuration: cart-pole K=1000 T=100, car K=4096 and 16384
     T=100, quadrotor K=8192 T=150, and the car and quadrotor with the per-time-step
-    cost-to-go weighting.  Per configuration: rollout-steps/s, iteration time and the
+    cost-to-go weighting and with a general per-step sampling covariance.  Per configuration: rollout-steps/s, iteration time and the
     rollout kernel's algorithmic FP32 rate against the FP32 peak (rollout timed alone)."""
     import torch
 
@@ -321,12 +324,14 @@ def run_systems(steps=200, warmup=10):
     out = []
     s = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for name, system, K, T, to_go in SYSTEM_CONFIGS:
+    for name, system, K, T, to_go, gen in SYSTEM_CONFIGS:
         cfg = W.config(system, K=K, T=T)
         c = N.Controller(system, K, T, cfg["dt"], cfg["nu"], cfg["lam"], cfg["Sigma"], cfg["R"])
         c.set_stream(s.cuda_stream)
         if to_go:
             c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+        if gen:
+            c.set_sampling_covariance(W.sampling_covariances(cfg))
         if system == W.CAR:
             c.set_cost_map(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL)
         elif system == W.QUAD:

@@ -57,25 +57,27 @@ __global__ void __launch_bounds__(BLK) k_rollout_to_go(const CtrlParams p, const
 }
 
 // car: three threads per sample (velocity recurrence / noise / pose and cost), see rollout_ws.cuh
-template <int NS>
+// (GEN: a general sampling covariance per step)
+template <int NS, bool GEN = false>
 __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlParams p, const float *__restrict__ x0,
                                                               const CtrlState *__restrict__ st,
                                                               const float *__restrict__ U, float *__restrict__ S_out,
                                                               float *__restrict__ part_sums,
                                                               BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block_car_ws<NS>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
-                           part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem);
+  rollout_block_car_ws<NS, false, GEN>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+                                       part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x,
+                                       smem);
 }
 
 // car, cost-to-go weighting: the three warp roles with per-step partials
-template <int NS>
+template <int NS, bool GEN = false>
 __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws_to_go(
     const CtrlParams p, const float *__restrict__ x0, const CtrlState *__restrict__ st, const float *__restrict__ U,
     float *__restrict__ S_out, float *__restrict__ part_sums, BlockPartial *__restrict__ part,
     float *__restrict__ part_rho, DF *__restrict__ part_eta) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block_car_ws<NS, true>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+  rollout_block_car_ws<NS, true, GEN>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
                                  part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem,
                                  part_rho + static_cast<size_t>(blockIdx.x) * p.T,
                                  part_eta + static_cast<size_t>(blockIdx.x) * p.T);
@@ -566,7 +568,7 @@ __global__ void k_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_bl
 // host launchers
 // ---------------------------------------------------------------------------
 size_t fused_smem_bytes(const CtrlParams &p, int blk) {
-  if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples);
+  if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples, false, p.gen != nullptr);
   if (blk == kFusedBlockQuadLanes) return quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
   if (blk == kFusedBlockQuadWs)
     return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p));
@@ -576,13 +578,13 @@ size_t fused_smem_bytes(const CtrlParams &p, int blk) {
 }
 
 int fused_block_size(int sys, const CtrlParams &p) {
-  if (p.gen) {  // the general sampling covariance runs on the one-thread kernels with du in shared memory
+  if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && fused_smem_bytes(p, kFusedBlockCarWs) <= kFusedSmemLimit)
+    return kFusedBlockCarWs;
+  if (p.gen) {  // else the general sampling covariance runs on the one-thread kernels, du in shared memory
     if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;
     if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
     return 0;
   }
-  if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && fused_smem_bytes(p, kFusedBlockCarWs) <= kFusedSmemLimit)
-    return kFusedBlockCarWs;
   if (sys == 2 && p.T <= kQwsChunk * kQwsMaxChunks && fused_smem_bytes(p, kFusedBlockQuadWs) <= kFusedSmemLimit)
     return kFusedBlockQuadWs;
   if (sys == 2 && fused_smem_bytes(p, kFusedBlockQuadLanes) <= kFusedSmemLimit) return kFusedBlockQuadLanes;
@@ -625,9 +627,12 @@ static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const float *x
 
 static cudaError_t launch_car_ws(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                  float *ps, BlockPartial *part, cudaStream_t s) {
-  const size_t smem = car_ws_smem_bytes(p.T, kWsSamples);
+  const size_t smem = car_ws_smem_bytes(p.T, kWsSamples, false, p.gen != nullptr);
   const int grid = (p.K + kWsSamples - 1) / kWsSamples;
-  k_rollout_car_ws<kWsSamples><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, ps, part);
+  if (p.gen)
+    k_rollout_car_ws<kWsSamples, true><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, ps, part);
+  else
+    k_rollout_car_ws<kWsSamples><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, ps, part);
   return cudaGetLastError();
 }
 
@@ -660,7 +665,7 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
 
 int fused_block_size_to_go(int sys, const CtrlParams &p) {
   const bool gen = p.gen != nullptr;
-  if (sys == 1 && !gen && p.T <= kWsChunk * kWsMaxChunks && car_ws_smem_bytes(p.T, kWsSamples, true) <= kToGoWsSmemLimit)
+  if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && car_ws_smem_bytes(p.T, kWsSamples, true, gen) <= kToGoWsSmemLimit)
     return kFusedBlockCarWs;
   if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true, gen, quad_grid_bytes(p)) <= kFusedSmemLimit)
     return kFusedBlockLarge;
@@ -699,10 +704,14 @@ cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const fl
     case 4: return launch_to_go_sys<CartPoleVel>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     case 1:
       if (blk == kFusedBlockCarWs) {
-        const size_t smem = car_ws_smem_bytes(p.T, kWsSamples, true);
+        const size_t smem = car_ws_smem_bytes(p.T, kWsSamples, true, p.gen != nullptr);
         const int grid = (p.K + kWsSamples - 1) / kWsSamples;
-        k_rollout_car_ws_to_go<kWsSamples><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part,
-                                                                                   part_rho, part_eta);
+        if (p.gen)
+          k_rollout_car_ws_to_go<kWsSamples, true><<<grid, kWsRoles * kWsSamples, smem, s>>>(
+              p, x0, st, U, S, part_sums, part, part_rho, part_eta);
+        else
+          k_rollout_car_ws_to_go<kWsSamples><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, part_sums,
+                                                                                     part, part_rho, part_eta);
         return cudaGetLastError();
       }
       return launch_to_go_sys<Car>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
@@ -768,7 +777,9 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Car, kFusedBlockLarge, true>),
       reinterpret_cast<const void *>(k_rollout_car_ws<kWsSamples>),
+      reinterpret_cast<const void *>(k_rollout_car_ws<kWsSamples, true>),
       reinterpret_cast<const void *>(k_rollout_car_ws_to_go<kWsSamples>),
+      reinterpret_cast<const void *>(k_rollout_car_ws_to_go<kWsSamples, true>),
       reinterpret_cast<const void *>(k_rollout_to_go<CartPole, kFusedBlockLarge>),
       reinterpret_cast<const void *>(k_rollout_to_go<CartPole, kFusedBlockSmall>),
       reinterpret_cast<const void *>(k_rollout_to_go<Car, kFusedBlockLarge>),

@@ -21,6 +21,9 @@
 //                      full/empty mbarriers
 // With TOGO (the per-time-step cost-to-go weighting) the pose role also keeps each step's
 // term of S~ in sC [T][NS] and its terminal cost, and the block forms per-step partials.
+// With GEN (a general sampling covariance per step, Theorem 1) the noise role scales step
+// i's normals by chol(Sigma_E,i) and the pose role's IS term is 1/2 du^T (R - lambda
+// Sigma_E,i^-1) du + u^T R du + 1/2 u^T R u, the per-step matrices staged in sGen.
 // Every wait is bounded; a thread whose wait runs out stops and its sample's cost is +inf.
 #pragma once
 #include <type_traits>
@@ -36,14 +39,14 @@ constexpr int kWsChunk = 8;       // steps per hand-off
 constexpr int kWsRing = 4;        // chunks in the velocity ring
 constexpr int kWsMaxChunks = 32;  // noise barriers: T <= kWsChunk * kWsMaxChunks
 
-__host__ __device__ inline size_t car_ws_smem_bytes(int T, int ns, bool to_go = false) {
+__host__ __device__ inline size_t car_ws_smem_bytes(int T, int ns, bool to_go = false, bool gen = false) {
   const size_t TM = 2 * static_cast<size_t>(T);
   return sizeof(float) * (2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
                           static_cast<size_t>(kWsRing) * kWsChunk * 3 * ns +
-                          (to_go ? (static_cast<size_t>(T) + 1) * ns : 0));
+                          (to_go ? (static_cast<size_t>(T) + 1) * ns : 0) + (gen ? 2 * TM * 2 : 0));
 }
 
-template <int NS, bool TOGO = false>
+template <int NS, bool TOGO = false, bool GEN = false>
 __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                                      const float *__restrict__ U, int k0, float *__restrict__ S_out,
                                                      float *__restrict__ part_sums, BlockPartial *__restrict__ part,
@@ -63,9 +66,12 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
   float *sVel = sDu + static_cast<size_t>(TM) * NS;  // [R][C][3][NS]
   float *sC = sVel + R * C * 3 * NS;                 // TOGO: [T][NS] step terms of S~
   float *sPhi = sC + static_cast<size_t>(T) * NS;    // TOGO: [NS] terminal costs
+  float *sGen = TOGO ? sPhi + NS : sC;              // GEN: [T][2][M][M] (chol(Sigma_E,i), R_IS,i)
 
   __shared__ float sx0[Car::N];  // x0 staged once (it may live in mapped host memory)
   for (int o = tid; o < TM; o += NT) sU[o] = U[o];
+  if (GEN)
+    for (int o = tid; o < 2 * TM * M; o += NT) sGen[o] = p.gen[o];
   if (tid < Car::N) sx0[tid] = x0[tid];
   if (tid == 0) {
     for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], NS);
@@ -148,7 +154,7 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
       for (int s = 0; s < 2; ++s) {
         const int i = 2 * b + s;
         float du[M];
-        scale_noise<M>(Lnu, e + s * M, du);
+        scale_noise<M>(GEN ? sGen + static_cast<size_t>(min(i, T - 1)) * 2 * M * M : Lnu, e + s * M, du);
         if (i < T) {
 #pragma unroll
           for (int a = 0; a < M; ++a) sDu[(i * M + a) * NS + slot] = du[a];
@@ -180,16 +186,17 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
       float du[M];
 #pragma unroll
       for (int a = 0; a < M; ++a) du[a] = sDu[(i * M + a) * NS + slot];
+      const float *Rg = sGen + static_cast<size_t>(i) * 2 * M * M + M * M;  // GEN: R_IS,i
       float duRdu = 0.0f, uRdu = 0.0f;
 #pragma unroll
       for (int a = 0; a < M; ++a) {
         uRdu = fmaf(sRu[i * M + a], du[a], uRdu);
         float rd = 0.0f;
 #pragma unroll
-        for (int l = 0; l < M; ++l) rd = fmaf(Rm[a * M + l], du[l], rd);
+        for (int l = 0; l < M; ++l) rd = fmaf(GEN ? Rg[a * M + l] : Rm[a * M + l], du[l], rd);
         duRdu = fmaf(du[a], rd, duRdu);
       }
-      return p.is_du * duRdu + uRdu + sHu[i];
+      return (GEN ? 0.5f : p.is_du) * duRdu + uRdu + sHu[i];
     };
     // S~ gains q(x_{i+1}) + is_i one step late (the cost-map loads of a step are issued
     // before they are needed).  The pending term starts as an exact zero, whose Kahan

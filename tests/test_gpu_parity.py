@@ -405,17 +405,8 @@ def test_cartpole_vel_cost_to_go(N):
 # general per-step sampling covariance (Theorem 1 with a general A_t, control space)
 # ---------------------------------------------------------------------------
 def _sigma_e(cfg, seed=5):
-    """Per-step SPD covariances around nu * Sigma: a rotation-and-scale that varies over the
-    horizon (neither a scalar multiple of Sigma nor constant in time)."""
-    rng = np.random.default_rng(seed)
-    m, T = np.atleast_2d(cfg["Sigma"]).shape[0], cfg["T"]
-    base = cfg["nu"] * np.atleast_2d(cfg["Sigma"])
-    out = []
-    for i in range(T):
-        A = np.eye(m) + 0.3 * rng.standard_normal((m, m))
-        s = 0.5 + 1.5 * (i + 1) / T
-        out.append(s * A @ base @ A.T + 1e-3 * np.trace(base) * np.eye(m))
-    return np.asarray(out, np.float32).astype(np.float64)
+    """Per-step SPD covariances around nu * Sigma (workloads.sampling_covariances)."""
+    return W.sampling_covariances(cfg, seed)
 
 
 def _oracle_general(cfg, SE, to_go=False):

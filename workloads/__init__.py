@@ -188,6 +188,21 @@ def config(system: int, **over) -> dict:
     return c
 
 
+def sampling_covariances(cfg: dict, seed: int = 5) -> np.ndarray:
+    """Per-step SPD sampling covariances [T][m][m] around nu * Sigma for the general
+    sampling covariance: a seeded rotation-and-scale that grows over the horizon (neither a
+    multiple of Sigma nor constant in time), plus a small ridge."""
+    rng = np.random.default_rng(seed)
+    m, T = np.atleast_2d(cfg["Sigma"]).shape[0], cfg["T"]
+    base = cfg["nu"] * np.atleast_2d(cfg["Sigma"])
+    out = []
+    for i in range(T):
+        A = np.eye(m) + 0.3 * rng.standard_normal((m, m))
+        s = 0.5 + 1.5 * (i + 1) / T
+        out.append(s * A @ base @ A.T + 1e-3 * np.trace(base) * np.eye(m))
+    return np.asarray(out, np.float32).astype(np.float64)
+
+
 def env_for(system: int, seed: int = 0):
     """Environment array of a system: the cost map (car), the forest (quad), or None."""
     if system in (CAR, CAR_MLP):
