@@ -84,14 +84,14 @@ __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws_to_go(
 }
 
 // quadrotor: noise / RK4 dynamics / crash decisions and cost in three warp roles, see rollout_quad_ws.cuh
-template <int NS>
+template <int NS, bool GEN = false>
 __global__ void __launch_bounds__(3 * NS, 1) k_rollout_quad_ws(const CtrlParams p, const float *__restrict__ x0,
                                                                const CtrlState *__restrict__ st,
                                                                const float *__restrict__ U, float *__restrict__ S_out,
                                                                float *__restrict__ part_sums,
                                                                BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block_quad_ws<NS>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+  rollout_block_quad_ws<NS, GEN>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
                             part_sums + static_cast<size_t>(blockIdx.x) * p.T * Quad::M, part + blockIdx.x, smem);
 }
 
@@ -571,7 +571,7 @@ size_t fused_smem_bytes(const CtrlParams &p, int blk) {
   if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples, false, p.gen != nullptr);
   if (blk == kFusedBlockQuadLanes) return quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
   if (blk == kFusedBlockQuadWs)
-    return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p));
+    return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p), p.gen != nullptr);
   const bool regen = blk == kFusedBlockRegen;
   return rollout_smem_bytes(p.T, p.m, p.n_obs, regen ? kFusedBlockLarge : blk, regen, false, p.gen != nullptr,
                             quad_grid_bytes(p));
@@ -580,6 +580,8 @@ size_t fused_smem_bytes(const CtrlParams &p, int blk) {
 int fused_block_size(int sys, const CtrlParams &p) {
   if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && fused_smem_bytes(p, kFusedBlockCarWs) <= kFusedSmemLimit)
     return kFusedBlockCarWs;
+  if (sys == 2 && p.gen && p.T <= kQwsChunk * kQwsMaxChunks && fused_smem_bytes(p, kFusedBlockQuadWs) <= kBigWsSmemLimit)
+    return kFusedBlockQuadWs;
   if (p.gen) {  // else the general sampling covariance runs on the one-thread kernels, du in shared memory
     if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;
     if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
@@ -648,7 +650,10 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
       if (blk == kFusedBlockQuadWs) {
         const size_t smem = fused_smem_bytes(p, kFusedBlockQuadWs);
         const int grid = (p.K + kQwsSamples - 1) / kQwsSamples;
-        k_rollout_quad_ws<kQwsSamples><<<grid, 3 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part);
+        if (p.gen)
+          k_rollout_quad_ws<kQwsSamples, true><<<grid, 3 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part);
+        else
+          k_rollout_quad_ws<kQwsSamples><<<grid, 3 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part);
         return cudaGetLastError();
       }
       if (blk == kFusedBlockQuadLanes) {
@@ -665,7 +670,7 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
 
 int fused_block_size_to_go(int sys, const CtrlParams &p) {
   const bool gen = p.gen != nullptr;
-  if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && car_ws_smem_bytes(p.T, kWsSamples, true, gen) <= kToGoWsSmemLimit)
+  if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && car_ws_smem_bytes(p.T, kWsSamples, true, gen) <= kBigWsSmemLimit)
     return kFusedBlockCarWs;
   if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true, gen, quad_grid_bytes(p)) <= kFusedSmemLimit)
     return kFusedBlockLarge;
@@ -788,6 +793,7 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_to_go<Quad, kFusedBlockSmall>),
       reinterpret_cast<const void *>(k_rollout_quad_lanes<kQuadLanesBlock, kQuadLanes>),
       reinterpret_cast<const void *>(k_rollout_quad_ws<kQwsSamples>),
+      reinterpret_cast<const void *>(k_rollout_quad_ws<kQwsSamples, true>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, true>),

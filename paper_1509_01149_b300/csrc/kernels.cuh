@@ -18,7 +18,9 @@ constexpr int kMinBlockSamples = kQuadLanesBlock / kQuadLanes;  // fewest sample
 constexpr int kMergeThreads = 256;
 constexpr int kMergeOutputs = 32;       // outputs (i, j) per merge block
 constexpr size_t kFusedSmemLimit = 200 * 1024;
-constexpr size_t kToGoWsSmemLimit = 220 * 1024;  // the car's warp roles with per-step cost storage
+// the warp-role kernels whose per-step tables (the car's step costs, the quadrotor's
+// per-step covariances) take them past kFusedSmemLimit
+constexpr size_t kBigWsSmemLimit = 220 * 1024;
 
 // Raise the dynamic shared-memory limit of the kernels that need it (once per
 // device, before any launch or capture).
@@ -54,7 +56,7 @@ cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float
                                       float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
                                       CtrlState *st, cudaStream_t s, unsigned int *u0_ready = nullptr);
 // Cost-to-go weighting (Eq. App_PI per time step): block shape (the car's warp roles,
-// kFusedBlockCarWs, when their shared memory fits kToGoWsSmemLimit; else 128 or 64 samples,
+// kFusedBlockCarWs, when their shared memory fits kBigWsSmemLimit; else 128 or 64 samples,
 // du and the step costs in shared memory; 0 if they do not fit), the rollout with per-step
 // block partials
 // (part_rho / part_eta [nblk][T]) and their FP64 merge + update.

@@ -23,6 +23,9 @@
 //   ring [R][C][P][NS]   dynamics -> cost: per step the P = 8 state values the cost role
 //                        reads (p, v, pitch, yaw; px replaced by NaN when any component of
 //                        the new state is not finite), full/empty mbarriers
+// With GEN (a general sampling covariance per step, Theorem 1) the noise role scales step
+// i's normals by chol(Sigma_E,i) and the cost role's IS term is 1/2 du^T (R - lambda
+// Sigma_E,i^-1) du + u^T R du + 1/2 u^T R u, the per-step matrices staged in sGen.
 // Every wait is bounded; a thread whose wait runs out stops and its sample's cost is +inf.
 #pragma once
 #include "rollout_body.cuh"
@@ -36,14 +39,14 @@ constexpr int kQwsRing = 2;      // chunks in the state ring
 constexpr int kQwsMaxChunks = 32;
 constexpr int kQwsPass = 8;      // values per step handed from the dynamics to the cost role
 
-__host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns, size_t grid_bytes) {
+__host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns, size_t grid_bytes, bool gen = false) {
   const size_t TM = 4 * static_cast<size_t>(T);
   return sizeof(float) * (4 * static_cast<size_t>(n_obs) + 2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
-                          static_cast<size_t>(kQwsRing) * kQwsChunk * kQwsPass * ns) +
+                          static_cast<size_t>(kQwsRing) * kQwsChunk * kQwsPass * ns + (gen ? 2 * TM * 4 : 0)) +
          grid_bytes;
 }
 
-template <int NS>
+template <int NS, bool GEN = false>
 __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                                       const float *__restrict__ U, int k0,
                                                       float *__restrict__ S_out, float *__restrict__ part_sums,
@@ -62,11 +65,14 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
   float *sS = sW + NS;                                   // [NS]  path costs (cost role -> block partial)
   float *sDu = sS + NS;                                  // [TM][NS] perturbations
   float *sRing = sDu + static_cast<size_t>(TM) * NS;     // [R][C][P][NS]
-  unsigned short *sOff = reinterpret_cast<unsigned short *>(sRing + R * C * P * NS);  // [cells + 1]
+  float *sGen = sRing + R * C * P * NS;                  // GEN: [T][2][M][M] (chol(Sigma_E,i), R_IS,i)
+  unsigned short *sOff = reinterpret_cast<unsigned short *>(sGen + (GEN ? 2 * TM * M : 0));  // [cells + 1]
   const int ncell = p.grid_nx * p.grid_ny;
   unsigned char *sIdx = reinterpret_cast<unsigned char *>(sOff + (ncell + 1));       // [grid_nidx]
 
   for (int o = tid; o < TM; o += NT) sU[o] = U[o];
+  if (GEN)
+    for (int o = tid; o < 2 * TM * M; o += NT) sGen[o] = p.gen[o];
   for (int o = tid; o < 4 * p.n_obs; o += NT) sObs[o] = (o & 3) == 3 ? 0.0f : p.obs[3 * (o >> 2) + (o & 3)];
   if (p.grid_nx > 0) {
     for (int o = tid; o <= ncell; o += NT) sOff[o] = p.grid_off[o];
@@ -106,7 +112,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
       float e[4];
       normals4(static_cast<uint32_t>(i), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, e);
       float du[M];
-      scale_noise<M>(Lnu, e, du);
+      scale_noise<M>(GEN ? sGen + static_cast<size_t>(i) * 2 * M * M : Lnu, e, du);
 #pragma unroll
       for (int a = 0; a < M; ++a) sDu[(i * M + a) * NS + slot] = du[a];
     };
@@ -185,13 +191,14 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
         float du[M];
 #pragma unroll
         for (int a = 0; a < M; ++a) du[a] = sDu[(i * M + a) * NS + slot];
+        const float *Rg = sGen + static_cast<size_t>(i) * 2 * M * M + M * M;  // GEN: R_IS,i
         float duRdu = 0.0f, uRdu = 0.0f;
 #pragma unroll
         for (int a = 0; a < M; ++a) {
           uRdu = fmaf(sRu[i * M + a], du[a], uRdu);
           float rd = 0.0f;
 #pragma unroll
-          for (int l = 0; l < M; ++l) rd = fmaf(Rm[a * M + l], du[l], rd);
+          for (int l = 0; l < M; ++l) rd = fmaf(GEN ? Rg[a * M + l] : Rm[a * M + l], du[l], rd);
           duRdu = fmaf(du[a], rd, duRdu);
         }
         // the sequential step's crash test on the new state (a crashed sample keeps its state
@@ -213,7 +220,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
           aux.d = d;
         }
         aux.crashed = aux.crashed || hit;
-        S.add(Quad::cost(x, aux, env) + (p.is_du * duRdu + uRdu + sHu[i]));
+        S.add(Quad::cost(x, aux, env) + ((GEN ? 0.5f : p.is_du) * duRdu + uRdu + sHu[i]));
       }
       tc::mbar_arrive(&bar_empty[c % R]);
     }
