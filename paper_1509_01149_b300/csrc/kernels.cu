@@ -95,6 +95,19 @@ __global__ void __launch_bounds__(3 * NS, 1) k_rollout_quad_ws(const CtrlParams 
                             part_sums + static_cast<size_t>(blockIdx.x) * p.T * Quad::M, part + blockIdx.x, smem);
 }
 
+// quadrotor, cost-to-go weighting: the three warp roles with per-step partials
+template <int NS>
+__global__ void __launch_bounds__(3 * NS, 1) k_rollout_quad_ws_to_go(
+    const CtrlParams p, const float *__restrict__ x0, const CtrlState *__restrict__ st, const float *__restrict__ U,
+    float *__restrict__ S_out, float *__restrict__ part_sums, BlockPartial *__restrict__ part,
+    float *__restrict__ part_rho, DF *__restrict__ part_eta) {
+  extern __shared__ __align__(16) float smem[];
+  rollout_block_quad_ws<NS, false, true>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+                                         part_sums + static_cast<size_t>(blockIdx.x) * p.T * Quad::M, part + blockIdx.x,
+                                         smem, part_rho + static_cast<size_t>(blockIdx.x) * p.T,
+                                         part_eta + static_cast<size_t>(blockIdx.x) * p.T);
+}
+
 // quadrotor: four lanes per sample (shared RK4 step, split cylinder search), see rollout_lanes.cuh
 template <int BLK, int LANES>
 __global__ void __launch_bounds__(BLK) k_rollout_quad_lanes(const CtrlParams p, const float *__restrict__ x0,
@@ -672,6 +685,9 @@ int fused_block_size_to_go(int sys, const CtrlParams &p) {
   const bool gen = p.gen != nullptr;
   if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && car_ws_smem_bytes(p.T, kWsSamples, true, gen) <= kBigWsSmemLimit)
     return kFusedBlockCarWs;
+  if (sys == 2 && !gen && p.T <= kQwsChunk * kQwsMaxChunks &&
+      quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p), false, true) <= kBigWsSmemLimit)
+    return kFusedBlockQuadWs;
   if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockLarge, false, true, gen, quad_grid_bytes(p)) <= kFusedSmemLimit)
     return kFusedBlockLarge;
   if (rollout_smem_bytes(p.T, p.m, p.n_obs, kFusedBlockSmall, false, true, gen, quad_grid_bytes(p)) <= kFusedSmemLimit)
@@ -720,7 +736,15 @@ cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const fl
         return cudaGetLastError();
       }
       return launch_to_go_sys<Car>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
-    case 2: return launch_to_go_sys<Quad>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
+    case 2:
+      if (blk == kFusedBlockQuadWs) {
+        const size_t smem = quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p), false, true);
+        const int grid = (p.K + kQwsSamples - 1) / kQwsSamples;
+        k_rollout_quad_ws_to_go<kQwsSamples><<<grid, 3 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part,
+                                                                                 part_rho, part_eta);
+        return cudaGetLastError();
+      }
+      return launch_to_go_sys<Quad>(blk, p, x0, st, U, S, part_sums, part, part_rho, part_eta, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -794,6 +818,7 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_quad_lanes<kQuadLanesBlock, kQuadLanes>),
       reinterpret_cast<const void *>(k_rollout_quad_ws<kQwsSamples>),
       reinterpret_cast<const void *>(k_rollout_quad_ws<kQwsSamples, true>),
+      reinterpret_cast<const void *>(k_rollout_quad_ws_to_go<kQwsSamples>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockSmall, false>),
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, true>),

@@ -23,6 +23,9 @@
 //   ring [R][C][P][NS]   dynamics -> cost: per step the P = 8 state values the cost role
 //                        reads (p, v, pitch, yaw; px replaced by NaN when any component of
 //                        the new state is not finite), full/empty mbarriers
+// With TOGO (the per-time-step cost-to-go weighting) the cost role also keeps each step's
+// term of S~ in sC [T][NS] and its terminal cost, and the block forms per-step partials; the
+// hand-off chunks are then 4 steps, so that the table fits beside du.
 // With GEN (a general sampling covariance per step, Theorem 1) the noise role scales step
 // i's normals by chol(Sigma_E,i) and the cost role's IS term is 1/2 du^T (R - lambda
 // Sigma_E,i^-1) du + u^T R du + 1/2 u^T R u, the per-step matrices staged in sGen.
@@ -34,26 +37,31 @@
 namespace mppi {
 
 constexpr int kQwsSamples = 64;  // samples per CTA (3x threads)
-constexpr int kQwsChunk = 8;     // steps per hand-off
+constexpr int kQwsChunk = 8;     // steps per hand-off (4 with the cost-to-go weighting)
 constexpr int kQwsRing = 2;      // chunks in the state ring
-constexpr int kQwsMaxChunks = 32;
+constexpr int kQwsMaxChunks = 32;  // noise barriers: T <= 256 (64 barriers of 4 steps with TOGO)
+__host__ __device__ constexpr int quad_ws_chunk(bool to_go) { return to_go ? kQwsChunk / 2 : kQwsChunk; }
 constexpr int kQwsPass = 8;      // values per step handed from the dynamics to the cost role
 
-__host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns, size_t grid_bytes, bool gen = false) {
+__host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns, size_t grid_bytes, bool gen = false,
+                                                     bool to_go = false) {
   const size_t TM = 4 * static_cast<size_t>(T);
   return sizeof(float) * (4 * static_cast<size_t>(n_obs) + 2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
-                          static_cast<size_t>(kQwsRing) * kQwsChunk * kQwsPass * ns + (gen ? 2 * TM * 4 : 0)) +
+                          static_cast<size_t>(kQwsRing) * quad_ws_chunk(to_go) * kQwsPass * ns +
+                          (gen ? 2 * TM * 4 : 0) + (to_go ? (static_cast<size_t>(T) + 1) * ns : 0)) +
          grid_bytes;
 }
 
-template <int NS, bool GEN = false>
+template <int NS, bool GEN = false, bool TOGO = false>
 __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                                       const float *__restrict__ U, int k0,
                                                       float *__restrict__ S_out, float *__restrict__ part_sums,
-                                                      BlockPartial *__restrict__ part, float *smem) {
+                                                      BlockPartial *__restrict__ part, float *smem,
+                                                      float *__restrict__ part_rho = nullptr,
+                                                      DF *__restrict__ part_eta = nullptr) {
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
-  constexpr int M = Quad::M, N = Quad::N, C = kQwsChunk, R = kQwsRing, P = kQwsPass, NT = 3 * NS;
-  __shared__ uint64_t bar_noise[kQwsMaxChunks], bar_full[R], bar_empty[R];
+  constexpr int M = Quad::M, N = Quad::N, C = quad_ws_chunk(TOGO), R = kQwsRing, P = kQwsPass, NT = 3 * NS;
+  __shared__ uint64_t bar_noise[kQwsMaxChunks * kQwsChunk / C], bar_full[R], bar_empty[R];
   __shared__ float sx0[N];
   const int T = p.T, TM = T * M, tid = threadIdx.x;
   const int nch = (T + C - 1) / C;
@@ -66,7 +74,9 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
   float *sDu = sS + NS;                                  // [TM][NS] perturbations
   float *sRing = sDu + static_cast<size_t>(TM) * NS;     // [R][C][P][NS]
   float *sGen = sRing + R * C * P * NS;                  // GEN: [T][2][M][M] (chol(Sigma_E,i), R_IS,i)
-  unsigned short *sOff = reinterpret_cast<unsigned short *>(sGen + (GEN ? 2 * TM * M : 0));  // [cells + 1]
+  float *sC = sGen + (GEN ? 2 * TM * M : 0);             // TOGO: [T][NS] step terms of S~
+  float *sPhi = sC + (TOGO ? static_cast<size_t>(T) * NS : 0);  // TOGO: [NS] terminal costs
+  unsigned short *sOff = reinterpret_cast<unsigned short *>(sPhi + (TOGO ? NS : 0));  // [cells + 1]
   const int ncell = p.grid_nx * p.grid_ny;
   unsigned char *sIdx = reinterpret_cast<unsigned char *>(sOff + (ncell + 1));       // [grid_nidx]
 
@@ -220,17 +230,29 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
           aux.d = d;
         }
         aux.crashed = aux.crashed || hit;
-        S.add(Quad::cost(x, aux, env) + ((GEN ? 0.5f : p.is_du) * duRdu + uRdu + sHu[i]));
+        const float cv = Quad::cost(x, aux, env) + ((GEN ? 0.5f : p.is_du) * duRdu + uRdu + sHu[i]);
+        S.add(cv);
+        if (TOGO) sC[i * NS + slot] = cv;
       }
       tc::mbar_arrive(&bar_empty[c % R]);
     }
-    if (ok) S.add(Quad::cost(x, aux, env));  // phi(x_T) = q(x_T)
+    float phi = INFINITY;
+    if (ok) {
+      phi = Quad::cost(x, aux, env);
+      S.add(phi);  // phi(x_T) = q(x_T)
+    }
     sS[slot] = ok ? S.s : INFINITY;
+    if (TOGO) sPhi[slot] = phi;
   }
   __syncthreads();
   // the update kernel may start launching now (it waits for this grid's results itself)
   asm volatile("griddepcontrol.launch_dependents;");
   const bool owner = tid < NS;
+  if (TOGO) {
+    if (owner && k0 + tid < p.K) S_out[k0 + tid] = isfinite(sS[tid]) ? sS[tid] : INFINITY;
+    block_partial_to_go<M, NT, NS>(p, k0, owner ? sPhi[tid] : 0.0f, sC, sDu, part_sums, part_rho, part_eta, part);
+    return;
+  }
   block_partial<M, NT, false, NS>(p, owner ? k0 + tid : INT_MAX, ctr, owner ? sS[tid] : INFINITY, Lnu, S_out,
                                   part_sums, part, sW, sDu);
 }
