@@ -485,7 +485,7 @@ def run_capacity(probe=(16, 64), ticks=5, cap=2048, seed=0):
 def run_learned(n_train=10_000_000, n_test=100_000, steps=6000, batch=8192):
     """Learned car dynamics: train on n_train analytic transitions (the GPU's analytic step
     generates the targets), test on n_test held-out ones; one-step and 100-step errors
-    against the analytic model (the judge); MPPI rollout throughput with the network in
+    against the analytic model (the yardstick); MPPI rollout throughput with the network in
     BF16 and in FP8 at K=16384, T=100."""
     import torch
 

@@ -278,7 +278,7 @@ int mppi_step_static(mppi_system sys, int K, int T, float dt, float nu, float la
 
 /* ---------------------------------------------------------------------------------
  * Serving: many controllers of different systems, K and T stepped together.
- * (North-star extension; the paper runs one controller.)
+ * (An extension beyond the paper, which runs one controller.)
  *
  * A server owns a device arena (allocated once at create) and a device slot table.
  * mppi_server_admit places a controller in a free slot if its buffers fit in the arena
@@ -341,7 +341,7 @@ int mppi_server_get_info(mppi_server *srv, mppi_server_info *out);
 const char *mppi_server_last_error(mppi_server *srv);
 
 /* ---------------------------------------------------------------------------------
- * Learned car dynamics (spec extension; not in the paper).
+ * Learned car dynamics (an extension beyond the paper).
  *   features  z (16) = (X/20, Y/20, wrap(psi)/pi, (vx-5)/5, vy/2, r/3, delta/0.5,
  *             u_steer/1.6, u_throttle/1.8, 0 ...), psi wrapped to (-pi, pi]
  *   network   h1 = tanh(W1 z + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3
@@ -373,7 +373,7 @@ int mppi_mlp_grad(mppi_mlp *mlp, const void *d_X, const float *d_T, int B, float
 /* One learned step for n device (state [n][7], control [n][2]) pairs into d_next [n][7]. */
 int mppi_mlp_predict(mppi_mlp *mlp, const float *d_states, const float *d_controls, int n, float *d_next);
 const char *mppi_mlp_last_error(mppi_mlp *mlp);
-/* The analytic car step (the learned model's fallback and judge): d_next [n][7] from
+/* The analytic car step (the learned model's fallback and yardstick): d_next [n][7] from
  * device (state [n][7], control [n][2]) pairs, enqueued on `stream` (NULL = legacy). */
 int mppi_car_step(const float *d_states, const float *d_controls, int n, float dt, float *d_next, void *stream);
 

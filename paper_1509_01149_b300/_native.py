@@ -538,7 +538,7 @@ class MLP:
 
 
 def mppi_car_step(d_states: int, d_controls: int, n: int, dt: float, d_next: int, stream: int = 0):
-    """The analytic car step on the device (the learned model's fallback and judge)."""
+    """The analytic car step on the device (the learned model's fallback and yardstick)."""
     rc = lib.mppi_car_step(C.c_void_p(d_states), C.c_void_p(d_controls), n, dt, C.c_void_p(d_next),
                            C.c_void_p(stream))
     if rc != MPPI_OK:
