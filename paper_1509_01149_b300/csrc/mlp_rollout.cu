@@ -6,7 +6,8 @@
 //                        a time; threads 0..127 also own one sample each (noise, features,
 //                        state update, cost);
 //   MMA warp 8           one thread issues every tcgen05.mma and commit.
-// The weights are copied once into shared memory in the K-major core-matrix layout.  TMEM
+// The weights are copied once into shared memory in the K-major core-matrix layout (bulk
+// asynchronous copies completing on an mbarrier the MMA thread waits for).  TMEM
 // (512 columns) holds the FP32 accumulators: layer 1 in columns 0..255, layer 2 in
 // 256..511, the output layer in 0..15.  Per time step:
 //   owners: noise du_i (Philox), v = u_i + du_i, features z(x, v) -> X tile    [bar_x]
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   // bar_x: X tile written (128 owner threads); bar_l1/l2/l3: products done (MMA commits);
   // hb[c]: H columns 32c..32c+31 written (128 threads of one column half), twice per step;
   // bar_drain: the MMA thread's last commit before TMEM is freed
-  __shared__ uint64_t bar_x, bar_l1, bar_l2, bar_l3, bar_drain, hb[8];
+  __shared__ uint64_t bar_x, bar_l1, bar_l2, bar_l3, bar_drain, hb[8], bar_w;
   __shared__ uint32_t tmem_base;
   const MlpDev *md = static_cast<const MlpDev *>(p.mlp);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -164,18 +165,18 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
     tc::mbar_init(&bar_l3, 1);
     tc::mbar_init(&bar_drain, 1);
     for (int c = 0; c < 8; ++c) tc::mbar_init(&hb[c], 128);
+    tc::mbar_init(&bar_w, 1);
+    tc::fence_mbar_init();
+    // weights (already in tile layout): three bulk copies completing on bar_w, read only by
+    // the MMAs (which wait for them)
+    constexpr uint32_t b2 = 256 * 256 * E, b1 = 256 * L::K1 * E, b3 = 16 * 256 * E;
+    tc::mbar_arrive_expect_tx(&bar_w, b1 + b2 + b3);
+    tc::bulk_g2s(smem + L::W2, md->w2, b2, &bar_w);
+    tc::bulk_g2s(smem + L::W1, md->w1, b1, &bar_w);
+    tc::bulk_g2s(smem + L::W3, md->w3, b3, &bar_w);
   }
-  // weights (already in tile layout) and biases
+  // biases and scales
   {
-    const uint4 *w2 = reinterpret_cast<const uint4 *>(md->w2);
-    const uint4 *w1 = reinterpret_cast<const uint4 *>(md->w1);
-    const uint4 *w3 = reinterpret_cast<const uint4 *>(md->w3);
-    uint4 *d2 = reinterpret_cast<uint4 *>(smem + L::W2);
-    uint4 *d1 = reinterpret_cast<uint4 *>(smem + L::W1);
-    uint4 *d3 = reinterpret_cast<uint4 *>(smem + L::W3);
-    for (int i = tid; i < 256 * 256 * E / 16; i += kMlpThreads) d2[i] = w2[i];
-    for (int i = tid; i < static_cast<int>(256 * L::K1 * E / 16); i += kMlpThreads) d1[i] = w1[i];
-    for (int i = tid; i < 16 * 256 * E / 16; i += kMlpThreads) d3[i] = w3[i];
     for (int i = tid; i < 256; i += kMlpThreads) {
       sb1[i] = md->b1[i];
       sb2[i] = md->b2[i];
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
       const uint32_t sbase = tc::smem_u32(smem);
       const uint32_t id256 = E == 2 ? tc::idesc_bf16_f32(128, 256) : tc::idesc_e4m3_f32(128, 256);
       const uint32_t id16 = E == 2 ? tc::idesc_bf16_f32(128, 16) : tc::idesc_e4m3_f32(128, 16);
+      ok = tc::mbar_wait(&bar_w, 0u);  // the weight tiles are in shared memory
       for (int i = 0; i < T && ok; ++i) {
         const uint32_t ph = static_cast<uint32_t>(i & 1);
         ok = tc::mbar_wait(&bar_x, ph);
@@ -424,6 +426,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, L::kTmemCols);
+  if (tid == 0) tc::mbar_wait(&bar_w, 0u);  // no weight copy still in flight when the CTA exits
 }
 
 size_t mlp_rollout_smem_bytes(int T, int precision) {

@@ -97,6 +97,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 // ---- MMA -------------------------------------------------------------------------------
+// this thread's arrival on `bar`, which also expects `bytes` more bytes of asynchronous copies
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// make mbarrier initialisations visible to the asynchronous proxy (the bulk copies)
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to shared
+// memory by the asynchronous copy engine; its bytes complete on `bar`'s transaction count
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
