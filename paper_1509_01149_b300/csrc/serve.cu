@@ -9,8 +9,9 @@
 //                read back by the same CTA, so it stays in L2) rather than to shared
 //                memory, so many CTAs share an SM.  Items of different systems / K / T
 //                run side by side.
-//   k_serve_merge          persistent: one slot per CTA taken from a second queue; FP64
-//                merge of the slot's block partials, U update, u_0 out, shift, counter++.
+//   k_serve_merge          persistent: one slot per CTA taken from a second queue; merge of
+//                the slot's block partials (FP64 normaliser, double-FP32 weighted sums), U
+//                update, u_0 out, shift, counter++.
 // Host side
 //   first-fit arena allocator (admission by memory), work-item builder, one CUDA graph
 //   (memset queue counters -> H2D tick buffer -> rollout -> merge -> D2H u_0) whose copy
@@ -29,6 +30,7 @@
 
 #include "../../include/mppi.h"
 #include "forest_grid.h"
+#include "merge_common.cuh"
 #include "kernels.cuh"
 #include "rollout_body.cuh"
 
@@ -112,8 +114,8 @@ __global__ void __launch_bounds__(BLK, MINB) k_serve_rollout(const ServeArgs a) 
 __global__ void __launch_bounds__(kServeMergeThreads) k_serve_merge(const ServeArgs a, int max_nblk) {
   constexpr int NW = kServeMergeThreads / 32;
   extern __shared__ __align__(16) unsigned char msm[];
-  double *s_scale = reinterpret_cast<double *>(msm);             // [max_nblk]
-  float *s_unew = reinterpret_cast<float *>(s_scale + max_nblk);  // [T*m]
+  float *s_scale = reinterpret_cast<float *>(msm);  // [max_nblk]
+  float *s_unew = s_scale + max_nblk;                // [T*m]
   __shared__ int s_slot;
   __shared__ float s_rho[NW];
   __shared__ int s_k[NW];
@@ -157,10 +159,9 @@ __global__ void __launch_bounds__(kServeMergeThreads) k_serve_merge(const ServeA
     const float rho = s_rho[0];
     double e = 0.0;
     for (int b = tid; b < nblk; b += kServeMergeThreads) {
-      const float rb = d->part[b].rho;
-      const double sc = (isfinite(rho) && isfinite(rb)) ? static_cast<double>(expf(-(rb - rho) * inv_lambda)) : 0.0;
+      const float sc = merge_scale(d->part[b].rho, rho, inv_lambda);
       s_scale[b] = sc;
-      e += sc * d->part[b].eta;
+      e += static_cast<double>(sc) * d->part[b].eta;
     }
     e = warp_sum_d(e);
     if (lane == 0) s_e[warp] = e;
@@ -168,10 +169,25 @@ __global__ void __launch_bounds__(kServeMergeThreads) k_serve_merge(const ServeA
     double eta = 0.0;
 #pragma unroll
     for (int q = 0; q < NW; ++q) eta += s_e[q];
+    // per output: double-FP32 sums (exact products, TwoSum) over the blocks in four
+    // interleaved chains (b mod 4), combined in order; du in FP64
     for (int o = tid; o < TM; o += kServeMergeThreads) {
-      double acc = 0.0;
-      for (int b = 0; b < nblk; ++b) acc += s_scale[b] * static_cast<double>(d->part_sums[static_cast<size_t>(b) * TM + o]);
-      const double du = eta > 0.0 ? acc / eta : 0.0;
+      DF acc[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+      const float *ps = d->part_sums + o;
+      int b = 0;
+      for (; b + 3 < nblk; b += 4) {
+        const float x0 = ps[static_cast<size_t>(b) * TM], x1 = ps[static_cast<size_t>(b + 1) * TM];
+        const float x2 = ps[static_cast<size_t>(b + 2) * TM], x3 = ps[static_cast<size_t>(b + 3) * TM];
+        df_add_prod(acc[0], s_scale[b], x0);
+        df_add_prod(acc[1], s_scale[b + 1], x1);
+        df_add_prod(acc[2], s_scale[b + 2], x2);
+        df_add_prod(acc[3], s_scale[b + 3], x3);
+      }
+      for (; b < nblk; ++b) df_add_prod(acc[b & 3], s_scale[b], ps[static_cast<size_t>(b) * TM]);
+      df_add(acc[0], acc[1]);
+      df_add(acc[0], acc[2]);
+      df_add(acc[0], acc[3]);
+      const double du = eta > 0.0 ? merge_du(acc[0], 1.0 / eta) : 0.0;
       s_unew[o] = d->U[o] + static_cast<float>(du);
     }
     __syncthreads();
@@ -373,7 +389,7 @@ size_t slot_bytes(int K, int T, int m) {
 size_t rollout_smem(const mppi_server *s, int blk) {
   return rollout_smem_bytes(s->max_tm, 1, s->max_nobs, blk, true, false, false, s->max_grid);
 }
-size_t merge_smem(const mppi_server *s) { return sizeof(double) * s->max_nblk + sizeof(float) * s->max_tm; }
+size_t merge_smem(const mppi_server *s) { return sizeof(float) * (s->max_nblk + s->max_tm); }
 
 // Rollout kernel variants the autotuner chooses from: block size and the register cap
 // implied by a minimum number of resident blocks per SM.
