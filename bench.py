@@ -107,12 +107,17 @@ _REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_pow
 
 
 class ClockSampler:
-    def __init__(self, gpu_id: str | None):
+    """nvidia-smi clocks and throttle reasons every 20 ms.  Started ahead of the timed region
+    (it waits for the first sample), it keeps the samples whose timestamps fall between
+    mark_start() and mark_end() (host wall clock around the timed region)."""
+
+    def __init__(self, gpu_id: str | None, settle_s: float = 2.0):
         self.path = tempfile.mktemp(suffix=".csv")
+        self.t0 = self.t1 = None
         q = ("timestamp,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-        cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100"]
+        cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "20"]
         if gpu_id:
             cmd += ["-i", gpu_id]
         try:
@@ -120,6 +125,26 @@ class ClockSampler:
             self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        deadline = time.time() + settle_s
+        while time.time() < deadline and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def _inside(self, stamp: str) -> bool:
+        if self.t0 is None or self.t1 is None:
+            return True
+        try:
+            import datetime
+            t = datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return True
+        return self.t0 <= t <= self.t1
 
     def stop(self):
         if self.p is None:
@@ -133,7 +158,7 @@ class ClockSampler:
         rows = []
         for line in open(self.path):
             parts = [s.strip() for s in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 9 or not self._inside(parts[0]):
                 continue
             try:
                 rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), util=float(parts[3]),
@@ -625,22 +650,23 @@ def run_ours(args, rank, world, local_rank):
         d_u0 = torch.zeros(m, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
-    # warm-up
-    for _ in range(args.warmup):
-        ctrl.iterate_async(d_x0.data_ptr(), d_u0.data_ptr())
-    torch.cuda.synchronize()
-
+    # clock sampling runs from before the warm-up; only the timed region's samples are kept
     try:
         gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
         gpu_id = gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}"
     except Exception:
         gpu_id = None
     clocks = ClockSampler(gpu_id)
+    # warm-up
+    for _ in range(args.warmup):
+        ctrl.iterate_async(d_x0.data_ptr(), d_u0.data_ptr())
+    torch.cuda.synchronize()
 
     # ---- value: inputs resident, one graph launch per receding-horizon iteration ---
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
+    clocks.mark_start()
     with torch.cuda.stream(stream):
         for s in range(args.steps):
             flush.zero_()                              # evict L2 between timed steps
@@ -649,6 +675,7 @@ def run_ours(args, rank, world, local_rank):
             ctrl.iterate_async(d_x0.data_ptr(), d_u0.data_ptr())
             e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     total_s = reduce_max(sum(step_ms) / 1e3, dist, dev)
