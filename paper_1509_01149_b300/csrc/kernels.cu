@@ -600,7 +600,7 @@ int fused_block_size(int sys, const CtrlParams &p) {
     if (fused_smem_bytes(p, kFusedBlockSmall) <= kFusedSmemLimit) return kFusedBlockSmall;
     return 0;
   }
-  if (sys == 2 && p.T <= kQwsChunk * kQwsMaxChunks && fused_smem_bytes(p, kFusedBlockQuadWs) <= kFusedSmemLimit)
+  if (sys == 2 && p.T <= kQwsChunk * kQwsMaxChunks && fused_smem_bytes(p, kFusedBlockQuadWs) <= kBigWsSmemLimit)
     return kFusedBlockQuadWs;
   if (sys == 2 && fused_smem_bytes(p, kFusedBlockQuadLanes) <= kFusedSmemLimit) return kFusedBlockQuadLanes;
   if (fused_smem_bytes(p, kFusedBlockLarge) <= kFusedSmemLimit) return kFusedBlockLarge;

@@ -38,16 +38,17 @@ namespace mppi {
 
 constexpr int kQwsSamples = 64;  // samples per CTA (3x threads)
 constexpr int kQwsChunk = 8;     // steps per hand-off (4 with the cost-to-go weighting)
-constexpr int kQwsRing = 2;      // chunks in the state ring
+constexpr int kQwsRing = 3;      // chunks in the state ring (2 with the per-step tables)
 constexpr int kQwsMaxChunks = 32;  // noise barriers: T <= 256 (64 barriers of 4 steps with TOGO)
 __host__ __device__ constexpr int quad_ws_chunk(bool to_go) { return to_go ? kQwsChunk / 2 : kQwsChunk; }
+__host__ __device__ constexpr int quad_ws_ring(bool to_go, bool gen) { return (to_go || gen) ? kQwsRing - 1 : kQwsRing; }
 constexpr int kQwsPass = 8;      // values per step handed from the dynamics to the cost role
 
 __host__ __device__ inline size_t quad_ws_smem_bytes(int T, int n_obs, int ns, size_t grid_bytes, bool gen = false,
                                                      bool to_go = false) {
   const size_t TM = 4 * static_cast<size_t>(T);
   return sizeof(float) * (4 * static_cast<size_t>(n_obs) + 2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
-                          static_cast<size_t>(kQwsRing) * quad_ws_chunk(to_go) * kQwsPass * ns +
+                          static_cast<size_t>(quad_ws_ring(to_go, gen)) * quad_ws_chunk(to_go) * kQwsPass * ns +
                           (gen ? 2 * TM * 4 : 0) + (to_go ? (static_cast<size_t>(T) + 1) * ns : 0)) +
          grid_bytes;
 }
@@ -60,7 +61,8 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
                                                       float *__restrict__ part_rho = nullptr,
                                                       DF *__restrict__ part_eta = nullptr) {
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
-  constexpr int M = Quad::M, N = Quad::N, C = quad_ws_chunk(TOGO), R = kQwsRing, P = kQwsPass, NT = 3 * NS;
+  constexpr int M = Quad::M, N = Quad::N, C = quad_ws_chunk(TOGO), R = quad_ws_ring(TOGO, GEN), P = kQwsPass,
+                NT = 3 * NS;
   __shared__ uint64_t bar_noise[kQwsMaxChunks * kQwsChunk / C], bar_full[R], bar_empty[R];
   __shared__ float sx0[N];
   const int T = p.T, TM = T * M, tid = threadIdx.x;
