@@ -706,7 +706,8 @@ def run_ours(args, rank, world, local_rank):
     e2e_steps = args.e2e_steps or max(args.steps // 2, 10)
     x_host = np.asarray(cfg["x0"], dtype=np.float32)
     lat = []
-    for s in range(e2e_steps + 5):
+    e2e_warm = 50                                      # untimed steps before the measured ones
+    for s in range(e2e_steps + e2e_warm):
         with torch.cuda.stream(stream):
             flush.zero_()
         stream.synchronize()
@@ -714,7 +715,7 @@ def run_ours(args, rank, world, local_rank):
         ctrl.step_shift(x_host)
         lat.append(time.perf_counter() - t0)
     stream.synchronize()
-    lat = lat[5:]
+    lat = lat[e2e_warm:]
     e2e_total = reduce_max(sum(lat), dist, dev)
     e2e_value = whole_job_rate(K_SAMPLES * T_STEPS * e2e_steps, world, e2e_total)
 
