@@ -124,11 +124,15 @@ CAR_DEFAULTS = dict(
 
 def bilinear(M: np.ndarray, origin: float, h: float, X, Y):
     """Bilinear interpolation of grid M[iy][ix] (node (ix, iy) at origin + (ix, iy) h),
-    coordinates clamped to the grid."""
+    finite coordinates clamped to the grid.  The map has no value at a non-finite
+    position: NaN there, so that such a sample's cost is non-finite (weight 0)."""
     W = M.shape[1]
     Hn = M.shape[0]
-    fx = np.clip((X - origin) / h, 0.0, W - 1.0)
-    fy = np.clip((Y - origin) / h, 0.0, Hn - 1.0)
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    finite = np.isfinite(X) & np.isfinite(Y)
+    fx = np.clip((np.where(finite, X, origin) - origin) / h, 0.0, W - 1.0)
+    fy = np.clip((np.where(finite, Y, origin) - origin) / h, 0.0, Hn - 1.0)
     ix = np.minimum(np.floor(fx), W - 2).astype(np.int64)
     iy = np.minimum(np.floor(fy), Hn - 2).astype(np.int64)
     tx = fx - ix
@@ -138,7 +142,8 @@ def bilinear(M: np.ndarray, origin: float, h: float, X, Y):
     m10 = M[iy, ix + 1]
     m01 = M[iy + 1, ix]
     m11 = M[iy + 1, ix + 1]
-    return (1 - tx) * (1 - ty) * m00 + tx * (1 - ty) * m10 + (1 - tx) * ty * m01 + tx * ty * m11
+    val = (1 - tx) * (1 - ty) * m00 + tx * (1 - ty) * m10 + (1 - tx) * ty * m01 + tx * ty * m11
+    return np.where(finite, val, np.nan)
 
 
 class Car:

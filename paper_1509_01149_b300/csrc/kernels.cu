@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, 
 #pragma unroll
       for (int q = 0; q < NW; ++q) eta += s_e0[q];
       dbg->rho = vv;
-      dbg->kstar = ii;
+      dbg->kstar = (ii == INT_MAX) ? 0 : ii;  // every cost +inf: all tie at rho, the lowest k is 0
       dbg->eta = eta;
     }
   }

@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_rollout_mlp(const CtrlParams
         pend_ty = fy - static_cast<float>(iy);
         pend_row = env.map + static_cast<size_t>(iy) * env.map_w + ix;
         const float dv = x[3] - Car::v_target;
-        pend_speed = dv * dv;
+        pend_speed = fmaf(dv, dv, position_nan(x[0], x[1]));
         pend_is = is_cur;
         have_pend = true;
         v_cur[0] = v_nxt[0];

@@ -113,8 +113,13 @@ struct CartPoleVel {
 };
 
 // ---------------------------------------------------------------------------
+// +-0 for a finite position, NaN for a non-finite one.  The cost map has no value at a
+// non-finite position: adding this to the map term makes the sample's cost NaN (weight 0)
+// instead of the clamped edge value, and leaves every finite cost unchanged to the bit.
+__device__ __forceinline__ float position_nan(float X, float Y) { return fmaf(Y, 0.0f, X * 0.0f); }
+
 // Bilinear lookup of a cost map [H][W], node (ix, iy) at (ox + ix/inv_cell, oy + iy/inv_cell),
-// coordinates clamped to the grid (NaN clamps to node 0).
+// finite coordinates clamped to the grid; NaN at a non-finite coordinate.
 __device__ __forceinline__ float map_bilinear(const Env &e, float X, float Y) {
   const float fx = fminf(fmaxf((X - e.map_ox) * e.map_inv_cell, 0.0f), static_cast<float>(e.map_w - 1));
   const float fy = fminf(fmaxf((Y - e.map_oy) * e.map_inv_cell, 0.0f), static_cast<float>(e.map_h - 1));
@@ -127,7 +132,7 @@ __device__ __forceinline__ float map_bilinear(const Env &e, float X, float Y) {
   const float m01 = __ldg(row + e.map_w), m11 = __ldg(row + e.map_w + 1);
   const float a = m00 + tx * (m10 - m00);
   const float b = m01 + tx * (m11 - m01);
-  return a + ty * (b - a);
+  return (a + ty * (b - a)) + position_nan(X, Y);
 }
 
 struct Car {
@@ -279,7 +284,7 @@ struct Car {
     pd.m01 = __ldg(row + e.map_w);
     pd.m11 = __ldg(row + e.map_w + 1);
     const float dv = x[3] - v_target;
-    pd.speed = dv * dv;
+    pd.speed = fmaf(dv, dv, position_nan(x[0], x[1]));
     return pd;
   }
   __device__ __forceinline__ static float cost_finish(const Pending &pd, const Env &) {

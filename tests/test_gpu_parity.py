@@ -199,6 +199,38 @@ def test_zero_noise_leaves_controls_unchanged(N):
     assert np.array_equal(g["U"], np.full((20, 2), 0.1, dtype=np.float32))
 
 
+# a state component that enters every system's running cost q: a NaN there makes every path
+# cost non-finite (the car's position only indexes the clamped cost map, so its speed is taken)
+_NAN_COMPONENT = {W.CARTPOLE: 0, W.CAR: 3, W.QUAD: 3, W.CARTPOLE_VEL: 0}
+
+
+@pytest.mark.parametrize("system", [W.CARTPOLE, W.CAR, W.QUAD, W.CARTPOLE_VEL])
+@pytest.mark.parametrize("to_go", [False, True])
+def test_non_finite_state_leaves_the_controls_unchanged(N, system, to_go):
+    """The degenerate case of the weighting: with a NaN state every cost is non-finite, so in
+    the oracle rho = +inf, k* = 0, eta = 0 and every weight is 0.  The kernels agree: costs
+    reported as +inf, k* = 0, a zero update, U unchanged bit for bit and u0 its first row."""
+    cfg = W.config(system, K=777, T=23)
+    rng = np.random.default_rng(7)
+    U0 = (np.asarray(cfg["U"]) + 0.1 * rng.standard_normal(np.shape(cfg["U"]))).astype(np.float32)
+    x0 = np.asarray(cfg["x0"], np.float32).copy()
+    x0[_NAN_COMPONENT[system]] = np.nan
+    cfg = dict(cfg, U=U0, x0=x0)
+    o = P.oracle_iteration_to_go(cfg) if to_go else P.oracle_iteration(cfg)
+    assert not np.isfinite(o.S).any() and np.all(o.dU == 0.0)
+    c = P.make_controller(cfg)
+    if to_go:
+        c.set_weighting(N.MPPI_WEIGHT_TO_GO)
+    u0 = c.step(x0)
+    g = c.get_debug()
+    assert np.all(g["S"] == np.inf)
+    assert g["kstar"] == 0 and g["eta"] == 0.0
+    assert np.all(g["dU"] == 0.0)
+    assert np.array_equal(c.get_controls(), U0)
+    assert np.array_equal(u0, U0[0])
+    c.close()
+
+
 def test_step_without_env_is_a_state_error(N):
     c = N.Controller(N.MPPI_CAR, 64, 10, 0.02, 10.0, 1.0, np.diag([0.3, 0.35]))
     with pytest.raises(N.MppiError) as ei:

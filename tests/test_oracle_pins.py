@@ -183,6 +183,18 @@ def test_bilinear_exact_on_bilinear_functions_and_clamped():
     assert systems.bilinear(M, 0.0, 0.5, np.array([9.0]), np.array([99.0]))[0] == pytest.approx(f(3.5, 3.5))
 
 
+def test_bilinear_is_nan_at_a_non_finite_position():
+    """The map has no value at a non-finite position: NaN there (the sample's cost is then
+    non-finite and its weight 0), the finite positions of the same call unaffected."""
+    f = lambda X, Y: 3.0 + 2.0 * X - 0.5 * Y + 0.25 * X * Y
+    M = _flat_map(8, 0.5, f)
+    X = np.array([1.0, np.nan, 1.0, np.inf, -np.inf, 2.25])
+    Y = np.array([np.nan, 1.0, -np.inf, 1.0, 2.0, 1.5])
+    out = systems.bilinear(M, 0.0, 0.5, X, Y)
+    assert np.all(np.isnan(out[:5]))
+    assert out[5] == pytest.approx(f(2.25, 1.5), abs=1e-12)
+
+
 def test_bilinear_error_bound_on_paper_ellipse_cost():
     """The race-car cost of Sec. V-B, 100 d^2 with d = |(x/13)^2+(y/6)^2-1|, sampled on a grid:
     bilinear lookup stays within the interpolation bound h^2/8 (|f_xx| + |f_yy|) + h^2/4 |f_xy|."""
