@@ -25,6 +25,7 @@ import json
 import math
 import os
 import statistics
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -120,6 +121,8 @@ class ClockSampler:
         cmd = ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "20"]
         if gpu_id:
             cmd += ["-i", gpu_id]
+        if shutil.which("stdbuf"):
+            cmd = ["stdbuf", "-oL"] + cmd     # line-buffered: no sample left in a buffer at stop()
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
@@ -136,19 +139,40 @@ class ClockSampler:
     def mark_end(self):
         self.t1 = time.time()
 
+    @staticmethod
+    def _stamp(stamp: str):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def _inside(self, stamp: str) -> bool:
         if self.t0 is None or self.t1 is None:
             return True
+        t = self._stamp(stamp)
+        return True if t is None else self.t0 <= t <= self.t1
+
+    def _past_end(self) -> bool:
+        """True once the file holds a sample stamped after mark_end()."""
         try:
-            import datetime
-            t = datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
-        except ValueError:
-            return True
-        return self.t0 <= t <= self.t1
+            with open(self.path) as f:
+                lines = f.read().splitlines()
+        except OSError:
+            return False
+        for line in reversed(lines):
+            t = self._stamp(line.split(",")[0].strip())
+            if t is not None:
+                return t > self.t1
+        return False
 
     def stop(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        if self.t1 is not None:   # every sample of the timed region written before the stop
+            deadline = time.time() + 3.0
+            while time.time() < deadline and not self._past_end():
+                time.sleep(0.02)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
