@@ -180,7 +180,7 @@ __global__ void k_apply(const float *__restrict__ xs, const float *__restrict__ 
   xn[idx] = xs[idx] + Y[static_cast<size_t>(i) * kOut + j] * out_scale[j];
 }
 
-// the analytic car step (the learned model's fallback and judge)
+// the analytic car step (the learned model's fallback and the yardstick of its error)
 __global__ void k_analytic_step(const float *__restrict__ xs, const float *__restrict__ us, int n, float dt,
                                 float *__restrict__ xn) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -225,7 +225,7 @@ def _closed_loop(N, ctl, c, steps, plant):
 def test_trained_network_gains_over_the_untrained_one(env, trained):
     """Closed loop on the true (analytic FP64) plant, 60 control steps at 50 Hz: MPPI whose
     rollouts use the trained network drives the car far better than the same MPPI with
-    the untrained network, and comes close to MPPI with the analytic model (the judge).
+    the untrained network, and comes close to MPPI with the analytic model (the yardstick).
     Measured with a shorter training run: 6.3 (trained) vs 89.8 (untrained) vs 1.8 (analytic)
     average running cost."""
     torch, N = env
