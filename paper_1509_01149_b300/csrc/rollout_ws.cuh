@@ -46,6 +46,29 @@ __host__ __device__ inline size_t car_ws_smem_bytes(int T, int ns, bool to_go = 
                           (to_go ? (static_cast<size_t>(T) + 1) * ns : 0) + (gen ? 2 * TM * 2 : 0));
 }
 
+// The car's velocity state (vx, vy, r, delta), passed by value.
+struct CarVel {
+  float x[4];
+};
+
+// Steps i0 .. i0+n-1 of the velocity recurrence in the arctangent form (Car::vel_step) from x,
+// controls u_i + du_i re-read from shared memory, velocities stored to the ring slot: the
+// rare redo of a chunk whose slip ratios left their domain.  Not inlined, so that the hot
+// loop's code holds only the call.
+static __device__ __noinline__ CarVel car_vel_chunk_atan(CarVel x, const float *sU, const float *sDu, float *vel, int i0,
+                                                        int n, int NS, int slot, float dt) {
+  constexpr int M = Car::M;
+  for (int j = 0; j < n; ++j) {
+    const int i = i0 + j;
+    const float v[M] = {sU[i * M] + sDu[(i * M) * NS + slot], sU[i * M + 1] + sDu[(i * M + 1) * NS + slot]};
+    Car::vel_step(x.x, v, dt);
+    vel[(3 * j) * NS + slot] = x.x[0];
+    vel[(3 * j + 1) * NS + slot] = x.x[1];
+    vel[(3 * j + 2) * NS + slot] = x.x[2];
+  }
+  return x;
+}
+
 template <int NS, bool TOGO = false, bool GEN = false>
 __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const float *__restrict__ x0, uint32_t ctr,
                                                      const float *__restrict__ U, int k0, float *__restrict__ S_out,
@@ -122,12 +145,22 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
           vv[j][0] = sU[i * M] + sDu[(i * M) * NS + slot];
           vv[j][1] = sU[i * M + 1] + sDu[(i * M + 1) * NS + slot];
         }
+        // the chunk through the slip ratios; a lane that leaves their domain (rare: an extreme
+        // slide or steering angle) redoes the chunk from its start with the arctangent form,
+        // under a warp vote so that the common case carries no second path
+        const float xs[4] = {xv[0], xv[1], xv[2], xv[3]};
+        bool in = true;
 #pragma unroll
         for (int j = 0; j < C; ++j) {
-          Car::vel_step(xv, vv[j], p.dt);
+          in &= Car::vel_step_ratio(xv, vv[j], p.dt);
           vel[(3 * j) * NS + slot] = xv[0];
           vel[(3 * j + 1) * NS + slot] = xv[1];
           vel[(3 * j + 2) * NS + slot] = xv[2];
+        }
+        if (__any_sync(__activemask(), !in) && !in) {
+          const CarVel r = car_vel_chunk_atan(CarVel{{xs[0], xs[1], xs[2], xs[3]}}, sU, sDu, vel, i0, C, NS, slot, p.dt);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xv[q] = r.x[q];
         }
       } else {
 #pragma unroll 1

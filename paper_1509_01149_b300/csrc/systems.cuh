@@ -156,10 +156,6 @@ struct Car {
   // itself and the control, and the pose rates (X, Y, psi), which read the velocities but
   // never feed back into them.
   //
-  // The steering angle stays small, where the special-function-unit sine/cosine are
-  // accurate to about 2^-21 absolute: they run as single SFU operations with no slow-path
-  // branch.
-  //
   // The shape sin(C atan z), z = B alpha, is evaluated on the whole real line through
   // v = |z| / (1 + |z|) in [0, 1], where it is analytic: sign(z) v P(v) / Q(v), a rational
   // fitted towards minimax (maximum absolute error 3.0e-7 in exact arithmetic, ~6.5e-7 in
@@ -183,20 +179,104 @@ struct Car {
     Q = fmaf(Q, v, 1.000000000e+00f);
     return copysignf(__fdividef(v * P, Q), z);
   }
+  // The same force as a function of t = tan(alpha) = n / d (d > 0, so |alpha| < pi/2):
+  // sin(C atan(B atan t)) = sign(n) v P(v) / Q(v) with v = |t| / (1 + |t|) = |n| / (|n| + d),
+  // P and Q of degree 6 fitted like tyre_shape (maximum error 2.5e-7 in exact arithmetic,
+  // ~4.5e-7 in FP32; tyre_shape_fit.py prints the coefficients).  Given the slip angle as a
+  // ratio, no arctangent and no reciprocal of the speed are needed.
+  __device__ __forceinline__ static float slip_shape(float n, float d) {
+    const float an = fabsf(n);
+    const float v = __fdividef(an, an + d);
+    float P = 8.201814610e+00f;
+    P = fmaf(P, v, 6.672181936e+01f);
+    P = fmaf(P, v, 3.717660575e+01f);
+    P = fmaf(P, v, 4.971201143e+00f);
+    P = fmaf(P, v, 2.782720545e+01f);
+    P = fmaf(P, v, 1.013812583e+01f);
+    P = fmaf(P, v, 7.200033913e+00f);
+    float Q = 2.088930100e+02f;
+    Q = fmaf(Q, v, -5.017322148e+01f);
+    Q = fmaf(Q, v, 8.035395784e+01f);
+    Q = fmaf(Q, v, 3.080427926e+01f);
+    Q = fmaf(Q, v, 1.677532802e+01f);
+    Q = fmaf(Q, v, 4.081411398e-01f);
+    Q = fmaf(Q, v, 1.000000000e+00f);
+    return copysignf(__fdividef(v * P, Q), n);
+  }
+  // The shape sin(C atan(B theta)) of a slip angle of magnitude theta in [0, pi] given as a
+  // direction (n, d), a positive multiple of (sin alpha, cos alpha), signed like n.  Through the
+  // half-angle tangent tau = tan(theta / 2) = |n| / (rho + d) = (rho - d) / |n|, rho = |(n, d)|
+  // (the first form for d >= 0, the second for d < 0: neither cancels),
+  // v = tau / (1 + tau) = num / (|n| + rho + |d|), and v P(v) / Q(v) with P and Q of degree 7
+  // fitted like tyre_shape (maximum error 3.5e-8 in exact arithmetic, ~2.7e-7 in FP32;
+  // tyre_shape_fit.py prints the coefficients).  One square root and two reciprocals on the
+  // special-function unit, no arctangent.  (n, d) is finite and not (0, 0).
+  __device__ __forceinline__ static float angle_shape(float n, float d) {
+    const float an = fabsf(n), ad = fabsf(d);
+    const float q = fmaf(n, n, d * d);
+    const float rho = q * rsqrtf(q);
+    const float num = d >= 0.0f ? an : rho + ad;
+    const float v = __fdividef(num, (an + rho) + ad);
+    float P = -8.540411824e+01f;
+    P = fmaf(P, v, 1.562593909e+03f);
+    P = fmaf(P, v, -4.858328297e+02f);
+    P = fmaf(P, v, 1.212054441e+03f);
+    P = fmaf(P, v, -4.118799750e+02f);
+    P = fmaf(P, v, 5.340800569e+02f);
+    P = fmaf(P, v, 2.681955798e+01f);
+    P = fmaf(P, v, 1.439997149e+01f);
+    float Q = 2.627731536e+03f;
+    Q = fmaf(Q, v, 1.923390719e+03f);
+    Q = fmaf(Q, v, -1.496429105e+03f);
+    Q = fmaf(Q, v, 2.121401013e+03f);
+    Q = fmaf(Q, v, 9.330799874e+01f);
+    Q = fmaf(Q, v, 9.149840455e+01f);
+    Q = fmaf(Q, v, 8.619579532e-01f);
+    Q = fmaf(Q, v, 1.000000000e+00f);
+    return copysignf(__fdividef(v * P, Q), n);
+  }
+  // Velocity rates from the two lateral forces (shared by both step forms below).
+  __device__ __forceinline__ static void vel_rates(float vx, float vy, float r, float delta, const float v[M],
+                                                   float Fyf, float Fyr, float sd, float cd, float d[4]) {
+    const float Fx = Cm * v[1] - Crr * vx - Cd * vx * fabsf(vx);
+    d[0] = (Fx - Fyf * sd) * (1.0f / m) + vy * r;
+    d[1] = (Fyr + Fyf * cd) * (1.0f / m) - vx * r;
+    d[2] = (lf * Fyf * cd - lr * Fyr) * (1.0f / Iz);
+    d[3] = (delta_max * v[0] - delta) * (1.0f / tau_delta);
+  }
+  // The steering angle's sine and cosine run on the special-function unit (about 2^-21
+  // absolute for |delta| < pi), as single operations with no slow-path branch.
   __device__ __forceinline__ static void deriv_vel(float vx, float vy, float r, float delta, const float v[M],
                                                    float d[4]) {
     const float inv_vxs = __fdividef(1.0f, fmaxf(vx, vx_floor));
     const float alpha_f = delta - atanf((vy + lf * r) * inv_vxs);
     const float alpha_r = -atanf((vy - lr * r) * inv_vxs);
-    const float Fyf = Df * tyre_shape(B * alpha_f);
-    const float Fyr = Dr * tyre_shape(B * alpha_r);
-    const float Fx = Cm * v[1] - Crr * vx - Cd * vx * fabsf(vx);
     float sd, cd;
     __sincosf(delta, &sd, &cd);
-    d[0] = (Fx - Fyf * sd) * (1.0f / m) + vy * r;
-    d[1] = (Fyr + Fyf * cd) * (1.0f / m) - vx * r;
-    d[2] = (lf * Fyf * cd - lr * Fyr) * (1.0f / Iz);
-    d[3] = (delta_max * v[0] - delta) * (1.0f / tau_delta);
+    vel_rates(vx, vy, r, delta, v, Df * tyre_shape(B * alpha_f), Dr * tyre_shape(B * alpha_r), sd, cd, d);
+  }
+  // The same rates with no arctangent and no reciprocal of the speed on the recurrence's
+  // critical path.  Rear: alpha_r = -atan((vy - lr r) / vxs), so tan(alpha_r) =
+  // (lr r - vy) / vxs with vxs >= 1 > 0 (slip_shape).  Front: alpha_f = delta - phi,
+  // phi = atan(w / vxs) in (-pi/2, pi/2), w = vy + lf r; by the angle difference
+  // (n, d) = (vxs sin(delta) - w cos(delta), vxs cos(delta) + w sin(delta)) is a positive
+  // multiple of (sin alpha_f, cos alpha_f), so angle_shape(n, d) is the force of the angle
+  // wrapped into [-pi, pi].  That is alpha_f itself when |delta| < 1.5 (< pi/2, so
+  // |alpha_f| < pi), and when |delta| < 3 (< pi, so |alpha_f| < 3 pi/2) with n of delta's
+  // sign (alpha_f in (delta - pi/2, delta + pi/2) wraps only past +-pi, which flips the sign
+  // of n).  Returns false outside that domain (a slip angle past +-pi, a steering angle of
+  // 3 rad or more, or a NaN), where the rates are not valid and the caller takes deriv_vel.
+  __device__ __forceinline__ static bool deriv_vel_ratio(float vx, float vy, float r, float delta, const float v[M],
+                                                         float d[4]) {
+    const float vxs = fmaxf(vx, vx_floor);
+    float sd, cd;
+    __sincosf(delta, &sd, &cd);
+    const float w = fmaf(lf, r, vy);
+    const float nf = fmaf(sd, vxs, -(w * cd));
+    const float df = fmaf(cd, vxs, w * sd);
+    vel_rates(vx, vy, r, delta, v, Df * angle_shape(nf, df), Dr * slip_shape(fmaf(lr, r, -vy), vxs), sd, cd, d);
+    const float ad = fabsf(delta);
+    return ad < 1.5f || (ad < 3.0f && nf * delta > 0.0f);
   }
   // The heading is unbounded: it is first reduced to [-pi, pi] by the two-constant
   // Cody-Waite scheme (k = nearest integer to psi / 2 pi; psi - k hi - k lo with
@@ -248,6 +328,14 @@ struct Car {
     deriv_vel(xv[0], xv[1], xv[2], xv[3], v, d);
 #pragma unroll
     for (int i = 0; i < 4; ++i) xv[i] += dt * d[i];
+  }
+  // vel_step through deriv_vel_ratio; false (xv not valid) outside the ratio's domain.
+  __device__ __forceinline__ static bool vel_step_ratio(float xv[4], const float v[M], float dt) {
+    float d[4];
+    const bool in = deriv_vel_ratio(xv[0], xv[1], xv[2], xv[3], v, d);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xv[i] += dt * d[i];
+    return in;
   }
   // pose (X, Y, psi) over one step from the velocities (vx, vy, r) at the step's start
   __device__ __forceinline__ static void pose_step(float &X, float &Y, float &psi, Aux &a, float vx, float vy, float r,
