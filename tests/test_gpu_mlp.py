@@ -120,8 +120,8 @@ def trained(env):
     dx, du = torch.tensor(xs).cuda(), torch.tensor(us).cuda()
     net = N.MLP(3)
     net.set_data(dx.data_ptr(), du.data_ptr(), 1 << 20, 0.02)
-    net.train(2500, 8192, 2e-3, seed=5)
-    net.train(1000, 8192, 5e-4, seed=6)
+    net.train(5000, 8192, 2e-3, seed=5)
+    net.train(2000, 8192, 5e-4, seed=6)
     params, scale = net.get_params()
     net.close()
     return params, scale
@@ -223,31 +223,36 @@ def _closed_loop(N, ctl, c, steps, plant):
 
 
 def test_trained_network_gains_over_the_untrained_one(env, trained):
-    """Closed loop on the true (analytic FP64) plant, 60 control steps at 50 Hz: MPPI whose
-    rollouts use the trained network drives the car far better than the same MPPI with
-    the untrained network, and comes close to MPPI with the analytic model (the yardstick).
-    Measured with a shorter training run: 6.3 (trained) vs 89.8 (untrained) vs 1.8 (analytic)
-    average running cost."""
+    """Closed loop on the true (analytic FP64) plant, 60 control steps at 50 Hz, averaged over
+    three MPPI noise seeds: MPPI whose rollouts use the trained network drives the car far
+    better than the same MPPI with the untrained network, and comes close to MPPI with the
+    analytic model (the yardstick).  Training is not bit-reproducible (split-K atomics) and the
+    closed loop is chaotic in the weights, so one seed's cost varies from run to run: four
+    trainings of this length measured 0.74-1.13 times the analytic model's mean cost, against
+    1.15-2.44 after half the training (and 6.0 for one seed once)."""
     torch, N = env
     params, scale = trained
     plant = osys.Car(0.02, W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL)
-    K, T, steps = 2048, 50, 60
-    ctl, c = _mlp_ctrl(N, N.mlp_blob(params, scale), K, T)
-    learned = _closed_loop(N, ctl, c, steps, plant)
-    ctl.close()
+    K, T, steps, seeds = 2048, 50, 60, (0, 1, 2)
+    from tests import parity as P
+
+    def mean_cost(make):
+        costs = []
+        for seed in seeds:
+            ctl, c = make()
+            ctl.set_seed(seed)
+            costs.append(_closed_loop(N, ctl, c, steps, plant))
+            ctl.close()
+        return float(np.mean(costs))
+    learned = mean_cost(lambda: _mlp_ctrl(N, N.mlp_blob(params, scale), K, T))
     raw = N.MLP(77)
     p0, _ = raw.get_params()
     raw.close()
-    ctl, c = _mlp_ctrl(N, N.mlp_blob(p0, scale), K, T)
-    untrained = _closed_loop(N, ctl, c, steps, plant)
-    ctl.close()
-    from tests import parity as P
-    c = W.config(W.CAR, K=K, T=T, U=np.zeros((T, 2)))
-    ctl = P.make_controller(c)
-    analytic = _closed_loop(N, ctl, c, steps, plant)
-    ctl.close()
+    untrained = mean_cost(lambda: _mlp_ctrl(N, N.mlp_blob(p0, scale), K, T))
+    cfg = W.config(W.CAR, K=K, T=T, U=np.zeros((T, 2)))
+    analytic = mean_cost(lambda: (P.make_controller(cfg), cfg))
     assert learned < 0.25 * untrained, (learned, untrained, analytic)
-    assert learned < 4.0 * analytic, (learned, untrained, analytic)
+    assert learned < 3.0 * analytic, (learned, untrained, analytic)
 
 
 def test_fp8_iteration_matches_the_e4m3_oracle(env, trained):

@@ -116,8 +116,9 @@ def test_quad_iteration(N):
 
 
 @pytest.mark.parametrize("system,K,T", [(W.CARTPOLE, 1, 1), (W.CARTPOLE, 33, 3), (W.CARTPOLE, 129, 7),
-                                        (W.CAR, 65, 1), (W.CAR, 200, 5), (W.CAR, 1000, 9), (W.CAR, 300, 17),
-                                        (W.CAR, 257, 33), (W.QUAD, 63, 2), (W.QUAD, 130, 9)])
+                                        (W.CAR, 1, 1), (W.CAR, 65, 1), (W.CAR, 200, 5), (W.CAR, 1000, 9),
+                                        (W.CAR, 300, 17), (W.CAR, 257, 33), (W.QUAD, 1, 1), (W.QUAD, 63, 2),
+                                        (W.QUAD, 130, 9), (W.CARTPOLE_VEL, 1, 1), (W.CARTPOLE_VEL, 97, 11)])
 def test_ragged_sizes(N, system, K, T):
     cfg = W.config(system, K=K, T=T)
     for impl in (0, 1):
