@@ -108,13 +108,42 @@ _REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_pow
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons every 20 ms.  Started ahead of the timed region
-    (it waits for the first sample), it keeps the samples whose timestamps fall between
-    mark_start() and mark_end() (host wall clock around the timed region)."""
+    """SM clocks and throttle reasons during the timed region.  An NVML thread (read-only
+    queries) samples every 2 ms between mark_start() and mark_end(), so that a short timed
+    region still has a record; nvidia-smi runs beside it every 20 ms (started ahead of the
+    timed region, waiting for its first sample) and is the record where NVML is unavailable,
+    keeping the samples whose timestamps fall between the marks."""
 
     def __init__(self, gpu_id: str | None, settle_s: float = 2.0):
         self.path = tempfile.mktemp(suffix=".csv")
         self.t0 = self.t1 = None
+        self.nvml_rows, self.nvml_on, self.nvml_stop, self.nvml_thread = [], False, False, None
+        try:
+            import threading
+            import pynvml as nv
+            nv.nvmlInit()
+            h = nv.nvmlDeviceGetHandleByUUID(gpu_id) if gpu_id else nv.nvmlDeviceGetHandleByIndex(0)
+            bits = {"hw_slowdown": nv.nvmlClocksEventReasonHwSlowdown,
+                    "hw_thermal_slowdown": nv.nvmlClocksEventReasonHwThermalSlowdown,
+                    "sw_thermal_slowdown": nv.nvmlClocksEventReasonSwThermalSlowdown,
+                    "sw_power_cap": nv.nvmlClocksEventReasonSwPowerCap}
+
+            def loop():
+                while not self.nvml_stop:
+                    if self.nvml_on:
+                        try:
+                            why = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                            self.nvml_rows.append(dict(
+                                sm=float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)),
+                                smax=float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)),
+                                reasons={r: bool(why & b) for r, b in bits.items()}))
+                        except Exception:
+                            pass
+                    time.sleep(0.002)
+            self.nvml_thread = threading.Thread(target=loop, daemon=True)
+            self.nvml_thread.start()
+        except Exception:
+            self.nvml_thread = None
         q = ("timestamp,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -135,8 +164,10 @@ class ClockSampler:
 
     def mark_start(self):
         self.t0 = time.time()
+        self.nvml_on = True
 
     def mark_end(self):
+        self.nvml_on = False
         self.t1 = time.time()
 
     @staticmethod
@@ -167,6 +198,19 @@ class ClockSampler:
         return False
 
     def stop(self):
+        if self.nvml_thread is not None:
+            self.nvml_stop = True
+            self.nvml_thread.join(timeout=2)
+        smi = self._stop_smi()
+        rows = self.nvml_rows
+        if not rows:
+            return dict(smi, source="nvidia-smi")
+        reasons = sorted({r for row in rows for r, on in row["reasons"].items() if on})
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": reasons, "samples": len(rows), "source": "nvml, every 2 ms",
+                "nvidia_smi": {k: smi.get(k) for k in ("sm_mhz", "reasons", "samples")}}
+
+    def _stop_smi(self):
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         if self.t1 is not None:   # every sample of the timed region written before the stop

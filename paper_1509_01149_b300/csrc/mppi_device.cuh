@@ -44,14 +44,17 @@ __device__ __forceinline__ float unit_uniform(uint32_t w) {
 
 // Box-Muller on one pair of words: rad = sqrt(-2 ln ua), angle 2 pi ub.  The radicand is at
 // least 2^-23 (ua <= 1 - 2^-24), a normal number, so the square root is taken as s * rsqrt(s)
-// (a few ulp, no special-case branch).
+// (a few ulp, no special-case branch).  The angle is taken half a turn back,
+// 2 pi (ub - 1/2) in [-pi, pi) (ub - 1/2 is exact), where the special-function-unit sine and
+// cosine are accurate to about 2^-21 absolute: cos(2 pi ub) = -cos(2 pi (ub - 1/2)), and the
+// same for the sine.  The normals are then within ~rad * 6e-7 absolute.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float &e0, float &e1) {
   const float s2 = -2.0f * logf(unit_uniform(wa));
   const float rad = s2 * rsqrtf(s2);
   float s, c;
-  sincospif(2.0f * unit_uniform(wb), &s, &c);
-  e0 = rad * c;
-  e1 = rad * s;
+  __sincosf(6.28318530717958648f * (unit_uniform(wb) - 0.5f), &s, &c);
+  e0 = -rad * c;
+  e1 = -rad * s;
 }
 
 // Four standard normals of Philox block (b, k, counter, gid).

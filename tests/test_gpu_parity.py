@@ -44,8 +44,9 @@ def test_noise_matches_oracle(N, system):
     du = c.get_noise(3)
     want = P.noise_oracle(cfg, 3)
     scale = P.control_scale(cfg)[None, :, None]
-    # FP32 log/sqrt/sincospi (a few ulp each) against FP64
-    assert np.all(np.abs(du - want) <= 4e-6 * np.abs(want) + 1e-6 * scale)
+    # FP32 log and square root (a few ulp each) and the special-function-unit sine and cosine
+    # (about 2^-21 absolute, times a radius of at most ~5.6) against FP64
+    assert np.all(np.abs(du - want) <= 4e-6 * np.abs(want) + 4e-6 * scale)
 
 
 # ---------------------------------------------------------------------------
