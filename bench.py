@@ -107,6 +107,47 @@ KERNEL_SOURCES = {
 _REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
 
+# NVML clock-event reason bits (nvml.h: nvmlClocksEventReason*)
+_REASON_BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
+
+
+def _nvml_clock_reader(gpu_id: str | None):
+    """A function returning (SM clock MHz, max SM clock MHz, clock-event reason bits) of the GPU
+    from NVML's read-only queries (the Python bindings, else the driver's libnvidia-ml through
+    ctypes), or None where NVML is unavailable."""
+    try:
+        import pynvml as nv
+        nv.nvmlInit()
+        h = nv.nvmlDeviceGetHandleByUUID(gpu_id) if gpu_id else nv.nvmlDeviceGetHandleByIndex(0)
+        return lambda: (nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM), nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM),
+                        nv.nvmlDeviceGetCurrentClocksEventReasons(h))
+    except Exception:
+        pass
+    try:
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = C.c_void_p()
+        rc = (lib.nvmlDeviceGetHandleByUUID(gpu_id.encode(), C.byref(h)) if gpu_id else
+              lib.nvmlDeviceGetHandleByIndex_v2(0, C.byref(h)))
+        if rc != 0:
+            return None
+        sm, smax, why = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+        def read():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, C.byref(sm)) or lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(smax))
+                    or reasons(h, C.byref(why))):
+                raise RuntimeError("NVML query failed")
+            return sm.value, smax.value, why.value
+        read()
+        return read
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """SM clocks and throttle reasons during the timed region.  An NVML thread (read-only
     queries) samples every 2 ms between mark_start() and mark_end(), so that a short timed
@@ -118,32 +159,22 @@ class ClockSampler:
         self.path = tempfile.mktemp(suffix=".csv")
         self.t0 = self.t1 = None
         self.nvml_rows, self.nvml_on, self.nvml_stop, self.nvml_thread = [], False, False, None
-        try:
+        read = _nvml_clock_reader(gpu_id)
+        if read is not None:
             import threading
-            import pynvml as nv
-            nv.nvmlInit()
-            h = nv.nvmlDeviceGetHandleByUUID(gpu_id) if gpu_id else nv.nvmlDeviceGetHandleByIndex(0)
-            bits = {"hw_slowdown": nv.nvmlClocksEventReasonHwSlowdown,
-                    "hw_thermal_slowdown": nv.nvmlClocksEventReasonHwThermalSlowdown,
-                    "sw_thermal_slowdown": nv.nvmlClocksEventReasonSwThermalSlowdown,
-                    "sw_power_cap": nv.nvmlClocksEventReasonSwPowerCap}
 
             def loop():
                 while not self.nvml_stop:
                     if self.nvml_on:
                         try:
-                            why = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
-                            self.nvml_rows.append(dict(
-                                sm=float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)),
-                                smax=float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM)),
-                                reasons={r: bool(why & b) for r, b in bits.items()}))
+                            sm, smax, why = read()
+                            self.nvml_rows.append(dict(sm=float(sm), smax=float(smax),
+                                                       reasons={r: bool(why & b) for r, b in _REASON_BITS.items()}))
                         except Exception:
                             pass
                     time.sleep(0.002)
             self.nvml_thread = threading.Thread(target=loop, daemon=True)
             self.nvml_thread.start()
-        except Exception:
-            self.nvml_thread = None
         q = ("timestamp,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
