@@ -257,10 +257,8 @@ def test_car_linear_bicycle_steady_turn():
     car = _car()
     p = car.p
     vx, delta = 5.0, 0.002
-    L = p["lf"] + p["lr"]
-    Df = p["mu"] * p["m"] * p["g"] * p["lr"] / L
-    Dr = p["mu"] * p["m"] * p["g"] * p["lf"] / L
-    Cf, Cr = p["B"] * p["C"] * Df, p["B"] * p["C"] * Dr
+    Nf, Nr = _static_loads(p)                   # axle loads from the static moment balance
+    Cf, Cr = p["B"] * p["C"] * p["mu"] * Nf, p["B"] * p["C"] * p["mu"] * Nr
     m, Iz, lf, lr = p["m"], p["Iz"], p["lf"], p["lr"]
     # m (vy' + vx r) = Fyf + Fyr ;  Iz r' = lf Fyf - lr Fyr ; linear tyres
     A = np.array([[-(Cf + Cr) / vx, -(Cf * lf - Cr * lr) / vx - m * vx],
@@ -273,6 +271,175 @@ def test_car_linear_bicycle_steady_turn():
     assert abs(d[4, 0]) < 2e-4 * scale_vy      # residual is the tyre nonlinearity, O(delta^3)
     assert abs(d[5, 0]) < 2e-4 * scale_r
     assert abs(d[6, 0]) < 1e-12
+
+
+# --- the car's rigid-body rows, tyre saturation and static load split -----------------------
+# These fix the rows that the straight-line, mirror and steady-turn pins leave free: the
+# body-frame couplings (+vy r in vx', -vx r in vy'), the steering projection of the front
+# force (-Fyf sin(delta), Fyf cos(delta)), the front/rear static loads and the tyre's peak.
+def _world_rot(a):
+    """2x2 rotation by angle a, from the library's 3-D rotation about z."""
+    return Rotation.from_euler("z", a).as_matrix()[:2, :2]
+
+
+def _pin_car_newton_euler(car, n=64, seed=11):
+    """Newton's and Euler's laws in the inertial frame: the mass times the world-frame
+    acceleration of the centre of gravity equals the sum of the contact forces, each
+    rotated into the world frame by its own direction (the front tyre's lateral force is
+    normal to the steered wheel, the rear's normal to the body, the drive force along the
+    body), and the yaw inertia times r' equals the moment of those forces about the centre
+    of gravity (np.cross of lever arm and force).  The world-frame acceleration is formed
+    from deriv()'s body-frame rows by the product rule d/dt (Rot(psi) v_b)."""
+    p = car.p
+    rng = np.random.default_rng(seed)
+    for _ in range(n):
+        x = np.array([rng.uniform(-5, 5), rng.uniform(-5, 5), rng.uniform(-3, 3), rng.uniform(0.5, 9),
+                      rng.uniform(-2, 2), rng.uniform(-2, 2), rng.uniform(-0.45, 0.45)])[:, None]
+        v = rng.normal(0, 1, (2, 1))
+        d = car.deriv(x, v)[:, 0]
+        X = x[:, 0]
+        psi, vx, vy, r, delta = X[2], X[3], X[4], X[5], X[6]
+        Fyf, Fyr = (float(f[0]) for f in car.tyre_forces(x))
+        Fx = p["Cm"] * v[1, 0] - p["Crr"] * vx - p["Cd"] * vx * abs(vx)
+        Rp = _world_rot(psi)
+        # kinematics: world velocity is the body velocity rotated by the heading; psi' = r
+        assert np.allclose(d[0:2], Rp @ [vx, vy], rtol=1e-12, atol=1e-12)
+        assert d[2] == pytest.approx(r, rel=1e-12, abs=1e-12)
+        # Newton: m d/dt (Rot(psi) v_b) = sum of world-frame forces
+        dRp = _world_rot(psi + 0.5 * math.pi)       # d Rot(psi) / d psi
+        acc_world = Rp @ d[3:5] + r * (dRp @ [vx, vy])
+        F_world = (Rp @ [Fx, 0.0] + _world_rot(psi + delta) @ [0.0, Fyf] + Rp @ [0.0, Fyr])
+        scale = abs(Fx) + abs(Fyf) + abs(Fyr) + 1.0
+        assert np.allclose(p["m"] * acc_world, F_world, rtol=0, atol=1e-11 * scale)
+        # Euler (yaw): Iz r' = moments about the centre of gravity of the contact forces
+        f_front = np.r_[_world_rot(delta) @ [0.0, Fyf], 0.0]
+        f_rear = np.array([Fx, Fyr, 0.0])
+        Mz = np.cross([p["lf"], 0.0, 0.0], f_front)[2] + np.cross([-p["lr"], 0.0, 0.0], f_rear)[2]
+        assert p["Iz"] * d[5] == pytest.approx(Mz, rel=1e-11, abs=1e-11 * scale)
+
+
+def _static_loads(p):
+    """Axle loads from the static balance of a rigid car: N_f + N_r = m g and zero moment
+    about the centre of gravity, N_f l_f = N_r l_r (linear solve, no closed form typed in)."""
+    A = np.array([[1.0, 1.0], [p["lf"], -p["lr"]]])
+    return np.linalg.solve(A, [p["m"] * p["g"], 0.0])
+
+
+def _pin_car_tyre_peak(car):
+    """Each tyre's lateral force peaks at the friction limit mu N of its axle's static load,
+    at the slip angle where C atan(B alpha) reaches pi/2 (the shape sin(.) peaks there), and
+    falls beyond it.  The front slip angle is set by the steering at vy = r = 0, the rear's by
+    vy at r = 0; the peak is located by the library's bounded scalar minimiser."""
+    from scipy.optimize import minimize_scalar
+    p = car.p
+    Nf, Nr = _static_loads(p)
+    vx = 5.0
+    alpha_peak = math.tan(math.pi / (2.0 * p["C"])) / p["B"]
+
+    def front(a):
+        return float(car.tyre_forces(np.array([[0], [0], [0], [vx], [0.0], [0.0], [a]], float))[0][0])
+
+    def rear(a):
+        vy = -vx * math.tan(a)                      # rear slip angle -atan(vy / vx) = a
+        return float(car.tyre_forces(np.array([[0], [0], [0], [vx], [vy], [0.0], [0.0]], float))[1][0])
+
+    for force, N in ((front, Nf), (rear, Nr)):
+        res = minimize_scalar(lambda a: -force(a), bounds=(1e-3, 1.2), method="bounded",
+                              options={"xatol": 1e-10})
+        assert -res.fun == pytest.approx(p["mu"] * N, rel=1e-9)
+        assert res.x == pytest.approx(alpha_peak, abs=1e-4)
+        assert force(1.1) < force(alpha_peak) - 1e-3 * p["mu"] * N      # sliding: past the peak it falls
+        assert force(-alpha_peak) == pytest.approx(-p["mu"] * N, rel=1e-12)   # odd in the slip angle
+
+
+def _pin_car_free_drift(car):
+    """Tyres off (mu = 0) and no drive force: nothing acts on the body, so the world-frame
+    velocity of the centre of gravity is constant for any vy and yaw rate; over a fine Euler
+    integration it drifts only at O(dt)."""
+    free = type(car)(1e-4, car.map, car.origin, car.h, **dict(car.p, mu=0.0, Crr=0.0, Cd=0.0))
+    x = free.init([0.0, 0.0, 0.3, 4.0, 1.5, 2.0, 0.2], 1)
+    v0 = _world_rot(0.3) @ [4.0, 1.5]
+    for _ in range(5000):                           # 0.5 s: a full turn of the body is 1 rad
+        x = free.step(x, np.array([[0.7], [0.0]]))
+    vw = _world_rot(x[2, 0]) @ [x[3, 0], x[4, 0]]
+    assert np.allclose(vw, v0, atol=2e-3)
+    assert x[5, 0] == pytest.approx(2.0, rel=1e-12)     # no moment: r constant
+
+
+def test_car_newton_euler_in_the_inertial_frame():
+    _pin_car_newton_euler(_car())
+
+
+def test_car_tyre_peak_is_the_friction_limit_of_the_static_load():
+    _pin_car_tyre_peak(_car())
+
+
+def test_car_free_body_keeps_its_world_velocity():
+    _pin_car_free_drift(_car())
+
+
+def _car_mutants():
+    """Plausible mistakes in the car rows, planted in copies of the oracle's model."""
+    base = systems.Car
+
+    def with_deriv(edit):
+        class Mutant(base):
+            def deriv(self, x, v):
+                d = base.deriv(self, x, v).copy()
+                return edit(self, x, v, d)
+        return Mutant
+
+    def tyres(fn):
+        class Mutant(base):
+            def tyre_forces(self, x):
+                return fn(self, x)
+        return Mutant
+
+    def vyr(self, x, v, d):             # +vy r coupling written with the wrong sign
+        d[3] -= 2 * x[4] * x[5]
+        return d
+
+    def vxr(self, x, v, d):             # -vx r coupling written with the wrong sign
+        d[4] += 2 * x[3] * x[5]
+        return d
+
+    def sin_delta(self, x, v, d):       # front force projected with +sin(delta)
+        Fyf, _ = self.tyre_forces(x)
+        d[3] += 2 * Fyf * np.sin(x[6]) / self.p["m"]
+        return d
+
+    def no_cos(self, x, v, d):          # cos(delta) dropped from the lateral row
+        Fyf, _ = self.tyre_forces(x)
+        d[4] += Fyf * (1 - np.cos(x[6])) / self.p["m"]
+        return d
+
+    def swapped_loads(self, x):         # static loads on the wrong axles
+        Fyf, Fyr = base.tyre_forces(self, x)
+        L, lf, lr = self.p["lf"] + self.p["lr"], self.p["lf"], self.p["lr"]
+        return Fyf * lf / lr, Fyr * lr / lf
+
+    def shape(self, x):                 # B and C exchanged in the tyre shape
+        q = dict(self.p, B=self.p["C"], C=self.p["B"])
+        m = base(self.dt, self.map, self.origin, self.h, **q)
+        return base.tyre_forces(m, x)
+
+    return {"+vy r sign": with_deriv(vyr), "-vx r sign": with_deriv(vxr), "-Fyf sin(delta) sign": with_deriv(sin_delta),
+            "cos(delta) dropped": with_deriv(no_cos), "static loads swapped": tyres(swapped_loads),
+            "B and C swapped": tyres(shape)}
+
+
+@pytest.mark.parametrize("name", list(_car_mutants()))
+def test_car_pins_catch_planted_mistakes(name):
+    """Each planted mistake fails at least one of the car pins (on a copy of the model)."""
+    cls = _car_mutants()[name]
+    car = cls(0.02, np.zeros((16, 16), dtype=np.float32), -100.0, 20.0)
+    caught = []
+    for pin in (_pin_car_newton_euler, _pin_car_tyre_peak, _pin_car_free_drift):
+        try:
+            pin(car)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"no pin catches: {name}"
 
 
 def _quad(dt=0.01, **kw):
