@@ -60,13 +60,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--plain-steps", type=int, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=1000,
+                    help="timed end-to-end steps for the p50/p99 latency (after 50 untimed)")
+    ap.add_argument("--plain-steps", type=int, default=1000,
+                    help="timed plain-loop steps for its p50/p99 latency (after 50 untimed)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", default="256,512,1024",
                     help="concurrency levels of the serving measurement ('' to skip)")
-    ap.add_argument("--serving-ticks", type=int, default=30)
+    ap.add_argument("--serving-ticks", type=int, default=500)
+    ap.add_argument("--serving-async", default="256,512,1024",
+                    help="concurrency levels of the real-time closed loop over submit / reap ('' to skip)")
+    ap.add_argument("--serving-async-periods", type=int, default=500,
+                    help="50 Hz control periods per level of the real-time closed loop")
     ap.add_argument("--serving-heavy", default="256",
                     help="concurrency levels of the heavy-skewed serving mix ('' to skip)")
     ap.add_argument("--serving-capacity", action="store_true",
@@ -158,6 +164,7 @@ class ClockSampler:
     def __init__(self, gpu_id: str | None, settle_s: float = 2.0):
         self.path = tempfile.mktemp(suffix=".csv")
         self.t0 = self.t1 = None
+        self.windows = []                  # (start, end) of each timed region
         self.nvml_rows, self.nvml_on, self.nvml_stop, self.nvml_thread = [], False, False, None
         read = _nvml_clock_reader(gpu_id)
         if read is not None:
@@ -200,6 +207,7 @@ class ClockSampler:
     def mark_end(self):
         self.nvml_on = False
         self.t1 = time.time()
+        self.windows.append((self.t0, self.t1))
 
     @staticmethod
     def _stamp(stamp: str):
@@ -210,10 +218,10 @@ class ClockSampler:
             return None
 
     def _inside(self, stamp: str) -> bool:
-        if self.t0 is None or self.t1 is None:
+        if not self.windows:
             return True
         t = self._stamp(stamp)
-        return True if t is None else self.t0 <= t <= self.t1
+        return True if t is None else any(a <= t <= b for a, b in self.windows)
 
     def _past_end(self) -> bool:
         """True once the file holds a sample stamped after mark_end()."""
@@ -352,6 +360,57 @@ def oracle_rate_all_cores(seconds: float, k_sample: int = 1024, max_procs: int =
     return total, procs
 
 
+def oracle_errors(N, stream_handle, seed, gid, U, counter, **over):
+    """The error of one headline iteration against the FP64 oracle (part of the CPU-baseline leg,
+    outside every timed region): the GPU runs one iteration of the car K=16384, T=100 from the
+    controls and iteration counter the timed loop reached; the oracle runs the same iteration
+    (same FP32 inputs, same Philox noise).  Reports, per result, the whole iteration's error
+    (path costs S~, argmin k*, normaliser eta, update dU, u0) and the weighting's own error
+    (the oracle's FP64 weighting and weighted sum of the GPU's own costs and perturbations)."""
+    from oracle import mppi as om
+    from oracle import systems as osys
+    c, cfg = make_ctrl(N, N.MPPI_IMPL_FUSED, seed=seed, gid=gid, stream_handle=stream_handle, **over)
+    c.set_controls(np.asarray(U, dtype=np.float32))
+    c.set_iteration(counter)
+    x0 = np.asarray(cfg["x0"], dtype=np.float32)
+    u0 = c.step(x0)
+    d = c.get_debug()
+    U_gpu = c.get_controls().astype(np.float64)
+    du = c.get_noise(counter).astype(np.float64)
+    c.close()
+    f64 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    lam, nu = float(np.float32(cfg["lam"])), float(np.float32(cfg["nu"]))
+    car = osys.Car(cfg["dt"], W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL)
+    o = om.iteration_seeded(car, f64(x0), f64(U), cfg["K"], lam, nu, f64(cfg["Sigma"]), f64(cfg["R"]), seed, counter,
+                            gid)
+    scale = np.sqrt(cfg["nu"] * np.diag(cfg["Sigma"]))
+    Sg = d["S"].astype(np.float64)
+    fin = np.isfinite(o.S)
+    rel = np.abs(Sg[fin] - o.S[fin]) / np.abs(o.S[fin])
+    srt = np.sort(o.S[fin])
+    rho, kst, eta_r, w_r = om.weights(Sg, lam)                      # the weighting of the GPU's own costs
+    dU_r = np.einsum("tmk,k->tm", du, w_r)
+    ess = 1.0 / float(np.sum(o.w ** 2))
+    return {
+        "workload": f"car K={cfg['K']} T={cfg['T']} nu={cfg['nu']} lambda={cfg['lam']}"
+                    f"{'' if not over else ', R fixed at Sigma^-1'}, controls and counter {counter} of the timed loop",
+        "effective_sample_size": ess,
+        "S_rel_max": float(rel.max()), "S_rel_p99": float(np.percentile(rel, 99)),
+        "kstar_match": bool(d["kstar"] == o.kstar), "kstar_unique": bool(srt[1] - srt[0] > 2e-4 * abs(srt[0])),
+        "eta_rel_iteration": abs(d["eta"] - o.eta) / o.eta,
+        "dU_err_over_scale_iteration": float(np.max(np.abs(d["dU"] - o.dU) / scale[None, :])),
+        "U_err_over_scale_iteration": float(np.max(np.abs(U_gpu - o.U) / scale[None, :])),
+        "u0_err_over_scale": float(np.max(np.abs(u0.astype(np.float64) - o.u0) / scale)),
+        "kstar_match_on_gpu_costs": bool(d["kstar"] == kst),
+        "eta_rel_reduction": abs(d["eta"] - eta_r) / eta_r,
+        "dU_err_over_scale_reduction": float(np.max(np.abs(d["dU"] - dU_r) / scale[None, :])),
+        "bars": {"S_rel": 1e-4, "U_over_scale": 1e-3, "kstar": "exact where the oracle's minimum is unique"},
+        "note": "iteration: GPU vs the oracle's full FP64 iteration; reduction: GPU vs the oracle's FP64 weighting "
+                "of the GPU's own path costs and perturbations (the error of the FP32 weights, FP32 block sums and "
+                "double-FP32 cross-block sums alone)",
+    }
+
+
 def run_reference(args, rank, world, max_procs: int = 64):
     """The reference arm: the FP64 oracle on the host cores, one single-threaded child process
     per core (up to max_procs), each iterating its own 1024-sample batch at the full horizon,
@@ -389,8 +448,8 @@ def run_reference(args, rank, world, max_procs: int = 64):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def make_ctrl(N, impl, seed, gid, stream_handle):
-    cfg = W.config(SYSTEM, K=K_SAMPLES, T=T_STEPS, nu=NU, seed=seed, gid=gid)
+def make_ctrl(N, impl, seed, gid, stream_handle, **over):
+    cfg = W.config(SYSTEM, **dict(dict(K=K_SAMPLES, T=T_STEPS, nu=NU, seed=seed, gid=gid), **over))
     c = N.Controller(cfg["system"], cfg["K"], cfg["T"], cfg["dt"], cfg["nu"], cfg["lam"], cfg["Sigma"], cfg["R"])
     c.set_stream(stream_handle)
     c.set_seed(seed)
@@ -512,6 +571,82 @@ def cartpole_vel_plant(x, u, dt):
     acc = 10.0 * (u - v)
     th_acc = -(3.0 / (4.0 * 0.5)) * (9.81 * np.sin(th) + acc * np.cos(th))
     return np.array([p + dt * v, v + dt * acc, th + dt * om, om + dt * th_acc])
+
+
+def serving_plant(system, X, U, dt):
+    """The simulated plants of the serving measurement, one control period in FP64 on the host,
+    vectorised over controllers of one system (X [n][nx], U [n][m]): the force-input cart-pole
+    (Euler), the dynamic bicycle car with its steering actuator and Pacejka tyres (Euler) and
+    the quadrotor (RK4), the models the controllers optimise over (no collision model: a
+    crashed plant keeps flying).  Non-finite results are reset by the serving loop."""
+    X = np.asarray(X, dtype=np.float64).T.copy()
+    U = np.asarray(U, dtype=np.float64).T
+    with np.errstate(all="ignore"):
+        if system == W.CARTPOLE:
+            mc, mp, l, g = 1.0, 0.1, 0.5, 9.81
+            _, v, th, om = X
+            s, c = np.sin(th), np.cos(th)
+            tmp = (U[0] + mp * l * om * om * s) / (mc + mp)
+            tha = (g * s - c * tmp) / (l * (4.0 / 3.0 - mp * c * c / (mc + mp)))
+            xa = tmp - mp * l * tha * c / (mc + mp)
+            X = X + dt * np.stack([v, xa, om, tha])
+        elif system == W.CAR:
+            m, Iz, lf, lr, B, C, mu, g = 21.7, 1.12, 0.34, 0.23, 4.0, 1.8, 0.9, 9.81
+            _, _, psi, vx, vy, r, de = X
+            vxs = np.maximum(vx, 1.0)
+            L = lf + lr
+            Fyf = mu * m * g * lr / L * np.sin(C * np.arctan(B * (de - np.arctan((vy + lf * r) / vxs))))
+            Fyr = mu * m * g * lf / L * np.sin(C * np.arctan(B * -np.arctan((vy - lr * r) / vxs)))
+            Fx = 120.0 * U[1] - 2.0 * vx - 0.35 * vx * np.abs(vx)
+            X = X + dt * np.stack([vx * np.cos(psi) - vy * np.sin(psi), vx * np.sin(psi) + vy * np.cos(psi), r,
+                                   (Fx - Fyf * np.sin(de)) / m + vy * r, (Fyr + Fyf * np.cos(de)) / m - vx * r,
+                                   (lf * Fyf * np.cos(de) - lr * Fyr) / Iz, (0.5 * U[0] - de) / 0.1])
+        elif system == W.QUAD:
+            ms, g, arm, kap, Ix, Iy, Izz = 0.5, 9.81, 0.17, 0.016, 2.3e-3, 2.3e-3, 4.0e-3
+            f = U
+
+            def deriv(x):
+                ph, th, ps, wp, wq, wr = x[6], x[7], x[8], x[9], x[10], x[11]
+                a = (f[0] + f[1] + f[2] + f[3]) / ms
+                cph, sph, cth, sth, cps, sps = np.cos(ph), np.sin(ph), np.cos(th), np.sin(th), np.cos(ps), np.sin(ps)
+                ws = wq * sph + wr * cph
+                return np.stack([x[3], x[4], x[5], a * (cps * sth * cph + sps * sph), a * (sps * sth * cph - cps * sph),
+                                 a * cth * cph - g, wp + ws * sth / cth, wq * cph - wr * sph, ws / cth,
+                                 (arm * (f[1] - f[3]) - (Izz - Iy) * wq * wr) / Ix,
+                                 (arm * (f[2] - f[0]) - (Ix - Izz) * wr * wp) / Iy,
+                                 (kap * (f[0] - f[1] + f[2] - f[3]) - (Iy - Ix) * wp * wq) / Izz])
+            k1 = deriv(X)
+            k2 = deriv(X + 0.5 * dt * k1)
+            k3 = deriv(X + 0.5 * dt * k2)
+            k4 = deriv(X + dt * k3)
+            X = X + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return X.T
+
+
+def run_serving_async(levels, periods, seed=0, mix=None):
+    """The real-time closed loop over the asynchronous serving interface at each target
+    concurrency: controllers at 50 Hz from random phases, each request submitted from its plant's
+    state and the plant advanced by the returned u0 (serving_plant), Poisson arrivals and
+    departures with admission and release while ticks are on the GPU.  Per level: the latency of
+    every request from submit to result (p50 / p99 / max), deadline misses and rollout-steps/s."""
+    from paper_1509_01149_b300 import _native as N
+    from paper_1509_01149_b300 import serving
+    out = {}
+    for target in levels:
+        srv = N.Server(max(2 * target, 64), max(256 << 20, target << 21))
+        srv.set_env(0, N.map_blob(W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_ORIGIN, W.MAP_H_CELL))
+        srv.set_env(1, N.forest_blob(W.quad_forest(0), W.QUAD_GOAL))
+        loop = serving.AsyncServingLoop(srv, W, {W.CAR: 0, W.QUAD: 1}, plant=serving_plant, seed=seed + target,
+                                        **(mix or {}))
+        summ = loop.run(periods * serving.DEADLINE_MS / 1e3, target_active=target)
+        summ["periods_per_controller"] = periods
+        st = srv.stats()
+        summ["ticks"] = st["ticks"]
+        summ["mean_requests_per_tick"] = st["completed"] / max(st["ticks"], 1)
+        out[str(target)] = summ
+        loop.drain()
+        srv.close()
+    return out
 
 
 def run_nu_sweep(nus=(1.0, 10.0, 50.0, 100.0, 300.0, 1000.0, 1500.0), Ks=(100, 1000, 10000), seconds=10.0, seed=0):
@@ -689,9 +824,10 @@ def run_learned(n_train=10_000_000, n_test=100_000, steps=6000, batch=8192):
     return out
 
 
-def load_traffic(kernel_tag: str):
-    """DRAM traffic per launch from a committed ncu summary, if it was taken on the
-    current kernel sources (same source hash); else None."""
+def load_profile(kernel_tag: str):
+    """The committed ncu record of a kernel (DRAM bytes per launch, FP32 work per rollout-step
+    from its instruction counters), if it was taken on the current kernel sources (same
+    source hash); else None."""
     p = os.path.join(ROOT, "profiles", f"{kernel_tag}.json")
     if not os.path.exists(p):
         return None
@@ -701,7 +837,7 @@ def load_traffic(kernel_tag: str):
         return None
     if d.get("source_hash") != source_hash(KERNEL_SOURCES.get(kernel_tag)):
         return None
-    return d.get("dram_bytes_per_launch")
+    return d
 
 
 def run_ours(args, rank, world, local_rank):
@@ -722,6 +858,9 @@ def run_ours(args, rank, world, local_rank):
     if args.serving_only:
         from paper_1509_01149_b300.serving import HEAVY_MIX
         res = {"serving": run_serving(levels, args.serving_ticks)}
+        async_levels = [int(v) for v in args.serving_async.split(",") if v.strip()]
+        if async_levels:
+            res["serving_async"] = run_serving_async(async_levels, args.serving_async_periods)
         if heavy_levels:
             res["serving_heavy"] = run_serving(heavy_levels, args.serving_ticks, mix=HEAVY_MIX)
         if args.serving_capacity:
@@ -786,7 +925,6 @@ def run_ours(args, rank, world, local_rank):
                    "thread-block cluster)" if fused_shift else
                    "per step one CUDA-graph launch of 3 kernels (rollout, merge (FP64 normaliser, double-FP32 sums) + update, shift)")
     ms_per_step = 1e3 * total_s / args.steps
-    clk = clocks.stop()
     # the dominant kernel alone (for the roofline): rollout launches between events, same stream
     n_roll = max(min(args.steps, 200), 5)
     rev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_roll)]
@@ -802,7 +940,7 @@ def run_ours(args, rank, world, local_rank):
     roll_ms = [a.elapsed_time(b) for a, b in rev]
 
     # ---- e2e: host buffers through mppi_step (graph), x0 H2D + u0 D2H per step ---
-    e2e_steps = args.e2e_steps or max(args.steps // 2, 10)
+    e2e_steps = max(args.e2e_steps, 1)
     x_host = np.asarray(cfg["x0"], dtype=np.float32)
     lat = []
     e2e_warm = 50                                      # untimed steps before the measured ones
@@ -810,34 +948,46 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(stream):
             flush.zero_()
         stream.synchronize()
+        if s == e2e_warm:
+            clocks.mark_start()
         t0 = time.perf_counter()
         ctrl.step_shift(x_host)
         lat.append(time.perf_counter() - t0)
     stream.synchronize()
+    clocks.mark_end()
     lat = lat[e2e_warm:]
     e2e_total = reduce_max(sum(lat), dist, dev)
     e2e_value = whole_job_rate(K_SAMPLES * T_STEPS * e2e_steps, world, e2e_total)
 
     # ---- plain loop baseline (unfused kernels, sync per step) -----------------
-    plain_steps = args.plain_steps or max(args.steps // 4, 10)
+    plain_steps = max(args.plain_steps, 1)
+    plain_warm = 50
     pctrl, _ = make_ctrl(N, N.MPPI_IMPL_PLAIN, seed=1000 + rank, gid=rank, stream_handle=stream.cuda_stream)
     plat = []
-    for s in range(plain_steps + 3):
+    for s in range(plain_steps + plain_warm):
         with torch.cuda.stream(stream):
             flush.zero_()
         stream.synchronize()
+        if s == plain_warm:
+            clocks.mark_start()
         t0 = time.perf_counter()
         pctrl.step(x_host)
         pctrl.shift()
         plat.append(time.perf_counter() - t0)
     stream.synchronize()
-    plat = plat[3:]
+    clocks.mark_end()
+    clk = clocks.stop()
+    clk["windows"] = "the device-resident timed steps, the e2e steps and the plain-loop steps"
+    plat = plat[plain_warm:]
     plain_value = K_SAMPLES * T_STEPS * len(plat) * world / sum(plat)
     pctrl.close()
 
+    U_end, it_end = ctrl.get_controls(), ctrl.get_iteration()     # for the oracle-error sample
     serving_res = run_serving(levels, args.serving_ticks, seed=rank) if levels else None
     from paper_1509_01149_b300.serving import HEAVY_MIX
     heavy_res = run_serving(heavy_levels, args.serving_ticks, seed=rank, mix=HEAVY_MIX) if heavy_levels else None
+    async_levels = [int(v) for v in args.serving_async.split(",") if v.strip()]
+    async_res = run_serving_async(async_levels, args.serving_async_periods, seed=rank) if async_levels else None
     capacity_res = run_capacity(seed=rank) if args.serving_capacity else None
     learned_res = None if args.no_learned else run_learned(args.learned_train, steps=args.learned_steps)
     systems_res = None if args.no_systems else run_systems()
@@ -847,13 +997,24 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    flops = ALGO_FLOPS_PER_ROLLOUT_STEP[SYSTEM] * K_SAMPLES * T_STEPS
+    prof = load_profile("rollout_car_ws_k16384")
+    formula_flops = ALGO_FLOPS_PER_ROLLOUT_STEP[SYSTEM]
+    counted = prof.get("flops_per_rollout_step") if prof else None
+    flops_step = counted or formula_flops
+    flops = flops_step * K_SAMPLES * T_STEPS
     roll_mean_s = statistics.mean(roll_ms) / 1e3
     achieved = flops / roll_mean_s / 1e12
     peak = fp32_peak_tflops()
-    traffic = load_traffic("rollout_car_ws_k16384")
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
     cpu = None
+    oracle_err = None
     if not args.no_cpu_baseline:
+        oracle_err = oracle_errors(N, stream.cuda_stream, 1000 + rank, rank, U_end, it_end)
+        # the same iteration with weights spread over many samples (R fixed, a larger temperature),
+        # so that the normaliser and the weighted sum are exercised, not just the argmin
+        oracle_err = {"headline": oracle_err,
+                      "spread_weights": oracle_errors(N, stream.cuda_stream, 1000 + rank, rank, U_end, it_end,
+                                                      lam=300.0, R=np.linalg.inv(np.diag([0.3, 0.35])))}
         rate1, iters, _ = oracle_rate(args.cpu_seconds, 1024)
         rate_all, procs = oracle_rate_all_cores(args.cpu_seconds, 1024)
         cpu = {"value": rate_all, "unit": UNIT, "cores": procs, "kind": "oracle",
@@ -879,25 +1040,34 @@ def run_ours(args, rank, world, local_rank):
         "iters_per_s": value / (K_SAMPLES * T_STEPS),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * m,
                 "p50_ms": pct(lat_ms, 0.5), "p99_ms": pct(lat_ms, 0.99), "steps": e2e_steps,
+                "latency_samples": len(lat_ms), "untimed_warmup_steps": e2e_warm,
                 "call": "mppi_step_shift (x0 copied from pinned host memory, u0 written by the update kernel "
                         "into mapped pinned memory; one graph per step, blocking until u0 is on the host)"},
         "plain_loop": {"value": plain_value, "unit": UNIT, "p50_ms": pct(plat_ms, 0.5), "p99_ms": pct(plat_ms, 0.99),
-                       "steps": len(plat), "e2e_speedup": e2e_value / plain_value,
+                       "steps": len(plat), "latency_samples": len(plat_ms), "untimed_warmup_steps": plain_warm,
+                       "e2e_speedup": e2e_value / plain_value,
                        "what": "unfused: noise->HBM, rollout, min, normaliser, weighted-sum kernels, "
                                "sync per step, no graph"},
         "gpu_launches": launches_per_step * args.steps,
         "launch_note": launch_note,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "k_rollout_car_ws<128> (core, noise and pose warps per 128 samples)",
-                     "flops_per_rollout_step": ALGO_FLOPS_PER_ROLLOUT_STEP[SYSTEM],
+                     "flops_per_rollout_step": flops_step,
+                     "flops_basis": ("ncu FP32 thread-instruction counters of the kernel, 2 ffma + fadd + fmul per "
+                                     "rollout-step (profiles/rollout_car_ws_k16384.json)" if counted else
+                                     "formula count (no counter record for the current sources)"),
+                     "flops_per_rollout_step_formula": formula_flops,
+                     "frac_formula": formula_flops * K_SAMPLES * T_STEPS / roll_mean_s / 1e12 / peak,
                      "rollout_ms_mean": 1e3 * roll_mean_s,
                      "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (derived, not measured)",
                      "frac_at_observed_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])) if clk.get("sm_mhz")
                      else None},
         "clocks": clk,
+        "oracle_error": oracle_err,
         "cpu_baseline": cpu,
         "serving": serving_res,
         "serving_heavy": heavy_res and dict(heavy_res, mix=HEAVY_MIX),
+        "serving_async": async_res,
         "serving_capacity": capacity_res,
         "systems": systems_res,
         "learned": learned_res,

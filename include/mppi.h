@@ -48,6 +48,7 @@ extern "C" {
 #define MPPI_ESTATE (-5)   /* call not valid in the ctx's current state (e.g. no env set)   */
 #define MPPI_ENOSYS (-6)   /* feature not built into this library                           */
 #define MPPI_EBUSY (-7)    /* admission refused: no free slot or not enough arena memory     */
+#define MPPI_EAGAIN (-8)   /* a submitted step request has not finished yet (serving poll)   */
 
 /* systems (plants and their state costs; see the design notes for the models) */
 typedef enum {
@@ -249,17 +250,25 @@ int mppi_philox_words(uint64_t seed, int K, int n_blocks, uint32_t counter, uint
  *
  * It does what mppi_step_async does (noise, rollout, cost, weights, update of U, u_0
  * out; not the shift) on buffers the caller owns:
- *   sys, K, T, dt, nu, lambda, h_Sigma, h_R   as in mppi_create (host arrays, copied)
- *   seed, gid, counter                        Philox key, controller id, iteration counter
- *   h_env_header   host mppi_env_map (car) or mppi_env_forest (quadrotor); NULL for
- *                  the cart-pole
- *   d_env_payload  device: the map values [height][width] or the cylinder rows [n][3]
- *   d_state        device [n] state, read
- *   d_U            device [T][m] nominal controls, updated in place
- *   d_u0_out       device [m] updated u_0
- *   cuda_stream    stream for all work (cudaStream_t, may be NULL = legacy stream)
- *   h_err, err_len optional host buffer that receives the error text (may be NULL)
- * The work is enqueued on cuda_stream and not waited for.
+ *   sys                the cart-pole (either form), the car or the quadrotor; MPPI_CAR_MLP
+ *                      (learned dynamics) is refused with MPPI_EINVAL
+ *   K, T, dt, nu, lambda, h_Sigma, h_R   as in mppi_create, with the same checks (host
+ *                      arrays, copied; h_R NULL gives R = lambda Sigma^-1)
+ *   seed, gid, counter Philox key, controller id, iteration counter
+ *   h_env_header       host mppi_env_map (car) or mppi_env_forest (quadrotor); NULL for
+ *                      the cart-pole
+ *   d_env_payload      device: the map values [height][width] or the cylinder rows [n][3]
+ *                      (float32), read by the kernels
+ *   env_payload_bytes  size of the caller's d_env_payload buffer; a header that needs more
+ *                      (4*width*height or 12*n bytes) is refused with MPPI_EINVAL
+ *   d_state            device [n] state, read
+ *   d_U                device [T][m] nominal controls, updated in place
+ *   d_u0_out           device [m] updated u_0
+ *   cuda_stream        stream for all work (cudaStream_t, may be NULL = legacy stream)
+ *   h_err, err_len     optional host buffer that receives the error text (may be NULL)
+ * The work is enqueued on cuda_stream and not waited for.  For the same inputs the
+ * cart-pole and the car give the bits mppi_step gives; the quadrotor searches every
+ * cylinder where a ctx uses its nearest-cylinder grid (the same distances, to rounding).
  *
  * Scratch: a static device array of MPPI_STATIC_SCRATCH_BYTES (4 MiB) inside the
  * library, which every GPU that loads the library holds until the process exits.
@@ -268,13 +277,13 @@ int mppi_philox_words(uint64_t seed, int K, int n_blocks, uint32_t counter, uint
  * MPPI_EINVAL with the sizes in the error text.  Every call on a device shares the
  * array and leaves the last call's contents in it, so calls whose work overlaps on
  * the GPU (two streams, two host threads) race.  The first call on each device looks
- * up the array's device address and sets kernel attributes (once per device); make
- * that first call before any stream capture. */
+ * up the array's device address and sets kernel attributes (once per device, retried
+ * if it failed); make that first call before any stream capture. */
 #define MPPI_STATIC_SCRATCH_BYTES (4u << 20)
 int mppi_step_static(mppi_system sys, int K, int T, float dt, float nu, float lambda, const float *h_Sigma,
                      const float *h_R, uint64_t seed, uint32_t gid, uint32_t counter, const void *h_env_header,
-                     const float *d_env_payload, const float *d_state, float *d_U, float *d_u0_out,
-                     void *cuda_stream, char *h_err, size_t err_len);
+                     const float *d_env_payload, size_t env_payload_bytes, const float *d_state, float *d_U,
+                     float *d_u0_out, void *cuda_stream, char *h_err, size_t err_len);
 
 /* ---------------------------------------------------------------------------------
  * Serving: many controllers of different systems, K and T stepped together.
@@ -330,6 +339,10 @@ int mppi_server_admit(mppi_server *srv, const mppi_slot_config *cfg, int *slot_o
 int mppi_server_release(mppi_server *srv, int slot);
 int mppi_server_set_controls(mppi_server *srv, int slot, const float *h_U);
 int mppi_server_get_controls(mppi_server *srv, int slot, float *h_U);
+/* Results of the slot's last tick, host outputs (any may be NULL); synchronises the server:
+ *   S [K] path costs S~ (non-finite as +inf), argmin the lowest k attaining rho, eta the
+ *   FP64 normaliser sum_k exp(-(S~_k - rho)/lambda) -- as mppi_get_debug for a ctx. */
+int mppi_server_get_debug(mppi_server *srv, int slot, float *h_S, int *argmin, double *eta);
 /* One receding-horizon step of the n listed slots: h_states [n][16] (state in the first
  * n_x entries of each row), h_u0_out [n][4] receives each slot's u_0 (first m entries).
  * Blocks until the results are on the host. */
@@ -338,7 +351,65 @@ int mppi_server_tick(mppi_server *srv, int n, const int *slots, const float *h_s
  * (tick on the listed slots, restoring their controls and counters afterwards). */
 int mppi_server_autotune(mppi_server *srv, int n, const int *slots, const float *h_states);
 int mppi_server_get_info(mppi_server *srv, mppi_server_info *out);
+/* Text of the server's last error (or of the last failed mppi_server_create when srv is NULL). */
 const char *mppi_server_last_error(mppi_server *srv);
+
+/* ---- Asynchronous serving: submit / poll / cancel (continuous batching) ----------------
+ * mppi_server_start launches the server's scheduler thread.  From then on a step request
+ * (one receding-horizon iteration + shift of one admitted controller from a given state) is
+ * submitted with mppi_server_submit and returns at once with a request id.  The scheduler
+ * batches queued requests into ticks -- at most one per controller and tick, at most
+ * max_batch per tick (0: no limit) -- and keeps two ticks in the GPU's queue: while one runs,
+ * the requests that arrived meanwhile are filled into the other tick's buffers and enqueued
+ * behind it, so requests that arrive while others are on the GPU join the next tick without
+ * waiting for a host round trip.  Requests of one controller run in submission order.  A
+ * request's result is the u_0 the synchronous mppi_server_tick (and a lone mppi_ctx with the
+ * same configuration, seed, controller id and iteration counter) gives for the same state.
+ *
+ * While the scheduler runs, mppi_server_admit, _release, _set_env, _get_controls,
+ * _set_controls and _get_debug may be called from any thread (one lock guards the host
+ * state; admission uploads go on a separate copy stream and do not wait for ticks in flight;
+ * control and debug copies are ordered after every tick already enqueued).  A slot released
+ * while a tick in flight uses it has its queued requests cancelled and its memory returned to
+ * the arena when that tick retires.  mppi_server_tick and mppi_server_autotune return
+ * MPPI_ESTATE while the scheduler runs (tune first, then start). */
+typedef struct {
+  int32_t running, pad;
+  int64_t queued;     /* submitted, not yet on the GPU                       */
+  int64_t in_flight;  /* in a tick on the GPU                                */
+  int64_t ticks;      /* ticks the scheduler has retired                      */
+  int64_t completed;  /* requests those ticks finished                        */
+} mppi_server_stats;
+
+/* Start the scheduler thread.  ESTATE if it already runs. */
+int mppi_server_start(mppi_server *srv, int max_batch);
+/* Finish every submitted request, then stop the thread.  Safe when it is not running. */
+int mppi_server_stop(mppi_server *srv);
+/* Queue one step of the controller in `slot` from h_state (host [16], state in the first n
+ * entries, copied).  *id_out receives the request id (ids are never reused).  ESTATE if the
+ * scheduler is not running; EINVAL for a slot that is not admitted; EBUSY past 2^20
+ * outstanding requests. */
+int mppi_server_submit(mppi_server *srv, int slot, const float *h_state, uint64_t *id_out);
+/* mppi_server_submit for n requests at once (one lock, one wake-up): slot_ids [n],
+ * h_states [n][16], ids_out [n].  All or none are queued (EINVAL / EBUSY / ESTATE as above). */
+int mppi_server_submit_batch(mppi_server *srv, int n, const int *slot_ids, const float *h_states, uint64_t *ids_out);
+/* MPPI_OK and u_0 into h_u0 (host [4], first m entries) if the request has finished (the id
+ * is then forgotten), MPPI_EAGAIN if not yet, the tick's error status if it failed, EINVAL
+ * for an unknown (never issued, already taken or cancelled) id. */
+int mppi_server_poll(mppi_server *srv, uint64_t id, float *h_u0);
+/* As poll, but waits up to timeout_ms for the request to finish (ETIMEOUT after that). */
+int mppi_server_wait(mppi_server *srv, uint64_t id, double timeout_ms, float *h_u0);
+/* Take up to max_n finished requests in completion order, waiting up to timeout_ms for the
+ * first: ids [max_n], h_u0 [max_n][4], status [max_n] (may be NULL: MPPI_OK or the tick's
+ * error per request); *n_out receives how many (0 after the timeout). */
+int mppi_server_reap(mppi_server *srv, int max_n, uint64_t *ids, float *h_u0, int *status, double timeout_ms,
+                     int *n_out);
+/* Forget a request.  Queued: it never runs (the controller's controls and iteration counter
+ * are untouched).  In flight: its tick completes (the controller's controls and counter
+ * advance, every other request of the tick is unaffected) and the result is dropped.
+ * Finished: the result is dropped.  EINVAL for an unknown id. */
+int mppi_server_cancel(mppi_server *srv, uint64_t id);
+int mppi_server_get_stats(mppi_server *srv, mppi_server_stats *out);
 
 /* ---------------------------------------------------------------------------------
  * Learned car dynamics (an extension beyond the paper).
@@ -383,6 +454,19 @@ int mppi_car_step(const float *d_states, const float *d_controls, int n, float d
  * Returns 0, MPPI_EINVAL, MPPI_ENOMEM, MPPI_ECUDA or MPPI_ETIMEOUT (a bounded wait ran out). */
 int mppi_debug_gemm_bf16(int M, int N, int K, const void *dA, int64_t sam, int64_t sak, const void *dB, int64_t sbk,
                          int64_t sbn, float *dC, int64_t ldc, int BN);
+
+/* Check hook of the bounded-wait exit path of the tensor-core kernels: one GEMM CTA whose MMA
+ * issuer issues nothing, so its mbarrier wait gives up after `polls` polls (1 .. 2^20); the
+ * kernel raises its error flag, waits once more (bounded), frees its TMEM and returns, with no
+ * MMA or bulk copy outstanding.  Returns MPPI_ETIMEOUT (the expected outcome), MPPI_OK if the
+ * wait did not run out, MPPI_EINVAL, MPPI_ENOMEM or MPPI_ECUDA.  Synchronises the device. */
+int mppi_debug_gemm_wait_timeout(uint32_t polls);
+
+/* Host-side fault injection for tests of the out-of-memory paths: with after_n >= 0 the
+ * device or pinned allocation of mppi_create / mppi_server_create that follows after_n
+ * successful ones fails (once) with MPPI_ENOMEM as if CUDA had refused it; after_n < 0
+ * disarms it.  Process-wide; always returns MPPI_OK. */
+int mppi_debug_fail_allocations(int after_n);
 
 /* Check hook for the quadrotor's nearest-cylinder grid (host only, no GPU needed).  Builds
  * the grid that mppi_set_env builds for the forest obs [n_obs][3] (x, y, radius; n_obs in

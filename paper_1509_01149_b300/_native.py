@@ -24,6 +24,7 @@ STATE_DIM = {MPPI_CARTPOLE: 4, MPPI_CAR: 7, MPPI_QUAD: 12, MPPI_CAR_MLP: 7, MPPI
 CONTROL_DIM = {MPPI_CARTPOLE: 1, MPPI_CAR: 2, MPPI_QUAD: 4, MPPI_CAR_MLP: 2, MPPI_CARTPOLE_VEL: 1}
 
 MPPI_EBUSY = -7
+MPPI_EAGAIN = -8
 
 
 class SlotConfig(C.Structure):
@@ -39,6 +40,11 @@ class ServerInfo(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("active_slots", C.c_int32), ("arena_bytes", C.c_uint64),
                 ("arena_used", C.c_uint64), ("rollout_block", C.c_int32), ("rollout_ctas_per_sm", C.c_int32),
                 ("ticks", C.c_int32), ("last_tick_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("running", C.c_int32), ("pad", C.c_int32), ("queued", C.c_int64), ("in_flight", C.c_int64),
+                ("ticks", C.c_int64), ("completed", C.c_int64)]
 
 
 # (name, restype, argtypes) of every exported symbol declared in include/mppi.h
@@ -70,8 +76,8 @@ SIGNATURES = [
     ("mppi_get_noise", C.c_int, [_P, C.c_uint32, _FP]),
     ("mppi_philox_words", C.c_int, [C.c_uint64, C.c_int, C.c_int, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32)]),
     ("mppi_step_static", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float, _FP, _FP,
-                                   C.c_uint64, C.c_uint32, C.c_uint32, C.c_char_p, _P, _P, _P, _P, _P,
-                                   C.c_char_p, C.c_size_t]),
+                                   C.c_uint64, C.c_uint32, C.c_uint32, C.c_char_p, _P, C.c_size_t, _P, _P, _P,
+                                   _P, C.c_char_p, C.c_size_t]),
     ("mppi_server_create", C.c_int, [C.c_int, C.c_size_t, C.POINTER(_P)]),
     ("mppi_server_destroy", C.c_int, [_P]),
     ("mppi_server_set_env", C.c_int, [_P, C.c_int, C.c_char_p, C.c_size_t]),
@@ -79,13 +85,26 @@ SIGNATURES = [
     ("mppi_server_release", C.c_int, [_P, C.c_int]),
     ("mppi_server_set_controls", C.c_int, [_P, C.c_int, _FP]),
     ("mppi_server_get_controls", C.c_int, [_P, C.c_int, _FP]),
+    ("mppi_server_get_debug", C.c_int, [_P, C.c_int, _FP, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("mppi_server_tick", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP, _FP]),
     ("mppi_server_autotune", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP]),
     ("mppi_server_get_info", C.c_int, [_P, C.POINTER(ServerInfo)]),
     ("mppi_server_last_error", C.c_char_p, [_P]),
+    ("mppi_server_start", C.c_int, [_P, C.c_int]),
+    ("mppi_server_stop", C.c_int, [_P]),
+    ("mppi_server_submit", C.c_int, [_P, C.c_int, _FP, C.POINTER(C.c_uint64)]),
+    ("mppi_server_submit_batch", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP, C.POINTER(C.c_uint64)]),
+    ("mppi_server_poll", C.c_int, [_P, C.c_uint64, _FP]),
+    ("mppi_server_wait", C.c_int, [_P, C.c_uint64, C.c_double, _FP]),
+    ("mppi_server_reap", C.c_int, [_P, C.c_int, C.POINTER(C.c_uint64), _FP, C.POINTER(C.c_int), C.c_double,
+                                   C.POINTER(C.c_int)]),
+    ("mppi_server_cancel", C.c_int, [_P, C.c_uint64]),
+    ("mppi_server_get_stats", C.c_int, [_P, C.POINTER(ServerStats)]),
     ("mppi_debug_forest_nearest", C.c_int, [_FP, C.c_int, C.c_int, _FP, _FP, _FP, _FP, C.POINTER(C.c_int)]),
     ("mppi_debug_gemm_bf16", C.c_int, [C.c_int, C.c_int, C.c_int, _P, C.c_int64, C.c_int64, _P, C.c_int64,
                                        C.c_int64, _P, C.c_int64, C.c_int]),
+    ("mppi_debug_gemm_wait_timeout", C.c_int, [C.c_uint32]),
+    ("mppi_debug_fail_allocations", C.c_int, [C.c_int]),
     ("mppi_mlp_create", C.c_int, [C.c_uint64, C.POINTER(_P)]),
     ("mppi_mlp_destroy", C.c_int, [_P]),
     ("mppi_mlp_set_params", C.c_int, [_P, _FP, _FP]),
@@ -182,16 +201,18 @@ def mppi_philox_words(seed: int, K: int, n_blocks: int, counter: int, gid: int) 
 
 
 def mppi_step_static(system: int, K: int, T: int, dt: float, nu: float, lam: float, Sigma, R, seed: int, gid: int,
-                     counter: int, env_header: bytes | None, d_env_payload: int, d_state: int, d_U: int,
-                     d_u0_out: int, stream: int = 0):
+                     counter: int, env_header: bytes | None, d_env_payload: int, env_payload_bytes: int,
+                     d_state: int, d_U: int, d_u0_out: int, stream: int = 0):
     """The allocation-free iteration (mppi_step_static): every buffer is a device pointer the
-    caller owns; the work is enqueued on `stream` and not waited for."""
+    caller owns (env_payload_bytes: the size of the d_env_payload buffer); the work is
+    enqueued on `stream` and not waited for."""
     m = CONTROL_DIM[int(system)]
     S = _f32(Sigma, m * m)
     Rm = None if R is None else _f32(R, m * m)
     err = C.create_string_buffer(512)
     rc = lib.mppi_step_static(int(system), K, T, dt, nu, lam, _fp(S), None if Rm is None else _fp(Rm), seed, gid,
-                              counter, env_header, C.c_void_p(d_env_payload or 0), C.c_void_p(d_state),
+                              counter, env_header, C.c_void_p(d_env_payload or 0), int(env_payload_bytes),
+                              C.c_void_p(d_state),
                               C.c_void_p(d_U), C.c_void_p(d_u0_out), C.c_void_p(stream), err, len(err))
     if rc != MPPI_OK:
         raise MppiError(rc, err.value.decode())
@@ -439,6 +460,14 @@ class Server:
         self._chk(lib.mppi_server_get_controls(self._h, slot, _fp(U)))
         return U
 
+    def get_debug(self, slot: int, K: int) -> dict:
+        """The slot's last tick: path costs S [K], argmin and the FP64 normaliser eta."""
+        S = np.zeros(K, dtype=np.float32)
+        k = C.c_int()
+        eta = C.c_double()
+        self._chk(lib.mppi_server_get_debug(self._h, slot, _fp(S), C.byref(k), C.byref(eta)))
+        return dict(S=S, kstar=k.value, eta=eta.value)
+
     @staticmethod
     def _pack(slots, states):
         ids = np.ascontiguousarray(np.asarray(slots, dtype=np.int32))
@@ -463,6 +492,63 @@ class Server:
         i = ServerInfo()
         self._chk(lib.mppi_server_get_info(self._h, C.byref(i)))
         return {k: getattr(i, k) for k, _ in ServerInfo._fields_}
+
+    # -- asynchronous interface (continuous batching) ------------------------------------
+    def start(self, max_batch: int = 0):
+        self._chk(lib.mppi_server_start(self._h, max_batch))
+
+    def stop(self):
+        self._chk(lib.mppi_server_stop(self._h))
+
+    def submit(self, slot: int, state) -> int:
+        """Queue one step of the controller in `slot`; returns the request id."""
+        st = np.zeros(16, dtype=np.float32)
+        x = np.asarray(state, dtype=np.float32).reshape(-1)
+        st[:x.size] = x
+        rid = C.c_uint64()
+        self._chk(lib.mppi_server_submit(self._h, slot, _fp(st), C.byref(rid)))
+        return rid.value
+
+    def submit_batch(self, slots, states) -> np.ndarray:
+        """Queue one step for each listed slot (states [n][<=16]); returns the request ids [n]."""
+        ids, st = self._pack(slots, states)
+        out = np.zeros(len(ids), dtype=np.uint64)
+        self._chk(lib.mppi_server_submit_batch(self._h, len(ids), ids.ctypes.data_as(C.POINTER(C.c_int)), _fp(st),
+                                               out.ctypes.data_as(C.POINTER(C.c_uint64))))
+        return out
+
+    def poll(self, rid: int):
+        """u0 [4] if the request has finished, None if not yet (raises on a failed or unknown id)."""
+        u0 = np.zeros(4, dtype=np.float32)
+        rc = lib.mppi_server_poll(self._h, rid, _fp(u0))
+        if rc == MPPI_EAGAIN:
+            return None
+        self._chk(rc)
+        return u0
+
+    def wait(self, rid: int, timeout_ms: float = 10000.0):
+        u0 = np.zeros(4, dtype=np.float32)
+        self._chk(lib.mppi_server_wait(self._h, rid, timeout_ms, _fp(u0)))
+        return u0
+
+    def reap(self, max_n: int = 4096, timeout_ms: float = 0.0):
+        """Finished requests in completion order: (ids [n], u0 [n][4], status [n])."""
+        ids = np.zeros(max_n, dtype=np.uint64)
+        u0 = np.zeros((max_n, 4), dtype=np.float32)
+        st = np.zeros(max_n, dtype=np.int32)
+        n = C.c_int()
+        self._chk(lib.mppi_server_reap(self._h, max_n, ids.ctypes.data_as(C.POINTER(C.c_uint64)), _fp(u0),
+                                       st.ctypes.data_as(C.POINTER(C.c_int)), timeout_ms, C.byref(n)))
+        k = n.value
+        return ids[:k], u0[:k], st[:k]
+
+    def cancel(self, rid: int):
+        self._chk(lib.mppi_server_cancel(self._h, rid))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self._chk(lib.mppi_server_get_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_ if k != "pad"}
 
 
 MLP_NUM_PARAMS = 74256

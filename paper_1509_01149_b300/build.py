@@ -3,8 +3,9 @@
     python -m paper_1509_01149_b300.build [--force]
 
 nvcc compiles every .cu under csrc/ for sm_103a (-gencode arch=compute_103a,code=sm_103a)
-with -O3 -lineinfo and links one shared library with the CUDA runtime linked statically.
-The build is skipped when the library is newer than every source.
+with -O3 -lineinfo, one process per source file in parallel (object files under
+_build/ at the repository root), and links one shared library with the CUDA runtime
+linked statically.  The build is skipped when the library is newer than every source.
 """
 from __future__ import annotations
 
@@ -13,11 +14,14 @@ import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libmppi_b300.so")
+OBJ_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def sources():
@@ -25,7 +29,8 @@ def sources():
 
 
 def _deps():
-    return sources() + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + [os.path.join(ROOT, "include", "mppi.h")]
+    return (sources() + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + glob.glob(os.path.join(HERE, "csrc", "*.h"))
+            + [os.path.join(ROOT, "include", "mppi.h")])
 
 
 def up_to_date() -> bool:
@@ -45,14 +50,29 @@ def nvcc() -> str:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    inc = ["-I", os.path.join(ROOT, "include")]
+
+    def compile_one(src):
+        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+        cmd = [nvcc(), *FLAGS, *inc, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        return obj, r
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(sources()), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(compile_one, sources()))
+    errs = [r.stdout + r.stderr for _, r in results if r.returncode != 0]
+    if errs:
+        raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, *sources()]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     if verbose:
-        print(" ".join(cmd))
+        print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
     return LIB
 

@@ -12,9 +12,15 @@
 #include <vector>
 
 #include "../../include/mppi.h"
+#include "alloc_fault.h"
 #include "forest_grid.h"
+#include "host_params.h"
 #include "kernels.cuh"
 #include "mlp_model.cuh"
+
+namespace mppi {
+std::atomic<int> g_alloc_fail_countdown{-1};
+}
 
 using namespace mppi;
 
@@ -43,54 +49,9 @@ int control_dim(int sys) {
   }
 }
 
-// Textbook Cholesky of a symmetric positive semi-definite m x m matrix (double).
-bool cholesky_psd(const double *S, int m, double *L) {
-  for (int i = 0; i < m * m; ++i) L[i] = 0.0;
-  for (int j = 0; j < m; ++j) {
-    double d = S[j * m + j];
-    for (int l = 0; l < j; ++l) d -= L[j * m + l] * L[j * m + l];
-    if (d < -1e-9 * std::fmax(1.0, std::fabs(S[j * m + j]))) return false;
-    L[j * m + j] = std::sqrt(std::fmax(d, 0.0));
-    for (int i = j + 1; i < m; ++i) {
-      double a = S[i * m + j];
-      for (int l = 0; l < j; ++l) a -= L[i * m + l] * L[j * m + l];
-      L[i * m + j] = L[j * m + j] > 0.0 ? a / L[j * m + j] : 0.0;
-    }
-  }
-  return true;
-}
-
-bool symmetric(const double *A, int m) {
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < i; ++j)
-      if (std::fabs(A[i * m + j] - A[j * m + i]) > 1e-6 * (std::fabs(A[i * m + j]) + std::fabs(A[j * m + i]) + 1e-30))
-        return false;
-  return true;
-}
-
-// Gauss-Jordan inverse (double), false if singular.
-bool invert(const double *A, int m, double *Ai) {
-  double a[kMaxM * 2 * kMaxM];
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < 2 * m; ++j) a[i * 2 * m + j] = j < m ? A[i * m + j] : (j - m == i ? 1.0 : 0.0);
-  for (int c = 0; c < m; ++c) {
-    int piv = c;
-    for (int r = c + 1; r < m; ++r)
-      if (std::fabs(a[r * 2 * m + c]) > std::fabs(a[piv * 2 * m + c])) piv = r;
-    if (std::fabs(a[piv * 2 * m + c]) < 1e-300) return false;
-    for (int j = 0; j < 2 * m; ++j) std::swap(a[c * 2 * m + j], a[piv * 2 * m + j]);
-    const double d = a[c * 2 * m + c];
-    for (int j = 0; j < 2 * m; ++j) a[c * 2 * m + j] /= d;
-    for (int r = 0; r < m; ++r)
-      if (r != c) {
-        const double f = a[r * 2 * m + c];
-        for (int j = 0; j < 2 * m; ++j) a[r * 2 * m + j] -= f * a[c * 2 * m + j];
-      }
-  }
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) Ai[i * m + j] = a[i * 2 * m + m + j];
-  return true;
-}
+using host::cholesky_psd;
+using host::invert;
+using host::symmetric;
 
 // Bump allocator over one device allocation (256-byte aligned slices).
 struct Arena {
@@ -131,6 +92,7 @@ struct mppi_ctx {
   BlockPartial *d_part = nullptr;
   StepDebug *d_dbg = nullptr;
   float *d_du = nullptr;       // plain-loop / debug noise [TM][K] (lazy)
+  double *d_plain = nullptr;   // plain-loop reduction scratch, inside the d_du allocation
   uint32_t *d_ctr = nullptr;   // scratch counter for mppi_get_noise
   float *d_env = nullptr;      // cost map or forest (separate allocation)
   size_t env_bytes = 0;
@@ -221,17 +183,21 @@ int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
   return launch_update(c, c->d_u0, s);
 }
 
+// du [T*m][K] for the plain loop and the noise check hook, followed (256-byte aligned) by the
+// plain loop's FP64 reduction scratch; allocated on first use.
 int ensure_noise_buffer(mppi_ctx *c) {
   if (c->d_du) return MPPI_OK;
-  const size_t bytes = sizeof(float) * static_cast<size_t>(c->T) * c->m * c->K;
-  return c->cuda(cudaMalloc(&c->d_du, bytes), "cudaMalloc(noise)");
+  const size_t du_bytes = (sizeof(float) * static_cast<size_t>(c->T) * c->m * c->K + 255) & ~static_cast<size_t>(255);
+  MPPI_TRY(c->cuda(cudaMalloc(&c->d_du, du_bytes + sizeof(double) * plain_scratch_doubles(c->p)), "cudaMalloc(noise)"));
+  c->d_plain = reinterpret_cast<double *>(reinterpret_cast<char *>(c->d_du) + du_bytes);
+  return MPPI_OK;
 }
 
 int enqueue_plain(mppi_ctx *c, cudaStream_t s) {
   MPPI_TRY(ensure_noise_buffer(c));
   MPPI_TRY(c->cuda(launch_plain_noise(c->p, &c->d_st->counter, c->d_du, s), "plain noise"));
   MPPI_TRY(c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->d_U, c->d_du, c->d_S, s), "plain rollout"));
-  return c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, s),
+  return c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, c->d_plain, s),
                  "plain reduce/update");
 }
 
@@ -402,6 +368,11 @@ int set_mlp_env(mppi_ctx *c, const void *blob, size_t bytes) {
 
 extern "C" {
 
+int mppi_debug_fail_allocations(int after_n) {
+  g_alloc_fail_countdown.store(after_n < 0 ? -1 : after_n);
+  return MPPI_OK;
+}
+
 const char *mppi_version(void) { return "mppi-b300 0.1 (sm_103a)"; }
 
 const char *mppi_last_error(mppi_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
@@ -418,27 +389,8 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   if (n == 0) return bad("unknown system");
   if (K < 1 || K > (1 << 20)) return bad("K out of range [1, 1048576]");
   if (T < 1 || T > 1024) return bad("T out of range [1, 1024]");
-  if (!(dt > 0.0f) || !std::isfinite(dt)) return bad("dt must be > 0");
-  if (!(nu > 0.0f) || !std::isfinite(nu)) return bad("nu must be > 0");
-  if (!(lambda > 0.0f) || !std::isfinite(lambda)) return bad("lambda must be > 0");
-  if (!Sigma) return bad("Sigma is NULL");
-
-  double S[kMaxM * kMaxM], L[kMaxM * kMaxM], Rd[kMaxM * kMaxM];
-  for (int i = 0; i < m * m; ++i) S[i] = Sigma[i];
-  if (!symmetric(S, m)) return bad("Sigma is not symmetric");
-  if (!cholesky_psd(S, m, L)) return bad("Sigma is not positive semi-definite");
-  if (R) {
-    for (int i = 0; i < m * m; ++i) Rd[i] = R[i];
-    double LR[kMaxM * kMaxM];
-    if (!symmetric(Rd, m)) return bad("R is not symmetric");
-    if (!cholesky_psd(Rd, m, LR)) return bad("R is not positive definite");
-    for (int j = 0; j < m; ++j)
-      if (!(LR[j * m + j] > 0.0)) return bad("R is not positive definite");
-  } else {
-    double Si[kMaxM * kMaxM];
-    if (!invert(S, m, Si)) return bad("R = lambda Sigma^-1 needs Sigma positive definite");
-    for (int i = 0; i < m * m; ++i) Rd[i] = lambda * Si[i];
-  }
+  float Lnu[kMaxM * kMaxM], Rf[kMaxM * kMaxM];
+  if (const char *why = host::control_constants(m, dt, nu, lambda, Sigma, R, Lnu, Rf)) return bad(why);
 
   mppi_ctx *c = new (std::nothrow) mppi_ctx();
   if (!c) return MPPI_ENOMEM;
@@ -457,10 +409,9 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   p.lambda = lambda;
   p.inv_lambda = 1.0f / lambda;
   p.is_du = 0.5f * static_cast<float>(1.0 - 1.0 / static_cast<double>(nu));
-  const double snu = std::sqrt(static_cast<double>(nu));
   for (int i = 0; i < m * m; ++i) {
-    p.Lnu[i] = static_cast<float>(snu * L[i]);
-    p.R[i] = static_cast<float>(Rd[i]);
+    p.Lnu[i] = Lnu[i];
+    p.R[i] = Rf[i];
   }
   p.key_lo = 0;
   p.key_hi = 0;
@@ -492,7 +443,7 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   c->nblk_cap = static_cast<int>(nb_max);
   c->arena.size = 256 * 16 + sizeof(CtrlState) + sizeof(float) * (2 * TM + 2 * kMaxM + K + nb_max * TM) +
                   sizeof(BlockPartial) * nb_max + sizeof(StepDebug) + 2 * sizeof(uint32_t);
-  if (rc == MPPI_OK) rc = c->cuda(cudaMalloc(&c->arena.base, c->arena.size), "cudaMalloc(arena)");
+  if (rc == MPPI_OK) rc = c->cuda(dev_malloc(&c->arena.base, c->arena.size), "cudaMalloc(arena)");
   if (rc == MPPI_OK) {
     c->d_st = c->arena.take<CtrlState>(1);
     c->d_U = c->arena.take<float>(TM);
@@ -509,17 +460,17 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   }
   if (rc == MPPI_OK) rc = c->cuda(cudaMemsetAsync(c->arena.base, 0, c->arena.size, c->stream), "memset");
   if (rc == MPPI_OK)
-    rc = c->cuda(cudaHostAlloc(reinterpret_cast<void **>(&c->h_x0), sizeof(float) * kMaxN, cudaHostAllocMapped),
+    rc = c->cuda(host_alloc(&c->h_x0, sizeof(float) * kMaxN, cudaHostAllocMapped),
                  "cudaHostAlloc");
   if (rc == MPPI_OK)
-    rc = c->cuda(cudaHostAlloc(reinterpret_cast<void **>(&c->h_u0), sizeof(float) * kMaxM, cudaHostAllocMapped),
+    rc = c->cuda(host_alloc(&c->h_u0, sizeof(float) * kMaxM, cudaHostAllocMapped),
                  "cudaHostAlloc");
   if (rc == MPPI_OK)
     rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_x0), c->h_x0, 0), "mapped x0");
   if (rc == MPPI_OK)
     rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_u0), c->h_u0, 0), "mapped u0");
   if (rc == MPPI_OK)
-    rc = c->cuda(cudaHostAlloc(reinterpret_cast<void **>(&c->h_ready), sizeof(unsigned int), cudaHostAllocMapped),
+    rc = c->cuda(host_alloc(&c->h_ready, sizeof(unsigned int), cudaHostAllocMapped),
                  "cudaHostAlloc");
   if (rc == MPPI_OK)
     rc = c->cuda(cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->dh_ready), c->h_ready, 0), "mapped flag");
@@ -896,7 +847,7 @@ int mppi_update_async(mppi_ctx *c, float *d_u0_out) {
   if (!c) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
   if (c->impl == MPPI_IMPL_PLAIN) {
-    MPPI_TRY(c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, c->stream),
+    MPPI_TRY(c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, c->d_plain, c->stream),
                      "plain reduce/update"));
     if (d_u0_out)
       MPPI_TRY(c->cuda(cudaMemcpyAsync(d_u0_out, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToDevice, c->stream),

@@ -514,51 +514,93 @@ __global__ void __launch_bounds__(1024) k_plain_min(const float *__restrict__ S,
   }
 }
 
-__global__ void __launch_bounds__(1024) k_plain_eta(const float *__restrict__ S, int K, float inv_lambda,
-                                                    StepDebug *__restrict__ dbg) {
-  __shared__ double s_e[32];
+// The plain loop's reduction (Eq. App_PI with the min shift), unfused but coalesced and in
+// FP64 throughout: k_plain_weights forms every w_k = exp(-(S~_k - rho)/lambda) once (FP64
+// exponential) with per-block partial sums of eta; k_plain_wsum reads each row of du [T*m][K]
+// once, kPlainRows rows by kPlainSplitK samples per block, FP64 products and sums into
+// per-split partials; k_plain_finalize adds the partials in a fixed order, divides by eta and
+// updates U.  Scratch (doubles): w [K] | eta partials [ceil(K/256)] | wsum partials [splits][T*m].
+constexpr int kPlainBlock = 256;
+constexpr int kPlainRows = 4;
+constexpr int kPlainSplitK = 2048;
+
+__global__ void __launch_bounds__(kPlainBlock) k_plain_weights(const float *__restrict__ S, int K, float lambda,
+                                                               const StepDebug *__restrict__ dbg,
+                                                               double *__restrict__ w, double *__restrict__ eta_part) {
+  __shared__ double s_e[kPlainBlock / 32];
+  const int k = blockIdx.x * kPlainBlock + threadIdx.x;
   const float rho = dbg->rho;
   double e = 0.0;
-  if (isfinite(rho))
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-      if (isfinite(S[k])) e += exp(-static_cast<double>(S[k] - rho) * inv_lambda);
+  if (k < K) {
+    const float Sk = S[k];
+    if (isfinite(rho) && isfinite(Sk))
+      e = exp(-(static_cast<double>(Sk) - static_cast<double>(rho)) / static_cast<double>(lambda));
+    w[k] = e;
+  }
   e = warp_sum_d(e);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) s_e[warp] = e;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int q = 0; q < static_cast<int>(blockDim.x >> 5); ++q) t += s_e[q];
-    dbg->eta = t;
+#pragma unroll
+    for (int q = 0; q < kPlainBlock / 32; ++q) t += s_e[q];
+    eta_part[blockIdx.x] = t;
   }
 }
 
-__global__ void __launch_bounds__(256) k_plain_wsum(const float *__restrict__ S, const float *__restrict__ du, int K,
-                                                    int m, float inv_lambda, const StepDebug *__restrict__ dbg,
-                                                    float *__restrict__ U, float *__restrict__ u0_out,
-                                                    float *__restrict__ dU_dbg) {
-  __shared__ double s_a[8];
-  const int o = blockIdx.x;
-  const float rho = dbg->rho;
-  const double eta = dbg->eta;
-  double acc = 0.0;
-  if (isfinite(rho))
-    for (int k = threadIdx.x; k < K; k += blockDim.x)
-      if (isfinite(S[k]))
-        acc += exp(-static_cast<double>(S[k] - rho) * inv_lambda) * static_cast<double>(du[static_cast<size_t>(o) * K + k]);
-  acc = warp_sum_d(acc);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) s_a[warp] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += s_a[q];
-    const double d = eta > 0.0 ? t / eta : 0.0;
-    const float un = U[o] + static_cast<float>(d);
-    U[o] = un;
-    dU_dbg[o] = static_cast<float>(d);
-    if (o < m) u0_out[o] = un;
+__global__ void __launch_bounds__(kPlainBlock) k_plain_wsum(const float *__restrict__ du, const double *__restrict__ w,
+                                                            int K, int TM, double *__restrict__ part) {
+  __shared__ double s_a[kPlainRows][kPlainBlock / 32];
+  const int k0 = blockIdx.x * kPlainSplitK, r0 = blockIdx.y * kPlainRows;
+  const int k1 = min(K, k0 + kPlainSplitK);
+  double acc[kPlainRows];
+#pragma unroll
+  for (int r = 0; r < kPlainRows; ++r) acc[r] = 0.0;
+  for (int k = k0 + threadIdx.x; k < k1; k += kPlainBlock) {
+    const double wk = w[k];
+#pragma unroll
+    for (int r = 0; r < kPlainRows; ++r)
+      if (r0 + r < TM) acc[r] = fma(wk, static_cast<double>(du[static_cast<size_t>(r0 + r) * K + k]), acc[r]);
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < kPlainRows; ++r) {
+    const double v = warp_sum_d(acc[r]);
+    if (lane == 0) s_a[r][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kPlainRows && r0 + threadIdx.x < TM) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kPlainBlock / 32; ++q) t += s_a[threadIdx.x][q];
+    part[static_cast<size_t>(blockIdx.x) * TM + r0 + threadIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kPlainBlock) k_plain_finalize(const double *__restrict__ eta_part, int n_eta,
+                                                                const double *__restrict__ part, int n_split, int TM,
+                                                                int m, StepDebug *__restrict__ dbg,
+                                                                float *__restrict__ U, float *__restrict__ u0_out,
+                                                                float *__restrict__ dU_dbg) {
+  __shared__ double s_eta;
+  if (threadIdx.x == 0) {
+    double e = 0.0;
+    for (int b = 0; b < n_eta; ++b) e += eta_part[b];
+    s_eta = e;
+    if (blockIdx.x == 0) dbg->eta = e;
+  }
+  __syncthreads();
+  const double eta = s_eta;
+  const int o = blockIdx.x * kPlainBlock + threadIdx.x;
+  if (o >= TM) return;
+  double t = 0.0;
+  for (int b = 0; b < n_split; ++b) t += part[static_cast<size_t>(b) * TM + o];
+  const double d = eta > 0.0 ? t / eta : 0.0;
+  const float un = U[o] + static_cast<float>(d);
+  U[o] = un;
+  dU_dbg[o] = static_cast<float>(d);
+  if (o < m) u0_out[o] = un;
 }
 
 // ---------------------------------------------------------------------------
@@ -917,15 +959,28 @@ cudaError_t launch_plain_rollout(int sys, const CtrlParams &p, const CtrlState *
   return cudaGetLastError();
 }
 
+size_t plain_scratch_doubles(const CtrlParams &p) {
+  const size_t TM = static_cast<size_t>(p.T) * p.m;
+  const size_t n_eta = (p.K + kPlainBlock - 1) / kPlainBlock, n_split = (p.K + kPlainSplitK - 1) / kPlainSplitK;
+  return static_cast<size_t>(p.K) + n_eta + n_split * TM;
+}
+
 cudaError_t launch_plain_reduce_update(const CtrlParams &p, const float *S, const float *du, float *U, float *u0_out,
-                                       float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
+                                       float *dU_dbg, StepDebug *dbg, double *scratch, cudaStream_t s) {
+  const int TM = p.T * p.m;
+  const int n_eta = (p.K + kPlainBlock - 1) / kPlainBlock, n_split = (p.K + kPlainSplitK - 1) / kPlainSplitK;
+  double *w = scratch, *eta_part = scratch + p.K, *part = eta_part + n_eta;
   k_plain_min<<<1, 1024, 0, s>>>(S, p.K, dbg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_plain_eta<<<1, 1024, 0, s>>>(S, p.K, p.inv_lambda, dbg);
+  k_plain_weights<<<n_eta, kPlainBlock, 0, s>>>(S, p.K, p.lambda, dbg, w, eta_part);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_plain_wsum<<<p.T * p.m, 256, 0, s>>>(S, du, p.K, p.m, p.inv_lambda, dbg, U, u0_out, dU_dbg);
+  k_plain_wsum<<<dim3(n_split, (TM + kPlainRows - 1) / kPlainRows), kPlainBlock, 0, s>>>(du, w, p.K, TM, part);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_plain_finalize<<<(TM + kPlainBlock - 1) / kPlainBlock, kPlainBlock, 0, s>>>(eta_part, n_eta, part, n_split, TM, p.m,
+                                                                                 dbg, U, u0_out, dU_dbg);
   return cudaGetLastError();
 }
 

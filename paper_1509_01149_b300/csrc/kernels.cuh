@@ -88,8 +88,10 @@ cudaError_t launch_rollout_mlp(const CtrlParams &p, const float *x0, const CtrlS
 cudaError_t launch_plain_noise(const CtrlParams &p, const uint32_t *counter, float *du, cudaStream_t s);
 cudaError_t launch_plain_rollout(int sys, const CtrlParams &p, const CtrlState *st, const float *U,
                                  const float *du, float *S, cudaStream_t s);
+// Scratch (doubles) of the plain loop's reduction for this configuration.
+size_t plain_scratch_doubles(const CtrlParams &p);
 cudaError_t launch_plain_reduce_update(const CtrlParams &p, const float *S, const float *du, float *U,
-                                       float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s);
+                                       float *u0_out, float *dU_dbg, StepDebug *dbg, double *scratch, cudaStream_t s);
 
 // Debug ------------------------------------------------------------------------
 cudaError_t launch_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_blocks, uint32_t counter,

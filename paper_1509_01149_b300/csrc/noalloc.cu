@@ -18,6 +18,7 @@
 #include <string>
 
 #include "../../include/mppi.h"
+#include "host_params.h"
 #include "kernels.cuh"
 
 using namespace mppi;
@@ -45,24 +46,32 @@ struct ErrorSink {
   }
 };
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device.  Only a
+// successful set-up is remembered: a failed one (for example a first call made during a
+// stream capture) is tried again by the next call.
 struct DeviceSetup {
-  std::once_flag once;
+  std::mutex mu;
+  bool ready = false;
   unsigned char *ptr = nullptr;
-  cudaError_t status = cudaSuccess;
 };
 DeviceSetup g_setup[kMaxDevices];
 
 cudaError_t scratch_for_device(int dev, unsigned char **out) {
   DeviceSetup &s = g_setup[dev];
-  std::call_once(s.once, [&s] {
+  std::lock_guard<std::mutex> lock(s.mu);
+  if (!s.ready) {
     void *p = nullptr;
-    s.status = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (s.status == cudaSuccess) s.status = prepare_kernels();
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e == cudaSuccess) e = prepare_kernels();
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e;
+    }
     s.ptr = static_cast<unsigned char *>(p);
-  });
+    s.ready = true;
+  }
   *out = s.ptr;
-  return s.status;
+  return cudaSuccess;
 }
 
 // Copies the caller's state into the scratch state block and sets the iteration
@@ -83,57 +92,25 @@ int dims(int sys, int *n, int *m) {
   }
 }
 
-// Lower Cholesky factor of a symmetric positive semi-definite matrix (double).
-bool chol(const double *S, int m, double *L) {
-  for (int i = 0; i < m * m; ++i) L[i] = 0.0;
-  for (int j = 0; j < m; ++j) {
-    double d = S[j * m + j];
-    for (int l = 0; l < j; ++l) d -= L[j * m + l] * L[j * m + l];
-    if (d < -1e-9 * std::fmax(1.0, std::fabs(S[j * m + j]))) return false;
-    L[j * m + j] = std::sqrt(std::fmax(d, 0.0));
-    for (int i = j + 1; i < m; ++i) {
-      double a = S[i * m + j];
-      for (int l = 0; l < j; ++l) a -= L[i * m + l] * L[j * m + l];
-      L[i * m + j] = L[j * m + j] > 0.0 ? a / L[j * m + j] : 0.0;
-    }
-  }
-  return true;
-}
-
-// Inverse of an SPD matrix from its Cholesky factor (double).
-void spd_inverse(const double *L, int m, double *Ai) {
-  double Li[kMaxM * kMaxM] = {0};
-  for (int j = 0; j < m; ++j) {
-    Li[j * m + j] = 1.0 / L[j * m + j];
-    for (int i = j + 1; i < m; ++i) {
-      double a = 0.0;
-      for (int l = j; l < i; ++l) a -= L[i * m + l] * Li[l * m + j];
-      Li[i * m + j] = a / L[i * m + i];
-    }
-  }
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) {
-      double a = 0.0;
-      for (int l = 0; l < m; ++l) a += Li[l * m + i] * Li[l * m + j];
-      Ai[i * m + j] = a;
-    }
-}
-
 size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 
 }  // namespace
 
 extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float nu, float lambda, const float *h_Sigma,
                                 const float *h_R, uint64_t seed, uint32_t gid, uint32_t counter,
-                                const void *h_env_header, const float *d_env_payload, const float *d_state,
+                                const void *h_env_header, const float *d_env_payload, size_t env_payload_bytes,
+                                const float *d_state,
                                 float *d_U, float *d_u0_out, void *cuda_stream, char *h_err, size_t err_len) {
   const ErrorSink fail{h_err, err_len};
   if (h_err && err_len > 0) h_err[0] = '\0';
   int n = 0, m = 0;
-  if (dims(sys, &n, &m) != MPPI_OK) return fail(MPPI_EINVAL, "unknown or unsupported system");
-  if (K < 1 || T < 1 || T > 1024) return fail(MPPI_EINVAL, "K must be >= 1 and T in [1, 1024]");
-  if (!(dt > 0.0f) || !(nu > 0.0f) || !(lambda > 0.0f)) return fail(MPPI_EINVAL, "dt, nu, lambda must be > 0");
-  if (!h_Sigma || !d_state || !d_U || !d_u0_out) return fail(MPPI_EINVAL, "null Sigma, state, U or u0 pointer");
+  if (dims(sys, &n, &m) != MPPI_OK)
+    return fail(MPPI_EINVAL, "unknown or unsupported system (the learned-dynamics car is not served here)");
+  if (K < 1 || K > (1 << 20) || T < 1 || T > 1024) return fail(MPPI_EINVAL, "K must be in [1, 1048576] and T in [1, 1024]");
+  if (!d_state || !d_U || !d_u0_out) return fail(MPPI_EINVAL, "null state, U or u0 pointer");
+  float Lnu[kMaxM * kMaxM], Rf[kMaxM * kMaxM];
+  if (const char *why = host::control_constants(m, dt, nu, lambda, h_Sigma, h_R, Lnu, Rf))
+    return fail(MPPI_EINVAL, why);
 
   CtrlParams p{};
   p.K = K;
@@ -150,31 +127,9 @@ extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float n
   p.gid = gid;
   p.map_w = p.map_h = 2;
   p.map_inv_cell = 1.0f;
-
-  double S[kMaxM * kMaxM], L[kMaxM * kMaxM], Rd[kMaxM * kMaxM];
-  for (int i = 0; i < m * m; ++i) S[i] = h_Sigma[i];
-  if (!chol(S, m, L)) return fail(MPPI_EINVAL, "Sigma is not positive semi-definite");
-  if (h_R) {
-    for (int i = 0; i < m * m; ++i) Rd[i] = h_R[i];
-    double LR[kMaxM * kMaxM];
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < i; ++j)
-        if (std::fabs(Rd[i * m + j] - Rd[j * m + i]) > 1e-6 * (std::fabs(Rd[i * m + j]) + std::fabs(Rd[j * m + i])))
-          return fail(MPPI_EINVAL, "R is not symmetric");
-    if (!chol(Rd, m, LR)) return fail(MPPI_EINVAL, "R is not positive definite");
-    for (int j = 0; j < m; ++j)
-      if (!(LR[j * m + j] > 0.0)) return fail(MPPI_EINVAL, "R is not positive definite");
-  } else {
-    for (int j = 0; j < m; ++j)
-      if (!(L[j * m + j] > 0.0)) return fail(MPPI_EINVAL, "R = lambda Sigma^-1 needs Sigma positive definite");
-    double Si[kMaxM * kMaxM];
-    spd_inverse(L, m, Si);
-    for (int i = 0; i < m * m; ++i) Rd[i] = lambda * Si[i];
-  }
-  const double snu = std::sqrt(static_cast<double>(nu));
   for (int i = 0; i < m * m; ++i) {
-    p.Lnu[i] = static_cast<float>(snu * L[i]);
-    p.R[i] = static_cast<float>(Rd[i]);
+    p.Lnu[i] = Lnu[i];
+    p.R[i] = Rf[i];
   }
 
   // environment: a host header describing a device payload the caller owns
@@ -185,8 +140,13 @@ extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float n
     if (sys == MPPI_CAR) {
       mppi_env_map h;
       std::memcpy(&h, h_env_header, sizeof h);
-      if (kind != MPPI_ENV_MAP || h.width < 2 || h.height < 2 || !(h.cell > 0.0f))
+      if (kind != MPPI_ENV_MAP || h.width < 2 || h.height < 2 || h.width > 16384 || h.height > 16384 ||
+          !(h.cell > 0.0f) || !std::isfinite(h.cell) || !std::isfinite(h.origin_x) || !std::isfinite(h.origin_y))
         return fail(MPPI_EINVAL, "bad cost-map header");
+      const size_t need = sizeof(float) * static_cast<size_t>(h.width) * static_cast<size_t>(h.height);
+      if (env_payload_bytes < need)
+        return fail(MPPI_EINVAL, "cost-map payload holds " + std::to_string(env_payload_bytes) + " bytes; the header needs " +
+                                     std::to_string(need));
       p.map = d_env_payload;
       p.map_w = h.width;
       p.map_h = h.height;
@@ -198,6 +158,10 @@ extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float n
       std::memcpy(&h, h_env_header, sizeof h);
       if (kind != MPPI_ENV_FOREST || h.n_obstacles < 0 || h.n_obstacles > 256)
         return fail(MPPI_EINVAL, "bad forest header");
+      const size_t need = sizeof(float) * 3 * static_cast<size_t>(h.n_obstacles);
+      if (env_payload_bytes < need)
+        return fail(MPPI_EINVAL, "forest payload holds " + std::to_string(env_payload_bytes) + " bytes; the header needs " +
+                                     std::to_string(need));
       p.obs = d_env_payload;
       p.n_obs = h.n_obstacles;
       for (int i = 0; i < 3; ++i) p.goal[i] = h.goal[i];
@@ -219,8 +183,10 @@ extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float n
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return fail(MPPI_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(MPPI_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(MPPI_EINVAL, "device " + std::to_string(dev) + " is beyond the " + std::to_string(kMaxDevices) +
+                                 " devices this entry point keeps a scratch address for");
   unsigned char *base = nullptr;
   e = scratch_for_device(dev, &base);
   if (e != cudaSuccess || !base) return fail(MPPI_ECUDA, std::string("static scratch set-up: ") + cudaGetErrorString(e));

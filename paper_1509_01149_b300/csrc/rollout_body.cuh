@@ -263,23 +263,31 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
     }
   } else {
     const int nb = (TM + 3) >> 2;
+    // A warp whose samples all have weight exactly 0 (exp underflow: S~ - rho_b beyond ~103
+    // lambda) adds exactly 0 to every output, so it skips the regeneration; with sharp
+    // weights that is most warps of a block.
+    const bool warp_live = __any_sync(0xffffffffu, w != 0.0f);
     // regenerate du, weight it, transpose-reduce 32 outputs (8 Philox blocks) at a time
     for (int g = 0; g < nb; g += 8) {
       float v[32];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (g + q < nb && k != INT_MAX)  // k == INT_MAX: a thread that owns no sample
-          normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+      for (int q = 0; q < 32; ++q) v[q] = 0.0f;
+      if (warp_live) {
 #pragma unroll
-        for (int s = 0; s < SPB; ++s) {
-          float du[M];
-          scale_noise<M>(Lnu, eps + s * M, du);
+        for (int q = 0; q < 8; ++q) {
+          float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+          if (g + q < nb && k != INT_MAX)  // k == INT_MAX: a thread that owns no sample
+            normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
 #pragma unroll
-          for (int j = 0; j < M; ++j) v[q * 4 + s * M + j] = w * du[j];
+          for (int s = 0; s < SPB; ++s) {
+            float du[M];
+            scale_noise<M>(Lnu, eps + s * M, du);
+#pragma unroll
+            for (int j = 0; j < M; ++j) v[q * 4 + s * M + j] = w * du[j];
+          }
         }
       }
-      const float wsum = transpose_reduce32(v);
+      const float wsum = warp_live ? transpose_reduce32(v) : 0.0f;
       s_red[warp][lane] = wsum;
       __syncthreads();
       if (warp == 0) {

@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+  const uint32_t wait_limit = g.wait_limit ? g.wait_limit : tc::kWaitLimit;
   uint32_t phase = 0;
   bool ok = true;
 
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
     }
     tc::fence_smem_to_async();
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !g.debug_skip_mma) {
       tc::fence_after_sync();
       const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
       const uint32_t lbo_a = kBM * 16, lbo_b = BN * 16;
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
       }
       tc::mma_commit(&bar);
     }
-    const bool got = tc::mbar_wait(&bar, phase);
+    const bool got = tc::mbar_wait(&bar, phase, wait_limit);
     phase ^= 1u;
     tc::fence_after_sync();
     ok = __syncthreads_and(got) != 0;  // block-uniform
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
 
   if (!ok) {
     if (tid == 0) atomicExch(g.err, 1);
-    tc::mbar_wait(&bar, phase ^ 1u);  // second, bounded chance for the MMAs in flight
+    tc::mbar_wait(&bar, phase ^ 1u, wait_limit);  // second, bounded chance for the MMAs in flight
   } else {
     // epilogue: row m = m0 + 32*warp + lane, columns n0 .. n0+BN
     const int m = m0 + 32 * warp + lane;
@@ -206,6 +207,53 @@ extern "C" int mppi_debug_gemm_bf16(int M, int N, int K, const void *dA, int64_t
   int err = 0;
   if (e == cudaSuccess) e = cudaMemcpy(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(d_err);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return -3;
+  }
+  return err ? -4 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI check hook of the bounded-wait exit path: one GEMM CTA (128 x 128 x 128, zero
+// operands) whose MMA issuer issues nothing, so its accumulator barrier never completes; the
+// waits give up after `polls` polls, the kernel raises its error flag, frees its TMEM and
+// returns.  Nothing asynchronous (no MMA, no bulk copy) is outstanding when it does.
+// ---------------------------------------------------------------------------
+extern "C" int mppi_debug_gemm_wait_timeout(uint32_t polls) {
+  using namespace mppi;
+  if (polls < 1 || polls > (1u << 20)) return -1;
+  constexpr int M = 128, N = 128, K = 128;
+  void *buf = nullptr;
+  const size_t ab = sizeof(__nv_bfloat16) * M * K, cb = sizeof(float) * M * N;
+  if (cudaMalloc(&buf, 2 * ab + cb + 256) != cudaSuccess) {
+    cudaGetLastError();
+    return -2;
+  }
+  cudaError_t e = cudaMemset(buf, 0, 2 * ab + cb + 256);
+  GemmArgs g{};
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.BN = N;
+  g.A = static_cast<const __nv_bfloat16 *>(buf);
+  g.sam = K;
+  g.sak = 1;
+  g.B = reinterpret_cast<const __nv_bfloat16 *>(static_cast<char *>(buf) + ab);
+  g.sbk = N;
+  g.sbn = 1;
+  g.mode = kEpiStoreF32;
+  g.alpha = 1.0f;
+  g.Cf = reinterpret_cast<float *>(static_cast<char *>(buf) + 2 * ab);
+  g.ldc = N;
+  g.err = reinterpret_cast<int *>(static_cast<char *>(buf) + 2 * ab + cb);
+  g.wait_limit = polls;
+  g.debug_skip_mma = 1;
+  if (e == cudaSuccess) e = launch_gemm_bf16(g, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&err, g.err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return -3;

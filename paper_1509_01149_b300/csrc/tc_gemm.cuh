@@ -33,6 +33,8 @@ struct GemmArgs {
   int64_t ldh;
   int *err;                     // set to 1 if a bounded wait ran out
   int ksplit;                   // K range split over gridDim.z CTAs (mode kEpiAtomicF32); 0/1 = no split
+  uint32_t wait_limit;          // mbarrier polls before a wait gives up (0: tc::kWaitLimit)
+  int debug_skip_mma;           // check hook only: issue no MMA (so the waits run out, nothing in flight)
 };
 
 // Dynamic shared memory of the GEMM CTA.  Sized so the tiles (48 KB) sit well inside the

@@ -176,3 +176,181 @@ class ServingLoop:
 def poisson_rate_for(target_active: int, mean_lifetime: float) -> float:
     """Arrivals per tick that hold `target_active` controllers in steady state (Little's law)."""
     return target_active / mean_lifetime if mean_lifetime > 0 else math.inf
+
+
+# ---------------------------------------------------------------------------------------
+# Real-time closed loop over the asynchronous interface (submit / reap)
+# ---------------------------------------------------------------------------------------
+@dataclass
+class AsyncStats:
+    latency_ms: list = field(default_factory=list)    # submit -> result, every request
+    missed_periods: int = 0                           # periods skipped: the previous result came too late
+    periods: int = 0
+    rollout_steps: int = 0
+    admitted: int = 0
+    released: int = 0
+    refused_attempts: int = 0
+    plant_resets: int = 0
+    active: list = field(default_factory=list)
+
+    def summary(self, wall_s: float) -> dict:
+        lat = np.asarray(self.latency_ms, dtype=np.float64)
+        return {
+            "requests": int(lat.size),
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "max_ms": float(lat.max()) if lat.size else None,
+            "deadline_miss_rate": float((lat > DEADLINE_MS).mean()) if lat.size else None,
+            "missed_periods": self.missed_periods,
+            "periods": self.periods,
+            "mean_active": float(np.mean(self.active)) if self.active else 0.0,
+            "rollout_steps_per_s": self.rollout_steps / wall_s if wall_s > 0 else None,
+            "admitted": self.admitted, "released": self.released, "refused_attempts": self.refused_attempts,
+            "plant_resets": self.plant_resets,
+        }
+
+
+class AsyncServingLoop:
+    """Controllers arrive as a Poisson process in time and stay for a random number of control
+    periods; each runs at `period_ms` (50 Hz) from a random phase, in closed loop: at each
+    period it submits a step request from its plant's current state, and when the u0 comes
+    back the plant advances by one period under it (`plant(system, X [n][nx], U [n][m], dt)`,
+    vectorised over controllers of one system; None keeps the state fixed).  A controller
+    whose result has not come back by its next period skips that period (a deadline miss).
+    Admission and release happen while ticks are on the GPU.  Records every request's
+    latency from submit to result."""
+
+    def __init__(self, server, workloads_mod, env_ids: dict, plant=None, seed: int = 0, period_ms: float = 20.0,
+                 systems=SYSTEMS, k_choices=K_CHOICES, t_choices=T_CHOICES, system_p=None, k_p=None, t_p=None):
+        self.server, self.W, self.env_ids, self.plant = server, workloads_mod, env_ids, plant
+        self.rng = np.random.default_rng(seed)
+        self.period = period_ms / 1e3
+        self.systems, self.k_choices, self.t_choices = systems, k_choices, t_choices
+        self.system_p, self.k_p, self.t_p = system_p, k_p, t_p
+        self.ctrl = {}        # slot -> dict(system, K, T, x, x0, dt, due, left, outstanding, t_submit)
+        self.waiting = []     # arrived, not yet admitted: (system, K, T, lifetime)
+        self.next_rid = 0
+        self.stats = AsyncStats()
+
+    def _arrival(self, mean_lifetime_periods: float):
+        return (int(self.rng.choice(self.systems, p=self.system_p)), int(self.rng.choice(self.k_choices, p=self.k_p)),
+                int(self.rng.choice(self.t_choices, p=self.t_p)),
+                max(1, int(self.rng.geometric(1.0 / max(mean_lifetime_periods, 1.0)))))
+
+    def _admit_waiting(self, now: float):
+        still = []
+        for system, K, T, life in self.waiting:
+            cfg = default_config(system, K, T, self.next_rid, self.server, self.W, self.env_ids)
+            slot = self.server.admit(cfg)
+            if slot is None:
+                self.stats.refused_attempts += 1
+                still.append((system, K, T, life))
+                continue
+            self.next_rid += 1
+            c = self.W.config(system)
+            x0 = np.asarray(c["x0"], dtype=np.float64)
+            self.ctrl[slot] = dict(system=system, K=K, T=T, x=x0.copy(), x0=x0, dt=c["dt"],
+                                   due=now + self.rng.uniform(0.0, self.period), left=life, outstanding=None,
+                                   t_submit=0.0)
+            self.stats.admitted += 1
+        self.waiting = still
+
+    def _apply_results(self, ids, u0, status, now):
+        by_sys = {}
+        for rid, u, st in zip(ids, u0, status):
+            slot = self._by_id.pop(int(rid), None)
+            if slot is None:
+                continue
+            c = self.ctrl[slot]
+            c["outstanding"] = None
+            self.stats.latency_ms.append(1e3 * (now - c["t_submit"]))
+            self.stats.rollout_steps += c["K"] * c["T"]
+            if st != 0:
+                continue
+            by_sys.setdefault(c["system"], []).append((slot, u))
+        for system, items in by_sys.items():
+            slots = [s for s, _ in items]
+            m = self.W.CONTROL_DIM[system]
+            U = np.stack([u[:m] for _, u in items]).astype(np.float64)
+            X = np.stack([self.ctrl[s]["x"] for s in slots])
+            if self.plant is not None:
+                X = self.plant(system, X, U, self.ctrl[slots[0]]["dt"])
+            for s, x in zip(slots, X):
+                c = self.ctrl[s]
+                if not np.all(np.isfinite(x)):
+                    x = c["x0"].copy()
+                    self.stats.plant_resets += 1
+                c["x"] = x
+
+    def run(self, duration_s: float, target_active: int, mean_lifetime_periods: float = 200.0,
+            warmup_s: float = 0.5) -> dict:
+        """Hold about `target_active` controllers for warmup_s + duration_s of wall time
+        (arrival rate from Little's law); statistics cover the last duration_s."""
+        srv = self.server
+        self._by_id = {}
+        rate = target_active / (mean_lifetime_periods * self.period)      # arrivals per second
+        t0 = time.perf_counter()
+        for _ in range(target_active):
+            self.waiting.append(self._arrival(mean_lifetime_periods))
+        self._admit_waiting(t0)
+        srv.start()
+        t_rec, t_end, t_last = t0 + warmup_s, t0 + warmup_s + duration_s, t0
+        recording = False
+        try:
+            while True:
+                now = time.perf_counter()
+                if now >= t_end:
+                    break
+                if not recording and now >= t_rec:
+                    recording = True
+                    self.stats = AsyncStats(admitted=self.stats.admitted)
+                # arrivals (Poisson in time) and admission, with ticks in flight
+                for _ in range(self.rng.poisson(rate * (now - t_last))):
+                    self.waiting.append(self._arrival(mean_lifetime_periods))
+                t_last = now
+                if self.waiting:
+                    self._admit_waiting(now)
+                # due controllers submit; one whose last result is still out skips the period
+                due_slots, due_states = [], []
+                for slot, c in list(self.ctrl.items()):
+                    if c["due"] > now:
+                        continue
+                    c["due"] += self.period
+                    if c["outstanding"] is not None:
+                        self.stats.missed_periods += 1
+                        continue
+                    if c["left"] <= 0:
+                        srv.release(slot)
+                        del self.ctrl[slot]
+                        self.stats.released += 1
+                        continue
+                    c["left"] -= 1
+                    self.stats.periods += 1
+                    due_slots.append(slot)
+                    due_states.append(c["x"].astype(np.float32))
+                if due_slots:
+                    ids = srv.submit_batch(due_slots, due_states)
+                    ts = time.perf_counter()
+                    for slot, rid in zip(due_slots, ids):
+                        self.ctrl[slot]["outstanding"] = int(rid)
+                        self.ctrl[slot]["t_submit"] = ts
+                        self._by_id[int(rid)] = slot
+                self.stats.active.append(len(self.ctrl))
+                # results: wait until the next due time at most
+                next_due = min((c["due"] for c in self.ctrl.values()), default=now + 1e-3)
+                wait_ms = max(0.0, min(1.0, 1e3 * (next_due - time.perf_counter())))
+                ids, u0, st = srv.reap(4096, timeout_ms=wait_ms)
+                if len(ids):
+                    self._apply_results(ids, u0, st, time.perf_counter())
+        finally:
+            srv.stop()
+            ids, u0, st = srv.reap(4096, timeout_ms=0.0)
+            if len(ids):
+                self._apply_results(ids, u0, st, time.perf_counter())
+        return self.stats.summary(duration_s)
+
+    def drain(self):
+        for slot in list(self.ctrl):
+            self.server.release(slot)
+        self.ctrl.clear()
+        self.waiting.clear()

@@ -123,3 +123,42 @@ def update_step_within_cost_error(U_gpu, U_orc, U0, du, S, rho, lam, tol, band_r
     big = 1e3
     w, _ = nnls(np.vstack([D, big * np.ones((1, A.size))]), np.concatenate([U_gpu - U0, [big]]))
     return bool(np.all(np.abs(U_gpu - (U0 + D @ w)) <= tol))
+
+
+U32 = 2.0 ** -24       # unit roundoff of FP32
+
+
+def reduction_errors(S_gpu, du_gpu, lam, eta_gpu, dU_gpu, kstar_gpu):
+    """The weighting and weighted sum (Eq. App_PI with the min shift) checked on the GPU's own
+    path costs and perturbations, so that the rollout's FP32 error drops out: the oracle's
+    FP64 `weights` and `weighted_update` run on S_gpu [K] and du_gpu [T][m][K].
+
+    Error budget of the kernels (u = 2^-24): each weight exp(-X_k), X_k = (S_k - rho)/lambda,
+    is formed in FP32 as a block weight times a block scale, each from a rounded difference,
+    a rounded product with the FP32 1/lambda and the FP32 exponential (2 ulp), so its relative
+    error is at most (3 X_k + 8) u; the block sums of w_k du_k are FP32 sums over at most 9
+    levels (4 per lane, then a 5-level butterfly), and everything after them (the cross-block
+    double-FP32 sums, the FP64 normaliser and division) adds errors of order 2^-48.  Bounds:
+      |eta_gpu - eta| <= sum_k e^-X_k (4 X_k + 10) u
+      |dU_gpu - dU|   <= [sum_k e^-X_k |du_k| ((4 X_k + 10) u + 12 u)] / eta
+                         + |dU| (|eta_gpu - eta| bound / eta + 2 u)   (+ FP32 storage of dU).
+    Returns a dict with the oracle values, the observed errors and the bounds."""
+    S = np.asarray(S_gpu, dtype=np.float64)
+    du = np.asarray(du_gpu, dtype=np.float64)
+    rho, kstar, eta, w = omppi.weights(S, lam)
+    dU, _ = omppi.weighted_update(np.zeros(du.shape[:2]), du, w)
+    fin = np.isfinite(S)
+    X = np.where(fin, (S - rho) / lam, np.inf) if np.isfinite(rho) else np.full_like(S, np.inf)
+    E = np.where(fin, np.exp(-X), 0.0)
+    a = np.where(fin, (4.0 * np.where(fin, X, 0.0) + 10.0) * U32, 0.0)
+    eta_bound = float(np.sum(E * a)) + 1e-15 * eta
+    if eta > 0:
+        num = np.einsum("tmk,k->tm", np.abs(du), E * (a + 12.0 * U32))
+        dU_bound = num / eta + np.abs(dU) * (eta_bound / eta + 2.0 * U32) + 1e-30
+    else:
+        dU_bound = np.full(dU.shape, 1e-30)
+    eta_err = abs(float(eta_gpu) - eta)
+    dU_err = np.abs(np.asarray(dU_gpu, dtype=np.float64) - dU)
+    return dict(rho=rho, kstar=kstar, eta=eta, dU=dU, eta_err=eta_err, eta_bound=eta_bound,
+                eta_rel=eta_err / eta if eta > 0 else 0.0, dU_err=dU_err, dU_bound=dU_bound,
+                kstar_match=(int(kstar_gpu) == kstar))

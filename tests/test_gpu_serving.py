@@ -99,6 +99,39 @@ def test_served_result_matches_the_oracle(N):
     srv.close()
 
 
+def test_served_ticks_match_the_oracle_costs_argmin_and_controls(N):
+    """Three receding-horizon ticks of every system in one batch, each checked against the
+    oracle on the same inputs (the oracle is given the slot's FP32 controls before each tick):
+    path costs S~ within the S~ bar, k* exact where the oracle's minimum is unique, the
+    normaliser and weighted sum on the GPU's own costs at the kernels' own error, and the
+    updated, shifted controls within the U bar."""
+    from oracle import mppi as om
+    srv = make_server(N)
+    picks = [(W.CAR, 2048, 60), (W.CARTPOLE, 1000, 100), (W.QUAD, 1024, 40), (W.CAR, 777, 13)]
+    slots, cfgs = zip(*[admit(srv, s, K, T, 200 + i) for i, (s, K, T) in enumerate(picks)])
+    states = [W.config(p[0])["x0"] for p in picks]
+    for tick in range(3):
+        U_before = [srv.get_controls(sl) for sl in slots]
+        u0 = srv.tick(list(slots), states)
+        for i, (s, K, T) in enumerate(picks):
+            c = dict(cfgs[i], seed=200 + i, gid=200 + i, U=U_before[i].astype(np.float64))
+            o = P.oracle_iteration(c, counter=tick)
+            dbg = srv.get_debug(slots[i], K)
+            keep = (o.margin > 1e-3) if o.margin is not None else None
+            rel = P.s_errors(dbg["S"], o.S, keep)
+            assert rel.size > 0 and rel.max() <= P.S_RTOL, (i, tick, rel.max())
+            if P.argmin_is_unique(o.S):
+                assert dbg["kstar"] == o.kstar, (i, tick)
+            du = P.noise_oracle(c, tick).astype(np.float32)
+            r = P.reduction_errors(dbg["S"], du, float(np.float32(c["lam"])), dbg["eta"],
+                                   np.zeros((T, W.CONTROL_DIM[s])), dbg["kstar"])
+            assert r["kstar_match"] and r["eta_err"] <= r["eta_bound"], (i, tick, r["eta_err"], r["eta_bound"])
+            m = W.CONTROL_DIM[s]
+            assert within(u0[i, :m], o.u0, c), (i, tick)
+            assert within(srv.get_controls(slots[i]), om.shift(o.U, c["u_init"]), c), (i, tick)
+    srv.close()
+
+
 def test_admission_is_by_arena_memory(N):
     srv = make_server(N, max_slots=64, arena=6 << 20)
     got = []
