@@ -79,6 +79,9 @@ def parse():
                     help="measure the largest 50 Hz concurrency of every (system, K, T) (about a minute)")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-dynamics measurement")
+    ap.add_argument("--shard-k", action="store_true",
+                    help="with several ranks: one controller K-sharded over them (weak scaling) instead of "
+                         "one independent controller per rank")
     ap.add_argument("--learned-only", action="store_true")
     ap.add_argument("--no-systems", action="store_true", help="skip the per-workload iteration table")
     ap.add_argument("--nu-sweep", action="store_true",
@@ -840,6 +843,73 @@ def load_profile(kernel_tag: str):
     return d
 
 
+def run_sharded(args, rank, world, dev, stream, dist):
+    """One controller K-sharded over the ranks (weak scaling: K_SAMPLES samples per rank, the
+    controller has K_SAMPLES * world): per step each rank rolls out its shard, the ranks
+    all-gather their partials (NCCL, the only collective) and every rank merges them and
+    shifts.  Same timing rules as the replicated run (barrier + synchronize around the timed
+    steps, L2 flushed between them outside the events, max over ranks)."""
+    import torch
+
+    from paper_1509_01149_b300 import _native as N
+    from paper_1509_01149_b300 import sharded
+    K_total = K_SAMPLES * world
+    ctrl, cfg = make_ctrl(N, N.MPPI_IMPL_FUSED, seed=1000, gid=0, stream_handle=stream.cuda_stream, K=K_total)
+    sc = sharded.ShardedController(ctrl, rank, world, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        d_x0 = torch.tensor(cfg["x0"], dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        sc.step(d_x0.data_ptr(), stream)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            sc.step(d_x0.data_ptr(), stream)
+            ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    total_s = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, dev)
+    value = K_total * T_STEPS * args.steps / total_s
+    # e2e: x0 from pinned host memory, u0 back to the host, every step
+    x_host = torch.tensor(cfg["x0"], dtype=torch.float32).pin_memory()
+    lat = []
+    for s in range(args.e2e_steps + 50):
+        dist.barrier()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            d_x0.copy_(x_host, non_blocking=True)
+        u0 = sc.step(d_x0.data_ptr(), stream)
+        with torch.cuda.stream(stream):
+            u0_host = u0.to("cpu", non_blocking=False)
+        lat.append(time.perf_counter() - t0)
+    lat = lat[50:]
+    e2e_total = reduce_max(sum(lat), dist, dev)
+    if rank == 0:
+        lat_ms = sorted(1e3 * x for x in lat)
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "car on cost-map track, one K-sharded controller, one MPPI iteration + shift per step",
+                       "K": K_total, "K_per_rank": K_SAMPLES, "T": T_STEPS, "nu": NU, "lambda": 1.0,
+                       "parallelism": f"K-sharded over {world} ranks, one all-gather of (T*m + 3) doubles per rank "
+                                      f"and step (NCCL)",
+                       "l2": "flushed between timed steps (256 MB write, outside the timed events)"},
+            "e2e": {"value": K_total * T_STEPS * len(lat) / e2e_total, "unit": UNIT,
+                    "h2d_bytes_per_step": 4 * ctrl.n, "d2h_bytes_per_step": 4 * ctrl.m,
+                    "p50_ms": lat_ms[len(lat_ms) // 2], "p99_ms": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))],
+                    "latency_samples": len(lat_ms)},
+            "gpu_launches": 4 * args.steps,
+            "source_hash": source_hash()}), flush=True)
+    dist.destroy_process_group()
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -880,6 +950,9 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     stream = torch.cuda.Stream(device=dev)
+    if args.shard_k and world > 1:
+        run_sharded(args, rank, world, dev, stream, dist)
+        return
     ctrl, cfg = make_ctrl(N, N.MPPI_IMPL_FUSED, seed=1000 + rank, gid=rank, stream_handle=stream.cuda_stream)
     n, m = ctrl.n, ctrl.m
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 126 MB L2

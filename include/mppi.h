@@ -242,7 +242,31 @@ int mppi_get_noise(mppi_ctx *ctx, uint32_t counter, float *h_du);
 int mppi_philox_words(uint64_t seed, int K, int n_blocks, uint32_t counter, uint32_t gid,
                       uint32_t *h_out);
 
-/* One MPPI iteration that allocates nothing (no ctx, no cudaMalloc, no pinned memory).
+/* ---- K-sharding: one controller's K samples over R ranks (data parallel) --------------
+ * The samples of one iteration are independent (the sampling loop of Algorithm 1), so rank r
+ * rolls out a contiguous range of them and the ranks exchange one small partial each:
+ *   1. every rank: mppi_set_shard(ctx, k_begin_r, k_count_r) once (global sample indices, so
+ *      the noise is the unsharded controller's; boundaries multiples of 128 except at K);
+ *   2. every rank: mppi_shard_partial_async(ctx, d_state, d_partial_r) -- rollout of the
+ *      rank's samples and its partial, TM + 3 doubles (TM = T*m):
+ *        [0] rho_r = min over the rank's S~ (+inf if none is finite), [1] k*_r (lowest global
+ *        index attaining it), [2] eta_r = sum_k exp(-(S~_k - rho_r)/lambda),
+ *        [3 + o] N_r[o] = sum_k exp(-(S~_k - rho_r)/lambda) du_{o,k}   (o = i*m + j);
+ *   3. the caller gathers the R partials in rank order into d_partials [R][TM + 3] on every
+ *      rank (one all-gather of (TM + 3) * R doubles);
+ *   4. every rank: mppi_shard_update_async(ctx, d_partials, R, d_u0_out) merges them in rank
+ *      order (FP64: rho = min rho_r, s_r = exp(-(rho_r - rho)/lambda), eta = sum_r s_r eta_r,
+ *      du = sum_r s_r N_r / eta -- Eq. App_PI with the min shift), updates U and writes u_0;
+ *      every rank holds the same U; then mppi_shift as usual.
+ * The result equals the unsharded iteration's up to the order of the FP64 sums.  With a
+ * shard set, mppi_step and the other iteration calls run the shard's samples alone.  Fused
+ * path, path weighting, analytic dynamics only (EINVAL otherwise).  All calls are
+ * asynchronous on the ctx stream; pointers named d_* are device memory. */
+int mppi_set_shard(mppi_ctx *ctx, int k_begin, int k_count);
+int mppi_shard_partial_async(mppi_ctx *ctx, const float *d_state, double *d_partial);
+int mppi_shard_update_async(mppi_ctx *ctx, const double *d_partials, int n_ranks, float *d_u0_out);
+
+/* One MPPI iteration that allocates nothing (no ctx, no cudaMalloc, no pinned memory)./* One MPPI iteration that allocates nothing (no ctx, no cudaMalloc, no pinned memory).
  * The paper has no counterpart: this is a service for callers that may not allocate
  * device memory while they run -- a real-time control loop that must not call
  * cudaMalloc after start-up (it can synchronise the device and its latency has no
@@ -383,6 +407,11 @@ typedef struct {
 
 /* Start the scheduler thread.  ESTATE if it already runs. */
 int mppi_server_start(mppi_server *srv, int max_batch);
+/* Batching of the scheduler: whenever the GPU has no tick, the queued requests are launched
+ * at once; while a tick runs, the next tick is formed once min_batch (>= 1) requests wait or
+ * the oldest has waited max_wait_ms (>= 0), so that it gathers what arrives meanwhile.
+ * Defaults 256 and 1.0 ms.  May be called at any time. */
+int mppi_server_set_batching(mppi_server *srv, int min_batch, double max_wait_ms);
 /* Finish every submitted request, then stop the thread.  Safe when it is not running. */
 int mppi_server_stop(mppi_server *srv);
 /* Queue one step of the controller in `slot` from h_state (host [16], state in the first n

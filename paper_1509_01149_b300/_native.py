@@ -68,6 +68,9 @@ SIGNATURES = [
     ("mppi_set_impl", C.c_int, [_P, C.c_int]),
     ("mppi_set_sampling_covariance", C.c_int, [_P, _FP]),
     ("mppi_set_weighting", C.c_int, [_P, C.c_int]),
+    ("mppi_set_shard", C.c_int, [_P, C.c_int, C.c_int]),
+    ("mppi_shard_partial_async", C.c_int, [_P, _P, _P]),
+    ("mppi_shard_update_async", C.c_int, [_P, _P, C.c_int, _P]),
     ("mppi_set_controls", C.c_int, [_P, _FP]),
     ("mppi_get_controls", C.c_int, [_P, _FP]),
     ("mppi_set_u_init", C.c_int, [_P, _FP]),
@@ -92,6 +95,7 @@ SIGNATURES = [
     ("mppi_server_last_error", C.c_char_p, [_P]),
     ("mppi_server_start", C.c_int, [_P, C.c_int]),
     ("mppi_server_stop", C.c_int, [_P]),
+    ("mppi_server_set_batching", C.c_int, [_P, C.c_int, C.c_double]),
     ("mppi_server_submit", C.c_int, [_P, C.c_int, _FP, C.POINTER(C.c_uint64)]),
     ("mppi_server_submit_batch", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP, C.POINTER(C.c_uint64)]),
     ("mppi_server_poll", C.c_int, [_P, C.c_uint64, _FP]),
@@ -339,6 +343,15 @@ class Controller:
 
     set_sampling_covariance = mppi_set_sampling_covariance
 
+    def mppi_set_shard(self, k_begin: int, k_count: int):
+        self._chk(lib.mppi_set_shard(self._h, k_begin, k_count))
+
+    def mppi_shard_partial_async(self, d_state: int, d_partial: int):
+        self._chk(lib.mppi_shard_partial_async(self._h, C.c_void_p(d_state), C.c_void_p(d_partial)))
+
+    def mppi_shard_update_async(self, d_partials: int, n_ranks: int, d_u0_out: int | None = None):
+        self._chk(lib.mppi_shard_update_async(self._h, C.c_void_p(d_partials), n_ranks, C.c_void_p(d_u0_out or 0)))
+
     def mppi_set_controls(self, U):
         self._chk(lib.mppi_set_controls(self._h, _fp(_f32(U, self.T * self.m))))
 
@@ -386,6 +399,9 @@ class Controller:
     set_env = mppi_set_env
     get_debug = mppi_get_debug
     get_noise = mppi_get_noise
+    set_shard = mppi_set_shard
+    shard_partial_async = mppi_shard_partial_async
+    shard_update_async = mppi_shard_update_async
 
 
 class Server:
@@ -499,6 +515,9 @@ class Server:
 
     def stop(self):
         self._chk(lib.mppi_server_stop(self._h))
+
+    def set_batching(self, min_batch: int = 256, max_wait_ms: float = 1.0):
+        self._chk(lib.mppi_server_set_batching(self._h, min_batch, max_wait_ms))
 
     def submit(self, slot: int, state) -> int:
         """Queue one step of the controller in `slot`; returns the request id."""

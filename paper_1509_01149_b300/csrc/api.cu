@@ -15,6 +15,7 @@
 #include "alloc_fault.h"
 #include "forest_grid.h"
 #include "host_params.h"
+#include "nvtx_range.h"
 #include "kernels.cuh"
 #include "mlp_model.cuh"
 
@@ -176,6 +177,11 @@ int launch_update_shift(mppi_ctx *c, float *u0_out, cudaStream_t s, unsigned int
   }
   MPPI_TRY(launch_update(c, u0_out, s, u0_ready));
   return c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, s), "shift launch");
+}
+
+// Blocks the rollout launches for this ctx's samples (all of K, or its shard).
+int block_count(const mppi_ctx *c) {
+  return (shard_samples(c->p) + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
 }
 
 int enqueue_fused(mppi_ctx *c, cudaStream_t s) {
@@ -431,7 +437,7 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
     delete c;
     return bad("T*m too large for the fused rollout's shared memory");
   }
-  c->nblk = (K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+  c->nblk = block_count(c);
 
   int rc = c->cuda(cudaGetDevice(&c->device), "cudaGetDevice");
   if (rc == MPPI_OK) rc = c->cuda(prepare_kernels(), "kernel attributes");
@@ -549,6 +555,8 @@ int mppi_set_impl(mppi_ctx *c, mppi_impl impl) {
     return c->fail(MPPI_EINVAL, "the plain loop is built for the path weighting only");
   if (impl == MPPI_IMPL_PLAIN && c->p.gen)
     return c->fail(MPPI_EINVAL, "the plain loop is built for the nu * Sigma sampling covariance only");
+  if (impl == MPPI_IMPL_PLAIN && (c->p.k_begin != 0 || c->p.k_count != 0))
+    return c->fail(MPPI_EINVAL, "the plain loop runs all K samples: clear the shard first");
   c->impl = impl;
   return MPPI_OK;
 }
@@ -598,12 +606,12 @@ int mppi_set_sampling_covariance(mppi_ctx *c, const float *h_Sigma_E) {
   if (blk == 0) {
     c->p.gen = nullptr;
     c->blk = block_shape(c, c->p);
-    c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+    c->nblk = block_count(c);
     c->graph_dirty = c->iter_graph_dirty = true;
     return c->fail(MPPI_EINVAL, "horizon too long for the per-step covariances in shared memory");
   }
   c->blk = blk;
-  c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+  c->nblk = block_count(c);
   c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
@@ -612,6 +620,8 @@ int mppi_set_weighting(mppi_ctx *c, int mode) {
   if (!c || (mode != MPPI_WEIGHT_PATH && mode != MPPI_WEIGHT_TO_GO)) return MPPI_EINVAL;
   if (mode == MPPI_WEIGHT_TO_GO) {
     if (c->sys == MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "the cost-to-go weighting is not built for the learned dynamics");
+    if (c->p.k_begin != 0 || c->p.k_count != 0)
+      return c->fail(MPPI_EINVAL, "the cost-to-go weighting is not built for K-sharding");
     if (c->impl == MPPI_IMPL_PLAIN) return c->fail(MPPI_EINVAL, "the plain loop is built for the path weighting only");
     if (fused_block_size_to_go(c->sys, c->p) == 0)
       return c->fail(MPPI_EINVAL, "horizon too long for the cost-to-go weighting's shared memory");
@@ -623,7 +633,7 @@ int mppi_set_weighting(mppi_ctx *c, int mode) {
   }
   c->weighting = mode;
   c->blk = block_shape(c, c->p);
-  c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+  c->nblk = block_count(c);
   c->graph_dirty = c->iter_graph_dirty = true;
   return MPPI_OK;
 }
@@ -770,7 +780,7 @@ int mppi_set_env(mppi_ctx *c, const void *blob, size_t bytes) {
   c->p = np;
   c->blk = block_shape(c, c->p);
   if (c->blk == 0) return c->fail(MPPI_EINVAL, "environment too large for the block's shared memory");
-  c->nblk = (c->K + fused_block_samples(c->blk) - 1) / fused_block_samples(c->blk);
+  c->nblk = block_count(c);
   if (c->nblk > c->nblk_cap) return c->fail(MPPI_EINVAL, "block shape needs more partials than allocated");
   c->env_ok = true;
   c->graph_dirty = c->iter_graph_dirty = true;
@@ -795,6 +805,7 @@ int wait_u0(mppi_ctx *c) {
 }
 
 int step_host(mppi_ctx *c, const float *state, float *u0_out, bool shift) {
+  const NvtxRange range(shift ? "mppi_step_shift (rollout, merge + update + shift)" : "mppi_step (rollout, merge + update)");
   if (!c || !state || !u0_out) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
   std::memcpy(c->h_x0, state, sizeof(float) * c->n);
@@ -858,11 +869,13 @@ int mppi_update_async(mppi_ctx *c, float *d_u0_out) {
 }
 
 int mppi_step_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
+  const NvtxRange range("mppi_step_async (rollout, merge + update)");
   MPPI_TRY(mppi_rollout_async(c, d_state));
   return mppi_update_async(c, d_u0_out);
 }
 
 int mppi_iterate_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
+  const NvtxRange range("mppi_iterate_async (graph: rollout, merge + update + shift)");
   if (!c || !d_state) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
   if (c->impl == MPPI_IMPL_PLAIN || c->stream == nullptr) {
@@ -941,6 +954,47 @@ int mppi_philox_words(uint64_t seed, int K, int n_blocks, uint32_t counter, uint
     cudaGetLastError();
     return MPPI_ECUDA;
   }
+  return MPPI_OK;
+}
+
+// ---- K-sharding: one controller's samples over several ranks --------------------------
+int mppi_set_shard(mppi_ctx *c, int k_begin, int k_count) {
+  if (!c) return MPPI_EINVAL;
+  const bool whole = k_begin == 0 && (k_count == 0 || k_count == c->K);
+  if (!whole) {
+    if (c->sys == MPPI_CAR_MLP) return c->fail(MPPI_EINVAL, "K-sharding is not built for the learned dynamics");
+    if (c->impl == MPPI_IMPL_PLAIN) return c->fail(MPPI_EINVAL, "K-sharding runs on the fused path only");
+    if (c->weighting != MPPI_WEIGHT_PATH) return c->fail(MPPI_EINVAL, "K-sharding is built for the path weighting only");
+    if (k_begin < 0 || k_count < 1 || static_cast<int64_t>(k_begin) + k_count > c->K)
+      return c->fail(MPPI_EINVAL, "shard [%d, %d + %d) is not inside [0, K = %d)", k_begin, k_begin, k_count, c->K);
+    if (k_begin % kShardAlign != 0 || (k_begin + k_count != c->K && k_count % kShardAlign != 0))
+      return c->fail(MPPI_EINVAL, "shard boundaries must be multiples of %d (except at K)", kShardAlign);
+  }
+  MPPI_TRY(c->cuda(cudaStreamSynchronize(c->stream), "sync"));  // no step of this ctx in flight
+  c->p.k_begin = whole ? 0 : k_begin;
+  c->p.k_count = whole ? 0 : k_count;
+  c->nblk = block_count(c);
+  c->graph_dirty = c->iter_graph_dirty = true;
+  return MPPI_OK;
+}
+
+int mppi_shard_partial_async(mppi_ctx *c, const float *d_state, double *d_partial) {
+  const NvtxRange range("mppi_shard_partial_async (rollout, shard partial)");
+  if (!c || !d_state || !d_partial) return MPPI_EINVAL;
+  MPPI_TRY(check_ready(c));
+  if (c->sys == MPPI_CAR_MLP || c->impl == MPPI_IMPL_PLAIN || c->weighting != MPPI_WEIGHT_PATH)
+    return c->fail(MPPI_EINVAL, "the shard partial is built for the fused path with the path weighting");
+  MPPI_TRY(launch_rollout(c, d_state, c->stream));
+  return c->cuda(launch_shard_partial(c->nblk, c->p, c->d_psum, c->d_part, d_partial, c->stream), "shard partial");
+}
+
+int mppi_shard_update_async(mppi_ctx *c, const double *d_partials, int n_ranks, float *d_u0_out) {
+  const NvtxRange range("mppi_shard_update_async (shard merge + update)");
+  if (!c || !d_partials || n_ranks < 1 || n_ranks > 4096) return MPPI_EINVAL;
+  MPPI_TRY(check_ready(c));
+  MPPI_TRY(c->cuda(launch_shard_update(c->p, d_partials, n_ranks, c->d_U, d_u0_out ? d_u0_out : c->d_u0, c->d_dU,
+                                       c->d_dbg, c->stream),
+                   "shard update"));
   return MPPI_OK;
 }
 

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(BLK) k_rollout_fused(const CtrlParams p, const
                                                        float *__restrict__ S_out, float *__restrict__ part_sums,
                                                        BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block<Sys, BLK, REGEN, false, GEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
+  rollout_block<Sys, BLK, REGEN, false, GEN>(p, x0, st->counter, U, p.k_begin + blockIdx.x * BLK, S_out,
                                  part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
                                  smem);
 }
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(BLK) k_rollout_to_go(const CtrlParams p, const
                                                        BlockPartial *__restrict__ part, float *__restrict__ part_rho,
                                                        DF *__restrict__ part_eta) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block<Sys, BLK, false, true, GEN>(p, x0, st->counter, U, blockIdx.x * BLK, S_out,
+  rollout_block<Sys, BLK, false, true, GEN>(p, x0, st->counter, U, p.k_begin + blockIdx.x * BLK, S_out,
                                        part_sums + static_cast<size_t>(blockIdx.x) * p.T * Sys::M, part + blockIdx.x,
                                        smem, nullptr, part_rho + static_cast<size_t>(blockIdx.x) * p.T,
                                        part_eta + static_cast<size_t>(blockIdx.x) * p.T);
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws(const CtrlP
                                                               float *__restrict__ part_sums,
                                                               BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block_car_ws<NS, false, GEN>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+  rollout_block_car_ws<NS, false, GEN>(p, x0, st->counter, U, p.k_begin + blockIdx.x * NS, S_out,
                                        part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x,
                                        smem);
 }
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kWsRoles * NS, 1) k_rollout_car_ws_to_go(
     float *__restrict__ S_out, float *__restrict__ part_sums, BlockPartial *__restrict__ part,
     float *__restrict__ part_rho, DF *__restrict__ part_eta) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block_car_ws<NS, true, GEN>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+  rollout_block_car_ws<NS, true, GEN>(p, x0, st->counter, U, p.k_begin + blockIdx.x * NS, S_out,
                                  part_sums + static_cast<size_t>(blockIdx.x) * p.T * Car::M, part + blockIdx.x, smem,
                                  part_rho + static_cast<size_t>(blockIdx.x) * p.T,
                                  part_eta + static_cast<size_t>(blockIdx.x) * p.T);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(3 * NS, 1) k_rollout_quad_ws(const CtrlParams 
                                                                float *__restrict__ part_sums,
                                                                BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block_quad_ws<NS, GEN>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+  rollout_block_quad_ws<NS, GEN>(p, x0, st->counter, U, p.k_begin + blockIdx.x * NS, S_out,
                             part_sums + static_cast<size_t>(blockIdx.x) * p.T * Quad::M, part + blockIdx.x, smem);
 }
 
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(3 * NS, 1) k_rollout_quad_ws_to_go(
     float *__restrict__ S_out, float *__restrict__ part_sums, BlockPartial *__restrict__ part,
     float *__restrict__ part_rho, DF *__restrict__ part_eta) {
   extern __shared__ __align__(16) float smem[];
-  rollout_block_quad_ws<NS, false, true>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+  rollout_block_quad_ws<NS, false, true>(p, x0, st->counter, U, p.k_begin + blockIdx.x * NS, S_out,
                                          part_sums + static_cast<size_t>(blockIdx.x) * p.T * Quad::M, part + blockIdx.x,
                                          smem, part_rho + static_cast<size_t>(blockIdx.x) * p.T,
                                          part_eta + static_cast<size_t>(blockIdx.x) * p.T);
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(BLK) k_rollout_quad_lanes(const CtrlParams p, 
                                                             BlockPartial *__restrict__ part) {
   extern __shared__ __align__(16) float smem[];
   constexpr int NS = BLK / LANES;
-  rollout_block_quad_lanes<BLK, LANES>(p, x0, st->counter, U, blockIdx.x * NS, S_out,
+  rollout_block_quad_lanes<BLK, LANES>(p, x0, st->counter, U, p.k_begin + blockIdx.x * NS, S_out,
                                        part_sums + static_cast<size_t>(blockIdx.x) * p.T * Quad::M,
                                        part + blockIdx.x, smem);
 }
@@ -250,6 +250,125 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
     cluster_sync_all();  // all shifted values read before any is overwritten
     if (warp == 0 && o < TM) U[o] = sh;
     if (blockIdx.x == 0 && tid == 0) st->counter += 1u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K-sharding: the rank-local reduction and the merge of every rank's partial
+// ---------------------------------------------------------------------------
+// k_shard_partial reduces this rank's block partials in the merge's fixed order (merge_common.cuh)
+// relative to the rank's own minimum, and writes the rank's partial as TM + 3 doubles:
+//   [0] rho_r (+inf if no finite cost), [1] k*_r (lowest global sample index attaining it),
+//   [2] eta_r = sum_{k in rank} exp(-(S~_k - rho_r)/lambda),
+//   [3 + o] N_r[o] = sum_{k in rank} exp(-(S~_k - rho_r)/lambda) du_{o,k}.
+// One CTA per 32 outputs, warp r = range r of the block partials.
+__global__ void __launch_bounds__(kMergeThreads) k_shard_partial(int nblk, int TM, float inv_lambda,
+                                                                 const float *__restrict__ part_sums,
+                                                                 const BlockPartial *__restrict__ part,
+                                                                 double *__restrict__ out) {
+  constexpr int NW = kMergeThreads / 32;
+  extern __shared__ double s_eb[];  // [nblk] eta_b, then [nblk] floats: rho_b, then s_b
+  float *s_sc = reinterpret_cast<float *>(s_eb + nblk);
+  __shared__ float s_rho[NW];
+  __shared__ int s_k[NW];
+  __shared__ DF s_part[NW][kMergeOutputs];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int o = blockIdx.x * kMergeOutputs + lane;
+  const int L = merge_range_len(nblk), b0 = min(nblk, warp * L), b1 = min(nblk, b0 + L);
+  float v = INFINITY;
+  int idx = INT_MAX;
+  for (int b = tid; b < nblk; b += kMergeThreads) {
+    const BlockPartial bp = part[b];
+    s_eb[b] = bp.eta;
+    s_sc[b] = bp.rho;
+    if (bp.rho < v || (bp.rho == v && bp.kstar < idx)) {
+      v = bp.rho;
+      idx = bp.kstar;
+    }
+  }
+  warp_argmin(v, idx);
+  if (lane == 0) {
+    s_rho[warp] = v;
+    s_k[warp] = idx;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float vv = lane < NW ? s_rho[lane] : INFINITY;
+    int ii = lane < NW ? s_k[lane] : INT_MAX;
+    warp_argmin(vv, ii);
+    if (lane == 0) {
+      s_rho[0] = vv;
+      s_k[0] = ii;
+    }
+  }
+  __syncthreads();
+  const float rho = s_rho[0];
+  for (int b = tid; b < nblk; b += kMergeThreads) s_sc[b] = merge_scale(s_sc[b], rho, inv_lambda);
+  __syncthreads();
+  if (warp == 0) {
+    const double eta = merge_eta_warp(s_sc, s_eb, nblk, lane);
+    if (lane == 0 && blockIdx.x == 0) {
+      out[0] = static_cast<double>(rho);
+      out[1] = static_cast<double>(s_k[0]);
+      out[2] = eta;
+    }
+  }
+  DF acc{0.0f, 0.0f};
+  if (o < TM)
+    for (int b = b0; b < b1; ++b) df_add_prod(acc, s_sc[b], part_sums[static_cast<size_t>(b) * TM + o]);
+  s_part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && o < TM) {
+    DF tot = s_part[0][lane];
+#pragma unroll
+    for (int r = 1; r < kMergeRanges; ++r) df_add(tot, s_part[r][lane]);
+    out[3 + o] = static_cast<double>(tot.hi) + static_cast<double>(tot.lo);
+  }
+}
+
+// k_shard_update merges the R rank partials [R][TM + 3] in rank order (FP64):
+//   rho = min_r rho_r (lowest k* on ties), s_r = exp(-(rho_r - rho)/lambda),
+//   eta = sum_r s_r eta_r, du[o] = sum_r s_r N_r[o] / eta;  U += du, u0 out.
+// Every rank runs it on the same gathered partials and gets the same U.
+__global__ void __launch_bounds__(256) k_shard_update(const double *__restrict__ all, int R, int TM, int m,
+                                                      double inv_lambda, float *__restrict__ U,
+                                                      float *__restrict__ u0_out, float *__restrict__ dU_dbg,
+                                                      StepDebug *__restrict__ dbg) {
+  const int W = TM + 3;
+  double rho = INFINITY;
+  int ks = INT_MAX;
+  for (int r = 0; r < R; ++r) {
+    const double rr = all[static_cast<size_t>(r) * W];
+    const int kk = static_cast<int>(all[static_cast<size_t>(r) * W + 1]);
+    if (rr < rho || (rr == rho && kk < ks)) {
+      rho = rr;
+      ks = kk;
+    }
+  }
+  double eta = 0.0;
+  for (int r = 0; r < R; ++r) {
+    const double rr = all[static_cast<size_t>(r) * W];
+    const double sr = (isfinite(rho) && isfinite(rr)) ? exp(-(rr - rho) * inv_lambda) : 0.0;
+    eta = fma(sr, all[static_cast<size_t>(r) * W + 2], eta);
+  }
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < TM) {
+    double n = 0.0;
+    for (int r = 0; r < R; ++r) {
+      const double rr = all[static_cast<size_t>(r) * W];
+      const double sr = (isfinite(rho) && isfinite(rr)) ? exp(-(rr - rho) * inv_lambda) : 0.0;
+      n = fma(sr, all[static_cast<size_t>(r) * W + 3 + o], n);
+    }
+    const double du = eta > 0.0 ? n / eta : 0.0;
+    const float un = U[o] + static_cast<float>(du);
+    U[o] = un;
+    dU_dbg[o] = static_cast<float>(du);
+    if (o < m) u0_out[o] = un;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    dbg->rho = static_cast<float>(rho);
+    dbg->kstar = ks == INT_MAX ? 0 : ks;
+    dbg->eta = eta;
   }
 }
 
@@ -552,16 +671,26 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_weights(const float *__re
 __global__ void __launch_bounds__(kPlainBlock) k_plain_wsum(const float *__restrict__ du, const double *__restrict__ w,
                                                             int K, int TM, double *__restrict__ part) {
   __shared__ double s_a[kPlainRows][kPlainBlock / 32];
+  constexpr int J = kPlainSplitK / kPlainBlock;  // samples per thread
   const int k0 = blockIdx.x * kPlainSplitK, r0 = blockIdx.y * kPlainRows;
   const int k1 = min(K, k0 + kPlainSplitK);
-  double acc[kPlainRows];
+  // every load of the thread issued before the first product (latency paid once)
+  double wk[J];
+  float dv[kPlainRows][J];
 #pragma unroll
-  for (int r = 0; r < kPlainRows; ++r) acc[r] = 0.0;
-  for (int k = k0 + threadIdx.x; k < k1; k += kPlainBlock) {
-    const double wk = w[k];
+  for (int j = 0; j < J; ++j) {
+    const int k = k0 + threadIdx.x + j * kPlainBlock;
+    wk[j] = k < k1 ? w[k] : 0.0;
 #pragma unroll
     for (int r = 0; r < kPlainRows; ++r)
-      if (r0 + r < TM) acc[r] = fma(wk, static_cast<double>(du[static_cast<size_t>(r0 + r) * K + k]), acc[r]);
+      dv[r][j] = (k < k1 && r0 + r < TM) ? du[static_cast<size_t>(r0 + r) * K + k] : 0.0f;
+  }
+  double acc[kPlainRows];
+#pragma unroll
+  for (int r = 0; r < kPlainRows; ++r) {
+    acc[r] = 0.0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[r] = fma(wk[j], static_cast<double>(dv[r][j]), acc[r]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -663,7 +792,7 @@ static cudaError_t launch_fused_t(const CtrlParams &p, const float *x0, const Ct
                                   float *ps, BlockPartial *part, cudaStream_t s) {
   const bool gen = p.gen != nullptr;
   const size_t smem = rollout_smem_bytes(p.T, Sys::M, p.n_obs, BLK, REGEN, false, gen, quad_grid_bytes(p));
-  const int grid = (p.K + BLK - 1) / BLK;
+  const int grid = (shard_samples(p) + BLK - 1) / BLK;
   if (gen) {
     if (REGEN) return cudaErrorInvalidValue;
     k_rollout_fused<Sys, BLK, false, true><<<grid, BLK, smem, s>>>(p, x0, st, U, S, ps, part);
@@ -685,7 +814,7 @@ static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const float *x
 static cudaError_t launch_car_ws(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                  float *ps, BlockPartial *part, cudaStream_t s) {
   const size_t smem = car_ws_smem_bytes(p.T, kWsSamples, false, p.gen != nullptr);
-  const int grid = (p.K + kWsSamples - 1) / kWsSamples;
+  const int grid = (shard_samples(p) + kWsSamples - 1) / kWsSamples;
   if (p.gen)
     k_rollout_car_ws<kWsSamples, true><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, ps, part);
   else
@@ -704,7 +833,7 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
     case 2:
       if (blk == kFusedBlockQuadWs) {
         const size_t smem = fused_smem_bytes(p, kFusedBlockQuadWs);
-        const int grid = (p.K + kQwsSamples - 1) / kQwsSamples;
+        const int grid = (shard_samples(p) + kQwsSamples - 1) / kQwsSamples;
         if (p.gen)
           k_rollout_quad_ws<kQwsSamples, true><<<grid, 3 * kQwsSamples, smem, s>>>(p, x0, st, U, S, part_sums, part);
         else
@@ -713,7 +842,7 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
       }
       if (blk == kFusedBlockQuadLanes) {
         const size_t smem = quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
-        const int grid = (p.K + kQuadLanesBlock / kQuadLanes - 1) / (kQuadLanesBlock / kQuadLanes);
+        const int grid = (shard_samples(p) + kQuadLanesBlock / kQuadLanes - 1) / (kQuadLanesBlock / kQuadLanes);
         k_rollout_quad_lanes<kQuadLanesBlock, kQuadLanes><<<grid, kQuadLanesBlock, smem, s>>>(p, x0, st, U, S,
                                                                                               part_sums, part);
         return cudaGetLastError();
@@ -896,6 +1025,23 @@ cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part
   CtrlState *no_st = nullptr;
   return cudaLaunchKernelEx(&cfg, k_merge_update<false>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,
                             no_uinit, no_st, u0_ready);
+}
+
+cudaError_t launch_shard_partial(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
+                                 double *out, cudaStream_t s) {
+  const int TM = p.T * p.m;
+  k_shard_partial<<<(TM + kMergeOutputs - 1) / kMergeOutputs, kMergeThreads,
+                    (sizeof(double) + sizeof(float)) * static_cast<size_t>(nblk), s>>>(nblk, TM, p.inv_lambda,
+                                                                                       part_sums, part, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shard_update(const CtrlParams &p, const double *all, int n_ranks, float *U, float *u0_out,
+                                float *dU_dbg, StepDebug *dbg, cudaStream_t s) {
+  const int TM = p.T * p.m;
+  k_shard_update<<<(TM + 255) / 256, 256, 0, s>>>(all, n_ranks, TM, p.m, 1.0 / static_cast<double>(p.lambda), U,
+                                                  u0_out, dU_dbg, dbg);
+  return cudaGetLastError();
 }
 
 bool merge_shift_fusable(const CtrlParams &p) {

@@ -88,6 +88,12 @@ cudaError_t launch_rollout_mlp(const CtrlParams &p, const float *x0, const CtrlS
 cudaError_t launch_plain_noise(const CtrlParams &p, const uint32_t *counter, float *du, cudaStream_t s);
 cudaError_t launch_plain_rollout(int sys, const CtrlParams &p, const CtrlState *st, const float *U,
                                  const float *du, float *S, cudaStream_t s);
+// K-sharding (kernels.cu): the rank's partial [TM + 3] doubles, and the merge of R of them.
+constexpr int kShardAlign = 128;  // shard boundaries: multiples of every rollout block's sample count
+cudaError_t launch_shard_partial(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
+                                 double *out, cudaStream_t s);
+cudaError_t launch_shard_update(const CtrlParams &p, const double *all, int n_ranks, float *U, float *u0_out,
+                                float *dU_dbg, StepDebug *dbg, cudaStream_t s);
 // Scratch (doubles) of the plain loop's reduction for this configuration.
 size_t plain_scratch_doubles(const CtrlParams &p);
 cudaError_t launch_plain_reduce_update(const CtrlParams &p, const float *S, const float *du, float *U,

@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "nvtx_range.h"
 #include "../../include/mppi.h"
 #include "mlp_model.cuh"
 #include "systems.cuh"
@@ -503,6 +504,7 @@ int mppi_mlp_set_data(mppi_mlp *q, const float *d_states, const float *d_control
 }
 
 int mppi_mlp_train(mppi_mlp *q, int steps, int batch, float lr, uint64_t seed, float *h_loss_trace) {
+  const NvtxRange range("mppi_mlp_train (forward, backward GEMMs, Adam)");
   if (!q || steps < 0 || batch < 128 || (batch % 128) || !(lr > 0.0f)) return MPPI_EINVAL;
   if (q->n_data < 1) return q->fail(MPPI_ESTATE, "no training data (mppi_mlp_set_data)");
   MLP_TRY(ensure_batch(q, batch));
@@ -547,6 +549,7 @@ int mppi_mlp_grad(mppi_mlp *q, const void *d_X, const float *d_T, int B, float *
 }
 
 int mppi_mlp_predict(mppi_mlp *q, const float *d_states, const float *d_controls, int n, float *d_next) {
+  const NvtxRange range("mppi_mlp_predict (tensor-core forward)");
   if (!q || !d_states || !d_controls || !d_next || n < 1) return MPPI_EINVAL;
   MLP_TRY(ensure_batch(q, ((n + 127) / 128) * 128));
   mlp::k_features<<<(n + 255) / 256, 256, 0, q->stream>>>(d_states, d_controls, n, q->Xb);

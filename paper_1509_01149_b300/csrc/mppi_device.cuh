@@ -129,7 +129,15 @@ struct CtrlParams {
   const void *mlp;          // learned dynamics weights (car_mlp)
   const float *gen;         // general sampling covariance: [T][2][m][m] = (chol(Sigma_E,i),
                             // R - lambda Sigma_E,i^-1) per step, row-major; null: nu Sigma
+  // K-sharding: this context rolls out the samples [k_begin, k_begin + k_count) of the K
+  // (global sample indices, so the noise is the unsharded controller's); k_count 0: to K
+  int k_begin, k_count;
 };
+
+// Samples this context rolls out.
+__host__ __device__ inline int shard_samples(const CtrlParams &p) {
+  return p.k_count > 0 ? p.k_count : p.K - p.k_begin;
+}
 
 // Per-controller mutable device state.
 struct CtrlState {

@@ -19,6 +19,7 @@
 
 #include "../../include/mppi.h"
 #include "host_params.h"
+#include "nvtx_range.h"
 #include "kernels.cuh"
 
 using namespace mppi;
@@ -103,6 +104,7 @@ extern "C" int mppi_step_static(mppi_system sys, int K, int T, float dt, float n
                                 float *d_U, float *d_u0_out, void *cuda_stream, char *h_err, size_t err_len) {
   const ErrorSink fail{h_err, err_len};
   if (h_err && err_len > 0) h_err[0] = '\0';
+  const NvtxRange range("mppi_step_static (state copy, rollout, merge + update)");
   int n = 0, m = 0;
   if (dims(sys, &n, &m) != MPPI_OK)
     return fail(MPPI_EINVAL, "unknown or unsupported system (the learned-dynamics car is not served here)");

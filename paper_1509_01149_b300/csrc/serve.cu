@@ -46,6 +46,7 @@
 #include "alloc_fault.h"
 #include "forest_grid.h"
 #include "host_params.h"
+#include "nvtx_range.h"
 #include "merge_common.cuh"
 #include "kernels.cuh"
 #include "rollout_body.cuh"
@@ -303,6 +304,7 @@ struct Request {
   int code = MPPI_OK;  // kFailed: the status the tick failed with
   float state[16];
   float u0[4];
+  std::chrono::steady_clock::time_point t_submit;
 };
 
 // A tick's buffers and CUDA graph.  Two of them alternate on the server's stream: while one
@@ -367,6 +369,10 @@ struct mppi_server {
   std::thread worker;
   bool running = false, stop_req = false;
   int max_batch = 0;
+  // while a tick runs, the next one is formed once min_batch requests wait or the oldest has
+  // waited max_wait_ms (a tick is launched at once whenever the GPU has none)
+  int min_batch = 256;
+  double max_wait_ms = 1.0;
   uint64_t next_id = 0;
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> queue;       // submitted, not yet launched (lazy: cancelled ids are skipped)
@@ -606,6 +612,7 @@ int refresh_shapes(mppi_server *s, int n, const int *slot_ids) {
 
 // Synchronous tick on context 0 (the scheduler is not running).
 int run_tick(mppi_server *s, int n, const int *slot_ids, const float *states, float *u0_out) {
+  const NvtxRange range("server tick (serve rollout, serve merge)");
   SRV_TRY(refresh_shapes(s, n, slot_ids));
   TickCtx &t = s->tc[0];
   const auto t0 = std::chrono::steady_clock::now();
@@ -650,6 +657,7 @@ void CUDART_CB on_tick_done(void *p) {
 
 // Publish the results of finished ticks, oldest first (caller holds mu).
 void retire(mppi_server *s) {
+  const NvtxRange range("server: retire finished ticks");
   for (;;) {
     TickCtx *oldest = nullptr;
     for (auto &t : s->tc)
@@ -687,16 +695,34 @@ void retire(mppi_server *s) {
   }
 }
 
+// Drop cancelled requests from the front of the queue; the oldest live request's age in ms
+// (caller holds mu), or -1 when nothing is queued.
+double oldest_wait_ms(mppi_server *s) {
+  while (!s->queue.empty()) {
+    auto r = s->reqs.find(s->queue.front());
+    if (r != s->reqs.end() && r->second.status == kQueued)
+      return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->second.t_submit).count();
+    s->queue.pop_front();
+  }
+  return -1.0;
+}
+
 // Launch the queued requests (at most one per slot, up to max_batch) on an idle context
-// (caller holds mu).  Returns true when a tick was launched.
+// (caller holds mu).  With a tick already on the GPU the next one is only formed once
+// min_batch requests wait or the oldest has waited max_wait_ms, so that it batches what
+// arrives meanwhile.  Returns true when a tick was launched.
 bool launch_queued(mppi_server *s) {
+  const NvtxRange range("server: batch queued requests and launch a tick");
   TickCtx *idle = nullptr;
-  for (auto &t : s->tc)
-    if (!t.busy) {
-      idle = &t;
-      break;
-    }
-  if (!idle || s->queue.empty()) return false;
+  bool busy = false;
+  for (auto &t : s->tc) {
+    if (!t.busy && !idle) idle = &t;
+    busy = busy || t.busy;
+  }
+  if (!idle) return false;
+  const double age = oldest_wait_ms(s);
+  if (age < 0.0) return false;
+  if (busy && static_cast<int>(s->queue.size()) < s->min_batch && age < s->max_wait_ms) return false;
   std::vector<uint64_t> ids;
   std::vector<int> slot_ids;
   std::vector<float> states;
@@ -753,10 +779,13 @@ void scheduler(mppi_server *s) {
     for (auto &t : s->tc) busy = busy || t.busy;
     if (s->stop_req && !busy && s->queue.empty()) break;
     if (busy) {
-      // woken by the completion callback, a submission or the stop; the timeout only bounds a
-      // wake-up lost between the check above and the wait
+      // woken by the completion callback, a submission or the stop; the timeout bounds a
+      // wake-up lost between the check above and the wait, and the batching delay
       const uint64_t seen = s->wakeups.load(std::memory_order_acquire);
-      s->cv_work.wait_for(lk, std::chrono::microseconds(500),
+      double wait_us = 500.0;
+      const double age = oldest_wait_ms(s);
+      if (age >= 0.0) wait_us = std::max(20.0, std::min(wait_us, 1e3 * (s->max_wait_ms - age)));
+      s->cv_work.wait_for(lk, std::chrono::microseconds(static_cast<int64_t>(wait_us)),
                           [&] { return s->wakeups.load(std::memory_order_acquire) != seen; });
     } else {
       s->cv_work.wait(lk, [&] { return s->stop_req || !s->queue.empty(); });
@@ -1194,6 +1223,18 @@ int mppi_server_start(mppi_server *s, int max_batch) {
   return MPPI_OK;
 }
 
+int mppi_server_set_batching(mppi_server *s, int min_batch, double max_wait_ms) {
+  if (!s || min_batch < 1 || !(max_wait_ms >= 0.0) || max_wait_ms > 1e4) return MPPI_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->min_batch = min_batch;
+    s->max_wait_ms = max_wait_ms;
+    s->wakeups.fetch_add(1, std::memory_order_release);
+  }
+  s->cv_work.notify_all();
+  return MPPI_OK;
+}
+
 int mppi_server_stop(mppi_server *s) {
   if (!s) return MPPI_EINVAL;
   stop_scheduler(s);
@@ -1215,6 +1256,7 @@ int mppi_server_submit(mppi_server *s, int slot, const float *h_state, uint64_t 
     r.status = kQueued;
     std::memcpy(r.state, h_state, sizeof r.state);
     std::memset(r.u0, 0, sizeof r.u0);
+    r.t_submit = std::chrono::steady_clock::now();
     if (s->slots[slot].desc.blk != s->blk) {
       // admitted before an autotune changed the block shape: refresh it (between ticks)
       SRV_TRY(refresh_shapes(s, 1, &slot));
@@ -1249,6 +1291,7 @@ int mppi_server_submit_batch(mppi_server *s, int n, const int *slot_ids, const f
       r.status = kQueued;
       std::memcpy(r.state, h_states + 16 * static_cast<size_t>(q), sizeof r.state);
       std::memset(r.u0, 0, sizeof r.u0);
+      r.t_submit = std::chrono::steady_clock::now();
       s->reqs.emplace(id, r);
       s->queue.push_back(id);
       ids_out[q] = id;

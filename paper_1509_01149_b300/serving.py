@@ -285,7 +285,9 @@ class AsyncServingLoop:
     def run(self, duration_s: float, target_active: int, mean_lifetime_periods: float = 200.0,
             warmup_s: float = 0.5) -> dict:
         """Hold about `target_active` controllers for warmup_s + duration_s of wall time
-        (arrival rate from Little's law); statistics cover the last duration_s."""
+        (arrival rate from Little's law); statistics cover the last duration_s.  Due times sit
+        in a heap, so each loop pass costs O(log n) per due controller, not O(n)."""
+        import heapq
         srv = self.server
         self._by_id = {}
         rate = target_active / (mean_lifetime_periods * self.period)      # arrivals per second
@@ -293,9 +295,13 @@ class AsyncServingLoop:
         for _ in range(target_active):
             self.waiting.append(self._arrival(mean_lifetime_periods))
         self._admit_waiting(t0)
+        heap = [(c["due"], slot) for slot, c in self.ctrl.items()]
+        heapq.heapify(heap)
+        known = set(self.ctrl)
         srv.start()
         t_rec, t_end, t_last = t0 + warmup_s, t0 + warmup_s + duration_s, t0
         recording = False
+        busy_s, t_busy0 = 0.0, None
         try:
             while True:
                 now = time.perf_counter()
@@ -304,30 +310,38 @@ class AsyncServingLoop:
                 if not recording and now >= t_rec:
                     recording = True
                     self.stats = AsyncStats(admitted=self.stats.admitted)
+                    busy_s = 0.0
+                t_busy0 = now
                 # arrivals (Poisson in time) and admission, with ticks in flight
                 for _ in range(self.rng.poisson(rate * (now - t_last))):
                     self.waiting.append(self._arrival(mean_lifetime_periods))
                 t_last = now
                 if self.waiting:
                     self._admit_waiting(now)
+                    for slot in set(self.ctrl) - known:
+                        heapq.heappush(heap, (self.ctrl[slot]["due"], slot))
+                    known = set(self.ctrl)
                 # due controllers submit; one whose last result is still out skips the period
                 due_slots, due_states = [], []
-                for slot, c in list(self.ctrl.items()):
-                    if c["due"] > now:
-                        continue
+                while heap and heap[0][0] <= now:
+                    _, slot = heapq.heappop(heap)
+                    c = self.ctrl[slot]
                     c["due"] += self.period
                     if c["outstanding"] is not None:
                         self.stats.missed_periods += 1
+                        heapq.heappush(heap, (c["due"], slot))
                         continue
                     if c["left"] <= 0:
                         srv.release(slot)
                         del self.ctrl[slot]
+                        known.discard(slot)
                         self.stats.released += 1
                         continue
                     c["left"] -= 1
                     self.stats.periods += 1
                     due_slots.append(slot)
                     due_states.append(c["x"].astype(np.float32))
+                    heapq.heappush(heap, (c["due"], slot))
                 if due_slots:
                     ids = srv.submit_batch(due_slots, due_states)
                     ts = time.perf_counter()
@@ -336,18 +350,23 @@ class AsyncServingLoop:
                         self.ctrl[slot]["t_submit"] = ts
                         self._by_id[int(rid)] = slot
                 self.stats.active.append(len(self.ctrl))
+                busy_s += time.perf_counter() - t_busy0
                 # results: wait until the next due time at most
-                next_due = min((c["due"] for c in self.ctrl.values()), default=now + 1e-3)
+                next_due = heap[0][0] if heap else now + 1e-3
                 wait_ms = max(0.0, min(1.0, 1e3 * (next_due - time.perf_counter())))
                 ids, u0, st = srv.reap(4096, timeout_ms=wait_ms)
                 if len(ids):
-                    self._apply_results(ids, u0, st, time.perf_counter())
+                    t_busy0 = time.perf_counter()
+                    self._apply_results(ids, u0, st, t_busy0)
+                    busy_s += time.perf_counter() - t_busy0
         finally:
             srv.stop()
             ids, u0, st = srv.reap(4096, timeout_ms=0.0)
             if len(ids):
                 self._apply_results(ids, u0, st, time.perf_counter())
-        return self.stats.summary(duration_s)
+        out = self.stats.summary(duration_s)
+        out["client_busy_fraction"] = busy_s / duration_s
+        return out
 
     def drain(self):
         for slot in list(self.ctrl):

@@ -75,7 +75,8 @@ def test_request_submitted_during_a_tick_joins_a_later_tick(N):
     srv = make_server(N)
     slots = [admit(srv, s, K, T, i)[0] for i, (s, K, T) in enumerate(picks)]
     srv.start()
-    heavy_ids = [srv.submit(sl, _x0(p[0])) for sl, p in zip(slots[:-1], picks[:-1])]
+    # one submission for all of them, so that they are queued together and form one tick
+    heavy_ids = [int(i) for i in srv.submit_batch(slots[:-1], [_x0(p[0]) for p in picks[:-1]])]
     _until(lambda: srv.stats()["queued"] == 0)                 # the heavy tick is on the GPU
     assert srv.poll(heavy_ids[0]) is None                       # ... and has not finished
     light_id = srv.submit(slots[-1], _x0(light[0]))
@@ -182,6 +183,9 @@ def test_synchronous_calls_are_refused_while_the_scheduler_runs(N):
     srv = make_server(N)
     sl = admit(srv, W.CARTPOLE, 256, 20, 0)[0]
     srv.start()
+    srv.set_batching(64, 0.5)                                   # adjustable while running
+    with pytest.raises(N.MppiError):
+        srv.set_batching(0, 0.5)
     with pytest.raises(N.MppiError) as ei:
         srv.tick([sl], [_x0(W.CARTPOLE)])
     assert ei.value.rc == N.MPPI_ESTATE
