@@ -408,9 +408,12 @@ typedef struct {
 /* Start the scheduler thread.  ESTATE if it already runs. */
 int mppi_server_start(mppi_server *srv, int max_batch);
 /* Batching of the scheduler: whenever the GPU has no tick, the queued requests are launched
- * at once; while a tick runs, the next tick is formed once min_batch (>= 1) requests wait or
- * the oldest has waited max_wait_ms (>= 0), so that it gathers what arrives meanwhile.
- * Defaults 256 and 1.0 ms.  May be called at any time. */
+ * at once; while a tick runs, the next tick is formed when the running tick is predicted to
+ * end within 0.25 ms (its work, sum of K*T per controller weighted by system, times the
+ * GPU time per unit of work of the recent ticks), or once min_batch (>= 1) requests wait, or
+ * once the oldest has waited max_wait_ms (>= 0) -- so that it gathers what arrives while the
+ * GPU is busy and is enqueued just before the GPU would go idle.  Defaults 1024 and 4.0 ms.
+ * May be called at any time. */
 int mppi_server_set_batching(mppi_server *srv, int min_batch, double max_wait_ms);
 /* Finish every submitted request, then stop the thread.  Safe when it is not running. */
 int mppi_server_stop(mppi_server *srv);
@@ -430,9 +433,10 @@ int mppi_server_poll(mppi_server *srv, uint64_t id, float *h_u0);
 int mppi_server_wait(mppi_server *srv, uint64_t id, double timeout_ms, float *h_u0);
 /* Take up to max_n finished requests in completion order, waiting up to timeout_ms for the
  * first: ids [max_n], h_u0 [max_n][4], status [max_n] (may be NULL: MPPI_OK or the tick's
- * error per request); *n_out receives how many (0 after the timeout). */
-int mppi_server_reap(mppi_server *srv, int max_n, uint64_t *ids, float *h_u0, int *status, double timeout_ms,
-                     int *n_out);
+ * error per request), latency_ms [max_n] (may be NULL: from the submission to the moment the
+ * scheduler saw its tick finish); *n_out receives how many (0 after the timeout). */
+int mppi_server_reap(mppi_server *srv, int max_n, uint64_t *ids, float *h_u0, int *status, double *latency_ms,
+                     double timeout_ms, int *n_out);
 /* Forget a request.  Queued: it never runs (the controller's controls and iteration counter
  * are untouched).  In flight: its tick completes (the controller's controls and counter
  * advance, every other request of the tick is unaffected) and the result is dropped.

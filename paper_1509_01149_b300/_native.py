@@ -100,8 +100,8 @@ SIGNATURES = [
     ("mppi_server_submit_batch", C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP, C.POINTER(C.c_uint64)]),
     ("mppi_server_poll", C.c_int, [_P, C.c_uint64, _FP]),
     ("mppi_server_wait", C.c_int, [_P, C.c_uint64, C.c_double, _FP]),
-    ("mppi_server_reap", C.c_int, [_P, C.c_int, C.POINTER(C.c_uint64), _FP, C.POINTER(C.c_int), C.c_double,
-                                   C.POINTER(C.c_int)]),
+    ("mppi_server_reap", C.c_int, [_P, C.c_int, C.POINTER(C.c_uint64), _FP, C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_int)]),
     ("mppi_server_cancel", C.c_int, [_P, C.c_uint64]),
     ("mppi_server_get_stats", C.c_int, [_P, C.POINTER(ServerStats)]),
     ("mppi_debug_forest_nearest", C.c_int, [_FP, C.c_int, C.c_int, _FP, _FP, _FP, _FP, C.POINTER(C.c_int)]),
@@ -550,15 +550,20 @@ class Server:
         self._chk(lib.mppi_server_wait(self._h, rid, timeout_ms, _fp(u0)))
         return u0
 
-    def reap(self, max_n: int = 4096, timeout_ms: float = 0.0):
-        """Finished requests in completion order: (ids [n], u0 [n][4], status [n])."""
+    def reap(self, max_n: int = 4096, timeout_ms: float = 0.0, with_latency: bool = False):
+        """Finished requests in completion order: (ids [n], u0 [n][4], status [n]) and, with
+        with_latency, the server-side latency [n] in ms (submission to tick retirement)."""
         ids = np.zeros(max_n, dtype=np.uint64)
         u0 = np.zeros((max_n, 4), dtype=np.float32)
         st = np.zeros(max_n, dtype=np.int32)
+        lat = np.zeros(max_n, dtype=np.float64)
         n = C.c_int()
         self._chk(lib.mppi_server_reap(self._h, max_n, ids.ctypes.data_as(C.POINTER(C.c_uint64)), _fp(u0),
-                                       st.ctypes.data_as(C.POINTER(C.c_int)), timeout_ms, C.byref(n)))
+                                       st.ctypes.data_as(C.POINTER(C.c_int)),
+                                       lat.ctypes.data_as(C.POINTER(C.c_double)), timeout_ms, C.byref(n)))
         k = n.value
+        if with_latency:
+            return ids[:k], u0[:k], st[:k], lat[:k]
         return ids[:k], u0[:k], st[:k]
 
     def cancel(self, rid: int):

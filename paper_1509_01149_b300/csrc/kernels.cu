@@ -633,19 +633,21 @@ __global__ void __launch_bounds__(1024) k_plain_min(const float *__restrict__ S,
   }
 }
 
-// The plain loop's reduction (Eq. App_PI with the min shift), unfused but coalesced and in
-// FP64 throughout: k_plain_weights forms every w_k = exp(-(S~_k - rho)/lambda) once (FP64
-// exponential) with per-block partial sums of eta; k_plain_wsum reads each row of du [T*m][K]
-// once, kPlainRows rows by kPlainSplitK samples per block, FP64 products and sums into
-// per-split partials; k_plain_finalize adds the partials in a fixed order, divides by eta and
-// updates U.  Scratch (doubles): w [K] | eta partials [ceil(K/256)] | wsum partials [splits][T*m].
+// The plain loop's reduction (Eq. App_PI with the min shift), unfused and coalesced:
+// k_plain_weights forms every w_k = exp(-(S~_k - rho)/lambda) once (FP64 exponential, stored
+// rounded to FP32) with per-block FP64 partial sums of eta; k_plain_wsum reads each row of du
+// [T*m][K] once, kPlainRows rows by kPlainSplitK samples per block: each thread sums its
+// kPlainSplitK / kPlainBlock products per row in FP32, the block adds the thread sums in FP64
+// into per-split partials; k_plain_finalize adds the partials in a fixed order (FP64), divides
+// by eta and updates U.  Scratch: w [K] floats (in a K-double slot) | eta partials
+// [ceil(K/256)] | wsum partials [splits][T*m] (doubles).
 constexpr int kPlainBlock = 256;
 constexpr int kPlainRows = 4;
 constexpr int kPlainSplitK = 2048;
 
 __global__ void __launch_bounds__(kPlainBlock) k_plain_weights(const float *__restrict__ S, int K, float lambda,
                                                                const StepDebug *__restrict__ dbg,
-                                                               double *__restrict__ w, double *__restrict__ eta_part) {
+                                                               float *__restrict__ w, double *__restrict__ eta_part) {
   __shared__ double s_e[kPlainBlock / 32];
   const int k = blockIdx.x * kPlainBlock + threadIdx.x;
   const float rho = dbg->rho;
@@ -654,7 +656,7 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_weights(const float *__re
     const float Sk = S[k];
     if (isfinite(rho) && isfinite(Sk))
       e = exp(-(static_cast<double>(Sk) - static_cast<double>(rho)) / static_cast<double>(lambda));
-    w[k] = e;
+    w[k] = static_cast<float>(e);
   }
   e = warp_sum_d(e);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -668,34 +670,30 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_weights(const float *__re
   }
 }
 
-__global__ void __launch_bounds__(kPlainBlock) k_plain_wsum(const float *__restrict__ du, const double *__restrict__ w,
+__global__ void __launch_bounds__(kPlainBlock) k_plain_wsum(const float *__restrict__ du, const float *__restrict__ w,
                                                             int K, int TM, double *__restrict__ part) {
   __shared__ double s_a[kPlainRows][kPlainBlock / 32];
   constexpr int J = kPlainSplitK / kPlainBlock;  // samples per thread
   const int k0 = blockIdx.x * kPlainSplitK, r0 = blockIdx.y * kPlainRows;
   const int k1 = min(K, k0 + kPlainSplitK);
   // every load of the thread issued before the first product (latency paid once)
-  double wk[J];
+  float wk[J];
   float dv[kPlainRows][J];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int k = k0 + threadIdx.x + j * kPlainBlock;
-    wk[j] = k < k1 ? w[k] : 0.0;
+    wk[j] = k < k1 ? w[k] : 0.0f;
 #pragma unroll
     for (int r = 0; r < kPlainRows; ++r)
       dv[r][j] = (k < k1 && r0 + r < TM) ? du[static_cast<size_t>(r0 + r) * K + k] : 0.0f;
   }
-  double acc[kPlainRows];
-#pragma unroll
-  for (int r = 0; r < kPlainRows; ++r) {
-    acc[r] = 0.0;
-#pragma unroll
-    for (int j = 0; j < J; ++j) acc[r] = fma(wk[j], static_cast<double>(dv[r][j]), acc[r]);
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int r = 0; r < kPlainRows; ++r) {
-    const double v = warp_sum_d(acc[r]);
+    float acc = 0.0f;
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc = fmaf(wk[j], dv[r][j], acc);
+    const double v = warp_sum_d(static_cast<double>(acc));
     if (lane == 0) s_a[r][warp] = v;
   }
   __syncthreads();
@@ -1115,7 +1113,8 @@ cudaError_t launch_plain_reduce_update(const CtrlParams &p, const float *S, cons
                                        float *dU_dbg, StepDebug *dbg, double *scratch, cudaStream_t s) {
   const int TM = p.T * p.m;
   const int n_eta = (p.K + kPlainBlock - 1) / kPlainBlock, n_split = (p.K + kPlainSplitK - 1) / kPlainSplitK;
-  double *w = scratch, *eta_part = scratch + p.K, *part = eta_part + n_eta;
+  float *w = reinterpret_cast<float *>(scratch);
+  double *eta_part = scratch + p.K, *part = eta_part + n_eta;
   k_plain_min<<<1, 1024, 0, s>>>(S, p.K, dbg);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -57,7 +57,7 @@ __global__ void k_datagen(const float *__restrict__ xs, const float *__restrict_
 }
 
 // per-state sums of increments and their squares (FP64)
-__global__ void k_moments(const float *__restrict__ D, int n, double *__restrict__ acc /*[14]*/) {
+__global__ void k_moments(const float *__restrict__ D, int n, double *__restrict__ acc /*[gridDim.x][14]*/) {
   __shared__ double s[2 * kState][8];
   double a[2 * kState] = {0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -77,7 +77,7 @@ __global__ void k_moments(const float *__restrict__ D, int n, double *__restrict
   if (threadIdx.x < 2 * kState) {
     double v = 0.0;
     for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) v += s[threadIdx.x][w];
-    atomicAdd(&acc[threadIdx.x], v);
+    acc[static_cast<size_t>(blockIdx.x) * 2 * kState + threadIdx.x] = v;  // this block's partial
   }
 }
 
@@ -129,7 +129,18 @@ __global__ void k_colsum(const T *__restrict__ A, int rows, int cols, float *__r
   if (ty == 0 && c < cols) {
     float t = 0.0f;
     for (int q = 0; q < 8; ++q) t += s[q][threadIdx.x];
-    atomicAdd(&out[c], t);
+    out[static_cast<size_t>(blockIdx.y) * cols + c] = t;  // this block's partial (rows r = y, y + 8 gridDim.y, ...)
+  }
+}
+
+// out[i] = sum over z = 0 .. nsplit-1 (in that order) of part[z][i]: the fixed-order reduction of
+// split-K partial products and of column-sum partials, so that training is bit-reproducible
+__global__ void k_sum_splits(const float *__restrict__ part, int nsplit, size_t count, float *__restrict__ out) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    float a = 0.0f;
+    for (int z = 0; z < nsplit; ++z) a += part[static_cast<size_t>(z) * count + i];
+    out[i] = a;
   }
 }
 
@@ -219,6 +230,11 @@ __global__ void k_features(const float *__restrict__ xs, const float *__restrict
 using namespace mppi;
 using namespace mppi::mlp;
 
+namespace {
+constexpr int kMaxSplit = 64;       // split-K partials of a weight-gradient GEMM
+constexpr int kMomentBlocks = 512;  // blocks of the data-set moment kernel
+}  // namespace
+
 struct mppi_mlp {
   std::string err;
   cudaStream_t stream = nullptr;
@@ -237,6 +253,8 @@ struct mppi_mlp {
   float *Tb = nullptr, *Y = nullptr, *dYf = nullptr;
   double *loss = nullptr;
   int *d_err = nullptr;
+  float *gsplit = nullptr;    // split-K and column-sum partials [splits][count]
+  double *moments = nullptr;  // per-block moment partials [kMomentBlocks][2 * kState]
 
   int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -340,15 +358,24 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   const int nthr = 256;
   mlp::k_loss_grad<<<(B * kOut + nthr - 1) / nthr, nthr, 0, q->stream>>>(q->Y, T, B, q->dYf, q->dYb, q->loss);
   MLP_TRY(q->cuda(cudaGetLastError(), "loss"));
-  MLP_TRY(q->cuda(cudaMemsetAsync(q->g, 0, sizeof(float) * kNumParams, q->stream), "grad zero"));
-  const int split = std::max(1, std::min(64, B / 256));
+  // Weight gradients are sums over the batch: split-K GEMMs, each split storing its partial
+  // product to its own slice of gsplit, then a fixed-order sum of the slices (no atomics: the
+  // same data and seed give the same bits)
+  const int split = std::max(1, std::min(kMaxSplit, B / 256));
+  auto split_sum = [&](size_t count, float *out, const char *what) {
+    mlp::k_sum_splits<<<static_cast<int>(std::min<size_t>(1024, (count + 255) / 256)), 256, 0, q->stream>>>(
+        q->gsplit, split, count, out);
+    return q->cuda(cudaGetLastError(), what);
+  };
   // gW3 (stored [16][256]): C(m = hidden j, n = output i) = sum_b H2[b][j] dY[b][i]
-  GemmArgs g = gemm(kHid, kOut, B, 16, q->H2, 1, kHid, q->dYb, kOut, 1, kEpiAtomicF32, q->d_err);
-  g.Cf = q->g + kOffW3;
+  GemmArgs g = gemm(kHid, kOut, B, 16, q->H2, 1, kHid, q->dYb, kOut, 1, kEpiStoreF32, q->d_err);
+  g.Cf = q->gsplit;
   g.ldc = 1;
   g.ldcn = kHid;
   g.ksplit = split;
+  g.split_stride = static_cast<int64_t>(kOut) * kHid;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW3"));
+  MLP_TRY(split_sum(static_cast<size_t>(kOut) * kHid, q->g + kOffW3, "gW3 sum"));
   // dZ2 = (dY W3) * (1 - H2^2)
   g = gemm(B, kHid, kOut, 64, q->dYb, kOut, 1, q->w3, kHid, 1, kEpiTanhGrad, q->d_err);
   g.H = q->H2;
@@ -357,11 +384,13 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   g.ldcb = kHid;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm dZ2"));
   // gW2 [256][256] = dZ2^T H1
-  g = gemm(kHid, kHid, B, 128, q->dZ2, 1, kHid, q->H1, kHid, 1, kEpiAtomicF32, q->d_err);
-  g.Cf = q->g + kOffW2;
+  g = gemm(kHid, kHid, B, 128, q->dZ2, 1, kHid, q->H1, kHid, 1, kEpiStoreF32, q->d_err);
+  g.Cf = q->gsplit;
   g.ldc = kHid;
   g.ksplit = split;
+  g.split_stride = static_cast<int64_t>(kHid) * kHid;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW2"));
+  MLP_TRY(split_sum(static_cast<size_t>(kHid) * kHid, q->g + kOffW2, "gW2 sum"));
   // dZ1 = (dZ2 W2) * (1 - H1^2)
   g = gemm(B, kHid, kHid, 64, q->dZ2, kHid, 1, q->w2, kHid, 1, kEpiTanhGrad, q->d_err);
   g.H = q->H1;
@@ -370,16 +399,21 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   g.ldcb = kHid;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm dZ1"));
   // gW1 [256][16] = dZ1^T X
-  g = gemm(kHid, kIn, B, 16, q->dZ1, 1, kHid, X, kIn, 1, kEpiAtomicF32, q->d_err);
-  g.Cf = q->g + kOffW1;
+  g = gemm(kHid, kIn, B, 16, q->dZ1, 1, kHid, X, kIn, 1, kEpiStoreF32, q->d_err);
+  g.Cf = q->gsplit;
   g.ldc = kIn;
   g.ksplit = split;
+  g.split_stride = static_cast<int64_t>(kHid) * kIn;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW1"));
-  // bias gradients
-  const dim3 cg(kHid / 32, 16);
-  mlp::k_colsum<float><<<dim3(1, 16), 256, 0, q->stream>>>(q->dYf, B, kOut, q->g + kOffB3);
-  mlp::k_colsum<__nv_bfloat16><<<cg, 256, 0, q->stream>>>(q->dZ2, B, kHid, q->g + kOffB2);
-  mlp::k_colsum<__nv_bfloat16><<<cg, 256, 0, q->stream>>>(q->dZ1, B, kHid, q->g + kOffB1);
+  MLP_TRY(split_sum(static_cast<size_t>(kHid) * kIn, q->g + kOffW1, "gW1 sum"));
+  // bias gradients: column sums, 16 row partials each, summed in a fixed order
+  constexpr int kRowParts = 16;
+  mlp::k_colsum<float><<<dim3(1, kRowParts), 256, 0, q->stream>>>(q->dYf, B, kOut, q->gsplit);
+  mlp::k_sum_splits<<<1, 256, 0, q->stream>>>(q->gsplit, kRowParts, kOut, q->g + kOffB3);
+  mlp::k_colsum<__nv_bfloat16><<<dim3(kHid / 32, kRowParts), 256, 0, q->stream>>>(q->dZ2, B, kHid, q->gsplit);
+  mlp::k_sum_splits<<<1, 256, 0, q->stream>>>(q->gsplit, kRowParts, kHid, q->g + kOffB2);
+  mlp::k_colsum<__nv_bfloat16><<<dim3(kHid / 32, kRowParts), 256, 0, q->stream>>>(q->dZ1, B, kHid, q->gsplit);
+  mlp::k_sum_splits<<<1, 256, 0, q->stream>>>(q->gsplit, kRowParts, kHid, q->g + kOffB1);
   return q->cuda(cudaGetLastError(), "bias grads");
 }
 
@@ -413,6 +447,10 @@ int mppi_mlp_create(uint64_t seed, mppi_mlp **out) {
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->out_scale, sizeof(float) * kOut), "scale");
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->loss, sizeof(double) * 16), "loss");
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->d_err, sizeof(int)), "err");
+  if (rc == MPPI_OK)
+    rc = q->cuda(cudaMalloc(&q->gsplit, sizeof(float) * static_cast<size_t>(kMaxSplit) * kHid * kHid), "split partials");
+  if (rc == MPPI_OK)
+    rc = q->cuda(cudaMalloc(&q->moments, sizeof(double) * static_cast<size_t>(kMomentBlocks) * 2 * kState), "moments");
   if (rc == MPPI_OK) rc = q->cuda(cudaMemsetAsync(q->d_err, 0, sizeof(int), q->stream), "err zero");
   if (rc == MPPI_OK) rc = q->cuda(cudaMemsetAsync(q->m, 0, pb, q->stream), "m zero");
   if (rc == MPPI_OK) rc = q->cuda(cudaMemsetAsync(q->v, 0, pb, q->stream), "v zero");
@@ -439,7 +477,7 @@ int mppi_mlp_destroy(mppi_mlp *q) {
   if (!q) return MPPI_OK;
   if (q->stream) cudaStreamSynchronize(q->stream);
   void *bufs[] = {q->p, q->g, q->m, q->v, q->w1, q->w2, q->w3, q->out_scale, q->Xf, q->D, q->Xb, q->H1, q->H2,
-                  q->dYb, q->dZ2, q->dZ1, q->Tb, q->Y, q->dYf, q->loss, q->d_err};
+                  q->dYb, q->dZ2, q->dZ1, q->Tb, q->Y, q->dYf, q->loss, q->d_err, q->gsplit, q->moments};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (q->stream) cudaStreamDestroy(q->stream);
@@ -486,12 +524,16 @@ int mppi_mlp_set_data(mppi_mlp *q, const float *d_states, const float *d_control
   MLP_TRY(q->cuda(cudaMalloc(&q->D, sizeof(float) * kState * static_cast<size_t>(n)), "data D"));
   mlp::k_datagen<<<(n + 255) / 256, 256, 0, q->stream>>>(d_states, d_controls, n, dt, q->Xf, q->D);
   MLP_TRY(q->cuda(cudaGetLastError(), "datagen"));
-  MLP_TRY(q->cuda(cudaMemsetAsync(q->loss, 0, sizeof(double) * 16, q->stream), "zero"));
-  mlp::k_moments<<<512, 256, 0, q->stream>>>(q->D, n, q->loss);
+  mlp::k_moments<<<kMomentBlocks, 256, 0, q->stream>>>(q->D, n, q->moments);
   MLP_TRY(q->cuda(cudaGetLastError(), "moments"));
-  double acc[16];
-  MLP_TRY(q->cuda(cudaMemcpyAsync(acc, q->loss, sizeof acc, cudaMemcpyDeviceToHost, q->stream), "moments copy"));
+  std::vector<double> part(static_cast<size_t>(kMomentBlocks) * 2 * kState);
+  MLP_TRY(q->cuda(cudaMemcpyAsync(part.data(), q->moments, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
+                                  q->stream),
+                  "moments copy"));
   MLP_TRY(q->cuda(cudaStreamSynchronize(q->stream), "sync"));
+  double acc[2 * kState] = {0};
+  for (int b = 0; b < kMomentBlocks; ++b)  // block order: the same bits every time
+    for (int j = 0; j < 2 * kState; ++j) acc[j] += part[static_cast<size_t>(b) * 2 * kState + j];
   for (int j = 0; j < kState; ++j) {
     const double mean = acc[j] / n, var = acc[kState + j] / n - mean * mean;
     q->h_out_scale[j] = static_cast<float>(std::sqrt(std::fmax(var, 0.0)) + 1e-9);

@@ -304,7 +304,7 @@ struct Request {
   int code = MPPI_OK;  // kFailed: the status the tick failed with
   float state[16];
   float u0[4];
-  std::chrono::steady_clock::time_point t_submit;
+  std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
 // A tick's buffers and CUDA graph.  Two of them alternate on the server's stream: while one
@@ -321,9 +321,11 @@ struct TickCtx {
   ServeArgs args{};
   int max_nblk_arg = 1;
   int built_gen = -1;  // shape generation the graph was built for
-  cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;  // around the tick on the stream (timing events)
+  std::chrono::steady_clock::time_point launched;
   bool busy = false;
   uint64_t seq = 0;                 // launch order
+  double work = 0.0;                // sum over its controllers of K * T * step weight
   std::vector<uint64_t> req_ids;    // asynchronous requests of the tick in flight, in tick order
   std::vector<int> slot_ids;        // slot of each
 };
@@ -369,10 +371,14 @@ struct mppi_server {
   std::thread worker;
   bool running = false, stop_req = false;
   int max_batch = 0;
-  // while a tick runs, the next one is formed once min_batch requests wait or the oldest has
-  // waited max_wait_ms (a tick is launched at once whenever the GPU has none)
-  int min_batch = 256;
-  double max_wait_ms = 1.0;
+  // while a tick runs, the next one is formed when the running tick is predicted to end within
+  // kLaunchSlackMs (from the recent ticks' GPU time per unit of work), or once min_batch
+  // requests wait, or once the oldest has waited max_wait_ms (a tick is launched at once
+  // whenever the GPU has none)
+  int min_batch = 1024;
+  double max_wait_ms = 4.0;
+  double ms_per_work = 0.0;   // GPU milliseconds per unit of tick work (EMA over retired ticks)
+  std::chrono::steady_clock::time_point last_retire;
   uint64_t next_id = 0;
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> queue;       // submitted, not yet launched (lazy: cancelled ids are skipped)
@@ -442,6 +448,7 @@ void free_tick_ctx(TickCtx &t) {
   if (t.h_u0) cudaFreeHost(t.h_u0);
   if (t.d_counters) cudaFree(t.d_counters);
   if (t.done) cudaEventDestroy(t.done);
+  if (t.start) cudaEventDestroy(t.start);
   t = TickCtx{};
 }
 
@@ -449,7 +456,8 @@ int init_tick_ctx(mppi_server *s, TickCtx &t) {
   SRV_TRY(s->cuda(dev_malloc(&t.d_u0, sizeof(float) * 4 * s->max_slots), "cudaMalloc(u0)"));
   SRV_TRY(s->cuda(host_alloc(&t.h_u0, sizeof(float) * 4 * s->max_slots, cudaHostAllocDefault), "cudaMallocHost(u0)"));
   SRV_TRY(s->cuda(dev_malloc(&t.d_counters, sizeof(int) * 2), "cudaMalloc(counters)"));
-  return s->cuda(cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming), "event");
+  SRV_TRY(s->cuda(cudaEventCreate(&t.start), "event"));
+  return s->cuda(cudaEventCreate(&t.done), "event");
 }
 
 // The context's tick buffer must hold `items` work items; reallocating needs the context idle.
@@ -560,6 +568,11 @@ int launch_tick(mppi_server *s, TickCtx &t, int n, const int *slot_ids, const fl
     const HostSlot &x = s->slots[slot_ids[a]], &y = s->slots[slot_ids[b]];
     return step_weight(x.sys) * x.T > step_weight(y.sys) * y.T;
   });
+  t.work = 0.0;
+  for (int q = 0; q < n; ++q) {
+    const HostSlot &h = s->slots[slot_ids[q]];
+    t.work += step_weight(h.sys) * static_cast<double>(h.K) * h.T;
+  }
   SRV_TRY(ensure_tick_capacity(s, t, n_items));
   if (t.built_gen != s->shape_gen) SRV_TRY(build_graph(s, t));
 
@@ -586,9 +599,11 @@ int launch_tick(mppi_server *s, TickCtx &t, int n, const int *slot_ids, const fl
   SRV_TRY(s->cuda(cudaGraphExecMemcpyNodeSetParams1D(t.exec, t.n_d2h, t.h_u0, t.d_u0, sizeof(float) * 4 * n,
                                                      cudaMemcpyDeviceToHost),
                   "d2h update"));
+  SRV_TRY(s->cuda(cudaEventRecord(t.start, s->stream), "event record"));
   SRV_TRY(s->cuda(cudaGraphLaunch(t.exec, s->stream), "graph launch"));
   SRV_TRY(s->cuda(cudaEventRecord(t.done, s->stream), "event record"));
   t.seq = ++s->launches;
+  t.launched = std::chrono::steady_clock::now();
   return MPPI_OK;
 }
 
@@ -670,12 +685,20 @@ void retire(mppi_server *s) {
       code = s->cuda(q, "tick");
     }
     TickCtx &t = *oldest;
+    float gpu_ms = 0.0f;
+    if (code == MPPI_OK && cudaEventElapsedTime(&gpu_ms, t.start, t.done) == cudaSuccess && t.work > 0.0) {
+      const double r = gpu_ms / t.work;
+      s->ms_per_work = s->ms_per_work > 0.0 ? 0.8 * s->ms_per_work + 0.2 * r : r;
+    }
+    cudaGetLastError();
+    s->last_retire = std::chrono::steady_clock::now();
     for (size_t i = 0; i < t.req_ids.size(); ++i) {
       HostSlot &h = s->slots[t.slot_ids[i]];
       h.inflight -= 1;
       if (h.releasing && h.inflight == 0) free_slot(s, t.slot_ids[i]);
       auto r = s->reqs.find(t.req_ids[i]);
       if (r == s->reqs.end()) continue;  // cancelled while in flight: the result is dropped
+      r->second.t_done = s->last_retire;
       if (code == MPPI_OK) {
         std::memcpy(r->second.u0, t.h_u0 + 4 * i, sizeof(float) * 4);
         r->second.status = kDone;
@@ -693,6 +716,21 @@ void retire(mppi_server *s) {
     s->ticks += 1;
     s->cv_done.notify_all();
   }
+}
+
+constexpr double kLaunchSlackMs = 0.25;  // form the next tick this long before the running one ends
+
+// Predicted milliseconds until the tick on the GPU finishes (caller holds mu): its work times
+// the recent GPU time per unit of work, counted from when it can have started (its launch, or
+// the retirement of the tick before it); 0 without a prediction.
+double running_tick_remaining_ms(mppi_server *s) {
+  const TickCtx *run = nullptr;
+  for (const auto &t : s->tc)
+    if (t.busy && (!run || t.seq < run->seq)) run = &t;
+  if (!run || s->ms_per_work <= 0.0) return 0.0;
+  const auto began = std::max(run->launched, s->last_retire);
+  const double elapsed = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - began).count();
+  return std::max(0.0, run->work * s->ms_per_work - elapsed);
 }
 
 // Drop cancelled requests from the front of the queue; the oldest live request's age in ms
@@ -722,7 +760,9 @@ bool launch_queued(mppi_server *s) {
   if (!idle) return false;
   const double age = oldest_wait_ms(s);
   if (age < 0.0) return false;
-  if (busy && static_cast<int>(s->queue.size()) < s->min_batch && age < s->max_wait_ms) return false;
+  if (busy && static_cast<int>(s->queue.size()) < s->min_batch && age < s->max_wait_ms &&
+      running_tick_remaining_ms(s) > kLaunchSlackMs)
+    return false;
   std::vector<uint64_t> ids;
   std::vector<int> slot_ids;
   std::vector<float> states;
@@ -784,7 +824,12 @@ void scheduler(mppi_server *s) {
       const uint64_t seen = s->wakeups.load(std::memory_order_acquire);
       double wait_us = 500.0;
       const double age = oldest_wait_ms(s);
-      if (age >= 0.0) wait_us = std::max(20.0, std::min(wait_us, 1e3 * (s->max_wait_ms - age)));
+      if (age >= 0.0) {
+        wait_us = std::min(wait_us, 1e3 * (s->max_wait_ms - age));
+        const double rem = running_tick_remaining_ms(s);
+        if (rem > kLaunchSlackMs) wait_us = std::min(wait_us, 1e3 * (rem - kLaunchSlackMs));
+        wait_us = std::max(20.0, wait_us);
+      }
       s->cv_work.wait_for(lk, std::chrono::microseconds(static_cast<int64_t>(wait_us)),
                           [&] { return s->wakeups.load(std::memory_order_acquire) != seen; });
     } else {
@@ -1348,8 +1393,8 @@ int mppi_server_wait(mppi_server *s, uint64_t id, double timeout_ms, float *h_u0
   }
 }
 
-int mppi_server_reap(mppi_server *s, int max_n, uint64_t *ids, float *h_u0, int *status, double timeout_ms,
-                     int *n_out) {
+int mppi_server_reap(mppi_server *s, int max_n, uint64_t *ids, float *h_u0, int *status, double *latency_ms,
+                     double timeout_ms, int *n_out) {
   if (!s || max_n < 0 || !n_out || (max_n > 0 && (!ids || !h_u0))) return MPPI_EINVAL;
   *n_out = 0;
   std::unique_lock<std::mutex> lk(s->mu);
@@ -1363,6 +1408,8 @@ int mppi_server_reap(mppi_server *s, int max_n, uint64_t *ids, float *h_u0, int 
       auto r = s->reqs.find(id);
       if (r == s->reqs.end()) continue;  // already taken by poll / wait, or cancelled
       ids[k] = id;
+      if (latency_ms)
+        latency_ms[k] = std::chrono::duration<double, std::milli>(r->second.t_done - r->second.t_submit).count();
       const int rc = take_result(s, r, h_u0 + 4 * k);
       if (status) status[k] = rc;
       ++k;

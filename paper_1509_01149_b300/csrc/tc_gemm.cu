@@ -4,11 +4,17 @@
 //   C[M x N] = A[M x K] . B[K x N],   A(m, k) = A[m*sam + k*sak],  B(k, n) = B[k*sbk + n*sbn]
 //
 // One CTA (128 threads) per 128 x BN output tile.  Each 64-wide K slab of A and B is
-// gathered from global memory by all threads (any strides, so transposed operands cost
-// nothing extra) into the no-swizzle K-major core-matrix layout, then one elected
-// thread issues the 16-deep tcgen05.mma instructions and commits them to an mbarrier.
-// The epilogue reads the FP32 accumulator back with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31, i.e. output rows) and applies the fused operation.
+// gathered from global memory by all threads into the no-swizzle K-major core-matrix layout
+// (any strides, so transposed operands need no copy): 16-byte loads where 8 consecutive
+// elements are contiguous in memory along K (one 16-byte core-matrix row per load) or along
+// the rows (one load feeds 8 rows), element-wise loads otherwise.  Two shared-memory stages:
+// while the tensor core multiplies slab s (one elected thread issues the 16-deep
+// tcgen05.mma instructions and commits them to the stage's mbarrier), the threads gather slab
+// s + 1 into the other stage, after the MMAs of slab s - 1 have released it.  The epilogue
+// reads the FP32 accumulator back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e.
+// output rows) and applies the fused operation.  Split-K (gridDim.z > 1) either adds into C
+// atomically (kEpiAtomicF32) or stores each split's partial product to its own slice
+// Cf + z * split_stride (kEpiStoreF32), for a reduction in a fixed order afterwards.
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -20,97 +26,171 @@ namespace mppi {
 namespace {
 constexpr int kBM = 128, kKT = 64, kThreads = 128;
 constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kStageA = kBM * kKT * 2;     // 16 KB
+constexpr uint32_t kStageB = 256 * kKT * 2;     // 32 KB (BN <= 256)
+constexpr uint32_t kStageBytes = kStageA + kStageB;
+static_assert(2 * kStageBytes <= kGemmSmemBytes, "two stages fit the dynamic shared memory");
+
+__device__ __forceinline__ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Rows [r0, r0 + Rn) x K slab [k0, k0 + klen) of X(r, k) = X[r*srow + k*sk] (rows >= nrows and
+// k >= klen read as 0) into the K-major core-matrix tile `dst` with Rn rows and kpad columns.
+__device__ __forceinline__ void gather_tile(const __nv_bfloat16 *__restrict__ X, int64_t srow, int64_t sk, int r0,
+                                            int nrows, int Rn, int k0, int klen, int kpad, unsigned char *dst,
+                                            int tid) {
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  if (sk == 1 && (srow & 7) == 0 && aligned16(X)) {
+    // eight consecutive k of one row: one 16-byte load, one 16-byte core-matrix row
+    const int cpr = kpad >> 3;
+    for (int idx = tid; idx < Rn * cpr; idx += kThreads) {
+      const int r = idx / cpr, c = (idx - r * cpr) << 3;
+      const int row = r0 + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (row < nrows) {
+        const __nv_bfloat16 *src = X + static_cast<int64_t>(row) * srow + k0 + c;
+        if (c + 8 <= klen) {
+          v = *reinterpret_cast<const uint4 *>(src);
+        } else {
+          __nv_bfloat16 t[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) t[e] = c + e < klen ? src[e] : zero;
+          v = *reinterpret_cast<const uint4 *>(t);
+        }
+      }
+      *reinterpret_cast<uint4 *>(dst + tc::kmajor_offset(r, c, Rn)) = v;
+    }
+  } else if (srow == 1 && (sk & 7) == 0 && (r0 & 7) == 0 && aligned16(X)) {
+    // eight consecutive rows at one k: one 16-byte load feeds eight core-matrix rows
+    const int groups = Rn >> 3;
+    for (int idx = tid; idx < groups * kpad; idx += kThreads) {
+      const int c = idx / groups, r = (idx - c * groups) << 3;
+      const int row = r0 + r;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (c < klen) {
+        const __nv_bfloat16 *src = X + row + static_cast<int64_t>(k0 + c) * sk;
+        if (row + 8 <= nrows) {
+          v = *reinterpret_cast<const uint4 *>(src);
+        } else {
+          __nv_bfloat16 t[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) t[e] = row + e < nrows ? src[e] : zero;
+          v = *reinterpret_cast<const uint4 *>(t);
+        }
+      }
+      const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) *reinterpret_cast<__nv_bfloat16 *>(dst + tc::kmajor_offset(r + i, c, Rn)) = e[i];
+    }
+  } else {
+    for (int idx = tid; idx < Rn * kpad; idx += kThreads) {
+      int r, c;
+      if (sk == 1) {
+        r = idx / kpad;
+        c = idx % kpad;
+      } else {
+        r = idx % Rn;
+        c = idx / Rn;
+      }
+      const int row = r0 + r;
+      __nv_bfloat16 v = zero;
+      if (row < nrows && c < klen) v = X[static_cast<int64_t>(row) * srow + static_cast<int64_t>(k0 + c) * sk];
+      *reinterpret_cast<__nv_bfloat16 *>(dst + tc::kmajor_offset(r, c, Rn)) = v;
+    }
+  }
+}
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * g.BN;
   const int BN = g.BN;
-  unsigned char *sA = smem;               // [128 x 64] K-major
-  unsigned char *sB = smem + 128 * kKT * 2;  // [BN x 64] K-major
 
   if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
-  if (tid == 0) tc::mbar_init(&bar, 1);
+  if (tid == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
   const uint32_t wait_limit = g.wait_limit ? g.wait_limit : tc::kWaitLimit;
-  uint32_t phase = 0;
   bool ok = true;
 
   // split-K: this CTA reduces K in [kbeg, kend)
   const int nsplit = g.ksplit > 1 ? g.ksplit : 1;
   const int kchunk = ((g.K + nsplit - 1) / nsplit + kKT - 1) / kKT * kKT;
   const int kbeg = blockIdx.z * kchunk, kend = min(g.K, kbeg + kchunk);
-  const int64_t csn = g.ldcn ? g.ldcn : 1;
-  for (int k0 = kbeg; k0 < kend && ok; k0 += kKT) {
-    const int klen = min(kKT, kend - k0);
-    const int kpad = (klen + 15) & ~15;
-    // gather the A slab
-    for (int idx = tid; idx < kBM * kpad; idx += kThreads) {
-      int r, c;
-      if (g.sak == 1) {
-        r = idx / kpad;
-        c = idx % kpad;
-      } else {
-        r = idx % kBM;
-        c = idx / kBM;
-      }
-      const int m = m0 + r, k = k0 + c;
-      __nv_bfloat16 v = __float2bfloat16(0.0f);
-      if (m < g.M && c < klen) v = g.A[static_cast<int64_t>(m) * g.sam + static_cast<int64_t>(k) * g.sak];
-      *reinterpret_cast<__nv_bfloat16 *>(sA + tc::kmajor_offset(r, c, kBM)) = v;
-    }
-    // gather the B slab (rows = n)
-    for (int idx = tid; idx < BN * kpad; idx += kThreads) {
-      int r, c;
-      if (g.sbk == 1) {
-        r = idx / kpad;
-        c = idx % kpad;
-      } else {
-        r = idx % BN;
-        c = idx / BN;
-      }
-      const int n = n0 + r, k = k0 + c;
-      __nv_bfloat16 v = __float2bfloat16(0.0f);
-      if (n < g.N && c < klen) v = g.B[static_cast<int64_t>(k) * g.sbk + static_cast<int64_t>(n) * g.sbn];
-      *reinterpret_cast<__nv_bfloat16 *>(sB + tc::kmajor_offset(r, c, BN)) = v;
-    }
+  const int ns = kbeg < kend ? (kend - kbeg + kKT - 1) / kKT : 0;  // K slabs
+  auto gather = [&](int s) {
+    const int k0 = kbeg + s * kKT, klen = min(kKT, kend - k0), kpad = (klen + 15) & ~15;
+    unsigned char *sA = smem + (s & 1) * kStageBytes, *sB = sA + kStageA;
+    gather_tile(g.A, g.sam, g.sak, m0, g.M, kBM, k0, klen, kpad, sA, tid);
+    gather_tile(g.B, g.sbn, g.sbk, n0, g.N, BN, k0, klen, kpad, sB, tid);
+  };
+  int last = -1;  // the last slab whose MMAs were committed
+  if (ns > 0) {
+    gather(0);
     tc::fence_smem_to_async();
     __syncthreads();
-    if (tid == 0 && !g.debug_skip_mma) {
-      tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-      const uint32_t lbo_a = kBM * 16, lbo_b = BN * 16;
-      for (int kk = 0; kk < kpad / 16; ++kk) {
-        const uint64_t ad = tc::smem_desc(a0 + kk * 2 * lbo_a, lbo_a, 128);
-        const uint64_t bd = tc::smem_desc(b0 + kk * 2 * lbo_b, lbo_b, 128);
-        tc::mma_bf16(tmem, ad, bd, idesc, (k0 > kbeg || kk > 0) ? 1u : 0u);
+    for (int s = 0; s < ns; ++s) {
+      if (tid == 0 && !g.debug_skip_mma) {
+        tc::fence_after_sync();
+        const int k0 = kbeg + s * kKT, klen = min(kKT, kend - k0), kpad = (klen + 15) & ~15;
+        const uint32_t a0 = tc::smem_u32(smem + (s & 1) * kStageBytes), b0 = a0 + kStageA;
+        const uint32_t lbo_a = kBM * 16, lbo_b = BN * 16;
+        for (int kk = 0; kk < kpad / 16; ++kk) {
+          const uint64_t ad = tc::smem_desc(a0 + kk * 2 * lbo_a, lbo_a, 128);
+          const uint64_t bd = tc::smem_desc(b0 + kk * 2 * lbo_b, lbo_b, 128);
+          tc::mma_bf16(tmem, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc::mma_commit(&bar[s & 1]);
       }
-      tc::mma_commit(&bar);
+      last = s;
+      if (s + 1 < ns) {
+        if (s >= 1) {
+          // the other stage was read by slab s - 1's MMAs: its commit is that barrier's
+          // ((s - 1) / 2)-th completion
+          const bool got = tc::mbar_wait(&bar[(s + 1) & 1], ((s - 1) >> 1) & 1u, wait_limit);
+          ok = __syncthreads_and(got) != 0;  // block-uniform
+          if (!ok) break;
+        }
+        gather(s + 1);
+        tc::fence_smem_to_async();
+      }
+      __syncthreads();
     }
-    const bool got = tc::mbar_wait(&bar, phase, wait_limit);
-    phase ^= 1u;
+    if (ok) {
+      const bool got = tc::mbar_wait(&bar[(ns - 1) & 1], ((ns - 1) >> 1) & 1u, wait_limit);
+      ok = __syncthreads_and(got) != 0;
+    }
     tc::fence_after_sync();
-    ok = __syncthreads_and(got) != 0;  // block-uniform
   }
 
   if (!ok) {
     if (tid == 0) atomicExch(g.err, 1);
-    tc::mbar_wait(&bar, phase ^ 1u, wait_limit);  // second, bounded chance for the MMAs in flight
+    // second, bounded chance for the MMAs in flight (they complete in order: the last commit)
+    if (last >= 0) tc::mbar_wait(&bar[last & 1], (last >> 1) & 1u, wait_limit);
   } else {
     // epilogue: row m = m0 + 32*warp + lane, columns n0 .. n0+BN
     const int m = m0 + 32 * warp + lane;
-    const bool empty = kbeg >= kend;  // a split with no K range contributes nothing
-    for (int c0 = 0; c0 < BN && !empty; c0 += 8) {
+    const bool empty = ns == 0;  // a split with no K range contributes nothing
+    const int64_t csn = g.ldcn ? g.ldcn : 1;
+    float *Cf = g.Cf ? g.Cf + static_cast<int64_t>(blockIdx.z) * g.split_stride : nullptr;
+    for (int c0 = 0; c0 < BN; c0 += 8) {
       float v[8];
-      tc::tmem_ld8(tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(c0), v);
-      tc::tmem_ld_wait();
+      if (!empty) {
+        tc::tmem_ld8(tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(c0), v);
+        tc::tmem_ld_wait();
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+        if (g.mode != kEpiStoreF32 || g.split_stride == 0) break;  // only a split slice must be written
+      }
       if (m < g.M) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -119,22 +199,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
           float a = g.alpha * v[j];
           switch (g.mode) {
             case kEpiStoreF32:
-              g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = a;
+              Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = a;
               break;
             case kEpiAddF32:
-              g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] += a;
+              Cf[static_cast<int64_t>(m) * g.ldc + n * csn] += a;
               break;
             case kEpiAtomicF32:
-              atomicAdd(&g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn], a);
+              atomicAdd(&Cf[static_cast<int64_t>(m) * g.ldc + n * csn], a);
               break;
             case kEpiBiasTanh: {
               const float h = tanhf(a + g.bias[n]);
               g.Cb[static_cast<int64_t>(m) * g.ldcb + n] = __float2bfloat16(h);
-              if (g.Cf) g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = h;
+              if (Cf) Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = h;
               break;
             }
             case kEpiBiasF32:
-              g.Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = a + g.bias[n];
+              Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = a + g.bias[n];
               break;
             case kEpiTanhGrad: {
               const float h = __bfloat162float(g.H[static_cast<int64_t>(m) * g.ldh + n]);
@@ -165,7 +245,8 @@ cudaError_t launch_gemm_bf16(const GemmArgs &g, cudaStream_t s) {
   }
   if (g.BN < 16 || g.BN > 256 || (g.BN & 15) != 0) return cudaErrorInvalidValue;
   const int nsplit = g.ksplit > 1 ? g.ksplit : 1;
-  if (nsplit > 1 && g.mode != kEpiAtomicF32) return cudaErrorInvalidValue;
+  if (nsplit > 1 && g.mode != kEpiAtomicF32 && !(g.mode == kEpiStoreF32 && g.split_stride > 0))
+    return cudaErrorInvalidValue;
   const dim3 grid((g.M + kBM - 1) / kBM, (g.N + g.BN - 1) / g.BN, nsplit);
   k_gemm_bf16<<<grid, kThreads, kGemmSmemBytes, s>>>(g);
   return cudaGetLastError();

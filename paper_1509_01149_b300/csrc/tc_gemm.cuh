@@ -32,7 +32,9 @@ struct GemmArgs {
   const __nv_bfloat16 *H;
   int64_t ldh;
   int *err;                     // set to 1 if a bounded wait ran out
-  int ksplit;                   // K range split over gridDim.z CTAs (mode kEpiAtomicF32); 0/1 = no split
+  int ksplit;                   // K range split over gridDim.z CTAs (kEpiAtomicF32, or kEpiStoreF32 with
+                                // split_stride > 0); 0/1 = no split
+  int64_t split_stride;         // kEpiStoreF32 with splits: split z writes its partial to Cf + z * split_stride
   uint32_t wait_limit;          // mbarrier polls before a wait gives up (0: tc::kWaitLimit)
   int debug_skip_mma;           // check hook only: issue no MMA (so the waits run out, nothing in flight)
 };

@@ -183,7 +183,8 @@ def poisson_rate_for(target_active: int, mean_lifetime: float) -> float:
 # ---------------------------------------------------------------------------------------
 @dataclass
 class AsyncStats:
-    latency_ms: list = field(default_factory=list)    # submit -> result, every request
+    latency_ms: list = field(default_factory=list)    # submit -> result in the client's hands, every request
+    server_latency_ms: list = field(default_factory=list)   # submit -> the scheduler saw its tick finish
     missed_periods: int = 0                           # periods skipped: the previous result came too late
     periods: int = 0
     rollout_steps: int = 0
@@ -195,8 +196,11 @@ class AsyncStats:
 
     def summary(self, wall_s: float) -> dict:
         lat = np.asarray(self.latency_ms, dtype=np.float64)
+        slat = np.asarray(self.server_latency_ms, dtype=np.float64)
         return {
             "requests": int(lat.size),
+            "server_p50_ms": float(np.percentile(slat, 50)) if slat.size else None,
+            "server_p99_ms": float(np.percentile(slat, 99)) if slat.size else None,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "max_ms": float(lat.max()) if lat.size else None,
@@ -218,19 +222,42 @@ class AsyncServingLoop:
     vectorised over controllers of one system; None keeps the state fixed).  A controller
     whose result has not come back by its next period skips that period (a deadline miss).
     Admission and release happen while ticks are on the GPU.  Records every request's
-    latency from submit to result."""
+    latency from submit to result in the client's hands, and the server's own (submit to the
+    retirement of its tick).  The per-controller state lives in arrays indexed by slot, so a
+    pass of the loop costs a few vectorised operations, not a Python loop over controllers."""
+
+    NX = 16
 
     def __init__(self, server, workloads_mod, env_ids: dict, plant=None, seed: int = 0, period_ms: float = 20.0,
-                 systems=SYSTEMS, k_choices=K_CHOICES, t_choices=T_CHOICES, system_p=None, k_p=None, t_p=None):
+                 systems=SYSTEMS, k_choices=K_CHOICES, t_choices=T_CHOICES, system_p=None, k_p=None, t_p=None,
+                 max_slots: int | None = None):
         self.server, self.W, self.env_ids, self.plant = server, workloads_mod, env_ids, plant
         self.rng = np.random.default_rng(seed)
         self.period = period_ms / 1e3
         self.systems, self.k_choices, self.t_choices = systems, k_choices, t_choices
         self.system_p, self.k_p, self.t_p = system_p, k_p, t_p
-        self.ctrl = {}        # slot -> dict(system, K, T, x, x0, dt, due, left, outstanding, t_submit)
+        S = max_slots or getattr(server, "max_slots", 4096)
+        self.active = np.zeros(S, dtype=bool)
+        self.system = np.zeros(S, dtype=np.int64)
+        self.K = np.zeros(S, dtype=np.int64)
+        self.T = np.zeros(S, dtype=np.int64)
+        self.due = np.full(S, np.inf)
+        self.left = np.zeros(S, dtype=np.int64)
+        self.outstanding = np.zeros(S, dtype=np.uint64)      # request id in flight, 0: none
+        self.t_submit = np.zeros(S)
+        self.X = np.zeros((S, self.NX))
+        self.X0 = np.zeros((S, self.NX))
+        self.dt = {sy: workloads_mod.config(sy)["dt"] for sy in systems}
+        self.nx = {sy: workloads_mod.STATE_DIM[sy] for sy in systems}
         self.waiting = []     # arrived, not yet admitted: (system, K, T, lifetime)
         self.next_rid = 0
+        self._by_id = {}
         self.stats = AsyncStats()
+
+    @property
+    def ctrl(self):
+        """Slots of the admitted controllers."""
+        return set(np.flatnonzero(self.active).tolist())
 
     def _arrival(self, mean_lifetime_periods: float):
         return (int(self.rng.choice(self.systems, p=self.system_p)), int(self.rng.choice(self.k_choices, p=self.k_p)),
@@ -238,56 +265,58 @@ class AsyncServingLoop:
                 max(1, int(self.rng.geometric(1.0 / max(mean_lifetime_periods, 1.0)))))
 
     def _admit_waiting(self, now: float):
+        """Admit waiting controllers in arrival order until the first refusal (FIFO: a large
+        controller at the head is not overtaken by smaller ones behind it)."""
         still = []
-        for system, K, T, life in self.waiting:
+        for n, (system, K, T, life) in enumerate(self.waiting):
             cfg = default_config(system, K, T, self.next_rid, self.server, self.W, self.env_ids)
             slot = self.server.admit(cfg)
             if slot is None:
                 self.stats.refused_attempts += 1
-                still.append((system, K, T, life))
-                continue
+                still = self.waiting[n:]
+                break
             self.next_rid += 1
-            c = self.W.config(system)
-            x0 = np.asarray(c["x0"], dtype=np.float64)
-            self.ctrl[slot] = dict(system=system, K=K, T=T, x=x0.copy(), x0=x0, dt=c["dt"],
-                                   due=now + self.rng.uniform(0.0, self.period), left=life, outstanding=None,
-                                   t_submit=0.0)
+            x0 = np.asarray(self.W.config(system)["x0"], dtype=np.float64)
+            self.active[slot] = True
+            self.system[slot], self.K[slot], self.T[slot] = system, K, T
+            self.due[slot] = now + self.rng.uniform(0.0, self.period)
+            self.left[slot] = life
+            self.outstanding[slot] = 0
+            self.X0[slot] = 0.0
+            self.X0[slot, :x0.size] = x0
+            self.X[slot] = self.X0[slot]
             self.stats.admitted += 1
         self.waiting = still
 
-    def _apply_results(self, ids, u0, status, now):
-        by_sys = {}
-        for rid, u, st in zip(ids, u0, status):
-            slot = self._by_id.pop(int(rid), None)
-            if slot is None:
+    def _apply_results(self, ids, u0, status, now, server_lat=None):
+        if server_lat is not None:
+            self.stats.server_latency_ms.extend(np.asarray(server_lat, dtype=np.float64).tolist())
+        slots = np.array([self._by_id.pop(int(r), -1) for r in ids], dtype=np.int64)
+        keep = slots >= 0
+        slots, u0, status = slots[keep], np.asarray(u0)[keep], np.asarray(status)[keep]
+        if slots.size == 0:
+            return
+        self.outstanding[slots] = 0
+        self.stats.latency_ms.extend((1e3 * (now - self.t_submit[slots])).tolist())
+        self.stats.rollout_steps += int(np.sum(self.K[slots] * self.T[slots]))
+        ok = status == 0
+        for system in self.systems:
+            sel = ok & (self.system[slots] == system)
+            if not np.any(sel) or self.plant is None:
                 continue
-            c = self.ctrl[slot]
-            c["outstanding"] = None
-            self.stats.latency_ms.append(1e3 * (now - c["t_submit"]))
-            self.stats.rollout_steps += c["K"] * c["T"]
-            if st != 0:
-                continue
-            by_sys.setdefault(c["system"], []).append((slot, u))
-        for system, items in by_sys.items():
-            slots = [s for s, _ in items]
-            m = self.W.CONTROL_DIM[system]
-            U = np.stack([u[:m] for _, u in items]).astype(np.float64)
-            X = np.stack([self.ctrl[s]["x"] for s in slots])
-            if self.plant is not None:
-                X = self.plant(system, X, U, self.ctrl[slots[0]]["dt"])
-            for s, x in zip(slots, X):
-                c = self.ctrl[s]
-                if not np.all(np.isfinite(x)):
-                    x = c["x0"].copy()
-                    self.stats.plant_resets += 1
-                c["x"] = x
+            ss = slots[sel]
+            n, m = self.nx[system], self.W.CONTROL_DIM[system]
+            Xn = self.plant(system, self.X[ss, :n], u0[sel, :m].astype(np.float64), self.dt[system])
+            bad = ~np.all(np.isfinite(Xn), axis=1)
+            if np.any(bad):
+                Xn[bad] = self.X0[ss[bad], :n]
+                self.stats.plant_resets += int(np.sum(bad))
+            self.X[ss, :n] = Xn
 
     def run(self, duration_s: float, target_active: int, mean_lifetime_periods: float = 200.0,
             warmup_s: float = 0.5) -> dict:
         """Hold about `target_active` controllers for warmup_s + duration_s of wall time
-        (arrival rate from Little's law); statistics cover the last duration_s.  Due times sit
-        in a heap, so each loop pass costs O(log n) per due controller, not O(n)."""
-        import heapq
+        (arrival rate from Little's law); statistics cover the last duration_s."""
         srv = self.server
         self._by_id = {}
         rate = target_active / (mean_lifetime_periods * self.period)      # arrivals per second
@@ -295,13 +324,13 @@ class AsyncServingLoop:
         for _ in range(target_active):
             self.waiting.append(self._arrival(mean_lifetime_periods))
         self._admit_waiting(t0)
-        heap = [(c["due"], slot) for slot, c in self.ctrl.items()]
-        heapq.heapify(heap)
-        known = set(self.ctrl)
+        t0 = time.perf_counter()                 # phases count from the end of the first admissions
+        act = np.flatnonzero(self.active)
+        self.due[act] = t0 + self.rng.uniform(0.0, self.period, act.size)
         srv.start()
         t_rec, t_end, t_last = t0 + warmup_s, t0 + warmup_s + duration_s, t0
         recording = False
-        busy_s, t_busy0 = 0.0, None
+        busy_s = 0.0
         try:
             while True:
                 now = time.perf_counter()
@@ -318,58 +347,52 @@ class AsyncServingLoop:
                 t_last = now
                 if self.waiting:
                     self._admit_waiting(now)
-                    for slot in set(self.ctrl) - known:
-                        heapq.heappush(heap, (self.ctrl[slot]["due"], slot))
-                    known = set(self.ctrl)
-                # due controllers submit; one whose last result is still out skips the period
-                due_slots, due_states = [], []
-                while heap and heap[0][0] <= now:
-                    _, slot = heapq.heappop(heap)
-                    c = self.ctrl[slot]
-                    c["due"] += self.period
-                    if c["outstanding"] is not None:
-                        self.stats.missed_periods += 1
-                        heapq.heappush(heap, (c["due"], slot))
-                        continue
-                    if c["left"] <= 0:
+                # due controllers submit; one whose last result is still out skips the period;
+                # periods that passed entirely while the loop was elsewhere are missed
+                due = np.flatnonzero(self.active & (self.due <= now))
+                if due.size:
+                    late = np.floor((now - self.due[due]) / self.period).astype(np.int64)
+                    self.stats.missed_periods += int(late.sum())
+                    self.due[due] += (late + 1) * self.period
+                    busy = self.outstanding[due] != 0
+                    self.stats.missed_periods += int(busy.sum())
+                    due = due[~busy]
+                    done = due[self.left[due] <= 0]
+                    for slot in done.tolist():
                         srv.release(slot)
-                        del self.ctrl[slot]
-                        known.discard(slot)
+                        self.active[slot] = False
+                        self.due[slot] = np.inf
                         self.stats.released += 1
-                        continue
-                    c["left"] -= 1
-                    self.stats.periods += 1
-                    due_slots.append(slot)
-                    due_states.append(c["x"].astype(np.float32))
-                    heapq.heappush(heap, (c["due"], slot))
-                if due_slots:
-                    ids = srv.submit_batch(due_slots, due_states)
-                    ts = time.perf_counter()
-                    for slot, rid in zip(due_slots, ids):
-                        self.ctrl[slot]["outstanding"] = int(rid)
-                        self.ctrl[slot]["t_submit"] = ts
-                        self._by_id[int(rid)] = slot
-                self.stats.active.append(len(self.ctrl))
+                    due = due[self.left[due] > 0]
+                if due.size:
+                    self.left[due] -= 1
+                    self.stats.periods += int(due.size)
+                    ids = srv.submit_batch(due.tolist(), self.X[due].astype(np.float32))
+                    self.outstanding[due] = ids
+                    self.t_submit[due] = time.perf_counter()
+                    self._by_id.update(zip(np.asarray(ids).tolist(), due.tolist()))
+                self.stats.active.append(int(self.active.sum()))
                 busy_s += time.perf_counter() - t_busy0
                 # results: wait until the next due time at most
-                next_due = heap[0][0] if heap else now + 1e-3
-                wait_ms = max(0.0, min(1.0, 1e3 * (next_due - time.perf_counter())))
-                ids, u0, st = srv.reap(4096, timeout_ms=wait_ms)
+                nxt = float(self.due.min()) if self.active.any() else now + 1e-3
+                wait_ms = max(0.0, min(1.0, 1e3 * (nxt - time.perf_counter())))
+                ids, u0, st, slat = srv.reap(4096, timeout_ms=wait_ms, with_latency=True)
                 if len(ids):
                     t_busy0 = time.perf_counter()
-                    self._apply_results(ids, u0, st, t_busy0)
+                    self._apply_results(ids, u0, st, t_busy0, slat)
                     busy_s += time.perf_counter() - t_busy0
         finally:
             srv.stop()
-            ids, u0, st = srv.reap(4096, timeout_ms=0.0)
+            ids, u0, st, slat = srv.reap(4096, timeout_ms=0.0, with_latency=True)
             if len(ids):
-                self._apply_results(ids, u0, st, time.perf_counter())
+                self._apply_results(ids, u0, st, time.perf_counter(), slat)
         out = self.stats.summary(duration_s)
         out["client_busy_fraction"] = busy_s / duration_s
         return out
 
     def drain(self):
-        for slot in list(self.ctrl):
+        for slot in np.flatnonzero(self.active).tolist():
             self.server.release(slot)
-        self.ctrl.clear()
+        self.active[:] = False
+        self.due[:] = np.inf
         self.waiting.clear()

@@ -46,17 +46,17 @@ class FakeAsyncServer:
         self.submitted += len(slots)
         return ids
 
-    def reap(self, max_n=4096, timeout_ms=0.0):
+    def reap(self, max_n=4096, timeout_ms=0.0, with_latency=False):
         out, self.done = self.done[:max_n], self.done[max_n:]
-        return (np.asarray(out, dtype=np.uint64), np.zeros((len(out), 4), np.float32),
-                np.zeros(len(out), np.int32))
+        res = (np.asarray(out, dtype=np.uint64), np.zeros((len(out), 4), np.float32), np.zeros(len(out), np.int32))
+        return res + (np.full(len(out), 0.5),) if with_latency else res
 
 
 def test_async_loop_submits_every_period_and_records_each_latency():
     srv = FakeAsyncServer(64, 10 ** 12)
     loop = serving.AsyncServingLoop(srv, W, {W.CAR: 0, W.QUAD: 1}, seed=3)
     summ = loop.run(0.3, target_active=20, mean_lifetime_periods=5.0, warmup_s=0.05)
-    assert summ["requests"] > 100 and summ["p99_ms"] < serving.DEADLINE_MS
+    assert summ["requests"] > 100 and summ["p99_ms"] < serving.DEADLINE_MS and summ["server_p99_ms"] == 0.5
     assert summ["missed_periods"] == 0 and summ["released"] > 0 and summ["admitted"] > 0
     assert not srv.running                               # the loop stops the scheduler
     loop.drain()
