@@ -60,8 +60,7 @@ typedef enum {
   MPPI_CAR_MLP = 3,  /* MPPI_CAR's cost with learned dynamics x' = x + MLP([x; u])       */
   MPPI_CARTPOLE_VEL = 4 /* the cart-pole of Sec. V-A: n=4 (p, pdot, theta, thetadot), theta = 0
                            hanging down; m=1 desired cart velocity, pddot = 10 (u - pdot); Euler;
-                           q = p^2 + 500 (1 + cos theta)^2 + thetadot^2 + pdot^2.  Single
-                           controllers only (not in the server)                              */
+                           q = p^2 + 500 (1 + cos theta)^2 + thetadot^2 + pdot^2            */
 } mppi_system;
 
 /* implementation of mppi_step */

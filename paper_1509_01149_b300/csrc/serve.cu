@@ -116,6 +116,10 @@ __global__ void __launch_bounds__(BLK, MINB) k_serve_rollout(const ServeArgs a) 
       case MPPI_QUAD:
         rollout_block<Quad, BLK, true>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block, smem);
         break;
+      case MPPI_CARTPOLE_VEL:
+        rollout_block<CartPoleVel, BLK, true>(s_p, x0, d->counter, d->U, w.block * BLK, d->S, ps, d->part + w.block,
+                                              smem);
+        break;
       default:
         break;
     }
@@ -226,6 +230,7 @@ int dims_of(int sys, int *n, int *m) {
     case MPPI_CARTPOLE: *n = 4; *m = 1; return MPPI_OK;
     case MPPI_CAR: *n = 7; *m = 2; return MPPI_OK;
     case MPPI_QUAD: *n = 12; *m = 4; return MPPI_OK;
+    case MPPI_CARTPOLE_VEL: *n = 4; *m = 1; return MPPI_OK;
     default: return MPPI_EINVAL;
   }
 }

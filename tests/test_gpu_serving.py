@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 ENV = {W.CAR: 0, W.QUAD: 1}
 MIX = [(W.CARTPOLE, 1000, 100), (W.CAR, 4096, 100), (W.QUAD, 2048, 150), (W.CAR, 512, 50),
        (W.CARTPOLE, 16384, 200), (W.QUAD, 1024, 50), (W.CAR, 16384, 200), (W.CARTPOLE, 513, 150),
-       (W.QUAD, 777, 7), (W.CAR, 129, 3)]
+       (W.QUAD, 777, 7), (W.CAR, 129, 3), (W.CARTPOLE_VEL, 2000, 50)]
 
 
 @pytest.fixture(scope="module")
@@ -107,7 +107,8 @@ def test_served_ticks_match_the_oracle_costs_argmin_and_controls(N):
     updated, shifted controls within the U bar."""
     from oracle import mppi as om
     srv = make_server(N)
-    picks = [(W.CAR, 2048, 60), (W.CARTPOLE, 1000, 100), (W.QUAD, 1024, 40), (W.CAR, 777, 13)]
+    picks = [(W.CAR, 2048, 60), (W.CARTPOLE, 1000, 100), (W.QUAD, 1024, 40), (W.CAR, 777, 13),
+             (W.CARTPOLE_VEL, 1500, 50)]
     slots, cfgs = zip(*[admit(srv, s, K, T, 200 + i) for i, (s, K, T) in enumerate(picks)])
     states = [W.config(p[0])["x0"] for p in picks]
     for tick in range(3):
