@@ -56,13 +56,15 @@ def uniform_from_word(w) -> np.ndarray:
     return ((w >> np.uint64(9)).astype(np.float64) + 0.5) * 2.0 ** -23
 
 
-def philox_words(seed: int, K: int, T: int, m: int, counter: int, gid: int) -> np.ndarray:
+def philox_words(seed: int, K: int, T: int, m: int, counter: int, gid: int, samples=None) -> np.ndarray:
     """Raw Philox words for one iteration: array [n_blocks, 4, K] of uint32 values
-    (as uint64), block b covering normal indices 4b..4b+3."""
+    (as uint64), block b covering normal indices 4b..4b+3.  `samples` (sample indices) gives
+    the columns of those samples only, [n_blocks, 4, len(samples)]."""
     n_blocks = (T * m + 3) // 4
     b = np.arange(n_blocks, dtype=np.uint64)[:, None]
-    k = np.arange(K, dtype=np.uint64)[None, :]
-    shape = (n_blocks, K)
+    ks = np.arange(K) if samples is None else np.asarray(samples)
+    k = ks.astype(np.uint64)[None, :]
+    shape = (n_blocks, ks.size)
     out = philox4x32_10(np.broadcast_to(b, shape), np.broadcast_to(k, shape),
                         np.full(shape, counter & 0xFFFFFFFF, dtype=np.uint64),
                         np.full(shape, gid & 0xFFFFFFFF, dtype=np.uint64),
@@ -70,9 +72,10 @@ def philox_words(seed: int, K: int, T: int, m: int, counter: int, gid: int) -> n
     return np.stack(out, axis=1)
 
 
-def standard_normals(seed: int, K: int, T: int, m: int, counter: int = 0, gid: int = 0) -> np.ndarray:
-    """eps[i][j][k] ~ N(0, 1), float64 [T][m][K], by Box-Muller on Philox uniforms."""
-    words = philox_words(seed, K, T, m, counter, gid)         # [B][4][K]
+def standard_normals(seed: int, K: int, T: int, m: int, counter: int = 0, gid: int = 0, samples=None) -> np.ndarray:
+    """eps[i][j][k] ~ N(0, 1), float64 [T][m][K], by Box-Muller on Philox uniforms (the
+    columns of `samples` only, if given)."""
+    words = philox_words(seed, K, T, m, counter, gid, samples)         # [B][4][K]
     u = uniform_from_word(words)
     rad01 = np.sqrt(-2.0 * np.log(u[:, 0]))
     rad23 = np.sqrt(-2.0 * np.log(u[:, 2]))
@@ -80,18 +83,20 @@ def standard_normals(seed: int, K: int, T: int, m: int, counter: int = 0, gid: i
     ang23 = 2.0 * np.pi * u[:, 3]
     eps = np.stack([rad01 * np.cos(ang01), rad01 * np.sin(ang01),
                     rad23 * np.cos(ang23), rad23 * np.sin(ang23)], axis=1)  # [B][4][K]
-    flat = eps.reshape(-1, K)[: T * m]            # normal index r = 4b + lane
-    return flat.reshape(T, m, K)
+    n = words.shape[2]
+    flat = eps.reshape(-1, n)[: T * m]            # normal index r = 4b + lane
+    return flat.reshape(T, m, n)
 
 
 def exploration_noise(seed: int, K: int, T: int, Sigma, nu: float,
-                      counter: int = 0, gid: int = 0) -> np.ndarray:
-    """delta_u[i][:, k] = sqrt(nu) * L @ eps[i][:, k], L = chol(Sigma); float64 [T][m][K].
-    Sigma may be positive semi-definite (a zero Sigma gives zero noise)."""
+                      counter: int = 0, gid: int = 0, samples=None) -> np.ndarray:
+    """delta_u[i][:, k] = sqrt(nu) * L @ eps[i][:, k], L = chol(Sigma); float64 [T][m][K]
+    (the columns of `samples` only, if given).  Sigma may be positive semi-definite (a zero
+    Sigma gives zero noise)."""
     Sigma = np.atleast_2d(np.asarray(Sigma, dtype=np.float64))
     m = Sigma.shape[0]
     L = cholesky_psd(Sigma)
-    eps = standard_normals(seed, K, T, m, counter, gid)
+    eps = standard_normals(seed, K, T, m, counter, gid, samples)
     return np.sqrt(nu) * np.einsum("ab,tbk->tak", L, eps)
 
 

@@ -191,7 +191,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
         for (int j = 0; j < 8; ++j) v[j] = 0.0f;
         if (g.mode != kEpiStoreF32 || g.split_stride == 0) break;  // only a split slice must be written
       }
-      if (m < g.M) {
+      // BF16 outputs of 8 whole columns: one 16-byte store per row (and one 16-byte load of H)
+      const int nb = n0 + c0;
+      const bool vec_bf16 = (g.mode == kEpiBiasTanh && !Cf) || g.mode == kEpiTanhGrad;
+      if (m < g.M && vec_bf16 && nb + 8 <= g.N && (g.ldcb & 7) == 0 && aligned16(g.Cb) &&
+          (g.mode != kEpiTanhGrad || ((g.ldh & 7) == 0 && aligned16(g.H)))) {
+        float o[8];
+        if (g.mode == kEpiBiasTanh) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) o[j] = tanhf(g.alpha * v[j] + g.bias[nb + j]);
+        } else {
+          const uint4 hv = *reinterpret_cast<const uint4 *>(g.H + static_cast<int64_t>(m) * g.ldh + nb);
+          const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&hv);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float hj = __bfloat162float(h[j]);
+            o[j] = g.alpha * v[j] * (1.0f - hj * hj);
+          }
+        }
+        __nv_bfloat16 ob[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ob[j] = __float2bfloat16(o[j]);
+        *reinterpret_cast<uint4 *>(g.Cb + static_cast<int64_t>(m) * g.ldcb + nb) = *reinterpret_cast<const uint4 *>(ob);
+      } else if (m < g.M && g.mode == kEpiStoreF32 && csn == 1 && nb + 8 <= g.N && (g.ldc & 3) == 0 &&
+                 aligned16(Cf)) {
+        // FP32 outputs of 8 whole contiguous columns: two 16-byte stores per row
+        float4 *dst = reinterpret_cast<float4 *>(Cf + static_cast<int64_t>(m) * g.ldc + nb);
+        dst[0] = make_float4(g.alpha * v[0], g.alpha * v[1], g.alpha * v[2], g.alpha * v[3]);
+        dst[1] = make_float4(g.alpha * v[4], g.alpha * v[5], g.alpha * v[6], g.alpha * v[7]);
+      } else if (m < g.M) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int n = n0 + c0 + j;

@@ -176,3 +176,58 @@ def test_autotune_leaves_no_trace(N):
     for rid, (s, K, T) in enumerate(MIX):
         assert within(got[rid, :W.CONTROL_DIM[s]], want[rid, :W.CONTROL_DIM[s]], W.config(s))
     srv.close()
+
+
+def test_full_size_serving_tick_on_sampled_outputs(N):
+    """The serving benchmark's configuration: 256 controllers of the uniform mix (cart-pole, car,
+    quadrotor; K in {512, 1024, 4096, 16384}; T in {50, 100, 150, 200}) stepped in one tick in
+    the launch configuration the bench times (after the autotuner), each from its own state.
+    For 12 controllers spread over the mix (the heaviest among them), the path costs of 64
+    samples spread over every block, computed by the oracle one sample at a time with the same
+    noise, are within the S~ bar; on every one of the 256 the argmin is the argmin of its own
+    costs and the normaliser is within the weighting's error bound on those costs."""
+    from oracle import mppi as om
+    from oracle import philox
+    from paper_1509_01149_b300 import serving
+    rng = np.random.default_rng(0)
+    srv = make_server(N, max_slots=512, arena=1 << 30)
+    n = 256
+    picks = [(int(rng.choice(serving.SYSTEMS)), int(rng.choice(serving.K_CHOICES)), int(rng.choice(serving.T_CHOICES)))
+             for _ in range(n)]
+    slots, cfgs = zip(*[admit(srv, s, K, T, 1000 + i) for i, (s, K, T) in enumerate(picks)])
+    states = []
+    for (s, K, T), c in zip(picks, cfgs):
+        x = np.asarray(c["x0"], dtype=np.float64).copy()
+        x[:2] += rng.normal(0.0, 0.05, 2)                   # each controller from its own state
+        states.append(x.astype(np.float32))
+    srv.autotune(list(slots), states)                       # leaves no trace on the controllers
+    srv.tick(list(slots), states)
+    work = np.array([K * T * (7 if s == W.QUAD else 1) for s, K, T in picks])
+    chosen = set(np.argsort(-work)[:4].tolist())            # the heaviest
+    for s in serving.SYSTEMS:                               # and some of every system
+        chosen |= set([i for i, p in enumerate(picks) if p[0] == s][:3])
+    chosen = sorted(chosen)[:12] if len(chosen) > 12 else sorted(chosen)
+    for i, (s, K, T) in enumerate(picks):
+        c = dict(cfgs[i], seed=1000 + i, gid=1000 + i)
+        dbg = srv.get_debug(slots[i], K)
+        lam = float(np.float32(c["lam"]))
+        fin = np.isfinite(dbg["S"])
+        assert dbg["kstar"] == int(np.argmin(np.where(fin, dbg["S"], np.inf)))
+        r = P.reduction_errors(dbg["S"], np.zeros((1, 1, K), np.float32), lam, dbg["eta"], np.zeros((1, 1)),
+                               dbg["kstar"])
+        assert r["eta_err"] <= r["eta_bound"], (i, r["eta_err"], r["eta_bound"])
+        if i not in chosen:
+            continue
+        idx = np.unique(np.concatenate([np.linspace(0, K - 1, 63).astype(int), [dbg["kstar"]]]))
+        du = philox.exploration_noise(c["seed"], K, T, np.asarray(c["Sigma"], np.float32).astype(np.float64),
+                                      float(np.float32(c["nu"])), 0, c["gid"], samples=idx)
+        sys_ = P.oracle_system(s, c["dt"])
+        R = np.asarray(c["R"], np.float32).astype(np.float64)
+        U0 = np.tile(np.asarray(c["u_init"], np.float32).astype(np.float64), (T, 1))
+        S_o, st = om.path_costs(sys_, states[i].astype(np.float64), U0, du, R, float(np.float32(c["nu"])))
+        keep = np.isfinite(S_o)
+        if getattr(st, "margin", None) is not None:
+            keep &= st.margin > 1e-3
+        rel = np.abs(dbg["S"][idx][keep].astype(np.float64) - S_o[keep]) / np.abs(S_o[keep])
+        assert rel.size > 0 and rel.max() <= P.S_RTOL, (i, s, K, T, rel.max())
+    srv.close()

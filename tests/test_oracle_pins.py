@@ -1040,3 +1040,12 @@ def test_general_covariance_one_iteration_reaches_the_lq_optimum():
     ustar, _ = _lq_optimum(lin, x0, T, R)
     est = np.mean([mppi.iteration_general(lin, x0, U, 200000, lam, R, SE, seed=s).U for s in range(4)], axis=0)
     assert np.abs(est - ustar).max() < 0.02 * np.abs(ustar).max() + 0.01
+
+
+def test_noise_of_a_sample_subset_is_those_columns():
+    """The sampled form of the noise (used to check full-size runs on a subset of samples)
+    gives exactly the columns of the full draw."""
+    S = np.array([[0.3, 0.1], [0.1, 0.35]])
+    full = philox.exploration_noise(11, 777, 9, S, 10.0, 4, 2)
+    idx = np.array([776, 0, 400, 129, 3])
+    assert np.array_equal(philox.exploration_noise(11, 777, 9, S, 10.0, 4, 2, samples=idx), full[:, :, idx])
