@@ -608,10 +608,21 @@ __global__ void __launch_bounds__(1024) k_plain_min(const float *__restrict__ S,
   __shared__ int s_i[32];
   float v = INFINITY;
   int idx = INT_MAX;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    if (S[k] < v || (S[k] == v && k < idx)) {
-      v = S[k];
-      idx = k;
+  constexpr int J = 8;  // loads of a pass issued before its comparisons
+  for (int k0 = threadIdx.x; k0 < K; k0 += J * blockDim.x) {
+    float s[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k = k0 + j * blockDim.x;
+      s[j] = k < K ? S[k] : INFINITY;
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int k = k0 + j * blockDim.x;
+      if (s[j] < v || (s[j] == v && k < idx)) {
+        v = s[j];
+        idx = k;
+      }
     }
   }
   warp_argmin(v, idx);
@@ -637,8 +648,8 @@ __global__ void __launch_bounds__(1024) k_plain_min(const float *__restrict__ S,
 // k_plain_weights forms every w_k = exp(-(S~_k - rho)/lambda) once (FP64 exponential, stored
 // rounded to FP32) with per-block FP64 partial sums of eta; k_plain_wsum reads each row of du
 // [T*m][K] once, kPlainRows rows by kPlainSplitK samples per block: each thread sums its
-// kPlainSplitK / kPlainBlock products per row in FP32, the block adds the thread sums in FP64
-// into per-split partials; k_plain_finalize adds the partials in a fixed order (FP64), divides
+// kPlainSplitK / kPlainBlock products per row in FP32, each warp adds its lanes' sums in FP32
+// (a fixed tree), the block adds the warp sums in FP64 into per-split partials; k_plain_finalize adds the partials in a fixed order (FP64), divides
 // by eta and updates U.  Scratch: w [K] floats (in a K-double slot) | eta partials
 // [ceil(K/256)] | wsum partials [splits][T*m] (doubles).
 constexpr int kPlainBlock = 256;
@@ -693,8 +704,8 @@ __global__ void __launch_bounds__(kPlainBlock) k_plain_wsum(const float *__restr
     float acc = 0.0f;
 #pragma unroll
     for (int j = 0; j < J; ++j) acc = fmaf(wk[j], dv[r][j], acc);
-    const double v = warp_sum_d(static_cast<double>(acc));
-    if (lane == 0) s_a[r][warp] = v;
+    acc = warp_sum_f(acc);
+    if (lane == 0) s_a[r][warp] = static_cast<double>(acc);
   }
   __syncthreads();
   if (threadIdx.x < kPlainRows && r0 + threadIdx.x < TM) {

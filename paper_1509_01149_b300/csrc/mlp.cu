@@ -335,12 +335,12 @@ int refresh_bf16(mppi_mlp *q) {
 
 // forward on Xb [B][16] into H1, H2 (bf16) and Y (f32)
 int forward(mppi_mlp *q, const __nv_bfloat16 *X, int B) {
-  GemmArgs g = gemm(B, kHid, kIn, 64, X, kIn, 1, q->w1, 1, kIn, kEpiBiasTanh, q->d_err);
+  GemmArgs g = gemm(B, kHid, kIn, 128, X, kIn, 1, q->w1, 1, kIn, kEpiBiasTanh, q->d_err);
   g.bias = q->p + kOffB1;
   g.Cb = q->H1;
   g.ldcb = kHid;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm h1"));
-  g = gemm(B, kHid, kHid, 64, q->H1, kHid, 1, q->w2, 1, kHid, kEpiBiasTanh, q->d_err);
+  g = gemm(B, kHid, kHid, 128, q->H1, kHid, 1, q->w2, 1, kHid, kEpiBiasTanh, q->d_err);
   g.bias = q->p + kOffB2;
   g.Cb = q->H2;
   g.ldcb = kHid;
@@ -377,7 +377,7 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW3"));
   MLP_TRY(split_sum(static_cast<size_t>(kOut) * kHid, q->g + kOffW3, "gW3 sum"));
   // dZ2 = (dY W3) * (1 - H2^2)
-  g = gemm(B, kHid, kOut, 64, q->dYb, kOut, 1, q->w3, kHid, 1, kEpiTanhGrad, q->d_err);
+  g = gemm(B, kHid, kOut, 128, q->dYb, kOut, 1, q->w3, kHid, 1, kEpiTanhGrad, q->d_err);
   g.H = q->H2;
   g.ldh = kHid;
   g.Cb = q->dZ2;
@@ -392,7 +392,7 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW2"));
   MLP_TRY(split_sum(static_cast<size_t>(kHid) * kHid, q->g + kOffW2, "gW2 sum"));
   // dZ1 = (dZ2 W2) * (1 - H1^2)
-  g = gemm(B, kHid, kHid, 64, q->dZ2, kHid, 1, q->w2, kHid, 1, kEpiTanhGrad, q->d_err);
+  g = gemm(B, kHid, kHid, 128, q->dZ2, kHid, 1, q->w2, kHid, 1, kEpiTanhGrad, q->d_err);
   g.H = q->H1;
   g.ldh = kHid;
   g.Cb = q->dZ1;

@@ -71,10 +71,16 @@ class LoopStats:
         }
 
 
+_workload_configs: dict = {}
+
+
 def default_config(system: int, K: int, T: int, rid: int, server, workloads_mod, env_ids: dict):
-    """Server slot configuration of one request from the workload defaults."""
-    W = workloads_mod
-    c = W.config(system, K=K, T=T)
+    """Server slot configuration of one request from the workload defaults (the defaults of
+    each (system, K, T) are built once: the car's start state walks its track)."""
+    key = (workloads_mod.__name__, system, K, T)
+    c = _workload_configs.get(key)
+    if c is None:
+        c = _workload_configs[key] = workloads_mod.config(system, K=K, T=T)
     return server.slot_config(system, K, T, c["dt"], c["nu"], c["lam"], c["Sigma"], c["R"], seed=rid, gid=rid,
                               env_id=env_ids.get(system, -1), u_init=c["u_init"])
 
@@ -247,7 +253,10 @@ class AsyncServingLoop:
         self.t_submit = np.zeros(S)
         self.X = np.zeros((S, self.NX))
         self.X0 = np.zeros((S, self.NX))
+        self.U_pend = np.zeros((S, 4))                       # returned u0 not yet applied to the plant
+        self.pend = np.zeros(S, dtype=bool)
         self.dt = {sy: workloads_mod.config(sy)["dt"] for sy in systems}
+        self._x0 = {sy: np.asarray(workloads_mod.config(sy)["x0"], dtype=np.float64) for sy in systems}
         self.nx = {sy: workloads_mod.STATE_DIM[sy] for sy in systems}
         self.waiting = []     # arrived, not yet admitted: (system, K, T, lifetime)
         self.next_rid = 0
@@ -276,8 +285,9 @@ class AsyncServingLoop:
                 still = self.waiting[n:]
                 break
             self.next_rid += 1
-            x0 = np.asarray(self.W.config(system)["x0"], dtype=np.float64)
+            x0 = self._x0[system]
             self.active[slot] = True
+            self.pend[slot] = False
             self.system[slot], self.K[slot], self.T[slot] = system, K, T
             self.due[slot] = now + self.rng.uniform(0.0, self.period)
             self.left[slot] = life
@@ -300,13 +310,26 @@ class AsyncServingLoop:
         self.stats.latency_ms.extend((1e3 * (now - self.t_submit[slots])).tolist())
         self.stats.rollout_steps += int(np.sum(self.K[slots] * self.T[slots]))
         ok = status == 0
+        if self.plant is not None and np.any(ok):
+            u = np.asarray(u0, dtype=np.float64)[ok]
+            self.U_pend[slots[ok], :u.shape[1]] = u
+            self.pend[slots[ok]] = True
+
+    def _advance_plants(self, horizon: float):
+        """Advance by one period, under its returned u0, the plant of every controller whose
+        result has come back and whose next period starts before `horizon` (so that plants are
+        stepped in batches of many controllers, each before its next request)."""
+        ready = np.flatnonzero(self.pend & (self.due <= horizon))
+        if ready.size == 0:
+            return
+        self.pend[ready] = False
+        sys_of = self.system[ready]
         for system in self.systems:
-            sel = ok & (self.system[slots] == system)
-            if not np.any(sel) or self.plant is None:
+            ss = ready[sys_of == system]
+            if ss.size == 0:
                 continue
-            ss = slots[sel]
             n, m = self.nx[system], self.W.CONTROL_DIM[system]
-            Xn = self.plant(system, self.X[ss, :n], u0[sel, :m].astype(np.float64), self.dt[system])
+            Xn = self.plant(system, self.X[ss, :n], self.U_pend[ss, :m], self.dt[system])
             bad = ~np.all(np.isfinite(Xn), axis=1)
             if np.any(bad):
                 Xn[bad] = self.X0[ss[bad], :n]
@@ -349,6 +372,8 @@ class AsyncServingLoop:
                     self._admit_waiting(now)
                 # due controllers submit; one whose last result is still out skips the period;
                 # periods that passed entirely while the loop was elsewhere are missed
+                if self.plant is not None and (self.pend & (self.due <= now)).any():
+                    self._advance_plants(now + 0.1 * self.period)
                 due = np.flatnonzero(self.active & (self.due <= now))
                 if due.size:
                     late = np.floor((now - self.due[due]) / self.period).astype(np.int64)
