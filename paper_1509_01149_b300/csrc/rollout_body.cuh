@@ -263,41 +263,83 @@ __device__ __forceinline__ void block_partial(const CtrlParams &p, int k, uint32
     }
   } else {
     const int nb = (TM + 3) >> 2;
-    // A warp whose samples all have weight exactly 0 (exp underflow: S~ - rho_b beyond ~103
-    // lambda) adds exactly 0 to every output, so it skips the regeneration; with sharp
-    // weights that is most warps of a block.
-    const bool warp_live = __any_sync(0xffffffffu, w != 0.0f);
-    // regenerate du, weight it, transpose-reduce 32 outputs (8 Philox blocks) at a time
-    for (int g = 0; g < nb; g += 8) {
-      float v[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) v[q] = 0.0f;
-      if (warp_live) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-          if (g + q < nb && k != INT_MAX)  // k == INT_MAX: a thread that owns no sample
-            normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+    // The samples of the block with a weight not exactly 0 (exp underflows beyond ~103 lambda
+    // above rho_b), listed in sample order.  With sharp weights they are few: then the block's
+    // threads share their regeneration, each forming whole Philox blocks of outputs summed over
+    // the listed samples in order (FP32, at most kLive deep); otherwise each warp with a live
+    // sample regenerates its 32 samples' du and the warps' sums are added.
+    constexpr int kLive = 32;
+    __shared__ int s_live_k[kLive];
+    __shared__ float s_live_w[kLive];
+    __shared__ int s_nlive[NW];
+    const bool live = w != 0.0f;  // implies a valid sample with a finite cost
+    const unsigned live_bits = __ballot_sync(0xffffffffu, live);
+    if (lane == 0) s_nlive[warp] = __popc(live_bits);
+    __syncthreads();
+    int before = 0, n_live = 0;
+    for (int q = 0; q < NW; ++q) {
+      before += q < warp ? s_nlive[q] : 0;
+      n_live += s_nlive[q];
+    }
+    if (n_live <= kLive) {
+      if (live) {
+        const int pos = before + __popc(live_bits & ((1u << lane) - 1u));
+        s_live_k[pos] = k;
+        s_live_w[pos] = w;
+      }
+      __syncthreads();
+      for (int b = tid; b < nb; b += BLK) {
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int j = 0; j < n_live; ++j) {
+          float eps[4];
+          normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(s_live_k[j]), ctr, p.gid, p.key_lo, p.key_hi, eps);
+          const float wj = s_live_w[j];
 #pragma unroll
           for (int s = 0; s < SPB; ++s) {
             float du[M];
             scale_noise<M>(Lnu, eps + s * M, du);
 #pragma unroll
-            for (int j = 0; j < M; ++j) v[q * 4 + s * M + j] = w * du[j];
+            for (int q = 0; q < M; ++q) acc[s * M + q] = fmaf(wj, du[q], acc[s * M + q]);
           }
         }
-      }
-      const float wsum = warp_live ? transpose_reduce32(v) : 0.0f;
-      s_red[warp][lane] = wsum;
-      __syncthreads();
-      if (warp == 0) {
-        float t = 0.0f;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) t += s_red[q][lane];
-        const int o = 4 * g + lane;
-        if (o < TM) part_sums[o] = t;
+        for (int q = 0; q < 4; ++q)
+          if (4 * b + q < TM) part_sums[4 * b + q] = acc[q];
       }
-      __syncthreads();
+    } else {
+      const bool warp_live = live_bits != 0u;
+      // regenerate du, weight it, transpose-reduce 32 outputs (8 Philox blocks) at a time
+      for (int g = 0; g < nb; g += 8) {
+        float v[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) v[q] = 0.0f;
+        if (warp_live) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            float eps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (g + q < nb && k != INT_MAX)  // k == INT_MAX: a thread that owns no sample
+              normals4(static_cast<uint32_t>(g + q), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, eps);
+#pragma unroll
+            for (int s = 0; s < SPB; ++s) {
+              float du[M];
+              scale_noise<M>(Lnu, eps + s * M, du);
+#pragma unroll
+              for (int j = 0; j < M; ++j) v[q * 4 + s * M + j] = w * du[j];
+            }
+          }
+        }
+        const float wsum = warp_live ? transpose_reduce32(v) : 0.0f;
+        s_red[warp][lane] = wsum;
+        __syncthreads();
+        if (warp == 0) {
+          float t = 0.0f;
+#pragma unroll
+          for (int q = 0; q < NW; ++q) t += s_red[q][lane];
+          const int o = 4 * g + lane;
+          if (o < TM) part_sums[o] = t;
+        }
+        __syncthreads();
+      }
     }
   }
   __syncthreads();
