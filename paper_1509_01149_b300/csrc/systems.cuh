@@ -41,6 +41,20 @@ struct Env {
 };
 
 // ---------------------------------------------------------------------------
+// sin and cos of an unbounded angle: reduced to [-pi, pi] by the two-constant Cody-Waite
+// scheme (k = nearest integer to a / 2 pi; a - k hi - k lo with hi + lo = 2 pi, hi the nearest
+// float), then both on the special-function unit (about 2^-21 absolute on the reduced range).
+// No slow-path branch, so consecutive steps interleave.
+__device__ __forceinline__ void sincos_reduced(float a, float &s, float &c) {
+  constexpr float two_pi_hi = 6.28318548202514648f;
+  constexpr float two_pi_lo = -1.7484556025237907e-07f;
+  constexpr float inv_two_pi = 0.159154943091895336f;
+  const float kk = rintf(a * inv_two_pi);
+  float red = fmaf(-kk, two_pi_hi, a);
+  red = fmaf(-kk, two_pi_lo, red);
+  __sincosf(red, &s, &c);
+}
+
 struct CartPole {
   static constexpr int N = 4, M = 1;
   struct Aux {};
@@ -49,12 +63,12 @@ struct CartPole {
   __device__ __forceinline__ static void init(const float *, Aux &, const Env &) {}
 
   __device__ __forceinline__ static void step(float x[N], const float v[M], Aux &, const Env &, float dt) {
-    constexpr float Mt = mc + mp;
+    constexpr float inv_Mt = 1.0f / (mc + mp);
     float s, c;
-    sincosf(x[2], &s, &c);
-    const float tmp = (v[0] + mp * l * x[3] * x[3] * s) / Mt;
-    const float th_acc = (g * s - c * tmp) / (l * (4.0f / 3.0f - mp * c * c / Mt));
-    const float x_acc = tmp - mp * l * th_acc * c / Mt;
+    sincos_reduced(x[2], s, c);
+    const float tmp = (v[0] + mp * l * x[3] * x[3] * s) * inv_Mt;
+    const float th_acc = __fdividef(g * s - c * tmp, l * (4.0f / 3.0f - mp * c * c * inv_Mt));
+    const float x_acc = tmp - mp * l * th_acc * c * inv_Mt;
     x[0] += dt * x[1];
     x[1] += dt * x_acc;
     x[2] += dt * x[3];
@@ -89,7 +103,7 @@ struct CartPoleVel {
 
   __device__ __forceinline__ static void step(float x[N], const float v[M], Aux &, const Env &, float dt) {
     float s, c;
-    sincosf(x[2], &s, &c);
+    sincos_reduced(x[2], s, c);
     const float acc = k_vel * (v[0] - x[1]);
     const float th_acc = -(3.0f / (4.0f * l)) * (g * s + acc * c);
     x[0] += dt * x[1];
@@ -99,7 +113,9 @@ struct CartPoleVel {
   }
 
   __device__ __forceinline__ static float cost(const float x[N], const Aux &, const Env &) {
-    const float up = 1.0f + cosf(x[2]);
+    float s, c;
+    sincos_reduced(x[2], s, c);
+    const float up = 1.0f + c;
     return x[0] * x[0] + 500.0f * up * up + x[3] * x[3] + x[1] * x[1];
   }
 
@@ -278,20 +294,8 @@ struct Car {
     const float ad = fabsf(delta);
     return ad < 1.5f || (ad < 3.0f && nf * delta > 0.0f);
   }
-  // The heading is unbounded: it is first reduced to [-pi, pi] by the two-constant
-  // Cody-Waite scheme (k = nearest integer to psi / 2 pi; psi - k hi - k lo with
-  // hi + lo = 2 pi, hi the nearest float), then its sine and cosine run on the SFU
-  // (about 2^-21 absolute on the reduced range).  No slow-path branch, so the pose
-  // updates of consecutive steps interleave.
-  __device__ __forceinline__ static void sincos_heading(float psi, float &s, float &c) {
-    constexpr float two_pi_hi = 6.28318548202514648f;
-    constexpr float two_pi_lo = -1.7484556025237907e-07f;
-    constexpr float inv_two_pi = 0.159154943091895336f;
-    const float kk = rintf(psi * inv_two_pi);
-    float red = fmaf(-kk, two_pi_hi, psi);
-    red = fmaf(-kk, two_pi_lo, red);
-    __sincosf(red, &s, &c);
-  }
+  // The heading is unbounded: sincos_reduced (Cody-Waite reduction, then the SFU).
+  __device__ __forceinline__ static void sincos_heading(float psi, float &s, float &c) { sincos_reduced(psi, s, c); }
   __device__ __forceinline__ static void pose_rates(float psi, float vx, float vy, float &dX, float &dY) {
     float sp, cp;
     sincos_heading(psi, sp, cp);
@@ -521,7 +525,7 @@ struct Quad {
     d[5] = a * (cth * cph) - g;
     const float wp = x[9], wq = x[10], wr = x[11];
     const float ws = wq * sph + wr * cph;
-    const float inv_cth = 1.0f / cth;
+    const float inv_cth = __fdividef(1.0f, cth);
     d[6] = wp + ws * sth * inv_cth;
     d[7] = wq * cph - wr * sph;
     d[8] = ws * inv_cth;
