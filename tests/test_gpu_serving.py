@@ -231,3 +231,48 @@ def test_full_size_serving_tick_on_sampled_outputs(N):
         rel = np.abs(dbg["S"][idx][keep].astype(np.float64) - S_o[keep]) / np.abs(S_o[keep])
         assert rel.size > 0 and rel.max() <= P.S_RTOL, (i, s, K, T, rel.max())
     srv.close()
+
+
+def test_served_spread_weights_match_the_oracle_and_the_ctx_path(N):
+    """Temperatures that spread the weights over many samples per block (more than the 32 live
+    samples whose regeneration a block shares), next to a sharp one (a few live samples per
+    block): after one tick the served u0 and shifted controls are within the U bar of the
+    oracle's iteration and of the single-controller path, and the normaliser on the GPU's own
+    costs is within the weighting's error bound."""
+    from oracle import mppi as om
+    Rcar = np.linalg.inv(np.diag([0.3, 0.35]))
+    picks = [(W.CARTPOLE, 4099, 100, 300.0, None), (W.CAR, 2048, 30, 300.0, Rcar), (W.CAR, 2048, 30, 30.0, Rcar),
+             (W.CAR, 2048, 30, 1.0, None)]
+    srv = make_server(N)
+    slots, cfgs = [], []
+    for i, (s, K, T, lam, R) in enumerate(picks):
+        c = W.config(s, K=K, T=T, lam=lam, **({} if R is None else {"R": R}))
+        cfg = srv.slot_config(s, K, T, c["dt"], c["nu"], c["lam"], c["Sigma"], c["R"], seed=300 + i, gid=300 + i,
+                              env_id=ENV.get(s, -1), u_init=c["u_init"])
+        slot = srv.admit(cfg)
+        assert slot is not None
+        slots.append(slot)
+        cfgs.append(dict(c, seed=300 + i, gid=300 + i))
+    states = [W.config(p[0])["x0"] for p in picks]
+    u0 = srv.tick(slots, states)
+    spread = 0
+    for i, (s, K, T, lam, R) in enumerate(picks):
+        c = cfgs[i]
+        o = P.oracle_iteration(c)
+        ess = 1.0 / np.sum(o.w ** 2)
+        spread += ess > 64
+        m = W.CONTROL_DIM[s]
+        assert within(u0[i, :m], o.u0, c), (i, ess)
+        assert within(srv.get_controls(slots[i]), om.shift(o.U, c["u_init"]), c), (i, ess)
+        dbg = srv.get_debug(slots[i], K)
+        r = P.reduction_errors(dbg["S"], P.noise_oracle(c).astype(np.float32), float(np.float32(lam)), dbg["eta"],
+                               np.zeros((T, m)), dbg["kstar"])
+        assert r["eta_err"] <= r["eta_bound"], (i, r["eta_err"], r["eta_bound"])
+        ctrl = P.make_controller(c)
+        cu0 = ctrl.step(np.asarray(c["x0"], dtype=np.float32))
+        ctrl.shift()
+        assert within(u0[i, :m], cu0, c), (i, ess)
+        assert within(srv.get_controls(slots[i]), ctrl.get_controls(), c), (i, ess)
+        ctrl.close()
+    assert spread >= 2   # the shared-regeneration limit is really exceeded
+    srv.close()
