@@ -90,10 +90,18 @@ __global__ void k_gather(const __nv_bfloat16 *__restrict__ Xf, const float *__re
   const Words4 w = philox4x32_10(static_cast<uint32_t>(b), step, 0x4d4c5000u, 0u, key_lo, key_hi);
   const uint64_t r = (static_cast<uint64_t>(w.x) << 32) | w.y;
   const size_t i = static_cast<size_t>(r % static_cast<uint64_t>(n));
+  static_assert(kIn == 16 && kOut == 16, "one 32-byte feature row, one 64-byte target row");
+  const uint4 *xs = reinterpret_cast<const uint4 *>(Xf + i * kIn);
+  uint4 *xd = reinterpret_cast<uint4 *>(Xb + static_cast<size_t>(b) * kIn);
+  const uint4 x0 = xs[0], x1 = xs[1];
+  float t[kOut];
 #pragma unroll
-  for (int j = 0; j < kIn; ++j) Xb[static_cast<size_t>(b) * kIn + j] = Xf[i * kIn + j];
+  for (int j = 0; j < kOut; ++j) t[j] = j < kState ? D[i * kState + j] / out_scale[j] : 0.0f;
+  xd[0] = x0;
+  xd[1] = x1;
+  float4 *td = reinterpret_cast<float4 *>(Tb + static_cast<size_t>(b) * kOut);
 #pragma unroll
-  for (int j = 0; j < kOut; ++j) Tb[static_cast<size_t>(b) * kOut + j] = j < kState ? D[i * kState + j] / out_scale[j] : 0.0f;
+  for (int j = 0; j < kOut / 4; ++j) td[j] = make_float4(t[4 * j], t[4 * j + 1], t[4 * j + 2], t[4 * j + 3]);
 }
 
 // dY = 2 (Y - T) / B on the first 7 outputs; loss accumulated in FP64
@@ -121,9 +129,20 @@ template <class T>
 __global__ void k_colsum(const T *__restrict__ A, int rows, int cols, float *__restrict__ out) {
   __shared__ float s[8][33];
   const int c = blockIdx.x * 32 + (threadIdx.x & 31), ty = threadIdx.x >> 5;
+  const int stride = 8 * gridDim.y;
   float a = 0.0f;
-  if (c < cols)
-    for (int r = ty + blockIdx.y * 8; r < rows; r += 8 * gridDim.y) a += static_cast<float>(A[static_cast<size_t>(r) * cols + c]);
+  if (c < cols) {
+    // rows r = ty + 8 y, r + stride, ... added in that order, eight loads in flight at a time
+    int r = ty + blockIdx.y * 8;
+    for (; r + 7 * stride < rows; r += 8 * stride) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = static_cast<float>(A[static_cast<size_t>(r + u * stride) * cols + c]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a += v[u];
+    }
+    for (; r < rows; r += stride) a += static_cast<float>(A[static_cast<size_t>(r) * cols + c]);
+  }
   s[ty][threadIdx.x & 31] = a;
   __syncthreads();
   if (ty == 0 && c < cols) {
@@ -139,7 +158,15 @@ __global__ void k_sum_splits(const float *__restrict__ part, int nsplit, size_t 
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < count;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
     float a = 0.0f;
-    for (int z = 0; z < nsplit; ++z) a += part[static_cast<size_t>(z) * count + i];
+    int z = 0;
+    for (; z + 8 <= nsplit; z += 8) {  // eight loads in flight, added in z order
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = part[static_cast<size_t>(z + u) * count + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a += v[u];
+    }
+    for (; z < nsplit; ++z) a += part[static_cast<size_t>(z) * count + i];
     out[i] = a;
   }
 }
@@ -407,7 +434,7 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW1"));
   MLP_TRY(split_sum(static_cast<size_t>(kHid) * kIn, q->g + kOffW1, "gW1 sum"));
   // bias gradients: column sums, 16 row partials each, summed in a fixed order
-  constexpr int kRowParts = 16;
+  constexpr int kRowParts = 64;
   mlp::k_colsum<float><<<dim3(1, kRowParts), 256, 0, q->stream>>>(q->dYf, B, kOut, q->gsplit);
   mlp::k_sum_splits<<<1, 256, 0, q->stream>>>(q->gsplit, kRowParts, kOut, q->g + kOffB3);
   mlp::k_colsum<__nv_bfloat16><<<dim3(kHid / 32, kRowParts), 256, 0, q->stream>>>(q->dZ2, B, kHid, q->gsplit);

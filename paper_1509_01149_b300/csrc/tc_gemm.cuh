@@ -39,9 +39,9 @@ struct GemmArgs {
   int debug_skip_mma;           // check hook only: issue no MMA (so the waits run out, nothing in flight)
 };
 
-// Dynamic shared memory of the GEMM CTA.  Sized so the tiles (48 KB) sit well inside the
-// allocation: one CTA per SM, which also keeps the 512-column TMEM allocation uncontended.
-constexpr size_t kGemmSmemBytes = 200 * 1024;
+// Largest dynamic shared memory of a GEMM CTA: two stages of the widest (BN = 256) tile.  A
+// launch requests two stages of its own tile width.
+constexpr size_t kGemmSmemBytes = 96 * 1024;
 
 cudaError_t launch_gemm_bf16(const GemmArgs &g, cudaStream_t s);
 

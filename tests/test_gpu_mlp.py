@@ -38,6 +38,28 @@ def test_tc_gemm_matches_torch(env):
         # FP32 accumulation in a different order: error ~ sqrt(K) * 2^-24 * sum_k |a||b|
         bound = 8.0 * np.sqrt(K) * 2.0 ** -24 * (A.float().abs() @ B.float().abs()) + 1e-6
         assert bool(((Cm - ref).abs() <= bound).all())
+    # the other operand layouts of the gather: A stored transposed (eight rows contiguous at one
+    # k), B with K contiguous (the asynchronous-copy path for B), and rows with an odd stride
+    # (element by element), each with ragged M, N and K
+    for M, Nn, K, BN in ((256, 48, 100, 48), (136, 256, 72, 256), (129, 32, 40, 32)):
+        A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+        B = torch.randn(K, Nn, generator=g).to(torch.bfloat16)
+        ref = A.float() @ B.float()
+        bound = 8.0 * np.sqrt(K) * 2.0 ** -24 * (A.float().abs() @ B.float().abs()) + 1e-6
+        At = A.t().contiguous().cuda()                          # A(m, k) = At[k * M + m]
+        Bt = B.t().contiguous().cuda()                          # B(k, n) = Bt[n * K + k]
+        Ao = torch.zeros(M, K + 3, dtype=torch.bfloat16)        # rows of K + 3 (an odd stride)
+        Ao[:, :K] = A
+        Ao = Ao.cuda()
+        cases = [(At, 1, M, Bt, 1, K), (Ao, K + 3, 1, Bt, 1, K)]
+        if M % 8 == 0:
+            cases.append((At, 1, M, B.cuda(), Nn, 1))
+        for Ad, sam, sak, Bd, sbk, sbn in cases:
+            Cm = torch.zeros(M, Nn, device="cuda")
+            rc = N.lib.mppi_debug_gemm_bf16(M, Nn, K, C.c_void_p(Ad.data_ptr()), sam, sak, C.c_void_p(Bd.data_ptr()),
+                                            sbk, sbn, C.c_void_p(Cm.data_ptr()), Nn, BN)
+            assert rc == 0
+            assert bool(((Cm.cpu() - ref).abs() <= bound).all()), (M, Nn, K, sam, sak, sbk, sbn)
 
 
 def test_gradients_match_the_oracle(env):
