@@ -184,6 +184,15 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
   }
 }
 
+// dst [cols][rows] = src [rows][cols] transposed, in BF16 (the weights as the backward data
+// GEMMs read them: their K dimension contiguous)
+__global__ void k_to_bf16_t(const float *__restrict__ src, __nv_bfloat16 *__restrict__ dst, int rows, int cols) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * cols; i += gridDim.x * blockDim.x) {
+    const int r = i / cols, c = i - r * cols;
+    dst[static_cast<size_t>(c) * rows + r] = __float2bfloat16(src[i]);
+  }
+}
+
 __global__ void k_to_bf16(const float *__restrict__ src, __nv_bfloat16 *__restrict__ dst, size_t n) {
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<size_t>(gridDim.x) * blockDim.x)
@@ -267,6 +276,7 @@ struct mppi_mlp {
   cudaStream_t stream = nullptr;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, grads, Adam moments
   __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr;      // BF16 copies for the GEMMs
+  __nv_bfloat16 *w2t = nullptr, *w3t = nullptr;                   // and W2, W3 transposed (backward)
   float *out_scale = nullptr;                                    // [16] (first 7 used)
   float h_out_scale[kOut] = {0};
   int adam_t = 0;
@@ -357,17 +367,19 @@ int refresh_bf16(mppi_mlp *q) {
   k_to_bf16<<<64, 256, 0, q->stream>>>(q->p + kOffW1, q->w1, static_cast<size_t>(kHid) * kIn);
   k_to_bf16<<<256, 256, 0, q->stream>>>(q->p + kOffW2, q->w2, static_cast<size_t>(kHid) * kHid);
   k_to_bf16<<<64, 256, 0, q->stream>>>(q->p + kOffW3, q->w3, static_cast<size_t>(kOut) * kHid);
+  k_to_bf16_t<<<256, 256, 0, q->stream>>>(q->p + kOffW2, q->w2t, kHid, kHid);
+  k_to_bf16_t<<<16, 256, 0, q->stream>>>(q->p + kOffW3, q->w3t, kOut, kHid);
   return q->cuda(cudaGetLastError(), "bf16 copy");
 }
 
 // forward on Xb [B][16] into H1, H2 (bf16) and Y (f32)
 int forward(mppi_mlp *q, const __nv_bfloat16 *X, int B) {
-  GemmArgs g = gemm(B, kHid, kIn, 128, X, kIn, 1, q->w1, 1, kIn, kEpiBiasTanh, q->d_err);
+  GemmArgs g = gemm(B, kHid, kIn, 64, X, kIn, 1, q->w1, 1, kIn, kEpiBiasTanh, q->d_err);
   g.bias = q->p + kOffB1;
   g.Cb = q->H1;
   g.ldcb = kHid;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm h1"));
-  g = gemm(B, kHid, kHid, 128, q->H1, kHid, 1, q->w2, 1, kHid, kEpiBiasTanh, q->d_err);
+  g = gemm(B, kHid, kHid, 64, q->H1, kHid, 1, q->w2, 1, kHid, kEpiBiasTanh, q->d_err);
   g.bias = q->p + kOffB2;
   g.Cb = q->H2;
   g.ldcb = kHid;
@@ -404,7 +416,7 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW3"));
   MLP_TRY(split_sum(static_cast<size_t>(kOut) * kHid, q->g + kOffW3, "gW3 sum"));
   // dZ2 = (dY W3) * (1 - H2^2)
-  g = gemm(B, kHid, kOut, 128, q->dYb, kOut, 1, q->w3, kHid, 1, kEpiTanhGrad, q->d_err);
+  g = gemm(B, kHid, kOut, 64, q->dYb, kOut, 1, q->w3t, 1, kOut, kEpiTanhGrad, q->d_err);
   g.H = q->H2;
   g.ldh = kHid;
   g.Cb = q->dZ2;
@@ -419,7 +431,7 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW2"));
   MLP_TRY(split_sum(static_cast<size_t>(kHid) * kHid, q->g + kOffW2, "gW2 sum"));
   // dZ1 = (dZ2 W2) * (1 - H1^2)
-  g = gemm(B, kHid, kHid, 128, q->dZ2, kHid, 1, q->w2, kHid, 1, kEpiTanhGrad, q->d_err);
+  g = gemm(B, kHid, kHid, 64, q->dZ2, kHid, 1, q->w2t, 1, kHid, kEpiTanhGrad, q->d_err);
   g.H = q->H1;
   g.ldh = kHid;
   g.Cb = q->dZ1;
@@ -471,6 +483,8 @@ int mppi_mlp_create(uint64_t seed, mppi_mlp **out) {
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->w1, sizeof(__nv_bfloat16) * kHid * kIn), "w1");
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->w2, sizeof(__nv_bfloat16) * kHid * kHid), "w2");
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->w3, sizeof(__nv_bfloat16) * kOut * kHid), "w3");
+  if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->w2t, sizeof(__nv_bfloat16) * kHid * kHid), "w2t");
+  if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->w3t, sizeof(__nv_bfloat16) * kOut * kHid), "w3t");
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->out_scale, sizeof(float) * kOut), "scale");
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->loss, sizeof(double) * 16), "loss");
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->d_err, sizeof(int)), "err");
@@ -503,7 +517,7 @@ int mppi_mlp_create(uint64_t seed, mppi_mlp **out) {
 int mppi_mlp_destroy(mppi_mlp *q) {
   if (!q) return MPPI_OK;
   if (q->stream) cudaStreamSynchronize(q->stream);
-  void *bufs[] = {q->p, q->g, q->m, q->v, q->w1, q->w2, q->w3, q->out_scale, q->Xf, q->D, q->Xb, q->H1, q->H2,
+  void *bufs[] = {q->p, q->g, q->m, q->v, q->w1, q->w2, q->w3, q->w2t, q->w3t, q->out_scale, q->Xf, q->D, q->Xb, q->H1, q->H2,
                   q->dYb, q->dZ2, q->dZ1, q->Tb, q->Y, q->dYf, q->loss, q->d_err, q->gsplit, q->moments};
   for (void *b : bufs)
     if (b) cudaFree(b);
