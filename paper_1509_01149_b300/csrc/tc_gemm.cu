@@ -65,11 +65,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
 
 // Rows [r0, r0 + Rn) x K slab [k0, k0 + klen) of X(r, k) = X[r*srow + k*sk] (rows >= nrows and
 // k >= klen read as 0) into the K-major core-matrix tile `dst` with Rn rows and kpad columns.
+// KIND: kGatherK (8 elements contiguous along K), kGatherRows (8 rows contiguous at one k), or
+// kGatherAny (chosen per call from the strides and alignment, element-wise if neither).  The
+// launcher picks the kind from the same conditions, so that the common kernels carry only the
+// code of their own gathers (a smaller instruction footprint for the four warps of a CTA).
+constexpr int kGatherK = 0, kGatherRows = 1, kGatherAny = 2;
+
+template <int KIND>
 __device__ __forceinline__ void gather_tile(const __nv_bfloat16 *__restrict__ X, int64_t srow, int64_t sk, int r0,
                                             int nrows, int Rn, int k0, int klen, int kpad, unsigned char *dst,
                                             int tid) {
   const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  if (sk == 1 && (srow & 7) == 0 && aligned16(X)) {
+  if (KIND == kGatherK || (KIND == kGatherAny && sk == 1 && (srow & 7) == 0 && aligned16(X))) {
     // eight consecutive k of one row: one 16-byte asynchronous copy per core-matrix row (zeros
     // past the last row or past klen); a chunk that klen cuts is gathered element-wise
     const int cpr = kpad >> 3;
@@ -89,7 +96,9 @@ __device__ __forceinline__ void gather_tile(const __nv_bfloat16 *__restrict__ X,
         *reinterpret_cast<uint4 *>(d) = *reinterpret_cast<const uint4 *>(t);
       }
     }
-  } else if (srow == 1 && (sk & 7) == 0 && (r0 & 7) == 0 && aligned16(X) && (Rn >> 3) * kpad <= kMaxRowLoads * kThreads) {
+  } else if (KIND == kGatherRows ||
+             (KIND == kGatherAny && srow == 1 && (sk & 7) == 0 && (r0 & 7) == 0 && aligned16(X) &&
+              (Rn >> 3) * kpad <= kMaxRowLoads * kThreads)) {
     // eight consecutive rows at one k: every 16-byte load of the thread is issued first, then
     // each feeds eight core-matrix rows
     const int groups = Rn >> 3, total = groups * kpad;
@@ -124,7 +133,7 @@ __device__ __forceinline__ void gather_tile(const __nv_bfloat16 *__restrict__ X,
         for (int i = 0; i < 8; ++i) *reinterpret_cast<__nv_bfloat16 *>(dst + tc::kmajor_offset(r + i, c, Rn)) = e[i];
       }
     }
-  } else {
+  } else if (KIND == kGatherAny) {
     for (int idx = tid; idx < Rn * kpad; idx += kThreads) {
       int r, c;
       if (sk == 1) {
@@ -143,6 +152,7 @@ __device__ __forceinline__ void gather_tile(const __nv_bfloat16 *__restrict__ X,
 }
 }  // namespace
 
+template <int GA, int GB>
 __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint64_t bar[2];
@@ -174,8 +184,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
   auto gather = [&](int s) {
     const int k0 = kbeg + s * kKT, klen = min(kKT, kend - k0), kpad = (klen + 15) & ~15;
     unsigned char *sA = smem + (s & 1) * sbytes, *sB = sA + kStageA;
-    gather_tile(g.A, g.sam, g.sak, m0, g.M, kBM, k0, klen, kpad, sA, tid);
-    gather_tile(g.B, g.sbn, g.sbk, n0, g.N, BN, k0, klen, kpad, sB, tid);
+    gather_tile<GA>(g.A, g.sam, g.sak, m0, g.M, kBM, k0, klen, kpad, sA, tid);
+    gather_tile<GB>(g.B, g.sbn, g.sbk, n0, g.N, BN, k0, klen, kpad, sB, tid);
     cp_async_wait_all();  // this thread's asynchronous copies have landed
   };
   int last = -1;  // the last slab whose MMAs were committed
@@ -324,20 +334,36 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
 
 size_t gemm_smem_bytes() { return kGemmSmemBytes; }
 
+// gather kind of an operand X(r, k) = X[r*srow + k*sk] (the device conditions of gather_tile)
+static int gather_kind(const void *X, int64_t srow, int64_t sk) {
+  const bool a16 = (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
+  if (sk == 1 && (srow & 7) == 0 && a16) return kGatherK;
+  if (srow == 1 && (sk & 7) == 0 && a16) return kGatherRows;
+  return kGatherAny;
+}
+
 cudaError_t launch_gemm_bf16(const GemmArgs &g, cudaStream_t s) {
+  using Kern = void (*)(const GemmArgs);
+  static const Kern kernels[5] = {k_gemm_bf16<kGatherK, kGatherK>, k_gemm_bf16<kGatherK, kGatherRows>,
+                                  k_gemm_bf16<kGatherRows, kGatherK>, k_gemm_bf16<kGatherRows, kGatherRows>,
+                                  k_gemm_bf16<kGatherAny, kGatherAny>};
   static bool attr_set = false;
   if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(kGemmSmemBytes));
-    if (e != cudaSuccess) return e;
+    for (Kern k : kernels) {
+      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(kGemmSmemBytes));
+      if (e != cudaSuccess) return e;
+    }
     attr_set = true;
   }
   if (g.BN < 16 || g.BN > 256 || (g.BN & 15) != 0) return cudaErrorInvalidValue;
   const int nsplit = g.ksplit > 1 ? g.ksplit : 1;
   if (nsplit > 1 && g.mode != kEpiAtomicF32 && !(g.mode == kEpiStoreF32 && g.split_stride > 0))
     return cudaErrorInvalidValue;
+  const int ga = gather_kind(g.A, g.sam, g.sak), gb = gather_kind(g.B, g.sbn, g.sbk);
+  const Kern k = (ga == kGatherAny || gb == kGatherAny) ? kernels[4] : kernels[2 * ga + gb];
   const dim3 grid((g.M + kBM - 1) / kBM, (g.N + g.BN - 1) / g.BN, nsplit);
-  k_gemm_bf16<<<grid, kThreads, 2 * stage_bytes(g.BN), s>>>(g);
+  k<<<grid, kThreads, 2 * stage_bytes(g.BN), s>>>(g);
   return cudaGetLastError();
 }
 
