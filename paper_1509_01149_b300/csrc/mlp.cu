@@ -9,8 +9,12 @@
 //   loss    L = (1/B) sum_b sum_{i<7} (Y - Tb)^2, dY = 2 (Y - Tb) / B
 //   backward gW3 = dY^T H2, dZ2 = (dY W3) * (1 - H2^2), gW2 = dZ2^T H1,
 //            dZ1 = (dZ2 W2) * (1 - H1^2), gW1 = dZ1^T Xb  (weight gradients split over
-//            the batch across CTAs, accumulated with atomics), bias gradients = column sums
-//   Adam    on FP32 master weights, BF16 copies refreshed for the next step.
+//            the batch across CTAs, each split's partial stored to its own slice and the
+//            slices summed in a fixed order, so training is bit-reproducible; their operands
+//            are transposed copies [features][B] written by the producing GEMM epilogues, so
+//            the batch, their K dimension, is contiguous), bias gradients = column sums
+//   Adam    on FP32 master weights, BF16 copies (and W2, W3 transposed for the backward
+//            data products) refreshed for the next step.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -104,24 +108,56 @@ __global__ void k_gather(const __nv_bfloat16 *__restrict__ Xf, const float *__re
   for (int j = 0; j < kOut / 4; ++j) td[j] = make_float4(t[4 * j], t[4 * j + 1], t[4 * j + 2], t[4 * j + 3]);
 }
 
-// dY = 2 (Y - T) / B on the first 7 outputs; loss accumulated in FP64
+// dY = 2 (Y - T) / B on the first 7 outputs, one thread per batch row (dYf and dYb row-major,
+// dYt [16][B] transposed for the weight-gradient GEMM); the loss is summed in FP32 over each
+// row and warp and added across warps in FP64
 __global__ void k_loss_grad(const float *__restrict__ Y, const float *__restrict__ T, int B, float *__restrict__ dYf,
-                            __nv_bfloat16 *__restrict__ dYb, double *__restrict__ loss) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  double l = 0.0;
-  if (idx < B * kOut) {
-    const int j = idx % kOut;
-    float g = 0.0f;
-    if (j < kState) {
-      const float r = Y[idx] - T[idx];
-      l = static_cast<double>(r) * r;
-      g = 2.0f * r / static_cast<float>(B);
+                            __nv_bfloat16 *__restrict__ dYb, __nv_bfloat16 *__restrict__ dYt,
+                            double *__restrict__ loss) {
+  static_assert(kOut == 16, "one 64-byte output row");
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.0f;
+  if (b < B) {
+    const float4 *y4 = reinterpret_cast<const float4 *>(Y + static_cast<size_t>(b) * kOut);
+    const float4 *t4 = reinterpret_cast<const float4 *>(T + static_cast<size_t>(b) * kOut);
+    float g[kOut];
+#pragma unroll
+    for (int q = 0; q < kOut / 4; ++q) {
+      const float4 y = y4[q], t = t4[q];
+      const float r[4] = {y.x - t.x, y.y - t.y, y.z - t.z, y.w - t.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int jj = 4 * q + e;
+        g[jj] = jj < kState ? 2.0f * r[e] / static_cast<float>(B) : 0.0f;
+        if (jj < kState) l = fmaf(r[e], r[e], l);
+      }
     }
-    dYf[idx] = g;
-    dYb[idx] = __float2bfloat16(g);
+    float4 *gf = reinterpret_cast<float4 *>(dYf + static_cast<size_t>(b) * kOut);
+#pragma unroll
+    for (int q = 0; q < kOut / 4; ++q) gf[q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+    __nv_bfloat16 gb[kOut];
+#pragma unroll
+    for (int jj = 0; jj < kOut; ++jj) gb[jj] = __float2bfloat16(g[jj]);
+    uint4 *db = reinterpret_cast<uint4 *>(dYb + static_cast<size_t>(b) * kOut);
+    db[0] = *reinterpret_cast<const uint4 *>(gb);
+    db[1] = *reinterpret_cast<const uint4 *>(gb + 8);
+#pragma unroll
+    for (int jj = 0; jj < kOut; ++jj) dYt[static_cast<size_t>(jj) * B + b] = gb[jj];
   }
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l / B);
+  if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss, static_cast<double>(l) / B);
+}
+
+// Xt [16][B] = X [B][16] transposed (the batch-contiguous input of the first weight gradient)
+__global__ void k_transpose16(const __nv_bfloat16 *__restrict__ X, int B, __nv_bfloat16 *__restrict__ Xt) {
+  static_assert(kIn == 16, "one 32-byte feature row");
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const uint4 *xs = reinterpret_cast<const uint4 *>(X + static_cast<size_t>(b) * kIn);
+  uint4 v[2] = {xs[0], xs[1]};
+  const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(v);
+#pragma unroll
+  for (int jj = 0; jj < kIn; ++jj) Xt[static_cast<size_t>(jj) * B + b] = e[jj];
 }
 
 // column sums of a [rows][cols] matrix (f32 or bf16) into out[cols]
@@ -287,6 +323,9 @@ struct mppi_mlp {
   // batch workspace
   int cap = 0;
   __nv_bfloat16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *dYb = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+  // the same activations and errors transposed ([features][B]): the batch is the K dimension of
+  // the weight-gradient GEMMs, which then read it contiguously
+  __nv_bfloat16 *Xt = nullptr, *H1t = nullptr, *H2t = nullptr, *dYt = nullptr, *dZ2t = nullptr, *dZ1t = nullptr;
   float *Tb = nullptr, *Y = nullptr, *dYf = nullptr;
   double *loss = nullptr;
   int *d_err = nullptr;
@@ -319,6 +358,8 @@ namespace {
 
 int ensure_batch(mppi_mlp *q, int B) {
   if (B <= q->cap) return MPPI_OK;
+  for (__nv_bfloat16 *t : {q->Xt, q->H1t, q->H2t, q->dYt, q->dZ2t, q->dZ1t}) cudaFree(t);
+  q->Xt = q->H1t = q->H2t = q->dYt = q->dZ2t = q->dZ1t = nullptr;
   cudaFree(q->Xb);
   cudaFree(q->H1);
   cudaFree(q->H2);
@@ -339,6 +380,12 @@ int ensure_batch(mppi_mlp *q, int B) {
   MLP_TRY(q->cuda(cudaMalloc(&q->Tb, b * kOut * 4), "batch"));
   MLP_TRY(q->cuda(cudaMalloc(&q->Y, b * kOut * 4), "batch"));
   MLP_TRY(q->cuda(cudaMalloc(&q->dYf, b * kOut * 4), "batch"));
+  MLP_TRY(q->cuda(cudaMalloc(&q->Xt, b * kIn * 2), "batch"));
+  MLP_TRY(q->cuda(cudaMalloc(&q->H1t, b * kHid * 2), "batch"));
+  MLP_TRY(q->cuda(cudaMalloc(&q->H2t, b * kHid * 2), "batch"));
+  MLP_TRY(q->cuda(cudaMalloc(&q->dYt, b * kOut * 2), "batch"));
+  MLP_TRY(q->cuda(cudaMalloc(&q->dZ2t, b * kHid * 2), "batch"));
+  MLP_TRY(q->cuda(cudaMalloc(&q->dZ1t, b * kHid * 2), "batch"));
   q->cap = B;
   return MPPI_OK;
 }
@@ -372,17 +419,22 @@ int refresh_bf16(mppi_mlp *q) {
   return q->cuda(cudaGetLastError(), "bf16 copy");
 }
 
-// forward on Xb [B][16] into H1, H2 (bf16) and Y (f32)
-int forward(mppi_mlp *q, const __nv_bfloat16 *X, int B) {
+// forward on Xb [B][16] into H1, H2 (bf16) and Y (f32); with `transposed` (training) also
+// H1t, H2t for the weight gradients
+int forward(mppi_mlp *q, const __nv_bfloat16 *X, int B, bool transposed) {
   GemmArgs g = gemm(B, kHid, kIn, 64, X, kIn, 1, q->w1, 1, kIn, kEpiBiasTanh, q->d_err);
   g.bias = q->p + kOffB1;
   g.Cb = q->H1;
   g.ldcb = kHid;
+  g.Ct = transposed ? q->H1t : nullptr;
+  g.ldct = B;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm h1"));
   g = gemm(B, kHid, kHid, 64, q->H1, kHid, 1, q->w2, 1, kHid, kEpiBiasTanh, q->d_err);
   g.bias = q->p + kOffB2;
   g.Cb = q->H2;
   g.ldcb = kHid;
+  g.Ct = transposed ? q->H2t : nullptr;
+  g.ldct = B;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm h2"));
   g = gemm(B, kOut, kHid, 16, q->H2, kHid, 1, q->w3, 1, kHid, kEpiBiasF32, q->d_err);
   g.bias = q->p + kOffB3;
@@ -395,7 +447,8 @@ int forward(mppi_mlp *q, const __nv_bfloat16 *X, int B) {
 int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   MLP_TRY(q->cuda(cudaMemsetAsync(q->loss, 0, sizeof(double), q->stream), "loss zero"));
   const int nthr = 256;
-  mlp::k_loss_grad<<<(B * kOut + nthr - 1) / nthr, nthr, 0, q->stream>>>(q->Y, T, B, q->dYf, q->dYb, q->loss);
+  mlp::k_loss_grad<<<(B + nthr - 1) / nthr, nthr, 0, q->stream>>>(q->Y, T, B, q->dYf, q->dYb, q->dYt, q->loss);
+  mlp::k_transpose16<<<(B + nthr - 1) / nthr, nthr, 0, q->stream>>>(X, B, q->Xt);
   MLP_TRY(q->cuda(cudaGetLastError(), "loss"));
   // Weight gradients are sums over the batch: split-K GEMMs, each split storing its partial
   // product to its own slice of gsplit, then a fixed-order sum of the slices (no atomics: the
@@ -407,7 +460,7 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
     return q->cuda(cudaGetLastError(), what);
   };
   // gW3 (stored [16][256]): C(m = hidden j, n = output i) = sum_b H2[b][j] dY[b][i]
-  GemmArgs g = gemm(kHid, kOut, B, 16, q->H2, 1, kHid, q->dYb, kOut, 1, kEpiStoreF32, q->d_err);
+  GemmArgs g = gemm(kHid, kOut, B, 16, q->H2t, B, 1, q->dYt, 1, B, kEpiStoreF32, q->d_err);
   g.Cf = q->gsplit;
   g.ldc = 1;
   g.ldcn = kHid;
@@ -421,9 +474,11 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   g.ldh = kHid;
   g.Cb = q->dZ2;
   g.ldcb = kHid;
+  g.Ct = q->dZ2t;
+  g.ldct = B;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm dZ2"));
   // gW2 [256][256] = dZ2^T H1
-  g = gemm(kHid, kHid, B, 128, q->dZ2, 1, kHid, q->H1, kHid, 1, kEpiStoreF32, q->d_err);
+  g = gemm(kHid, kHid, B, 128, q->dZ2t, B, 1, q->H1t, 1, B, kEpiStoreF32, q->d_err);
   g.Cf = q->gsplit;
   g.ldc = kHid;
   g.ksplit = split;
@@ -436,9 +491,11 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   g.ldh = kHid;
   g.Cb = q->dZ1;
   g.ldcb = kHid;
+  g.Ct = q->dZ1t;
+  g.ldct = B;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm dZ1"));
   // gW1 [256][16] = dZ1^T X
-  g = gemm(kHid, kIn, B, 16, q->dZ1, 1, kHid, X, kIn, 1, kEpiStoreF32, q->d_err);
+  g = gemm(kHid, kIn, B, 16, q->dZ1t, B, 1, q->Xt, 1, B, kEpiStoreF32, q->d_err);
   g.Cf = q->gsplit;
   g.ldc = kIn;
   g.ksplit = split;
@@ -518,7 +575,8 @@ int mppi_mlp_destroy(mppi_mlp *q) {
   if (!q) return MPPI_OK;
   if (q->stream) cudaStreamSynchronize(q->stream);
   void *bufs[] = {q->p, q->g, q->m, q->v, q->w1, q->w2, q->w3, q->w2t, q->w3t, q->out_scale, q->Xf, q->D, q->Xb, q->H1, q->H2,
-                  q->dYb, q->dZ2, q->dZ1, q->Tb, q->Y, q->dYf, q->loss, q->d_err, q->gsplit, q->moments};
+                  q->dYb, q->dZ2, q->dZ1, q->Tb, q->Y, q->dYf, q->loss, q->d_err, q->gsplit, q->moments,
+                  q->Xt, q->H1t, q->H2t, q->dYt, q->dZ2t, q->dZ1t};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (q->stream) cudaStreamDestroy(q->stream);
@@ -599,7 +657,7 @@ int mppi_mlp_train(mppi_mlp *q, int steps, int batch, float lr, uint64_t seed, f
                                                              static_cast<uint32_t>(seed >> 32), static_cast<uint32_t>(s),
                                                              q->Xb, q->Tb);
     MLP_TRY(q->cuda(cudaGetLastError(), "gather"));
-    MLP_TRY(forward(q, q->Xb, batch));
+    MLP_TRY(forward(q, q->Xb, batch, true));
     MLP_TRY(backward(q, q->Xb, q->Tb, batch));
     q->adam_t += 1;
     const float c1 = 1.0f - std::pow(b1, static_cast<float>(q->adam_t));
@@ -621,7 +679,7 @@ int mppi_mlp_grad(mppi_mlp *q, const void *d_X, const float *d_T, int B, float *
   if (!q || !d_X || !d_T || B < 1 || !h_grads) return MPPI_EINVAL;
   MLP_TRY(ensure_batch(q, B));
   const __nv_bfloat16 *X = static_cast<const __nv_bfloat16 *>(d_X);
-  MLP_TRY(forward(q, X, B));
+  MLP_TRY(forward(q, X, B, true));
   MLP_TRY(backward(q, X, d_T, B));
   MLP_TRY(q->cuda(cudaMemcpyAsync(h_grads, q->g, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, q->stream), "g"));
   double l = 0.0;
@@ -637,7 +695,7 @@ int mppi_mlp_predict(mppi_mlp *q, const float *d_states, const float *d_controls
   MLP_TRY(ensure_batch(q, ((n + 127) / 128) * 128));
   mlp::k_features<<<(n + 255) / 256, 256, 0, q->stream>>>(d_states, d_controls, n, q->Xb);
   MLP_TRY(q->cuda(cudaGetLastError(), "features"));
-  MLP_TRY(forward(q, q->Xb, n));
+  MLP_TRY(forward(q, q->Xb, n, false));
   mlp::k_apply<<<(n * kState + 255) / 256, 256, 0, q->stream>>>(d_states, q->Y, q->out_scale, n, d_next);
   MLP_TRY(q->cuda(cudaGetLastError(), "apply"));
   return check_err(q);

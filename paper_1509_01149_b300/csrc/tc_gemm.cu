@@ -283,6 +283,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
 #pragma unroll
           for (int j = 0; j < 8; ++j) ob[j] = __float2bfloat16(o[j]);
           *reinterpret_cast<uint4 *>(g.Cb + static_cast<int64_t>(m) * g.ldcb + nb) = *reinterpret_cast<const uint4 *>(ob);
+          if (g.Ct) {  // the warp's 32 rows of one column are 64 contiguous bytes
+#pragma unroll
+            for (int j = 0; j < 8; ++j) g.Ct[static_cast<int64_t>(nb + j) * g.ldct + m] = ob[j];
+          }
         } else if (m < g.M && g.mode == kEpiStoreF32 && csn == 1 && nb + 8 <= g.N && (g.ldc & 3) == 0 &&
                    aligned16(Cf)) {
           // FP32 outputs of 8 whole contiguous columns: two 16-byte stores per row
@@ -308,6 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
               case kEpiBiasTanh: {
                 const float h = tc::tanh_approx(a + g.bias[n]);
                 g.Cb[static_cast<int64_t>(m) * g.ldcb + n] = __float2bfloat16(h);
+                if (g.Ct) g.Ct[static_cast<int64_t>(n) * g.ldct + m] = __float2bfloat16(h);
                 if (Cf) Cf[static_cast<int64_t>(m) * g.ldc + n * csn] = h;
                 break;
               }
@@ -317,6 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_bf16(const GemmArgs g) {
               case kEpiTanhGrad: {
                 const float h = __bfloat162float(g.H[static_cast<int64_t>(m) * g.ldh + n]);
                 g.Cb[static_cast<int64_t>(m) * g.ldcb + n] = __float2bfloat16(a * (1.0f - h * h));
+                if (g.Ct) g.Ct[static_cast<int64_t>(n) * g.ldct + m] = __float2bfloat16(a * (1.0f - h * h));
                 break;
               }
               default:

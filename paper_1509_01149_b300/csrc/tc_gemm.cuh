@@ -28,6 +28,8 @@ struct GemmArgs {
   int64_t ldcn;                 // column stride of Cf (1 = row-major; 0 is read as 1)
   __nv_bfloat16 *Cb;
   int64_t ldcb;
+  __nv_bfloat16 *Ct;            // optional transposed copy of the BF16 output: Ct[n*ldct + m]
+  int64_t ldct;                 // (the batch-contiguous operand of a later weight-gradient GEMM)
   const float *bias;
   const __nv_bfloat16 *H;
   int64_t ldh;
