@@ -160,11 +160,17 @@ __global__ void k_transpose16(const __nv_bfloat16 *__restrict__ X, int B, __nv_b
   for (int jj = 0; jj < kIn; ++jj) Xt[static_cast<size_t>(jj) * B + b] = e[jj];
 }
 
-// column sums of a [rows][cols] matrix (f32 or bf16) into out[cols]
+// column sums of a [rows][cols] matrix (f32 or bf16) into out[cols]: block (x, y) sums the rows
+// r = y, y + 8 gridDim.y, ... of its 32 columns into part[y][cols]; the last block of each column
+// group to finish (a ticket, reset for the next launch) adds the gridDim.y partials in a fixed
+// order (eight warps over eight partials each, then the warps in order), so the result does not
+// depend on which block finishes last
 template <class T>
-__global__ void k_colsum(const T *__restrict__ A, int rows, int cols, float *__restrict__ out) {
+__global__ void k_colsum(const T *__restrict__ A, int rows, int cols, float *__restrict__ part,
+                         float *__restrict__ out, unsigned int *__restrict__ tickets) {
   __shared__ float s[8][33];
-  const int c = blockIdx.x * 32 + (threadIdx.x & 31), ty = threadIdx.x >> 5;
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, c = blockIdx.x * 32 + lane, ty = threadIdx.x >> 5;
   const int stride = 8 * gridDim.y;
   float a = 0.0f;
   if (c < cols) {
@@ -179,13 +185,32 @@ __global__ void k_colsum(const T *__restrict__ A, int rows, int cols, float *__r
     }
     for (; r < rows; r += stride) a += static_cast<float>(A[static_cast<size_t>(r) * cols + c]);
   }
-  s[ty][threadIdx.x & 31] = a;
+  s[ty][lane] = a;
   __syncthreads();
   if (ty == 0 && c < cols) {
     float t = 0.0f;
-    for (int q = 0; q < 8; ++q) t += s[q][threadIdx.x];
-    out[static_cast<size_t>(blockIdx.y) * cols + c] = t;  // this block's partial (rows r = y, y + 8 gridDim.y, ...)
+    for (int q = 0; q < 8; ++q) t += s[q][lane];
+    part[static_cast<size_t>(blockIdx.y) * cols + c] = t;  // this block's partial
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&tickets[blockIdx.x], 1u) == gridDim.y - 1;
+  __syncthreads();
+  if (!last) return;
+  const int per = (gridDim.y + 7) / 8;  // partials per warp
+  float w = 0.0f;
+  if (c < cols) {
+    for (int z = ty * per; z < min(static_cast<int>(gridDim.y), (ty + 1) * per); ++z)
+      w += __ldcg(part + static_cast<size_t>(z) * cols + c);
+  }
+  s[ty][lane] = w;
+  __syncthreads();
+  if (ty == 0 && c < cols) {
+    float t = 0.0f;
+    for (int q = 0; q < 8; ++q) t += s[q][lane];
+    out[c] = t;
+  }
+  if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
 }
 
 // out[i] = sum over z = 0 .. nsplit-1 (in that order) of part[z][i]: the fixed-order reduction of
@@ -207,8 +232,13 @@ __global__ void k_sum_splits(const float *__restrict__ part, int nsplit, size_t 
   }
 }
 
-__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
-                       size_t n, float lr, float b1, float b2, float c1, float c2, float eps) {
+// Adam step fused with the BF16 weight copies of the next step's GEMMs (the same conversions
+// as refresh_bf16: W1, W2, W3 as stored and W2, W3 transposed)
+__global__ void k_adam_bf16(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, size_t n, float lr, float b1, float b2, float c1, float c2, float eps,
+                            __nv_bfloat16 *__restrict__ w1, __nv_bfloat16 *__restrict__ w2,
+                            __nv_bfloat16 *__restrict__ w3, __nv_bfloat16 *__restrict__ w2t,
+                            __nv_bfloat16 *__restrict__ w3t) {
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
     const float gi = g[i];
@@ -216,7 +246,20 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
     const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    const __nv_bfloat16 h = __float2bfloat16(pi);
+    if (i < kOffB1) {
+      w1[i - kOffW1] = h;
+    } else if (i >= kOffW2 && i < kOffB2) {
+      const size_t e = i - kOffW2, r = e / kHid, c = e % kHid;
+      w2[e] = h;
+      w2t[c * kHid + r] = h;
+    } else if (i >= kOffW3 && i < kOffB3) {
+      const size_t e = i - kOffW3, r = e / kHid, c = e % kHid;
+      w3[e] = h;
+      w3t[c * kOut + r] = h;
+    }
   }
 }
 
@@ -330,6 +373,7 @@ struct mppi_mlp {
   double *loss = nullptr;
   int *d_err = nullptr;
   float *gsplit = nullptr;    // split-K and column-sum partials [splits][count]
+  unsigned int *tickets = nullptr;  // column-sum completion tickets [kHid / 32], zero between launches
   double *moments = nullptr;  // per-block moment partials [kMomentBlocks][2 * kState]
 
   int fail(int code, const char *fmt, ...) {
@@ -502,14 +546,14 @@ int backward(mppi_mlp *q, const __nv_bfloat16 *X, const float *T, int B) {
   g.split_stride = static_cast<int64_t>(kHid) * kIn;
   MLP_TRY(q->cuda(launch_gemm_bf16(g, q->stream), "gemm gW1"));
   MLP_TRY(split_sum(static_cast<size_t>(kHid) * kIn, q->g + kOffW1, "gW1 sum"));
-  // bias gradients: column sums, 16 row partials each, summed in a fixed order
+  // bias gradients: column sums, 64 row partials each, summed in a fixed order by the last block
   constexpr int kRowParts = 64;
-  mlp::k_colsum<float><<<dim3(1, kRowParts), 256, 0, q->stream>>>(q->dYf, B, kOut, q->gsplit);
-  mlp::k_sum_splits<<<1, 256, 0, q->stream>>>(q->gsplit, kRowParts, kOut, q->g + kOffB3);
-  mlp::k_colsum<__nv_bfloat16><<<dim3(kHid / 32, kRowParts), 256, 0, q->stream>>>(q->dZ2, B, kHid, q->gsplit);
-  mlp::k_sum_splits<<<1, 256, 0, q->stream>>>(q->gsplit, kRowParts, kHid, q->g + kOffB2);
-  mlp::k_colsum<__nv_bfloat16><<<dim3(kHid / 32, kRowParts), 256, 0, q->stream>>>(q->dZ1, B, kHid, q->gsplit);
-  mlp::k_sum_splits<<<1, 256, 0, q->stream>>>(q->gsplit, kRowParts, kHid, q->g + kOffB1);
+  mlp::k_colsum<float><<<dim3(1, kRowParts), 256, 0, q->stream>>>(q->dYf, B, kOut, q->gsplit, q->g + kOffB3,
+                                                                    q->tickets);
+  mlp::k_colsum<__nv_bfloat16><<<dim3(kHid / 32, kRowParts), 256, 0, q->stream>>>(q->dZ2, B, kHid, q->gsplit,
+                                                                                  q->g + kOffB2, q->tickets);
+  mlp::k_colsum<__nv_bfloat16><<<dim3(kHid / 32, kRowParts), 256, 0, q->stream>>>(q->dZ1, B, kHid, q->gsplit,
+                                                                                  q->g + kOffB1, q->tickets);
   return q->cuda(cudaGetLastError(), "bias grads");
 }
 
@@ -547,6 +591,8 @@ int mppi_mlp_create(uint64_t seed, mppi_mlp **out) {
   if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->d_err, sizeof(int)), "err");
   if (rc == MPPI_OK)
     rc = q->cuda(cudaMalloc(&q->gsplit, sizeof(float) * static_cast<size_t>(kMaxSplit) * kHid * kHid), "split partials");
+  if (rc == MPPI_OK) rc = q->cuda(cudaMalloc(&q->tickets, sizeof(unsigned int) * (kHid / 32)), "tickets");
+  if (rc == MPPI_OK) rc = q->cuda(cudaMemset(q->tickets, 0, sizeof(unsigned int) * (kHid / 32)), "tickets");
   if (rc == MPPI_OK)
     rc = q->cuda(cudaMalloc(&q->moments, sizeof(double) * static_cast<size_t>(kMomentBlocks) * 2 * kState), "moments");
   if (rc == MPPI_OK) rc = q->cuda(cudaMemsetAsync(q->d_err, 0, sizeof(int), q->stream), "err zero");
@@ -576,7 +622,7 @@ int mppi_mlp_destroy(mppi_mlp *q) {
   if (q->stream) cudaStreamSynchronize(q->stream);
   void *bufs[] = {q->p, q->g, q->m, q->v, q->w1, q->w2, q->w3, q->w2t, q->w3t, q->out_scale, q->Xf, q->D, q->Xb, q->H1, q->H2,
                   q->dYb, q->dZ2, q->dZ1, q->Tb, q->Y, q->dYf, q->loss, q->d_err, q->gsplit, q->moments,
-                  q->Xt, q->H1t, q->H2t, q->dYt, q->dZ2t, q->dZ1t};
+                  q->Xt, q->H1t, q->H2t, q->dYt, q->dZ2t, q->dZ1t, q->tickets};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (q->stream) cudaStreamDestroy(q->stream);
@@ -662,9 +708,9 @@ int mppi_mlp_train(mppi_mlp *q, int steps, int batch, float lr, uint64_t seed, f
     q->adam_t += 1;
     const float c1 = 1.0f - std::pow(b1, static_cast<float>(q->adam_t));
     const float c2 = 1.0f - std::pow(b2, static_cast<float>(q->adam_t));
-    mlp::k_adam<<<296, 256, 0, q->stream>>>(q->p, q->g, q->m, q->v, kNumParams, lr, b1, b2, c1, c2, 1e-8f);
+    mlp::k_adam_bf16<<<296, 256, 0, q->stream>>>(q->p, q->g, q->m, q->v, kNumParams, lr, b1, b2, c1, c2, 1e-8f,
+                                                  q->w1, q->w2, q->w3, q->w2t, q->w3t);
     MLP_TRY(q->cuda(cudaGetLastError(), "adam"));
-    MLP_TRY(refresh_bf16(q));
     if (h_loss_trace) {
       double l = 0.0;
       MLP_TRY(q->cuda(cudaMemcpyAsync(&l, q->loss, sizeof l, cudaMemcpyDeviceToHost, q->stream), "loss"));
