@@ -471,7 +471,8 @@ int mppi_mlp_set_data(mppi_mlp *mlp, const float *d_states, const float *d_contr
  * (may be NULL; recording it synchronises every step). */
 int mppi_mlp_train(mppi_mlp *mlp, int steps, int batch, float lr, uint64_t seed, float *h_loss_trace);
 /* Loss and gradients of one batch: d_X [B][16] BF16 features, d_T [B][16] FP32 targets
- * (normalised increments; entries 7..15 ignored).  h_grads [MPPI_MLP_NUM_PARAMS]. */
+ * (normalised increments; entries 7..15 ignored), both 16-byte aligned (MPPI_EINVAL
+ * otherwise).  h_grads [MPPI_MLP_NUM_PARAMS]. */
 int mppi_mlp_grad(mppi_mlp *mlp, const void *d_X, const float *d_T, int B, float *h_grads, double *h_loss);
 /* One learned step for n device (state [n][7], control [n][2]) pairs into d_next [n][7]. */
 int mppi_mlp_predict(mppi_mlp *mlp, const float *d_states, const float *d_controls, int n, float *d_next);

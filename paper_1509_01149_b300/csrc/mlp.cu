@@ -723,6 +723,8 @@ int mppi_mlp_train(mppi_mlp *q, int steps, int batch, float lr, uint64_t seed, f
 
 int mppi_mlp_grad(mppi_mlp *q, const void *d_X, const float *d_T, int B, float *h_grads, double *h_loss) {
   if (!q || !d_X || !d_T || B < 1 || !h_grads) return MPPI_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_X) | reinterpret_cast<uintptr_t>(d_T)) & 15u)
+    return q->fail(MPPI_EINVAL, "d_X and d_T must be 16-byte aligned (their rows are read as 16-byte vectors)");
   MLP_TRY(ensure_batch(q, B));
   const __nv_bfloat16 *X = static_cast<const __nv_bfloat16 *>(d_X);
   MLP_TRY(forward(q, X, B, true));

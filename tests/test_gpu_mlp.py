@@ -89,6 +89,11 @@ def test_gradients_match_the_oracle(env):
     for k in go:
         rel = np.linalg.norm(g[k] - go[k]) / np.linalg.norm(go[k])
         assert rel < 3e-2, (k, rel)
+    # rows are read as 16-byte vectors: a misaligned batch is refused before any launch
+    with pytest.raises(N.MppiError):
+        net.grad(dX.data_ptr() + 2, dT.data_ptr(), B - 1)
+    with pytest.raises(N.MppiError):
+        net.grad(dX.data_ptr(), dT.data_ptr() + 4, B - 1)
     net.close()
 
 
