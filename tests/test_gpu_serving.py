@@ -276,3 +276,48 @@ def test_served_spread_weights_match_the_oracle_and_the_ctx_path(N):
         ctrl.close()
     assert spread >= 2   # the shared-regeneration limit is really exceeded
     srv.close()
+
+
+def test_serving_at_its_size_limits(N):
+    """The largest controllers a server takes (K = 65536, T = 256) for the car and the
+    quadrotor in one tick: u0 and the shifted controls within the U bar of the single-controller
+    path, the argmin of the slot's own costs, the path costs of 64 samples spread over every
+    block within the S~ bar of the oracle (same noise); one sample or one step more is refused."""
+    from oracle import mppi as om
+    from oracle import philox
+    srv = make_server(N, max_slots=8, arena=2 << 30)
+    picks = [(W.CAR, 65536, 256), (W.QUAD, 65536, 256)]
+    slots, cfgs = zip(*[admit(srv, s, K, T, 500 + i) for i, (s, K, T) in enumerate(picks)])
+    states = [W.config(p[0])["x0"] for p in picks]
+    u0 = srv.tick(list(slots), states)
+    for i, (s, K, T) in enumerate(picks):
+        c = dict(cfgs[i], seed=500 + i, gid=500 + i)
+        m = W.CONTROL_DIM[s]
+        dbg = srv.get_debug(slots[i], K)
+        fin = np.isfinite(dbg["S"])
+        assert dbg["kstar"] == int(np.argmin(np.where(fin, dbg["S"], np.inf)))
+        ctrl = P.make_controller(c)
+        cu0 = ctrl.step(np.asarray(c["x0"], dtype=np.float32))
+        ctrl.shift()
+        assert within(u0[i, :m], cu0, c), i
+        assert within(srv.get_controls(slots[i]), ctrl.get_controls(), c), i
+        ctrl.close()
+        idx = np.linspace(0, K - 1, 64).astype(int)
+        du = philox.exploration_noise(c["seed"], K, T, np.asarray(c["Sigma"], np.float32).astype(np.float64),
+                                      float(np.float32(c["nu"])), 0, c["gid"], samples=idx)
+        R = np.asarray(c["R"], np.float32).astype(np.float64)
+        U0 = np.tile(np.asarray(c["u_init"], np.float32).astype(np.float64), (T, 1))
+        S_o, st = om.path_costs(P.oracle_system(s, c["dt"]), np.asarray(states[i], np.float32).astype(np.float64),
+                                U0, du, R, float(np.float32(c["nu"])))
+        keep = np.isfinite(S_o)
+        if getattr(st, "margin", None) is not None:
+            keep &= st.margin > 1e-3
+        rel = np.abs(dbg["S"][idx][keep].astype(np.float64) - S_o[keep]) / np.abs(S_o[keep])
+        assert rel.size > 0 and rel.max() <= P.S_RTOL, (i, rel.max())
+    for s, K, T in ((W.CAR, 65537, 100), (W.CAR, 1024, 257)):
+        c = W.config(s, K=K, T=T)
+        cfg = srv.slot_config(s, K, T, c["dt"], c["nu"], c["lam"], c["Sigma"], c["R"], seed=1, gid=1,
+                              env_id=ENV.get(s, -1), u_init=c["u_init"])
+        with pytest.raises(N.MppiError):
+            srv.admit(cfg)
+    srv.close()
