@@ -160,34 +160,45 @@ def _nvml_clock_reader(gpu_id: str | None):
         return None
 
 
+def _nvml_sample_loop(gpu_id: str, path: str, period_s: float = 0.002):
+    """Sampler process: every period_s append 'unix time,SM MHz,max SM MHz,reason bits' to path
+    (line-buffered) until terminated.  Run as its own process, so that the timed host loops of
+    the bench never wait for this thread's interpreter lock."""
+    read = _nvml_clock_reader(gpu_id or None)
+    if read is None:
+        return
+    with open(path, "w", buffering=1) as f:
+        while True:
+            try:
+                sm, smax, why = read()
+                f.write("%.6f,%d,%d,%d\n" % (time.time(), sm, smax, why))
+            except Exception:
+                pass
+            time.sleep(period_s)
+
+
 class ClockSampler:
-    """SM clocks and throttle reasons during the timed region.  An NVML thread (read-only
-    queries) samples every 2 ms between mark_start() and mark_end(), so that a short timed
-    region still has a record; nvidia-smi runs beside it every 20 ms (started ahead of the
-    timed region, waiting for its first sample) and is the record where NVML is unavailable,
-    keeping the samples whose timestamps fall between the marks."""
+    """SM clocks and throttle reasons during the timed regions.  A sampler process of its own
+    (NVML, read-only queries) timestamps a sample every 2 ms, so that a short timed region still
+    has a record without a thread of this process competing with the timed host loops;
+    nvidia-smi runs beside it every 20 ms (started ahead of the timed region, waiting for its
+    first sample) and is the record where NVML is unavailable.  Only samples whose timestamps
+    fall between a mark_start() and its mark_end() are kept."""
 
     def __init__(self, gpu_id: str | None, settle_s: float = 2.0):
         self.path = tempfile.mktemp(suffix=".csv")
         self.t0 = self.t1 = None
         self.windows = []                  # (start, end) of each timed region
-        self.nvml_rows, self.nvml_on, self.nvml_stop, self.nvml_thread = [], False, False, None
-        read = _nvml_clock_reader(gpu_id)
-        if read is not None:
-            import threading
-
-            def loop():
-                while not self.nvml_stop:
-                    if self.nvml_on:
-                        try:
-                            sm, smax, why = read()
-                            self.nvml_rows.append(dict(sm=float(sm), smax=float(smax),
-                                                       reasons={r: bool(why & b) for r, b in _REASON_BITS.items()}))
-                        except Exception:
-                            pass
-                    time.sleep(0.002)
-            self.nvml_thread = threading.Thread(target=loop, daemon=True)
-            self.nvml_thread.start()
+        # NVML in a sampler process of its own (read-only queries, every 2 ms, timestamped);
+        # the samples inside the timed windows are kept at stop()
+        self.nvml_path = tempfile.mktemp(suffix=".nvml")
+        try:
+            self.nvml_p = subprocess.Popen(
+                [sys.executable, "-c", "import sys; sys.path.insert(0, sys.argv[1]); import bench; "
+                 "bench._nvml_sample_loop(sys.argv[2], sys.argv[3])", ROOT, gpu_id or "", self.nvml_path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.nvml_p = None
         q = ("timestamp,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -205,15 +216,55 @@ class ClockSampler:
         deadline = time.time() + settle_s
         while time.time() < deadline and os.path.getsize(self.path) == 0:
             time.sleep(0.01)
+        deadline = time.time() + 4 * settle_s
+        while (self.nvml_p is not None and self.nvml_p.poll() is None and time.time() < deadline and
+               not (os.path.exists(self.nvml_path) and os.path.getsize(self.nvml_path) > 0)):
+            time.sleep(0.01)
 
     def mark_start(self):
         self.t0 = time.time()
-        self.nvml_on = True
 
     def mark_end(self):
-        self.nvml_on = False
         self.t1 = time.time()
         self.windows.append((self.t0, self.t1))
+
+    def _stop_nvml(self):
+        """The sampler process's samples inside the timed windows."""
+        if self.nvml_p is None:
+            return []
+        if self.t1 is not None:   # a sample stamped past the last window, or a short wait
+            deadline = time.time() + 0.5
+            while time.time() < deadline and self.nvml_p.poll() is None:
+                time.sleep(0.01)
+                try:
+                    with open(self.nvml_path) as f:
+                        last = f.read().splitlines()[-1:]
+                    if last and float(last[0].split(",")[0]) > self.t1:
+                        break
+                except (OSError, ValueError, IndexError):
+                    pass
+        self.nvml_p.terminate()
+        try:
+            self.nvml_p.wait(timeout=5)
+        except Exception:
+            self.nvml_p.kill()
+        rows = []
+        try:
+            with open(self.nvml_path) as f:
+                for line in f:
+                    try:
+                        t, sm, smax, why = line.strip().split(",")
+                        t, why = float(t), int(why)
+                    except ValueError:
+                        continue
+                    if self.windows and not any(a <= t <= b for a, b in self.windows):
+                        continue
+                    rows.append(dict(sm=float(sm), smax=float(smax),
+                                     reasons={r: bool(why & b) for r, b in _REASON_BITS.items()}))
+            os.unlink(self.nvml_path)
+        except OSError:
+            pass
+        return rows
 
     @staticmethod
     def _stamp(stamp: str):
@@ -243,16 +294,13 @@ class ClockSampler:
         return False
 
     def stop(self):
-        if self.nvml_thread is not None:
-            self.nvml_stop = True
-            self.nvml_thread.join(timeout=2)
+        rows = self._stop_nvml()
         smi = self._stop_smi()
-        rows = self.nvml_rows
         if not rows:
             return dict(smi, source="nvidia-smi")
         reasons = sorted({r for row in rows for r, on in row["reasons"].items() if on})
         return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
-                "reasons": reasons, "samples": len(rows), "source": "nvml, every 2 ms",
+                "reasons": reasons, "samples": len(rows), "source": "nvml, every 2 ms (a sampler process)",
                 "nvidia_smi": {k: smi.get(k) for k in ("sm_mhz", "reasons", "samples")}}
 
     def _stop_smi(self):
