@@ -63,3 +63,28 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
         steps, warmup, gpus = 1, 0, 2
     bench.run_reference(A, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_clock_sampler_keeps_only_samples_inside_the_timed_windows(tmp_path, monkeypatch):
+    """The NVML sampler runs as a process of its own and timestamps its samples; stop() keeps
+    those inside the mark_start/mark_end windows.  Here a stand-in process writes samples at
+    known times (no GPU or NVML on this host)."""
+    import subprocess
+    import time
+    sys.path.insert(0, ROOT)
+    import bench
+    s = bench.ClockSampler.__new__(bench.ClockSampler)
+    s.nvml_path = str(tmp_path / "samples.nvml")
+    now = time.time()
+    s.windows = [(now + 10.0, now + 20.0)]
+    s.t0, s.t1 = now + 10.0, now + 20.0
+    with open(s.nvml_path, "w") as f:
+        f.write("%.6f,2032,2032,0\n" % (now + 5.0))     # before the window: dropped
+        f.write("%.6f,1900,2032,4\n" % (now + 12.0))    # inside, with reason bit 4
+        f.write("%.6f,2032,2032,0\n" % (now + 25.0))    # after: dropped (and ends the wait)
+        f.write("not a sample\n")
+    s.nvml_p = subprocess.Popen([sys.executable, "-c", "import time; time.sleep(30)"])
+    rows = s._stop_nvml()
+    assert s.nvml_p.poll() is not None                  # the sampler process was stopped
+    assert len(rows) == 1 and rows[0]["sm"] == 1900.0 and rows[0]["smax"] == 2032.0
+    assert [r for r, on in rows[0]["reasons"].items() if on] == [r for r, b in bench._REASON_BITS.items() if b == 4]
