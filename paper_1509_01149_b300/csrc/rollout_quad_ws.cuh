@@ -63,6 +63,7 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
   constexpr int M = Quad::M, N = Quad::N, C = quad_ws_chunk(TOGO), R = quad_ws_ring(TOGO, GEN), P = kQwsPass,
                 NT = 3 * NS;
+  static_assert(C % 2 == 0, "chunk 0 splits into two halves");
   __shared__ uint64_t bar_noise[kQwsMaxChunks * kQwsChunk / C], bar_full[R], bar_empty[R];
   __shared__ float sx0[N];
   const int T = p.T, TM = T * M, tid = threadIdx.x;
@@ -92,7 +93,8 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
   }
   if (tid < N) sx0[tid] = x0[tid];
   if (tid == 0) {
-    for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], NS);
+    // chunk 0's noise is drawn by the dynamics and cost roles together (2 NS arrivals)
+    for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], c == 0 ? 2 * NS : NS);
     for (int r = 0; r < R; ++r) {
       tc::mbar_init(&bar_full[r], NS);
       tc::mbar_init(&bar_empty[r], NS);
@@ -117,25 +119,35 @@ __device__ __forceinline__ void rollout_block_quad_ws(const CtrlParams &p, const
 #pragma unroll
   for (int a = 0; a < M * M; ++a) Lnu[a] = p.Lnu[a];
   bool ok = true;
-  if (tid < NS) {
-    // ---- noise: du of chunk c into sDu (Philox block i covers step i's four controls) ----
-    const int slot = tid, k = k0 + slot;
-    auto block = [&](int i) {
-      float e[4];
-      normals4(static_cast<uint32_t>(i), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, e);
-      float du[M];
-      scale_noise<M>(GEN ? sGen + static_cast<size_t>(i) * 2 * M * M : Lnu, e, du);
+  // Philox block i -> du_i (four controls) of sample k0 + slot
+  auto block = [&](int i, int slot) {
+    float e[4];
+    normals4(static_cast<uint32_t>(i), static_cast<uint32_t>(k0 + slot), ctr, p.gid, p.key_lo, p.key_hi, e);
+    float du[M];
+    scale_noise<M>(GEN ? sGen + static_cast<size_t>(i) * 2 * M * M : Lnu, e, du);
 #pragma unroll
-      for (int a = 0; a < M; ++a) sDu[(i * M + a) * NS + slot] = du[a];
-    };
-    for (int c = 0; c < nch; ++c) {
+    for (int a = 0; a < M; ++a) sDu[(i * M + a) * NS + slot] = du[a];
+  };
+  // Chunk 0's noise: the dynamics and the cost role would otherwise wait for the noise role's
+  // first chunk, so they draw its steps themselves, half each, while the noise role starts on
+  // chunk 1.
+  if (tid >= NS) {
+    const int slot = tid % NS, i0 = tid < 2 * NS ? 0 : C / 2;
+#pragma unroll 1
+    for (int i = i0; i < min(i0 + C / 2, T); ++i) block(i, slot);
+    tc::mbar_arrive(&bar_noise[0]);
+  }
+  if (tid < NS) {
+    // ---- noise: du of chunks 1.. into sDu (Philox block i covers step i's four controls) --
+    const int slot = tid;
+    for (int c = 1; c < nch; ++c) {
       const int i0 = c * C;
       if (i0 + C <= T) {
 #pragma unroll
-        for (int j = 0; j < C; ++j) block(i0 + j);
+        for (int j = 0; j < C; ++j) block(i0 + j, slot);
       } else {
 #pragma unroll 1
-        for (int i = i0; i < T; ++i) block(i);
+        for (int i = i0; i < T; ++i) block(i, slot);
       }
       tc::mbar_arrive(&bar_noise[c]);
     }

@@ -76,6 +76,7 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
                                                      float *smem, float *__restrict__ part_rho = nullptr,
                                                      DF *__restrict__ part_eta = nullptr) {
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
+  static_assert(kWsChunk % 4 == 0, "chunk 0 splits into two halves of whole Philox blocks");
   constexpr int M = 2, C = kWsChunk, R = kWsRing, NT = kWsRoles * NS;
   __shared__ uint64_t bar_noise[kWsMaxChunks], bar_full[R], bar_empty[R];
   const int T = p.T, TM = T * M, tid = threadIdx.x;
@@ -97,7 +98,8 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
     for (int o = tid; o < 2 * TM * M; o += NT) sGen[o] = p.gen[o];
   if (tid < Car::N) sx0[tid] = x0[tid];
   if (tid == 0) {
-    for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], NS);
+    // chunk 0's noise is drawn by the core and pose roles together (2 NS arrivals)
+    for (int c = 0; c < nch; ++c) tc::mbar_init(&bar_noise[c], c == 0 ? 2 * NS : NS);
     for (int r = 0; r < R; ++r) {
       tc::mbar_init(&bar_full[r], NS);
       tc::mbar_init(&bar_empty[r], NS);
@@ -122,6 +124,34 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
   const int slot = tid - role * NS;
   const int k = k0 + slot;
   bool ok = true;
+
+  // Philox block b -> du of steps 2b and 2b+1 (those < T) of this thread's sample
+  auto noise_block = [&](int b, const float *Lnu) {
+    float e[4];
+    normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, e);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int i = 2 * b + s;
+      float du[M];
+      scale_noise<M>(GEN ? sGen + static_cast<size_t>(min(i, T - 1)) * 2 * M * M : Lnu, e + s * M, du);
+      if (i < T) {
+#pragma unroll
+        for (int a = 0; a < M; ++a) sDu[(i * M + a) * NS + slot] = du[a];
+      }
+    }
+  };
+  // Chunk 0's noise: the core and the pose role would otherwise wait for the noise role's
+  // first chunk, so they draw its blocks themselves, half each, while the noise role starts
+  // on chunk 1.
+  if (role != 1) {
+    float Lnu[M * M];
+#pragma unroll
+    for (int a = 0; a < M * M; ++a) Lnu[a] = p.Lnu[a];
+    const int bq = role == 0 ? 0 : C / 4;
+#pragma unroll 1
+    for (int b = bq; b < bq + C / 4 && 2 * b < T; ++b) noise_block(b, Lnu);
+    tc::mbar_arrive(&bar_noise[0]);
+  }
 
   // Each role runs whole chunks through one fully unrolled body (one basic block, so the
   // compiler can interleave the steps) and the ragged last chunk through a small rolled
@@ -176,32 +206,18 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
       tc::mbar_arrive(&bar_full[c % R]);
     }
   } else if (role == 1) {
-    // ---- noise: du of chunk c into sDu (block b of the generator covers steps 2b, 2b+1) --
+    // ---- noise: du of chunks 1.. into sDu (block b of the generator covers steps 2b, 2b+1)
     float Lnu[M * M];
 #pragma unroll
     for (int a = 0; a < M * M; ++a) Lnu[a] = p.Lnu[a];
-    auto block = [&](int b) {  // Philox block b -> du of steps 2b and 2b+1 (those < T)
-      float e[4];
-      normals4(static_cast<uint32_t>(b), static_cast<uint32_t>(k), ctr, p.gid, p.key_lo, p.key_hi, e);
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int i = 2 * b + s;
-        float du[M];
-        scale_noise<M>(GEN ? sGen + static_cast<size_t>(min(i, T - 1)) * 2 * M * M : Lnu, e + s * M, du);
-        if (i < T) {
-#pragma unroll
-          for (int a = 0; a < M; ++a) sDu[(i * M + a) * NS + slot] = du[a];
-        }
-      }
-    };
-    for (int c = 0; c < nch; ++c) {
+    for (int c = 1; c < nch; ++c) {
       const int b0 = c * (C / 2);
       if ((c + 1) * C <= T) {
 #pragma unroll
-        for (int q = 0; q < C / 2; ++q) block(b0 + q);
+        for (int q = 0; q < C / 2; ++q) noise_block(b0 + q, Lnu);
       } else {
 #pragma unroll 1
-        for (int b = b0; 2 * b < T; ++b) block(b);
+        for (int b = b0; 2 * b < T; ++b) noise_block(b, Lnu);
       }
       tc::mbar_arrive(&bar_noise[c]);
     }
