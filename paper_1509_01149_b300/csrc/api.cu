@@ -107,10 +107,18 @@ struct mppi_ctx {
   float *dh_x0 = nullptr, *dh_u0 = nullptr;  // h_x0 and write u0 into h_u0 directly
   unsigned int *h_ready = nullptr, *dh_ready = nullptr;  // pinned, mapped: set once u0 is in h_u0
 
-  cudaGraphExec_t graph = nullptr;        // mppi_step: rollout -> merge
-  cudaGraphExec_t graph_shift = nullptr;  // mppi_step_shift: rollout -> merge + shift
+  // The controls live in two buffers of T*m floats in d_U: half `ub` is current, and every
+  // shift writes the shifted update into the other half and makes it current (host-side
+  // bookkeeping: every shift is a call on this ctx, in stream order).  Each step graph is
+  // therefore captured once per half.
+  int ub = 0;
+  float *U_cur() const { return d_U + static_cast<size_t>(ub) * T * m; }
+  float *U_nxt() const { return d_U + static_cast<size_t>(ub ^ 1) * T * m; }
+
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};        // mppi_step: rollout -> merge
+  cudaGraphExec_t graph_shift[2] = {nullptr, nullptr};  // mppi_step_shift: rollout -> merge + shift
   bool graph_dirty = true;
-  cudaGraphExec_t iter_graph = nullptr;  // mppi_iterate_async: rollout -> merge -> shift
+  cudaGraphExec_t iter_graph[2] = {nullptr, nullptr};  // mppi_iterate_async: rollout -> merge + shift
   bool iter_graph_dirty = true;
   const float *iter_x0 = nullptr;
   float *iter_u0 = nullptr;
@@ -142,41 +150,45 @@ namespace {
 
 int launch_rollout(mppi_ctx *c, const float *x0, cudaStream_t s) {
   if (c->sys == MPPI_CAR_MLP)
-    return c->cuda(launch_rollout_mlp(c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, c->mlp_precision, s),
+    return c->cuda(launch_rollout_mlp(c->p, x0, c->d_st, c->U_cur(), c->d_S, c->d_psum, c->d_part, c->mlp_precision, s),
                    "mlp rollout launch");
   if (c->weighting == MPPI_WEIGHT_TO_GO)
-    return c->cuda(launch_rollout_to_go(c->sys, c->blk, c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part,
+    return c->cuda(launch_rollout_to_go(c->sys, c->blk, c->p, x0, c->d_st, c->U_cur(), c->d_S, c->d_psum, c->d_part,
                                         c->d_prho, c->d_peta, s),
                    "cost-to-go rollout launch");
-  return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, x0, c->d_st, c->d_U, c->d_S, c->d_psum, c->d_part, s),
+  return c->cuda(launch_rollout_fused(c->sys, c->blk, c->p, x0, c->d_st, c->U_cur(), c->d_S, c->d_psum, c->d_part, s),
                  "fused rollout launch");
 }
 
 // u0_ready: the path-weighting merge raises this mapped flag once u0 is in u0_out
 int launch_update(mppi_ctx *c, float *u0_out, cudaStream_t s, unsigned int *u0_ready = nullptr) {
   if (c->weighting == MPPI_WEIGHT_TO_GO)
-    return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->d_U, u0_out,
-                                      c->d_dU, c->d_dbg, s, false, nullptr, nullptr, u0_ready),
+    return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->U_cur(), u0_out,
+                                      c->d_dU, c->d_dbg, s, false, nullptr, nullptr, nullptr, u0_ready),
                    "cost-to-go merge launch");
   return c->cuda(
-      launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU, c->d_dbg, s, u0_ready),
+      launch_merge_update(c->nblk, c->p, c->d_psum, c->d_part, c->U_cur(), u0_out, c->d_dU, c->d_dbg, s, u0_ready),
       "merge launch");
 }
 
-// The update and Algorithm 1's shift: in one launch (a thread-block cluster) when the outputs
-// fit one, else the update, then the shift kernel.
+// The update and Algorithm 1's shift in one launch, from the current control buffer into the
+// other one.  The caller makes the other buffer current once the launch (or the graph that
+// holds it) is enqueued.
 int launch_update_shift(mppi_ctx *c, float *u0_out, cudaStream_t s, unsigned int *u0_ready = nullptr) {
-  if (merge_shift_fusable(c->p)) {
-    if (c->weighting == MPPI_WEIGHT_PATH)
-      return c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->d_U, u0_out, c->d_dU,
-                                               c->d_dbg, c->d_uinit, c->d_st, s, u0_ready),
-                     "merge + shift launch");
-    return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->d_U, u0_out,
-                                      c->d_dU, c->d_dbg, s, true, c->d_uinit, c->d_st, u0_ready),
-                   "cost-to-go merge + shift launch");
-  }
-  MPPI_TRY(launch_update(c, u0_out, s, u0_ready));
-  return c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, s), "shift launch");
+  if (c->weighting == MPPI_WEIGHT_PATH)
+    return c->cuda(launch_merge_update_shift(c->nblk, c->p, c->d_psum, c->d_part, c->U_cur(), c->U_nxt(), u0_out,
+                                             c->d_dU, c->d_dbg, c->d_uinit, c->d_st, s, u0_ready),
+                   "merge + shift launch");
+  return c->cuda(launch_merge_to_go(c->nblk, c->p, c->d_psum, c->d_prho, c->d_peta, c->d_part, c->U_cur(), u0_out,
+                                    c->d_dU, c->d_dbg, s, true, c->d_uinit, c->d_st, c->U_nxt(), u0_ready),
+                 "cost-to-go merge + shift launch");
+}
+
+// Algorithm 1's shift on its own (the shift kernel), then the other buffer is current.
+int enqueue_shift(mppi_ctx *c, cudaStream_t s) {
+  MPPI_TRY(c->cuda(launch_shift(c->p, c->U_cur(), c->U_nxt(), c->d_uinit, c->d_st, s), "shift launch"));
+  c->ub ^= 1;
+  return MPPI_OK;
 }
 
 // Blocks the rollout launches for this ctx's samples (all of K, or its shard).
@@ -202,15 +214,15 @@ int ensure_noise_buffer(mppi_ctx *c) {
 int enqueue_plain(mppi_ctx *c, cudaStream_t s) {
   MPPI_TRY(ensure_noise_buffer(c));
   MPPI_TRY(c->cuda(launch_plain_noise(c->p, &c->d_st->counter, c->d_du, s), "plain noise"));
-  MPPI_TRY(c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->d_U, c->d_du, c->d_S, s), "plain rollout"));
-  return c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, c->d_plain, s),
+  MPPI_TRY(c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->U_cur(), c->d_du, c->d_S, s), "plain rollout"));
+  return c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->U_cur(), c->d_u0, c->d_dU, c->d_dbg, c->d_plain, s),
                  "plain reduce/update");
 }
 
-// Capture one step graph: x0 copied from the pinned buffer (one DMA: cheaper than every CTA
-// reading mapped host memory), the merge writes u0 straight into the mapped pinned buffer
-// (no copy node) and then raises the mapped ready flag, and with `shift` the shift runs in
-// the same launch when the outputs fit one cluster, else by the shift kernel after it.
+// Capture one step graph for the current control buffer: x0 copied from the pinned buffer
+// (one DMA: cheaper than every CTA reading mapped host memory), the merge writes u0 straight
+// into the mapped pinned buffer (no copy node) and then raises the mapped ready flag, and with
+// `shift` the shift runs in the same launch.
 int capture_step(mppi_ctx *c, bool shift, cudaGraphExec_t *out) {
   if (*out) {
     cudaGraphExecDestroy(*out);
@@ -235,9 +247,17 @@ int capture_step(mppi_ctx *c, bool shift, cudaGraphExec_t *out) {
   return rc;
 }
 
+// Both step graphs for each control buffer.
 int build_graph(mppi_ctx *c) {
-  MPPI_TRY(capture_step(c, false, &c->graph));
-  MPPI_TRY(capture_step(c, true, &c->graph_shift));
+  const int ub = c->ub;
+  int rc = MPPI_OK;
+  for (int q = 0; q < 2 && rc == MPPI_OK; ++q) {
+    c->ub = q;
+    rc = capture_step(c, false, &c->graph[q]);
+    if (rc == MPPI_OK) rc = capture_step(c, true, &c->graph_shift[q]);
+  }
+  c->ub = ub;
+  MPPI_TRY(rc);
   c->graph_dirty = false;
   return MPPI_OK;
 }
@@ -447,12 +467,12 @@ int mppi_create(mppi_system sys, int K, int T, float dt, float nu, float lambda,
   const size_t TM = static_cast<size_t>(T) * m;
   const size_t nb_max = (K + kMinBlockSamples - 1) / kMinBlockSamples;  // block partials of any shape fit
   c->nblk_cap = static_cast<int>(nb_max);
-  c->arena.size = 256 * 16 + sizeof(CtrlState) + sizeof(float) * (2 * TM + 2 * kMaxM + K + nb_max * TM) +
+  c->arena.size = 256 * 16 + sizeof(CtrlState) + sizeof(float) * (3 * TM + 2 * kMaxM + K + nb_max * TM) +
                   sizeof(BlockPartial) * nb_max + sizeof(StepDebug) + 2 * sizeof(uint32_t);
   if (rc == MPPI_OK) rc = c->cuda(dev_malloc(&c->arena.base, c->arena.size), "cudaMalloc(arena)");
   if (rc == MPPI_OK) {
     c->d_st = c->arena.take<CtrlState>(1);
-    c->d_U = c->arena.take<float>(TM);
+    c->d_U = c->arena.take<float>(2 * TM);  // two control buffers (shifts alternate them)
     c->d_dU = c->arena.take<float>(TM);
     c->d_uinit = c->arena.take<float>(kMaxM);
     c->d_u0 = c->arena.take<float>(kMaxM);
@@ -521,9 +541,11 @@ int mppi_debug_forest_nearest(const float *obs, int n_obs, int n_points, const f
 int mppi_destroy(mppi_ctx *c) {
   if (!c) return MPPI_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->graph) cudaGraphExecDestroy(c->graph);
-  if (c->graph_shift) cudaGraphExecDestroy(c->graph_shift);
-  if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
+  for (int q = 0; q < 2; ++q) {
+    if (c->graph[q]) cudaGraphExecDestroy(c->graph[q]);
+    if (c->graph_shift[q]) cudaGraphExecDestroy(c->graph_shift[q]);
+    if (c->iter_graph[q]) cudaGraphExecDestroy(c->iter_graph[q]);
+  }
   if (c->arena.base) cudaFree(c->arena.base);
   if (c->d_du) cudaFree(c->d_du);
   if (c->d_prho) cudaFree(c->d_prho);
@@ -670,14 +692,14 @@ int mppi_get_iteration(mppi_ctx *c, uint32_t *counter) {
 
 int mppi_set_controls(mppi_ctx *c, const float *U) {
   if (!c || !U) return MPPI_EINVAL;
-  MPPI_TRY(c->cuda(cudaMemcpyAsync(c->d_U, U, sizeof(float) * c->T * c->m, cudaMemcpyHostToDevice, c->stream),
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(c->U_cur(), U, sizeof(float) * c->T * c->m, cudaMemcpyHostToDevice, c->stream),
                    "U copy"));
   return c->cuda(cudaStreamSynchronize(c->stream), "sync");
 }
 
 int mppi_get_controls(mppi_ctx *c, float *U) {
   if (!c || !U) return MPPI_EINVAL;
-  MPPI_TRY(c->cuda(cudaMemcpyAsync(U, c->d_U, sizeof(float) * c->T * c->m, cudaMemcpyDeviceToHost, c->stream),
+  MPPI_TRY(c->cuda(cudaMemcpyAsync(U, c->U_cur(), sizeof(float) * c->T * c->m, cudaMemcpyDeviceToHost, c->stream),
                    "U copy"));
   return c->cuda(cudaStreamSynchronize(c->stream), "sync");
 }
@@ -816,14 +838,15 @@ int step_host(mppi_ctx *c, const float *state, float *u0_out, bool shift) {
     MPPI_TRY(c->impl == MPPI_IMPL_PLAIN ? enqueue_plain(c, c->stream) : enqueue_fused(c, c->stream));
     MPPI_TRY(c->cuda(cudaMemcpyAsync(c->h_u0, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToHost, c->stream),
                      "u0 copy"));
-    if (shift) MPPI_TRY(c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch"));
+    if (shift) MPPI_TRY(enqueue_shift(c, c->stream));
   } else {
     if (c->graph_dirty) MPPI_TRY(build_graph(c));
     // the merge raises the ready flag; the learned dynamics also need the kernel's own
     // status, read after the stream finishes
     const bool flag = c->sys != MPPI_CAR_MLP;
     if (flag) *reinterpret_cast<volatile unsigned int *>(c->h_ready) = 0u;
-    MPPI_TRY(c->cuda(cudaGraphLaunch(shift ? c->graph_shift : c->graph, c->stream), "graph launch"));
+    MPPI_TRY(c->cuda(cudaGraphLaunch(shift ? c->graph_shift[c->ub] : c->graph[c->ub], c->stream), "graph launch"));
+    if (shift) c->ub ^= 1;
     if (flag) {
       MPPI_TRY(wait_u0(c));
       std::memcpy(u0_out, c->h_u0, sizeof(float) * c->m);
@@ -849,7 +872,7 @@ int mppi_rollout_async(mppi_ctx *c, const float *d_state) {
                      "x0 copy"));
     MPPI_TRY(ensure_noise_buffer(c));
     MPPI_TRY(c->cuda(launch_plain_noise(c->p, &c->d_st->counter, c->d_du, c->stream), "plain noise"));
-    return c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->d_U, c->d_du, c->d_S, c->stream), "plain rollout");
+    return c->cuda(launch_plain_rollout(c->sys, c->p, c->d_st, c->U_cur(), c->d_du, c->d_S, c->stream), "plain rollout");
   }
   return launch_rollout(c, d_state, c->stream);  // the kernel reads the caller's state directly
 }
@@ -858,7 +881,7 @@ int mppi_update_async(mppi_ctx *c, float *d_u0_out) {
   if (!c) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
   if (c->impl == MPPI_IMPL_PLAIN) {
-    MPPI_TRY(c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->d_U, c->d_u0, c->d_dU, c->d_dbg, c->d_plain, c->stream),
+    MPPI_TRY(c->cuda(launch_plain_reduce_update(c->p, c->d_S, c->d_du, c->U_cur(), c->d_u0, c->d_dU, c->d_dbg, c->d_plain, c->stream),
                      "plain reduce/update"));
     if (d_u0_out)
       MPPI_TRY(c->cuda(cudaMemcpyAsync(d_u0_out, c->d_u0, sizeof(float) * c->m, cudaMemcpyDeviceToDevice, c->stream),
@@ -874,40 +897,53 @@ int mppi_step_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
   return mppi_update_async(c, d_u0_out);
 }
 
+namespace {
+// The iteration graph (rollout -> merge + update + shift) of control buffer q.
+int capture_iterate(mppi_ctx *c, int q, const float *d_state, float *u0) {
+  if (c->iter_graph[q]) cudaGraphExecDestroy(c->iter_graph[q]);
+  c->iter_graph[q] = nullptr;
+  const int ub = c->ub;
+  c->ub = q;
+  cudaGraph_t g = nullptr;
+  int rc = c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  if (rc == MPPI_OK) {
+    rc = launch_rollout(c, d_state, c->stream);
+    if (rc == MPPI_OK) rc = launch_update_shift(c, u0, c->stream);
+    const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
+    if (rc == MPPI_OK) rc = rc_end;
+    if (rc == MPPI_OK) rc = c->cuda(cudaGraphInstantiate(&c->iter_graph[q], g, 0), "graph instantiate");
+    if (g) cudaGraphDestroy(g);
+  }
+  c->ub = ub;
+  return rc;
+}
+}  // namespace
+
 int mppi_iterate_async(mppi_ctx *c, const float *d_state, float *d_u0_out) {
   const NvtxRange range("mppi_iterate_async (graph: rollout, merge + update + shift)");
   if (!c || !d_state) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
   if (c->impl == MPPI_IMPL_PLAIN || c->stream == nullptr) {
     MPPI_TRY(mppi_step_async(c, d_state, d_u0_out));
-    return c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+    return enqueue_shift(c, c->stream);
   }
   float *u0 = d_u0_out ? d_u0_out : c->d_u0;
-  if (c->iter_graph_dirty || c->iter_graph == nullptr || c->iter_x0 != d_state || c->iter_u0 != u0) {
-    if (c->iter_graph) cudaGraphExecDestroy(c->iter_graph);
-    c->iter_graph = nullptr;
-    cudaGraph_t g = nullptr;
-    MPPI_TRY(c->cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture"));
-    int rc = launch_rollout(c, d_state, c->stream);
-    if (rc == MPPI_OK) rc = launch_update_shift(c, u0, c->stream);
-    const int rc_end = c->cuda(cudaStreamEndCapture(c->stream, &g), "end capture");
-    if (rc != MPPI_OK || rc_end != MPPI_OK) {
-      if (g) cudaGraphDestroy(g);
-      return rc != MPPI_OK ? rc : rc_end;
-    }
-    rc = c->cuda(cudaGraphInstantiate(&c->iter_graph, g, 0), "graph instantiate");
-    cudaGraphDestroy(g);
-    MPPI_TRY(rc);
+  if (c->iter_graph_dirty || c->iter_graph[0] == nullptr || c->iter_graph[1] == nullptr || c->iter_x0 != d_state ||
+      c->iter_u0 != u0) {
+    c->iter_graph_dirty = true;
+    for (int q = 0; q < 2; ++q) MPPI_TRY(capture_iterate(c, q, d_state, u0));
     c->iter_x0 = d_state;
     c->iter_u0 = u0;
     c->iter_graph_dirty = false;
   }
-  return c->cuda(cudaGraphLaunch(c->iter_graph, c->stream), "graph launch");
+  MPPI_TRY(c->cuda(cudaGraphLaunch(c->iter_graph[c->ub], c->stream), "graph launch"));
+  c->ub ^= 1;
+  return MPPI_OK;
 }
 
 int mppi_shift(mppi_ctx *c) {
   if (!c) return MPPI_EINVAL;
-  return c->cuda(launch_shift(c->p, c->d_U, c->d_uinit, c->d_st, c->stream), "shift launch");
+  return enqueue_shift(c, c->stream);
 }
 
 int mppi_get_debug(mppi_ctx *c, float *S, int *argmin, double *eta, float *dU) {
@@ -992,7 +1028,7 @@ int mppi_shard_update_async(mppi_ctx *c, const double *d_partials, int n_ranks, 
   const NvtxRange range("mppi_shard_update_async (shard merge + update)");
   if (!c || !d_partials || n_ranks < 1 || n_ranks > 4096) return MPPI_EINVAL;
   MPPI_TRY(check_ready(c));
-  MPPI_TRY(c->cuda(launch_shard_update(c->p, d_partials, n_ranks, c->d_U, d_u0_out ? d_u0_out : c->d_u0, c->d_dU,
+  MPPI_TRY(c->cuda(launch_shard_update(c->p, d_partials, n_ranks, c->U_cur(), d_u0_out ? d_u0_out : c->d_u0, c->d_dU,
                                        c->d_dbg, c->stream),
                    "shard update"));
   return MPPI_OK;

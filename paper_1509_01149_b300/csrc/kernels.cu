@@ -123,30 +123,27 @@ __global__ void __launch_bounds__(BLK) k_rollout_quad_lanes(const CtrlParams p, 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 merge of block partials + update of U (+ the shift, fused, in one cluster)
+// FP64 merge of block partials + update of U (+ the shift, into the other control buffer)
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int kMergePrefetch = 16;  // block partials per thread loaded before the reductions
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 }  // namespace
 
 // One CTA per 32 outputs (i, j), warp r = range r of the block partials (merge_common.cuh:
 // the fixed arithmetic order every path shares).  The CTA's loads (block partials, the first
-// kMergePrefetch block sums of each lane's range) are issued first, so their latency is paid
-// once; then rho/k* (argmin), the block scales, eta (warp 0, FP64) and the double-FP32 range
-// sums, combined in range order by warp 0.
-// SHIFT: the grid is one thread-block cluster (all outputs in <= 8 CTAs); after the update
-// the cluster barrier makes every CTA's new U visible, each CTA reads its shifted values,
-// a second barrier separates those reads from the in-place writes, and CTA 0 advances the
-// iteration counter (Algorithm 1's shift, otherwise a kernel of its own).
+// kMergePrefetch block sums of each lane's range, the controls it updates) are issued first,
+// so their latency is paid once; then rho/k* (argmin), the block scales, eta (warp 0, FP64)
+// and the double-FP32 range sums, combined in range order by warp 0.
+// SHIFT: Algorithm 1's shift in the same launch.  The controls live in two buffers that the
+// shifts alternate: the update reads U and writes the shifted result, u_{i+1} + du_{i+1} into
+// slot i and u_init into the last step, to U_next, so no CTA reads what another writes;
+// CTA 0 advances the iteration counter.
 template <bool SHIFT>
 __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM, int m, float inv_lambda,
                                                                 const float *__restrict__ part_sums,
                                                                 const BlockPartial *__restrict__ part,
-                                                                float *__restrict__ U, float *__restrict__ u0_out,
+                                                                float *__restrict__ U, float *__restrict__ U_next,
+                                                                float *__restrict__ u0_out,
                                                                 float *__restrict__ dU_dbg,
                                                                 StepDebug *__restrict__ dbg,
                                                                 const float *__restrict__ u_init,
@@ -174,6 +171,9 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
     const int b = b0 + j;
     pre[j] = (o < TM && b < b1) ? part_sums[static_cast<size_t>(b) * TM + o] : 0.0f;
   }
+  const bool own = warp == 0 && o < TM;  // warp 0 writes the CTA's outputs
+  const float u_old = own ? U[o] : 0.0f;
+  const float u_last = (SHIFT && warp == 0 && o < m) ? u_init[o] : 0.0f;
   float v = INFINITY;
   int idx = INT_MAX;
   for (int b = tid; b < nblk; b += kMergeThreads) {
@@ -225,15 +225,21 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
       df_add_prod(acc, s_sc[b], part_sums[static_cast<size_t>(b) * TM + o]);
   s_part[warp][lane] = acc;
   __syncthreads();
-  if (warp == 0 && o < TM) {
+  if (own) {
     DF tot = s_part[0][lane];
 #pragma unroll
     for (int r = 1; r < kMergeRanges; ++r) df_add(tot, s_part[r][lane]);
     const double du = merge_du(tot, s_inv_eta);
-    const float un = U[o] + static_cast<float>(du);
-    U[o] = un;
+    const float un = u_old + static_cast<float>(du);
     dU_dbg[o] = static_cast<float>(du);
     if (o < m) u0_out[o] = un;
+    if (!SHIFT) {
+      U[o] = un;
+    } else if (o >= m) {
+      U_next[o - m] = un;
+    } else {
+      U_next[TM - m + o] = u_last;
+    }
   }
   // u0 is final: raise the host's flag (u0 in host memory before it) ahead of the rest
   if (u0_ready != nullptr && blockIdx.x == 0 && warp == 0) {
@@ -243,14 +249,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
       *reinterpret_cast<volatile unsigned int *>(u0_ready) = 1u;
     }
   }
-  if (SHIFT) {
-    cluster_sync_all();  // every CTA's updated U visible to the cluster
-    float sh = 0.0f;
-    if (warp == 0 && o < TM) sh = (o + m < TM) ? U[o + m] : u_init[o - (TM - m)];
-    cluster_sync_all();  // all shifted values read before any is overwritten
-    if (warp == 0 && o < TM) U[o] = sh;
-    if (blockIdx.x == 0 && tid == 0) st->counter += 1u;
-  }
+  if (SHIFT && blockIdx.x == 0 && tid == 0) st->counter += 1u;
 }
 
 // ---------------------------------------------------------------------------
@@ -380,15 +379,16 @@ __global__ void __launch_bounds__(256) k_shard_update(const double *__restrict__
 //   rho_i = min_b rho_{b,i},  s_b = exp(-(rho_{b,i} - rho_i)/lambda) (FP32),
 //   eta_i = sum_b s_b eta_{b,i},  N_o = sum_b s_b part_b[o]   (double-FP32, warps combined in
 //   order), du_o = N_o / eta_i (FP64), U[o] += du_o.
-// CTA 0 also reports step 0's (rho, k*, eta) from the BlockPartials.  SHIFT: the grid is one
-// thread-block cluster and Algorithm 1's shift follows the update as in k_merge_update.
+// CTA 0 also reports step 0's (rho, k*, eta) from the BlockPartials.  SHIFT: Algorithm 1's
+// shift as in k_merge_update (the shifted update written to the other control buffer).
 template <bool SHIFT>
 __global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, int m, float inv_lambda,
                                                                const float *__restrict__ part_sums,
                                                                const float *__restrict__ part_rho,
                                                                const DF *__restrict__ part_eta,
                                                                const BlockPartial *__restrict__ part,
-                                                               float *__restrict__ U, float *__restrict__ u0_out,
+                                                               float *__restrict__ U, float *__restrict__ U_next,
+                                                               float *__restrict__ u0_out,
                                                                float *__restrict__ dU_dbg,
                                                                StepDebug *__restrict__ dbg,
                                                                const float *__restrict__ u_init,
@@ -417,6 +417,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, 
     ps[j] = in ? part_sums[static_cast<size_t>(b) * TM + o] : 0.0f;
     pe[j] = in ? part_eta[static_cast<size_t>(b) * T + i] : DF{0.0f, 0.0f};
   }
+  const float u_old = (warp == 0 && live) ? U[o] : 0.0f;
+  const float u_last = (SHIFT && warp == 0 && o < m) ? u_init[o] : 0.0f;
   float r = INFINITY;
 #pragma unroll
   for (int j = 0; j < kMergePrefetch; ++j) r = fminf(r, pr[j]);
@@ -457,10 +459,16 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, 
     }
     const double eta = static_cast<double>(et.hi) + static_cast<double>(et.lo);
     const double du = eta > 0.0 ? (static_cast<double>(at.hi) + static_cast<double>(at.lo)) / eta : 0.0;
-    const float un = U[o] + static_cast<float>(du);
-    U[o] = un;
+    const float un = u_old + static_cast<float>(du);
     dU_dbg[o] = static_cast<float>(du);
     if (o < m) u0_out[o] = un;
+    if (!SHIFT) {
+      U[o] = un;
+    } else if (o >= m) {
+      U_next[o - m] = un;
+    } else {
+      U_next[TM - m + o] = u_last;
+    }
   }
   // u0 is final: raise the host's flag (u0 in host memory before it) ahead of the rest
   if (u0_ready != nullptr && blockIdx.x == 0 && warp == 0) {
@@ -512,26 +520,18 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_to_go(int nblk, int T, 
       dbg->eta = eta;
     }
   }
-  if (SHIFT) {
-    cluster_sync_all();  // every CTA's updated U visible to the cluster
-    float sh = 0.0f;
-    if (warp == 0 && live) sh = (o + m < TM) ? U[o + m] : u_init[o - (TM - m)];
-    cluster_sync_all();  // all shifted values read before any is overwritten
-    if (warp == 0 && live) U[o] = sh;
-    if (blockIdx.x == 0 && tid == 0) st->counter += 1u;
-  }
+  if (SHIFT && blockIdx.x == 0 && tid == 0) st->counter += 1u;
 }
 
 // ---------------------------------------------------------------------------
-// shift (Algorithm 1): u_i <- u_{i+1}, u_{T-1} <- u_init; counter += 1
+// shift (Algorithm 1): u_i <- u_{i+1}, u_{T-1} <- u_init; counter += 1.  From U into the
+// other control buffer U_next.
 // ---------------------------------------------------------------------------
-__global__ void k_shift(float *__restrict__ U, const float *__restrict__ u_init, int TM, int m,
-                        CtrlState *__restrict__ st) {
-  extern __shared__ float s_u[];
-  for (int o = threadIdx.x; o < TM; o += blockDim.x) s_u[o] = U[o];
-  __syncthreads();
-  for (int o = threadIdx.x; o < TM; o += blockDim.x) U[o] = (o + m < TM) ? s_u[o + m] : u_init[o - (TM - m)];
-  if (threadIdx.x == 0) st->counter += 1u;
+__global__ void k_shift(const float *__restrict__ U, float *__restrict__ U_next, const float *__restrict__ u_init,
+                        int TM, int m, CtrlState *__restrict__ st) {
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < TM; o += gridDim.x * blockDim.x)
+    U_next[o] = (o + m < TM) ? U[o + m] : u_init[o - (TM - m)];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->counter += 1u;
 }
 
 // ---------------------------------------------------------------------------
@@ -932,35 +932,28 @@ cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const fl
 cudaError_t launch_merge_to_go(int nblk, const CtrlParams &p, const float *part_sums, const float *part_rho,
                                const DF *part_eta, const BlockPartial *part, float *U, float *u0_out,
                                float *dU_dbg, StepDebug *dbg, cudaStream_t s, bool shift, const float *u_init,
-                               CtrlState *st, unsigned int *u0_ready) {
+                               CtrlState *st, float *U_next, unsigned int *u0_ready) {
   const int TM = p.T * p.m;
-  const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
-  if (shift && grid > kMergeClusterMax) return cudaErrorInvalidValue;
+  if (shift && (U_next == nullptr || U_next == U || u_init == nullptr || st == nullptr)) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.gridDim = dim3((TM + kMergeOutputs - 1) / kMergeOutputs, 1, 1);
   cfg.blockDim = dim3(kMergeThreads, 1, 1);
   cfg.stream = s;
-  cudaLaunchAttribute attr[2];
-  int na = 0;
-  attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[na++].val.programmaticStreamSerializationAllowed = 1;
-  if (shift) {
-    attr[na].id = cudaLaunchAttributeClusterDimension;
-    attr[na].val.clusterDim.x = grid;
-    attr[na].val.clusterDim.y = 1;
-    attr[na++].val.clusterDim.z = 1;
-  }
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = na;
+  cfg.numAttrs = 1;
   const int T = p.T, m = p.m;
   const float il = p.inv_lambda;
   if (shift)
     return cudaLaunchKernelEx(&cfg, k_merge_to_go<true>, nblk, T, m, il, part_sums, part_rho, part_eta, part, U,
-                              u0_out, dU_dbg, dbg, u_init, st, u0_ready);
+                              U_next, u0_out, dU_dbg, dbg, u_init, st, u0_ready);
+  float *no_next = nullptr;
   const float *no_uinit = nullptr;
   CtrlState *no_st = nullptr;
   return cudaLaunchKernelEx(&cfg, k_merge_to_go<false>, nblk, T, m, il, part_sums, part_rho, part_eta, part, U,
-                            u0_out, dU_dbg, dbg, no_uinit, no_st, u0_ready);
+                            no_next, u0_out, dU_dbg, dbg, no_uinit, no_st, u0_ready);
 }
 
 cudaError_t prepare_kernels() {
@@ -1012,17 +1005,20 @@ cudaError_t prepare_kernels() {
   return cudaSuccess;
 }
 
-cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
-                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s,
-                                unsigned int *u0_ready) {
+namespace {
+// The path-weighting merge: one CTA per 32 outputs, launched as a programmatic dependent of
+// the rollout (its CTAs start while the rollout drains and wait, griddepcontrol.wait, for its
+// results).  No thread-block cluster: the shift writes the other control buffer.
+template <bool SHIFT>
+cudaError_t launch_merge(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part, float *U,
+                         float *U_next, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
+                         CtrlState *st, cudaStream_t s, unsigned int *u0_ready) {
   const int TM = p.T * p.m;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((TM + kMergeOutputs - 1) / kMergeOutputs, 1, 1);
   cfg.blockDim = dim3(kMergeThreads, 1, 1);
   cfg.dynamicSmemBytes = (sizeof(double) + sizeof(float)) * static_cast<size_t>(nblk);
   cfg.stream = s;
-  // programmatic dependent launch: the merge's CTAs start while the rollout drains and wait
-  // (griddepcontrol.wait) for its results
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -1030,10 +1026,15 @@ cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part
   cfg.numAttrs = 1;
   const int m = p.m;
   const float il = p.inv_lambda;
-  const float *no_uinit = nullptr;
-  CtrlState *no_st = nullptr;
-  return cudaLaunchKernelEx(&cfg, k_merge_update<false>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,
-                            no_uinit, no_st, u0_ready);
+  return cudaLaunchKernelEx(&cfg, k_merge_update<SHIFT>, nblk, TM, m, il, part_sums, part, U, U_next, u0_out, dU_dbg,
+                            dbg, u_init, st, u0_ready);
+}
+}  // namespace
+
+cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
+                                float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s,
+                                unsigned int *u0_ready) {
+  return launch_merge<false>(nblk, p, part_sums, part, U, nullptr, u0_out, dU_dbg, dbg, nullptr, nullptr, s, u0_ready);
 }
 
 cudaError_t launch_shard_partial(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
@@ -1053,39 +1054,18 @@ cudaError_t launch_shard_update(const CtrlParams &p, const double *all, int n_ra
   return cudaGetLastError();
 }
 
-bool merge_shift_fusable(const CtrlParams &p) {
-  return (p.T * p.m + kMergeOutputs - 1) / kMergeOutputs <= kMergeClusterMax;
-}
-
 cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
-                                      float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
-                                      CtrlState *st, cudaStream_t s, unsigned int *u0_ready) {
-  const int TM = p.T * p.m;
-  const int grid = (TM + kMergeOutputs - 1) / kMergeOutputs;
-  if (grid > kMergeClusterMax) return cudaErrorInvalidValue;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid, 1, 1);
-  cfg.blockDim = dim3(kMergeThreads, 1, 1);
-  cfg.dynamicSmemBytes = (sizeof(double) + sizeof(float)) * static_cast<size_t>(nblk);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = grid;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 2;
-  const int m = p.m;
-  const float il = p.inv_lambda;
-  return cudaLaunchKernelEx(&cfg, k_merge_update<true>, nblk, TM, m, il, part_sums, part, U, u0_out, dU_dbg, dbg,
-                            u_init, st, u0_ready);
+                                      float *U, float *U_next, float *u0_out, float *dU_dbg, StepDebug *dbg,
+                                      const float *u_init, CtrlState *st, cudaStream_t s, unsigned int *u0_ready) {
+  if (U_next == nullptr || U_next == U || u_init == nullptr || st == nullptr) return cudaErrorInvalidValue;
+  return launch_merge<true>(nblk, p, part_sums, part, U, U_next, u0_out, dU_dbg, dbg, u_init, st, s, u0_ready);
 }
 
-cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s) {
+cudaError_t launch_shift(const CtrlParams &p, const float *U, float *U_next, const float *u_init, CtrlState *st,
+                         cudaStream_t s) {
+  if (U_next == nullptr || U_next == U) return cudaErrorInvalidValue;
   const int TM = p.T * p.m;
-  k_shift<<<1, 1024, sizeof(float) * TM, s>>>(U, u_init, TM, p.m, st);
+  k_shift<<<(TM + 1023) / 1024, 1024, 0, s>>>(U, U_next, u_init, TM, p.m, st);
   return cudaGetLastError();
 }
 

@@ -48,13 +48,13 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
 cudaError_t launch_merge_update(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
                                 float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, cudaStream_t s,
                                 unsigned int *u0_ready = nullptr);
-// The merge and the shift of Algorithm 1 in one launch (a thread-block cluster of one CTA
-// per 32 outputs), when the outputs fit in kMergeClusterMax CTAs.
-constexpr int kMergeClusterMax = 8;
-bool merge_shift_fusable(const CtrlParams &p);
+// The merge and the shift of Algorithm 1 in one launch.  The controls live in two buffers
+// that the shifts alternate: U (read) and U_next (written with the shifted update, u_init in
+// the last step); U_next must not alias U.
 cudaError_t launch_merge_update_shift(int nblk, const CtrlParams &p, const float *part_sums, const BlockPartial *part,
-                                      float *U, float *u0_out, float *dU_dbg, StepDebug *dbg, const float *u_init,
-                                      CtrlState *st, cudaStream_t s, unsigned int *u0_ready = nullptr);
+                                      float *U, float *U_next, float *u0_out, float *dU_dbg, StepDebug *dbg,
+                                      const float *u_init, CtrlState *st, cudaStream_t s,
+                                      unsigned int *u0_ready = nullptr);
 // Cost-to-go weighting (Eq. App_PI per time step): block shape (the car's warp roles,
 // kFusedBlockCarWs, when their shared memory fits kBigWsSmemLimit; else 128 or 64 samples,
 // du and the step costs in shared memory; 0 if they do not fit), the rollout with per-step
@@ -64,16 +64,18 @@ int fused_block_size_to_go(int sys, const CtrlParams &p);
 cudaError_t launch_rollout_to_go(int sys, int blk, const CtrlParams &p, const float *x0, const CtrlState *st,
                                  const float *U, float *S, float *part_sums, BlockPartial *part, float *part_rho,
                                  DF *part_eta, cudaStream_t s);
-// The merge of the per-step partials and the update; with `shift` (T*m <= 32 kMergeClusterMax)
-// also Algorithm 1's shift in the same launch (one thread-block cluster).  u0_ready as for
+// The merge of the per-step partials and the update; with `shift` also Algorithm 1's shift in
+// the same launch, from U into U_next as for launch_merge_update_shift.  u0_ready as for
 // launch_merge_update.
 cudaError_t launch_merge_to_go(int nblk, const CtrlParams &p, const float *part_sums, const float *part_rho,
                                const DF *part_eta, const BlockPartial *part, float *U, float *u0_out,
                                float *dU_dbg, StepDebug *dbg, cudaStream_t s, bool shift = false,
-                               const float *u_init = nullptr, CtrlState *st = nullptr,
+                               const float *u_init = nullptr, CtrlState *st = nullptr, float *U_next = nullptr,
                                unsigned int *u0_ready = nullptr);
-// Shift of Algorithm 1 and iteration counter increment.
-cudaError_t launch_shift(const CtrlParams &p, float *U, const float *u_init, CtrlState *st, cudaStream_t s);
+// Shift of Algorithm 1 from U into the other control buffer U_next, and the iteration counter
+// increment.
+cudaError_t launch_shift(const CtrlParams &p, const float *U, float *U_next, const float *u_init, CtrlState *st,
+                         cudaStream_t s);
 
 // Learned car dynamics (mlp_rollout.cu) -----------------------------------------
 constexpr size_t kMlpSmemLimit = 225 * 1024;

@@ -276,9 +276,9 @@ def test_graph_iteration_equals_step_and_shift(N):
 @pytest.mark.parametrize("system,K,T", [(W.CAR, 40000, 33), (W.CAR, 32768, 100), (W.CAR, 65, 1),
                                         (W.CAR, 16384, 100), (W.QUAD, 8192, 150), (W.CAR, 1024, 1000)])
 def test_merge_with_shift_equals_merge_then_shift_kernel(N, system, K, T):
-    """The iteration graph runs the merge and the shift in one thread-block cluster when
-    T*m <= 256 (else the merge, then the shift kernel: the quadrotor at T = 150, the car at
-    T = 1000); step_async runs the merge alone, then mppi_shift's kernel.  With up to 313 block
+    """The iteration graph runs the merge and the shift in one launch (the shifted update written
+    to the other control buffer); step_async runs the merge alone, then mppi_shift's kernel.
+    With up to 313 block
     partials (ranges of 40 blocks, beyond the merge's register prefetch) the fixed reduction
     order gives the same controls, u0, debug values and counter bit for bit, over three
     iterations."""
@@ -300,11 +300,58 @@ def test_merge_with_shift_equals_merge_then_shift_kernel(N, system, K, T):
     assert a.get_iteration() == b.get_iteration() == 3
 
 
+def test_shifts_through_every_entry_point_keep_one_control_sequence(N):
+    """Every shift makes the other of the two control buffers current.  Shifting through each
+    entry point in turn (the iteration graph, mppi_step_shift's graph, the shift kernel after
+    mppi_step_async, the plain launches on the legacy path's order), with get/set_controls and
+    a graph rebuild (set_weighting) while the second buffer is current, gives the same u0,
+    controls and counter bit for bit as mppi_step_async followed by mppi_shift throughout."""
+    import torch
+    cfg = W.config(W.CAR, K=4096, T=50)
+    a, b = P.make_controller(cfg), P.make_controller(cfg)
+    x = np.asarray(cfg["x0"], np.float32)
+    m = a.m
+    dx = torch.tensor(x, device="cuda")
+    ua, ub = torch.zeros(m, device="cuda"), torch.zeros(m, device="cuda")
+    for it in range(9):
+        xs = x + np.float32(0.01 * it)
+        dx.copy_(torch.from_numpy(xs))
+        torch.cuda.synchronize()  # the controllers run on streams of their own
+        b.step_async(dx.data_ptr(), ub.data_ptr())
+        b.shift()
+        kind = it % 4
+        if kind == 0:
+            a.iterate_async(dx.data_ptr(), ua.data_ptr())
+        elif kind == 1:
+            ua.copy_(torch.from_numpy(a.step_shift(xs)))
+        elif kind == 2:
+            a.step_async(dx.data_ptr(), ua.data_ptr())
+            a.shift()
+        else:
+            a.set_controls(a.get_controls())   # a round trip through the current buffer
+            a.set_weighting(N.MPPI_WEIGHT_PATH)  # marks every graph for a rebuild
+            a.iterate_async(dx.data_ptr(), ua.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(ua, ub), it
+        assert np.array_equal(a.get_controls(), b.get_controls()), it
+    assert a.get_iteration() == b.get_iteration() == 9
+    # set_controls writes the current buffer: both continue from the same sequence
+    U = np.asarray(cfg["U"], np.float32)
+    a.set_controls(U)
+    b.set_controls(U)
+    a.iterate_async(dx.data_ptr(), ua.data_ptr())
+    b.step_async(dx.data_ptr(), ub.data_ptr())
+    b.shift()
+    torch.cuda.synchronize()
+    assert torch.equal(ua, ub)
+    assert np.array_equal(a.get_controls(), b.get_controls())
+
+
 @pytest.mark.parametrize("system,T", [(W.CAR, 40), (W.QUAD, 80), (W.CARTPOLE, 30)])
 def test_step_shift_equals_step_then_shift(N, system, T):
-    """mppi_step_shift (host buffers; one graph with the shift in the update's launch when
-    T*m <= 256, else a shift kernel after it) gives the same u0, controls and counter as
-    mppi_step followed by mppi_shift, over three iterations from changing states."""
+    """mppi_step_shift (host buffers; one graph with the shift in the update's launch) gives the
+    same u0, controls and counter as mppi_step followed by mppi_shift, over three iterations
+    from changing states."""
     cfg = W.config(system, K=2000, T=T)
     a, b = P.make_controller(cfg), P.make_controller(cfg)
     x = np.asarray(cfg["x0"], np.float32)
@@ -365,8 +412,8 @@ def test_cost_to_go_iteration(N, system, K, T, lam):
 @pytest.mark.parametrize("system,T", [(W.CAR, 100), (W.QUAD, 60), (W.CARTPOLE, 300)])
 def test_cost_to_go_step_shift_equals_step_then_shift(N, system, T):
     """With the cost-to-go weighting, mppi_step_shift runs the per-step merge and the shift in
-    one thread-block cluster when T*m <= 256 (else the merge, then the shift kernel); mppi_step
-    then mppi_shift gives the same u0, controls and counter bit for bit, over three iterations."""
+    one launch; mppi_step then mppi_shift gives the same u0, controls and counter bit for bit,
+    over three iterations."""
     cfg = W.config(system, K=2048, T=T)
     a, b = P.make_controller(cfg), P.make_controller(cfg)
     for c in (a, b):
