@@ -132,14 +132,14 @@ constexpr int kMergePrefetch = 16;  // block partials per thread loaded before t
 // One CTA per 32 outputs (i, j), warp r = range r of the block partials (merge_common.cuh:
 // the fixed arithmetic order every path shares).  The CTA's loads (block partials, the first
 // kMergePrefetch block sums of each lane's range, the controls it updates) are issued first,
-// so their latency is paid once; then rho/k* (argmin), the block scales, eta (warp 0, FP64)
-// and the double-FP32 range sums, combined in range order by warp 0.
+// so their latency is paid once; then rho/k* (argmin), the block scales, and beside each other
+// eta (a ninth warp, FP64) and the double-FP32 range sums, combined in range order by warp 0.
 // SHIFT: Algorithm 1's shift in the same launch.  The controls live in two buffers that the
 // shifts alternate: the update reads U and writes the shifted result, u_{i+1} + du_{i+1} into
 // slot i and u_init into the last step, to U_next, so no CTA reads what another writes;
 // CTA 0 advances the iteration counter.
 template <bool SHIFT>
-__global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM, int m, float inv_lambda,
+__global__ void __launch_bounds__(kMergeUpdateThreads) k_merge_update(int nblk, int TM, int m, float inv_lambda,
                                                                 const float *__restrict__ part_sums,
                                                                 const BlockPartial *__restrict__ part,
                                                                 float *__restrict__ U, float *__restrict__ U_next,
@@ -149,17 +149,18 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
                                                                 const float *__restrict__ u_init,
                                                                 CtrlState *__restrict__ st,
                                                                 unsigned int *__restrict__ u0_ready) {
-  constexpr int NW = kMergeThreads / 32;
-  static_assert(NW == kMergeRanges, "one warp per range of block partials");
+  constexpr int NW = kMergeRanges;             // warps 0..NW-1: one range of block partials each
+  constexpr int NT = kMergeUpdateThreads;      // warp NW: the normaliser
+  static_assert(NT == 32 * (NW + 1), "range warps + the normaliser's warp");
   extern __shared__ double s_eb[];  // [nblk] eta_b, then [nblk] floats: rho_b, then s_b
   float *s_sc = reinterpret_cast<float *>(s_eb + nblk);
-  __shared__ float s_rho[NW];
-  __shared__ int s_k[NW];
+  __shared__ float s_rho[NW + 1];
+  __shared__ int s_k[NW + 1];
   __shared__ DF s_part[NW][kMergeOutputs];
   __shared__ double s_inv_eta;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int o = blockIdx.x * kMergeOutputs + lane;
-  const int L = merge_range_len(nblk), b0 = min(nblk, warp * L), b1 = min(nblk, b0 + L);
+  const int L = merge_range_len(nblk), b0 = min(nblk, warp * L), b1 = warp < NW ? min(nblk, b0 + L) : b0;
   // launched as a programmatic dependent of the rollout: its partials are complete and
   // visible after this wait (a no-op for an ordinary launch)
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   const float u_last = (SHIFT && warp == 0 && o < m) ? u_init[o] : 0.0f;
   float v = INFINITY;
   int idx = INT_MAX;
-  for (int b = tid; b < nblk; b += kMergeThreads) {
+  for (int b = tid; b < nblk; b += NT) {
     const BlockPartial bp = part[b];
     s_eb[b] = bp.eta;
     s_sc[b] = bp.rho;
@@ -192,8 +193,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   }
   __syncthreads();
   if (warp == 0) {
-    float vv = lane < NW ? s_rho[lane] : INFINITY;
-    int ii = lane < NW ? s_k[lane] : INT_MAX;
+    float vv = lane <= NW ? s_rho[lane] : INFINITY;
+    int ii = lane <= NW ? s_k[lane] : INT_MAX;
     warp_argmin(vv, ii);
     if (lane == 0) {
       s_rho[0] = vv;
@@ -202,9 +203,10 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   }
   __syncthreads();
   const float rho = s_rho[0];
-  for (int b = tid; b < nblk; b += kMergeThreads) s_sc[b] = merge_scale(s_sc[b], rho, inv_lambda);
+  for (int b = tid; b < nblk; b += NT) s_sc[b] = merge_scale(s_sc[b], rho, inv_lambda);
   __syncthreads();
-  if (warp == 0) {
+  // the normaliser (FP64, on B300's slow FP64 pipe) on its own warp, beside the range sums
+  if (warp == NW) {
     const double eta = merge_eta_warp(s_sc, s_eb, nblk, lane);
     if (lane == 0) {
       s_inv_eta = eta > 0.0 ? 1.0 / eta : 0.0;
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge_update(int nblk, int TM
   if (o < TM)
     for (int b = b0 + kMergePrefetch; b < b1; ++b)
       df_add_prod(acc, s_sc[b], part_sums[static_cast<size_t>(b) * TM + o]);
-  s_part[warp][lane] = acc;
+  if (warp < NW) s_part[warp][lane] = acc;
   __syncthreads();
   if (own) {
     DF tot = s_part[0][lane];
@@ -1016,7 +1018,7 @@ cudaError_t launch_merge(int nblk, const CtrlParams &p, const float *part_sums, 
   const int TM = p.T * p.m;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((TM + kMergeOutputs - 1) / kMergeOutputs, 1, 1);
-  cfg.blockDim = dim3(kMergeThreads, 1, 1);
+  cfg.blockDim = dim3(kMergeUpdateThreads, 1, 1);
   cfg.dynamicSmemBytes = (sizeof(double) + sizeof(float)) * static_cast<size_t>(nblk);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];

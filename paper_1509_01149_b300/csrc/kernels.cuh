@@ -16,6 +16,7 @@ constexpr int kFusedBlockQuadWs = 1025;    // code for "quadrotor, 64 samples, t
 constexpr int kQuadLanesBlock = 64, kQuadLanes = 2;
 constexpr int kMinBlockSamples = kQuadLanesBlock / kQuadLanes;  // fewest samples per block of any shape
 constexpr int kMergeThreads = 256;
+constexpr int kMergeUpdateThreads = kMergeThreads + 32;  // k_merge_update: + the normaliser's warp
 constexpr int kMergeOutputs = 32;       // outputs (i, j) per merge block
 constexpr size_t kFusedSmemLimit = 200 * 1024;
 // the warp-role kernels whose per-step tables (the car's step costs, the quadrotor's
