@@ -93,12 +93,19 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 // H row `row`, columns [c0, c0 + 32) = tanh(scale * v + bias) in the tile format (v: the 32
-// accumulator columns of this thread's lane, already loaded from TMEM)
+// accumulator columns of this thread's lane, already loaded from TMEM).  The scale-and-bias
+// FMAs go two columns per packed instruction (the same roundings as one fmaf per column).
 template <int E>
 __device__ __forceinline__ void hidden_store(float v[32], const float *bias, float scale, unsigned char *smem, int row,
                                              int c0) {
+  const float2 sc = make_float2(scale, scale);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = tc::tanh_approx(fmaf(v[j], scale, bias[c0 + j]));
+  for (int j = 0; j < 32; j += 2) {
+    const float2 b = *reinterpret_cast<const float2 *>(bias + c0 + j);
+    const float2 z = fma2(make_float2(v[j], v[j + 1]), sc, b);
+    v[j] = tc::tanh_approx(z.x);
+    v[j + 1] = tc::tanh_approx(z.y);
+  }
   if (E == 2) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
