@@ -1201,8 +1201,8 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "k_rollout_car_ws<128> (core, noise and pose warps per 128 samples)",
                      "flops_per_rollout_step": flops_step,
-                     "flops_basis": ("ncu FP32 thread-instruction counters of the kernel, 2 ffma + fadd + fmul per "
-                                     "rollout-step (profiles/rollout_car_ws_k16384.json)" if counted else
+                     "flops_basis": ("ncu FP32 thread-instruction counters of the kernel, 2 ffma + fadd + fmul (+ 4 ffma2 + 2 fadd2 + "
+                                     "2 fmul2, packed) per rollout-step (profiles/rollout_car_ws_k16384.json)" if counted else
                                      "formula count (no counter record for the current sources)"),
                      "flops_per_rollout_step_formula": formula_flops,
                      "frac_formula": formula_flops * K_SAMPLES * T_STEPS / roll_mean_s / 1e12 / peak,

@@ -74,35 +74,6 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
-// P(v) and Q(v), coefficients highest degree first (degree at most 7), by Estrin's scheme:
-// the pairs c_2j + c_2j+1 v, then pairs of those joined by v^2, then by v^4, so that the
-// dependency chain is four FMAs deep instead of Horner's degree-many.  P and Q advance
-// together, one in each half of the packed instructions: (P(v), Q(v)).
-template <int NP, int NQ>
-__device__ __forceinline__ float2 estrin_pq(const float (&P)[NP], const float (&Q)[NQ], float v) {
-  constexpr int D = (NP > NQ ? NP : NQ) - 1;  // the larger degree
-  static_assert(D >= 2 && D <= 7, "degree 2 to 7");
-  // the coefficient pair of v^j (zero above a polynomial's degree)
-  auto c = [&](int j) { return make_float2(j < NP ? P[NP - 1 - j] : 0.0f, j < NQ ? Q[NQ - 1 - j] : 0.0f); };
-  const float2 v1 = make_float2(v, v);
-  const float2 v2 = mul2(v1, v1);
-  const float2 a0 = fma2(c(1), v1, c(0));
-  const float2 a1 = D >= 3 ? fma2(c(3), v1, c(2)) : c(2);
-  const float2 b0 = fma2(a1, v2, a0);
-  if constexpr (D <= 3) {
-    return b0;
-  } else {
-    const float2 v4 = mul2(v2, v2);
-    const float2 a2 = D >= 5 ? fma2(c(5), v1, c(4)) : c(4);
-    if constexpr (D <= 5) {
-      return fma2(a2, v4, b0);
-    } else {
-      const float2 a3 = D >= 7 ? fma2(c(7), v1, c(6)) : c(6);
-      return fma2(fma2(a3, v2, a2), v4, b0);
-    }
-  }
-}
-
 // Kahan-compensated FP32 accumulator for the path cost.
 struct KahanSum {
   float s = 0.0f, c = 0.0f;

@@ -175,18 +175,25 @@ struct Car {
   // The shape sin(C atan z), z = B alpha, is evaluated on the whole real line through
   // v = |z| / (1 + |z|) in [0, 1], where it is analytic: sign(z) v P(v) / Q(v), a rational
   // fitted towards minimax (maximum absolute error 3.0e-7 in exact arithmetic, ~6.5e-7 in
-  // FP32; tyre_shape_fit.py prints the coefficients).  Two reciprocals and P and Q by Estrin's
-  // scheme in packed FMAs (estrin_pq), with no branch, replace an arctangent and a sine on the
-  // recurrence's critical path.  |z| is capped
+  // FP32; tyre_shape_fit.py prints the coefficients).  Two reciprocals and ten FMAs with no
+  // branch replace an arctangent and a sine on the recurrence's critical path.  |z| is capped
   // at 1e30 (the shape equals its limit sin(C pi / 2) there to FP32 precision; the cap keeps
   // the fast reciprocal in range); NaN propagates.
   __device__ __forceinline__ static float tyre_shape(float z) {
     const float a = fabsf(z) > 1.0e30f ? 1.0e30f : fabsf(z);
     const float v = __fdividef(a, 1.0f + a);
-    constexpr float P[] = {-1.802042631e+00f, 2.115236191e+00f, 2.735651234e-01f, -1.707349900e+00f, 1.799983406e+00f};
-    constexpr float Q[] = {2.216846433e+00f, -2.120366621e+00f, 1.076769485e+00f, 1.973980183e+00f, -1.948672322e+00f, 1.000000000e+00f};
-    const float2 pq = estrin_pq(P, Q, v);
-    return copysignf(__fdividef(v * pq.x, pq.y), z);
+    float P = -1.802042631e+00f;
+    P = fmaf(P, v, 2.115236191e+00f);
+    P = fmaf(P, v, 2.735651234e-01f);
+    P = fmaf(P, v, -1.707349900e+00f);
+    P = fmaf(P, v, 1.799983406e+00f);
+    float Q = 2.216846433e+00f;
+    Q = fmaf(Q, v, -2.120366621e+00f);
+    Q = fmaf(Q, v, 1.076769485e+00f);
+    Q = fmaf(Q, v, 1.973980183e+00f);
+    Q = fmaf(Q, v, -1.948672322e+00f);
+    Q = fmaf(Q, v, 1.000000000e+00f);
+    return copysignf(__fdividef(v * P, Q), z);
   }
   // The same force as a function of t = tan(alpha) = n / d (d > 0, so |alpha| < pi/2):
   // sin(C atan(B atan t)) = sign(n) v P(v) / Q(v) with v = |t| / (1 + |t|) = |n| / (|n| + d),
@@ -196,10 +203,21 @@ struct Car {
   __device__ __forceinline__ static float slip_shape(float n, float d) {
     const float an = fabsf(n);
     const float v = __fdividef(an, an + d);
-    constexpr float P[] = {8.201814610e+00f, 6.672181936e+01f, 3.717660575e+01f, 4.971201143e+00f, 2.782720545e+01f, 1.013812583e+01f, 7.200033913e+00f};
-    constexpr float Q[] = {2.088930100e+02f, -5.017322148e+01f, 8.035395784e+01f, 3.080427926e+01f, 1.677532802e+01f, 4.081411398e-01f, 1.000000000e+00f};
-    const float2 pq = estrin_pq(P, Q, v);
-    return copysignf(__fdividef(v * pq.x, pq.y), n);
+    float P = 8.201814610e+00f;
+    P = fmaf(P, v, 6.672181936e+01f);
+    P = fmaf(P, v, 3.717660575e+01f);
+    P = fmaf(P, v, 4.971201143e+00f);
+    P = fmaf(P, v, 2.782720545e+01f);
+    P = fmaf(P, v, 1.013812583e+01f);
+    P = fmaf(P, v, 7.200033913e+00f);
+    float Q = 2.088930100e+02f;
+    Q = fmaf(Q, v, -5.017322148e+01f);
+    Q = fmaf(Q, v, 8.035395784e+01f);
+    Q = fmaf(Q, v, 3.080427926e+01f);
+    Q = fmaf(Q, v, 1.677532802e+01f);
+    Q = fmaf(Q, v, 4.081411398e-01f);
+    Q = fmaf(Q, v, 1.000000000e+00f);
+    return copysignf(__fdividef(v * P, Q), n);
   }
   // The shape sin(C atan(B theta)) of a slip angle of magnitude theta in [0, pi] given as a
   // direction (n, d), a positive multiple of (sin alpha, cos alpha), signed like n.  Through the
@@ -215,10 +233,23 @@ struct Car {
     const float rho = q * rsqrtf(q);
     const float num = d >= 0.0f ? an : rho + ad;
     const float v = __fdividef(num, (an + rho) + ad);
-    constexpr float P[] = {-8.540411824e+01f, 1.562593909e+03f, -4.858328297e+02f, 1.212054441e+03f, -4.118799750e+02f, 5.340800569e+02f, 2.681955798e+01f, 1.439997149e+01f};
-    constexpr float Q[] = {2.627731536e+03f, 1.923390719e+03f, -1.496429105e+03f, 2.121401013e+03f, 9.330799874e+01f, 9.149840455e+01f, 8.619579532e-01f, 1.000000000e+00f};
-    const float2 pq = estrin_pq(P, Q, v);
-    return copysignf(__fdividef(v * pq.x, pq.y), n);
+    float P = -8.540411824e+01f;
+    P = fmaf(P, v, 1.562593909e+03f);
+    P = fmaf(P, v, -4.858328297e+02f);
+    P = fmaf(P, v, 1.212054441e+03f);
+    P = fmaf(P, v, -4.118799750e+02f);
+    P = fmaf(P, v, 5.340800569e+02f);
+    P = fmaf(P, v, 2.681955798e+01f);
+    P = fmaf(P, v, 1.439997149e+01f);
+    float Q = 2.627731536e+03f;
+    Q = fmaf(Q, v, 1.923390719e+03f);
+    Q = fmaf(Q, v, -1.496429105e+03f);
+    Q = fmaf(Q, v, 2.121401013e+03f);
+    Q = fmaf(Q, v, 9.330799874e+01f);
+    Q = fmaf(Q, v, 9.149840455e+01f);
+    Q = fmaf(Q, v, 8.619579532e-01f);
+    Q = fmaf(Q, v, 1.000000000e+00f);
+    return copysignf(__fdividef(v * P, Q), n);
   }
   // Velocity rates from the two lateral forces (shared by both step forms below).
   __device__ __forceinline__ static void vel_rates(float vx, float vy, float r, float delta, const float v[M],

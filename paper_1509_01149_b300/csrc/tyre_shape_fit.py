@@ -5,8 +5,7 @@ g(z) = sin(C atan z), z = B alpha, is evaluated on the whole real line through t
 variable v = |z| / (1 + |z|) in [0, 1]: z = v / (1 - v), so atan z = pi/2 - atan((1 - v) / v)
 is analytic on the closed interval (its nearest singularities sit at v = (1 +- i) / 2) and
 g = sign(z) v P(v) / Q(v) with P of degree 4 and Q of degree 5, Q(0) = 1.  That costs two
-reciprocals and a few FMAs (P and Q together by Estrin's scheme), with no branch, in place of
-an arctangent and a sine.
+reciprocals and ten FMAs, with no branch, in place of an arctangent and a sine.
 
 The slip shape h(t) = sin(C atan(B atan t)) is the same force as a function of t = tan alpha
 (|alpha| < pi/2).  The slip angle's own arctangent then drops out: the rear tyre's t is a

@@ -18,26 +18,11 @@ HEADER = ROOT / "paper_1509_01149_b300" / "csrc" / "systems.cuh"
 def _header_coefficients(signature="static float tyre_shape(float z)"):
     body = HEADER.read_text().split(signature)[1].split("return copysignf")[0]
 
-    def chain(name):   # "constexpr float P[] = {highest degree, ..., constant};"
-        lst = re.search(r"constexpr float %s\[\] = \{([^}]*)\};" % name, body).group(1)
-        return np.array([float(v.strip().rstrip("f")) for v in lst.split(",")][::-1])   # constant term first
+    def chain(name):
+        first = re.search(r"float %s = ([0-9.e+-]+)f;" % name, body).group(1)
+        rest = re.findall(r"%s = fmaf\(%s, v, ([0-9.e+-]+)f\);" % (name, name), body)
+        return np.array([float(v) for v in [first] + rest][::-1])   # constant term first
     return chain("P"), chain("Q")
-
-
-def _estrin_fp32(c, v):
-    """The kernel's polynomial evaluation in FP32 (c constant term first, degree <= 7): Estrin's
-    scheme, a_j = c_2j + c_2j+1 v, b = a_0 + a_1 v^2 (+ (a_2 + a_3 v^2) v^4), every step one
-    FMA (a single rounding) or one product."""
-    f = np.float32
-    v = np.asarray(v, f)
-    c = [np.full_like(v, f(x)) for x in list(c) + [0.0] * (8 - len(c))]
-
-    def fma(a, b, d):   # the product of two floats is exact in float64
-        return (a.astype(np.float64) * b.astype(np.float64) + d.astype(np.float64)).astype(f)
-    v2 = (v.astype(np.float64) * v).astype(f)
-    v4 = (v2.astype(np.float64) * v2).astype(f)
-    a = [fma(c[2 * j + 1], v, c[2 * j]) for j in range(4)]
-    return fma(fma(a[3], v2, a[2]), v4, fma(a[1], v2, a[0]))
 
 
 def _shape(z):
@@ -45,12 +30,17 @@ def _shape(z):
 
 
 def _kernel_fp32(P, Q, z):
-    """The header's evaluation in FP32: cap, v = a * (1 / (1 + a)), Estrin, v P * (1 / Q)."""
+    """The header's evaluation in FP32: cap, v = a * (1 / (1 + a)), Horner, v P * (1 / Q)."""
     f = np.float32
     z = np.asarray(z, f)
     a = np.where(np.abs(z) > f(1e30), f(1e30), np.abs(z)).astype(f)
     v = (a * (f(1) / (f(1) + a)).astype(f)).astype(f)
-    Pf, Qf = _estrin_fp32(P, v), _estrin_fp32(Q, v)
+    Pf = np.full_like(v, f(P[-1]))
+    for c in P[-2::-1]:
+        Pf = (Pf * v + f(c)).astype(f)
+    Qf = np.full_like(v, f(Q[-1]))
+    for c in Q[-2::-1]:
+        Qf = (Qf * v + f(c)).astype(f)
     return np.copysign(((v * Pf).astype(f) * (f(1) / Qf)).astype(f), z)
 
 
@@ -104,13 +94,19 @@ def _slip_exact(t):
 
 
 def _slip_kernel_fp32(P, Q, n, d):
-    """The header's evaluation in FP32: v = |n| * (1 / (|n| + d)), Estrin (FMA), v P * (1 / Q)."""
+    """The header's evaluation in FP32: v = |n| * (1 / (|n| + d)), Horner (FMA), v P * (1 / Q)."""
     f = np.float32
     n = np.asarray(n, f)
     d = np.asarray(d, f)
     an = np.abs(n)
     v = (an * (f(1) / (an + d)).astype(f)).astype(f)
-    return np.copysign(((v * _estrin_fp32(P, v)).astype(f) * (f(1) / _estrin_fp32(Q, v))).astype(f), n)
+
+    def horner(c):
+        acc = np.full_like(v, f(c[-1]))
+        for cj in c[-2::-1]:
+            acc = (acc.astype(np.float64) * v.astype(np.float64) + np.float64(f(cj))).astype(f)
+        return acc
+    return np.copysign(((v * horner(P)).astype(f) * (f(1) / horner(Q))).astype(f), n)
 
 
 def test_header_slip_rational_matches_on_the_whole_line():
@@ -151,7 +147,7 @@ def _angle_coefficients():
 
 def _angle_kernel_fp32(P, Q, n, d):
     """The header's evaluation in FP32: rho = q / sqrt(q), the half-angle numerator by the sign
-    of d, v = num * (1 / (|n| + rho + |d|)), Estrin (FMA), v P * (1 / Q), signed like n."""
+    of d, v = num * (1 / (|n| + rho + |d|)), Horner (FMA), v P * (1 / Q), signed like n."""
     f = np.float32
     n = np.asarray(n, f)
     d = np.asarray(d, f)
@@ -160,7 +156,13 @@ def _angle_kernel_fp32(P, Q, n, d):
     rho = (q * (f(1) / np.sqrt(q.astype(np.float64))).astype(f)).astype(f)
     num = np.where(d >= 0, an, (rho + ad).astype(f))
     v = (num * (f(1) / ((an + rho).astype(f) + ad).astype(f)).astype(f)).astype(f)
-    return np.copysign(((v * _estrin_fp32(P, v)).astype(f) * (f(1) / _estrin_fp32(Q, v))).astype(f), n)
+
+    def horner(c):
+        acc = np.full_like(v, f(c[-1]))
+        for cj in c[-2::-1]:
+            acc = (acc.astype(np.float64) * v.astype(np.float64) + np.float64(f(cj))).astype(f)
+        return acc
+    return np.copysign(((v * horner(P)).astype(f) * (f(1) / horner(Q))).astype(f), n)
 
 
 def test_header_angle_rational_matches_over_every_direction():
