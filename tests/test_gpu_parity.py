@@ -177,6 +177,33 @@ def test_car_extreme_steering_spans_the_tyre_curve(N):
         _check_iteration(cfg, g, o, ctrl=c)
 
 
+def test_car_front_slip_past_pi_matches_the_oracle(N):
+    """A slow sideways slide (vx = 1, vy = -3) at a steering angle of 2.5 rad puts the front slip
+    angle past pi (3.7 rad) for the first 17 steps of the nominal path with |delta| < 3, outside
+    the warp-role kernel's ratio form: its lanes redo those chunks with the arctangent form, the
+    one-thread kernel takes that form throughout; both agree with the oracle."""
+    from oracle import systems as osys
+    T = 40
+    U = np.zeros((T, 2))
+    U[:, 0], U[:, 1] = 5.0, 0.2
+    x0 = W.car_x0(0).copy()
+    x0[3], x0[4], x0[5], x0[6] = 1.0, -3.0, 0.0, 2.5
+    cfg = W.config(W.CAR, K=2048, T=T, U=U, lam=50.0, x0=x0)
+    car = osys.Car(cfg["dt"], W.car_cost_map(0), W.MAP_ORIGIN, W.MAP_H_CELL)
+    x = car.init(cfg["x0"], 1)
+    wrapped = 0
+    for i in range(T):
+        vxs = max(x[3, 0], car.p["vx_floor"])
+        a = x[6, 0] - math.atan((x[4, 0] + car.p["lf"] * x[5, 0]) / vxs)
+        wrapped += abs(a) > math.pi and abs(x[6, 0]) < 3.0
+        x = car.step(x, U[i][:, None])
+    assert wrapped >= 10, wrapped
+    for impl in (0, 1):
+        g, c = P.gpu_iteration(cfg, impl)
+        o = P.oracle_iteration(cfg)
+        _check_iteration(cfg, g, o, ctrl=c)
+
+
 def test_nonzero_controls_and_correlated_sigma(N):
     rng = np.random.default_rng(3)
     S = np.array([[0.3, 0.1], [0.1, 0.35]])
