@@ -165,12 +165,14 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
       if (!ok) break;
       float *vel = sVel + (c % R) * (C * 3 * NS);
       const int i0 = c * C;
-      if (i0 + C <= T) {
-        // the controls of all C steps first: the compiler cannot move a shared load above
+      // CN steps of the chunk through one unrolled body
+      auto core_chunk = [&](auto cn) {
+        constexpr int CN = decltype(cn)::value;
+        // the controls of all CN steps first: the compiler cannot move a shared load above
         // the velocity stores of earlier steps
-        float vv[C][M];
+        float vv[CN][M];
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
+        for (int j = 0; j < CN; ++j) {
           const int i = i0 + j;
           vv[j][0] = sU[i * M] + sDu[(i * M) * NS + slot];
           vv[j][1] = sU[i * M + 1] + sDu[(i * M + 1) * NS + slot];
@@ -181,17 +183,22 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
         const float xs[4] = {xv[0], xv[1], xv[2], xv[3]};
         bool in = true;
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
+        for (int j = 0; j < CN; ++j) {
           in &= Car::vel_step_ratio(xv, vv[j], p.dt);
           vel[(3 * j) * NS + slot] = xv[0];
           vel[(3 * j + 1) * NS + slot] = xv[1];
           vel[(3 * j + 2) * NS + slot] = xv[2];
         }
         if (__any_sync(__activemask(), !in) && !in) {
-          const CarVel r = car_vel_chunk_atan(CarVel{{xs[0], xs[1], xs[2], xs[3]}}, sU, sDu, vel, i0, C, NS, slot, p.dt);
+          const CarVel r = car_vel_chunk_atan(CarVel{{xs[0], xs[1], xs[2], xs[3]}}, sU, sDu, vel, i0, CN, NS, slot, p.dt);
 #pragma unroll
           for (int q = 0; q < 4; ++q) xv[q] = r.x[q];
         }
+      };
+      if (i0 + C <= T) {
+        core_chunk(std::integral_constant<int, C>{});
+      } else if (T - i0 == C / 2) {  // a half chunk at the end (T = 100): unrolled as well
+        core_chunk(std::integral_constant<int, C / 2>{});
       } else {
 #pragma unroll 1
         for (int j = 0; j < T - i0; ++j) {
@@ -259,21 +266,23 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
       if (!ok) break;
       const float *vel = sVel + (c % R) * (C * 3 * NS);
       const int i0 = c * C;
-      if (i0 + C <= T) {
-        float nv[C][3], is[C];
+      // CN steps of the chunk through one unrolled body
+      auto pose_chunk = [&](auto cn) {
+        constexpr int CN = decltype(cn)::value;
+        float nv[CN][3], is[CN];
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
+        for (int j = 0; j < CN; ++j) {
           nv[j][0] = vel[(3 * j) * NS + slot];
           nv[j][1] = vel[(3 * j + 1) * NS + slot];
           nv[j][2] = vel[(3 * j + 2) * NS + slot];
         }
         tc::mbar_arrive(&bar_empty[c % R]);
 #pragma unroll
-        for (int j = 0; j < C; ++j) is[j] = is_term(i0 + j);
-        // all C poses and their map loads first, then the C cost additions in step order
-        Car::Pending pq[C];
+        for (int j = 0; j < CN; ++j) is[j] = is_term(i0 + j);
+        // all CN poses and their map loads first, then the CN cost additions in step order
+        Car::Pending pq[CN];
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
+        for (int j = 0; j < CN; ++j) {
           Car::pose_step(X, Y, psi, aux, vx, vy, r, p.dt);
           vx = nv[j][0];
           vy = nv[j][1];
@@ -282,13 +291,18 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
           pq[j] = Car::cost_issue(xq, aux, env);
         }
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
+        for (int j = 0; j < CN; ++j) {
           const float cv = Car::cost_finish(pend, env) + pend_is;  // the term of step i0 + j - 1
           S.add(cv);
           if (TOGO && i0 + j > 0) sC[(i0 + j - 1) * NS + slot] = cv;
           pend = pq[j];
           pend_is = is[j];
         }
+      };
+      if (i0 + C <= T) {
+        pose_chunk(std::integral_constant<int, C>{});
+      } else if (T - i0 == C / 2) {  // a half chunk at the end (T = 100): unrolled as well
+        pose_chunk(std::integral_constant<int, C / 2>{});
       } else {
 #pragma unroll 1
         for (int j = 0; j < T - i0; ++j) {
