@@ -98,13 +98,17 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 template <int E>
 __device__ __forceinline__ void hidden_store(float v[32], const float *bias, float scale, unsigned char *smem, int row,
                                              int c0) {
+  static_assert(MlpLayout<E>::B % 16 == 0, "the biases are read as float4 vectors");
   const float2 sc = make_float2(scale, scale);
 #pragma unroll
-  for (int j = 0; j < 32; j += 2) {
-    const float2 b = *reinterpret_cast<const float2 *>(bias + c0 + j);
-    const float2 z = fma2(make_float2(v[j], v[j + 1]), sc, b);
-    v[j] = tc::tanh_approx(z.x);
-    v[j + 1] = tc::tanh_approx(z.y);
+  for (int j = 0; j < 32; j += 4) {
+    const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + j);
+    const float2 z0 = fma2(make_float2(v[j], v[j + 1]), sc, make_float2(b.x, b.y));
+    const float2 z1 = fma2(make_float2(v[j + 2], v[j + 3]), sc, make_float2(b.z, b.w));
+    v[j] = tc::tanh_approx(z0.x);
+    v[j + 1] = tc::tanh_approx(z0.y);
+    v[j + 2] = tc::tanh_approx(z1.x);
+    v[j + 3] = tc::tanh_approx(z1.y);
   }
   if (E == 2) {
 #pragma unroll
