@@ -17,7 +17,7 @@
 // Shared memory carries the hand-offs, in chunks of C steps:
 //   du  [T*M][NS]      noise -> core and pose, one single-use mbarrier per chunk (also the
 //                      operand of the block sums)
-//   vel [R][C][3][NS]  core -> pose, (vx, vy, r) after each step, a ring of R chunks with
+//   vel [R][C][3][NS]  core -> pose, (vx, vy, r) after each step, a ring of R chunks (car_ws_ring) with
 //                      full/empty mbarriers
 // With TOGO (the per-time-step cost-to-go weighting) the pose role also keeps each step's
 // term of S~ in sC [T][NS] and its terminal cost, and the block forms per-step partials.
@@ -36,13 +36,17 @@ namespace mppi {
 constexpr int kWsSamples = 128;   // samples per CTA (3x threads)
 constexpr int kWsRoles = 3;
 constexpr int kWsChunk = 8;       // steps per hand-off
-constexpr int kWsRing = 4;        // chunks in the velocity ring
+// Chunks in the velocity ring.  Two keep the shared memory of the path weighting (127 KB at
+// T = 100) and of the cost-to-go weighting inside smaller shared-memory configurations of the
+// SM, which leaves more L1 to the cost-map lookups; with the general sampling covariance two
+// would not reach the next configuration down, and four give the recurrence more run-ahead.
+__host__ __device__ constexpr int car_ws_ring(bool to_go, bool gen) { return gen && !to_go ? 4 : 2; }
 constexpr int kWsMaxChunks = 32;  // noise barriers: T <= kWsChunk * kWsMaxChunks
 
 __host__ __device__ inline size_t car_ws_smem_bytes(int T, int ns, bool to_go = false, bool gen = false) {
   const size_t TM = 2 * static_cast<size_t>(T);
   return sizeof(float) * (2 * TM + T + 2 * static_cast<size_t>(ns) + TM * ns +
-                          static_cast<size_t>(kWsRing) * kWsChunk * 3 * ns +
+                          static_cast<size_t>(car_ws_ring(to_go, gen)) * kWsChunk * 3 * ns +
                           (to_go ? (static_cast<size_t>(T) + 1) * ns : 0) + (gen ? 2 * TM * 2 : 0));
 }
 
@@ -77,7 +81,7 @@ __device__ __forceinline__ void rollout_block_car_ws(const CtrlParams &p, const 
                                                      DF *__restrict__ part_eta = nullptr) {
   static_assert(NS % 32 == 0, "roles must be warp-uniform");
   static_assert(kWsChunk % 4 == 0, "chunk 0 splits into two halves of whole Philox blocks");
-  constexpr int M = 2, C = kWsChunk, R = kWsRing, NT = kWsRoles * NS;
+  constexpr int M = 2, C = kWsChunk, R = car_ws_ring(TOGO, GEN), NT = kWsRoles * NS;
   __shared__ uint64_t bar_noise[kWsMaxChunks], bar_full[R], bar_empty[R];
   const int T = p.T, TM = T * M, tid = threadIdx.x;
   const int nch = (T + C - 1) / C;

@@ -142,11 +142,11 @@ def test_ragged_sizes(N, system, K, T):
         _check_iteration(cfg, g, o, margin_mask=mask, ctrl=c)
 
 
-@pytest.mark.parametrize("T", [148, 149])
+@pytest.mark.parametrize("T", [171, 172])
 def test_car_horizon_at_the_warp_role_limit(N, T):
     """The car's three-warp-role kernel keeps du for the whole horizon in shared memory; the
-    longest horizon that fits uses it (T = 148: 8-step chunks, a ragged last chunk of 4), the
-    next one falls back to the one-thread-per-sample kernel (T = 149).  Both match the oracle."""
+    longest horizon that fits uses it (T = 171: 8-step chunks, a ragged last chunk of 3), the
+    next one falls back to the one-thread-per-sample kernel (T = 172).  Both match the oracle."""
     cfg = W.config(W.CAR, K=700, T=T)
     g, c = P.gpu_iteration(cfg)
     o = P.oracle_iteration(cfg)
