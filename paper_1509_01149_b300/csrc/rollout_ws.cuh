@@ -38,8 +38,8 @@ constexpr int kWsRoles = 3;
 constexpr int kWsChunk = 8;       // steps per hand-off
 // Chunks in the velocity ring.  Two keep the shared memory of the path weighting (127 KB at
 // T = 100) and of the cost-to-go weighting inside smaller shared-memory configurations of the
-// SM, which leaves more L1 to the cost-map lookups; with the general sampling covariance two
-// would not reach the next configuration down, and four give the recurrence more run-ahead.
+// SM, which leaves more L1 to the cost-map lookups.  With the general sampling covariance two
+// and four measured the same; four are kept there.
 __host__ __device__ constexpr int car_ws_ring(bool to_go, bool gen) { return gen && !to_go ? 4 : 2; }
 constexpr int kWsMaxChunks = 32;  // noise barriers: T <= kWsChunk * kWsMaxChunks
 
