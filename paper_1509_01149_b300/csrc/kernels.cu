@@ -764,6 +764,7 @@ __global__ void k_philox_words(uint32_t key_lo, uint32_t key_hi, int K, int n_bl
 // ---------------------------------------------------------------------------
 size_t fused_smem_bytes(const CtrlParams &p, int blk) {
   if (blk == kFusedBlockCarWs) return car_ws_smem_bytes(p.T, kWsSamples, false, p.gen != nullptr);
+  if (blk == kFusedBlockCarWs32) return car_ws_smem_bytes(p.T, kWsSmallSamples, false, p.gen != nullptr);
   if (blk == kFusedBlockQuadLanes) return quad_lanes_smem_bytes(p.T, p.n_obs, kQuadLanesBlock / kQuadLanes);
   if (blk == kFusedBlockQuadWs)
     return quad_ws_smem_bytes(p.T, p.n_obs, kQwsSamples, quad_grid_bytes(p), p.gen != nullptr);
@@ -773,6 +774,11 @@ size_t fused_smem_bytes(const CtrlParams &p, int blk) {
 }
 
 int fused_block_size(int sys, const CtrlParams &p) {
+  // a small controller: 32 samples per CTA, so that its CTAs spread over the SMs and each
+  // role's warp has a scheduler to itself instead of sharing one with the other two roles
+  if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && shard_samples(p) <= kWsSmallMaxK &&
+      fused_smem_bytes(p, kFusedBlockCarWs32) <= kFusedSmemLimit)
+    return kFusedBlockCarWs32;
   if (sys == 1 && p.T <= kWsChunk * kWsMaxChunks && fused_smem_bytes(p, kFusedBlockCarWs) <= kFusedSmemLimit)
     return kFusedBlockCarWs;
   if (sys == 2 && p.gen && p.T <= kQwsChunk * kQwsMaxChunks && fused_smem_bytes(p, kFusedBlockQuadWs) <= kBigWsSmemLimit)
@@ -793,6 +799,7 @@ int fused_block_size(int sys, const CtrlParams &p) {
 
 int fused_block_samples(int blk) {
   if (blk == kFusedBlockCarWs) return kWsSamples;
+  if (blk == kFusedBlockCarWs32) return kWsSmallSamples;
   if (blk == kFusedBlockQuadLanes) return kQuadLanesBlock / kQuadLanes;
   if (blk == kFusedBlockQuadWs) return kQwsSamples;
   return blk == kFusedBlockRegen ? kFusedBlockLarge : blk;
@@ -822,14 +829,15 @@ static cudaError_t launch_fused_sys(int blk, const CtrlParams &p, const float *x
   return cudaErrorInvalidValue;
 }
 
+template <int NS>
 static cudaError_t launch_car_ws(const CtrlParams &p, const float *x0, const CtrlState *st, const float *U, float *S,
                                  float *ps, BlockPartial *part, cudaStream_t s) {
-  const size_t smem = car_ws_smem_bytes(p.T, kWsSamples, false, p.gen != nullptr);
-  const int grid = (shard_samples(p) + kWsSamples - 1) / kWsSamples;
+  const size_t smem = car_ws_smem_bytes(p.T, NS, false, p.gen != nullptr);
+  const int grid = (shard_samples(p) + NS - 1) / NS;
   if (p.gen)
-    k_rollout_car_ws<kWsSamples, true><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, ps, part);
+    k_rollout_car_ws<NS, true><<<grid, kWsRoles * NS, smem, s>>>(p, x0, st, U, S, ps, part);
   else
-    k_rollout_car_ws<kWsSamples><<<grid, kWsRoles * kWsSamples, smem, s>>>(p, x0, st, U, S, ps, part);
+    k_rollout_car_ws<NS><<<grid, kWsRoles * NS, smem, s>>>(p, x0, st, U, S, ps, part);
   return cudaGetLastError();
 }
 
@@ -839,7 +847,8 @@ cudaError_t launch_rollout_fused(int sys, int blk, const CtrlParams &p, const fl
     case 0: return launch_fused_sys<CartPole>(blk, p, x0, st, U, S, part_sums, part, s);
     case 4: return launch_fused_sys<CartPoleVel>(blk, p, x0, st, U, S, part_sums, part, s);
     case 1:
-      if (blk == kFusedBlockCarWs) return launch_car_ws(p, x0, st, U, S, part_sums, part, s);
+      if (blk == kFusedBlockCarWs) return launch_car_ws<kWsSamples>(p, x0, st, U, S, part_sums, part, s);
+      if (blk == kFusedBlockCarWs32) return launch_car_ws<kWsSmallSamples>(p, x0, st, U, S, part_sums, part, s);
       return launch_fused_sys<Car>(blk, p, x0, st, U, S, part_sums, part, s);
     case 2:
       if (blk == kFusedBlockQuadWs) {
@@ -999,6 +1008,8 @@ cudaError_t prepare_kernels() {
       reinterpret_cast<const void *>(k_rollout_fused<Quad, kFusedBlockLarge, true>),
       reinterpret_cast<const void *>(k_merge_update<false>),
       reinterpret_cast<const void *>(k_merge_update<true>),
+      reinterpret_cast<const void *>(k_rollout_car_ws<kWsSmallSamples>),
+      reinterpret_cast<const void *>(k_rollout_car_ws<kWsSmallSamples, true>),
   };
   for (const void *f : fns) {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

@@ -11,6 +11,9 @@ constexpr int kFusedBlockLarge = 128;
 constexpr int kFusedBlockSmall = 64;
 constexpr int kFusedBlockRegen = 129;   // code for "128 samples, du regenerated (no shared-memory copy)"
 constexpr int kFusedBlockCarWs = 257;   // code for "car, 128 samples, three threads per sample"
+constexpr int kFusedBlockCarWs32 = 258;  // code for "car, 32 samples, three threads per sample" (small K)
+constexpr int kWsSmallSamples = 32;
+constexpr int kWsSmallMaxK = 148 * kWsSmallSamples;  // up to one 32-sample CTA per SM of a B300
 constexpr int kFusedBlockQuadLanes = 513;  // code for "quadrotor, 32 samples, a group of lanes per sample"
 constexpr int kFusedBlockQuadWs = 1025;    // code for "quadrotor, 64 samples, three warp roles"
 constexpr int kQuadLanesBlock = 64, kQuadLanes = 2;
